@@ -1,0 +1,144 @@
+"""Plain FP64 oracle: hybrid-smoothed AMGe V-cycle and PCG.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Every step follows the
+paper in its own order; library primitives (sparse matrix-vector products, a
+dense Cholesky factorisation) serve as single steps, with no fusion or reordering.
+
+  * Algorithm 4.1 (Section 4): the V-cycle -- pre-relax, restrict the residual with
+    P^T, recurse (or solve on the coarsest level), prolong with P, post-relax with
+    the transposed smoother.  Called with x0 = 0 as the PCG preconditioner.
+  * Eq. 4.1 (Section 4.1): one hybrid smoothing step = a point sweep on A_l, then a
+    point sweep on the auxiliary matrix G^T A_l G reached through the exterior
+    derivative G (D_0 for H(curl), D_1 for H(div)), corrected back through G.  The
+    transposed step runs the two sweeps in the reverse order.
+  * Point smoother: l1-Jacobi, M = diag(sum_j |a_ij|) (the l1-scaled point variant
+    the paper cites in Section 4.1; this build's smoother choice).
+  * Coarsest level: dense FP64 Cholesky solve (in place of the paper's AMS/ADS).
+  * PCG (Sections 4 and 5.1): preconditioned conjugate gradients with x0 = 0 and
+    one V-cycle per iteration; stop on the true FP64 relative residual
+    ||b - A x|| / ||b|| <= rtol (residual replaced by the true one when the
+    recursive residual first meets the tolerance).
+"""
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+
+def l1_row_sums(A) -> np.ndarray:
+    """m_i = sum_j |a_ij|: the l1-Jacobi diagonal (Section 4.1 point smoother)."""
+    return np.asarray(abs(A).sum(axis=1)).ravel()
+
+
+class OracleHierarchy:
+    """The solve-phase operators of an AMGe hierarchy, in scipy FP64.
+
+    A: list of level matrices (level 0 finest); P[l]: level l+1 -> level l;
+    G[l]: exterior derivative into the problem space at level l (aux transition).
+    """
+
+    def __init__(self, A, P, G, nu_pre: int = 1, nu_post: int = 1):
+        self.A = [sp.csr_matrix(a, dtype=np.float64) for a in A]
+        self.P = [sp.csr_matrix(p, dtype=np.float64) for p in P]
+        self.G = [sp.csr_matrix(g, dtype=np.float64) for g in G]
+        self.L = len(self.A)
+        self.nu_pre, self.nu_post = nu_pre, nu_post
+        # smoother data of every smoothing level (all but the coarsest)
+        self.m = [l1_row_sums(self.A[l]) for l in range(self.L - 1)]
+        self.A_aux = [(self.G[l].T @ self.A[l] @ self.G[l]).tocsr() for l in range(self.L - 1)]
+        self.m_aux = [l1_row_sums(self.A_aux[l]) for l in range(self.L - 1)]
+        # coarsest level: dense Cholesky factor
+        Ac = self.A[-1].toarray()
+        self.coarse_factor = sla.cho_factor(Ac, lower=True)
+
+    @classmethod
+    def from_hierarchy(cls, h, nu_pre: int = 1, nu_post: int = 1):
+        return cls([a.to_scipy() for a in h.A], [p.to_scipy() for p in h.P],
+                   [g.to_scipy() for g in h.G], nu_pre, nu_post)
+
+    # ---------------------------------------------------------------- smoothers
+    def _point(self, l, x, b):
+        """x <- x + M^{-1} (b - A x), M = l1 diagonal (symmetric, so M^{-T} = M^{-1})."""
+        return x + _div(b - self.A[l] @ x, self.m[l])
+
+    def _aux(self, l, x, b):
+        """x <- x + G M_aux^{-1} G^T (b - A x) (second line of eq. 4.1)."""
+        G = self.G[l]
+        return x + G @ _div(G.T @ (b - self.A[l] @ x), self.m_aux[l])
+
+    def hybrid(self, l, x, b):
+        """One step of eq. 4.1: point sweep on A_l, then the auxiliary sweep."""
+        x = self._point(l, x, b)
+        return self._aux(l, x, b)
+
+    def hybrid_transposed(self, l, x, b):
+        """The transposed step: the two sweeps of eq. 4.1 in reverse order."""
+        x = self._aux(l, x, b)
+        return self._point(l, x, b)
+
+    # ---------------------------------------------------------------- V-cycle
+    def coarse_solve(self, b):
+        return sla.cho_solve(self.coarse_factor, b)
+
+    def vcycle(self, b, l: int = 0, x0=None):
+        """Algorithm 4.1 at level l: returns x = x0 + B^{-1}(b - A x0) (x0 = 0 default)."""
+        if self.L == 1:
+            return self.coarse_solve(b)
+        x = np.zeros_like(b) if x0 is None else x0.copy()
+        for _ in range(self.nu_pre):                      # pre-relax
+            x = self.hybrid(l, x, b)
+        r_c = self.P[l].T @ (b - self.A[l] @ x)           # restrict the residual
+        if l + 1 == self.L - 1:                           # coarsest level reached
+            e_c = self.coarse_solve(r_c)
+        else:
+            e_c = self.vcycle(r_c, l + 1)
+        x = x + self.P[l] @ e_c                           # correct
+        for _ in range(self.nu_post):                     # post-relax with M^{-T}
+            x = self.hybrid_transposed(l, x, b)
+        return x
+
+    def apply(self, r):
+        """The preconditioner B^{-1} r: one V-cycle from x0 = 0 at the finest level."""
+        return self.vcycle(r, 0)
+
+
+def _div(v, d):
+    return v / d if v.ndim == 1 else v / d[:, None]
+
+
+def pcg(h: OracleHierarchy, b, rtol: float = 1e-8, maxit: int = 1000):
+    """PCG with one V-cycle per iteration, x0 = 0 (Section 4, Section 5.1).
+
+    Returns (x, iterations, true relative residual, converged).  The iteration count
+    is the number of products A p.
+    """
+    A = h.A[0]
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, 0.0, True
+    r = b.copy()
+    z = h.apply(r)
+    p = z.copy()
+    rho = r @ z
+    it = 0
+    converged = False
+    while it < maxit:
+        q = A @ p
+        alpha = rho / (p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        it += 1
+        if np.linalg.norm(r) <= rtol * bnorm:
+            r_true = b - A @ x
+            if np.linalg.norm(r_true) <= rtol * bnorm:
+                converged = True
+                break
+            r = r_true
+        z = h.apply(r)
+        rho_new = r @ z
+        beta = rho_new / rho
+        p = z + beta * p
+        rho = rho_new
+    relres = np.linalg.norm(b - A @ x) / bnorm
+    return x, it, relres, converged

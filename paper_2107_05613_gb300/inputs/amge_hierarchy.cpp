@@ -1,0 +1,1363 @@
+// Host FP64 generator of AMGe de Rham hierarchies (input data for the solve phase).
+//
+// Section 2 of the paper: lowest-order conforming spaces (one dof per mesh entity),
+// the H(curl)/H(div) forms of eq. 2.2 and the discrete de Rham complex of eq. 2.3 whose
+// exterior derivatives are signed incidences.  Section 3.1: agglomerates, coarse facets,
+// edges and vertices by the intersection procedure, with +-1 orientation vectors.
+// Section 3.3: PV traces (eq. 3.5) extended by the local saddle-point problems of
+// eq. 3.6 (first extension) and eq. 3.8 (further extensions), built in the order
+// L2 -> H(div) -> H(curl) -> H1.  Section 3.2.1: element-based RAP for coarse local
+// and global matrices.
+//
+// Everything is double precision and sequential per entity; entities are processed
+// in parallel with OpenMP (each prolongator entry is written by exactly one task).
+#include "amge_hierarchy.h"
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+thread_local std::string g_err;
+
+bool verbose() {
+  static int v = -1;
+  if (v < 0) v = std::getenv("AMGH_VERBOSE") ? 1 : 0;
+  return v == 1;
+}
+struct Stage {
+  const char* name;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  explicit Stage(const char* n) : name(n) {}
+  ~Stage() {
+    if (verbose())
+      std::fprintf(stderr, "[amgh] %-28s %8.3f s\n", name,
+                   std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+  }
+};
+
+struct Fail : std::runtime_error {
+  explicit Fail(const std::string& s) : std::runtime_error(s) {}
+};
+#define REQUIRE(cond, msg)                                                   \
+  do {                                                                       \
+    if (!(cond)) throw Fail(std::string(msg) + " [" #cond "]");              \
+  } while (0)
+
+// ---------------------------------------------------------------- sparse containers
+struct Adj {  // row -> sorted column list
+  std::vector<int64_t> rp{0};
+  std::vector<int> ci;
+  int rows() const { return (int)rp.size() - 1; }
+  int len(int r) const { return (int)(rp[r + 1] - rp[r]); }
+  const int* row(int r) const { return ci.data() + rp[r]; }
+  int find(int r, int c) const {  // position within row, or -1
+    const int* b = row(r);
+    const int* e = b + len(r);
+    const int* p = std::lower_bound(b, e, c);
+    return (p != e && *p == c) ? (int)(p - b) : -1;
+  }
+};
+
+struct ICsr {  // signed integer incidence
+  int nr = 0, nc = 0;
+  Adj a;
+  std::vector<int8_t> v;
+  int8_t get(int r, int c) const {
+    int p = a.find(r, c);
+    return p < 0 ? 0 : v[a.rp[r] + p];
+  }
+};
+
+struct DCsr {
+  int nr = 0, nc = 0;
+  Adj a;
+  std::vector<double> v;
+  double get(int r, int c) const {
+    int p = a.find(r, c);
+    return p < 0 ? 0.0 : v[a.rp[r] + p];
+  }
+};
+
+Adj transpose_adj(const Adj& A, int ncols) {
+  Adj T;
+  T.rp.assign(ncols + 1, 0);
+  for (int c : A.ci) T.rp[c + 1]++;
+  for (int i = 0; i < ncols; i++) T.rp[i + 1] += T.rp[i];
+  T.ci.resize(A.ci.size());
+  std::vector<int64_t> pos(T.rp.begin(), T.rp.end() - 1);
+  for (int r = 0; r < A.rows(); r++)
+    for (int64_t p = A.rp[r]; p < A.rp[r + 1]; p++) T.ci[pos[A.ci[p]]++] = r;
+  return T;
+}
+
+ICsr transpose_i(const ICsr& A) {
+  ICsr T;
+  T.nr = A.nc;
+  T.nc = A.nr;
+  T.a.rp.assign(A.nc + 1, 0);
+  for (int c : A.a.ci) T.a.rp[c + 1]++;
+  for (int i = 0; i < A.nc; i++) T.a.rp[i + 1] += T.a.rp[i];
+  T.a.ci.resize(A.a.ci.size());
+  T.v.resize(A.v.size());
+  std::vector<int64_t> pos(T.a.rp.begin(), T.a.rp.end() - 1);
+  for (int r = 0; r < A.nr; r++)
+    for (int64_t p = A.a.rp[r]; p < A.a.rp[r + 1]; p++) {
+      int64_t q = pos[A.a.ci[p]]++;
+      T.a.ci[q] = r;
+      T.v[q] = A.v[p];
+    }
+  return T;
+}
+
+// rows of `outer` (d -> d-1) composed with `inner` (d-1 -> k): sorted unique union
+Adj compose_union(const Adj& outer, const Adj& inner) {
+  Adj R;
+  int n = outer.rows();
+  R.rp.assign(n + 1, 0);
+  std::vector<std::vector<int>> rows(n);
+#pragma omp parallel for schedule(static)
+  for (int r = 0; r < n; r++) {
+    std::vector<int>& s = rows[r];
+    for (int64_t p = outer.rp[r]; p < outer.rp[r + 1]; p++) {
+      int m = outer.ci[p];
+      s.insert(s.end(), inner.row(m), inner.row(m) + inner.len(m));
+    }
+    std::sort(s.begin(), s.end());
+    s.erase(std::unique(s.begin(), s.end()), s.end());
+  }
+  for (int r = 0; r < n; r++) R.rp[r + 1] = R.rp[r] + (int64_t)rows[r].size();
+  R.ci.resize(R.rp[n]);
+  for (int r = 0; r < n; r++) std::copy(rows[r].begin(), rows[r].end(), R.ci.begin() + R.rp[r]);
+  return R;
+}
+
+// ---------------------------------------------------------------- dense helpers
+// Solve A X = B with partial pivoting; A n x n row-major (destroyed), B n x m row-major.
+bool lu_solve(int n, double* A, int m, double* B) {
+  for (int k = 0; k < n; k++) {
+    int piv = k;
+    double best = std::fabs(A[(size_t)k * n + k]);
+    for (int i = k + 1; i < n; i++) {
+      double v = std::fabs(A[(size_t)i * n + k]);
+      if (v > best) best = v, piv = i;
+    }
+    if (best == 0.0) return false;
+    if (piv != k) {
+      for (int j = 0; j < n; j++) std::swap(A[(size_t)k * n + j], A[(size_t)piv * n + j]);
+      for (int j = 0; j < m; j++) std::swap(B[(size_t)k * m + j], B[(size_t)piv * m + j]);
+    }
+    double inv = 1.0 / A[(size_t)k * n + k];
+    for (int i = k + 1; i < n; i++) {
+      double f = A[(size_t)i * n + k] * inv;
+      if (f == 0.0) continue;
+      A[(size_t)i * n + k] = f;
+      for (int j = k + 1; j < n; j++) A[(size_t)i * n + j] -= f * A[(size_t)k * n + j];
+      for (int j = 0; j < m; j++) B[(size_t)i * m + j] -= f * B[(size_t)k * m + j];
+    }
+  }
+  for (int k = n - 1; k >= 0; k--) {
+    double inv = 1.0 / A[(size_t)k * n + k];
+    for (int j = 0; j < m; j++) {
+      double s = B[(size_t)k * m + j];
+      for (int i = k + 1; i < n; i++) s -= A[(size_t)k * n + i] * B[(size_t)i * m + j];
+      B[(size_t)k * m + j] = s * inv;
+    }
+  }
+  return true;
+}
+
+inline double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+inline void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+const int kEdgeLoc[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+const int kFaceLoc[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+const int kTriEdge[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+const int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+// Whitney element matrices of one tetrahedron with vertices p[0..3] in increasing global
+// index order (edges and faces oriented by increasing vertex index).
+struct TetMats {
+  double vol;
+  double M0[16], M1[36], M2[16], M3;  // H1, Nedelec, RT, P0 masses
+  double K1[36], K2[16];              // (curl, curl) and (div, div)
+};
+
+TetMats tet_mats(const double p[4][3]) {
+  TetMats t;
+  double J[3][3];
+  for (int c = 0; c < 3; c++)
+    for (int r = 0; r < 3; r++) J[r][c] = p[c + 1][r] - p[0][r];
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+               J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  t.vol = std::fabs(det) / 6.0;
+  double inv[3][3];
+  inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  double g[4][3];  // gradients of barycentric coordinates
+  for (int c = 0; c < 3; c++)
+    for (int r = 0; r < 3; r++) g[c + 1][r] = inv[c][r];
+  for (int r = 0; r < 3; r++) g[0][r] = -(g[1][r] + g[2][r] + g[3][r]);
+  double I[4][4];  // integral of lambda_a lambda_b
+  for (int a = 0; a < 4; a++)
+    for (int b = 0; b < 4; b++) I[a][b] = t.vol * (a == b ? 2.0 : 1.0) / 20.0;
+  for (int a = 0; a < 4; a++)
+    for (int b = 0; b < 4; b++) t.M0[a * 4 + b] = I[a][b];
+  // Nedelec: w_ij = l_i grad l_j - l_j grad l_i
+  for (int e = 0; e < 6; e++)
+    for (int f = 0; f < 6; f++) {
+      int i = kEdgeLoc[e][0], j = kEdgeLoc[e][1], k = kEdgeLoc[f][0], l = kEdgeLoc[f][1];
+      t.M1[e * 6 + f] = I[i][k] * dot3(g[j], g[l]) - I[i][l] * dot3(g[j], g[k]) -
+                        I[j][k] * dot3(g[i], g[l]) + I[j][l] * dot3(g[i], g[k]);
+      double ce[3], cf[3];
+      cross3(g[i], g[j], ce);
+      cross3(g[k], g[l], cf);
+      t.K1[e * 6 + f] = t.vol * 4.0 * dot3(ce, cf);
+    }
+  // Raviart-Thomas: w_ijk = 2 (l_i gl_j x gl_k + l_j gl_k x gl_i + l_k gl_i x gl_j)
+  double cf[4][3][3];  // per face, per vertex slot: the cross product multiplying lambda
+  int fv[4][3];
+  double divw[4];
+  for (int f = 0; f < 4; f++) {
+    int i = kFaceLoc[f][0], j = kFaceLoc[f][1], k = kFaceLoc[f][2];
+    fv[f][0] = i, fv[f][1] = j, fv[f][2] = k;
+    cross3(g[j], g[k], cf[f][0]);
+    cross3(g[k], g[i], cf[f][1]);
+    cross3(g[i], g[j], cf[f][2]);
+    divw[f] = 2.0 * (dot3(g[i], cf[f][0]) + dot3(g[j], cf[f][1]) + dot3(g[k], cf[f][2]));
+  }
+  for (int f = 0; f < 4; f++)
+    for (int h = 0; h < 4; h++) {
+      double s = 0;
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) s += I[fv[f][a]][fv[h][b]] * dot3(cf[f][a], cf[h][b]);
+      t.M2[f * 4 + h] = 4.0 * s;
+      t.K2[f * 4 + h] = t.vol * divw[f] * divw[h];
+    }
+  t.M3 = 1.0 / t.vol;
+  return t;
+}
+
+// ---------------------------------------------------------------- level data
+struct Level {
+  int m = 0;                 // cells per side of the agglomeration grid
+  int64_t cnt[4] = {0, 0, 0, 0};
+  ICsr D[3];                 // D[k]: cnt[k+1] x cnt[k]
+  ICsr DT[3];
+  std::vector<int8_t> face_side;  // -1 interior, else boundary side 0..5
+  std::vector<int> cell_ijk;      // 3 ints per cell
+  Adj clo[4][4];                  // clo[d][k] (k < d): sub-entities of dim k, sorted
+  // finest level geometry
+  bool fine = false;
+  int n = 0;
+  std::vector<double> beta, alpha;  // per fine tet
+  TetMats perm_mats[6];             // the six Kuhn tets are translates of six shapes
+  // coarse levels: stored local matrices (dense, row-major, closure order)
+  std::vector<double> lm[4][4];
+  std::vector<int64_t> lmoff[4][4];
+  std::vector<double> la;
+  std::vector<int64_t> laoff;
+};
+
+int local_size(const Level& L, int d, int k, int x) { return k == d ? 1 : L.clo[d][k].len(x); }
+
+void vert_coord(const Level& L, int v, double* x) {
+  int n1 = L.n + 1;
+  x[0] = (double)(v / (n1 * n1)) / L.n;
+  x[1] = (double)((v / n1) % n1) / L.n;
+  x[2] = (double)(v % n1) / L.n;
+}
+
+// Finest-level trace matrices on a triangle (k = 0 H1 trace, 1 tangential Nedelec
+// trace, 2 normal-flux trace) and on a segment (k = 0 H1 trace, 1 tangential trace).
+void fine_face_mat(const Level& L, int f, int k, double* out) {
+  const int* vv = L.clo[2][0].row(f);
+  double q[3][3];
+  for (int a = 0; a < 3; a++) vert_coord(L, vv[a], q[a]);
+  double e1[3], e2[3], nrm[3];
+  for (int r = 0; r < 3; r++) e1[r] = q[1][r] - q[0][r], e2[r] = q[2][r] - q[0][r];
+  cross3(e1, e2, nrm);
+  double area = 0.5 * std::sqrt(dot3(nrm, nrm));
+  if (k == 2) {
+    out[0] = 1.0 / area;
+    return;
+  }
+  double I[3][3];
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) I[a][b] = area * (a == b ? 2.0 : 1.0) / 12.0;
+  if (k == 0) {
+    for (int a = 0; a < 9; a++) out[a] = I[a / 3][a % 3];
+    return;
+  }
+  double G00 = dot3(e1, e1), G01 = dot3(e1, e2), G11 = dot3(e2, e2);
+  double det = G00 * G11 - G01 * G01;
+  double i00 = G11 / det, i01 = -G01 / det, i11 = G00 / det;
+  double g[3][3];
+  for (int r = 0; r < 3; r++) {
+    g[1][r] = i00 * e1[r] + i01 * e2[r];
+    g[2][r] = i01 * e1[r] + i11 * e2[r];
+    g[0][r] = -(g[1][r] + g[2][r]);
+  }
+  for (int e = 0; e < 3; e++)
+    for (int h = 0; h < 3; h++) {
+      int i = kTriEdge[e][0], j = kTriEdge[e][1], a = kTriEdge[h][0], b = kTriEdge[h][1];
+      out[e * 3 + h] = I[i][a] * dot3(g[j], g[b]) - I[i][b] * dot3(g[j], g[a]) -
+                       I[j][a] * dot3(g[i], g[b]) + I[j][b] * dot3(g[i], g[a]);
+    }
+}
+
+void fine_edge_mat(const Level& L, int e, int k, double* out) {
+  const int* vv = L.clo[1][0].row(e);
+  double a[3], b[3];
+  vert_coord(L, vv[0], a);
+  vert_coord(L, vv[1], b);
+  double d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double len = std::sqrt(dot3(d, d));
+  if (k == 1) {
+    out[0] = 1.0 / len;
+    return;
+  }
+  out[0] = out[3] = len / 3.0;
+  out[1] = out[2] = len / 6.0;
+}
+
+// Local trace mass of space k on entity x of dimension d, in closure order.
+void local_mass(const Level& L, int d, int k, int x, double* out) {
+  if (!L.fine) {
+    int s = local_size(L, d, k, x);
+    const double* src = L.lm[d][k].data() + L.lmoff[d][k][x];
+    std::copy(src, src + (size_t)s * s, out);
+    return;
+  }
+  if (d == 3) {
+    const TetMats& t = L.perm_mats[x % 6];
+    if (k == 0) std::copy(t.M0, t.M0 + 16, out);
+    else if (k == 1) std::copy(t.M1, t.M1 + 36, out);
+    else if (k == 2) std::copy(t.M2, t.M2 + 16, out);
+    else out[0] = t.M3;
+  } else if (d == 2) {
+    fine_face_mat(L, x, k, out);
+  } else if (d == 1) {
+    fine_edge_mat(L, x, k, out);
+  } else {
+    out[0] = 1.0;
+  }
+}
+
+// Local problem matrix (eq. 2.2) on cell x: beta (Du, Dv) + alpha (u, v) for space kf.
+void local_form(const Level& L, int kf, int x, double* out) {
+  if (!L.fine) {
+    int s = local_size(L, 3, kf, x);
+    const double* src = L.la.data() + L.laoff[x];
+    std::copy(src, src + (size_t)s * s, out);
+    return;
+  }
+  const TetMats& t = L.perm_mats[x % 6];
+  double b = L.beta[x], a = L.alpha[x];
+  if (kf == 1)
+    for (int i = 0; i < 36; i++) out[i] = b * t.K1[i] + a * t.M1[i];
+  else
+    for (int i = 0; i < 16; i++) out[i] = b * t.K2[i] + a * t.M2[i];
+}
+
+void build_closures(Level& L) {
+  for (int d = 1; d <= 3; d++) L.clo[d][d - 1] = L.D[d - 1].a;
+  L.clo[2][0] = compose_union(L.clo[2][1], L.clo[1][0]);
+  L.clo[3][1] = compose_union(L.clo[3][2], L.clo[2][1]);
+  L.clo[3][0] = compose_union(L.clo[3][1], L.clo[1][0]);
+}
+
+// ---------------------------------------------------------------- finest level
+void build_fine(Level& L, int n, const double* beta, const double* alpha) {
+  L.fine = true;
+  L.n = n;
+  L.m = n;
+  const int64_t n1 = n + 1, NV = n1 * n1 * n1, NT = 6LL * n * n * n;
+  REQUIRE(NV < (1LL << 21), "mesh too large for 63-bit face keys");
+  auto vid = [&](int i, int j, int k) { return (int)((i * n1 + j) * n1 + k); };
+  std::vector<std::array<int, 4>> tv(NT);
+  L.cell_ijk.resize(3 * NT);
+  for (int a = 0; a < n; a++)
+    for (int b = 0; b < n; b++)
+      for (int c = 0; c < n; c++) {
+        int64_t cube = ((int64_t)a * n + b) * n + c;
+        for (int p = 0; p < 6; p++) {
+          int ijk[3] = {a, b, c};
+          std::array<int, 4> t;
+          t[0] = vid(ijk[0], ijk[1], ijk[2]);
+          ijk[kPerm[p][0]]++;
+          t[1] = vid(ijk[0], ijk[1], ijk[2]);
+          ijk[kPerm[p][1]]++;
+          t[2] = vid(ijk[0], ijk[1], ijk[2]);
+          t[3] = vid(a + 1, b + 1, c + 1);
+          int64_t id = cube * 6 + p;
+          tv[id] = t;
+          L.cell_ijk[3 * id] = a, L.cell_ijk[3 * id + 1] = b, L.cell_ijk[3 * id + 2] = c;
+        }
+      }
+  // edges and faces: sorted unique vertex tuples
+  std::vector<int64_t> ek(6 * NT), fk(4 * NT);
+#pragma omp parallel for schedule(static)
+  for (int64_t t = 0; t < NT; t++) {
+    for (int e = 0; e < 6; e++) ek[6 * t + e] = (int64_t)tv[t][kEdgeLoc[e][0]] * NV + tv[t][kEdgeLoc[e][1]];
+    for (int f = 0; f < 4; f++)
+      fk[4 * t + f] = ((int64_t)tv[t][kFaceLoc[f][0]] * NV + tv[t][kFaceLoc[f][1]]) * NV + tv[t][kFaceLoc[f][2]];
+  }
+  std::vector<int64_t> eu = ek, fu = fk;
+  std::sort(eu.begin(), eu.end());
+  eu.erase(std::unique(eu.begin(), eu.end()), eu.end());
+  std::sort(fu.begin(), fu.end());
+  fu.erase(std::unique(fu.begin(), fu.end()), fu.end());
+  const int64_t NE = eu.size(), NF = fu.size();
+  L.cnt[0] = NV, L.cnt[1] = NE, L.cnt[2] = NF, L.cnt[3] = NT;
+  auto eid = [&](int a, int b) {
+    return (int)(std::lower_bound(eu.begin(), eu.end(), (int64_t)a * NV + b) - eu.begin());
+  };
+  // D0 (grad): edge (a<b) = -a + b
+  ICsr& D0 = L.D[0];
+  D0.nr = NE, D0.nc = NV;
+  D0.a.rp.resize(NE + 1);
+  D0.a.ci.resize(2 * NE);
+  D0.v.resize(2 * NE);
+  for (int64_t e = 0; e < NE; e++) {
+    D0.a.rp[e] = 2 * e;
+    D0.a.ci[2 * e] = (int)(eu[e] / NV), D0.v[2 * e] = -1;
+    D0.a.ci[2 * e + 1] = (int)(eu[e] % NV), D0.v[2 * e + 1] = 1;
+  }
+  D0.a.rp[NE] = 2 * NE;
+  // D1 (curl): face (a<b<c) has boundary [a,b] + [b,c] - [a,c]
+  ICsr& D1 = L.D[1];
+  D1.nr = NF, D1.nc = NE;
+  D1.a.rp.resize(NF + 1);
+  D1.a.ci.resize(3 * NF);
+  D1.v.resize(3 * NF);
+#pragma omp parallel for schedule(static)
+  for (int64_t f = 0; f < NF; f++) {
+    int a = (int)(fu[f] / (NV * NV)), b = (int)((fu[f] / NV) % NV), c = (int)(fu[f] % NV);
+    D1.a.rp[f] = 3 * f;
+    D1.a.ci[3 * f] = eid(a, b), D1.v[3 * f] = 1;
+    D1.a.ci[3 * f + 1] = eid(a, c), D1.v[3 * f + 1] = -1;
+    D1.a.ci[3 * f + 2] = eid(b, c), D1.v[3 * f + 2] = 1;
+  }
+  D1.a.rp[NF] = 3 * NF;
+  // D2 (div): +1 where the face normal (x_b - x_a) x (x_c - x_a) points out of the tet
+  ICsr& D2 = L.D[2];
+  D2.nr = NT, D2.nc = NF;
+  D2.a.rp.resize(NT + 1);
+  D2.a.ci.resize(4 * NT);
+  D2.v.resize(4 * NT);
+#pragma omp parallel for schedule(static)
+  for (int64_t t = 0; t < NT; t++) {
+    D2.a.rp[t] = 4 * t;
+    double p[4][3];
+    for (int a = 0; a < 4; a++) vert_coord(L, tv[t][a], p[a]);
+    for (int f = 0; f < 4; f++) {
+      int64_t key = fk[4 * t + f];
+      D2.a.ci[4 * t + f] = (int)(std::lower_bound(fu.begin(), fu.end(), key) - fu.begin());
+      const int* lv = kFaceLoc[f];
+      int opp = 6 - lv[0] - lv[1] - lv[2];
+      double e1[3], e2[3], nr[3], out[3];
+      for (int r = 0; r < 3; r++) {
+        e1[r] = p[lv[1]][r] - p[lv[0]][r];
+        e2[r] = p[lv[2]][r] - p[lv[0]][r];
+        out[r] = p[lv[0]][r] - p[opp][r];
+      }
+      cross3(e1, e2, nr);
+      D2.v[4 * t + f] = dot3(nr, out) > 0 ? 1 : -1;
+    }
+  }
+  D2.a.rp[NT] = 4 * NT;
+  for (int k = 0; k < 3; k++) L.DT[k] = transpose_i(L.D[k]);
+  build_closures(L);
+  // boundary side of each face (natural boundary conditions: attributes only)
+  L.face_side.assign(NF, -1);
+  for (int64_t f = 0; f < NF; f++) {
+    if (L.DT[2].a.len((int)f) != 1) continue;
+    const int* vv = L.clo[2][0].row((int)f);
+    int c[3][3];
+    for (int a = 0; a < 3; a++) {
+      c[a][0] = (int)(vv[a] / (n1 * n1)), c[a][1] = (int)((vv[a] / n1) % n1), c[a][2] = (int)(vv[a] % n1);
+    }
+    int side = -1;
+    for (int ax = 0; ax < 3 && side < 0; ax++) {
+      if (c[0][ax] == 0 && c[1][ax] == 0 && c[2][ax] == 0) side = 2 * ax;
+      else if (c[0][ax] == n && c[1][ax] == n && c[2][ax] == n) side = 2 * ax + 1;
+    }
+    REQUIRE(side >= 0, "boundary face not on a cube side");
+    L.face_side[f] = (int8_t)side;
+  }
+  // element matrices of the six Kuhn tetrahedra of the first cube (translation invariant)
+  for (int p = 0; p < 6; p++) {
+    double q[4][3];
+    for (int a = 0; a < 4; a++) vert_coord(L, tv[p][a], q[a]);
+    L.perm_mats[p] = tet_mats(q);
+  }
+  if (beta) L.beta.assign(beta, beta + NT);
+  else L.beta.assign(NT, 1.0);
+  if (alpha) L.alpha.assign(alpha, alpha + NT);
+  else L.alpha.assign(NT, 1.0);
+  for (int64_t t = 0; t < NT; t++)
+    REQUIRE(L.beta[t] > 0 && L.alpha[t] > 0 && std::isfinite(L.beta[t]) && std::isfinite(L.alpha[t]),
+            "coefficients must be positive and finite");
+}
+
+// ---------------------------------------------------------------- coarsening
+struct Transfer {
+  Adj cons[4];                  // coarse entity -> constituent fine entities (same dim)
+  std::vector<int8_t> phi[4];   // orientation of each constituent (aligned with cons.ci)
+  std::vector<int8_t> own_dim[4];
+  std::vector<int> own_id[4];   // owner coarse entity of each fine entity
+  Adj fclo[4][4];               // fine closure (space k) of coarse entity of dim d
+  std::vector<uint8_t> fint[4][4];
+  DCsr P[4];
+  bool built[4] = {false, false, false, false};
+};
+
+// Group items by key: sorts (key, item) pairs; groups[i] lists the items of the i-th key.
+template <class K>
+void group_sorted(std::vector<std::pair<K, int>>& kv, Adj& groups, std::vector<K>* keys) {
+  std::sort(kv.begin(), kv.end());
+  groups.rp.assign(1, 0);
+  groups.ci.clear();
+  for (size_t i = 0; i < kv.size(); i++) {
+    bool start = (i == 0) || !(kv[i].first == kv[i - 1].first);
+    if (start && i > 0) groups.rp.push_back((int64_t)i);
+    if (start && keys) keys->push_back(kv[i].first);
+    groups.ci.push_back(kv[i].second);
+  }
+  if (!kv.empty()) groups.rp.push_back((int64_t)kv.size());
+}
+
+// Orientation of the constituents of each coarse entity of dim d (d = 1 or 2) so that
+// shared (d-1)-sub-entities interior to the coarse entity cancel in the chain boundary.
+void orient_chain(const Adj& cons, const ICsr& Dsub, std::vector<int8_t>& phi) {
+  phi.assign(cons.ci.size(), 0);
+  int nc = cons.rows();
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int X = 0; X < nc; X++) {
+    int len = cons.len(X);
+    const int* c = cons.row(X);
+    int8_t* ph = phi.data() + cons.rp[X];
+    // incidence list: (sub-entity, constituent position, sign)
+    std::vector<std::array<int, 3>> inc;
+    for (int i = 0; i < len; i++) {
+      int x = c[i];
+      for (int64_t p = Dsub.a.rp[x]; p < Dsub.a.rp[x + 1]; p++) inc.push_back({Dsub.a.ci[p], i, Dsub.v[p]});
+    }
+    std::sort(inc.begin(), inc.end());
+    std::vector<std::vector<std::array<int, 2>>> nb(len);  // neighbor, sign product
+    for (size_t a = 0; a < inc.size();) {
+      size_t b = a;
+      while (b < inc.size() && inc[b][0] == inc[a][0]) b++;
+      if (b - a == 2) {
+        int i = inc[a][1], j = inc[a + 1][1], s = inc[a][2] * inc[a + 1][2];
+        nb[i].push_back({j, s});
+        nb[j].push_back({i, s});
+      }
+      a = b;
+    }
+    std::vector<int> queue{0};
+    ph[0] = 1;
+    for (size_t q = 0; q < queue.size(); q++) {
+      int i = queue[q];
+      for (auto& e : nb[i]) {
+        int8_t want = (int8_t)(-ph[i] * e[1]);
+        if (ph[e[0]] == 0) {
+          ph[e[0]] = want;
+          queue.push_back(e[0]);
+        } else if (ph[e[0]] != want) {
+          throw Fail("coarse entity is not orientable");
+        }
+      }
+    }
+    if ((int)queue.size() != len) throw Fail("coarse entity is not connected");
+  }
+}
+
+// Build the coarse topology (Section 3.1) and owner / closure maps of the transfer.
+void coarsen_topology(const Level& L, Level& C, Transfer& T, double& incid_dev) {
+  REQUIRE(L.m % 2 == 0, "agglomeration needs an even number of cells per side");
+  const int m2 = L.m / 2;
+  const int nCell = (int)L.cnt[3];
+  // agglomerates: 2 x 2 x 2 blocks of cells
+  std::vector<int> agg(nCell);
+  for (int c = 0; c < nCell; c++) {
+    const int* ijk = &L.cell_ijk[3 * c];
+    agg[c] = ((ijk[0] / 2) * m2 + ijk[1] / 2) * m2 + ijk[2] / 2;
+  }
+  const int nAgg = m2 * m2 * m2;
+  {
+    std::vector<std::pair<int, int>> kv(nCell);
+    for (int c = 0; c < nCell; c++) kv[c] = {agg[c], c};
+    group_sorted(kv, T.cons[3], (std::vector<int>*)nullptr);
+    REQUIRE(T.cons[3].rows() == nAgg, "empty agglomerate");
+    T.phi[3].assign(T.cons[3].ci.size(), 1);
+  }
+  C.m = m2;
+  C.cell_ijk.resize(3 * nAgg);
+  for (int a = 0; a < nAgg; a++) {
+    C.cell_ijk[3 * a] = a / (m2 * m2), C.cell_ijk[3 * a + 1] = (a / m2) % m2, C.cell_ijk[3 * a + 2] = a % m2;
+  }
+  // coarse faces: fine faces grouped by the pair of agglomerates they separate, or by
+  // (agglomerate, boundary side) on the domain boundary
+  const int nF = (int)L.cnt[2];
+  std::vector<int8_t> cface_side;
+  {
+    std::vector<std::pair<std::pair<int, int>, int>> kv;
+    for (int f = 0; f < nF; f++) {
+      const int* cells = L.DT[2].a.row(f);
+      int nc = L.DT[2].a.len(f);
+      if (nc == 2) {
+        int a1 = agg[cells[0]], a2 = agg[cells[1]];
+        if (a1 == a2) continue;
+        kv.push_back({{std::min(a1, a2), std::max(a1, a2)}, f});
+      } else {
+        REQUIRE(nc == 1 && L.face_side[f] >= 0, "face without boundary side");
+        kv.push_back({{agg[cells[0]], nAgg + L.face_side[f]}, f});
+      }
+    }
+    std::vector<std::pair<int, int>> keys;
+    group_sorted(kv, T.cons[2], &keys);
+    cface_side.resize(keys.size());
+    for (size_t i = 0; i < keys.size(); i++)
+      cface_side[i] = keys[i].second >= nAgg ? (int8_t)(keys[i].second - nAgg) : (int8_t)-1;
+  }
+  orient_chain(T.cons[2], L.D[1], T.phi[2]);
+  const int nCF = T.cons[2].rows();
+  for (int k = 0; k < 4; k++) {
+    T.own_dim[k].assign(L.cnt[k], -1);
+    T.own_id[k].assign(L.cnt[k], -1);
+  }
+  for (int X = 0; X < nCF; X++)
+    for (int64_t p = T.cons[2].rp[X]; p < T.cons[2].rp[X + 1]; p++) {
+      int f = T.cons[2].ci[p];
+      T.own_dim[2][f] = 2, T.own_id[2][f] = X;
+    }
+  // coarse edges: fine edges lying on >= 2 coarse faces, grouped by that set
+  const int nE = (int)L.cnt[1];
+  {
+    std::vector<std::pair<std::vector<int>, int>> kv;
+    for (int e = 0; e < nE; e++) {
+      std::vector<int> s;
+      for (int64_t p = L.DT[1].a.rp[e]; p < L.DT[1].a.rp[e + 1]; p++) {
+        int f = L.DT[1].a.ci[p];
+        if (T.own_dim[2][f] == 2) s.push_back(T.own_id[2][f]);
+      }
+      std::sort(s.begin(), s.end());
+      s.erase(std::unique(s.begin(), s.end()), s.end());
+      if (s.size() >= 2) kv.push_back({s, e});
+    }
+    group_sorted(kv, T.cons[1], (std::vector<std::vector<int>>*)nullptr);
+  }
+  orient_chain(T.cons[1], L.D[0], T.phi[1]);
+  const int nCE = T.cons[1].rows();
+  for (int X = 0; X < nCE; X++)
+    for (int64_t p = T.cons[1].rp[X]; p < T.cons[1].rp[X + 1]; p++) {
+      int e = T.cons[1].ci[p];
+      T.own_dim[1][e] = 1, T.own_id[1][e] = X;
+    }
+  // coarse vertices: fine vertices on >= 2 coarse edges, grouped by that set
+  const int nV = (int)L.cnt[0];
+  {
+    std::vector<std::pair<std::vector<int>, int>> kv;
+    for (int v = 0; v < nV; v++) {
+      std::vector<int> s;
+      for (int64_t p = L.DT[0].a.rp[v]; p < L.DT[0].a.rp[v + 1]; p++) {
+        int e = L.DT[0].a.ci[p];
+        if (T.own_dim[1][e] == 1) s.push_back(T.own_id[1][e]);
+      }
+      std::sort(s.begin(), s.end());
+      s.erase(std::unique(s.begin(), s.end()), s.end());
+      if (s.size() >= 2) kv.push_back({s, v});
+    }
+    group_sorted(kv, T.cons[0], (std::vector<std::vector<int>>*)nullptr);
+    T.phi[0].assign(T.cons[0].ci.size(), 1);
+    for (int X = 0; X < T.cons[0].rows(); X++) REQUIRE(T.cons[0].len(X) == 1, "coarse vertex with several fine vertices");
+  }
+  const int nCV = T.cons[0].rows();
+  for (int X = 0; X < nCV; X++) {
+    int v = T.cons[0].ci[T.cons[0].rp[X]];
+    T.own_dim[0][v] = 0, T.own_id[0][v] = X;
+  }
+  for (int X = 0; X < nAgg; X++)
+    for (int64_t p = T.cons[3].rp[X]; p < T.cons[3].rp[X + 1]; p++) {
+      int c = T.cons[3].ci[p];
+      T.own_dim[3][c] = 3, T.own_id[3][c] = X;
+    }
+  C.cnt[0] = nCV, C.cnt[1] = nCE, C.cnt[2] = nCF, C.cnt[3] = nAgg;
+  C.face_side = cface_side;
+
+  // coarse incidences: chain boundary of each coarse entity, read on its coarse sub-entities
+  incid_dev = 0.0;
+  for (int d = 1; d <= 3; d++) {
+    const int k = d - 1;
+    const ICsr& Dk = L.D[k];
+    const int nX = T.cons[d].rows();
+    std::vector<std::vector<std::pair<int, int>>> rows(nX);
+    double dev = 0.0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : dev)
+    for (int X = 0; X < nX; X++) {
+      std::vector<std::pair<int, int>> b;  // (fine sub-entity, coefficient)
+      for (int64_t p = T.cons[d].rp[X]; p < T.cons[d].rp[X + 1]; p++) {
+        int x = T.cons[d].ci[p];
+        int ph = T.phi[d][p];
+        for (int64_t q = Dk.a.rp[x]; q < Dk.a.rp[x + 1]; q++) b.push_back({Dk.a.ci[q], ph * Dk.v[q]});
+      }
+      std::sort(b.begin(), b.end());
+      std::vector<std::pair<int, int>> acc;
+      for (size_t i = 0; i < b.size();) {
+        size_t j = i;
+        int s = 0;
+        while (j < b.size() && b[j].first == b[i].first) s += b[j].second, j++;
+        if (s != 0) acc.push_back({b[i].first, s});
+        i = j;
+      }
+      // group nonzero boundary coefficients by the coarse sub-entity that owns them
+      std::vector<std::array<int, 3>> g;  // coarse sub-entity, value * phi, fine sub-entity
+      for (auto& pr : acc) {
+        int y = pr.first;
+        if (T.own_dim[k][y] != k) throw Fail("chain boundary leaves the coarse skeleton");
+        int Y = T.own_id[k][y];
+        int py = T.cons[k].find(Y, y);
+        int ph = T.phi[k][T.cons[k].rp[Y] + py];
+        g.push_back({Y, pr.second * ph, y});
+      }
+      std::sort(g.begin(), g.end());
+      for (size_t i = 0; i < g.size();) {
+        size_t j = i;
+        int cnt = 0;
+        while (j < g.size() && g[j][0] == g[i][0]) {
+          if (g[j][1] != g[i][1]) dev = std::max(dev, (double)std::abs(g[j][1] - g[i][1]));
+          cnt++, j++;
+        }
+        if (cnt != T.cons[k].len(g[i][0])) dev = std::max(dev, 1.0);
+        if (std::abs(g[i][1]) != 1) dev = std::max(dev, (double)std::abs(g[i][1]));
+        rows[X].push_back({g[i][0], g[i][1]});
+        i = j;
+      }
+    }
+    incid_dev = std::max(incid_dev, dev);
+    ICsr& DH = C.D[k];
+    DH.nr = nX, DH.nc = (int)C.cnt[k];
+    DH.a.rp.assign(nX + 1, 0);
+    for (int X = 0; X < nX; X++) DH.a.rp[X + 1] = DH.a.rp[X] + (int64_t)rows[X].size();
+    DH.a.ci.resize(DH.a.rp[nX]);
+    DH.v.resize(DH.a.rp[nX]);
+    for (int X = 0; X < nX; X++)
+      for (size_t i = 0; i < rows[X].size(); i++) {
+        DH.a.ci[DH.a.rp[X] + i] = rows[X][i].first;
+        DH.v[DH.a.rp[X] + i] = (int8_t)rows[X][i].second;
+      }
+  }
+  REQUIRE(incid_dev == 0.0, "coarse incidence depends on the constituent chosen");
+  for (int k = 0; k < 3; k++) C.DT[k] = transpose_i(C.D[k]);
+  build_closures(C);
+
+  // fine closures of coarse entities, interior flags, owners of interior fine entities
+  for (int d = 1; d <= 3; d++) {
+    const int nX = T.cons[d].rows();
+    T.fclo[d][d] = T.cons[d];
+    T.fint[d][d].assign(T.cons[d].ci.size(), 1);
+    for (int k = 0; k < d; k++) T.fclo[d][k] = compose_union(T.cons[d], L.clo[d][k]);
+    // boundary (d-1)-entities: in exactly one constituent
+    std::vector<std::vector<int>> bnd(nX);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int X = 0; X < nX; X++) {
+      std::vector<int> s;
+      for (int64_t p = T.cons[d].rp[X]; p < T.cons[d].rp[X + 1]; p++) {
+        int x = T.cons[d].ci[p];
+        s.insert(s.end(), L.clo[d][d - 1].row(x), L.clo[d][d - 1].row(x) + L.clo[d][d - 1].len(x));
+      }
+      std::sort(s.begin(), s.end());
+      for (size_t i = 0; i < s.size();) {
+        size_t j = i;
+        while (j < s.size() && s[j] == s[i]) j++;
+        if (j - i == 1) bnd[X].push_back(s[i]);
+        i = j;
+      }
+    }
+    for (int k = 0; k < d; k++) {
+      T.fint[d][k].assign(T.fclo[d][k].ci.size(), 1);
+#pragma omp parallel for schedule(dynamic, 64)
+      for (int X = 0; X < nX; X++) {
+        std::vector<int> bk;
+        for (int y : bnd[X]) {
+          if (k == d - 1) bk.push_back(y);
+          else bk.insert(bk.end(), L.clo[d - 1][k].row(y), L.clo[d - 1][k].row(y) + L.clo[d - 1][k].len(y));
+        }
+        std::sort(bk.begin(), bk.end());
+        const int* fc = T.fclo[d][k].row(X);
+        for (int i = 0; i < T.fclo[d][k].len(X); i++)
+          if (std::binary_search(bk.begin(), bk.end(), fc[i])) T.fint[d][k][T.fclo[d][k].rp[X] + i] = 0;
+      }
+      for (int X = 0; X < nX; X++) {
+        const int* fc = T.fclo[d][k].row(X);
+        for (int i = 0; i < T.fclo[d][k].len(X); i++) {
+          if (!T.fint[d][k][T.fclo[d][k].rp[X] + i]) continue;
+          int y = fc[i];
+          REQUIRE(T.own_dim[k][y] < 0, "fine entity interior to two coarse entities");
+          T.own_dim[k][y] = (int8_t)d, T.own_id[k][y] = X;
+        }
+      }
+    }
+  }
+  for (int k = 0; k < 4; k++)
+    for (int64_t y = 0; y < L.cnt[k]; y++) REQUIRE(T.own_dim[k][y] >= 0, "fine entity without owner");
+}
+
+// Coarse dofs of space k whose basis functions are supported on coarse entity X (dim d).
+inline int coarse_dofs(const Level& C, int d, int k, int X, const int** out) {
+  static thread_local int self;
+  if (k == d) {
+    self = X;
+    *out = &self;
+    return 1;
+  }
+  *out = C.clo[d][k].row(X);
+  return C.clo[d][k].len(X);
+}
+
+// Allocate the pattern of P_k: each fine row owned by coarse X of dim d has the coarse
+// dofs of X as columns.
+void alloc_P(const Level& L, const Level& C, Transfer& T, int k) {
+  DCsr& P = T.P[k];
+  P.nr = (int)L.cnt[k], P.nc = (int)C.cnt[k];
+  P.a.rp.assign(P.nr + 1, 0);
+  for (int i = 0; i < P.nr; i++) {
+    const int* c;
+    P.a.rp[i + 1] = P.a.rp[i] + coarse_dofs(C, T.own_dim[k][i], k, T.own_id[k][i], &c);
+  }
+  P.a.ci.resize(P.a.rp[P.nr]);
+  P.v.assign(P.a.rp[P.nr], 0.0);
+  for (int i = 0; i < P.nr; i++) {
+    const int* c;
+    int n = coarse_dofs(C, T.own_dim[k][i], k, T.own_id[k][i], &c);
+    std::copy(c, c + n, P.a.ci.begin() + P.a.rp[i]);
+  }
+}
+
+// Assemble the trace mass of space k over the constituents of coarse X (dim d), on the
+// fine dof list S (sorted).
+void assemble_mass(const Level& L, const Transfer& T, int d, int k, int X, const int* S, int nS,
+                   std::vector<double>& M, std::vector<double>& buf) {
+  M.assign((size_t)nS * nS, 0.0);
+  for (int64_t p = T.cons[d].rp[X]; p < T.cons[d].rp[X + 1]; p++) {
+    int x = T.cons[d].ci[p];
+    int s = local_size(L, d, k, x);
+    buf.resize((size_t)s * s);
+    local_mass(L, d, k, x, buf.data());
+    int loc[64];
+    REQUIRE(s <= 64, "local closure too large");
+    if (k == d) loc[0] = (int)(std::lower_bound(S, S + nS, x) - S);
+    else
+      for (int i = 0; i < s; i++) loc[i] = (int)(std::lower_bound(S, S + nS, L.clo[d][k].row(x)[i]) - S);
+    for (int i = 0; i < s; i++)
+      for (int j = 0; j < s; j++) M[(size_t)loc[i] * nS + loc[j]] += buf[(size_t)i * s + j];
+  }
+}
+
+// Dense restriction of D_k to rows R (fine dim-(k+1) entities) and columns Cl (dim k).
+void restrict_D(const ICsr& D, const int* R, int nR, const int* Cl, int nC, std::vector<double>& out) {
+  out.assign((size_t)nR * nC, 0.0);
+  for (int r = 0; r < nR; r++) {
+    int y = R[r];
+    for (int64_t p = D.a.rp[y]; p < D.a.rp[y + 1]; p++) {
+      const int* q = std::lower_bound(Cl, Cl + nC, D.a.ci[p]);
+      if (q != Cl + nC && *q == D.a.ci[p]) out[(size_t)r * nC + (q - Cl)] = D.v[p];
+    }
+  }
+}
+
+struct ExtStats {
+  double lam_dev = 0, resid = 0;
+};
+
+// Extend space-k coarse dofs into the interior of every coarse entity of dimension d.
+void extend(const Level& L, const Level& C, Transfer& T, int k, int d, ExtStats& st) {
+  DCsr& P = T.P[k];
+  const int nX = T.cons[d].rows();
+  double lam_dev = 0, resid = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : lam_dev, resid)
+  for (int X = 0; X < nX; X++) {
+    std::vector<double> M, W, W2, Dm, D2m, buf, K, R, K0, R0, s;
+    const int* S = T.fclo[d][k].row(X);
+    const int nS = T.fclo[d][k].len(X);
+    const uint8_t* in = T.fint[d][k].data() + T.fclo[d][k].rp[X];
+    std::vector<int> I, B;
+    for (int i = 0; i < nS; i++) (in[i] ? I : B).push_back(i);
+    const int nI = (int)I.size(), nB = (int)B.size();
+    const int* J;
+    const int nJ = coarse_dofs(C, d, k, X, &J);
+    if (nI == 0 || nJ == 0) continue;
+    // boundary data: the already-built traces of each coarse dof on the boundary
+    std::vector<double> phiB((size_t)nB * nJ);
+    for (int b = 0; b < nB; b++)
+      for (int j = 0; j < nJ; j++) phiB[(size_t)b * nJ + j] = P.get(S[B[b]], J[j]);
+    assemble_mass(L, T, d, k, X, S, nS, M, buf);
+    int n;
+    if (d == k + 1) {
+      // eq. 3.6: unknowns (phi_I, psi on all constituents, lambda)
+      const int* S1 = T.cons[d].row(X);
+      const int n1 = T.cons[d].len(X);
+      assemble_mass(L, T, d, d, X, S1, n1, W, buf);
+      restrict_D(L.D[k], S1, n1, S, nS, Dm);
+      std::vector<double> p(n1), Wp(n1, 0.0);
+      for (int a = 0; a < n1; a++) p[a] = T.phi[d][T.cons[d].rp[X] + a] / (double)n1;
+      for (int a = 0; a < n1; a++)
+        for (int b = 0; b < n1; b++) Wp[a] += W[(size_t)a * n1 + b] * p[b];
+      std::vector<double> WD((size_t)n1 * nS, 0.0);
+      for (int a = 0; a < n1; a++)
+        for (int c = 0; c < n1; c++) {
+          double w = W[(size_t)a * n1 + c];
+          if (w == 0.0) continue;
+          for (int i = 0; i < nS; i++) WD[(size_t)a * nS + i] += w * Dm[(size_t)c * nS + i];
+        }
+      n = nI + n1 + 1;
+      K.assign((size_t)n * n, 0.0);
+      R.assign((size_t)n * nJ, 0.0);
+      for (int a = 0; a < nI; a++)
+        for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
+      for (int a = 0; a < n1; a++)
+        for (int b = 0; b < nI; b++) {
+          double v = WD[(size_t)a * nS + I[b]];
+          K[(size_t)(nI + a) * n + b] = v;
+          K[(size_t)b * n + nI + a] = v;
+        }
+      for (int a = 0; a < n1; a++) {
+        K[(size_t)(nI + a) * n + nI + n1] = -Wp[a];
+        K[(size_t)(nI + n1) * n + nI + a] = -Wp[a];
+      }
+      for (int j = 0; j < nJ; j++) {
+        for (int a = 0; a < nI; a++) {
+          double v = 0;
+          for (int b = 0; b < nB; b++) v += M[(size_t)I[a] * nS + B[b]] * phiB[(size_t)b * nJ + j];
+          R[(size_t)a * nJ + j] = -v;
+        }
+        for (int a = 0; a < n1; a++) {
+          double v = 0;
+          for (int b = 0; b < nB; b++) v += WD[(size_t)a * nS + B[b]] * phiB[(size_t)b * nJ + j];
+          R[(size_t)(nI + a) * nJ + j] = -v;
+        }
+      }
+    } else {
+      // eq. 3.8: unknowns (phi_I, chi on interior (k+1)-dofs)
+      const int* S1 = T.fclo[d][k + 1].row(X);
+      const int n1 = T.fclo[d][k + 1].len(X);
+      const uint8_t* in1 = T.fint[d][k + 1].data() + T.fclo[d][k + 1].rp[X];
+      const int* S2 = T.fclo[d][k + 2].row(X);
+      const int n2 = T.fclo[d][k + 2].len(X);
+      std::vector<int> I1;
+      for (int i = 0; i < n1; i++)
+        if (in1[i]) I1.push_back(i);
+      const int nI1 = (int)I1.size();
+      assemble_mass(L, T, d, k + 1, X, S1, n1, W, buf);
+      assemble_mass(L, T, d, k + 2, X, S2, n2, W2, buf);
+      restrict_D(L.D[k], S1, n1, S, nS, Dm);
+      restrict_D(L.D[k + 1], S2, n2, S1, n1, D2m);
+      // s_J = sum_J' (D_k^H)_{J',J} * (space-(k+1) shape function of J' on X)
+      const int* J1;
+      const int nJ1 = coarse_dofs(C, d, k + 1, X, &J1);
+      s.assign((size_t)n1 * nJ, 0.0);
+      for (int j1 = 0; j1 < nJ1; j1++)
+        for (int j = 0; j < nJ; j++) {
+          int8_t inc = C.D[k].get(J1[j1], J[j]);
+          if (!inc) continue;
+          for (int a = 0; a < n1; a++) s[(size_t)a * nJ + j] += inc * T.P[k + 1].get(S1[a], J1[j1]);
+        }
+      // residual target t = s - D_B phi_B on all (k+1)-dofs of X
+      std::vector<double> tgt = s;
+      for (int a = 0; a < n1; a++)
+        for (int b = 0; b < nB; b++) {
+          double dv = Dm[(size_t)a * nS + B[b]];
+          if (dv == 0.0) continue;
+          for (int j = 0; j < nJ; j++) tgt[(size_t)a * nJ + j] -= dv * phiB[(size_t)b * nJ + j];
+        }
+      n = nI + nI1;
+      K.assign((size_t)n * n, 0.0);
+      R.assign((size_t)n * nJ, 0.0);
+      for (int a = 0; a < nI; a++)
+        for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
+      // W_{I1,I1} D_{I1,I}
+      for (int a = 0; a < nI1; a++)
+        for (int b = 0; b < nI; b++) {
+          double v = 0;
+          for (int c = 0; c < nI1; c++) v += W[(size_t)I1[a] * n1 + I1[c]] * Dm[(size_t)I1[c] * nS + I[b]];
+          K[(size_t)(nI + a) * n + b] = v;
+          K[(size_t)b * n + nI + a] = v;
+        }
+      // -D2_{:,I1}^T W2 D2_{:,I1}
+      std::vector<double> W2D((size_t)n2 * nI1, 0.0);
+      for (int a = 0; a < n2; a++)
+        for (int c = 0; c < n2; c++) {
+          double w = W2[(size_t)a * n2 + c];
+          if (w == 0.0) continue;
+          for (int b = 0; b < nI1; b++) W2D[(size_t)a * nI1 + b] += w * D2m[(size_t)c * n1 + I1[b]];
+        }
+      for (int a = 0; a < nI1; a++)
+        for (int b = 0; b < nI1; b++) {
+          double v = 0;
+          for (int c = 0; c < n2; c++) v += D2m[(size_t)c * n1 + I1[a]] * W2D[(size_t)c * nI1 + b];
+          K[(size_t)(nI + a) * n + nI + b] = -v;
+        }
+      for (int j = 0; j < nJ; j++) {
+        for (int a = 0; a < nI; a++) {
+          double v = 0;
+          for (int b = 0; b < nB; b++) v += M[(size_t)I[a] * nS + B[b]] * phiB[(size_t)b * nJ + j];
+          R[(size_t)a * nJ + j] = -v;
+        }
+        for (int a = 0; a < nI1; a++) {
+          double v = 0;
+          for (int c = 0; c < n1; c++) v += W[(size_t)I1[a] * n1 + c] * tgt[(size_t)c * nJ + j];
+          R[(size_t)(nI + a) * nJ + j] = v;
+        }
+      }
+    }
+    K0 = K;
+    R0 = R;
+    if (!lu_solve(n, K.data(), nJ, R.data())) throw Fail("singular local extension problem");
+    // residual of the local solve
+    for (int j = 0; j < nJ; j++) {
+      double rn = 0, bn = 0;
+      for (int a = 0; a < n; a++) {
+        double v = -R0[(size_t)a * nJ + j];
+        for (int b = 0; b < n; b++) v += K0[(size_t)a * n + b] * R[(size_t)b * nJ + j];
+        rn += v * v;
+        bn += R0[(size_t)a * nJ + j] * R0[(size_t)a * nJ + j];
+      }
+      if (bn > 0) resid = std::max(resid, std::sqrt(rn / bn));
+      if (d == k + 1) {  // Stokes: the multiplier equals the coarse incidence (D_k^H)_{X,J}
+        double lam = R[(size_t)(n - 1) * nJ + j];
+        lam_dev = std::max(lam_dev, std::fabs(lam - (double)C.D[k].get(X, J[j])));
+      }
+    }
+    for (int a = 0; a < nI; a++) {
+      int row = S[I[a]];
+      for (int j = 0; j < nJ; j++) {
+        int pos = P.a.find(row, J[j]);
+        if (pos < 0) throw Fail("prolongator pattern mismatch");
+        P.v[P.a.rp[row] + pos] = R[(size_t)a * nJ + j];
+      }
+    }
+  }
+  st.lam_dev = std::max(st.lam_dev, lam_dev);
+  st.resid = std::max(st.resid, resid);
+}
+
+void build_P(const Level& L, const Level& C, Transfer& T, int k, ExtStats& st) {
+  alloc_P(L, C, T, k);
+  DCsr& P = T.P[k];
+  // PV traces on the coarse dim-k entities (eq. 3.5): orientation / number of constituents
+  for (int X = 0; X < T.cons[k].rows(); X++) {
+    int len = T.cons[k].len(X);
+    for (int64_t p = T.cons[k].rp[X]; p < T.cons[k].rp[X + 1]; p++) {
+      int y = T.cons[k].ci[p];
+      int pos = P.a.find(y, X);
+      REQUIRE(pos >= 0, "PV row pattern");
+      P.v[P.a.rp[y] + pos] = T.phi[k][p] / (double)len;
+    }
+  }
+  for (int d = k + 1; d <= 3; d++) extend(L, C, T, k, d, st);
+  T.built[k] = true;
+}
+
+// Coarse local matrices (Section 3.2.1): P_X^T M_X P_X for every coarse entity X and
+// every space kept, plus the problem form P_T^T A_T P_T on coarse cells.
+void coarse_local(const Level& L, Level& C, const Transfer& T, int kmin, int kf) {
+  for (int d = 1; d <= 3; d++)
+    for (int k = kmin; k <= d; k++) {
+      const int nX = T.cons[d].rows();
+      auto& off = C.lmoff[d][k];
+      off.assign(nX + 1, 0);
+      for (int X = 0; X < nX; X++) {
+        int s = local_size(C, d, k, X);
+        off[X + 1] = off[X] + (int64_t)s * s;
+      }
+      C.lm[d][k].assign(off[nX], 0.0);
+    }
+  C.laoff.assign(C.cnt[3] + 1, 0);
+  for (int X = 0; X < C.cnt[3]; X++) {
+    int s = local_size(C, 3, kf, X);
+    C.laoff[X + 1] = C.laoff[X] + (int64_t)s * s;
+  }
+  C.la.assign(C.laoff[C.cnt[3]], 0.0);
+  // out = Pl^T M Pl with Pl = P_k restricted to (fine closure of X) x (coarse dofs of X)
+  auto rap = [&](int d, int k, int X, const std::vector<double>& M, double* out) {
+    const int* S = T.fclo[d][k].row(X);
+    const int nS = T.fclo[d][k].len(X);
+    const int* J;
+    const int nJ = coarse_dofs(C, d, k, X, &J);
+    std::vector<double> Pl((size_t)nS * nJ, 0.0), MP((size_t)nS * nJ, 0.0);
+    for (int a = 0; a < nS; a++)
+      for (int j = 0; j < nJ; j++) Pl[(size_t)a * nJ + j] = T.P[k].get(S[a], J[j]);
+    for (int a = 0; a < nS; a++)
+      for (int b = 0; b < nS; b++) {
+        double mv = M[(size_t)a * nS + b];
+        if (mv == 0.0) continue;
+        for (int j = 0; j < nJ; j++) MP[(size_t)a * nJ + j] += mv * Pl[(size_t)b * nJ + j];
+      }
+    for (int i = 0; i < nJ; i++)
+      for (int j = 0; j < nJ; j++) {
+        double v = 0;
+        for (int a = 0; a < nS; a++) v += Pl[(size_t)a * nJ + i] * MP[(size_t)a * nJ + j];
+        out[(size_t)i * nJ + j] = v;
+      }
+    for (int i = 0; i < nJ; i++)  // exact symmetry (RAP of a symmetric matrix)
+      for (int j = i + 1; j < nJ; j++) {
+        double v = 0.5 * (out[(size_t)i * nJ + j] + out[(size_t)j * nJ + i]);
+        out[(size_t)i * nJ + j] = out[(size_t)j * nJ + i] = v;
+      }
+  };
+  for (int d = 1; d <= 3; d++) {
+    const int nX = T.cons[d].rows();
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int X = 0; X < nX; X++) {
+      std::vector<double> M, buf;
+      for (int k = kmin; k <= d; k++) {
+        const int* S = T.fclo[d][k].row(X);
+        const int nS = T.fclo[d][k].len(X);
+        assemble_mass(L, T, d, k, X, S, nS, M, buf);
+        rap(d, k, X, M, C.lm[d][k].data() + C.lmoff[d][k][X]);
+      }
+      if (d == 3) {
+        const int* S = T.fclo[3][kf].row(X);
+        const int nS = T.fclo[3][kf].len(X);
+        M.assign((size_t)nS * nS, 0.0);
+        for (int64_t p = T.cons[3].rp[X]; p < T.cons[3].rp[X + 1]; p++) {
+          int x = T.cons[3].ci[p];
+          int s = local_size(L, 3, kf, x);
+          buf.resize((size_t)s * s);
+          local_form(L, kf, x, buf.data());
+          int loc[64];
+          for (int i = 0; i < s; i++) loc[i] = (int)(std::lower_bound(S, S + nS, L.clo[3][kf].row(x)[i]) - S);
+          for (int i = 0; i < s; i++)
+            for (int j = 0; j < s; j++) M[(size_t)loc[i] * nS + loc[j]] += buf[(size_t)i * s + j];
+        }
+        rap(3, kf, X, M, C.la.data() + C.laoff[X]);
+      }
+    }
+  }
+}
+
+// Global problem matrix of a level, assembled row by row from the local cell matrices.
+DCsr assemble_global(const Level& L, int kf) {
+  const int nr = (int)L.cnt[kf];
+  const Adj& cl = L.clo[3][kf];
+  Adj tr = transpose_adj(cl, nr);
+  std::vector<std::vector<std::pair<int, double>>> rows(nr);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int r = 0; r < nr; r++) {
+    std::vector<double> buf;
+    std::vector<std::pair<int, double>> acc;
+    for (int64_t p = tr.rp[r]; p < tr.rp[r + 1]; p++) {
+      int c = tr.ci[p];
+      int s = cl.len(c);
+      buf.resize((size_t)s * s);
+      local_form(L, kf, c, buf.data());
+      int li = cl.find(c, r);
+      for (int j = 0; j < s; j++) acc.push_back({cl.row(c)[j], buf[(size_t)li * s + j]});
+    }
+    std::stable_sort(acc.begin(), acc.end(), [](auto& a, auto& b) { return a.first < b.first; });
+    auto& out = rows[r];
+    for (size_t i = 0; i < acc.size();) {
+      size_t j = i;
+      double s = 0;
+      while (j < acc.size() && acc[j].first == acc[i].first) s += acc[j].second, j++;
+      out.push_back({acc[i].first, s});
+      i = j;
+    }
+  }
+  DCsr A;
+  A.nr = A.nc = nr;
+  A.a.rp.assign(nr + 1, 0);
+  for (int r = 0; r < nr; r++) A.a.rp[r + 1] = A.a.rp[r] + (int64_t)rows[r].size();
+  A.a.ci.resize(A.a.rp[nr]);
+  A.v.resize(A.a.rp[nr]);
+  for (int r = 0; r < nr; r++)
+    for (size_t i = 0; i < rows[r].size(); i++) {
+      A.a.ci[A.a.rp[r] + i] = rows[r][i].first;
+      A.v[A.a.rp[r] + i] = rows[r][i].second;
+    }
+  return A;
+}
+
+struct Hier {
+  int form_k = 1;
+  std::vector<Level> levels;
+  std::vector<Transfer> transfers;
+  std::vector<DCsr> A;
+  double diag[4] = {0, 0, 0, 0};
+};
+
+Hier* build(int form, int n, int num_levels, const double* beta, const double* alpha, int all_spaces) {
+  auto t0 = std::chrono::steady_clock::now();
+  REQUIRE(form == AMGH_FORM_HCURL || form == AMGH_FORM_HDIV, "form");
+  REQUIRE(n >= 1 && n <= 127, "n out of range");
+  Hier* H = new Hier;
+  try {
+    H->form_k = form;  // H(curl) -> space 1, H(div) -> space 2
+    const int kf = H->form_k;
+    const int kmin = all_spaces ? 0 : kf;
+    int nl = num_levels;
+    if (nl <= 0) {
+      nl = 1;
+      for (int m = n; m > 8 && m % 2 == 0; m /= 2) nl++;
+    }
+    {
+      int m = n;
+      for (int l = 1; l < nl; l++) {
+        REQUIRE(m % 2 == 0, "num_levels needs an even cell count per side at every coarsened level");
+        m /= 2;
+      }
+    }
+    H->levels.resize(nl);
+    H->transfers.resize(nl - 1);
+    { Stage s("fine mesh"); build_fine(H->levels[0], n, beta, alpha); }
+    ExtStats st;
+    double incid = 0;
+    { Stage s("assemble A0"); H->A.push_back(assemble_global(H->levels[0], kf)); }
+    for (int l = 0; l + 1 < nl; l++) {
+      Level& L = H->levels[l];
+      Level& C = H->levels[l + 1];
+      Transfer& T = H->transfers[l];
+      double dev = 0;
+      { Stage s("coarsen topology"); coarsen_topology(L, C, T, dev); }
+      incid = std::max(incid, dev);
+      for (int k = 3; k >= kmin; k--) { Stage s("prolongator"); build_P(L, C, T, k, st); }
+      { Stage s("coarse local RAP"); coarse_local(L, C, T, kmin, kf); }
+      { Stage s("assemble coarse A"); H->A.push_back(assemble_global(C, kf)); }
+      // the finer level's local data is no longer needed
+      if (!L.fine) {
+        for (int d = 0; d < 4; d++)
+          for (int k = 0; k < 4; k++) {
+            std::vector<double>().swap(L.lm[d][k]);
+            std::vector<int64_t>().swap(L.lmoff[d][k]);
+          }
+        std::vector<double>().swap(L.la);
+      }
+      for (int d = 0; d < 4; d++)
+        for (int k = 0; k < 4; k++) {
+          T.fclo[d][k] = Adj();
+          std::vector<uint8_t>().swap(T.fint[d][k]);
+        }
+    }
+    H->diag[0] = st.lam_dev;
+    H->diag[1] = st.resid;
+    H->diag[2] = incid;
+    H->diag[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  } catch (...) {
+    delete H;
+    throw;
+  }
+  return H;
+}
+
+void copy_dcsr(const DCsr& M, int32_t* rp, int32_t* ci, double* v) {
+  for (int i = 0; i <= M.nr; i++) rp[i] = (int32_t)M.a.rp[i];
+  std::copy(M.a.ci.begin(), M.a.ci.end(), ci);
+  std::copy(M.v.begin(), M.v.end(), v);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* amgh_error(void) { return g_err.c_str(); }
+
+int amgh_build(int form, int n, int num_levels, const double* beta, const double* alpha, int all_spaces,
+               int nthreads, void** out) {
+  if (!out) {
+    g_err = "out is NULL";
+    return 1;
+  }
+  *out = nullptr;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  try {
+    *out = build(form, n, num_levels, beta, alpha, all_spaces);
+    return 0;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return 2;
+  }
+}
+
+int amgh_num_levels(const void* h) { return h ? (int)((const Hier*)h)->levels.size() : -1; }
+
+int amgh_level_counts(const void* h, int level, int64_t counts[4]) {
+  const Hier* H = (const Hier*)h;
+  if (!H || level < 0 || level >= (int)H->levels.size()) return 1;
+  for (int k = 0; k < 4; k++) counts[k] = H->levels[level].cnt[k];
+  return 0;
+}
+
+int amgh_matrix_info(const void* h, int kind, int level, int k, int64_t info[3]) {
+  const Hier* H = (const Hier*)h;
+  if (!H || level < 0 || level >= (int)H->levels.size()) return 1;
+  if (kind == AMGH_KIND_A) {
+    const DCsr& M = H->A[level];
+    info[0] = M.nr, info[1] = M.nc, info[2] = (int64_t)M.v.size();
+  } else if (kind == AMGH_KIND_P) {
+    if (level + 1 >= (int)H->levels.size() || k < 0 || k > 3 || !H->transfers[level].built[k]) return 1;
+    const DCsr& M = H->transfers[level].P[k];
+    info[0] = M.nr, info[1] = M.nc, info[2] = (int64_t)M.v.size();
+  } else if (kind == AMGH_KIND_D) {
+    if (k < 0 || k > 2) return 1;
+    const ICsr& M = H->levels[level].D[k];
+    info[0] = M.nr, info[1] = M.nc, info[2] = (int64_t)M.v.size();
+  } else {
+    return 1;
+  }
+  return 0;
+}
+
+int amgh_matrix_copy(const void* h, int kind, int level, int k, int32_t* rp, int32_t* ci, double* v) {
+  int64_t info[3];
+  if (amgh_matrix_info(h, kind, level, k, info)) return 1;
+  const Hier* H = (const Hier*)h;
+  if (kind == AMGH_KIND_A) copy_dcsr(H->A[level], rp, ci, v);
+  else if (kind == AMGH_KIND_P) copy_dcsr(H->transfers[level].P[k], rp, ci, v);
+  else {
+    const ICsr& M = H->levels[level].D[k];
+    for (int i = 0; i <= M.nr; i++) rp[i] = (int32_t)M.a.rp[i];
+    std::copy(M.a.ci.begin(), M.a.ci.end(), ci);
+    for (size_t i = 0; i < M.v.size(); i++) v[i] = M.v[i];
+  }
+  return 0;
+}
+
+int amgh_diagnostics(const void* h, double out[4]) {
+  const Hier* H = (const Hier*)h;
+  if (!H) return 1;
+  for (int i = 0; i < 4; i++) out[i] = H->diag[i];
+  return 0;
+}
+
+void amgh_free(void* h) { delete (Hier*)h; }
+
+}  // extern "C"

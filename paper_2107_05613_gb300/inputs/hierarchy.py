@@ -1,0 +1,150 @@
+"""ctypes binding of the host hierarchy generator (amge_hierarchy.cpp).
+
+The generator builds, on the host in FP64, the AMGe de Rham hierarchy of Sections
+2-3 of the paper on an n^3 Kuhn-split unit cube: fine Whitney-form operator A_0,
+prolongators P_l from PV traces (eq. 3.5) and local extensions (eqs. 3.6, 3.8),
+integer coarse exterior derivatives, and Galerkin operators A_{l+1} = P_l^T A_l P_l.
+The result is plain CSR arrays that both the CUDA path and the oracle read.
+
+Levels are numbered from 0 (finest); the paper numbers them from 1.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamge_hierarchy.so")
+
+FORMS = {"hcurl": 1, "hdiv": 2}
+KIND_A, KIND_P, KIND_D = 0, 1, 2
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        from .. import build as _build
+
+        _build.build_hierarchy_lib()
+    lib = ctypes.CDLL(LIB_PATH)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.amgh_build.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    lib.amgh_build.restype = ctypes.c_int
+    lib.amgh_error.restype = ctypes.c_char_p
+    lib.amgh_num_levels.argtypes = [ctypes.c_void_p]
+    lib.amgh_level_counts.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p]
+    lib.amgh_matrix_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p]
+    lib.amgh_matrix_copy.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.amgh_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    lib.amgh_free.argtypes = [ctypes.c_void_p]
+    lib.amgh_free.restype = None
+    _lib = lib
+    return lib
+
+
+@dataclass
+class CSR:
+    """Compressed sparse rows: int32 row_ptr / col, float64 values."""
+
+    shape: tuple
+    indptr: np.ndarray
+    indices: np.ndarray
+    data: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.indptr[-1])
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+
+        return sp.csr_matrix((self.data, self.indices, self.indptr), shape=self.shape)
+
+
+@dataclass
+class Hierarchy:
+    """An AMGe hierarchy: per level l, A[l]; per transfer l -> l+1, P[l] and G[l].
+
+    form      'hcurl' (edge dofs, aux space = vertices via the gradient D_0) or
+              'hdiv'  (face dofs, aux space = edges via the curl D_1)
+    A[l]      problem matrix of level l (paper: A_{l+1})
+    P[l]      prolongator of the problem space from level l+1 to level l
+    G[l]      aux transition at level l: D_0 (H(curl)) or D_1 (H(div)), integer values
+    counts[l] entity counts (vertices, edges, faces, cells)
+    P_all[l][k], D_all[l][k]: prolongators / incidences of every space built
+    """
+
+    form: str
+    n: int
+    A: list
+    P: list
+    G: list
+    counts: list
+    P_all: list
+    D_all: list
+    diagnostics: dict
+
+    @property
+    def num_levels(self) -> int:
+        return len(self.A)
+
+
+def _copy(lib, h, kind, level, k):
+    info = (ctypes.c_int64 * 3)()
+    if lib.amgh_matrix_info(h, kind, level, k, info) != 0:
+        return None
+    nr, nc, nnz = int(info[0]), int(info[1]), int(info[2])
+    rp = np.empty(nr + 1, np.int32)
+    ci = np.empty(nnz, np.int32)
+    v = np.empty(nnz, np.float64)
+    rc = lib.amgh_matrix_copy(h, kind, level, k, rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+    assert rc == 0
+    return CSR((nr, nc), rp, ci, v)
+
+
+def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=None,
+                    all_spaces: bool = False, nthreads: int = 0) -> Hierarchy:
+    """Build the hierarchy on an n^3 Kuhn-split cube (6 n^3 tetrahedra).
+
+    beta, alpha: per-tet coefficients of (Du, Dv) and (u, v) (None = 1).
+    num_levels: 0 = coarsen 2x2x2 while the cell grid side m > 8.
+    """
+    lib = _load()
+    kf = FORMS[form]
+    nt = 6 * n ** 3
+    b = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
+    a = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float64)
+    for arr in (b, a):
+        if arr is not None and arr.shape != (nt,):
+            raise ValueError(f"coefficient array must have {nt} entries")
+    h = ctypes.c_void_p()
+    rc = lib.amgh_build(kf, n, num_levels, None if b is None else b.ctypes.data,
+                        None if a is None else a.ctypes.data, int(all_spaces), nthreads, ctypes.byref(h))
+    if rc != 0:
+        raise RuntimeError("hierarchy generator: " + lib.amgh_error().decode())
+    try:
+        L = lib.amgh_num_levels(h)
+        A, P, G, counts, P_all, D_all = [], [], [], [], [], []
+        for l in range(L):
+            c = (ctypes.c_int64 * 4)()
+            lib.amgh_level_counts(h, l, c)
+            counts.append(tuple(int(x) for x in c))
+            A.append(_copy(lib, h, KIND_A, l, 0))
+            D_all.append([_copy(lib, h, KIND_D, l, k) for k in range(3)])
+            if l + 1 < L:
+                P_all.append([_copy(lib, h, KIND_P, l, k) for k in range(4)])
+                P.append(P_all[-1][kf])
+                G.append(D_all[-1][kf - 1])
+        d = (ctypes.c_double * 4)()
+        lib.amgh_diagnostics(h, d)
+        diag = {"lambda_dev": d[0], "local_residual": d[1], "incidence_dev": d[2], "seconds": d[3]}
+    finally:
+        lib.amgh_free(h)
+    return Hierarchy(form, n, A, P, G, counts, P_all, D_all, diag)
