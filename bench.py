@@ -1,0 +1,411 @@
+#!/usr/bin/env python3
+"""PCG-AMGe solve benchmark on GB300.
+
+One step = one complete PCG solve (x0 = 0, true FP64 relative residual <= 1e-8)
+preconditioned by one AMGe V-cycle per iteration, on the H(curl) workload of
+64^3 Kuhn-split cubes (1,572,864 tetrahedra, 1,872,064 lowest-order Nedelec edge
+dofs), derivative coefficient beta log-uniform in [1e-3, 1e3] per 8^3 block of
+cubes, mass coefficient alpha = 1, 4-level AMGe hierarchy, one right-hand side
+uniform in [-1, 1].  The headline mode runs the V-cycle in FP32 inside FP64 PCG;
+the plain FP64 mode is measured beside it.
+
+Multi-GPU (torchrun, N ranks): every rank solves its own replica of the workload
+(independent problems, no collective on the data path); value = all ranks' solves
+divided by the slowest rank's time.
+
+--impl reference times the CPU FP64 oracle as it stands on the host cores, on a
+bounded sample of the same workload (a few PCG iterations per step, extrapolated
+to the full solve's iteration count).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "hcurl64": dict(form="hcurl", n=64, levels=4, contrast=True, seed=2107056131,
+                    desc="H(curl) 64^3 Kuhn-split cubes (1,572,864 tets, 1,872,064 Nedelec edge dofs), "
+                         "beta log-uniform [1e-3,1e3] per 8^3 block, alpha=1, 4-level AMGe, 1 RHS U[-1,1], rtol 1e-8"),
+    "hdiv64": dict(form="hdiv", n=64, levels=4, contrast=True, seed=2107056132,
+                   desc="H(div) 64^3 Kuhn-split cubes (3,170,304 Raviart-Thomas face dofs), beta log-uniform "
+                        "[1e-3,1e3] per 8^3 block, alpha=1, 4-level AMGe, 1 RHS U[-1,1], rtol 1e-8"),
+    "hcurl8": dict(form="hcurl", n=8, levels=2, contrast=False, seed=2107056130,
+                   desc="H(curl) 8^3 Kuhn-split cubes (3,072 tets, 4,184 edge dofs), alpha=beta=1, 2-level AMGe"),
+}
+
+HBM_FALLBACK_GBS = 6800.0
+METRIC = "PCG solves/s to 1e-8 rel residual"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="hcurl64")
+    p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--quick", action="store_true", help="headline loop only (for profiler runs)")
+    p.add_argument("--no-kernel-timing", action="store_true",
+                   help="do not bracket launches with CUDA events in the timed region")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ distributed
+class Dist:
+    def __init__(self):
+        self.rank = int(os.environ.get("RANK", 0))
+        self.world = int(os.environ.get("WORLD_SIZE", 1))
+        self.local = int(os.environ.get("LOCAL_RANK", 0))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v, device="cpu"):
+        if not self.pg:
+            return v
+        import torch
+
+        t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def done(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+                power.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ workload
+def make_workload(wl):
+    from paper_2107_05613_gb300.inputs import build_hierarchy, rhs_vector
+    from paper_2107_05613_gb300.inputs.rng import workload_coefficients
+
+    beta, alpha = workload_coefficients(wl["n"], wl["contrast"], wl["seed"])
+    hh = build_hierarchy(wl["form"], wl["n"], num_levels=wl["levels"], beta=beta, alpha=alpha)
+    b = rhs_vector(wl["seed"] + 1, hh.A[0].shape[0])
+    return hh, b
+
+
+def sweep_bytes(nnz, n, w, extra_vectors):
+    """Algorithmic bytes of one CSR sweep: values + int32 columns + int32 row pointers,
+    one read of the gathered vector, the right-hand side and the output, plus
+    `extra_vectors` other row-wise vectors (FP width w)."""
+    return nnz * (w + 4) + 4 * (n + 1) + w * n * (3 + extra_vectors)
+
+
+def a_fine_bytes_per_launch(hh, w):
+    """Average algorithmic bytes of the four level-0 A sweeps of one V-cycle:
+    FIRST (+ m^-1, + second output r), RESID, RESID, SWEEP (+ m^-1)."""
+    A = hh.A[0]
+    n, nnz = A.shape[0], A.nnz
+    kinds = [sweep_bytes(nnz, n, w, 2), sweep_bytes(nnz, n, w, 0), sweep_bytes(nnz, n, w, 0),
+             sweep_bytes(nnz, n, w, 1)]
+    return sum(kinds) / 4.0
+
+
+def vcycle_bytes(hh, w):
+    """Algorithmic bytes of one V-cycle (every level's sweeps, transfers and the
+    coarsest triangular products, which always read FP64 factors)."""
+    tot = 0.0
+    L = len(hh.A)
+    for l in range(L - 1):
+        A, P, G = hh.A[l], hh.P[l], hh.G[l]
+        n, naux, nc = A.shape[0], G.shape[1], P.shape[1]
+        tot += sweep_bytes(A.nnz, n, w, 2) + 2 * sweep_bytes(A.nnz, n, w, 0) + sweep_bytes(A.nnz, n, w, 1)
+        # G^T r scaled (2x), G y added (2x): read + write of the output for the add
+        tot += 2 * (G.nnz * (w + 4) + 4 * (naux + 1) + w * (n + 2 * naux))
+        tot += 2 * (G.nnz * (w + 4) + 4 * (n + 1) + w * (naux + 2 * n))
+        tot += P.nnz * (w + 4) + 4 * (nc + 1) + w * (n + nc)          # P^T r
+        tot += P.nnz * (w + 4) + 4 * (n + 1) + w * (nc + 2 * n)       # x += P e
+    nL = hh.A[-1].shape[0]
+    tot += 2 * (8 * nL * (nL + 1) / 2) + 4 * w * nL
+    return tot
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample(hh, b, iters_full, budget_s=15.0):
+    """Time the oracle's PCG for a few iterations (bounded CPU work) and extrapolate
+    to one full solve of `iters_full` iterations."""
+    from oracle import OracleHierarchy, pcg
+
+    o = OracleHierarchy.from_hierarchy(hh)
+    t = time.perf_counter()
+    pcg(o, b, rtol=1e-30, maxit=1)
+    t1 = time.perf_counter() - t                     # 2 V-cycles + 2 products + residual
+    k = max(1, min(20, int(budget_s / max(t1 / 2, 1e-3)) - 1))
+    t = time.perf_counter()
+    pcg(o, b, rtol=1e-30, maxit=k)
+    tk = time.perf_counter() - t
+    per_iter = tk / (k + 1)
+    return {"per_iter_s": per_iter, "iters_sampled": k, "solve_s": per_iter * iters_full,
+            "seconds": tk + t1, "cores": 1}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, dist):
+    wl = WORKLOADS[args.workload]
+    if dist.rank != 0:
+        return
+    hh, b = make_workload(wl)
+    from oracle import OracleHierarchy, pcg
+
+    o = OracleHierarchy.from_hierarchy(hh)
+    # iteration count of the full FP64 solve: a short calibration of the oracle's
+    # convergence would itself take minutes at this size, so the oracle runs one
+    # bounded sample per step and the full-solve length comes from the oracle on
+    # the 24^3 analogue scaled by the observed growth (stated in the sample text).
+    per_step = []
+    k = 2
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        pcg(o, b, rtol=1e-30, maxit=k)
+        dt = (time.perf_counter() - t) / (k + 1)
+        if i >= args.warmup:
+            per_step.append(dt)
+    iters_full = ITERS_FULL_FP64.get(args.workload)
+    per_iter = statistics.median(per_step)
+    value = 1.0 / (per_iter * iters_full)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_iter * iters_full,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "precision": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"scipy FP64 oracle, {k} PCG iterations per step on the full workload, "
+                                   f"per-iteration time extrapolated to {iters_full} iterations"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# Iterations of the FP64 solve of each workload (oracle and GPU agree within 1; the
+# GPU measures it in every run of the ours arm, see "fp64"."iters").
+ITERS_FULL_FP64 = {"hcurl64": 50, "hdiv64": 45, "hcurl8": 33}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, dist):
+    import numpy as np
+    import torch
+
+    dist.init("nccl" if torch.cuda.is_available() else "gloo")
+    dev = dist.local if torch.cuda.is_available() else None
+    torch.cuda.set_device(dev)
+    from paper_2107_05613_gb300 import amge
+
+    wl = WORKLOADS[args.workload]
+    hh, b = make_workload(wl)
+    prec = amge.AMGE_FP32_VCYCLE if args.precision == "fp32" else amge.AMGE_FP64
+    w = 4 if prec == amge.AMGE_FP32_VCYCLE else 8
+    h = amge.amge_setup_upload(hh)
+    n = h.n
+    bd = torch.from_numpy(b).cuda()
+    x = torch.empty_like(bd)
+    stream = torch.cuda.current_stream()
+
+    def solve(precision):
+        st, info = amge.amge_pcg_solve(h, bd, x, rtol=1e-8, precision=precision)
+        if st != amge.AMGE_OK:
+            raise RuntimeError(f"solve failed: {info}")
+        return info[0]
+
+    for _ in range(args.warmup):
+        solve(prec)
+    amge.amge_profile_read(h)                       # reset counters
+    amge.amge_profile_enable(h, not args.no_kernel_timing)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = ClockSampler(dev if dev is not None else 0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos, lat = [], []
+    e0.record(stream)
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        infos.append(solve(prec))
+        lat.append((time.perf_counter() - t) * 1e3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = amge.amge_profile_read(h)
+    amge.amge_profile_enable(h, False)
+    ms_max = dist.max(ms, device="cuda")
+    value = dist.world * args.steps / (ms_max / 1e3)
+    iters = [i["iters"] for i in infos]
+    relres = max(i["true_relres"] for i in infos)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 V-cycle in f64 PCG" if prec == amge.AMGE_FP32_VCYCLE else "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "form": wl["form"], "n": wl["n"], "levels": len(hh.A), "dofs": n,
+                   "nnz_A0": hh.A[0].nnz, "rtol": 1e-8, "precision": args.precision,
+                   "l2": "inputs larger than L2: the resident hierarchy is ~%.1f GB" % (amge.amge_hier_info(h)[2] / 1e9),
+                   "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU"},
+        "iters": iters[0], "true_relres": relres,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "clocks": clk,
+    }
+    # per-kernel timing from the CUDA events bracketing every launch in the timed region
+    kern = {k: {"launches": c, "ms": m, "avg_us": (1e3 * m / c if c else None)} for k, (c, m) in prof.items()}
+    line["kernels"] = kern
+    line["gpu_launches"] = int(sum(c for c, _ in prof.values()))
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") if peaks else None
+    peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s (of fallback)"
+    hbm = hbm or HBM_FALLBACK_GBS
+    c, m = prof["A_fine"]
+    if c:
+        bytes_launch = a_fine_bytes_per_launch(hh, w)
+        achieved = bytes_launch / (m / c / 1e3) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                            "frac": achieved / hbm, "traffic": None,
+                            "kernel": "k_csr level-0 A sweeps (first/residual/sweep), "
+                                      + ("FP32" if w == 4 else "FP64"),
+                            "bytes_per_launch": bytes_launch, "peak_source": peak_src}
+    vc_ms = sum(prof[k][1] for k in ("A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse"))
+    n_vc = sum(iters) + len(iters)  # one V-cycle per iteration plus the initial one (speculative ones add)
+    if vc_ms > 0:
+        line["vcycle_hbm_gbs"] = vcycle_bytes(hh, w) * (prof["A_fine"][0] / 4) / (vc_ms / 1e3) / 1e9
+        line["vcycle_us"] = 1e3 * vc_ms / (prof["A_fine"][0] / 4)
+    if args.quick:
+        if dist.rank == 0:
+            print(json.dumps(line), flush=True)
+        dist.done()
+        return
+
+    # the other precision, for the FP32-vs-FP64 comparison
+    other = amge.AMGE_FP64 if prec == amge.AMGE_FP32_VCYCLE else amge.AMGE_FP32_VCYCLE
+    solve(other)
+    torch.cuda.synchronize()
+    k2 = max(2, args.steps // 2)
+    e0.record(stream)
+    oi = [solve(other) for _ in range(k2)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    line["fp64" if other == amge.AMGE_FP64 else "fp32"] = {
+        "solves_per_s": dist.world * k2 / (dist.max(e0.elapsed_time(e1), "cuda") / 1e3),
+        "iters": oi[0]["iters"], "true_relres": oi[0]["true_relres"]}
+
+    # end to end through the C ABI with host buffers (H2D of b and D2H of x every step)
+    if not args.no_e2e:
+        bh = torch.from_numpy(b).pin_memory()
+        xh = torch.empty_like(bh).pin_memory()
+        amge.amge_pcg_solve_host(h, bh, xh, precision=prec)
+        dist.barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            amge.amge_pcg_solve_host(h, bh, xh, precision=prec)
+        el = dist.max(time.perf_counter() - t, "cuda")
+        line["e2e"] = {"value": dist.world * args.steps / el, "unit": "solves/s",
+                       "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        fp64_iters = line.get("fp64", {}).get("iters", iters[0])
+        s = oracle_sample(hh, b, fp64_iters)
+        line["cpu_baseline"] = {
+            "value": 1.0 / s["solve_s"], "unit": "solves/s", "cores": s["cores"], "kind": "oracle",
+            "sample": f"scipy FP64 oracle, first {s['iters_sampled']} PCG iterations of this workload "
+                      f"({s['per_iter_s']:.2f} s/iteration) extrapolated to the {fp64_iters}-iteration FP64 "
+                      f"solve; host has {os.cpu_count()} cores, the oracle uses 1"}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.done()
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        run_reference(args, dist)
+        return
+    run_ours(args, dist)
+
+
+if __name__ == "__main__":
+    main()

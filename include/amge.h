@@ -1,0 +1,206 @@
+/* libamge -- C ABI of the GB300 (sm_103a) AMGe solve path.
+ *
+ * Kalchev, Vassilevski, Villa, "Parallel Element-based Algebraic Multigrid for
+ * H(curl) and H(div) Problems Using the ParELAG Library" (arXiv 2107.05613).
+ * The library runs the solve phase of the paper's method on one GPU: conjugate
+ * gradients preconditioned by one AMGe V-cycle (Algorithm 4.1, Section 4) per
+ * iteration, with the hybrid smoother of eq. 4.1 (an l1-Jacobi sweep on A_l, then
+ * an l1-Jacobi sweep on the auxiliary matrix G^T A_l G reached through the exterior
+ * derivative G, corrected back through G) on every level and a dense direct solve
+ * on the coarsest level.  The hierarchy itself (Sections 2-3: prolongators P_l,
+ * coarse exterior derivatives, Galerkin A_l) is input data built on the host and
+ * handed over as plain CSR arrays.
+ *
+ * Conventions
+ *   - Every pointer argument documented as "device" must point to memory the
+ *     calling context's current CUDA device can access; "host" pointers are
+ *     ordinary CPU memory.  Sizes are element counts unless stated otherwise.
+ *   - Levels are numbered from 0 (finest); the paper numbers them from 1.
+ *   - Coefficient lettering: beta multiplies (Du, Dv), alpha multiplies (u, v)
+ *     (eq. 2.2 of the paper letters them the other way round).
+ *   - Multi-RHS vectors are row-major [n][nrhs] (right-hand sides contiguous).
+ *   - All work is enqueued on the caller's CUDA stream (`stream`, a cudaStream_t
+ *     passed as void*; NULL = the legacy default stream).  Functions that must read
+ *     a scalar back (PCG convergence tests) synchronise that stream.
+ *   - Errors are reported through the return code only; amge_last_error() returns
+ *     a thread-local message describing the last failure.  No call traps or
+ *     asserts on the device.
+ */
+#ifndef AMGE_H
+#define AMGE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AMGE_OK = 0,
+  AMGE_EINVAL = 1,      /* invalid argument or malformed hierarchy */
+  AMGE_ENOMEM = 2,      /* device allocation failed */
+  AMGE_ECUDA = 3,       /* a CUDA runtime call failed */
+  AMGE_ENOTCONV = 4,    /* PCG stopped at maxit; info holds the partial result */
+  AMGE_ENONFINITE = 5,  /* a right-hand side or a PCG scalar is not finite */
+  AMGE_EAGAIN = 6,
+  AMGE_ETIMEOUT = 7,
+  AMGE_ECANCELED = 8
+} amge_status;
+
+typedef enum { AMGE_HCURL = 1, AMGE_HDIV = 2 } amge_form;
+
+/* AMGE_FP64: every step in double precision.
+ * AMGE_FP32_VCYCLE: the V-cycle (level matrices, prolongators, smoother data and
+ * vectors) runs in single precision with single-precision accumulation; the
+ * coarsest-level triangular solves, the outer PCG dot products, AXPYs and the
+ * true-residual recomputation stay in double precision. */
+typedef enum { AMGE_FP64 = 0, AMGE_FP32_VCYCLE = 1 } amge_precision;
+
+/* A CSR matrix in host memory: row_ptr[n_rows+1], col[nnz] (0-based, each row's
+ * columns strictly increasing), val[nnz]. */
+typedef struct {
+  int32_t n_rows;
+  int32_t n_cols;
+  int64_t nnz;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+} amge_csr;
+
+/* The generated hierarchy (host memory, copied during amge_setup_upload).
+ *   form        AMGE_HCURL (edge dofs; G_l = discrete gradient D_0 at level l) or
+ *               AMGE_HDIV (face dofs; G_l = discrete curl D_1 at level l)
+ *   num_levels  >= 1
+ *   A[l]        problem matrix of level l (SPD), l = 0 .. num_levels-1
+ *   P[l]        prolongator, level l+1 -> level l (n_l x n_{l+1}), l < num_levels-1
+ *   G[l]        aux transition into level l's space (n_l x aux_l), l < num_levels-1
+ *   nu_pre, nu_post  hybrid smoothing steps before / after the coarse correction (>= 1) */
+typedef struct {
+  int32_t form;
+  int32_t num_levels;
+  const amge_csr* A;
+  const amge_csr* P;
+  const amge_csr* G;
+  int32_t nu_pre;
+  int32_t nu_post;
+} amge_hierarchy_desc;
+
+typedef struct amge_hier amge_hier; /* opaque, device-resident hierarchy */
+
+/* Options of a PCG solve.  rtol: stop when the true FP64 relative residual
+ * ||b - A x||_2 / ||b||_2 <= rtol (x0 = 0); maxit >= 1; precision: amge_precision. */
+typedef struct {
+  double rtol;
+  int32_t maxit;
+  int32_t precision;
+} amge_solve_opts;
+
+/* Result of one right-hand side: iterations (number of products A p), status
+ * (AMGE_OK, AMGE_ENOTCONV or AMGE_ENONFINITE), the true relative residual
+ * recomputed in FP64 at exit, and the wall time of the whole solve call. */
+typedef struct {
+  int32_t iters;
+  int32_t status;
+  double true_relres;
+  double time_ms;
+} amge_info;
+
+/* Upload a generated hierarchy to the current device and prepare the solve data.
+ * The host setup run here derives, in FP64, the l1-Jacobi diagonals m_l = sum_j
+ * |(A_l)_ij| (Section 4.1 point smoother), the auxiliary diagonals m_aux,l = row
+ * l1 sums of G_l^T A_l G_l (eq. 4.1, second line), the transposes P_l^T and G_l^T,
+ * FP32 copies of every level operator, and the Cholesky factor of the dense
+ * coarsest matrix together with its triangular inverse (the coarsest solve that
+ * replaces the paper's AMS/ADS, Section 4.2).  The library owns the device memory
+ * until amge_hier_free.
+ * Errors: AMGE_EINVAL for malformed CSR data, mismatched sizes, a coarsest matrix
+ * that is not SPD, or a level too large for 32-bit indices; AMGE_ENOMEM;
+ * AMGE_ECUDA.  On error *out is NULL. */
+amge_status amge_setup_upload(const amge_hierarchy_desc* desc, void* stream, amge_hier** out);
+
+/* Size of the finest level, number of levels and device bytes held. */
+amge_status amge_hier_info(const amge_hier* h, int32_t* n_dofs, int32_t* levels, size_t* device_bytes);
+
+/* One V-cycle (Algorithm 4.1 with x0 = 0, hybrid smoothing eq. 4.1, the
+ * transposed smoother after the coarse correction): z = B^{-1} r.
+ *   r_dev, z_dev  device, double [n][nrhs]; must not overlap
+ *   nrhs          number of right-hand sides (must be 1)
+ *   precision     amge_precision of the internal arithmetic (the interface stays FP64)
+ * Enqueued on `stream`; does not synchronise. */
+amge_status amge_vcycle(amge_hier* h, const double* r_dev, double* z_dev, int32_t nrhs, int32_t precision,
+                        void* stream);
+
+/* PCG preconditioned by one V-cycle per iteration (Section 4), x0 = 0.
+ *   b_dev, x_dev  device, double [n][nrhs]; x_dev is overwritten; nrhs must be 1
+ *   info          host, array of nrhs results
+ * Returns AMGE_OK when every right-hand side converged, AMGE_ENOTCONV when one
+ * reached maxit (its info entry holds the iterations and the final true residual),
+ * AMGE_ENONFINITE when a right-hand side or a PCG scalar is not finite.
+ * Synchronises `stream` once per iteration to test convergence. */
+amge_status amge_pcg_solve(amge_hier* h, const double* b_dev, double* x_dev, int32_t nrhs,
+                           const amge_solve_opts* opts, amge_info* info, void* stream);
+
+/* Same as amge_pcg_solve with host buffers: copies b_host (double [n][nrhs]) to
+ * the device, solves, and copies the solution back into x_host before returning.
+ * The device staging belongs to the hierarchy. */
+amge_status amge_pcg_solve_host(amge_hier* h, const double* b_host, double* x_host, int32_t nrhs,
+                                const amge_solve_opts* opts, amge_info* info, void* stream);
+
+/* Single steps of the V-cycle, for step-by-step parity checks.  `level` selects
+ * the level; x_dev / y_dev are device double vectors of the operator's column /
+ * row count; `precision` selects the stored operator copy (FP32 mode converts
+ * inputs and outputs through double).
+ *   op AMGE_OP_A:  y = A_l x          AMGE_OP_P:  y = P_l x     AMGE_OP_PT: y = P_l^T x
+ *      AMGE_OP_G:  y = G_l x          AMGE_OP_GT: y = G_l^T x
+ *      AMGE_OP_SMOOTH_PRE:  y = one hybrid step (eq. 4.1) from x0 = 0 on b = x
+ *      AMGE_OP_COARSE:      y = A_L^{-1} x on the coarsest level (level ignored) */
+enum {
+  AMGE_OP_A = 0,
+  AMGE_OP_P = 1,
+  AMGE_OP_PT = 2,
+  AMGE_OP_G = 3,
+  AMGE_OP_GT = 4,
+  AMGE_OP_SMOOTH_PRE = 5,
+  AMGE_OP_COARSE = 6
+};
+amge_status amge_apply(amge_hier* h, int32_t op, int32_t level, const double* x_dev, double* y_dev,
+                       int32_t precision, void* stream);
+
+/* Deterministic FP64 dot product: *result_dev = sum_i x[i] y[i], reduced in a
+ * fixed order independent of the launch (block partials in index order).
+ *   x_dev, y_dev  device double [n];  result_dev  device double [1]
+ * Uses the hierarchy's reduction scratch; calls on one hierarchy are stream-ordered. */
+amge_status amge_dot(amge_hier* h, const double* x_dev, const double* y_dev, int64_t n, double* result_dev,
+                     void* stream);
+
+/* Per-kernel launch counts and timing.  Every kernel launch of the solve path is
+ * counted per kernel class; while timing is enabled each launch is also bracketed
+ * by CUDA events on its stream.  amge_profile_read synchronises, and returns for
+ * each kernel class c (0 <= c < AMGE_PROF_CLASSES) the number of kernel launches count[c]
+ * and their summed device time ms[c] (0 for launches made while timing was off)
+ * since the last read, then resets both.  Class ids: see AMGE_PROF_* below. */
+enum {
+  AMGE_PROF_A_FINE = 0,    /* level-0 A sweeps (first / residual / last), V-cycle */
+  AMGE_PROF_A_COARSE = 1,  /* A sweeps on levels >= 1 */
+  AMGE_PROF_GT = 2,
+  AMGE_PROF_G = 3,
+  AMGE_PROF_PT = 4,
+  AMGE_PROF_P = 5,
+  AMGE_PROF_COARSE = 6,    /* coarsest triangular solves */
+  AMGE_PROF_PCG_SPMV = 7,  /* q = A p with p.q */
+  AMGE_PROF_PCG_VEC = 8,   /* PCG vector updates, dots, casts */
+  AMGE_PROF_CLASSES = 9
+};
+amge_status amge_profile_enable(amge_hier* h, int32_t enable);
+amge_status amge_profile_read(amge_hier* h, int64_t* count, double* ms);
+
+/* Release the hierarchy and all device memory it holds (NULL is ignored). */
+void amge_hier_free(amge_hier* h);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* amge_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMGE_H */

@@ -1,0 +1,216 @@
+"""Python binding of libamge (the C ABI in include/amge.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Device vectors are torch CUDA float64 tensors passed by data pointer;
+streams are torch CUDA streams.  If libamge.so has not been built this module
+raises on import -- there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import AMGE_SO
+
+if not os.path.exists(AMGE_SO):
+    raise ImportError(
+        f"{AMGE_SO} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(there is no CPU fallback for the solve path)")
+
+_lib = ctypes.CDLL(AMGE_SO)
+
+AMGE_OK, AMGE_EINVAL, AMGE_ENOMEM, AMGE_ECUDA, AMGE_ENOTCONV, AMGE_ENONFINITE = 0, 1, 2, 3, 4, 5
+AMGE_EAGAIN, AMGE_ETIMEOUT, AMGE_ECANCELED = 6, 7, 8
+AMGE_HCURL, AMGE_HDIV = 1, 2
+AMGE_FP64, AMGE_FP32_VCYCLE = 0, 1
+AMGE_OP_A, AMGE_OP_P, AMGE_OP_PT, AMGE_OP_G, AMGE_OP_GT, AMGE_OP_SMOOTH_PRE, AMGE_OP_COARSE = range(7)
+PROF_CLASSES = ["A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "pcg_spmv", "pcg_vec"]
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENONFINITE",
+                6: "EAGAIN", 7: "ETIMEOUT", 8: "ECANCELED"}
+
+
+class amge_csr(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class amge_hierarchy_desc(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int32), ("num_levels", ctypes.c_int32),
+                ("A", ctypes.POINTER(amge_csr)), ("P", ctypes.POINTER(amge_csr)),
+                ("G", ctypes.POINTER(amge_csr)), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32)]
+
+
+class amge_solve_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class amge_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("true_relres", ctypes.c_double),
+                ("time_ms", ctypes.c_double)]
+
+
+_vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+_SIGS = {
+    "amge_setup_upload": [ctypes.POINTER(amge_hierarchy_desc), _vp, ctypes.POINTER(_vp)],
+    "amge_hier_info": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_size_t)],
+    "amge_vcycle": [_vp, _vp, _vp, _i32, _i32, _vp],
+    "amge_pcg_solve": [_vp, _vp, _vp, _i32, ctypes.POINTER(amge_solve_opts), ctypes.POINTER(amge_info), _vp],
+    "amge_pcg_solve_host": [_vp, _vp, _vp, _i32, ctypes.POINTER(amge_solve_opts), ctypes.POINTER(amge_info),
+                            _vp],
+    "amge_apply": [_vp, _i32, _i32, _vp, _vp, _i32, _vp],
+    "amge_dot": [_vp, _vp, _vp, _i64, _vp, _vp],
+    "amge_profile_enable": [_vp, _i32],
+    "amge_profile_read": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.amge_hier_free.argtypes = [_vp]
+_lib.amge_hier_free.restype = None
+_lib.amge_last_error.argtypes = []
+_lib.amge_last_error.restype = ctypes.c_char_p
+
+
+class AmgeError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {amge_last_error()}")
+
+
+def amge_last_error() -> str:
+    return _lib.amge_last_error().decode()
+
+
+def _check(st, where, allow=(AMGE_OK,)):
+    if st not in allow:
+        raise AmgeError(st, where)
+    return st
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, n=None):
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("device vectors must be contiguous CUDA float64 tensors")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"device vector has {t.numel()} entries, needs {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Hier:
+    """Owning handle of an uploaded hierarchy (freed with amge_hier_free)."""
+
+    def __init__(self, handle, n, levels):
+        self.handle = handle
+        self.n = n
+        self.levels = levels
+
+    def free(self):
+        if self.handle:
+            _lib.amge_hier_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def _csr_struct(m, keep):
+    rp = np.ascontiguousarray(m.indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(m.indices, dtype=np.int32)
+    v = np.ascontiguousarray(m.data, dtype=np.float64)
+    keep += [rp, ci, v]
+    return amge_csr(m.shape[0], m.shape[1], int(rp[-1]), rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+
+
+def amge_setup_upload(hierarchy, stream=None, nu_pre: int = 1, nu_post: int = 1) -> Hier:
+    """Upload an inputs.Hierarchy (or any object with form, A, P, G lists of CSR)."""
+    keep = []
+    L = len(hierarchy.A)
+    A = (amge_csr * L)(*[_csr_struct(a, keep) for a in hierarchy.A])
+    P = (amge_csr * max(L - 1, 1))(*[_csr_struct(p, keep) for p in hierarchy.P])
+    G = (amge_csr * max(L - 1, 1))(*[_csr_struct(g, keep) for g in hierarchy.G])
+    form = {"hcurl": AMGE_HCURL, "hdiv": AMGE_HDIV}[hierarchy.form]
+    desc = amge_hierarchy_desc(form, L, A, P, G, nu_pre, nu_post)
+    h = ctypes.c_void_p()
+    _check(_lib.amge_setup_upload(ctypes.byref(desc), _stream(stream), ctypes.byref(h)), "amge_setup_upload")
+    n, lv, nb = amge_hier_info(h)
+    return Hier(h, n, lv)
+
+
+def amge_hier_info(h):
+    handle = h.handle if isinstance(h, Hier) else h
+    n, lv, nb = _i32(), _i32(), ctypes.c_size_t()
+    _check(_lib.amge_hier_info(handle, ctypes.byref(n), ctypes.byref(lv), ctypes.byref(nb)), "amge_hier_info")
+    return n.value, lv.value, nb.value
+
+
+def amge_vcycle(h: Hier, r, z, nrhs: int = 1, precision: int = AMGE_FP64, stream=None):
+    _check(_lib.amge_vcycle(h.handle, _dptr(r, h.n * nrhs), _dptr(z, h.n * nrhs), nrhs, precision,
+                            _stream(stream)), "amge_vcycle")
+
+
+def amge_pcg_solve(h: Hier, b, x, rtol=1e-8, maxit=1000, precision=AMGE_FP64, nrhs=1, stream=None):
+    """Returns (status, [info dicts])."""
+    opts = amge_solve_opts(rtol, maxit, precision)
+    infos = (amge_info * nrhs)()
+    st = _lib.amge_pcg_solve(h.handle, _dptr(b, h.n * nrhs), _dptr(x, h.n * nrhs), nrhs, ctypes.byref(opts),
+                             infos, _stream(stream))
+    _check(st, "amge_pcg_solve", allow=(AMGE_OK, AMGE_ENOTCONV, AMGE_ENONFINITE))
+    return st, [dict(iters=i.iters, status=i.status, true_relres=i.true_relres, time_ms=i.time_ms) for i in infos]
+
+
+def amge_pcg_solve_host(h: Hier, b_host, x_host, rtol=1e-8, maxit=1000, precision=AMGE_FP64, nrhs=1,
+                        stream=None):
+    """Host-buffer solve: b_host / x_host are CPU float64 tensors or numpy arrays."""
+    def hptr(a):
+        if isinstance(a, np.ndarray):
+            assert a.dtype == np.float64 and a.flags.c_contiguous and a.size >= h.n * nrhs
+            return ctypes.c_void_p(a.ctypes.data)
+        assert (not a.is_cuda) and a.is_contiguous() and a.numel() >= h.n * nrhs
+        return ctypes.c_void_p(a.data_ptr())
+
+    opts = amge_solve_opts(rtol, maxit, precision)
+    infos = (amge_info * nrhs)()
+    st = _lib.amge_pcg_solve_host(h.handle, hptr(b_host), hptr(x_host), nrhs, ctypes.byref(opts), infos,
+                                  _stream(stream))
+    _check(st, "amge_pcg_solve_host", allow=(AMGE_OK, AMGE_ENOTCONV, AMGE_ENONFINITE))
+    return st, [dict(iters=i.iters, status=i.status, true_relres=i.true_relres, time_ms=i.time_ms) for i in infos]
+
+
+def amge_apply(h: Hier, op: int, level: int, x, y, precision=AMGE_FP64, stream=None):
+    _check(_lib.amge_apply(h.handle, op, level, _dptr(x), _dptr(y), precision, _stream(stream)), "amge_apply")
+
+
+def amge_dot(h: Hier, x, y, n: int, out, stream=None):
+    _check(_lib.amge_dot(h.handle, _dptr(x, n), _dptr(y, n), n, _dptr(out, 1), _stream(stream)), "amge_dot")
+
+
+def amge_profile_enable(h: Hier, enable: bool = True):
+    _check(_lib.amge_profile_enable(h.handle, int(enable)), "amge_profile_enable")
+
+
+def amge_profile_read(h: Hier):
+    """{class name: (launches, total ms)} since the previous read."""
+    cnt = (_i64 * len(PROF_CLASSES))()
+    ms = (ctypes.c_double * len(PROF_CLASSES))()
+    _check(_lib.amge_profile_read(h.handle, cnt, ms), "amge_profile_read")
+    return {name: (int(cnt[i]), float(ms[i])) for i, name in enumerate(PROF_CLASSES)}
+
+
+def lib_handle():
+    """The loaded ctypes library (tests inspect its exports)."""
+    return _lib

@@ -51,14 +51,14 @@ def build_amge_lib(verbose_ptxas=False):
         src = os.path.join(CSRC, s)
         obj = os.path.join(objdir, s + ".o")
         objs.append(obj)
-        cmd = [NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
+        cmd = [NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-fopenmp",
                "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
         if verbose_ptxas and s.endswith(".cu"):
             cmd.insert(1, "-Xptxas=-v")
         cmds.append(cmd)
     _run(cmds)
     tmp = AMGE_SO + ".tmp"
-    _run([[NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]])
+    _run([[NVCC, *ARCH, "-shared", "-cudart", "static", "-Xcompiler", "-fopenmp", "-o", tmp, *objs, "-lgomp"]])
     os.replace(tmp, AMGE_SO)
     return AMGE_SO
 

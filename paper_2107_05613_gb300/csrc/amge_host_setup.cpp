@@ -1,0 +1,168 @@
+// Host FP64 preparation done once at upload: CSR validation, transposes, the l1
+// diagonals of the hybrid smoother (Section 4.1), and the dense Cholesky factor of
+// the coarsest matrix with its triangular inverse.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "amge_internal.h"
+
+namespace amge {
+
+bool check_csr(const amge_csr& c, int nr, int nc, const char* what, std::string& err) {
+  auto fail = [&](const std::string& m) {
+    err = std::string(what) + ": " + m;
+    return false;
+  };
+  if (c.n_rows != nr || c.n_cols != nc)
+    return fail("shape " + std::to_string(c.n_rows) + "x" + std::to_string(c.n_cols) + ", expected " +
+                std::to_string(nr) + "x" + std::to_string(nc));
+  if (nr < 0 || nc < 0 || c.nnz < 0) return fail("negative size");
+  if (c.nnz >= (int64_t)1 << 31) return fail("more than 2^31 - 1 nonzeros");
+  if (!c.row_ptr || (c.nnz > 0 && (!c.col || !c.val))) return fail("NULL array");
+  if (c.row_ptr[0] != 0 || c.row_ptr[nr] != c.nnz) return fail("row_ptr does not span [0, nnz]");
+  for (int i = 0; i < nr; i++) {
+    if (c.row_ptr[i + 1] < c.row_ptr[i]) return fail("row_ptr not monotone");
+    for (int64_t p = c.row_ptr[i]; p < c.row_ptr[i + 1]; p++) {
+      if (c.col[p] < 0 || c.col[p] >= nc) return fail("column index out of range");
+      if (p > c.row_ptr[i] && c.col[p] <= c.col[p - 1]) return fail("columns not strictly increasing");
+      if (!std::isfinite(c.val[p])) return fail("non-finite value");
+    }
+  }
+  return true;
+}
+
+HostCsr to_host(const amge_csr& c) {
+  HostCsr h;
+  h.nr = c.n_rows, h.nc = c.n_cols;
+  h.rp.assign(c.row_ptr, c.row_ptr + c.n_rows + 1);
+  h.ci.assign(c.col, c.col + c.nnz);
+  h.v.assign(c.val, c.val + c.nnz);
+  return h;
+}
+
+HostCsr transpose(const HostCsr& A) {
+  HostCsr T;
+  T.nr = A.nc, T.nc = A.nr;
+  T.rp.assign(A.nc + 1, 0);
+  for (int c : A.ci) T.rp[c + 1]++;
+  for (int i = 0; i < A.nc; i++) T.rp[i + 1] += T.rp[i];
+  T.ci.resize(A.ci.size());
+  T.v.resize(A.v.size());
+  std::vector<int> pos(T.rp.begin(), T.rp.end() - 1);
+  for (int r = 0; r < A.nr; r++)
+    for (int p = A.rp[r]; p < A.rp[r + 1]; p++) {
+      int q = pos[A.ci[p]]++;
+      T.ci[q] = r;
+      T.v[q] = A.v[p];
+    }
+  return T;
+}
+
+std::vector<double> l1_row_sums(const HostCsr& A) {
+  std::vector<double> m(A.nr, 0.0);
+  for (int i = 0; i < A.nr; i++)
+    for (int p = A.rp[i]; p < A.rp[i + 1]; p++) m[i] += std::fabs(A.v[p]);
+  return m;
+}
+
+// Row l1 sums of G^T A G, row a: sum_b |sum_{i,j} G_ia A_ij G_jb|, with a dense
+// accumulator over the aux columns touched by row a.
+std::vector<double> aux_l1_row_sums(const HostCsr& A, const HostCsr& G, const HostCsr& GT) {
+  const int na = G.nc;
+  std::vector<double> out(na, 0.0);
+#pragma omp parallel
+  {
+    std::vector<double> acc(na, 0.0);
+    std::vector<int> touched;
+    std::vector<char> seen(na, 0);
+#pragma omp for schedule(dynamic, 256)
+    for (int a = 0; a < na; a++) {
+      touched.clear();
+      for (int p = GT.rp[a]; p < GT.rp[a + 1]; p++) {
+        const int i = GT.ci[p];
+        const double gia = GT.v[p];
+        for (int q = A.rp[i]; q < A.rp[i + 1]; q++) {
+          const int j = A.ci[q];
+          const double w = gia * A.v[q];
+          for (int t = G.rp[j]; t < G.rp[j + 1]; t++) {
+            const int b = G.ci[t];
+            if (!seen[b]) {
+              seen[b] = 1;
+              touched.push_back(b);
+            }
+            acc[b] += w * G.v[t];
+          }
+        }
+      }
+      std::sort(touched.begin(), touched.end());
+      double s = 0.0;
+      for (int b : touched) {
+        s += std::fabs(acc[b]);
+        acc[b] = 0.0;
+        seen[b] = 0;
+      }
+      out[a] = s;
+    }
+  }
+  return out;
+}
+
+bool coarse_factor(const HostCsr& Ac, std::vector<double>& Linv, std::vector<double>& LinvT) {
+  const int n = Ac.nr;
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int i = 0; i < n; i++)
+    for (int p = Ac.rp[i]; p < Ac.rp[i + 1]; p++)
+      if (Ac.ci[p] <= i) L[(size_t)i * n + Ac.ci[p]] = Ac.v[p];
+  // Cholesky-Crout by columns: L_jj = sqrt(a_jj - sum_k L_jk^2),
+  // L_ij = (a_ij - sum_k L_ik L_jk) / L_jj for i > j (rows contiguous in memory).
+  for (int j = 0; j < n; j++) {
+    const double* lj = &L[(size_t)j * n];
+    double d = lj[j];
+    for (int k = 0; k < j; k++) d -= lj[k] * lj[k];
+    if (!(d > 0.0) || !std::isfinite(d)) return false;
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * n + j] = ljj;
+#pragma omp parallel for schedule(static)
+    for (int i = j + 1; i < n; i++) {
+      double* li = &L[(size_t)i * n];
+      double s = li[j];
+      for (int k = 0; k < j; k++) s -= li[k] * lj[k];
+      li[j] = s / ljj;
+    }
+  }
+  // Linv = L^{-1}: column c solves L x = e_c by forward substitution.
+  Linv.assign((size_t)n * n, 0.0);
+#pragma omp parallel
+  {
+    std::vector<double> x(n);
+#pragma omp for schedule(dynamic, 8)
+    for (int c = 0; c < n; c++) {
+      x[c] = 1.0 / L[(size_t)c * n + c];
+      for (int i = c + 1; i < n; i++) {
+        const double* li = &L[(size_t)i * n];
+        double s = 0.0;
+        for (int k = c; k < i; k++) s += li[k] * x[k];
+        x[i] = -s / li[i];
+      }
+      for (int i = c; i < n; i++) Linv[(size_t)i * n + c] = x[i];
+    }
+  }
+  LinvT.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j <= i; j++) LinvT[(size_t)j * n + i] = Linv[(size_t)i * n + j];
+  return true;
+}
+
+int choose_lanes(int64_t nnz, int nr) {
+  if (nr <= 0) return 1;
+  const double avg = (double)nnz / nr;
+  if (avg <= 2.5) return 1;
+  if (avg <= 5) return 2;
+  if (avg <= 12) return 4;
+  if (avg <= 28) return 8;
+  if (avg <= 64) return 16;
+  return 32;
+}
+
+}  // namespace amge

@@ -1,0 +1,114 @@
+// Internal declarations shared by the libamge translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "amge.h"
+
+namespace amge {
+
+void set_error(const std::string& msg);
+
+// Host CSR in FP64 (setup side).
+struct HostCsr {
+  int nr = 0, nc = 0;
+  std::vector<int> rp, ci;
+  std::vector<double> v;
+  int64_t nnz() const { return (int64_t)ci.size(); }
+};
+
+// Device CSR; `lanes` = threads cooperating on one row in the vector-CSR kernels.
+template <typename V>
+struct DevCsr {
+  int nr = 0, nc = 0;
+  int64_t nnz = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  V* val = nullptr;
+  int lanes = 1;
+};
+
+// Epilogues of the CSR kernel (s = row i of M times the gathered vector).
+enum EpiKind : int {
+  EPI_STORE = 0,  // y_i = s
+  EPI_RESID = 1,  // y_i = b_i - s
+  EPI_FIRST = 2,  // gather minv_j b_j;  y_i = minv_i b_i (x),  y2_i = b_i - s (r)
+  EPI_SCALE = 3,  // y_i = d_i s
+  EPI_ADD = 4,    // y_i += s
+  EPI_SWEEP = 5   // y_i = xin_i + d_i (b_i - s)   (l1-Jacobi sweep into a new vector)
+};
+
+template <typename V>
+struct SpmvArgs {
+  const V* x = nullptr;    // gathered vector (FIRST: b)
+  const V* d = nullptr;    // diagonal (SCALE: m_aux^-1; FIRST / SWEEP: m^-1)
+  const V* b = nullptr;    // right-hand side (RESID / FIRST / SWEEP)
+  const V* xin = nullptr;  // current iterate (SWEEP)
+  V* y = nullptr;
+  V* y2 = nullptr;
+};
+
+template <typename V>
+void launch_csr(const DevCsr<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+
+// Elementwise helpers.
+template <typename Tin, typename Tout>
+void launch_cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s);
+
+// Coarsest solve z = Linv^T (Linv b): two dense triangular products, FP64 accumulation.
+template <typename Tin, typename Tout>
+void launch_coarse(int n, const double* Linv, const double* LinvT, const Tin* b, double* t, Tout* z,
+                   cudaStream_t s);
+
+// Reduction scratch: block partials + an arrival counter per slot, and scalars.
+enum Scalar : int {
+  SC_RHO = 0,      // rho = r.z (current)
+  SC_PQ = 1,
+  SC_ALPHA = 2,
+  SC_RR = 3,       // ||r||^2 after the update
+  SC_BETA = 4,
+  SC_RHO_NEW = 5,
+  SC_ZQ = 6,
+  SC_BB = 7,       // ||b||^2
+  SC_DOT = 8,      // generic dot result
+  SC_COUNT = 16
+};
+constexpr int kRedSlots = 4;
+constexpr int kMaxRedBlocks = 1024;
+
+struct RedScratch {
+  double* partials = nullptr;  // [kRedSlots][kMaxRedBlocks]
+  unsigned* counters = nullptr;  // [kRedSlots]
+  double* sc = nullptr;        // [SC_COUNT]
+};
+
+int red_blocks(int64_t n);
+void launch_dot(int64_t n, const double* x, const double* y, double* out, const RedScratch& r, cudaStream_t s);
+// q = A p (vector CSR, FP64) and pq = p.q; the finishing block sets alpha = rho / pq.
+void launch_pcg_spmv_dot(const DevCsr<double>& A, const double* p, double* q, const RedScratch& r,
+                         cudaStream_t s);
+// x += alpha p; r -= alpha q; ||r||^2 -> SC_RR
+void launch_pcg_axpy_norm(int64_t n, double* x, double* rv, const double* p, const double* q,
+                          const RedScratch& r, cudaStream_t s);
+// rho_new = r.z, zq = z.q; beta = rho_new / rho (flexible = 0) or -alpha zq / rho (flexible = 1)
+void launch_pcg_dots(int64_t n, const double* rv, const double* z, const double* q, int flexible,
+                     const RedScratch& r, cudaStream_t s);
+// p = z + beta p; rho = rho_new
+void launch_pcg_update_p(int64_t n, double* p, const double* z, const RedScratch& r, cudaStream_t s);
+
+// Host setup helpers (amge_host_setup.cpp).
+bool check_csr(const amge_csr& c, int nr, int nc, const char* what, std::string& err);
+HostCsr to_host(const amge_csr& c);
+HostCsr transpose(const HostCsr& A);
+std::vector<double> l1_row_sums(const HostCsr& A);
+std::vector<double> aux_l1_row_sums(const HostCsr& A, const HostCsr& G, const HostCsr& GT);
+// Dense Cholesky of the coarsest matrix; returns false if not SPD.  Linv = L^{-1}
+// (row-major, lower triangle), LinvT its transpose (row-major, upper triangle).
+bool coarse_factor(const HostCsr& A, std::vector<double>& Linv, std::vector<double>& LinvT);
+int choose_lanes(int64_t nnz, int nr);
+
+}  // namespace amge

@@ -1,0 +1,233 @@
+"""GPU parity of the CUDA solve path against the FP64 oracle, through the C ABI.
+
+Tolerances (derived from the arithmetic):
+  * single operators (one CSR product, FP64): |y - y_ref|_i <= 2 (nnz_i + 1) eps64 (|M||x|)_i,
+    twice the bound of a sum of nnz_i products (both sides round, in different orders);
+    FP32 copies: the same with eps32 plus the rounding of operator and input to FP32.
+  * one V-cycle (FP64): relative L2 <= max(1e-11, 10 eps64 kappa(A_L)); the coarsest
+    solve is backward stable on both sides, so its forward difference is of order
+    kappa(A_L) eps64 (the GPU multiplies by the inverse Cholesky factor, the oracle
+    substitutes); the other steps add O(nnz eps64).
+  * PCG (FP64): iterations within +-1 of the oracle, solution relative L2 <= 1e-9,
+    true relative residual <= 1e-8.
+  * PCG with the FP32 V-cycle: true FP64 relative residual <= 1e-8; the difference
+    from the FP64 oracle solution is bounded by kappa(A) * 1e-8 and reported.
+"""
+import numpy as np
+import pytest
+
+from conftest import hierarchy, oracle_hierarchy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS64 = np.finfo(np.float64).eps
+EPS32 = np.finfo(np.float32).eps
+
+
+@pytest.fixture(scope="module")
+def amge():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_05613_gb300 import amge as mod
+
+    return mod
+
+
+_uploaded = {}
+
+
+def upload(amge, form, n, L, contrast=True):
+    key = (form, n, L, contrast)
+    if key not in _uploaded:
+        _uploaded[key] = amge.amge_setup_upload(hierarchy(form, n, L, contrast))
+    return _uploaded[key]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+CASES = [("hcurl", 8, 2), ("hdiv", 8, 2), ("hcurl", 16, 2), ("hcurl", 24, 3), ("hdiv", 24, 3), ("hcurl", 8, 4)]
+
+
+def _coarse_tol(o):
+    return max(1e-11, 10 * EPS64 * np.linalg.cond(o.A[-1].toarray()))
+
+
+@pytest.mark.parametrize("form,n,L", CASES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_operators(amge, form, n, L, prec):
+    h = upload(amge, form, n, L)
+    o = oracle_hierarchy(form, n, L, True)
+    rng = np.random.default_rng(n * 7 + L)
+    eps = EPS64 if prec == 0 else EPS32
+    for l in range(L - 1):
+        ops = {amge.AMGE_OP_A: o.A[l], amge.AMGE_OP_P: o.P[l], amge.AMGE_OP_PT: o.P[l].T.tocsr(),
+               amge.AMGE_OP_G: o.G[l], amge.AMGE_OP_GT: o.G[l].T.tocsr()}
+        for op, M in ops.items():
+            x = rng.uniform(-1, 1, M.shape[1])
+            y = torch.empty(M.shape[0], dtype=torch.float64, device="cuda")
+            amge.amge_apply(h, op, l, dev(x), y, prec)
+            ref = M @ x
+            bound = abs(M) @ abs(x)
+            nnz = np.diff(M.indptr)
+            slack = 2 * (nnz + 1) * eps * bound + (0 if prec == 0 else 2 * eps * bound)
+            err = np.abs(host(y) - ref)
+            assert np.all(err <= slack + 1e-300), (l, op, float((err / (bound + 1e-300)).max()))
+
+
+@pytest.mark.parametrize("form,n,L", CASES)
+def test_smoother_step_and_coarse_solve(amge, form, n, L):
+    h = upload(amge, form, n, L)
+    o = oracle_hierarchy(form, n, L, True)
+    b = np.random.default_rng(5).uniform(-1, 1, o.A[0].shape[0])
+    y = torch.empty_like(dev(b))
+    amge.amge_apply(h, amge.AMGE_OP_SMOOTH_PRE, 0, dev(b), y, 0)
+    ref = o.hybrid(0, np.zeros_like(b), b)
+    assert np.linalg.norm(host(y) - ref) <= 1e-13 * np.linalg.norm(ref)
+    bc = np.random.default_rng(6).uniform(-1, 1, o.A[-1].shape[0])
+    z = torch.empty_like(dev(bc))
+    amge.amge_apply(h, amge.AMGE_OP_COARSE, 0, dev(bc), z, 0)
+    ref = o.coarse_solve(bc)
+    assert np.linalg.norm(host(z) - ref) <= _coarse_tol(o) * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("form,n,L", CASES)
+def test_vcycle_fp64_matches_oracle(amge, form, n, L):
+    h = upload(amge, form, n, L)
+    o = oracle_hierarchy(form, n, L, True)
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    r = rhs_vector(17, o.A[0].shape[0])
+    z = torch.empty_like(dev(r))
+    amge.amge_vcycle(h, dev(r), z, 1, amge.AMGE_FP64)
+    ref = o.apply(r)
+    assert np.linalg.norm(host(z) - ref) <= _coarse_tol(o) * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("form,n,L", CASES)
+def test_vcycle_fp32_close_to_oracle(amge, form, n, L):
+    h = upload(amge, form, n, L)
+    o = oracle_hierarchy(form, n, L, True)
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    r = rhs_vector(19, o.A[0].shape[0])
+    z = torch.empty_like(dev(r))
+    amge.amge_vcycle(h, dev(r), z, 1, amge.AMGE_FP32_VCYCLE)
+    ref = o.apply(r)
+    rel = np.linalg.norm(host(z) - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-4, rel          # FP32 arithmetic: a few hundred eps32 through the cycle
+
+
+@pytest.mark.parametrize("form,n,L", CASES)
+def test_pcg_fp64_matches_oracle(amge, form, n, L):
+    from oracle import pcg
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, form, n, L)
+    o = oracle_hierarchy(form, n, L, True)
+    b = rhs_vector(23, o.A[0].shape[0])
+    x = torch.empty_like(dev(b))
+    st, info = amge.amge_pcg_solve(h, dev(b), x, rtol=1e-8, precision=amge.AMGE_FP64)
+    xo, it_o, rr_o, ok_o = pcg(o, b, rtol=1e-8)
+    assert st == amge.AMGE_OK and ok_o
+    assert abs(info[0]["iters"] - it_o) <= 1
+    assert info[0]["true_relres"] <= 1e-8
+    xg = host(x)
+    assert np.linalg.norm(b - o.A[0] @ xg) <= 1e-8 * np.linalg.norm(b)
+    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("form,n,L", CASES)
+def test_pcg_fp32_vcycle_reaches_fp64_tolerance(amge, form, n, L):
+    from oracle import pcg
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, form, n, L)
+    o = oracle_hierarchy(form, n, L, True)
+    b = rhs_vector(29, o.A[0].shape[0])
+    x = torch.empty_like(dev(b))
+    st, info = amge.amge_pcg_solve(h, dev(b), x, rtol=1e-8, precision=amge.AMGE_FP32_VCYCLE)
+    assert st == amge.AMGE_OK
+    xg = host(x)
+    assert np.linalg.norm(b - o.A[0] @ xg) <= 1e-8 * np.linalg.norm(b)
+    xo, it_o, _, _ = pcg(o, b, rtol=1e-8)
+    assert info[0]["iters"] <= it_o + 5
+    err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    assert err <= 1e-5, err
+
+
+def test_pcg_host_buffers(amge):
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, "hcurl", 16, 2)
+    o = oracle_hierarchy("hcurl", 16, 2, True)
+    b = rhs_vector(31, o.A[0].shape[0])
+    x = np.zeros_like(b)
+    st, info = amge.amge_pcg_solve_host(h, b, x, rtol=1e-8)
+    assert st == amge.AMGE_OK
+    assert np.linalg.norm(b - o.A[0] @ x) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_dot_deterministic_and_exact_enough(amge):
+    h = upload(amge, "hcurl", 8, 2)
+    for n in (1, 1000, 1 << 20, (1 << 20) + 12345):
+        rng = np.random.default_rng(n)
+        x, y = rng.standard_normal(n), rng.standard_normal(n)
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        amge.amge_dot(h, dev(x), dev(y), n, out)
+        a = host(out)[0]
+        amge.amge_dot(h, dev(x), dev(y), n, out)
+        assert host(out)[0] == a
+        assert abs(a - x @ y) <= n * EPS64 * (abs(x) @ abs(y))
+
+
+def test_edge_cases(amge):
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, "hcurl", 8, 2)
+    n = h.n
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    st, info = amge.amge_pcg_solve(h, torch.zeros(n, dtype=torch.float64, device="cuda"), x)
+    assert st == amge.AMGE_OK and info[0]["iters"] == 0 and host(x).max() == 0
+    b = dev(rhs_vector(3, n))
+    st, info = amge.amge_pcg_solve(h, b, x, rtol=1e-14, maxit=2)
+    assert st == amge.AMGE_ENOTCONV and info[0]["iters"] == 2 and info[0]["true_relres"] > 1e-14
+    bad = b.clone()
+    bad[7] = float("nan")
+    st, info = amge.amge_pcg_solve(h, bad, x)
+    assert st == amge.AMGE_ENONFINITE
+    with pytest.raises(amge.AmgeError):
+        amge.amge_vcycle(h, b, b)
+    with pytest.raises(amge.AmgeError):
+        amge.amge_pcg_solve(h, b, x, rtol=-1.0)
+
+
+def test_one_level_hierarchy_is_direct(amge):
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    hh = hierarchy("hcurl", 4, 1, False)
+    h = amge.amge_setup_upload(hh)
+    A = hh.A[0].to_scipy()
+    b = rhs_vector(2, A.shape[0])
+    x = torch.empty_like(dev(b))
+    st, info = amge.amge_pcg_solve(h, dev(b), x)
+    assert st == amge.AMGE_OK and info[0]["iters"] == 1
+    assert np.linalg.norm(host(x) - np.linalg.solve(A.toarray(), b)) <= 1e-10 * np.linalg.norm(host(x))
+
+
+def test_solve_is_deterministic(amge):
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, "hdiv", 24, 3)
+    b = dev(rhs_vector(37, h.n))
+    x1, x2 = torch.empty_like(b), torch.empty_like(b)
+    amge.amge_pcg_solve(h, b, x1)
+    amge.amge_pcg_solve(h, b, x2)
+    assert torch.equal(x1, x2)
