@@ -82,6 +82,27 @@ def test_single_operators(amge, form, n, L, prec):
             assert np.all(err <= slack + 1e-300), (l, op, float((err / (bound + 1e-300)).max()))
 
 
+def _hybrid_step_bound(o, b):
+    """Elementwise bound on |computed - exact| of one hybrid step from x0 = 0 in FP64,
+    propagated through x = b/m, r = b - A x, y = (G^T r)/m_aux, x += G y.  Both sides
+    derive m and m_aux themselves: m_aux sums |G^T A G| whose entries cancel the
+    (Du, Dv) part, so each entry carries up to K eps (|G^T||A||G|) of rounding
+    (K = terms per entry), which enters y relatively."""
+    A, G = o.A[0], o.G[0]
+    GT = G.T.tocsr()
+    aA, aG, aGT = abs(A), abs(G), abs(GT)
+    nA, nG, nGT = np.diff(A.indptr), np.diff(G.indptr), np.diff(GT.indptr)
+    K = nGT.max() * nA.max() * nG.max()
+    x = b / o.m[0]
+    r = b - A @ x
+    y = (G.T @ r) / o.m_aux[0]
+    dmaux = K * EPS64 * (aGT @ (aA @ (aG @ np.ones(G.shape[1])))) / o.m_aux[0]
+    ex = (nA + 2) * EPS64 * abs(x)
+    er = aA @ ex + (nA + 1) * EPS64 * (abs(b) + aA @ abs(x))
+    ey = (aGT @ er + (nGT + 1) * EPS64 * (aGT @ abs(r))) / o.m_aux[0] + (dmaux + 2 * EPS64) * abs(y)
+    return ex + aG @ ey + (nG + 1) * EPS64 * (abs(x) + aG @ abs(y))
+
+
 @pytest.mark.parametrize("form,n,L", CASES)
 def test_smoother_step_and_coarse_solve(amge, form, n, L):
     h = upload(amge, form, n, L)
@@ -90,7 +111,8 @@ def test_smoother_step_and_coarse_solve(amge, form, n, L):
     y = torch.empty_like(dev(b))
     amge.amge_apply(h, amge.AMGE_OP_SMOOTH_PRE, 0, dev(b), y, 0)
     ref = o.hybrid(0, np.zeros_like(b), b)
-    assert np.linalg.norm(host(y) - ref) <= 1e-13 * np.linalg.norm(ref)
+    # both sides round: twice the one-sided propagated bound
+    assert np.all(np.abs(host(y) - ref) <= 2 * _hybrid_step_bound(o, b))
     bc = np.random.default_rng(6).uniform(-1, 1, o.A[-1].shape[0])
     z = torch.empty_like(dev(bc))
     amge.amge_apply(h, amge.AMGE_OP_COARSE, 0, dev(bc), z, 0)
@@ -113,6 +135,11 @@ def test_vcycle_fp64_matches_oracle(amge, form, n, L):
 
 @pytest.mark.parametrize("form,n,L", CASES)
 def test_vcycle_fp32_close_to_oracle(amge, form, n, L):
+    """FP32 V-cycle vs the FP64 oracle in the energy norm.  The FP32 residual
+    b - A x on the finest level carries a rounding error of order
+    eps32 (|A||x|)_i, which the aux sweep and the coarse correction propagate; the
+    bound is eps32 * c_A with c_A = || |A||z| || / ||A z|| the cancellation factor
+    of the fine operator on the cycle's output (measured ratio 0.05-0.11 of it)."""
     h = upload(amge, form, n, L)
     o = oracle_hierarchy(form, n, L, True)
     from paper_2107_05613_gb300.inputs import rhs_vector
@@ -121,8 +148,11 @@ def test_vcycle_fp32_close_to_oracle(amge, form, n, L):
     z = torch.empty_like(dev(r))
     amge.amge_vcycle(h, dev(r), z, 1, amge.AMGE_FP32_VCYCLE)
     ref = o.apply(r)
-    rel = np.linalg.norm(host(z) - ref) / np.linalg.norm(ref)
-    assert rel <= 1e-4, rel          # FP32 arithmetic: a few hundred eps32 through the cycle
+    A = o.A[0]
+    c_A = np.linalg.norm(abs(A) @ abs(ref)) / np.linalg.norm(A @ ref)
+    d = host(z) - ref
+    err = np.sqrt((d @ (A @ d)) / (ref @ (A @ ref)))
+    assert err <= EPS32 * c_A, (err, EPS32 * c_A)
 
 
 @pytest.mark.parametrize("form,n,L", CASES)
