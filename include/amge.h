@@ -180,7 +180,7 @@ amge_status amge_dot(amge_hier* h, const double* x_dev, const double* y_dev, int
  * and their summed device time ms[c] (0 for launches made while timing was off)
  * since the last read, then resets both.  Class ids: see AMGE_PROF_* below. */
 enum {
-  AMGE_PROF_A_FINE = 0,    /* level-0 A sweeps (first / residual / last), V-cycle */
+  AMGE_PROF_A_FINE = 0,    /* level-0 A sweeps of the V-cycle (residuals, the final l1 sweep) */
   AMGE_PROF_A_COARSE = 1,  /* A sweeps on levels >= 1 */
   AMGE_PROF_GT = 2,
   AMGE_PROF_G = 3,
@@ -189,7 +189,8 @@ enum {
   AMGE_PROF_COARSE = 6,    /* coarsest triangular solves */
   AMGE_PROF_PCG_SPMV = 7,  /* q = A p with p.q */
   AMGE_PROF_PCG_VEC = 8,   /* PCG vector updates, dots, casts */
-  AMGE_PROF_CLASSES = 9
+  AMGE_PROF_VCYCLE_VEC = 9, /* V-cycle elementwise products (x = m^-1 b on entry to a level) */
+  AMGE_PROF_CLASSES = 10
 };
 amge_status amge_profile_enable(amge_hier* h, int32_t enable);
 amge_status amge_profile_read(amge_hier* h, int64_t* count, double* ms);

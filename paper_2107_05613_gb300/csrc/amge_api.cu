@@ -18,7 +18,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 template <typename V>
 struct LevelDev {
   int n = 0, naux = 0;
-  DevCsr<V> A, P, PT, G, GT;
+  DevSell<V> A, P, PT, G, GT;
   V* minv = nullptr;
   V* mauxinv = nullptr;
   V *x = nullptr, *r = nullptr, *y = nullptr, *tmp = nullptr;
@@ -39,7 +39,7 @@ struct amge_hier {
   int n0 = 0;
   std::vector<LevelDev<double>> lv64;
   std::vector<LevelDev<float>> lv32;
-  DevCsr<double> A0;  // finest operator for the outer PCG
+  DevSell<double> A0;  // finest operator for the outer PCG
   int nC = 0;
   double *Linv = nullptr, *LinvT = nullptr, *ct = nullptr;
   double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
@@ -101,18 +101,24 @@ T* upload(amge_hier* h, const T* src, size_t count, cudaStream_t s) {
   return d;
 }
 
-// Upload a CSR matrix once (indices shared by both precisions).
-void upload_csr(amge_hier* h, const HostCsr& M, DevCsr<double>& d64, DevCsr<float>& d32, cudaStream_t s,
-                std::vector<std::vector<float>>& keep) {
-  d64.nr = d32.nr = M.nr;
-  d64.nc = d32.nc = M.nc;
-  d64.nnz = d32.nnz = M.nnz();
-  d64.rp = d32.rp = upload<int>(h, M.rp.data(), M.rp.size(), s);
-  d64.ci = d32.ci = upload<int>(h, M.ci.data(), M.ci.size(), s);
-  d64.val = upload<double>(h, M.v.data(), M.v.size(), s);
-  keep.emplace_back(M.v.begin(), M.v.end());
+constexpr int kSellSigma = 1024;
+
+// Upload an operator in the sliced-ELL layout once (indices shared by both precisions).
+void upload_sell(amge_hier* h, const HostCsr& M, DevSell<double>& d64, DevSell<float>& d32, cudaStream_t s,
+                 std::vector<std::vector<float>>& keep, std::vector<HostSell>& keeps) {
+  keeps.push_back(build_sell(M, kSellSigma));
+  const HostSell& S = keeps.back();
+  d64.nr = d32.nr = S.nr;
+  d64.nc = d32.nc = S.nc;
+  d64.nslices = d32.nslices = S.nslices;
+  d64.nnz = d32.nnz = S.nnz;
+  d64.stored = d32.stored = S.sptr[S.nslices];
+  d64.sptr = d32.sptr = upload<int64_t>(h, S.sptr.data(), S.sptr.size(), s);
+  d64.srow = d32.srow = upload<int>(h, S.srow.data(), S.srow.size(), s);
+  d64.ci = d32.ci = upload<int>(h, S.ci.data(), S.ci.size(), s);
+  d64.val = upload<double>(h, S.v.data(), S.v.size(), s);
+  keep.emplace_back(S.v.begin(), S.v.end());
   d32.val = upload<float>(h, keep.back().data(), keep.back().size(), s);
-  d64.lanes = d32.lanes = choose_lanes(M.nnz(), M.nr);
 }
 
 // RAII profile bracket around one kernel launch.
@@ -170,9 +176,9 @@ std::vector<LevelDev<float>>& levels<float>(amge_hier* h) {
 }
 
 template <typename V>
-void csr(amge_hier* h, int cls, const DevCsr<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+void sell(amge_hier* h, int cls, const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
   Prof p(h, cls, s);
-  launch_csr<V>(M, epi, a, s);
+  launch_sell<V>(M, epi, a, s);
 }
 
 // One V-cycle at level l: z = B_l^{-1} b (Algorithm 4.1, x0 = 0).
@@ -191,26 +197,28 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
   auto aux_sweep = [&]() {  // x += G M_aux^{-1} G^T r   (r = b - A x already formed)
     SpmvArgs<V> g;
     g.x = d.r, g.d = d.mauxinv, g.y = d.y;
-    csr<V>(h, AMGE_PROF_GT, d.GT, EPI_SCALE, g, s);
+    sell<V>(h, AMGE_PROF_GT, d.GT, EPI_SCALE, g, s);
     SpmvArgs<V> c;
     c.x = d.y, c.y = x;
-    csr<V>(h, AMGE_PROF_G, d.G, EPI_ADD, c, s);
+    sell<V>(h, AMGE_PROF_G, d.G, EPI_ADD, c, s);
   };
   auto residual = [&]() {
     SpmvArgs<V> a;
     a.x = x, a.b = b, a.y = d.r;
-    csr<V>(h, clsA, d.A, EPI_RESID, a, s);
+    sell<V>(h, clsA, d.A, EPI_RESID, a, s);
   };
   // pre-relaxation: nu_pre steps of eq. 4.1
   for (int k = 0; k < h->nu_pre; k++) {
-    if (k == 0) {
-      SpmvArgs<V> a;  // x = M^{-1} b, r = b - A x
-      a.x = b, a.d = d.minv, a.b = b, a.y = x, a.y2 = d.r;
-      csr<V>(h, clsA, d.A, EPI_FIRST, a, s);
+    if (k == 0) {  // from x0 = 0: x = M^{-1} b, then r = b - A x
+      {
+        Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
+        launch_mul<V>(d.n, d.minv, b, x, s);
+      }
+      residual();
     } else {
       SpmvArgs<V> a;  // x <- x + M^{-1} (b - A x)
       a.x = x, a.xin = x, a.d = d.minv, a.b = b, a.y = xt;
-      csr<V>(h, clsA, d.A, EPI_SWEEP, a, s);
+      sell<V>(h, clsA, d.A, EPI_SWEEP, a, s);
       std::swap(x, xt);
       residual();
     }
@@ -222,13 +230,13 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
   {
     SpmvArgs<V> a;
     a.x = d.r, a.y = c.b;
-    csr<V>(h, AMGE_PROF_PT, d.PT, EPI_STORE, a, s);
+    sell<V>(h, AMGE_PROF_PT, d.PT, EPI_STORE, a, s);
   }
   vcycle_level<V>(h, l + 1, c.b, c.z, s);
   {
     SpmvArgs<V> a;
     a.x = c.z, a.y = x;
-    csr<V>(h, AMGE_PROF_P, d.P, EPI_ADD, a, s);
+    sell<V>(h, AMGE_PROF_P, d.P, EPI_ADD, a, s);
   }
   // post-relaxation with the transposed step: aux sweep first, then the point sweep
   for (int k = 0; k < h->nu_post; k++) {
@@ -237,7 +245,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
     const bool last = (k == h->nu_post - 1);
     SpmvArgs<V> a;
     a.x = x, a.xin = x, a.d = d.minv, a.b = b, a.y = last ? z : xt;
-    csr<V>(h, clsA, d.A, EPI_SWEEP, a, s);
+    sell<V>(h, clsA, d.A, EPI_SWEEP, a, s);
     if (!last) std::swap(x, xt);
   }
 }
@@ -307,6 +315,7 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
   h->lv32.resize(L);
   std::vector<std::vector<float>> keep;
   std::vector<std::vector<double>> keepd;
+  std::vector<HostSell> keeps;
   try {
     for (int l = 0; l < L; l++) {
       HostCsr A = to_host(desc->A[l]);
@@ -334,11 +343,11 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
           mainv[i] = 1.0 / ma[i];
         }
         d64.naux = d32.naux = G.nc;
-        upload_csr(h, A, d64.A, d32.A, s, keep);
-        upload_csr(h, P, d64.P, d32.P, s, keep);
-        upload_csr(h, PT, d64.PT, d32.PT, s, keep);
-        upload_csr(h, G, d64.G, d32.G, s, keep);
-        upload_csr(h, GT, d64.GT, d32.GT, s, keep);
+        upload_sell(h, A, d64.A, d32.A, s, keep, keeps);
+        upload_sell(h, P, d64.P, d32.P, s, keep, keeps);
+        upload_sell(h, PT, d64.PT, d32.PT, s, keep, keeps);
+        upload_sell(h, G, d64.G, d32.G, s, keep, keeps);
+        upload_sell(h, GT, d64.GT, d32.GT, s, keep, keeps);
         keepd.push_back(minv);
         d64.minv = upload<double>(h, keepd.back().data(), n[l], s);
         keep.emplace_back(minv.begin(), minv.end());
@@ -372,8 +381,8 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
         h->LinvT = upload<double>(h, keepd.back().data(), (size_t)n[l] * n[l], s);
         h->ct = dalloc<double>(h, n[l]);
         if (L == 1) {
-          DevCsr<float> unused;
-          upload_csr(h, A, h->A0, unused, s, keep);
+          DevSell<float> unused;
+          upload_sell(h, A, h->A0, unused, s, keep, keeps);
           d32.b = dalloc<float>(h, n[l]);
           d32.z = dalloc<float>(h, n[l]);
         }
@@ -435,7 +444,7 @@ amge_status pcg_one(amge_hier* h, const double* b, double* x, const amge_solve_o
   auto resid_true = [&]() {  // r = b - A x in FP64
     SpmvArgs<double> a;
     a.x = x, a.b = b, a.y = h->pr;
-    csr<double>(h, AMGE_PROF_PCG_SPMV, h->A0, EPI_RESID, a, s);
+    sell<double>(h, AMGE_PROF_PCG_SPMV, h->A0, EPI_RESID, a, s);
     Prof p(h, AMGE_PROF_PCG_VEC, s);
     launch_dot(n, h->pr, h->pr, sc + SC_DOT, h->red, s);
   };
@@ -667,7 +676,7 @@ amge_status amge_apply(amge_hier* h, int32_t op, int32_t level, const double* x_
   auto run = [&](auto tag) -> amge_status {
     using V = decltype(tag);
     LevelDev<V>& d = levels<V>(h)[level];
-    const DevCsr<V>* M = nullptr;
+    const DevSell<V>* M = nullptr;
     switch (op) {
       case AMGE_OP_A: M = &d.A; break;
       case AMGE_OP_P: M = &d.P; break;
@@ -689,19 +698,20 @@ amge_status amge_apply(amge_hier* h, int32_t op, int32_t level, const double* x_
       yout = h->s32_out;
     }
     if (op == AMGE_OP_SMOOTH_PRE) {
+      launch_mul<V>(d.n, d.minv, xin, yout, s);
       SpmvArgs<V> a;
-      a.x = xin, a.d = d.minv, a.b = xin, a.y = yout, a.y2 = d.r;
-      launch_csr<V>(d.A, EPI_FIRST, a, s);
+      a.x = yout, a.b = xin, a.y = d.r;
+      launch_sell<V>(d.A, EPI_RESID, a, s);
       SpmvArgs<V> g;
       g.x = d.r, g.d = d.mauxinv, g.y = d.y;
-      launch_csr<V>(d.GT, EPI_SCALE, g, s);
+      launch_sell<V>(d.GT, EPI_SCALE, g, s);
       SpmvArgs<V> c;
       c.x = d.y, c.y = yout;
-      launch_csr<V>(d.G, EPI_ADD, c, s);
+      launch_sell<V>(d.G, EPI_ADD, c, s);
     } else {
       SpmvArgs<V> a;
       a.x = xin, a.y = yout;
-      launch_csr<V>(*M, EPI_STORE, a, s);
+      launch_sell<V>(*M, EPI_STORE, a, s);
     }
     if constexpr (!std::is_same<V, double>::value) launch_cast<float, double>(nout, h->s32_out, y_dev, s);
     return launch_status();

@@ -154,15 +154,50 @@ bool coarse_factor(const HostCsr& Ac, std::vector<double>& Linv, std::vector<dou
   return true;
 }
 
-int choose_lanes(int64_t nnz, int nr) {
-  if (nr <= 0) return 1;
-  const double avg = (double)nnz / nr;
-  if (avg <= 2.5) return 1;
-  if (avg <= 5) return 2;
-  if (avg <= 12) return 4;
-  if (avg <= 28) return 8;
-  if (avg <= 64) return 16;
-  return 32;
+HostSell build_sell(const HostCsr& M, int sigma) {
+  constexpr int C = 32;
+  HostSell S;
+  S.nr = M.nr, S.nc = M.nc, S.nnz = M.nnz();
+  S.nslices = (M.nr + C - 1) / C;
+  std::vector<int> perm(M.nr);
+  for (int i = 0; i < M.nr; i++) perm[i] = i;
+  auto len = [&](int r) { return M.rp[r + 1] - M.rp[r]; };
+  for (int w0 = 0; w0 < M.nr; w0 += sigma) {
+    const int w1 = std::min(M.nr, w0 + sigma);
+    std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int a, int b) { return len(a) > len(b); });
+  }
+  S.srow.assign((size_t)S.nslices * C, -1);
+  for (int i = 0; i < M.nr; i++) S.srow[i] = perm[i];
+  S.sptr.assign(S.nslices + 1, 0);
+  for (int s = 0; s < S.nslices; s++) {
+    int w = 0;
+    for (int j = 0; j < C; j++) {
+      const int r = S.srow[(size_t)s * C + j];
+      if (r >= 0) w = std::max(w, len(r));
+    }
+    w = (w + 1) & ~1;  // pairs
+    S.sptr[s + 1] = S.sptr[s] + (int64_t)w * C;
+  }
+  S.ci.assign(S.sptr[S.nslices], 0);
+  S.v.assign(S.sptr[S.nslices], 0.0);
+  for (int s = 0; s < S.nslices; s++) {
+    const int w = (int)((S.sptr[s + 1] - S.sptr[s]) / C);
+    for (int j = 0; j < C; j++) {
+      const int r = S.srow[(size_t)s * C + j];
+      const int l = r >= 0 ? len(r) : 0;
+      for (int k = 0; k < w; k++) {
+        const int64_t at = S.sptr[s] + (int64_t)(k / 2) * 2 * C + 2 * j + (k & 1);
+        if (k < l) {
+          S.ci[at] = M.ci[M.rp[r] + k];
+          S.v[at] = M.v[M.rp[r] + k];
+        } else {
+          S.ci[at] = l > 0 ? M.ci[M.rp[r] + l - 1] : 0;
+          S.v[at] = 0.0;
+        }
+      }
+    }
+  }
+  return S;
 }
 
 }  // namespace amge

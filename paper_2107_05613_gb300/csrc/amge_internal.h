@@ -21,22 +21,37 @@ struct HostCsr {
   int64_t nnz() const { return (int64_t)ci.size(); }
 };
 
-// Device CSR; `lanes` = threads cooperating on one row in the vector-CSR kernels.
+// Host sliced-ELL layout (SELL-C-sigma, C = 32): rows are sorted by length inside
+// windows of `sigma` consecutive rows, cut into slices of 32 rows, and each slice is
+// padded to its longest row.  Entries are stored column-major per slice in pairs:
+// pair k of lane j of slice s sits at pair index sptr[s]/2 + k*32 + j, so a warp
+// reads 32 consecutive 16-byte pairs per step.  srow maps (slice, lane) to the
+// original row (-1 for lanes past the last row).  Padding entries have value 0 and
+// a valid column of their row.
+struct HostSell {
+  int nr = 0, nc = 0, nslices = 0;
+  int64_t nnz = 0;                // stored entries of the CSR source
+  std::vector<int64_t> sptr;      // [nslices + 1], element offsets (multiples of 64)
+  std::vector<int> srow;          // [nslices * 32]
+  std::vector<int> ci;            // [sptr[nslices]]
+  std::vector<double> v;          // [sptr[nslices]]
+};
+HostSell build_sell(const HostCsr& M, int sigma);
+
 template <typename V>
-struct DevCsr {
-  int nr = 0, nc = 0;
-  int64_t nnz = 0;
-  int* rp = nullptr;
+struct DevSell {
+  int nr = 0, nc = 0, nslices = 0;
+  int64_t nnz = 0, stored = 0;
+  int64_t* sptr = nullptr;
+  int* srow = nullptr;
   int* ci = nullptr;
   V* val = nullptr;
-  int lanes = 1;
 };
 
-// Epilogues of the CSR kernel (s = row i of M times the gathered vector).
+// Epilogues of the sliced-ELL product (s = row i of M times the gathered vector).
 enum EpiKind : int {
   EPI_STORE = 0,  // y_i = s
   EPI_RESID = 1,  // y_i = b_i - s
-  EPI_FIRST = 2,  // gather minv_j b_j;  y_i = minv_i b_i (x),  y2_i = b_i - s (r)
   EPI_SCALE = 3,  // y_i = d_i s
   EPI_ADD = 4,    // y_i += s
   EPI_SWEEP = 5   // y_i = xin_i + d_i (b_i - s)   (l1-Jacobi sweep into a new vector)
@@ -44,16 +59,18 @@ enum EpiKind : int {
 
 template <typename V>
 struct SpmvArgs {
-  const V* x = nullptr;    // gathered vector (FIRST: b)
-  const V* d = nullptr;    // diagonal (SCALE: m_aux^-1; FIRST / SWEEP: m^-1)
-  const V* b = nullptr;    // right-hand side (RESID / FIRST / SWEEP)
+  const V* x = nullptr;    // gathered vector
+  const V* d = nullptr;    // diagonal (SCALE: m_aux^-1; SWEEP: m^-1)
+  const V* b = nullptr;    // right-hand side (RESID / SWEEP)
   const V* xin = nullptr;  // current iterate (SWEEP)
   V* y = nullptr;
-  V* y2 = nullptr;
 };
 
 template <typename V>
-void launch_csr(const DevCsr<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+// y = d .* x (elementwise)
+template <typename V>
+void launch_mul(int64_t n, const V* d, const V* x, V* y, cudaStream_t s);
 
 // Elementwise helpers.
 template <typename Tin, typename Tout>
@@ -88,8 +105,8 @@ struct RedScratch {
 
 int red_blocks(int64_t n);
 void launch_dot(int64_t n, const double* x, const double* y, double* out, const RedScratch& r, cudaStream_t s);
-// q = A p (vector CSR, FP64) and pq = p.q; the finishing block sets alpha = rho / pq.
-void launch_pcg_spmv_dot(const DevCsr<double>& A, const double* p, double* q, const RedScratch& r,
+// q = A p (sliced ELL, FP64) and pq = p.q; the finishing block sets alpha = rho / pq.
+void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, const RedScratch& r,
                          cudaStream_t s);
 // x += alpha p; r -= alpha q; ||r||^2 -> SC_RR
 void launch_pcg_axpy_norm(int64_t n, double* x, double* rv, const double* p, const double* q,
@@ -109,6 +126,5 @@ std::vector<double> aux_l1_row_sums(const HostCsr& A, const HostCsr& G, const Ho
 // Dense Cholesky of the coarsest matrix; returns false if not SPD.  Linv = L^{-1}
 // (row-major, lower triangle), LinvT its transpose (row-major, upper triangle).
 bool coarse_factor(const HostCsr& A, std::vector<double>& Linv, std::vector<double>& LinvT);
-int choose_lanes(int64_t nnz, int nr);
 
 }  // namespace amge

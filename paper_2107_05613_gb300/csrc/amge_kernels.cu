@@ -1,11 +1,16 @@
 // CUDA kernels of the AMGe solve path (sm_103a).
 //
-// All level operators are CSR; a row is handled by a group of LANES threads of one
-// warp (LANES = 1..32 chosen from the average row length), which stream the row's
-// column indices and values with read-only loads, gather the input vector through
-// the L1/texture path, and reduce with warp shuffles.  The epilogue fuses the
-// vector work of the hybrid smoother (eq. 4.1) and of Algorithm 4.1 into the
-// product: residuals, the l1-Jacobi sweep, diagonal scaling and correction adds.
+// Level operators are stored in a sliced-ELL layout (32 rows per slice, rows sorted
+// by length inside 1024-row windows, entries column-major per slice in 16-byte
+// pairs).  One thread computes one row: a warp streams its slice with fully
+// coalesced 16-byte loads of column-index pairs and value pairs, gathers the input
+// vector through the read-only path, and needs no cross-lane reduction.  On GB300
+// this matters for FP64: the FP64 pipe issues 1/65 of the FP32 rate, and a
+// shuffle-reduced warp-per-row layout spends three FP64 instructions per stored
+// nonzero, which made those kernels FP64-issue bound; here a row of w entries costs
+// w FMAs plus its epilogue.  The epilogue fuses the vector work of the hybrid
+// smoother (eq. 4.1) and of Algorithm 4.1: residuals, the l1-Jacobi sweep, diagonal
+// scaling and correction adds.
 //
 // Reductions (PCG dot products) are deterministic: a fixed grid (a function of n
 // only) writes block partials, and the last block to arrive sums them in index
@@ -25,71 +30,53 @@ __device__ __forceinline__ V ldg(const V* p) {
   return __ldg(p);
 }
 
-template <typename V, int LANES, int EPI>
-__global__ void __launch_bounds__(kBlock) k_csr(int nr, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                const V* __restrict__ val, SpmvArgs<V> a) {
-  const int gt = blockIdx.x * kBlock + threadIdx.x;
-  const int row = gt / LANES;
-  const int lane = gt & (LANES - 1);
-  const bool ok = row < nr;
-  int beg = 0, end = 0;
-  if (ok) {
-    beg = ldg(rp + row);
-    end = ldg(rp + row + 1);
-  }
+template <typename V>
+struct Pair;
+template <>
+struct Pair<double> {
+  using T = double2;
+};
+template <>
+struct Pair<float> {
+  using T = float2;
+};
+
+// One sliced-ELL slice per warp, one row per lane.
+template <typename V, int EPI>
+__global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __restrict__ sptr,
+                                                 const int* __restrict__ srow, const int2* __restrict__ ci2,
+                                                 const typename Pair<V>::T* __restrict__ val2, SpmvArgs<V> a) {
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nslices) return;
+  const int64_t p0 = ldg(sptr + warp) >> 1;
+  const int np = (int)((ldg(sptr + warp + 1) >> 1) - p0) >> 5;
+  const int row = ldg(srow + (size_t)warp * 32 + lane);
+  const int2* cp = ci2 + p0 + lane;
+  const typename Pair<V>::T* vp = val2 + p0 + lane;
   V s0 = V(0), s1 = V(0);
-  int j = beg + lane;
-  for (; j + LANES < end; j += 2 * LANES) {
-    const int c0 = ldg(ci + j), c1 = ldg(ci + j + LANES);
-    const V v0 = ldg(val + j), v1 = ldg(val + j + LANES);
-    V x0, x1;
-    if (EPI == EPI_FIRST) {
-      x0 = ldg(a.x + c0) * ldg(a.d + c0);
-      x1 = ldg(a.x + c1) * ldg(a.d + c1);
-    } else {
-      x0 = ldg(a.x + c0);
-      x1 = ldg(a.x + c1);
-    }
-    s0 = fma(v0, x0, s0);
-    s1 = fma(v1, x1, s1);
+#pragma unroll 2
+  for (int k = 0; k < np; k++) {
+    const int2 c = __ldg(cp + (size_t)k * 32);
+    const typename Pair<V>::T v = __ldg(vp + (size_t)k * 32);
+    s0 = fma(v.x, ldg(a.x + c.x), s0);
+    s1 = fma(v.y, ldg(a.x + c.y), s1);
   }
-  if (j < end) {
-    const int c0 = ldg(ci + j);
-    const V xv = (EPI == EPI_FIRST) ? ldg(a.x + c0) * ldg(a.d + c0) : ldg(a.x + c0);
-    s0 = fma(ldg(val + j), xv, s0);
-  }
-  V s = s0 + s1;
-#pragma unroll
-  for (int off = LANES / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (!ok || lane != 0) return;
+  if (row < 0) return;
+  const V s = s0 + s1;
   switch (EPI) {
     case EPI_STORE: a.y[row] = s; break;
     case EPI_RESID: a.y[row] = a.b[row] - s; break;
-    case EPI_FIRST: {
-      const V bi = a.b[row];
-      a.y[row] = a.d[row] * bi;
-      a.y2[row] = bi - s;
-      break;
-    }
     case EPI_SCALE: a.y[row] = a.d[row] * s; break;
     case EPI_ADD: a.y[row] += s; break;
-    case EPI_SWEEP: a.y[row] = a.xin[row] + a.d[row] * (a.b[row] - s); break;
+    case EPI_SWEEP: a.y[row] = fma(a.d[row], a.b[row] - s, a.xin[row]); break;
   }
 }
 
-template <typename V, int LANES>
-void launch_lanes(const DevCsr<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
-  const int64_t threads = (int64_t)M.nr * LANES;
-  const int grid = (int)((threads + kBlock - 1) / kBlock);
-  if (grid == 0) return;
-  switch (epi) {
-    case EPI_STORE: k_csr<V, LANES, EPI_STORE><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
-    case EPI_RESID: k_csr<V, LANES, EPI_RESID><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
-    case EPI_FIRST: k_csr<V, LANES, EPI_FIRST><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
-    case EPI_SCALE: k_csr<V, LANES, EPI_SCALE><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
-    case EPI_ADD: k_csr<V, LANES, EPI_ADD><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
-    case EPI_SWEEP: k_csr<V, LANES, EPI_SWEEP><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
-  }
+template <typename V>
+__global__ void k_mul(int64_t n, const V* __restrict__ d, const V* __restrict__ x, V* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = d[i] * x[i];
 }
 
 template <typename Tin, typename Tout>
@@ -178,37 +165,35 @@ __global__ void __launch_bounds__(kBlock) k_dot(int64_t n, const double* __restr
   if (finish_blocks<1>(&acc, r, 0, tot) && threadIdx.x == 0) *out = tot[0];
 }
 
-template <int LANES>
-__global__ void __launch_bounds__(kBlock) k_pcg_spmv_dot(int nr, const int* __restrict__ rp,
-                                                         const int* __restrict__ ci,
-                                                         const double* __restrict__ val,
+// q = A p with one row per lane over the slices of a grid-stride loop; each lane
+// accumulates its rows' p_i q_i and the block partials finish deterministically.
+__global__ void __launch_bounds__(kBlock) k_pcg_spmv_dot(int nslices, const int64_t* __restrict__ sptr,
+                                                         const int* __restrict__ srow,
+                                                         const int2* __restrict__ ci2,
+                                                         const double2* __restrict__ val2,
                                                          const double* __restrict__ p, double* __restrict__ q,
                                                          RedScratch r) {
   double contrib = 0.0;
-  // grid-stride over row groups; every warp runs whole iterations
-  const int rows_per_pass = gridDim.x * (kBlock / LANES);
-  const int lane = threadIdx.x & (LANES - 1);
-  for (int base = blockIdx.x * (kBlock / LANES); base < nr; base += rows_per_pass) {
-    const int row = base + threadIdx.x / LANES;
-    const bool ok = row < nr;
-    int beg = 0, end = 0;
-    if (ok) {
-      beg = ldg(rp + row);
-      end = ldg(rp + row + 1);
-    }
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (kBlock / 32);
+  for (int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5; warp < nslices; warp += warps) {
+    const int64_t p0 = ldg(sptr + warp) >> 1;
+    const int np = (int)((ldg(sptr + warp + 1) >> 1) - p0) >> 5;
+    const int row = ldg(srow + (size_t)warp * 32 + lane);
+    const int2* cp = ci2 + p0 + lane;
+    const double2* vp = val2 + p0 + lane;
     double s0 = 0.0, s1 = 0.0;
-    int j = beg + lane;
-    for (; j + LANES < end; j += 2 * LANES) {
-      s0 = fma(ldg(val + j), ldg(p + ldg(ci + j)), s0);
-      s1 = fma(ldg(val + j + LANES), ldg(p + ldg(ci + j + LANES)), s1);
+#pragma unroll 2
+    for (int k = 0; k < np; k++) {
+      const int2 c = __ldg(cp + (size_t)k * 32);
+      const double2 v = __ldg(vp + (size_t)k * 32);
+      s0 = fma(v.x, ldg(p + c.x), s0);
+      s1 = fma(v.y, ldg(p + c.y), s1);
     }
-    if (j < end) s0 = fma(ldg(val + j), ldg(p + ldg(ci + j)), s0);
-    double s = s0 + s1;
-#pragma unroll
-    for (int off = LANES / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (ok && lane == 0) {
+    if (row >= 0) {
+      const double s = s0 + s1;
       q[row] = s;
-      contrib = fma(p[row], s, contrib);
+      contrib = fma(ldg(p + row), s, contrib);
     }
   }
   double tot[1];
@@ -272,18 +257,28 @@ int red_blocks(int64_t n) {
 }
 
 template <typename V>
-void launch_csr(const DevCsr<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
-  switch (M.lanes) {
-    case 1: launch_lanes<V, 1>(M, epi, a, s); break;
-    case 2: launch_lanes<V, 2>(M, epi, a, s); break;
-    case 4: launch_lanes<V, 4>(M, epi, a, s); break;
-    case 8: launch_lanes<V, 8>(M, epi, a, s); break;
-    case 16: launch_lanes<V, 16>(M, epi, a, s); break;
-    default: launch_lanes<V, 32>(M, epi, a, s); break;
+void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  if (M.nslices == 0) return;
+  const int grid = (M.nslices + (kBlock / 32) - 1) / (kBlock / 32);
+  const int2* ci2 = reinterpret_cast<const int2*>(M.ci);
+  const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(M.val);
+  switch (epi) {
+    case EPI_STORE: k_sell<V, EPI_STORE><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_RESID: k_sell<V, EPI_RESID><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SCALE: k_sell<V, EPI_SCALE><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_ADD: k_sell<V, EPI_ADD><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SWEEP: k_sell<V, EPI_SWEEP><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
   }
 }
-template void launch_csr<double>(const DevCsr<double>&, int, const SpmvArgs<double>&, cudaStream_t);
-template void launch_csr<float>(const DevCsr<float>&, int, const SpmvArgs<float>&, cudaStream_t);
+template void launch_sell<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t);
+template void launch_sell<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t);
+
+template <typename V>
+void launch_mul(int64_t n, const V* d, const V* x, V* y, cudaStream_t s) {
+  if (n > 0) k_mul<V><<<vec_grid(n), kBlock, 0, s>>>(n, d, x, y);
+}
+template void launch_mul<double>(int64_t, const double*, const double*, double*, cudaStream_t);
+template void launch_mul<float>(int64_t, const float*, const float*, float*, cudaStream_t);
 
 template <typename Tin, typename Tout>
 void launch_cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s) {
@@ -308,19 +303,12 @@ void launch_dot(int64_t n, const double* x, const double* y, double* out, const 
   k_dot<<<red_blocks(n), kBlock, 0, s>>>(n, x, y, out, r);
 }
 
-void launch_pcg_spmv_dot(const DevCsr<double>& A, const double* p, double* q, const RedScratch& r,
+void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, const RedScratch& r,
                          cudaStream_t s) {
-  const int lanes = A.lanes;
-  const int rows_per_block = kBlock / lanes;
-  const int grid = std::min((A.nr + rows_per_block - 1) / rows_per_block, kMaxRedBlocks);
-  switch (lanes) {
-    case 1: k_pcg_spmv_dot<1><<<grid, kBlock, 0, s>>>(A.nr, A.rp, A.ci, A.val, p, q, r); break;
-    case 2: k_pcg_spmv_dot<2><<<grid, kBlock, 0, s>>>(A.nr, A.rp, A.ci, A.val, p, q, r); break;
-    case 4: k_pcg_spmv_dot<4><<<grid, kBlock, 0, s>>>(A.nr, A.rp, A.ci, A.val, p, q, r); break;
-    case 8: k_pcg_spmv_dot<8><<<grid, kBlock, 0, s>>>(A.nr, A.rp, A.ci, A.val, p, q, r); break;
-    case 16: k_pcg_spmv_dot<16><<<grid, kBlock, 0, s>>>(A.nr, A.rp, A.ci, A.val, p, q, r); break;
-    default: k_pcg_spmv_dot<32><<<grid, kBlock, 0, s>>>(A.nr, A.rp, A.ci, A.val, p, q, r); break;
-  }
+  const int warps_per_block = kBlock / 32;
+  const int grid = std::min((A.nslices + warps_per_block - 1) / warps_per_block, kMaxRedBlocks);
+  k_pcg_spmv_dot<<<std::max(grid, 1), kBlock, 0, s>>>(A.nslices, A.sptr, A.srow, reinterpret_cast<const int2*>(A.ci),
+                                                      reinterpret_cast<const double2*>(A.val), p, q, r);
 }
 
 void launch_pcg_axpy_norm(int64_t n, double* x, double* rv, const double* p, const double* q,
