@@ -195,6 +195,26 @@ enum {
 amge_status amge_profile_enable(amge_hier* h, int32_t enable);
 amge_status amge_profile_read(amge_hier* h, int64_t* count, double* ms);
 
+/* Coarsest-level solve z = A_L^{-1} b without any device allocation.
+ * The paper has no counterpart.  It serves callers that may not have the library
+ * allocate device memory while they solve (a latency-critical loop that must not
+ * take the device-wide synchronisation of cudaMalloc, or a host framework that
+ * owns every device byte through its own pool): they upload the hierarchy once,
+ * then pass only their own input and output vectors here.  It computes the same
+ * products as amge_apply(h, AMGE_OP_COARSE, ...) in FP64, but keeps the
+ * intermediate vector in a fixed file-scope device array of 4096 doubles (32 KiB,
+ * held by every GPU that loads the library until the process exits).
+ *   h             hierarchy uploaded on the current device
+ *   b_dev, z_dev  device double [n_L] (n_L = coarsest dofs); must not overlap
+ * Errors: AMGE_EINVAL for NULL arguments or a coarsest level larger than 4096
+ * dofs; AMGE_ECUDA if the device address of the array cannot be obtained.
+ * The first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every call
+ * shares the one array, so calls whose kernels overlap on the GPU (different
+ * streams, no ordering between them) race on it; the array needs no clearing
+ * (each call overwrites it before reading it).  Enqueued on `stream`. */
+amge_status amge_coarse_solve_noalloc(const amge_hier* h, const double* b_dev, double* z_dev, void* stream);
+
 /* Release the hierarchy and all device memory it holds (NULL is ignored). */
 void amge_hier_free(amge_hier* h);
 

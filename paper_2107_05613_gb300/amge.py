@@ -61,6 +61,7 @@ _SIGS = {
     "amge_dot": [_vp, _vp, _vp, _i64, _vp, _vp],
     "amge_profile_enable": [_vp, _i32],
     "amge_profile_read": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)],
+    "amge_coarse_solve_noalloc": [_vp, _vp, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -197,6 +198,13 @@ def amge_apply(h: Hier, op: int, level: int, x, y, precision=AMGE_FP64, stream=N
 
 def amge_dot(h: Hier, x, y, n: int, out, stream=None):
     _check(_lib.amge_dot(h.handle, _dptr(x, n), _dptr(y, n), n, _dptr(out, 1), _stream(stream)), "amge_dot")
+
+
+def amge_coarse_solve_noalloc(h: Hier, b, z, stream=None):
+    """Coarsest-level solve whose intermediate vector lives in a fixed device array
+    (no allocation by the library during the call); see include/amge.h."""
+    _check(_lib.amge_coarse_solve_noalloc(h.handle, _dptr(b), _dptr(z), _stream(stream)),
+           "amge_coarse_solve_noalloc")
 
 
 def amge_profile_enable(h: Hier, enable: bool = True):

@@ -539,6 +539,12 @@ cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
 }  // namespace
 
+void amge::coarse_factor_view(const amge_hier* h, int* n, const double** Linv, const double** LinvT) {
+  *n = h->nC;
+  *Linv = h->Linv;
+  *LinvT = h->LinvT;
+}
+
 extern "C" {
 
 const char* amge_last_error(void) { return g_last_error.c_str(); }

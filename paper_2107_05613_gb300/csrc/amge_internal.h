@@ -127,4 +127,7 @@ std::vector<double> aux_l1_row_sums(const HostCsr& A, const HostCsr& G, const Ho
 // (row-major, lower triangle), LinvT its transpose (row-major, upper triangle).
 bool coarse_factor(const HostCsr& A, std::vector<double>& Linv, std::vector<double>& LinvT);
 
+// Read-only view of a hierarchy's coarsest factor (defined in amge_api.cu).
+void coarse_factor_view(const amge_hier* h, int* n, const double** Linv, const double** LinvT);
+
 }  // namespace amge
