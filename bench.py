@@ -38,7 +38,15 @@ WORKLOADS = {
                         "[1e-3,1e3] per 8^3 block, alpha=1, 4-level AMGe, 1 RHS U[-1,1], rtol 1e-8"),
     "hcurl8": dict(form="hcurl", n=8, levels=2, contrast=False, seed=2107056130,
                    desc="H(curl) 8^3 Kuhn-split cubes (3,072 tets, 4,184 edge dofs), alpha=beta=1, 2-level AMGe"),
+    "hcurl48x32": dict(form="hcurl", n=48, levels=4, contrast=False, seed=2107056134, nrhs=32,
+                       desc="H(curl) 48^3 Kuhn-split cubes (795,024 edge dofs), alpha=beta=1, 4-level AMGe, "
+                            "32 RHS U[-1,1] solved as one block, rtol 1e-8 per column"),
 }
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one level-0 residual sweep from an
+# ncu capture (profiles/k_sell_fp64_resid_level0_hcurl64.md); only for that kernel
+# and workload, null elsewhere.
+NCU_TRAFFIC = {("hcurl64", 8): 441.7e6}
 
 HBM_FALLBACK_GBS = 6800.0
 METRIC = "PCG solves/s to 1e-8 rel residual"
@@ -156,24 +164,25 @@ def make_workload(wl):
 
     beta, alpha = workload_coefficients(wl["n"], wl["contrast"], wl["seed"])
     hh = build_hierarchy(wl["form"], wl["n"], num_levels=wl["levels"], beta=beta, alpha=alpha)
-    b = rhs_vector(wl["seed"] + 1, hh.A[0].shape[0])
+    b = rhs_vector(wl["seed"] + 1, hh.A[0].shape[0], wl.get("nrhs", 1))
     return hh, b
 
 
-def sweep_bytes(nnz, n, w, extra_vectors):
-    """Algorithmic bytes of one CSR sweep: values + int32 columns + int32 row pointers,
-    one read of the gathered vector, the right-hand side and the output, plus
-    `extra_vectors` other row-wise vectors (FP width w)."""
-    return nnz * (w + 4) + 4 * (n + 1) + w * n * (3 + extra_vectors)
+def sweep_bytes(nnz, n, w, extra_vectors, nrhs=1):
+    """Algorithmic bytes of one sweep: values + int32 columns + int32 row pointers,
+    one read of the gathered block, the right-hand side and the output, plus
+    `extra_vectors` other row-wise blocks (FP width w, nrhs columns; a diagonal
+    counts as one column)."""
+    return nnz * (w + 4) + 4 * (n + 1) + w * n * nrhs * 3 + w * n * extra_vectors
 
 
-def a_fine_bytes_per_launch(hh, w):
+def a_fine_bytes_per_launch(hh, w, nrhs=1):
     """Average algorithmic bytes of the four level-0 A sweeps of one V-cycle:
     three residuals r = b - A x and the final l1 sweep z = x + m^-1 (b - A x)
     (which also reads m^-1)."""
     A = hh.A[0]
     n, nnz = A.shape[0], A.nnz
-    kinds = [sweep_bytes(nnz, n, w, 0)] * 3 + [sweep_bytes(nnz, n, w, 1)]
+    kinds = [sweep_bytes(nnz, n, w, 0, nrhs)] * 3 + [sweep_bytes(nnz, n, w, 1, nrhs)]
     return sum(kinds) / 4.0
 
 
@@ -284,17 +293,21 @@ def run_ours(args, dist):
     x = torch.empty_like(bd)
     stream = torch.cuda.current_stream()
 
+    nrhs = wl.get("nrhs", 1)
+
     def solve(precision, strict=True, maxit=1000):
-        st, info = amge.amge_pcg_solve(h, bd, x, rtol=1e-8, maxit=maxit, precision=precision)
+        st, info = amge.amge_pcg_solve(h, bd, x, rtol=1e-8, maxit=maxit, precision=precision, nrhs=nrhs)
         if strict and st != amge.AMGE_OK:
             raise RuntimeError(f"solve failed: {info}")
-        info[0]["status_name"] = amge.STATUS_NAMES[st]
-        return info[0]
+        out = dict(info[0])
+        out["iters"] = max(i["iters"] for i in info)
+        out["true_relres"] = max(i["true_relres"] for i in info)
+        out["status_name"] = amge.STATUS_NAMES[st]
+        return out
 
     for _ in range(args.warmup):
         solve(prec)
-    amge.amge_profile_read(h)                       # reset counters
-    amge.amge_profile_enable(h, not args.no_kernel_timing)
+    amge.amge_profile_read(h)                       # reset the launch counters
     torch.cuda.synchronize()
     dist.barrier()
     clocks = ClockSampler(dev if dev is not None else 0)
@@ -311,10 +324,19 @@ def run_ours(args, dist):
     dist.barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    prof = amge.amge_profile_read(h)
-    amge.amge_profile_enable(h, False)
+    launches = amge.amge_profile_read(h)
+    # second pass of the same K steps with CUDA events around every launch, for the
+    # per-kernel durations (kept out of the headline region: the events cost time)
+    if not args.no_kernel_timing:
+        amge.amge_profile_enable(h, True)
+        for _ in range(args.steps):
+            solve(prec)
+        prof = amge.amge_profile_read(h)
+        amge.amge_profile_enable(h, False)
+    else:
+        prof = {k: (c, 0.0) for k, (c, _) in launches.items()}
     ms_max = dist.max(ms, device="cuda")
-    value = dist.world * args.steps / (ms_max / 1e3)
+    value = dist.world * args.steps * nrhs / (ms_max / 1e3)
     iters = [i["iters"] for i in infos]
     relres = max(i["true_relres"] for i in infos)
 
@@ -325,6 +347,7 @@ def run_ours(args, dist):
         "dtype": "f32 V-cycle in f64 PCG" if prec == amge.AMGE_FP32_VCYCLE else "f64",
         "data": "synthetic",
         "config": {"workload": wl["desc"], "form": wl["form"], "n": wl["n"], "levels": len(hh.A), "dofs": n,
+                   "nrhs": nrhs,
                    "nnz_A0": hh.A[0].nnz, "rtol": 1e-8, "precision": args.precision,
                    "l2": "inputs larger than L2: the resident hierarchy is ~%.1f GB" % (amge.amge_hier_info(h)[2] / 1e9),
                    "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU"},
@@ -335,21 +358,24 @@ def run_ours(args, dist):
     # per-kernel timing from the CUDA events bracketing every launch in the timed region
     kern = {k: {"launches": c, "ms": m, "avg_us": (1e3 * m / c if c else None)} for k, (c, m) in prof.items()}
     line["kernels"] = kern
-    line["gpu_launches"] = int(sum(c for c, _ in prof.values()))
+    line["kernel_timing"] = ("CUDA events around every launch, on the launching stream, over a second pass of the "
+                             "same K steps right after the headline timed region")
+    line["gpu_launches"] = int(sum(c for c, _ in launches.values()))
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs") if peaks else None
     peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s (of fallback)"
     hbm = hbm or HBM_FALLBACK_GBS
     c, m = prof["A_fine"]
     if c and m > 0:
-        bytes_launch = a_fine_bytes_per_launch(hh, w)
+        bytes_launch = a_fine_bytes_per_launch(hh, w, nrhs)
         achieved = bytes_launch / (m / c / 1e3) / 1e9
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                            "frac": achieved / hbm, "traffic": None,
+                            "frac": achieved / hbm,
+                            "traffic": NCU_TRAFFIC.get((args.workload, w)) if nrhs == 1 else None,
                             "kernel": "k_sell level-0 A sweeps (three residuals, final l1 sweep), "
                                       + ("FP32" if w == 4 else "FP64"),
                             "bytes_per_launch": bytes_launch, "peak_source": peak_src}
-    vc_ms = sum(prof[k][1] for k in ("A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse"))
+    vc_ms = sum(prof[k][1] for k in ("A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "vcycle_vec"))
     n_vc = sum(iters) + len(iters)  # one V-cycle per iteration plus the initial one (speculative ones add)
     if vc_ms > 0:
         line["vcycle_hbm_gbs"] = vcycle_bytes(hh, w) * (prof["A_fine"][0] / 4) / (vc_ms / 1e3) / 1e9
@@ -370,7 +396,7 @@ def run_ours(args, dist):
     e1.record(stream)
     torch.cuda.synchronize()
     line["fp64" if other == amge.AMGE_FP64 else "fp32"] = {
-        "solves_per_s": dist.world * k2 / (dist.max(e0.elapsed_time(e1), "cuda") / 1e3),
+        "solves_per_s": dist.world * k2 * nrhs / (dist.max(e0.elapsed_time(e1), "cuda") / 1e3),
         "iters": oi[0]["iters"], "true_relres": oi[0]["true_relres"], "status": oi[0]["status_name"],
         "maxit": 300}
 
@@ -378,16 +404,18 @@ def run_ours(args, dist):
     if not args.no_e2e:
         bh = torch.from_numpy(b).pin_memory()
         xh = torch.empty_like(bh).pin_memory()
-        amge.amge_pcg_solve_host(h, bh, xh, precision=prec)
+        amge.amge_pcg_solve_host(h, bh, xh, precision=prec, nrhs=nrhs)
         dist.barrier()
         t = time.perf_counter()
         for _ in range(args.steps):
-            amge.amge_pcg_solve_host(h, bh, xh, precision=prec)
+            amge.amge_pcg_solve_host(h, bh, xh, precision=prec, nrhs=nrhs)
         el = dist.max(time.perf_counter() - t, "cuda")
-        line["e2e"] = {"value": dist.world * args.steps / el, "unit": "solves/s",
-                       "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+        line["e2e"] = {"value": dist.world * args.steps * nrhs / el, "unit": "solves/s",
+                       "h2d_bytes_per_step": 8 * n * nrhs, "d2h_bytes_per_step": 8 * n * nrhs}
 
     if dist.rank == 0 and not args.no_cpu_baseline:
+        if nrhs > 1:
+            b = b[:, 0].copy()
         fp64_iters = iters[0] if prec == amge.AMGE_FP64 else line.get("fp64", {}).get("iters", iters[0])
         s = oracle_sample(hh, b, fp64_iters)
         line["cpu_baseline"] = {

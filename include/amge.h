@@ -124,15 +124,20 @@ amge_status amge_hier_info(const amge_hier* h, int32_t* n_dofs, int32_t* levels,
 /* One V-cycle (Algorithm 4.1 with x0 = 0, hybrid smoothing eq. 4.1, the
  * transposed smoother after the coarse correction): z = B^{-1} r.
  *   r_dev, z_dev  device, double [n][nrhs]; must not overlap
- *   nrhs          number of right-hand sides (must be 1)
+ *   nrhs          number of right-hand sides, 1 .. 32 (columns of a row-major block)
  *   precision     amge_precision of the internal arithmetic (the interface stays FP64)
- * Enqueued on `stream`; does not synchronise. */
+ * Enqueued on `stream`; does not synchronise (the first call with nrhs > 1 allocates
+ * the block workspace). */
 amge_status amge_vcycle(amge_hier* h, const double* r_dev, double* z_dev, int32_t nrhs, int32_t precision,
                         void* stream);
 
 /* PCG preconditioned by one V-cycle per iteration (Section 4), x0 = 0.
- *   b_dev, x_dev  device, double [n][nrhs]; x_dev is overwritten; nrhs must be 1
+ *   b_dev, x_dev  device, double [n][nrhs]; x_dev is overwritten; 1 <= nrhs <= 32
  *   info          host, array of nrhs results
+ * With nrhs > 1 the columns iterate together (one block V-cycle per iteration, one
+ * read of every operator for all columns); a column stops moving once its true
+ * residual meets the tolerance.  The first call with nrhs > 1 on a hierarchy
+ * allocates the block workspace (sized for 32 columns) on the device.
  * Returns AMGE_OK when every right-hand side converged, AMGE_ENOTCONV when one
  * reached maxit (its info entry holds the iterations and the final true residual),
  * AMGE_ENONFINITE when a right-hand side or a PCG scalar is not finite.
@@ -214,6 +219,67 @@ amge_status amge_profile_read(amge_hier* h, int64_t* count, double* ms);
  * streams, no ordering between them) race on it; the array needs no clearing
  * (each call overwrites it before reading it).  Enqueued on `stream`. */
 amge_status amge_coarse_solve_noalloc(const amge_hier* h, const double* b_dev, double* z_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Request server (continuous batching of solves on one GPU).
+ *
+ * A server owns one scheduler thread that does all of its GPU work on the device
+ * that was current at creation.  amge_submit copies the right-hand sides and returns
+ * a ticket at once; every right-hand side becomes a column solve that runs in a slot
+ * -- a workspace of its own (vectors, Krylov state, reduction scratch, captured PCG
+ * graph) over the submitted hierarchy's read-only operators, with its own stream.
+ * Queued columns are admitted as soon as an idle slot of the same hierarchy exists or
+ * a new slot fits the HBM budget (idle slots of other hierarchies are released
+ * first, least recently used), and every running column is advanced without
+ * blocking, so work of requests that arrive while others run overlaps on the device.
+ * Each column gives exactly the result amge_pcg_solve gives for that right-hand side
+ * on that hierarchy, whatever else is running.  Hierarchies must outlive the server.
+ * ------------------------------------------------------------------------- */
+typedef struct amge_server amge_server; /* opaque */
+
+/* hbm_budget_bytes: device bytes the slots may hold (0 = 80% of the free memory at
+ * creation); max_slots: concurrent column solves, 1 .. 4096. */
+amge_status amge_server_create(size_t hbm_budget_bytes, int32_t max_slots, amge_server** out);
+
+/* Queue a solve of nrhs (1 .. 32) right-hand sides b_host [n][nrhs] (copied before
+ * return) on hierarchy h; the solution is written to x_host [n][nrhs], which must stay
+ * valid until amge_poll / amge_wait has returned the final status.  Never blocks on
+ * the GPU.  *ticket identifies the request. */
+amge_status amge_submit(amge_server* s, amge_hier* h, const double* b_host, double* x_host, int32_t nrhs,
+                        const amge_solve_opts* opts, uint64_t* ticket);
+
+/* AMGE_EAGAIN while the request is pending.  Otherwise its final status (AMGE_OK,
+ * AMGE_ENOTCONV, AMGE_ENONFINITE, AMGE_ECANCELED, AMGE_ENOMEM when its workspace can
+ * never fit the budget, AMGE_ECUDA), with info[0 .. nrhs-1] filled (time_ms = time
+ * from submission to completion); the ticket is then released. */
+amge_status amge_poll(amge_server* s, uint64_t ticket, amge_info* info);
+
+/* As amge_poll, waiting up to timeout_ms (< 0: no limit); AMGE_ETIMEOUT if the
+ * request is still pending then (the ticket stays valid). */
+amge_status amge_wait(amge_server* s, uint64_t ticket, int32_t timeout_ms, amge_info* info);
+
+/* Cancel a pending request: columns not yet started are dropped, running ones finish;
+ * the final status is AMGE_ECANCELED.  AMGE_EINVAL for an unknown or finished ticket. */
+amge_status amge_cancel(amge_server* s, uint64_t ticket);
+
+/* Queue depth (requests with columns not yet started), running column solves,
+ * device bytes held by slots, number of slots. */
+amge_status amge_server_stats(amge_server* s, int64_t* queued, int64_t* running_columns, size_t* bytes_in_use,
+                              int32_t* slots);
+
+/* Stop the scheduler (running columns are waited for, pending requests dropped) and
+ * release every slot (NULL is ignored). */
+void amge_server_destroy(amge_server* s);
+
+/* Choose how single-right-hand-side PCG iterations are launched (default 1).
+ * 1: the iteration is captured once per precision into a CUDA graph whose WHILE
+ *    conditional node repeats it on the device until the recursive residual meets
+ *    the tolerance or maxit is reached (one host round trip per graph launch);
+ * 0: every kernel is launched from the host and the residual norm is read back
+ *    after each iteration.
+ * Both run the same kernels in the same order and give identical results.  While
+ * per-launch timing is enabled (amge_profile_enable), the host-launched loop is used. */
+amge_status amge_set_graphs(amge_hier* h, int32_t enable);
 
 /* Release the hierarchy and all device memory it holds (NULL is ignored). */
 void amge_hier_free(amge_hier* h);

@@ -60,6 +60,14 @@ _SIGS = {
     "amge_apply": [_vp, _i32, _i32, _vp, _vp, _i32, _vp],
     "amge_dot": [_vp, _vp, _vp, _i64, _vp, _vp],
     "amge_profile_enable": [_vp, _i32],
+    "amge_set_graphs": [_vp, _i32],
+    "amge_server_create": [ctypes.c_size_t, _i32, ctypes.POINTER(_vp)],
+    "amge_submit": [_vp, _vp, _vp, _vp, _i32, ctypes.POINTER(amge_solve_opts), ctypes.POINTER(ctypes.c_uint64)],
+    "amge_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(amge_info)],
+    "amge_wait": [_vp, ctypes.c_uint64, _i32, ctypes.POINTER(amge_info)],
+    "amge_cancel": [_vp, ctypes.c_uint64],
+    "amge_server_stats": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_size_t),
+                          ctypes.POINTER(_i32)],
     "amge_profile_read": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)],
     "amge_coarse_solve_noalloc": [_vp, _vp, _vp, _vp],
 }
@@ -69,6 +77,8 @@ for _name, _args in _SIGS.items():
     _f.restype = ctypes.c_int
 _lib.amge_hier_free.argtypes = [_vp]
 _lib.amge_hier_free.restype = None
+_lib.amge_server_destroy.argtypes = [_vp]
+_lib.amge_server_destroy.restype = None
 _lib.amge_last_error.argtypes = []
 _lib.amge_last_error.restype = ctypes.c_char_p
 
@@ -207,6 +217,11 @@ def amge_coarse_solve_noalloc(h: Hier, b, z, stream=None):
            "amge_coarse_solve_noalloc")
 
 
+def amge_set_graphs(h: Hier, enable: bool = True):
+    """Graph-driven (True) or host-launched (False) single-RHS PCG iterations."""
+    _check(_lib.amge_set_graphs(h.handle, int(enable)), "amge_set_graphs")
+
+
 def amge_profile_enable(h: Hier, enable: bool = True):
     _check(_lib.amge_profile_enable(h.handle, int(enable)), "amge_profile_enable")
 
@@ -217,6 +232,92 @@ def amge_profile_read(h: Hier):
     ms = (ctypes.c_double * len(PROF_CLASSES))()
     _check(_lib.amge_profile_read(h.handle, cnt, ms), "amge_profile_read")
     return {name: (int(cnt[i]), float(ms[i])) for i, name in enumerate(PROF_CLASSES)}
+
+
+class Server:
+    """Owning handle of a request server (amge_server_create / amge_server_destroy).
+
+    Keeps every submitted request's host buffers alive until its result is collected.
+    """
+
+    def __init__(self, handle):
+        self.handle = handle
+        self._live = {}
+
+    def destroy(self):
+        if self.handle:
+            _lib.amge_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def amge_server_create(hbm_budget_bytes: int = 0, max_slots: int = 16) -> Server:
+    h = ctypes.c_void_p()
+    _check(_lib.amge_server_create(hbm_budget_bytes, max_slots, ctypes.byref(h)), "amge_server_create")
+    return Server(h)
+
+
+def amge_submit(sv: Server, h: Hier, b_host, x_host, nrhs: int = 1, rtol=1e-8, maxit=1000, precision=AMGE_FP64):
+    """b_host / x_host: C-contiguous float64 numpy arrays of n*nrhs entries.  Returns a ticket."""
+    assert b_host.dtype == np.float64 and b_host.flags.c_contiguous and b_host.size == h.n * nrhs
+    assert x_host.dtype == np.float64 and x_host.flags.c_contiguous and x_host.size == h.n * nrhs
+    opts = amge_solve_opts(rtol, maxit, precision)
+    t = ctypes.c_uint64()
+    _check(_lib.amge_submit(sv.handle, h.handle, ctypes.c_void_p(b_host.ctypes.data),
+                            ctypes.c_void_p(x_host.ctypes.data), nrhs, ctypes.byref(opts), ctypes.byref(t)),
+           "amge_submit")
+    sv._live[t.value] = (b_host, x_host, nrhs, h)
+    return t.value
+
+
+def _collect(sv, ticket, st, infos, nrhs):
+    sv._live.pop(ticket, None)
+    return st, [dict(iters=i.iters, status=i.status, true_relres=i.true_relres, time_ms=i.time_ms)
+                for i in infos[:nrhs]]
+
+
+def amge_poll(sv: Server, ticket: int):
+    """(AMGE_EAGAIN, None) while pending, else (status, [info per column])."""
+    nrhs = sv._live[ticket][2] if ticket in sv._live else kMaxRhs
+    infos = (amge_info * max(nrhs, 1))()
+    st = _lib.amge_poll(sv.handle, ticket, infos)
+    if st == AMGE_EAGAIN:
+        return st, None
+    _check(st, "amge_poll", allow=(AMGE_OK, AMGE_ENOTCONV, AMGE_ENONFINITE, AMGE_ECANCELED, AMGE_ENOMEM, AMGE_ECUDA))
+    return _collect(sv, ticket, st, infos, nrhs)
+
+
+def amge_wait(sv: Server, ticket: int, timeout_ms: int = -1):
+    nrhs = sv._live[ticket][2] if ticket in sv._live else kMaxRhs
+    infos = (amge_info * max(nrhs, 1))()
+    st = _lib.amge_wait(sv.handle, ticket, timeout_ms, infos)
+    if st == AMGE_ETIMEOUT:
+        return st, None
+    _check(st, "amge_wait", allow=(AMGE_OK, AMGE_ENOTCONV, AMGE_ENONFINITE, AMGE_ECANCELED, AMGE_ENOMEM, AMGE_ECUDA))
+    return _collect(sv, ticket, st, infos, nrhs)
+
+
+def amge_cancel(sv: Server, ticket: int):
+    _check(_lib.amge_cancel(sv.handle, ticket), "amge_cancel")
+
+
+def amge_server_stats(sv: Server):
+    q, r, nb, ns = _i64(), _i64(), ctypes.c_size_t(), _i32()
+    _check(_lib.amge_server_stats(sv.handle, ctypes.byref(q), ctypes.byref(r), ctypes.byref(nb), ctypes.byref(ns)),
+           "amge_server_stats")
+    return dict(queued=q.value, running_columns=r.value, bytes_in_use=nb.value, slots=ns.value)
+
+
+def amge_server_destroy(sv: Server):
+    sv.destroy()
+
+
+kMaxRhs = 32
 
 
 def lib_handle():

@@ -20,7 +20,8 @@ HIER_SO = os.path.join(PKG, "inputs", "libamge_hierarchy.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CUDA_SOURCES = ["amge_api.cu", "amge_kernels.cu", "amge_host_setup.cpp", "amge_noalloc.cu"]
+CUDA_SOURCES = ["amge_api.cu", "amge_kernels.cu", "amge_kernels_mm.cu", "amge_server.cu", "amge_host_setup.cpp",
+                "amge_noalloc.cu"]
 
 
 def _run(cmds):

@@ -68,6 +68,31 @@ struct SpmvArgs {
 
 template <typename V>
 void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+
+// CSR copy of an operator for the multi-right-hand-side products (row pointers and
+// columns shared by both precisions).
+template <typename V>
+struct DevCsr {
+  int nr = 0, nc = 0;
+  int64_t nnz = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  V* val = nullptr;
+};
+
+// Multi-RHS product on [n][nrhs] blocks (nrhs <= 32): a group of K lanes (K = the
+// power of two >= nrhs) per row, lane c handling column c; the epilogues are those of
+// the single-vector kernels applied column by column (d is per row).
+constexpr int kMaxRhs = 32;
+template <typename V>
+void launch_csr_mm(const DevCsr<V>& M, int nrhs, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+// Y[i][c] = d[i] X[i][c]
+template <typename V>
+void launch_mul_mm(int64_t n, int nrhs, const V* d, const V* x, V* y, cudaStream_t s);
+// Coarsest solve for [n][nrhs] blocks: Z = Linv^T (Linv B), FP64 accumulation.
+template <typename Tin, typename Tout>
+void launch_coarse_mm(int n, int nrhs, const double* Linv, const double* LinvT, const Tin* b, double* t, Tout* z,
+                      cudaStream_t s);
 // y = d .* x (elementwise)
 template <typename V>
 void launch_mul(int64_t n, const V* d, const V* x, V* y, cudaStream_t s);
@@ -92,6 +117,7 @@ enum Scalar : int {
   SC_ZQ = 6,
   SC_BB = 7,       // ||b||^2
   SC_DOT = 8,      // generic dot result
+  SC_TOL2 = 9,     // rtol^2 ||b||^2 (graph-driven loop)
   SC_COUNT = 16
 };
 constexpr int kRedSlots = 4;
@@ -116,6 +142,50 @@ void launch_pcg_dots(int64_t n, const double* rv, const double* z, const double*
                      const RedScratch& r, cudaStream_t s);
 // p = z + beta p; rho = rho_new
 void launch_pcg_update_p(int64_t n, double* p, const double* z, const RedScratch& r, cudaStream_t s);
+// Loop test of the graph-driven PCG: state[0] += 1 (iterations done), then the WHILE
+// condition is set to (||r||^2 finite && > SC_TOL2 && state[0] < state[1] (maxit));
+// state[2] = 1 flags a non-finite ||r||^2.
+void launch_pcg_loop_cond(cudaGraphConditionalHandle hw, const RedScratch& r, int* state, cudaStream_t s);
+
+// Multi-RHS PCG: per-column scalars live in sc_mm[scalar][column]; `active[c]` masks
+// columns that have converged (their alpha and beta are forced to 0).
+struct RedScratchMM {
+  double* partials = nullptr;  // [kRedSlots][kMaxRedBlocks][kMaxRhs]
+  unsigned* counters = nullptr;  // [kRedSlots]
+  double* sc = nullptr;        // [SC_COUNT][kMaxRhs]
+  int* active = nullptr;       // [kMaxRhs]
+};
+// Per-column dot products of [n][nrhs] blocks: out[c] = sum_i x[i][c] y[i][c].
+void launch_dot_mm(int64_t n, int nrhs, const double* x, const double* y, int sc_index, const RedScratchMM& r,
+                   cudaStream_t s);
+// Q = A P (FP64) and pq_c; alpha_c = active_c ? rho_c / pq_c : 0.
+void launch_pcg_mm_spmv_dot(const DevCsr<double>& A, int nrhs, const double* p, double* q, const RedScratchMM& r,
+                            cudaStream_t s);
+void launch_pcg_mm_axpy_norm(int64_t n, int nrhs, double* x, double* rv, const double* p, const double* q,
+                             const RedScratchMM& r, cudaStream_t s);
+void launch_pcg_mm_dots(int64_t n, int nrhs, const double* rv, const double* z, const double* q, int flexible,
+                        const RedScratchMM& r, cudaStream_t s);
+void launch_pcg_mm_update_p(int64_t n, int nrhs, double* p, const double* z, const RedScratchMM& r,
+                            cudaStream_t s);
+
+// Resumable single-RHS PCG on a hierarchy's (or a view's) workspace, used by the
+// blocking solve and by the request server.  advance() returns 1 when finished,
+// 0 while the GPU is still working on the current phase, -1 on error.
+}  // namespace amge
+struct PcgRun;
+namespace amge {
+amge_status pcg_run_start(amge_hier* h, const double* b, double* x, const amge_solve_opts& o, cudaStream_t s,
+                          PcgRun** out);
+int pcg_run_advance(PcgRun* r, amge_status* err);
+void pcg_run_wait_event(PcgRun* r);
+amge_status pcg_run_finish(PcgRun* r, amge_info* info);  // frees r
+void pcg_run_free(PcgRun* r);                            // abandons r
+// A view shares the level operators of `src` and owns a separate workspace (so
+// solves on different views run concurrently without interfering).
+amge_status hier_make_view(const amge_hier* src, cudaStream_t s, amge_hier** out);
+size_t hier_workspace_bytes(const amge_hier* h);
+int hier_dofs(const amge_hier* h);
+const amge_hier* hier_base(const amge_hier* h);
 
 // Host setup helpers (amge_host_setup.cpp).
 bool check_csr(const amge_csr& c, int nr, int nc, const char* what, std::string& err);

@@ -244,6 +244,15 @@ __global__ void __launch_bounds__(kBlock) k_pcg_update_p(int64_t n, double* __re
   if (blockIdx.x == 0 && threadIdx.x == 0) r.sc[SC_RHO] = r.sc[SC_RHO_NEW];
 }
 
+__global__ void k_pcg_loop_cond(cudaGraphConditionalHandle hw, const double* __restrict__ sc, int* state) {
+  const double rr = sc[SC_RR];
+  const int it = state[0] + 1;
+  state[0] = it;
+  const bool fin = isfinite(rr);
+  if (!fin) state[2] = 1;
+  cudaGraphSetConditional(hw, (fin && rr > sc[SC_TOL2] && it < state[1]) ? 1u : 0u);
+}
+
 int vec_grid(int64_t n) {
   int64_t g = (n + kBlock - 1) / kBlock;
   return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 152 * 16);
@@ -323,6 +332,10 @@ void launch_pcg_dots(int64_t n, const double* rv, const double* z, const double*
 
 void launch_pcg_update_p(int64_t n, double* p, const double* z, const RedScratch& r, cudaStream_t s) {
   k_pcg_update_p<<<vec_grid(n), kBlock, 0, s>>>(n, p, z, r);
+}
+
+void launch_pcg_loop_cond(cudaGraphConditionalHandle hw, const RedScratch& r, int* state, cudaStream_t s) {
+  k_pcg_loop_cond<<<1, 1, 0, s>>>(hw, r.sc, state);
 }
 
 }  // namespace amge

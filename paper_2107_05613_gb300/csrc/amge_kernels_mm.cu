@@ -1,0 +1,339 @@
+// Multi-right-hand-side kernels (blocks of nrhs <= 32 vectors, row-major [n][nrhs]).
+//
+// The V-cycle and PCG of the single-vector path run on all columns at once: every
+// level operator is read once per product for all right-hand sides.  A row is
+// handled by a group of K lanes (K = the power of two >= nrhs); the group reads the
+// row's column indices and values as broadcast loads and lane c gathers X[col][c],
+// so each stored nonzero costs one coalesced load of the gathered row of X and one
+// FMA per column, with no cross-lane reduction.  Per-column dot products reduce in
+// a fixed order (per block, then over blocks in index order by the last block).
+#include <algorithm>
+#include <type_traits>
+
+#include "amge_internal.h"
+
+namespace amge {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <typename V>
+__device__ __forceinline__ V ldg(const V* p) {
+  return __ldg(p);
+}
+
+template <typename V, int K, int EPI>
+__global__ void __launch_bounds__(kBlock) k_csr_mm(int nr, int nrhs, const int* __restrict__ rp,
+                                                   const int* __restrict__ ci, const V* __restrict__ val,
+                                                   SpmvArgs<V> a) {
+  const int gt = blockIdx.x * kBlock + threadIdx.x;
+  const int row = gt / K;
+  const int c = gt & (K - 1);
+  if (row >= nr || c >= nrhs) return;
+  const int beg = ldg(rp + row), end = ldg(rp + row + 1);
+  V s0 = V(0), s1 = V(0);
+  int j = beg;
+  for (; j + 1 < end; j += 2) {
+    const int c0 = ldg(ci + j), c1 = ldg(ci + j + 1);
+    const V v0 = ldg(val + j), v1 = ldg(val + j + 1);
+    s0 = fma(v0, ldg(a.x + (size_t)c0 * nrhs + c), s0);
+    s1 = fma(v1, ldg(a.x + (size_t)c1 * nrhs + c), s1);
+  }
+  if (j < end) s0 = fma(ldg(val + j), ldg(a.x + (size_t)ldg(ci + j) * nrhs + c), s0);
+  const V s = s0 + s1;
+  const size_t e = (size_t)row * nrhs + c;
+  switch (EPI) {
+    case EPI_STORE: a.y[e] = s; break;
+    case EPI_RESID: a.y[e] = a.b[e] - s; break;
+    case EPI_SCALE: a.y[e] = a.d[row] * s; break;
+    case EPI_ADD: a.y[e] += s; break;
+    case EPI_SWEEP: a.y[e] = fma(a.d[row], a.b[e] - s, a.xin[e]); break;
+  }
+}
+
+template <typename V>
+__global__ void k_mul_mm(int64_t n, int nrhs, const V* __restrict__ d, const V* __restrict__ x, V* __restrict__ y) {
+  const int64_t tot = n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = d[e / nrhs] * x[e];
+}
+
+// Y = (triangle of M) X for [n][nrhs] blocks: warp per row, lane c per column.
+template <bool LOWER, typename Tin, typename Tout>
+__global__ void __launch_bounds__(kBlock) k_trimm(int n, int nrhs, const double* __restrict__ M,
+                                                  const Tin* __restrict__ x, Tout* __restrict__ y) {
+  const int row = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int c = threadIdx.x & 31;
+  if (row >= n || c >= nrhs) return;
+  const double* m = M + (size_t)row * n;
+  const int beg = LOWER ? 0 : row;
+  const int end = LOWER ? row + 1 : n;
+  double s0 = 0.0, s1 = 0.0;
+  int j = beg;
+  for (; j + 1 < end; j += 2) {
+    s0 = fma(ldg(m + j), (double)ldg(x + (size_t)j * nrhs + c), s0);
+    s1 = fma(ldg(m + j + 1), (double)ldg(x + (size_t)(j + 1) * nrhs + c), s1);
+  }
+  if (j < end) s0 = fma(ldg(m + j), (double)ldg(x + (size_t)j * nrhs + c), s0);
+  y[(size_t)row * nrhs + c] = (Tout)(s0 + s1);
+}
+
+// ---------------------------------------------------------------- per-column reductions
+constexpr size_t kColStride = (size_t)kMaxRedBlocks * kMaxRhs;
+
+// Each thread holds partials for column threadIdx.x % K.  Block sums per column (in
+// row-group order), then the last block to arrive sums the blocks in index order.
+// Returns true in that block, with the column totals in tot[k][c] (shared).
+template <int NV>
+__device__ bool finish_cols(const double* v, int K, int nrhs, const RedScratchMM& r, int slot0,
+                            double (*tot)[kMaxRhs]) {
+  __shared__ double sh[kBlock];
+  __shared__ bool last;
+  const int tid = threadIdx.x;
+  const int G = kBlock / K;
+  for (int k = 0; k < NV; k++) {
+    sh[tid] = v[k];
+    __syncthreads();
+    if (tid < nrhs) {
+      double a = 0.0;
+      for (int g = 0; g < G; g++) a += sh[g * K + tid];
+      r.partials[(slot0 + k) * kColStride + (size_t)blockIdx.x * kMaxRhs + tid] = a;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&r.counters[slot0], 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  const int c = tid % K, sub = tid / K;
+  for (int k = 0; k < NV; k++) {
+    double a = 0.0;
+    if (c < nrhs)
+      for (int b = sub; b < (int)gridDim.x; b += G)
+        a += __ldcg(r.partials + (slot0 + k) * kColStride + (size_t)b * kMaxRhs + c);
+    sh[tid] = a;
+    __syncthreads();
+    if (tid < nrhs) {
+      double t2 = 0.0;
+      for (int g = 0; g < G; g++) t2 += sh[g * K + tid];
+      tot[k][tid] = t2;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) r.counters[slot0] = 0u;
+  return true;
+}
+
+__device__ __forceinline__ double* scol(const RedScratchMM& r, int idx) { return r.sc + (size_t)idx * kMaxRhs; }
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_dot_mm(int64_t n, int nrhs, const double* __restrict__ x,
+                                                   const double* __restrict__ y, int sc_index, RedScratchMM r) {
+  const int c = threadIdx.x & (K - 1);
+  const int64_t groups = (int64_t)gridDim.x * (kBlock / K);
+  double acc = 0.0;
+  if (c < nrhs)
+    for (int64_t row = (blockIdx.x * (int64_t)kBlock + threadIdx.x) / K; row < n; row += groups)
+      acc = fma(x[row * nrhs + c], y[row * nrhs + c], acc);
+  __shared__ double tot[1][kMaxRhs];
+  if (finish_cols<1>(&acc, K, nrhs, r, 0, tot) && threadIdx.x < nrhs) scol(r, sc_index)[threadIdx.x] = tot[0][threadIdx.x];
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_mm_spmv_dot(int nr, int nrhs, const int* __restrict__ rp,
+                                                            const int* __restrict__ ci,
+                                                            const double* __restrict__ val,
+                                                            const double* __restrict__ p, double* __restrict__ q,
+                                                            RedScratchMM r) {
+  const int c = threadIdx.x & (K - 1);
+  const int groups = gridDim.x * (kBlock / K);
+  double contrib = 0.0;
+  if (c < nrhs)
+    for (int row = (blockIdx.x * kBlock + threadIdx.x) / K; row < nr; row += groups) {
+      const int beg = ldg(rp + row), end = ldg(rp + row + 1);
+      double s0 = 0.0, s1 = 0.0;
+      int j = beg;
+      for (; j + 1 < end; j += 2) {
+        s0 = fma(ldg(val + j), ldg(p + (size_t)ldg(ci + j) * nrhs + c), s0);
+        s1 = fma(ldg(val + j + 1), ldg(p + (size_t)ldg(ci + j + 1) * nrhs + c), s1);
+      }
+      if (j < end) s0 = fma(ldg(val + j), ldg(p + (size_t)ldg(ci + j) * nrhs + c), s0);
+      const double s = s0 + s1;
+      q[(size_t)row * nrhs + c] = s;
+      contrib = fma(ldg(p + (size_t)row * nrhs + c), s, contrib);
+    }
+  __shared__ double tot[1][kMaxRhs];
+  if (finish_cols<1>(&contrib, K, nrhs, r, 0, tot) && threadIdx.x < nrhs) {
+    const int cc = threadIdx.x;
+    scol(r, SC_PQ)[cc] = tot[0][cc];
+    scol(r, SC_ALPHA)[cc] = r.active[cc] ? scol(r, SC_RHO)[cc] / tot[0][cc] : 0.0;
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_mm_axpy_norm(int64_t n, int nrhs, double* __restrict__ x,
+                                                             double* __restrict__ rv, const double* __restrict__ p,
+                                                             const double* __restrict__ q, RedScratchMM r) {
+  const int c = threadIdx.x & (K - 1);
+  const int64_t groups = (int64_t)gridDim.x * (kBlock / K);
+  double acc = 0.0;
+  if (c < nrhs) {
+    const double alpha = scol(r, SC_ALPHA)[c];
+    for (int64_t row = (blockIdx.x * (int64_t)kBlock + threadIdx.x) / K; row < n; row += groups) {
+      const int64_t e = row * nrhs + c;
+      x[e] = fma(alpha, p[e], x[e]);
+      const double ri = fma(-alpha, q[e], rv[e]);
+      rv[e] = ri;
+      acc = fma(ri, ri, acc);
+    }
+  }
+  __shared__ double tot[1][kMaxRhs];
+  if (finish_cols<1>(&acc, K, nrhs, r, 1, tot) && threadIdx.x < nrhs) scol(r, SC_RR)[threadIdx.x] = tot[0][threadIdx.x];
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_mm_dots(int64_t n, int nrhs, const double* __restrict__ rv,
+                                                        const double* __restrict__ z, const double* __restrict__ q,
+                                                        int flexible, RedScratchMM r) {
+  const int c = threadIdx.x & (K - 1);
+  const int64_t groups = (int64_t)gridDim.x * (kBlock / K);
+  double acc[2] = {0.0, 0.0};
+  if (c < nrhs)
+    for (int64_t row = (blockIdx.x * (int64_t)kBlock + threadIdx.x) / K; row < n; row += groups) {
+      const int64_t e = row * nrhs + c;
+      const double zi = z[e];
+      acc[0] = fma(rv[e], zi, acc[0]);
+      acc[1] = fma(zi, q[e], acc[1]);
+    }
+  __shared__ double tot[2][kMaxRhs];
+  if (finish_cols<2>(acc, K, nrhs, r, 2, tot) && threadIdx.x < nrhs) {
+    const int cc = threadIdx.x;
+    const double rho = scol(r, SC_RHO)[cc];
+    scol(r, SC_RHO_NEW)[cc] = tot[0][cc];
+    scol(r, SC_ZQ)[cc] = tot[1][cc];
+    double beta = flexible ? -scol(r, SC_ALPHA)[cc] * tot[1][cc] / rho : tot[0][cc] / rho;
+    scol(r, SC_BETA)[cc] = r.active[cc] ? beta : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_pcg_mm_update_p(int64_t n, int nrhs, double* __restrict__ p,
+                                                            const double* __restrict__ z, RedScratchMM r) {
+  const int64_t tot = n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)kBlock + threadIdx.x; e < tot; e += (int64_t)gridDim.x * kBlock)
+    p[e] = fma(scol(r, SC_BETA)[e % nrhs], p[e], z[e]);
+  if (blockIdx.x == 0 && threadIdx.x < nrhs) scol(r, SC_RHO)[threadIdx.x] = scol(r, SC_RHO_NEW)[threadIdx.x];
+}
+
+int pow2_at_least(int v) {
+  int k = 1;
+  while (k < v) k <<= 1;
+  return k;
+}
+
+int mm_red_blocks(int64_t n, int K) {
+  const int64_t rows_per_block = kBlock / K;
+  int64_t g = (n + 4 * rows_per_block - 1) / (4 * rows_per_block);
+  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), kMaxRedBlocks);
+}
+
+int grid_for(int64_t tot) {
+  int64_t g = (tot + kBlock - 1) / kBlock;
+  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 152 * 16);
+}
+
+// Calls f(std::integral_constant<int, K>) for K in {1, 2, 4, 8, 16, 32}.
+template <typename F>
+void dispatch_k(int K, F&& f) {
+  switch (K) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    case 16: f(std::integral_constant<int, 16>{}); break;
+    default: f(std::integral_constant<int, 32>{}); break;
+  }
+}
+
+}  // namespace
+
+template <typename V>
+void launch_csr_mm(const DevCsr<V>& M, int nrhs, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  if (M.nr == 0) return;
+  const int K = pow2_at_least(nrhs);
+  const int grid = (int)(((int64_t)M.nr * K + kBlock - 1) / kBlock);
+  dispatch_k(K, [&](auto kk) {
+    constexpr int KK = decltype(kk)::value;
+    switch (epi) {
+      case EPI_STORE: k_csr_mm<V, KK, EPI_STORE><<<grid, kBlock, 0, s>>>(M.nr, nrhs, M.rp, M.ci, M.val, a); break;
+      case EPI_RESID: k_csr_mm<V, KK, EPI_RESID><<<grid, kBlock, 0, s>>>(M.nr, nrhs, M.rp, M.ci, M.val, a); break;
+      case EPI_SCALE: k_csr_mm<V, KK, EPI_SCALE><<<grid, kBlock, 0, s>>>(M.nr, nrhs, M.rp, M.ci, M.val, a); break;
+      case EPI_ADD: k_csr_mm<V, KK, EPI_ADD><<<grid, kBlock, 0, s>>>(M.nr, nrhs, M.rp, M.ci, M.val, a); break;
+      case EPI_SWEEP: k_csr_mm<V, KK, EPI_SWEEP><<<grid, kBlock, 0, s>>>(M.nr, nrhs, M.rp, M.ci, M.val, a); break;
+    }
+  });
+}
+template void launch_csr_mm<double>(const DevCsr<double>&, int, int, const SpmvArgs<double>&, cudaStream_t);
+template void launch_csr_mm<float>(const DevCsr<float>&, int, int, const SpmvArgs<float>&, cudaStream_t);
+
+template <typename V>
+void launch_mul_mm(int64_t n, int nrhs, const V* d, const V* x, V* y, cudaStream_t s) {
+  if (n > 0) k_mul_mm<V><<<grid_for(n * nrhs), kBlock, 0, s>>>(n, nrhs, d, x, y);
+}
+template void launch_mul_mm<double>(int64_t, int, const double*, const double*, double*, cudaStream_t);
+template void launch_mul_mm<float>(int64_t, int, const float*, const float*, float*, cudaStream_t);
+
+template <typename Tin, typename Tout>
+void launch_coarse_mm(int n, int nrhs, const double* Linv, const double* LinvT, const Tin* b, double* t, Tout* z,
+                      cudaStream_t s) {
+  const int grid = (n * 32 + kBlock - 1) / kBlock;
+  k_trimm<true, Tin, double><<<grid, kBlock, 0, s>>>(n, nrhs, Linv, b, t);
+  k_trimm<false, double, Tout><<<grid, kBlock, 0, s>>>(n, nrhs, LinvT, t, z);
+}
+template void launch_coarse_mm<double, double>(int, int, const double*, const double*, const double*, double*,
+                                               double*, cudaStream_t);
+template void launch_coarse_mm<float, float>(int, int, const double*, const double*, const float*, double*, float*,
+                                             cudaStream_t);
+
+void launch_dot_mm(int64_t n, int nrhs, const double* x, const double* y, int sc_index, const RedScratchMM& r,
+                   cudaStream_t s) {
+  dispatch_k(pow2_at_least(nrhs), [&](auto kk) {
+    constexpr int KK = decltype(kk)::value;
+    k_dot_mm<KK><<<mm_red_blocks(n, KK), kBlock, 0, s>>>(n, nrhs, x, y, sc_index, r);
+  });
+}
+
+void launch_pcg_mm_spmv_dot(const DevCsr<double>& A, int nrhs, const double* p, double* q, const RedScratchMM& r,
+                            cudaStream_t s) {
+  dispatch_k(pow2_at_least(nrhs), [&](auto kk) {
+    constexpr int KK = decltype(kk)::value;
+    k_pcg_mm_spmv_dot<KK><<<mm_red_blocks(A.nr, KK), kBlock, 0, s>>>(A.nr, nrhs, A.rp, A.ci, A.val, p, q, r);
+  });
+}
+
+void launch_pcg_mm_axpy_norm(int64_t n, int nrhs, double* x, double* rv, const double* p, const double* q,
+                             const RedScratchMM& r, cudaStream_t s) {
+  dispatch_k(pow2_at_least(nrhs), [&](auto kk) {
+    constexpr int KK = decltype(kk)::value;
+    k_pcg_mm_axpy_norm<KK><<<mm_red_blocks(n, KK), kBlock, 0, s>>>(n, nrhs, x, rv, p, q, r);
+  });
+}
+
+void launch_pcg_mm_dots(int64_t n, int nrhs, const double* rv, const double* z, const double* q, int flexible,
+                        const RedScratchMM& r, cudaStream_t s) {
+  dispatch_k(pow2_at_least(nrhs), [&](auto kk) {
+    constexpr int KK = decltype(kk)::value;
+    k_pcg_mm_dots<KK><<<mm_red_blocks(n, KK), kBlock, 0, s>>>(n, nrhs, rv, z, q, flexible, r);
+  });
+}
+
+void launch_pcg_mm_update_p(int64_t n, int nrhs, double* p, const double* z, const RedScratchMM& r,
+                            cudaStream_t s) {
+  k_pcg_mm_update_p<<<grid_for(n * nrhs), kBlock, 0, s>>>(n, nrhs, p, z, r);
+}
+
+}  // namespace amge

@@ -261,3 +261,109 @@ def test_solve_is_deterministic(amge):
     amge.amge_pcg_solve(h, b, x1)
     amge.amge_pcg_solve(h, b, x2)
     assert torch.equal(x1, x2)
+
+
+# ---------------------------------------------------------------- multi-RHS blocks
+@pytest.mark.parametrize("form,n,L", [("hcurl", 16, 2), ("hdiv", 24, 3)])
+@pytest.mark.parametrize("nrhs", [2, 3, 8, 32])
+def test_vcycle_block_matches_oracle_per_column(amge, form, n, L, nrhs):
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, form, n, L)
+    o = oracle_hierarchy(form, n, L, True)
+    R = rhs_vector(41, o.A[0].shape[0], nrhs)            # [n][nrhs]
+    Z = torch.empty_like(dev(R))
+    amge.amge_vcycle(h, dev(R), Z, nrhs, amge.AMGE_FP64)
+    Zg = host(Z)
+    ref = o.apply(R)
+    tol = _coarse_tol(o)
+    for c in range(nrhs):
+        assert np.linalg.norm(Zg[:, c] - ref[:, c]) <= tol * np.linalg.norm(ref[:, c]), c
+
+
+@pytest.mark.parametrize("form,n,L,nrhs", [("hcurl", 16, 2, 4), ("hdiv", 24, 3, 5), ("hcurl", 8, 4, 32)])
+def test_pcg_block_fp64_matches_oracle_per_column(amge, form, n, L, nrhs):
+    from oracle import pcg
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, form, n, L)
+    o = oracle_hierarchy(form, n, L, True)
+    B = rhs_vector(43, o.A[0].shape[0], nrhs)
+    X = torch.empty_like(dev(B))
+    st, infos = amge.amge_pcg_solve(h, dev(B), X, rtol=1e-8, precision=amge.AMGE_FP64, nrhs=nrhs)
+    assert st == amge.AMGE_OK
+    Xg = host(X)
+    for c in range(nrhs):
+        xo, it_o, _, ok = pcg(o, B[:, c], rtol=1e-8)
+        assert ok and abs(infos[c]["iters"] - it_o) <= 1, (c, infos[c], it_o)
+        assert infos[c]["true_relres"] <= 1e-8
+        assert np.linalg.norm(B[:, c] - o.A[0] @ Xg[:, c]) <= 1e-8 * np.linalg.norm(B[:, c])
+        assert np.linalg.norm(Xg[:, c] - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+def test_pcg_block_fp32_vcycle_and_zero_column(amge):
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, "hcurl", 24, 3)
+    o = oracle_hierarchy("hcurl", 24, 3, True)
+    B = rhs_vector(47, o.A[0].shape[0], 8)
+    B[:, 3] = 0.0                                        # a zero right-hand side stays zero
+    X = torch.empty_like(dev(B))
+    st, infos = amge.amge_pcg_solve(h, dev(B), X, rtol=1e-8, precision=amge.AMGE_FP32_VCYCLE, nrhs=8)
+    assert st == amge.AMGE_OK
+    Xg = host(X)
+    assert infos[3]["iters"] == 0 and not Xg[:, 3].any()
+    for c in (0, 1, 2, 4, 5, 6, 7):
+        assert np.linalg.norm(B[:, c] - o.A[0] @ Xg[:, c]) <= 1e-8 * np.linalg.norm(B[:, c])
+
+
+def test_pcg_block_host_buffers(amge):
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, "hcurl", 16, 2)
+    o = oracle_hierarchy("hcurl", 16, 2, True)
+    B = rhs_vector(53, o.A[0].shape[0], 6)
+    X = np.zeros_like(B)
+    st, infos = amge.amge_pcg_solve_host(h, B, X, rtol=1e-8, nrhs=6)
+    assert st == amge.AMGE_OK
+    for c in range(6):
+        assert np.linalg.norm(B[:, c] - o.A[0] @ X[:, c]) <= 1e-8 * np.linalg.norm(B[:, c])
+
+
+# ---------------------------------------------------------------- graph-driven loop
+@pytest.mark.parametrize("form,n,L", [("hcurl", 16, 2), ("hdiv", 24, 3), ("hcurl", 8, 4)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_loop_equals_host_loop(amge, form, n, L, prec):
+    """The WHILE-node graph and the host-launched loop run the same kernels in the
+    same order: identical iterates, iteration counts and residuals."""
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, form, n, L)
+    b = dev(rhs_vector(59, h.n))
+    xg, xh = torch.empty_like(b), torch.empty_like(b)
+    amge.amge_set_graphs(h, True)
+    st_g, ig = amge.amge_pcg_solve(h, b, xg, precision=prec)
+    amge.amge_set_graphs(h, False)
+    st_h, ih = amge.amge_pcg_solve(h, b, xh, precision=prec)
+    amge.amge_set_graphs(h, True)
+    assert st_g == st_h == amge.AMGE_OK
+    assert ig[0]["iters"] == ih[0]["iters"]
+    assert ig[0]["true_relres"] == ih[0]["true_relres"]
+    assert torch.equal(xg, xh)
+
+
+def test_graph_loop_maxit_and_nonfinite(amge):
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, "hcurl", 16, 2)
+    b = dev(rhs_vector(61, h.n))
+    x = torch.empty_like(b)
+    for maxit in (1, 2, 5):
+        st, info = amge.amge_pcg_solve(h, b, x, rtol=1e-14, maxit=maxit)
+        assert st == amge.AMGE_ENOTCONV and info[0]["iters"] == maxit
+    bad = b.clone()
+    bad[11] = float("inf")
+    st, info = amge.amge_pcg_solve(h, bad, x)
+    assert st == amge.AMGE_ENONFINITE
+    st, info = amge.amge_pcg_solve(h, b, x)        # the hierarchy stays usable
+    assert st == amge.AMGE_OK and info[0]["true_relres"] <= 1e-8
