@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quick", action="store_true", help="headline loop only (for profiler runs)")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--precision-serve", choices=["fp32", "fp64"], default="fp32")
     p.add_argument("--no-kernel-timing", action="store_true",
                    help="do not bracket launches with CUDA events in the timed region")
     return p.parse_args()
@@ -358,6 +360,8 @@ def run_ours(args, dist):
     # per-kernel timing from the CUDA events bracketing every launch in the timed region
     kern = {k: {"launches": c, "ms": m, "avg_us": (1e3 * m / c if c else None)} for k, (c, m) in prof.items()}
     line["kernels"] = kern
+    tuned = amge.amge_autotune_report(h)
+    line["autotune"] = {f"L{l}.{p}.{o}": v for (l, p, o), v in tuned.items() if v}
     line["kernel_timing"] = ("CUDA events around every launch, on the launching stream, over a second pass of the "
                              "same K steps right after the headline timed region")
     line["gpu_launches"] = int(sum(c for c, _ in launches.values()))
@@ -423,9 +427,83 @@ def run_ours(args, dist):
             "sample": f"scipy FP64 oracle, first {s['iters_sampled']} PCG iterations of this workload "
                       f"({s['per_iter_s']:.2f} s/iteration) extrapolated to the {fp64_iters}-iteration FP64 "
                       f"solve; host has {os.cpu_count()} cores, the oracle uses 1"}
+    if not args.no_serving and dist.world == 1:
+        line["serving"] = run_serving(args, amge)
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
     dist.done()
+
+
+# ------------------------------------------------------------------ serving
+def run_serving(args, amge, n_requests=1000, load=0.7, seed=2107056135, max_slots=32):
+    """Continuous-batching request stream: problems drawn from a resident pool of
+    16 hierarchies (H(curl) or H(div), n in {16, 24, 32, 48}, two beta draws each,
+    beta log-uniform in [1e-2, 1e2] constant per problem, alpha = 1), 1-8 RHS per
+    request, Poisson arrivals at `load` x the measured closed-loop capacity."""
+    import numpy as np
+
+    from paper_2107_05613_gb300.inputs import build_hierarchy, rhs_vector
+
+    rng = np.random.default_rng(seed)
+    pool, banks = [], []
+    t_setup = time.perf_counter()
+    for form in ("hcurl", "hdiv"):
+        for n in (16, 24, 32, 48):
+            for _ in range(2):
+                beta = 10.0 ** rng.uniform(-2.0, 2.0)
+                nt = 6 * n ** 3
+                hh = build_hierarchy(form, n, beta=np.full(nt, beta), alpha=np.ones(nt))
+                h = amge.amge_setup_upload(hh)
+                pool.append((form, n, beta, h))
+                sd = int(rng.integers(1 << 30))
+                banks.append([rhs_vector(sd, h.n, k).reshape(h.n, k) for k in range(1, 9)])
+    t_setup = time.perf_counter() - t_setup
+    prec = amge.AMGE_FP32_VCYCLE if args.precision_serve == "fp32" else amge.AMGE_FP64
+    reqs = [(int(rng.integers(len(pool))), int(rng.integers(1, 9))) for _ in range(n_requests)]
+    sv = amge.amge_server_create(0, max_slots)
+
+    def submit(j, k):
+        h = pool[j][3]
+        x = np.empty((h.n, k))
+        return amge.amge_submit(sv, h, banks[j][k - 1], x, nrhs=k, precision=prec), x
+
+    # closed-loop capacity (also warms up every slot's captured graph)
+    t0 = time.perf_counter()
+    warm = [submit(j, k) for j, k in reqs[:128]]
+    for t, _ in warm:
+        amge.amge_wait(sv, t)
+    cap = len(warm) / (time.perf_counter() - t0)
+    # open loop: Poisson arrivals at load x capacity
+    lam = load * cap
+    gaps = rng.exponential(1.0 / lam, n_requests)
+    t_start = time.perf_counter()
+    t_next = t_start
+    live, lat, nrhs_tot, bad = [], [], 0, 0
+    for (j, k), g in zip(reqs, gaps):
+        t_next += g
+        while time.perf_counter() < t_next:
+            pass
+        live.append(submit(j, k))
+        nrhs_tot += k
+    for t, _ in live:
+        st, infos = amge.amge_wait(sv, t)
+        lat.append(infos[0]["time_ms"])
+        bad += st != amge.AMGE_OK
+    t_end = time.perf_counter()
+    stats = amge.amge_server_stats(sv)
+    sv.destroy()
+    return {
+        "requests": n_requests, "rhs_total": nrhs_tot, "precision": args.precision_serve,
+        "arrival_rate_req_per_s": lam, "closed_loop_capacity_req_per_s": cap, "load": load,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(np.mean(lat))},
+        "solves_per_s": nrhs_tot / (t_end - t_start), "requests_per_s": n_requests / (t_end - t_start),
+        "failed": int(bad), "max_slots": max_slots, "slots_at_end": stats["slots"],
+        "slot_bytes_at_end": stats["bytes_in_use"], "pool_setup_s": t_setup,
+        "workload": "1000 requests, Poisson arrivals; each an H(curl) or H(div) problem on an n^3 Kuhn mesh, "
+                    "n in {16,24,32,48}, beta constant per problem log-uniform [1e-2,1e2] (16-problem resident "
+                    "pool), alpha=1, 1-8 RHS U[-1,1], rtol 1e-8",
+    }
 
 
 def main():

@@ -281,6 +281,13 @@ void amge_server_destroy(amge_server* s);
  * per-launch timing is enabled (amge_profile_enable), the host-launched loop is used. */
 amge_status amge_set_graphs(amge_hier* h, int32_t enable);
 
+/* The autotuner's kernel choice for every smoothing level's single-vector products:
+ * lanes[(l * 2 + p) * 5 + op] for level l < levels-1, precision p (0 FP64, 1 FP32),
+ * op 0..4 = A, P, P^T, G, G^T; 0 = sliced ELL (one row per lane), 2..32 = vector CSR
+ * with that many lanes per row.  The choice is made at upload by timing each
+ * candidate on the level's own operator.  lanes must hold (levels-1)*10 entries. */
+amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
+
 /* Release the hierarchy and all device memory it holds (NULL is ignored). */
 void amge_hier_free(amge_hier* h);
 

@@ -61,6 +61,7 @@ _SIGS = {
     "amge_dot": [_vp, _vp, _vp, _i64, _vp, _vp],
     "amge_profile_enable": [_vp, _i32],
     "amge_set_graphs": [_vp, _i32],
+    "amge_autotune_report": [_vp, ctypes.POINTER(_i32)],
     "amge_server_create": [ctypes.c_size_t, _i32, ctypes.POINTER(_vp)],
     "amge_submit": [_vp, _vp, _vp, _vp, _i32, ctypes.POINTER(amge_solve_opts), ctypes.POINTER(ctypes.c_uint64)],
     "amge_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(amge_info)],
@@ -215,6 +216,16 @@ def amge_coarse_solve_noalloc(h: Hier, b, z, stream=None):
     (no allocation by the library during the call); see include/amge.h."""
     _check(_lib.amge_coarse_solve_noalloc(h.handle, _dptr(b), _dptr(z), _stream(stream)),
            "amge_coarse_solve_noalloc")
+
+
+def amge_autotune_report(h: Hier):
+    """{(level, 'fp64'|'fp32', op): lanes} -- 0 = sliced ELL, k = vector CSR with k lanes/row."""
+    L = h.levels
+    buf = (_i32 * max((L - 1) * 10, 1))()
+    _check(_lib.amge_autotune_report(h.handle, buf), "amge_autotune_report")
+    ops = ["A", "P", "PT", "G", "GT"]
+    return {(l, p, ops[o]): int(buf[(l * 2 + pi) * 5 + o]) for l in range(L - 1)
+            for pi, p in enumerate(("fp64", "fp32")) for o in range(5)}
 
 
 def amge_set_graphs(h: Hier, enable: bool = True):

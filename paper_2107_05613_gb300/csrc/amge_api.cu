@@ -20,6 +20,9 @@ struct LevelDev {
   int n = 0, naux = 0;
   DevSell<V> A, P, PT, G, GT;
   DevCsr<V> cA, cP, cPT, cG, cGT;  // CSR copies for the multi-RHS products
+  // autotuned single-vector kernel per operator (A, P, PT, G, GT): 0 = sliced ELL,
+  // 2..32 = vector CSR with that many lanes per row
+  int lanes[5] = {0, 0, 0, 0, 0};
   V* minv = nullptr;
   V* mauxinv = nullptr;
   V *x = nullptr, *r = nullptr, *y = nullptr, *tmp = nullptr;
@@ -222,6 +225,38 @@ void sell(amge_hier* h, int cls, const DevSell<V>& M, int epi, const SpmvArgs<V>
   launch_sell<V>(M, epi, a, s);
 }
 
+enum OpId { OP_A = 0, OP_P = 1, OP_PT = 2, OP_G = 3, OP_GT = 4 };
+
+template <typename V>
+const DevSell<V>& op_sell(const LevelDev<V>& d, int op) {
+  switch (op) {
+    case OP_A: return d.A;
+    case OP_P: return d.P;
+    case OP_PT: return d.PT;
+    case OP_G: return d.G;
+    default: return d.GT;
+  }
+}
+template <typename V>
+const DevCsr<V>& op_csr(const LevelDev<V>& d, int op) {
+  switch (op) {
+    case OP_A: return d.cA;
+    case OP_P: return d.cP;
+    case OP_PT: return d.cPT;
+    case OP_G: return d.cG;
+    default: return d.cGT;
+  }
+}
+
+// Single-vector product with the autotuned kernel of operator `op` on level d.
+template <typename V>
+void opk(amge_hier* h, int cls, const LevelDev<V>& d, int op, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  Prof p(h, cls, s);
+  const int lanes = d.lanes[op];
+  if (lanes == 0) launch_sell<V>(op_sell(d, op), epi, a, s);
+  else launch_csrv<V>(op_csr(d, op), lanes, epi, a, s);
+}
+
 // One V-cycle at level l: z = B_l^{-1} b (Algorithm 4.1, x0 = 0).
 template <typename V>
 void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
@@ -238,15 +273,15 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
   auto aux_sweep = [&]() {  // x += G M_aux^{-1} G^T r   (r = b - A x already formed)
     SpmvArgs<V> g;
     g.x = d.r, g.d = d.mauxinv, g.y = d.y;
-    sell<V>(h, AMGE_PROF_GT, d.GT, EPI_SCALE, g, s);
+    opk<V>(h, AMGE_PROF_GT, d, OP_GT, EPI_SCALE, g, s);
     SpmvArgs<V> c;
     c.x = d.y, c.y = x;
-    sell<V>(h, AMGE_PROF_G, d.G, EPI_ADD, c, s);
+    opk<V>(h, AMGE_PROF_G, d, OP_G, EPI_ADD, c, s);
   };
   auto residual = [&]() {
     SpmvArgs<V> a;
     a.x = x, a.b = b, a.y = d.r;
-    sell<V>(h, clsA, d.A, EPI_RESID, a, s);
+    opk<V>(h, clsA, d, OP_A, EPI_RESID, a, s);
   };
   // pre-relaxation: nu_pre steps of eq. 4.1
   for (int k = 0; k < h->nu_pre; k++) {
@@ -259,7 +294,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
     } else {
       SpmvArgs<V> a;  // x <- x + M^{-1} (b - A x)
       a.x = x, a.xin = x, a.d = d.minv, a.b = b, a.y = xt;
-      sell<V>(h, clsA, d.A, EPI_SWEEP, a, s);
+      opk<V>(h, clsA, d, OP_A, EPI_SWEEP, a, s);
       std::swap(x, xt);
       residual();
     }
@@ -271,13 +306,13 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
   {
     SpmvArgs<V> a;
     a.x = d.r, a.y = c.b;
-    sell<V>(h, AMGE_PROF_PT, d.PT, EPI_STORE, a, s);
+    opk<V>(h, AMGE_PROF_PT, d, OP_PT, EPI_STORE, a, s);
   }
   vcycle_level<V>(h, l + 1, c.b, c.z, s);
   {
     SpmvArgs<V> a;
     a.x = c.z, a.y = x;
-    sell<V>(h, AMGE_PROF_P, d.P, EPI_ADD, a, s);
+    opk<V>(h, AMGE_PROF_P, d, OP_P, EPI_ADD, a, s);
   }
   // post-relaxation with the transposed step: aux sweep first, then the point sweep
   for (int k = 0; k < h->nu_post; k++) {
@@ -286,7 +321,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
     const bool last = (k == h->nu_post - 1);
     SpmvArgs<V> a;
     a.x = x, a.xin = x, a.d = d.minv, a.b = b, a.y = last ? z : xt;
-    sell<V>(h, clsA, d.A, EPI_SWEEP, a, s);
+    opk<V>(h, clsA, d, OP_A, EPI_SWEEP, a, s);
     if (!last) std::swap(x, xt);
   }
 }
@@ -921,6 +956,54 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
   return AMGE_OK;
 }
 
+// Autotuner: time every candidate kernel of every level operator (sliced ELL and
+// vector CSR with 2..32 lanes per row, up to the operator's row length) on the work
+// vectors and keep the fastest; vector CSR must beat sliced ELL by 10% to be chosen.
+template <typename V>
+amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  LevelDev<V>& d = levels<V>(h)[l];
+  LevelDev<V>& c = levels<V>(h)[l + 1];
+  for (int op = 0; op < 5; op++) {
+    const DevCsr<V>& M = op_csr(d, op);
+    const V* in = op == OP_A ? d.x : op == OP_P ? c.b : op == OP_PT ? d.r : op == OP_G ? d.y : d.r;
+    V* out = op == OP_A ? d.tmp : op == OP_P ? d.tmp : op == OP_PT ? c.z : op == OP_G ? d.tmp : d.y;
+    SpmvArgs<V> a;
+    a.x = in, a.y = out;
+    const double avg = M.nr ? (double)M.nnz / M.nr : 0.0;
+    float best = 0.f;
+    int best_lanes = 0;
+    for (int lanes : {0, 2, 4, 8, 16, 32}) {
+      if (lanes > 2 && lanes > 2 * avg) break;
+      d.lanes[op] = lanes;
+      for (int w = 0; w < 2; w++) opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
+      CK(cudaEventRecord(e0, s));
+      for (int r = 0; r < 5; r++) opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (lanes == 0 || ms < 0.9f * best) best = (lanes == 0 || ms < best) ? ms : best, best_lanes = lanes;
+    }
+    d.lanes[op] = best_lanes;
+  }
+  return AMGE_OK;
+}
+
+amge_status autotune(amge_hier* h, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  amge_status st = AMGE_OK;
+  for (int l = 0; l + 1 < h->L && st == AMGE_OK; l++) {
+    st = autotune_level<double>(h, l, s, e0, e1);
+    if (st == AMGE_OK) st = autotune_level<float>(h, l, s, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int c = 0; c < AMGE_PROF_CLASSES; c++) h->launches[c] = 0;
+  return st;
+}
+
 amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier* h) {
   const int L = desc->num_levels;
   std::string err;
@@ -1028,6 +1111,9 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
   }
   h->op_bytes = h->bytes;
   amge_status st = alloc_work(h, s);
+  if (st) return st;
+  CK(cudaStreamSynchronize(s));
+  st = autotune(h, s);
   if (st) return st;
   CK(cudaStreamSynchronize(s));  // host staging (keep, keepd) must outlive the copies
   return AMGE_OK;
@@ -1399,6 +1485,19 @@ amge_status amge_dot(amge_hier* h, const double* x_dev, const double* y_dev, int
   }
   launch_dot(n, x_dev, y_dev, result_dev, h->red, as_stream(stream));
   return launch_status();
+}
+
+amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes) {
+  if (!h || !lanes) {
+    set_error("NULL argument");
+    return AMGE_EINVAL;
+  }
+  for (int l = 0; l + 1 < h->L; l++)
+    for (int op = 0; op < 5; op++) {
+      lanes[(l * 2 + 0) * 5 + op] = h->lv64[l].lanes[op];
+      lanes[(l * 2 + 1) * 5 + op] = h->lv32[l].lanes[op];
+    }
+  return AMGE_OK;
 }
 
 amge_status amge_set_graphs(amge_hier* h, int32_t enable) {

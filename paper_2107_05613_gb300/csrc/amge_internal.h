@@ -80,6 +80,18 @@ struct DevCsr {
   V* val = nullptr;
 };
 
+template <typename V>
+void launch_csrv(const DevCsr<V>& M, int lanes, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+
+// A level operator in both layouts; `lanes` is the autotuned kernel choice for
+// single-vector products: 0 = sliced ELL (one row per lane), 2..32 = vector CSR.
+template <typename V>
+struct DevOp {
+  DevSell<V> sell;
+  DevCsr<V> csr;
+  int lanes = 0;
+};
+
 // Multi-RHS product on [n][nrhs] blocks (nrhs <= 32): a group of K lanes (K = the
 // power of two >= nrhs) per row, lane c handling column c; the epilogues are those of
 // the single-vector kernels applied column by column (d is per row).

@@ -73,6 +73,41 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
   }
 }
 
+// Vector CSR: a group of LANES lanes per row with a shuffle reduction.  Costs a few
+// extra adds per row but exposes LANES times more threads: the autotuner picks it for
+// operators with few or long rows, where one row per lane cannot hide latency.
+template <typename V, int LANES, int EPI>
+__global__ void __launch_bounds__(kBlock) k_csrv(int nr, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                 const V* __restrict__ val, SpmvArgs<V> a) {
+  const int gt = blockIdx.x * kBlock + threadIdx.x;
+  const int row = gt / LANES;
+  const int lane = gt & (LANES - 1);
+  const bool ok = row < nr;
+  int beg = 0, end = 0;
+  if (ok) {
+    beg = ldg(rp + row);
+    end = ldg(rp + row + 1);
+  }
+  V s0 = V(0), s1 = V(0);
+  int j = beg + lane;
+  for (; j + LANES < end; j += 2 * LANES) {
+    s0 = fma(ldg(val + j), ldg(a.x + ldg(ci + j)), s0);
+    s1 = fma(ldg(val + j + LANES), ldg(a.x + ldg(ci + j + LANES)), s1);
+  }
+  if (j < end) s0 = fma(ldg(val + j), ldg(a.x + ldg(ci + j)), s0);
+  V s = s0 + s1;
+#pragma unroll
+  for (int off = LANES / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (!ok || lane != 0) return;
+  switch (EPI) {
+    case EPI_STORE: a.y[row] = s; break;
+    case EPI_RESID: a.y[row] = a.b[row] - s; break;
+    case EPI_SCALE: a.y[row] = a.d[row] * s; break;
+    case EPI_ADD: a.y[row] += s; break;
+    case EPI_SWEEP: a.y[row] = fma(a.d[row], a.b[row] - s, a.xin[row]); break;
+  }
+}
+
 template <typename V>
 __global__ void k_mul(int64_t n, const V* __restrict__ d, const V* __restrict__ x, V* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -279,6 +314,32 @@ void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_
     case EPI_SWEEP: k_sell<V, EPI_SWEEP><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
   }
 }
+template <typename V, int LANES>
+static void launch_csrv_lanes(const DevCsr<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  const int grid = (int)(((int64_t)M.nr * LANES + kBlock - 1) / kBlock);
+  if (grid == 0) return;
+  switch (epi) {
+    case EPI_STORE: k_csrv<V, LANES, EPI_STORE><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
+    case EPI_RESID: k_csrv<V, LANES, EPI_RESID><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
+    case EPI_SCALE: k_csrv<V, LANES, EPI_SCALE><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
+    case EPI_ADD: k_csrv<V, LANES, EPI_ADD><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
+    case EPI_SWEEP: k_csrv<V, LANES, EPI_SWEEP><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
+  }
+}
+
+template <typename V>
+void launch_csrv(const DevCsr<V>& M, int lanes, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  switch (lanes) {
+    case 2: launch_csrv_lanes<V, 2>(M, epi, a, s); break;
+    case 4: launch_csrv_lanes<V, 4>(M, epi, a, s); break;
+    case 8: launch_csrv_lanes<V, 8>(M, epi, a, s); break;
+    case 16: launch_csrv_lanes<V, 16>(M, epi, a, s); break;
+    default: launch_csrv_lanes<V, 32>(M, epi, a, s); break;
+  }
+}
+template void launch_csrv<double>(const DevCsr<double>&, int, int, const SpmvArgs<double>&, cudaStream_t);
+template void launch_csrv<float>(const DevCsr<float>&, int, int, const SpmvArgs<float>&, cudaStream_t);
+
 template void launch_sell<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t);
 template void launch_sell<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t);
 
