@@ -178,17 +178,19 @@ def sweep_bytes(nnz, n, w, extra_vectors, nrhs=1):
     return nnz * (w + 4) + 4 * (n + 1) + w * n * nrhs * 3 + w * n * extra_vectors
 
 
-def a_fine_bytes_per_launch(hh, w, nrhs=1):
-    """Average algorithmic bytes of the four level-0 A sweeps of one V-cycle:
-    three residuals r = b - A x and the final l1 sweep z = x + m^-1 (b - A x)
-    (which also reads m^-1)."""
+def a_fine_bytes_per_launch(hh, w, nrhs=1, ag=False):
+    """Average algorithmic bytes of the level-0 A sweeps of one V-cycle.  Without the
+    A G update: three residuals r = b - A x and the final l1 sweep z = x + m^-1 (b - A x)
+    (which also reads m^-1); with it (H(curl)): two residuals r = b - A x."""
     A = hh.A[0]
     n, nnz = A.shape[0], A.nnz
+    if ag:
+        return float(sweep_bytes(nnz, n, w, 0, nrhs))
     kinds = [sweep_bytes(nnz, n, w, 0, nrhs)] * 3 + [sweep_bytes(nnz, n, w, 1, nrhs)]
     return sum(kinds) / 4.0
 
 
-def vcycle_bytes(hh, w):
+def vcycle_bytes(hh, w, ag_nnz=None):
     """Algorithmic bytes of one V-cycle (every level's sweeps, transfers and the
     coarsest triangular products, which always read FP64 factors)."""
     tot = 0.0
@@ -196,7 +198,13 @@ def vcycle_bytes(hh, w):
     for l in range(L - 1):
         A, P, G = hh.A[l], hh.P[l], hh.G[l]
         n, naux, nc = A.shape[0], G.shape[1], P.shape[1]
-        tot += 3 * sweep_bytes(A.nnz, n, w, 0) + sweep_bytes(A.nnz, n, w, 1) + 3 * w * n   # + x = m^-1 b
+        AGnnz = ag_nnz[l] if ag_nnz else None
+        if AGnnz:   # two residuals, r -= (A G) y (reads r, y; writes r), final sweep through A G
+            tot += 2 * sweep_bytes(A.nnz, n, w, 0) + 3 * w * n
+            tot += AGnnz * (w + 4) + 4 * (n + 1) + w * (naux + 2 * n)
+            tot += AGnnz * (w + 4) + 4 * (n + 1) + w * (naux + 4 * n)
+        else:
+            tot += 3 * sweep_bytes(A.nnz, n, w, 0) + sweep_bytes(A.nnz, n, w, 1) + 3 * w * n   # + x = m^-1 b
         # G^T r scaled (2x), G y added (2x): read + write of the output for the add
         tot += 2 * (G.nnz * (w + 4) + 4 * (naux + 1) + w * (n + 2 * naux))
         tot += 2 * (G.nnz * (w + 4) + 4 * (n + 1) + w * (naux + 2 * n))
@@ -371,19 +379,25 @@ def run_ours(args, dist):
     hbm = hbm or HBM_FALLBACK_GBS
     c, m = prof["A_fine"]
     if c and m > 0:
-        bytes_launch = a_fine_bytes_per_launch(hh, w, nrhs)
+        ag = tuned.get((0, "fp64" if w == 8 else "fp32", "AG"), -1) >= 0
+        bytes_launch = a_fine_bytes_per_launch(hh, w, nrhs, ag)
         achieved = bytes_launch / (m / c / 1e3) / 1e9
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                             "frac": achieved / hbm,
                             "traffic": NCU_TRAFFIC.get((args.workload, w)) if nrhs == 1 else None,
-                            "kernel": "k_sell level-0 A sweeps (three residuals, final l1 sweep), "
+                            "kernel": ("k_sell level-0 A residual sweeps r = b - A x" if ag else
+                                       "k_sell level-0 A sweeps (three residuals, final l1 sweep)") + ", "
                                       + ("FP32" if w == 4 else "FP64"),
                             "bytes_per_launch": bytes_launch, "peak_source": peak_src}
-    vc_ms = sum(prof[k][1] for k in ("A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "vcycle_vec"))
+    vc_ms = sum(prof[k][1] for k in ("A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "vcycle_vec", "AG"))
     n_vc = sum(iters) + len(iters)  # one V-cycle per iteration plus the initial one (speculative ones add)
-    if vc_ms > 0:
-        line["vcycle_hbm_gbs"] = vcycle_bytes(hh, w) * (prof["A_fine"][0] / 4) / (vc_ms / 1e3) / 1e9
-        line["vcycle_us"] = 1e3 * vc_ms / (prof["A_fine"][0] / 4)
+    n_vc = prof["coarse"][0] / 2          # one coarsest solve (two kernels) per V-cycle
+    if vc_ms > 0 and n_vc > 0:
+        pname = "fp64" if w == 8 else "fp32"
+        ag_nnz = [(hh.A[l].to_scipy() @ hh.G[l].to_scipy()).nnz if tuned.get((l, pname, "AG"), -1) >= 0 else None
+                  for l in range(len(hh.A) - 1)]
+        line["vcycle_hbm_gbs"] = vcycle_bytes(hh, w, ag_nnz) * n_vc / (vc_ms / 1e3) / 1e9
+        line["vcycle_us"] = 1e3 * vc_ms / n_vc
     if args.quick:
         if dist.rank == 0:
             print(json.dumps(line), flush=True)

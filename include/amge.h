@@ -195,7 +195,8 @@ enum {
   AMGE_PROF_PCG_SPMV = 7,  /* q = A p with p.q */
   AMGE_PROF_PCG_VEC = 8,   /* PCG vector updates, dots, casts */
   AMGE_PROF_VCYCLE_VEC = 9, /* V-cycle elementwise products (x = m^-1 b on entry to a level) */
-  AMGE_PROF_CLASSES = 10
+  AMGE_PROF_AG = 10,        /* residual updates r -= (A G) y after an aux sweep (H(curl)) */
+  AMGE_PROF_CLASSES = 11
 };
 amge_status amge_profile_enable(amge_hier* h, int32_t enable);
 amge_status amge_profile_read(amge_hier* h, int64_t* count, double* ms);
@@ -282,10 +283,13 @@ void amge_server_destroy(amge_server* s);
 amge_status amge_set_graphs(amge_hier* h, int32_t enable);
 
 /* The autotuner's kernel choice for every smoothing level's single-vector products:
- * lanes[(l * 2 + p) * 5 + op] for level l < levels-1, precision p (0 FP64, 1 FP32),
- * op 0..4 = A, P, P^T, G, G^T; 0 = sliced ELL (one row per lane), 2..32 = vector CSR
- * with that many lanes per row.  The choice is made at upload by timing each
- * candidate on the level's own operator.  lanes must hold (levels-1)*10 entries. */
+ * lanes[(l * 2 + p) * 6 + op] for level l < levels-1, precision p (0 FP64, 1 FP32),
+ * op 0..5 = A, P, P^T, G, G^T, AG; 0 = sliced ELL (one row per lane), 2..32 = vector
+ * CSR with that many lanes per row, -1 = operator not used (AG is stored only where
+ * A G = A_l G_l is much sparser than A_l, i.e. for H(curl): there the residual after
+ * an aux sweep is updated as r - (A G) y instead of recomputed as b - A x).  The
+ * choice is made at upload by timing each candidate on the level's own operator.
+ * lanes must hold (levels-1)*12 entries. */
 amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
 
 /* Release the hierarchy and all device memory it holds (NULL is ignored). */

@@ -24,7 +24,7 @@ AMGE_EAGAIN, AMGE_ETIMEOUT, AMGE_ECANCELED = 6, 7, 8
 AMGE_HCURL, AMGE_HDIV = 1, 2
 AMGE_FP64, AMGE_FP32_VCYCLE = 0, 1
 AMGE_OP_A, AMGE_OP_P, AMGE_OP_PT, AMGE_OP_G, AMGE_OP_GT, AMGE_OP_SMOOTH_PRE, AMGE_OP_COARSE = range(7)
-PROF_CLASSES = ["A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "pcg_spmv", "pcg_vec", "vcycle_vec"]
+PROF_CLASSES = ["A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "pcg_spmv", "pcg_vec", "vcycle_vec", "AG"]
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENONFINITE",
                 6: "EAGAIN", 7: "ETIMEOUT", 8: "ECANCELED"}
 
@@ -219,13 +219,14 @@ def amge_coarse_solve_noalloc(h: Hier, b, z, stream=None):
 
 
 def amge_autotune_report(h: Hier):
-    """{(level, 'fp64'|'fp32', op): lanes} -- 0 = sliced ELL, k = vector CSR with k lanes/row."""
+    """{(level, 'fp64'|'fp32', op): lanes} -- 0 = sliced ELL, k = vector CSR with k lanes/row,
+    -1 = operator not stored."""
     L = h.levels
-    buf = (_i32 * max((L - 1) * 10, 1))()
+    buf = (_i32 * max((L - 1) * 12, 1))()
     _check(_lib.amge_autotune_report(h.handle, buf), "amge_autotune_report")
-    ops = ["A", "P", "PT", "G", "GT"]
-    return {(l, p, ops[o]): int(buf[(l * 2 + pi) * 5 + o]) for l in range(L - 1)
-            for pi, p in enumerate(("fp64", "fp32")) for o in range(5)}
+    ops = ["A", "P", "PT", "G", "GT", "AG"]
+    return {(l, p, ops[o]): int(buf[(l * 2 + pi) * 6 + o]) for l in range(L - 1)
+            for pi, p in enumerate(("fp64", "fp32")) for o in range(6)}
 
 
 def amge_set_graphs(h: Hier, enable: bool = True):

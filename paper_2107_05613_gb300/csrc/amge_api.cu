@@ -20,9 +20,14 @@ struct LevelDev {
   int n = 0, naux = 0;
   DevSell<V> A, P, PT, G, GT;
   DevCsr<V> cA, cP, cPT, cG, cGT;  // CSR copies for the multi-RHS products
-  // autotuned single-vector kernel per operator (A, P, PT, G, GT): 0 = sliced ELL,
-  // 2..32 = vector CSR with that many lanes per row
-  int lanes[5] = {0, 0, 0, 0, 0};
+  // A G (n x naux), stored where it is much sparser than A: the residual after an aux
+  // sweep is then updated as r - (A G) y instead of recomputed as b - A x
+  DevSell<V> AG;
+  DevCsr<V> cAG;
+  bool use_ag = false;
+  // autotuned single-vector kernel per operator (A, P, PT, G, GT, AG): 0 = sliced
+  // ELL, 2..32 = vector CSR with that many lanes per row, -1 = not stored
+  int lanes[6] = {0, 0, 0, 0, 0, -1};
   V* minv = nullptr;
   V* mauxinv = nullptr;
   V *x = nullptr, *r = nullptr, *y = nullptr, *tmp = nullptr;
@@ -225,7 +230,7 @@ void sell(amge_hier* h, int cls, const DevSell<V>& M, int epi, const SpmvArgs<V>
   launch_sell<V>(M, epi, a, s);
 }
 
-enum OpId { OP_A = 0, OP_P = 1, OP_PT = 2, OP_G = 3, OP_GT = 4 };
+enum OpId { OP_A = 0, OP_P = 1, OP_PT = 2, OP_G = 3, OP_GT = 4, OP_AG = 5 };
 
 template <typename V>
 const DevSell<V>& op_sell(const LevelDev<V>& d, int op) {
@@ -234,7 +239,8 @@ const DevSell<V>& op_sell(const LevelDev<V>& d, int op) {
     case OP_P: return d.P;
     case OP_PT: return d.PT;
     case OP_G: return d.G;
-    default: return d.GT;
+    case OP_GT: return d.GT;
+    default: return d.AG;
   }
 }
 template <typename V>
@@ -244,7 +250,8 @@ const DevCsr<V>& op_csr(const LevelDev<V>& d, int op) {
     case OP_P: return d.cP;
     case OP_PT: return d.cPT;
     case OP_G: return d.cG;
-    default: return d.cGT;
+    case OP_GT: return d.cGT;
+    default: return d.cAG;
   }
 }
 
@@ -283,6 +290,37 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
     a.x = x, a.b = b, a.y = d.r;
     opk<V>(h, clsA, d, OP_A, EPI_RESID, a, s);
   };
+  if (d.use_ag) {  // nu_pre = nu_post = 1; residual after each aux sweep by r -= (A G) y
+    LevelDev<V>& c = lv[l + 1];
+    {
+      Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
+      launch_mul<V>(d.n, d.minv, b, x, s);
+    }
+    residual();
+    aux_sweep();
+    {
+      SpmvArgs<V> a;  // r = r - (A G) y (in place: row i reads and writes r_i only)
+      a.x = d.y, a.b = d.r, a.y = d.r;
+      opk<V>(h, AMGE_PROF_AG, d, OP_AG, EPI_RESID, a, s);
+    }
+    {
+      SpmvArgs<V> a;
+      a.x = d.r, a.y = c.b;
+      opk<V>(h, AMGE_PROF_PT, d, OP_PT, EPI_STORE, a, s);
+    }
+    vcycle_level<V>(h, l + 1, c.b, c.z, s);
+    {
+      SpmvArgs<V> a;
+      a.x = c.z, a.y = x;
+      opk<V>(h, AMGE_PROF_P, d, OP_P, EPI_ADD, a, s);
+    }
+    residual();
+    aux_sweep();
+    SpmvArgs<V> a;  // z = x + M^{-1} (r - (A G) y)
+    a.x = d.y, a.xin = x, a.d = d.minv, a.b = d.r, a.y = z;
+    opk<V>(h, AMGE_PROF_AG, d, OP_AG, EPI_SWEEP, a, s);
+    return;
+  }
   // pre-relaxation: nu_pre steps of eq. 4.1
   for (int k = 0; k < h->nu_pre; k++) {
     if (k == 0) {  // from x0 = 0: x = M^{-1} b, then r = b - A x
@@ -707,6 +745,37 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
     a.x = x, a.b = b, a.y = d.R;
     mm(clsA, d.cA, EPI_RESID, a);
   };
+  if (d.use_ag) {  // as in vcycle_level: r -= (A G) y after each aux sweep
+    LevelDev<V>& c = lv[l + 1];
+    {
+      Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
+      launch_mul_mm<V>(d.n, nrhs, d.minv, b, x, s);
+    }
+    residual();
+    aux_sweep();
+    {
+      SpmvArgs<V> a;
+      a.x = d.Y, a.b = d.R, a.y = d.R;
+      mm(AMGE_PROF_AG, d.cAG, EPI_RESID, a);
+    }
+    {
+      SpmvArgs<V> a;
+      a.x = d.R, a.y = c.B;
+      mm(AMGE_PROF_PT, d.cPT, EPI_STORE, a);
+    }
+    vcycle_level_mm<V>(h, l + 1, nrhs, c.B, c.Z, s);
+    {
+      SpmvArgs<V> a;
+      a.x = c.Z, a.y = x;
+      mm(AMGE_PROF_P, d.cP, EPI_ADD, a);
+    }
+    residual();
+    aux_sweep();
+    SpmvArgs<V> a;
+    a.x = d.Y, a.xin = x, a.d = d.minv, a.b = d.R, a.y = z;
+    mm(AMGE_PROF_AG, d.cAG, EPI_SWEEP, a);
+    return;
+  }
   for (int k = 0; k < h->nu_pre; k++) {
     if (k == 0) {
       {
@@ -963,10 +1032,11 @@ template <typename V>
 amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   LevelDev<V>& d = levels<V>(h)[l];
   LevelDev<V>& c = levels<V>(h)[l + 1];
-  for (int op = 0; op < 5; op++) {
+  for (int op = 0; op < 6; op++) {
+    if (op == OP_AG && !d.use_ag) continue;
     const DevCsr<V>& M = op_csr(d, op);
-    const V* in = op == OP_A ? d.x : op == OP_P ? c.b : op == OP_PT ? d.r : op == OP_G ? d.y : d.r;
-    V* out = op == OP_A ? d.tmp : op == OP_P ? d.tmp : op == OP_PT ? c.z : op == OP_G ? d.tmp : d.y;
+    const V* in = op == OP_A ? d.x : op == OP_P ? c.b : op == OP_PT ? d.r : op == OP_G ? d.y : op == OP_GT ? d.r : d.y;
+    V* out = op == OP_A ? d.tmp : op == OP_P ? d.tmp : op == OP_PT ? c.z : op == OP_G ? d.tmp : op == OP_GT ? d.y : d.tmp;
     SpmvArgs<V> a;
     a.x = in, a.y = out;
     const double avg = M.nr ? (double)M.nnz / M.nr : 0.0;
@@ -1073,6 +1143,15 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
         upload_csr(h, PT, d64.cPT, d32.cPT, s, keep);
         upload_csr(h, G, d64.cG, d32.cG, s, keep);
         upload_csr(h, GT, d64.cGT, d32.cGT, s, keep);
+        if (desc->form == AMGE_HCURL && desc->nu_pre == 1 && desc->nu_post == 1) {
+          HostCsr AG = sparse_product(A, G);
+          if (AG.nnz() < 0.6 * A.nnz()) {
+            upload_sell(h, AG, d64.AG, d32.AG, s, keep, keeps);
+            upload_csr(h, AG, d64.cAG, d32.cAG, s, keep);
+            d64.use_ag = d32.use_ag = true;
+            d64.lanes[OP_AG] = d32.lanes[OP_AG] = 0;
+          }
+        }
         if (l == 0) h->cA0 = d64.cA;
         keepd.push_back(minv);
         d64.minv = upload<double>(h, keepd.back().data(), n[l], s);
@@ -1493,9 +1572,9 @@ amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes) {
     return AMGE_EINVAL;
   }
   for (int l = 0; l + 1 < h->L; l++)
-    for (int op = 0; op < 5; op++) {
-      lanes[(l * 2 + 0) * 5 + op] = h->lv64[l].lanes[op];
-      lanes[(l * 2 + 1) * 5 + op] = h->lv32[l].lanes[op];
+    for (int op = 0; op < 6; op++) {
+      lanes[(l * 2 + 0) * 6 + op] = h->lv64[l].lanes[op];
+      lanes[(l * 2 + 1) * 6 + op] = h->lv32[l].lanes[op];
     }
   return AMGE_OK;
 }

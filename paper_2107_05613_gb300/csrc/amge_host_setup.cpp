@@ -66,6 +66,47 @@ std::vector<double> l1_row_sums(const HostCsr& A) {
   return m;
 }
 
+HostCsr sparse_product(const HostCsr& A, const HostCsr& B) {
+  HostCsr C;
+  C.nr = A.nr, C.nc = B.nc;
+  std::vector<std::vector<std::pair<int, double>>> rows(A.nr);
+#pragma omp parallel
+  {
+    std::vector<double> acc(B.nc, 0.0);
+    std::vector<char> seen(B.nc, 0);
+    std::vector<int> touched;
+#pragma omp for schedule(dynamic, 512)
+    for (int i = 0; i < A.nr; i++) {
+      touched.clear();
+      for (int p = A.rp[i]; p < A.rp[i + 1]; p++) {
+        const int k = A.ci[p];
+        const double a = A.v[p];
+        for (int q = B.rp[k]; q < B.rp[k + 1]; q++) {
+          const int j = B.ci[q];
+          if (!seen[j]) seen[j] = 1, touched.push_back(j);
+          acc[j] += a * B.v[q];
+        }
+      }
+      std::sort(touched.begin(), touched.end());
+      for (int j : touched) {
+        if (acc[j] != 0.0) rows[i].push_back({j, acc[j]});
+        acc[j] = 0.0;
+        seen[j] = 0;
+      }
+    }
+  }
+  C.rp.assign(A.nr + 1, 0);
+  for (int i = 0; i < A.nr; i++) C.rp[i + 1] = C.rp[i] + (int)rows[i].size();
+  C.ci.resize(C.rp[A.nr]);
+  C.v.resize(C.rp[A.nr]);
+  for (int i = 0; i < A.nr; i++)
+    for (size_t t = 0; t < rows[i].size(); t++) {
+      C.ci[C.rp[i] + t] = rows[i][t].first;
+      C.v[C.rp[i] + t] = rows[i][t].second;
+    }
+  return C;
+}
+
 // Row l1 sums of G^T A G, row a: sum_b |sum_{i,j} G_ia A_ij G_jb|, with a dense
 // accumulator over the aux columns touched by row a.
 std::vector<double> aux_l1_row_sums(const HostCsr& A, const HostCsr& G, const HostCsr& GT) {

@@ -133,7 +133,8 @@ enum Scalar : int {
   SC_COUNT = 16
 };
 constexpr int kRedSlots = 4;
-constexpr int kMaxRedBlocks = 1024;
+constexpr int kMaxRedBlocks = 8192;   // capacity of the block-partial arrays
+constexpr int kVecRedBlocks = 1024;   // grid cap of the vector reductions
 
 struct RedScratch {
   double* partials = nullptr;  // [kRedSlots][kMaxRedBlocks]
@@ -204,6 +205,8 @@ bool check_csr(const amge_csr& c, int nr, int nc, const char* what, std::string&
 HostCsr to_host(const amge_csr& c);
 HostCsr transpose(const HostCsr& A);
 std::vector<double> l1_row_sums(const HostCsr& A);
+// C = A B (FP64; entries that cancel to exactly zero are dropped).
+HostCsr sparse_product(const HostCsr& A, const HostCsr& B);
 std::vector<double> aux_l1_row_sums(const HostCsr& A, const HostCsr& G, const HostCsr& GT);
 // Dense Cholesky of the coarsest matrix; returns false if not SPD.  Linv = L^{-1}
 // (row-major, lower triangle), LinvT its transpose (row-major, upper triangle).

@@ -297,7 +297,7 @@ int vec_grid(int64_t n) {
 
 int red_blocks(int64_t n) {
   int64_t g = (n + 4 * kBlock - 1) / (4 * kBlock);
-  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), kMaxRedBlocks);
+  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), kVecRedBlocks);
 }
 
 template <typename V>
@@ -375,7 +375,7 @@ void launch_dot(int64_t n, const double* x, const double* y, double* out, const 
 
 void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, const RedScratch& r,
                          cudaStream_t s) {
-  const int warps_per_block = kBlock / 32;
+  const int warps_per_block = kBlock / 32;  // one slice per warp, as in the plain sweep
   const int grid = std::min((A.nslices + warps_per_block - 1) / warps_per_block, kMaxRedBlocks);
   k_pcg_spmv_dot<<<std::max(grid, 1), kBlock, 0, s>>>(A.nslices, A.sptr, A.srow, reinterpret_cast<const int2*>(A.ci),
                                                       reinterpret_cast<const double2*>(A.val), p, q, r);

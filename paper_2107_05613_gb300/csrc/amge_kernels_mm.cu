@@ -238,7 +238,7 @@ int pow2_at_least(int v) {
 int mm_red_blocks(int64_t n, int K) {
   const int64_t rows_per_block = kBlock / K;
   int64_t g = (n + 4 * rows_per_block - 1) / (4 * rows_per_block);
-  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), kMaxRedBlocks);
+  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), kVecRedBlocks);
 }
 
 int grid_for(int64_t tot) {

@@ -33,7 +33,8 @@ struct Request {
   amge_hier* hier = nullptr;
   int nrhs = 1;
   int64_t n = 0;
-  std::vector<double> b;  // [n][nrhs], copied at submission
+  double* bcol = nullptr;  // pinned [nrhs][n]: the right-hand sides, one column after another
+  double* xcol = nullptr;  // pinned [nrhs][n]: the solutions, scattered into x_host on collection
   double* x_host = nullptr;
   amge_solve_opts opts{};
   std::vector<amge_info> info;
@@ -50,8 +51,6 @@ struct Slot {
   cudaEvent_t ev = nullptr;
   double* b_dev = nullptr;
   double* x_dev = nullptr;
-  double* stage_in = nullptr;   // pinned [n]: gathered right-hand-side column
-  double* stage_out = nullptr;  // pinned [n]: solution column before the scatter
   size_t bytes = 0;
   PcgRun* run = nullptr;
   Request* req = nullptr;
@@ -88,8 +87,6 @@ void free_slot(amge_server* sv, Slot* sl) {
   if (sl->view) amge_hier_free(sl->view);
   if (sl->b_dev) cudaFree(sl->b_dev);
   if (sl->x_dev) cudaFree(sl->x_dev);
-  if (sl->stage_in) cudaFreeHost(sl->stage_in);
-  if (sl->stage_out) cudaFreeHost(sl->stage_out);
   if (sl->ev) cudaEventDestroy(sl->ev);
   if (sl->stream) cudaStreamDestroy(sl->stream);
   sv->used -= sl->bytes;
@@ -105,9 +102,7 @@ Slot* make_slot(amge_server* sv, amge_hier* hier) {
   bool ok = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&sl->ev, cudaEventDisableTiming) == cudaSuccess &&
             cudaMalloc(&sl->b_dev, n * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&sl->x_dev, n * sizeof(double)) == cudaSuccess &&
-            cudaMallocHost(&sl->stage_in, n * sizeof(double)) == cudaSuccess &&
-            cudaMallocHost(&sl->stage_out, n * sizeof(double)) == cudaSuccess;
+            cudaMalloc(&sl->x_dev, n * sizeof(double)) == cudaSuccess;
   if (ok) ok = amge::hier_make_view(hier, sl->stream, &sl->view) == AMGE_OK;
   if (!ok) {
     cudaGetLastError();
@@ -137,10 +132,8 @@ void finish_request(amge_server* sv, Request* rq) {
 // Start column `col` of `rq` in slot `sl` (mutex held).
 bool start_column(amge_server* sv, Slot* sl, Request* rq, int col) {
   const int64_t n = rq->n;
-  // the slot is idle, so its stream has finished every earlier use of stage_in
-  for (int64_t i = 0; i < n; i++) sl->stage_in[i] = rq->b[(size_t)i * rq->nrhs + col];
-  if (cudaMemcpyAsync(sl->b_dev, sl->stage_in, n * sizeof(double), cudaMemcpyHostToDevice, sl->stream) !=
-      cudaSuccess)
+  if (cudaMemcpyAsync(sl->b_dev, rq->bcol + (size_t)col * n, n * sizeof(double), cudaMemcpyHostToDevice,
+                      sl->stream) != cudaSuccess)
     return false;
   if (amge::pcg_run_start(sl->view, sl->b_dev, sl->x_dev, rq->opts, sl->stream, &sl->run) != AMGE_OK) return false;
   sl->req = rq;
@@ -178,7 +171,8 @@ bool advance_slots(amge_server* sv) {
         amge::pcg_run_finish(sl->run, &info);
         sl->run = nullptr;
         sl->req->info[sl->col] = info;
-        cudaMemcpyAsync(sl->stage_out, sl->x_dev, sl->req->n * sizeof(double), cudaMemcpyDeviceToHost, sl->stream);
+        cudaMemcpyAsync(sl->req->xcol + (size_t)sl->col * sl->req->n, sl->x_dev, sl->req->n * sizeof(double),
+                        cudaMemcpyDeviceToHost, sl->stream);
         cudaEventRecord(sl->ev, sl->stream);
         sl->phase = 2;
         progressed = true;
@@ -192,7 +186,6 @@ bool advance_slots(amge_server* sv) {
         progressed = true;
         continue;
       }
-      for (int64_t i = 0; i < rq->n; i++) rq->x_host[(size_t)i * rq->nrhs + sl->col] = sl->stage_out[i];
       rq->running--;
       rq->cols_done++;
       sv->running_cols--;
@@ -325,7 +318,18 @@ amge_status amge_submit(amge_server* sv, amge_hier* h, const double* b_host, dou
   rq->hier = h;
   rq->nrhs = nrhs;
   rq->n = amge::hier_dofs(h);
-  rq->b.assign(b_host, b_host + (size_t)rq->n * nrhs);
+  const size_t bytes = (size_t)rq->n * nrhs * sizeof(double);
+  if (cudaMallocHost(&rq->bcol, bytes) != cudaSuccess || cudaMallocHost(&rq->xcol, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    if (rq->bcol) cudaFreeHost(rq->bcol);
+    delete rq;
+    amge::set_error("amge_submit: pinned staging allocation failed");
+    return AMGE_ENOMEM;
+  }
+  std::memset(rq->xcol, 0, bytes);  // columns that never run (cancelled, failed) read as zero
+  // column-major copy, done here in the caller's thread (the scheduler only issues copies)
+  for (int64_t i = 0; i < rq->n; i++)
+    for (int c = 0; c < nrhs; c++) rq->bcol[(size_t)c * rq->n + i] = b_host[(size_t)i * nrhs + c];
   rq->x_host = x_host;
   rq->opts = *opts;
   rq->info.assign(nrhs, amge_info{0, AMGE_EAGAIN, 0.0, 0.0});
@@ -342,13 +346,29 @@ amge_status amge_submit(amge_server* sv, amge_hier* h, const double* b_host, dou
   return AMGE_OK;
 }
 
-static amge_status collect(amge_server* sv, std::map<uint64_t, Request*>::iterator it, amge_info* info) {
+static void release(Request* rq) {
+  if (rq->bcol) cudaFreeHost(rq->bcol);
+  if (rq->xcol) cudaFreeHost(rq->xcol);
+  delete rq;
+}
+
+// Detach a finished request (mutex held by the caller); the caller then finishes it
+// with hand_back() after releasing the mutex.
+static Request* detach(amge_server* sv, std::map<uint64_t, Request*>::iterator it) {
   Request* rq = it->second;
+  sv->reqs.erase(it);
+  return rq;
+}
+
+// Scatter the solution columns into the caller's x_host (in the caller's thread,
+// without the server mutex) and release the request.
+static amge_status hand_back(Request* rq, amge_info* info) {
   if (info)
     for (int c = 0; c < rq->nrhs; c++) info[c] = rq->info[c];
+  for (int64_t i = 0; i < rq->n; i++)
+    for (int c = 0; c < rq->nrhs; c++) rq->x_host[(size_t)i * rq->nrhs + c] = rq->xcol[(size_t)c * rq->n + i];
   const amge_status st = rq->status;
-  sv->reqs.erase(it);
-  delete rq;
+  release(rq);
   return st;
 }
 
@@ -357,14 +377,18 @@ amge_status amge_poll(amge_server* sv, uint64_t ticket, amge_info* info) {
     amge::set_error("amge_poll: NULL server");
     return AMGE_EINVAL;
   }
-  std::lock_guard<std::mutex> lk(sv->mu);
-  auto it = sv->reqs.find(ticket);
-  if (it == sv->reqs.end()) {
-    amge::set_error("amge_poll: unknown ticket");
-    return AMGE_EINVAL;
+  Request* rq = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) {
+      amge::set_error("amge_poll: unknown ticket");
+      return AMGE_EINVAL;
+    }
+    if (!it->second->done) return AMGE_EAGAIN;
+    rq = detach(sv, it);
   }
-  if (!it->second->done) return AMGE_EAGAIN;
-  return collect(sv, it, info);
+  return hand_back(rq, info);
 }
 
 amge_status amge_wait(amge_server* sv, uint64_t ticket, int32_t timeout_ms, amge_info* info) {
@@ -372,20 +396,24 @@ amge_status amge_wait(amge_server* sv, uint64_t ticket, int32_t timeout_ms, amge
     amge::set_error("amge_wait: NULL server");
     return AMGE_EINVAL;
   }
-  std::unique_lock<std::mutex> lk(sv->mu);
-  auto it = sv->reqs.find(ticket);
-  if (it == sv->reqs.end()) {
-    amge::set_error("amge_wait: unknown ticket");
-    return AMGE_EINVAL;
+  Request* rq = nullptr;
+  {
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) {
+      amge::set_error("amge_wait: unknown ticket");
+      return AMGE_EINVAL;
+    }
+    Request* r0 = it->second;
+    const auto pred = [&] { return r0->done; };
+    if (timeout_ms < 0) {
+      sv->cv_done.wait(lk, pred);
+    } else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) {
+      return AMGE_ETIMEOUT;
+    }
+    rq = detach(sv, sv->reqs.find(ticket));
   }
-  Request* rq = it->second;
-  const auto pred = [&] { return rq->done; };
-  if (timeout_ms < 0) {
-    sv->cv_done.wait(lk, pred);
-  } else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) {
-    return AMGE_ETIMEOUT;
-  }
-  return collect(sv, sv->reqs.find(ticket), info);
+  return hand_back(rq, info);
 }
 
 amge_status amge_cancel(amge_server* sv, uint64_t ticket) {
@@ -430,7 +458,7 @@ void amge_server_destroy(amge_server* sv) {
     if (sl->run) amge::pcg_run_free(sl->run);
     free_slot(sv, sl);
   }
-  for (auto& kv : sv->reqs) delete kv.second;
+  for (auto& kv : sv->reqs) release(kv.second);
   delete sv;
 }
 

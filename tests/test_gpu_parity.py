@@ -367,3 +367,13 @@ def test_graph_loop_maxit_and_nonfinite(amge):
     assert st == amge.AMGE_ENONFINITE
     st, info = amge.amge_pcg_solve(h, b, x)        # the hierarchy stays usable
     assert st == amge.AMGE_OK and info[0]["true_relres"] <= 1e-8
+
+
+def test_autotune_report(amge):
+    """Every smoothing-level operator has a kernel choice: 0 (sliced ELL) or a
+    power-of-two lane count; the parity tests above run with whatever was chosen."""
+    h = upload(amge, "hcurl", 24, 3)
+    rep = amge.amge_autotune_report(h)
+    assert len(rep) == 2 * 2 * 6
+    assert set(rep.values()) <= {-1, 0, 2, 4, 8, 16, 32}
+    assert rep[(0, "fp64", "AG")] >= 0          # H(curl): A G is stored (much sparser than A)
