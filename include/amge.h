@@ -158,7 +158,11 @@ amge_status amge_pcg_solve_host(amge_hier* h, const double* b_host, double* x_ho
  *   op AMGE_OP_A:  y = A_l x          AMGE_OP_P:  y = P_l x     AMGE_OP_PT: y = P_l^T x
  *      AMGE_OP_G:  y = G_l x          AMGE_OP_GT: y = G_l^T x
  *      AMGE_OP_SMOOTH_PRE:  y = one hybrid step (eq. 4.1) from x0 = 0 on b = x
- *      AMGE_OP_COARSE:      y = A_L^{-1} x on the coarsest level (level ignored) */
+ *      AMGE_OP_COARSE:      y = A_L^{-1} x on the coarsest level (level ignored)
+ *      AMGE_OP_AG: y = (A_l G_l) x, where that product is stored (see
+ *                  amge_autotune_report; AMGE_EINVAL elsewhere)
+ * Products run the kernel chosen for the operator (amge_autotune_report,
+ * amge_set_kernel). */
 enum {
   AMGE_OP_A = 0,
   AMGE_OP_P = 1,
@@ -166,7 +170,8 @@ enum {
   AMGE_OP_G = 3,
   AMGE_OP_GT = 4,
   AMGE_OP_SMOOTH_PRE = 5,
-  AMGE_OP_COARSE = 6
+  AMGE_OP_COARSE = 6,
+  AMGE_OP_AG = 7
 };
 amge_status amge_apply(amge_hier* h, int32_t op, int32_t level, const double* x_dev, double* y_dev,
                        int32_t precision, void* stream);
@@ -284,13 +289,23 @@ amge_status amge_set_graphs(amge_hier* h, int32_t enable);
 
 /* The autotuner's kernel choice for every smoothing level's single-vector products:
  * lanes[(l * 2 + p) * 6 + op] for level l < levels-1, precision p (0 FP64, 1 FP32),
- * op 0..5 = A, P, P^T, G, G^T, AG; 0 = sliced ELL (one row per lane), 2..32 = vector
- * CSR with that many lanes per row, -1 = operator not used (AG is stored only where
+ * op 0..5 = A, P, P^T, G, G^T, AG; 0 = sliced ELL (one row per lane, one warp per
+ * 32-row slice), 100 w (200, 400, 800) = sliced ELL with w warps sharing each slice,
+ * 2..32 = vector CSR with that many lanes per row, -1 = operator not used (AG is stored only where
  * A G = A_l G_l is much sparser than A_l, i.e. for H(curl): there the residual after
  * an aux sweep is updated as r - (A G) y instead of recomputed as b - A x).  The
  * choice is made at upload by timing each candidate on the level's own operator.
  * lanes must hold (levels-1)*12 entries. */
 amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
+
+/* Override one entry of that choice (level l < levels-1, precision 0/1, op 0..5 as
+ * above; lanes = a kernel code as above: 0, 200, 400, 800 or 2, 4, 8, 16, 32).  Captured PCG graphs
+ * of h are rebuilt on the next solve.  Every kernel computes the same products (in a
+ * different summation order), so a choice changes rounding, not results beyond it;
+ * pinning the choices makes results reproducible across uploads.  Not to be called
+ * while a call on h is in flight.  AMGE_EINVAL for an index out of range, an
+ * operator that is not stored (-1 in the report) or another lane count. */
+amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int32_t op, int32_t lanes);
 
 /* Release the hierarchy and all device memory it holds (NULL is ignored). */
 void amge_hier_free(amge_hier* h);

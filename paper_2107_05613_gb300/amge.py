@@ -23,7 +23,7 @@ AMGE_OK, AMGE_EINVAL, AMGE_ENOMEM, AMGE_ECUDA, AMGE_ENOTCONV, AMGE_ENONFINITE = 
 AMGE_EAGAIN, AMGE_ETIMEOUT, AMGE_ECANCELED = 6, 7, 8
 AMGE_HCURL, AMGE_HDIV = 1, 2
 AMGE_FP64, AMGE_FP32_VCYCLE = 0, 1
-AMGE_OP_A, AMGE_OP_P, AMGE_OP_PT, AMGE_OP_G, AMGE_OP_GT, AMGE_OP_SMOOTH_PRE, AMGE_OP_COARSE = range(7)
+AMGE_OP_A, AMGE_OP_P, AMGE_OP_PT, AMGE_OP_G, AMGE_OP_GT, AMGE_OP_SMOOTH_PRE, AMGE_OP_COARSE, AMGE_OP_AG = range(8)
 PROF_CLASSES = ["A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "pcg_spmv", "pcg_vec", "vcycle_vec", "AG"]
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENONFINITE",
                 6: "EAGAIN", 7: "ETIMEOUT", 8: "ECANCELED"}
@@ -62,6 +62,7 @@ _SIGS = {
     "amge_profile_enable": [_vp, _i32],
     "amge_set_graphs": [_vp, _i32],
     "amge_autotune_report": [_vp, ctypes.POINTER(_i32)],
+    "amge_set_kernel": [_vp, _i32, _i32, _i32, _i32],
     "amge_server_create": [ctypes.c_size_t, _i32, ctypes.POINTER(_vp)],
     "amge_submit": [_vp, _vp, _vp, _vp, _i32, ctypes.POINTER(amge_solve_opts), ctypes.POINTER(ctypes.c_uint64)],
     "amge_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(amge_info)],
@@ -219,14 +220,26 @@ def amge_coarse_solve_noalloc(h: Hier, b, z, stream=None):
 
 
 def amge_autotune_report(h: Hier):
-    """{(level, 'fp64'|'fp32', op): lanes} -- 0 = sliced ELL, k = vector CSR with k lanes/row,
-    -1 = operator not stored."""
+    """{(level, 'fp64'|'fp32', op): code} -- 0 = sliced ELL, 100 w = sliced ELL with w warps
+    per slice, k <= 32 = vector CSR with k lanes/row, -1 = operator not stored."""
     L = h.levels
     buf = (_i32 * max((L - 1) * 12, 1))()
     _check(_lib.amge_autotune_report(h.handle, buf), "amge_autotune_report")
     ops = ["A", "P", "PT", "G", "GT", "AG"]
     return {(l, p, ops[o]): int(buf[(l * 2 + pi) * 6 + o]) for l in range(L - 1)
             for pi, p in enumerate(("fp64", "fp32")) for o in range(6)}
+
+
+OPS = ["A", "P", "PT", "G", "GT", "AG"]
+
+
+def amge_set_kernel(h: Hier, level: int, precision, op, lanes: int):
+    """Pin the kernel of one operator: lanes 0 = sliced ELL, 200/400/800 = sliced ELL
+    with 2/4/8 warps per slice, 2..32 = vector CSR with that many lanes per row.
+    precision: 0/1 or 'fp64'/'fp32'; op: index or name from OPS."""
+    p = {"fp64": 0, "fp32": 1}.get(precision, precision)
+    o = OPS.index(op) if isinstance(op, str) else op
+    _check(_lib.amge_set_kernel(h.handle, level, int(p), int(o), lanes), "amge_set_kernel")
 
 
 def amge_set_graphs(h: Hier, enable: bool = True):

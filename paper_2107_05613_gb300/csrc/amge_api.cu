@@ -25,8 +25,12 @@ struct LevelDev {
   DevSell<V> AG;
   DevCsr<V> cAG;
   bool use_ag = false;
+  // G sign-coded with two entries per row in row order (the discrete gradient), for
+  // the fused aux correction (launch_ag_fused); null where G has another shape
+  int2* g2 = nullptr;
   // autotuned single-vector kernel per operator (A, P, PT, G, GT, AG): 0 = sliced
-  // ELL, 2..32 = vector CSR with that many lanes per row, -1 = not stored
+  // ELL, 100 w = sliced ELL with w warps per slice, 2..32 = vector CSR with that many
+  // lanes per row, -1 = not stored
   int lanes[6] = {0, 0, 0, 0, 0, -1};
   V* minv = nullptr;
   V* mauxinv = nullptr;
@@ -142,17 +146,23 @@ constexpr int kSellSigma = 1024;
 
 // Upload an operator in the sliced-ELL layout once (indices shared by both precisions).
 void upload_sell(amge_hier* h, const HostCsr& M, DevSell<double>& d64, DevSell<float>& d32, cudaStream_t s,
-                 std::vector<std::vector<float>>& keep, std::vector<HostSell>& keeps) {
-  keeps.push_back(build_sell(M, kSellSigma));
+                 std::vector<std::vector<float>>& keep, std::vector<HostSell>& keeps, bool allow_unit = false) {
+  keeps.push_back(build_sell(M, kSellSigma, allow_unit));
   const HostSell& S = keeps.back();
   d64.nr = d32.nr = S.nr;
   d64.nc = d32.nc = S.nc;
   d64.nslices = d32.nslices = S.nslices;
   d64.nnz = d32.nnz = S.nnz;
+  d64.unit = d32.unit = S.unit ? 1 : 0;
   d64.stored = d32.stored = S.sptr[S.nslices];
   d64.sptr = d32.sptr = upload<int64_t>(h, S.sptr.data(), S.sptr.size(), s);
   d64.srow = d32.srow = upload<int>(h, S.srow.data(), S.srow.size(), s);
   d64.ci = d32.ci = upload<int>(h, S.ci.data(), S.ci.size(), s);
+  if (S.unit) {  // sign-coded: the columns carry the +-1 entries
+    d64.val = nullptr;
+    d32.val = nullptr;
+    return;
+  }
   d64.val = upload<double>(h, S.v.data(), S.v.size(), s);
   keep.emplace_back(S.v.begin(), S.v.end());
   d32.val = upload<float>(h, keep.back().data(), keep.back().size(), s);
@@ -259,9 +269,9 @@ const DevCsr<V>& op_csr(const LevelDev<V>& d, int op) {
 template <typename V>
 void opk(amge_hier* h, int cls, const LevelDev<V>& d, int op, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
   Prof p(h, cls, s);
-  const int lanes = d.lanes[op];
-  if (lanes == 0) launch_sell<V>(op_sell(d, op), epi, a, s);
-  else launch_csrv<V>(op_csr(d, op), lanes, epi, a, s);
+  const int code = d.lanes[op];  // 0 / 100 w: sliced ELL (w warps per slice); 2..32: vector CSR lanes
+  if (code == 0 || code >= 100) launch_sell<V>(op_sell(d, op), epi, a, s, code >= 100 ? code / 100 : 1);
+  else launch_csrv<V>(op_csr(d, op), code, epi, a, s);
 }
 
 // One V-cycle at level l: z = B_l^{-1} b (Algorithm 4.1, x0 = 0).
@@ -277,10 +287,13 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
   const int clsA = l == 0 ? AMGE_PROF_A_FINE : AMGE_PROF_A_COARSE;
   V* x = d.x;
   V* xt = d.tmp;
-  auto aux_sweep = [&]() {  // x += G M_aux^{-1} G^T r   (r = b - A x already formed)
+  auto aux_gt = [&]() {  // y = M_aux^{-1} G^T r   (r = b - A x already formed)
     SpmvArgs<V> g;
     g.x = d.r, g.d = d.mauxinv, g.y = d.y;
     opk<V>(h, AMGE_PROF_GT, d, OP_GT, EPI_SCALE, g, s);
+  };
+  auto aux_sweep = [&]() {  // x += G M_aux^{-1} G^T r
+    aux_gt();
     SpmvArgs<V> c;
     c.x = d.y, c.y = x;
     opk<V>(h, AMGE_PROF_G, d, OP_G, EPI_ADD, c, s);
@@ -296,9 +309,18 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
       Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
       launch_mul<V>(d.n, d.minv, b, x, s);
     }
+    // G y and (A G) y in one pass where G is the two-entry gradient and both
+    // products run the one-warp sliced-ELL kernels (identical results)
+    const bool fused = d.g2 && d.lanes[OP_AG] == 0 && d.lanes[OP_G] == 0;
     residual();
-    aux_sweep();
-    {
+    if (fused) {
+      aux_gt();
+      Prof p(h, AMGE_PROF_AG, s);
+      AgArgs<V> f;  // x += G y; r -= (A G) y
+      f.y = d.y, f.g2 = d.g2, f.x = x, f.r = d.r;
+      launch_ag_fused<V>(d.AG, 0, f, s);
+    } else {
+      aux_sweep();
       SpmvArgs<V> a;  // r = r - (A G) y (in place: row i reads and writes r_i only)
       a.x = d.y, a.b = d.r, a.y = d.r;
       opk<V>(h, AMGE_PROF_AG, d, OP_AG, EPI_RESID, a, s);
@@ -315,6 +337,14 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
       opk<V>(h, AMGE_PROF_P, d, OP_P, EPI_ADD, a, s);
     }
     residual();
+    if (fused) {
+      aux_gt();
+      Prof p(h, AMGE_PROF_AG, s);
+      AgArgs<V> f;  // z = x + G y + M^{-1} (r - (A G) y)
+      f.y = d.y, f.g2 = d.g2, f.x = x, f.r = d.r, f.minv = d.minv, f.z = z;
+      launch_ag_fused<V>(d.AG, 1, f, s);
+      return;
+    }
     aux_sweep();
     SpmvArgs<V> a;  // z = x + M^{-1} (r - (A G) y)
     a.x = d.y, a.xin = x, a.d = d.minv, a.b = d.r, a.y = z;
@@ -414,7 +444,8 @@ amge_status build_pcg_graph(amge_hier* h, int prec) {
   h->prof = false;  // event records are not allowed inside conditional bodies
   CK(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   vcycle_fp64_iface(h, h->pr, h->pz, prec, h->cap);
-  launch_pcg_dots(n, h->pr, h->pz, h->pq, prec == AMGE_FP32_VCYCLE ? 1 : 0, h->red, h->cap);
+  const int flexible = prec == AMGE_FP32_VCYCLE ? 1 : 0;
+  launch_pcg_dots(n, h->pr, h->pz, h->pq, flexible, h->red, h->cap);
   launch_pcg_update_p(n, h->pp, h->pz, h->red, h->cap);
   launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, h->cap);
   launch_pcg_axpy_norm(n, h->gx, h->pr, h->pp, h->pq, h->red, h->cap);
@@ -701,7 +732,7 @@ amge_status ensure_mm(amge_hier* h, int nrhs, cudaStream_t s) {
     h->PQ = dalloc<double>(h, n0), h->SB = dalloc<double>(h, n0), h->SX = dalloc<double>(h, n0);
     h->S32in = dalloc<float>(h, n0), h->S32out = dalloc<float>(h, n0);
     h->CT = dalloc<double>(h, (size_t)h->nC * k);
-    h->redmm.partials = dalloc<double>(h, (size_t)kRedSlots * kMaxRedBlocks * kMaxRhs);
+    h->redmm.partials = dalloc<double>(h, (size_t)kRedSlots * kMaxRedBlocksMM * kMaxRhs);
     h->redmm.counters = dalloc<unsigned>(h, kRedSlots);
     h->redmm.sc = dalloc<double>(h, (size_t)SC_COUNT * kMaxRhs);
     h->redmm.active = dalloc<int>(h, kMaxRhs);
@@ -1012,12 +1043,13 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
     h->gx = dalloc<double>(h, n0);
     h->gstate = dalloc<int>(h, 4);
     h->red.partials = dalloc<double>(h, (size_t)kRedSlots * kMaxRedBlocks);
-    h->red.counters = dalloc<unsigned>(h, kRedSlots);
+    h->red.gpart = dalloc<double>(h, (size_t)kRedSlots * kRedGroups);
+    h->red.counters = dalloc<unsigned>(h, (size_t)kRedSlots * (kRedGroups + 1) * kCounterStride);
     h->red.sc = dalloc<double>(h, SC_COUNT);
   } catch (const UploadError& e) {
     return e.st;
   }
-  CK(cudaMemsetAsync(h->red.counters, 0, kRedSlots * sizeof(unsigned), s));
+  CK(cudaMemsetAsync(h->red.counters, 0, (size_t)kRedSlots * (kRedGroups + 1) * kCounterStride * sizeof(unsigned), s));
   CK(cudaMemsetAsync(h->red.sc, 0, SC_COUNT * sizeof(double), s));
   CK(cudaMallocHost(&h->pinned, 16 * sizeof(double)));
   CK(cudaMallocHost(&h->pinned_state, 4 * sizeof(int)));
@@ -1042,16 +1074,21 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
     const double avg = M.nr ? (double)M.nnz / M.nr : 0.0;
     float best = 0.f;
     int best_lanes = 0;
-    for (int lanes : {0, 2, 4, 8, 16, 32}) {
-      if (lanes > 2 && lanes > 2 * avg) break;
+    for (int lanes : {0, 200, 400, 800, 2, 4, 8, 16, 32}) {
+      if (lanes >= 100 && 2.0 * (lanes / 100) > avg + 1.0) continue;  // more warps than entry pairs
+      if (lanes > 2 && lanes < 100 && lanes > 2 * avg) continue;
       d.lanes[op] = lanes;
-      for (int w = 0; w < 2; w++) opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
-      CK(cudaEventRecord(e0, s));
-      for (int r = 0; r < 5; r++) opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
-      CK(cudaEventRecord(e1, s));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
+      for (int w = 0; w < 3; w++) opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
+      float ms = 1e30f;
+      for (int trial = 0; trial < 3; trial++) {  // best of three trials of 5 launches
+        CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < 5; r++) opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        ms = std::min(ms, t);
+      }
       if (lanes == 0 || ms < 0.9f * best) best = (lanes == 0 || ms < best) ? ms : best, best_lanes = lanes;
     }
     d.lanes[op] = best_lanes;
@@ -1096,6 +1133,10 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
     set_error("coarsest level larger than 8192 dofs (dense factor)");
     return AMGE_EINVAL;
   }
+  if ((int64_t)n[0] > (int64_t)kMaxRedBlocks * 16 * 32) {  // one p.q partial per 16 slices of 32 rows
+    set_error("finest level larger than 8,388,608 dofs");
+    return AMGE_EINVAL;
+  }
   h->form = desc->form;
   h->L = L;
   h->nu_pre = desc->nu_pre;
@@ -1105,6 +1146,7 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
   h->lv32.resize(L);
   std::vector<std::vector<float>> keep;
   std::vector<std::vector<double>> keepd;
+  std::vector<std::vector<int>> keepi;
   std::vector<HostSell> keeps;
   try {
     for (int l = 0; l < L; l++) {
@@ -1136,8 +1178,8 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
         upload_sell(h, A, d64.A, d32.A, s, keep, keeps);
         upload_sell(h, P, d64.P, d32.P, s, keep, keeps);
         upload_sell(h, PT, d64.PT, d32.PT, s, keep, keeps);
-        upload_sell(h, G, d64.G, d32.G, s, keep, keeps);
-        upload_sell(h, GT, d64.GT, d32.GT, s, keep, keeps);
+        upload_sell(h, G, d64.G, d32.G, s, keep, keeps, true);
+        upload_sell(h, GT, d64.GT, d32.GT, s, keep, keeps, true);
         upload_csr(h, A, d64.cA, d32.cA, s, keep);
         upload_csr(h, P, d64.cP, d32.cP, s, keep);
         upload_csr(h, PT, d64.cPT, d32.cPT, s, keep);
@@ -1150,6 +1192,15 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
             upload_csr(h, AG, d64.cAG, d32.cAG, s, keep);
             d64.use_ag = d32.use_ag = true;
             d64.lanes[OP_AG] = d32.lanes[OP_AG] = 0;
+            bool two = G.nnz() == 2 * (int64_t)G.nr;
+            for (int i = 0; two && i < G.nr; i++)
+              two = G.rp[i + 1] - G.rp[i] == 2 && std::fabs(G.v[G.rp[i]]) == 1.0 && std::fabs(G.v[G.rp[i] + 1]) == 1.0;
+            if (two) {
+              keepi.emplace_back(2 * (size_t)G.nr);
+              std::vector<int>& g2 = keepi.back();
+              for (size_t k = 0; k < g2.size(); k++) g2[k] = G.v[k] > 0 ? G.ci[k] : ~G.ci[k];
+              d64.g2 = d32.g2 = reinterpret_cast<int2*>(upload<int>(h, g2.data(), g2.size(), s));
+            }
           }
         }
         if (l == 0) h->cA0 = d64.cA;
@@ -1506,22 +1557,28 @@ amge_status amge_apply(amge_hier* h, int32_t op, int32_t level, const double* x_
     set_error("level must index a smoothing level (0 .. levels-2)");
     return AMGE_EINVAL;
   }
-  if (op < AMGE_OP_A || op > AMGE_OP_SMOOTH_PRE) {
+  if ((op < AMGE_OP_A || op > AMGE_OP_SMOOTH_PRE) && op != AMGE_OP_AG) {
     set_error("unknown op");
+    return AMGE_EINVAL;
+  }
+  if (op == AMGE_OP_AG && !h->lv64[level].use_ag) {
+    set_error("A G is not stored on this level");
     return AMGE_EINVAL;
   }
   auto run = [&](auto tag) -> amge_status {
     using V = decltype(tag);
     LevelDev<V>& d = levels<V>(h)[level];
-    const DevSell<V>* M = nullptr;
+    const int clsA = level == 0 ? AMGE_PROF_A_FINE : AMGE_PROF_A_COARSE;
+    int opid = OP_A, cls = clsA;
     switch (op) {
-      case AMGE_OP_A: M = &d.A; break;
-      case AMGE_OP_P: M = &d.P; break;
-      case AMGE_OP_PT: M = &d.PT; break;
-      case AMGE_OP_G: M = &d.G; break;
-      case AMGE_OP_GT: M = &d.GT; break;
-      default: M = &d.A; break;
+      case AMGE_OP_P: opid = OP_P, cls = AMGE_PROF_P; break;
+      case AMGE_OP_PT: opid = OP_PT, cls = AMGE_PROF_PT; break;
+      case AMGE_OP_G: opid = OP_G, cls = AMGE_PROF_G; break;
+      case AMGE_OP_GT: opid = OP_GT, cls = AMGE_PROF_GT; break;
+      case AMGE_OP_AG: opid = OP_AG, cls = AMGE_PROF_AG; break;
+      default: break;
     }
+    const DevSell<V>* M = &op_sell(d, opid);
     const V* xin;
     V* yout;
     const int nin = (op == AMGE_OP_SMOOTH_PRE) ? d.n : M->nc;
@@ -1538,17 +1595,17 @@ amge_status amge_apply(amge_hier* h, int32_t op, int32_t level, const double* x_
       launch_mul<V>(d.n, d.minv, xin, yout, s);
       SpmvArgs<V> a;
       a.x = yout, a.b = xin, a.y = d.r;
-      launch_sell<V>(d.A, EPI_RESID, a, s);
+      opk<V>(h, clsA, d, OP_A, EPI_RESID, a, s);
       SpmvArgs<V> g;
       g.x = d.r, g.d = d.mauxinv, g.y = d.y;
-      launch_sell<V>(d.GT, EPI_SCALE, g, s);
+      opk<V>(h, AMGE_PROF_GT, d, OP_GT, EPI_SCALE, g, s);
       SpmvArgs<V> c;
       c.x = d.y, c.y = yout;
-      launch_sell<V>(d.G, EPI_ADD, c, s);
+      opk<V>(h, AMGE_PROF_G, d, OP_G, EPI_ADD, c, s);
     } else {
       SpmvArgs<V> a;
       a.x = xin, a.y = yout;
-      launch_sell<V>(*M, EPI_STORE, a, s);
+      opk<V>(h, cls, d, opid, EPI_STORE, a, s);
     }
     if constexpr (!std::is_same<V, double>::value) launch_cast<float, double>(nout, h->s32_out, y_dev, s);
     return launch_status();
@@ -1576,6 +1633,34 @@ amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes) {
       lanes[(l * 2 + 0) * 6 + op] = h->lv64[l].lanes[op];
       lanes[(l * 2 + 1) * 6 + op] = h->lv32[l].lanes[op];
     }
+  return AMGE_OK;
+}
+
+amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int32_t op, int32_t lanes) {
+  if (!h) {
+    set_error("NULL hierarchy");
+    return AMGE_EINVAL;
+  }
+  if (level < 0 || level + 1 >= h->L || (precision != 0 && precision != 1) || op < 0 || op >= 6) {
+    set_error("level, precision or operator out of range");
+    return AMGE_EINVAL;
+  }
+  if (lanes != 0 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32 && lanes != 200 &&
+      lanes != 400 && lanes != 800) {
+    set_error("kernel code must be 0, 200, 400, 800 (sliced ELL) or 2, 4, 8, 16, 32 (vector CSR)");
+    return AMGE_EINVAL;
+  }
+  int& cur = precision == 0 ? h->lv64[level].lanes[op] : h->lv32[level].lanes[op];
+  if (cur < 0) {
+    set_error("operator not stored on this level");
+    return AMGE_EINVAL;
+  }
+  cur = lanes;
+  for (GraphPcg& G : h->gpcg) {  // the captured launches name the old kernels
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.g) cudaGraphDestroy(G.g);
+    G = GraphPcg{};
+  }
   return AMGE_OK;
 }
 

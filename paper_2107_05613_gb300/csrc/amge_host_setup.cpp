@@ -195,10 +195,12 @@ bool coarse_factor(const HostCsr& Ac, std::vector<double>& Linv, std::vector<dou
   return true;
 }
 
-HostSell build_sell(const HostCsr& M, int sigma) {
+HostSell build_sell(const HostCsr& M, int sigma, bool allow_unit) {
   constexpr int C = 32;
   HostSell S;
   S.nr = M.nr, S.nc = M.nc, S.nnz = M.nnz();
+  S.unit = allow_unit && M.nnz() > 0 &&
+           std::all_of(M.v.begin(), M.v.end(), [](double v) { return v == 1.0 || v == -1.0; });
   S.nslices = (M.nr + C - 1) / C;
   std::vector<int> perm(M.nr);
   for (int i = 0; i < M.nr; i++) perm[i] = i;
@@ -220,7 +222,7 @@ HostSell build_sell(const HostCsr& M, int sigma) {
     S.sptr[s + 1] = S.sptr[s] + (int64_t)w * C;
   }
   S.ci.assign(S.sptr[S.nslices], 0);
-  S.v.assign(S.sptr[S.nslices], 0.0);
+  if (!S.unit) S.v.assign(S.sptr[S.nslices], 0.0);
   for (int s = 0; s < S.nslices; s++) {
     const int w = (int)((S.sptr[s + 1] - S.sptr[s]) / C);
     for (int j = 0; j < C; j++) {
@@ -228,7 +230,9 @@ HostSell build_sell(const HostCsr& M, int sigma) {
       const int l = r >= 0 ? len(r) : 0;
       for (int k = 0; k < w; k++) {
         const int64_t at = S.sptr[s] + (int64_t)(k / 2) * 2 * C + 2 * j + (k & 1);
-        if (k < l) {
+        if (S.unit) {
+          S.ci[at] = k < l ? (M.v[M.rp[r] + k] > 0 ? M.ci[M.rp[r] + k] : ~M.ci[M.rp[r] + k]) : kSellPad;
+        } else if (k < l) {
           S.ci[at] = M.ci[M.rp[r] + k];
           S.v[at] = M.v[M.rp[r] + k];
         } else {

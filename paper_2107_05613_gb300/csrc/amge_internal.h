@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -28,19 +29,28 @@ struct HostCsr {
 // reads 32 consecutive 16-byte pairs per step.  srow maps (slice, lane) to the
 // original row (-1 for lanes past the last row).  Padding entries have value 0 and
 // a valid column of their row.
+// Sign-coded ("unit") slices: an operator whose entries are all +1 or -1 (the
+// integer incidences D and C of the de Rham sequence) stores no values.  Column
+// index c >= 0 stands for +1 at column c, c < 0 for -1 at column ~c, and kSellPad
+// marks a padding entry (contributes zero).
+constexpr int kSellPad = INT32_MIN;
+
 struct HostSell {
   int nr = 0, nc = 0, nslices = 0;
   int64_t nnz = 0;                // stored entries of the CSR source
+  bool unit = false;              // sign-coded columns, no values
   std::vector<int64_t> sptr;      // [nslices + 1], element offsets (multiples of 64)
   std::vector<int> srow;          // [nslices * 32]
   std::vector<int> ci;            // [sptr[nslices]]
-  std::vector<double> v;          // [sptr[nslices]]
+  std::vector<double> v;          // [sptr[nslices]] (empty when unit)
 };
-HostSell build_sell(const HostCsr& M, int sigma);
+// Sliced ELL of M; with allow_unit, an operator whose entries are all +-1 is sign-coded.
+HostSell build_sell(const HostCsr& M, int sigma, bool allow_unit = false);
 
 template <typename V>
 struct DevSell {
   int nr = 0, nc = 0, nslices = 0;
+  int unit = 0;  // sign-coded columns (val == nullptr)
   int64_t nnz = 0, stored = 0;
   int64_t* sptr = nullptr;
   int* srow = nullptr;
@@ -66,11 +76,30 @@ struct SpmvArgs {
   V* y = nullptr;
 };
 
+// wps = warps per 32-row slice (1, 2, 4, 8).
 template <typename V>
-void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, int wps = 1);
 
 // CSR copy of an operator for the multi-right-hand-side products (row pointers and
 // columns shared by both precisions).
+// Fused correction of the hybrid smoother's aux sweep where G has two +-1 entries per
+// row (the discrete gradient of every level) and A G is stored:
+//   pre  (post = 0): x_i += (G y)_i and r_i -= ((A G) y)_i
+//   post (post = 1): z_i = x_i + (G y)_i + m_i^-1 (r_i - ((A G) y)_i)
+// g2[i] holds row i of G sign-coded (see kSellPad); the sums are formed in the same
+// order as the separate G and A G products, so the results are identical.
+template <typename V>
+struct AgArgs {
+  const V* y = nullptr;    // aux vector
+  const int2* g2 = nullptr;
+  V* x = nullptr;          // iterate (read; written in the pre form)
+  V* r = nullptr;          // residual (read; written in the pre form)
+  const V* minv = nullptr; // post form
+  V* z = nullptr;          // post form output
+};
+template <typename V>
+void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s);
+
 template <typename V>
 struct DevCsr {
   int nr = 0, nc = 0;
@@ -132,19 +161,32 @@ enum Scalar : int {
   SC_TOL2 = 9,     // rtol^2 ||b||^2 (graph-driven loop)
   SC_COUNT = 16
 };
-constexpr int kRedSlots = 4;
-constexpr int kMaxRedBlocks = 8192;   // capacity of the block-partial arrays
-constexpr int kVecRedBlocks = 1024;   // grid cap of the vector reductions
+constexpr int kRedSlots = 5;
+// Partial slots of the single-vector reductions (rz and zq share one two-value slot).
+enum : int { kSlotPQ = 0, kSlotRR = 1, kSlotRZ = 2, kSlotZQ = 3, kSlotDot = 4 };
+constexpr int kMaxRedBlocks = 16384;  // capacity of the block-partial arrays (single vector)
+constexpr int kMaxRedBlocksMM = 1024;  // block-partial capacity per column (blocks of vectors)
+constexpr int kVecRedBlocks = 4096;   // grid cap of the vector reductions (one resident wave is used)
+
+// Grid reductions finish in a two-level arrival tree: block b signals counter
+// b % kRedGroups (each counter on its own 128-byte line); the last block of a group
+// sums the group's partials, the last group sums the group totals.  No address sees
+// more than ~gridDim / kRedGroups arrivals: on GB300 arrivals at one address from all
+// SMs serialise at several ns each.
+constexpr int kRedGroups = 64;
+constexpr int kCounterStride = 32;  // unsigned words between counters (128 bytes)
 
 struct RedScratch {
   double* partials = nullptr;  // [kRedSlots][kMaxRedBlocks]
-  unsigned* counters = nullptr;  // [kRedSlots]
+  double* gpart = nullptr;     // [kRedSlots][kRedGroups] group totals
+  unsigned* counters = nullptr;  // [kRedSlots][kRedGroups + 1][kCounterStride]
   double* sc = nullptr;        // [SC_COUNT]
 };
 
 int red_blocks(int64_t n);
 void launch_dot(int64_t n, const double* x, const double* y, double* out, const RedScratch& r, cudaStream_t s);
-// q = A p (sliced ELL, FP64) and pq = p.q; the finishing block sets alpha = rho / pq.
+// PCG kernels (scalars in RedScratch::sc, reductions finished by the tree above).
+// q = A p and pq = p.q; the finishing block sets alpha = rho / pq.
 void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, const RedScratch& r,
                          cudaStream_t s);
 // x += alpha p; r -= alpha q; ||r||^2 -> SC_RR
@@ -163,7 +205,7 @@ void launch_pcg_loop_cond(cudaGraphConditionalHandle hw, const RedScratch& r, in
 // Multi-RHS PCG: per-column scalars live in sc_mm[scalar][column]; `active[c]` masks
 // columns that have converged (their alpha and beta are forced to 0).
 struct RedScratchMM {
-  double* partials = nullptr;  // [kRedSlots][kMaxRedBlocks][kMaxRhs]
+  double* partials = nullptr;  // [kRedSlots][kMaxRedBlocksMM][kMaxRhs]
   unsigned* counters = nullptr;  // [kRedSlots]
   double* sc = nullptr;        // [SC_COUNT][kMaxRhs]
   int* active = nullptr;       // [kMaxRhs]

@@ -16,6 +16,7 @@
 // only) writes block partials, and the last block to arrive sums them in index
 // order with a fixed tree.
 #include <algorithm>
+#include <atomic>
 
 #include "amge_internal.h"
 
@@ -41,35 +42,138 @@ struct Pair<float> {
   using T = float2;
 };
 
-// One sliced-ELL slice per warp, one row per lane.
+// One sliced-ELL slice per warp, one row per lane.  Each row is one FMA chain that
+// starts from the epilogue's vector (b for r = b - A x and the sweep, y for y += A x)
+// with the stored values negated where the product is subtracted, so a row of w
+// stored entries costs exactly w FP64 FMAs (plus one for SCALE and SWEEP): on GB300
+// the FP64 pipe, not only HBM, bounds these kernels.
 template <typename V, int EPI>
+__device__ __forceinline__ V sell_init(const SpmvArgs<V>& a, int row) {
+  if (row < 0) return V(0);
+  if (EPI == EPI_RESID || EPI == EPI_SWEEP) return a.b[row];
+  if (EPI == EPI_ADD) return a.y[row];
+  return V(0);
+}
+template <int EPI>
+struct SellNeg {
+  static constexpr bool value = (EPI == EPI_RESID || EPI == EPI_SWEEP);
+};
+template <typename V, int EPI>
+__device__ __forceinline__ void sell_store(const SpmvArgs<V>& a, int row, V s) {
+  switch (EPI) {
+    case EPI_SCALE: a.y[row] = a.d[row] * s; break;
+    case EPI_SWEEP: a.y[row] = fma(a.d[row], s, a.xin[row]); break;
+    default: a.y[row] = s; break;  // STORE, RESID (s = b - A x), ADD (s = y + A x)
+  }
+}
+
+// Sign-coded slices (operators with entries +-1 only): one column index per entry and
+// no values.  The entry's sign (flipped once more where the product is subtracted)
+// is applied to the gathered value's bit pattern and padding becomes +0, so each
+// entry costs one FP64 add, as the FMA with +-1 does for a stored value.
+template <bool NEG>
+__device__ __forceinline__ double signed_entry(const double* x, int c) {
+  const bool pad = (c == kSellPad);
+  const double v = __ldg(x + (pad ? 0 : (c ^ (c >> 31))));
+  const unsigned sign = ((unsigned)c & 0x80000000u) ^ (NEG ? 0x80000000u : 0u);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v) ^ ((unsigned long long)sign << 32);
+  return pad ? 0.0 : __longlong_as_double((long long)b);
+}
+template <bool NEG>
+__device__ __forceinline__ float signed_entry(const float* x, int c) {
+  const bool pad = (c == kSellPad);
+  const float v = __ldg(x + (pad ? 0 : (c ^ (c >> 31))));
+  const unsigned sign = ((unsigned)c & 0x80000000u) ^ (NEG ? 0x80000000u : 0u);
+  return pad ? 0.f : __int_as_float(__float_as_int(v) ^ (int)sign);
+}
+
+// WPS warps per slice (1, 2, 4 or 8): warp g of a slice's group takes the entry
+// pairs k = g, g + WPS, ...; the group's partial row sums meet in shared memory and
+// the first warp adds them in warp order and writes the row.  More warps per slice
+// expose more loads in flight for operators with long rows and few slices (the
+// restriction P^T, coarse-level operators); WPS = 1 needs no shared memory.
+template <typename V, int EPI, int WPS, bool UNIT>
 __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __restrict__ sptr,
                                                  const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                  const typename Pair<V>::T* __restrict__ val2, SpmvArgs<V> a) {
+  constexpr bool NEG = SellNeg<EPI>::value;
+  const int wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int g = wib % WPS;
+  const int slice = (blockIdx.x * (kBlock / 32) + wib) / WPS;
+  V s = V(0);
+  int row = -1;
+  if (slice < nslices) {
+    const int64_t p0 = ldg(sptr + slice) >> 1;
+    const int np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+    row = ldg(srow + (size_t)slice * 32 + lane);
+    if (g == 0) s = sell_init<V, EPI>(a, row);
+    const int2* cp = ci2 + p0 + lane;
+    if (UNIT) {
+#pragma unroll 2
+      for (int k = g; k < np; k += WPS) {
+        const int2 c = __ldg(cp + (size_t)k * 32);
+        const V e0 = signed_entry<NEG>(a.x, c.x);
+        const V e1 = signed_entry<NEG>(a.x, c.y);
+        s += e0;
+        s += e1;
+      }
+    } else {
+      const typename Pair<V>::T* vp = val2 + p0 + lane;
+#pragma unroll 2
+      for (int k = g; k < np; k += WPS) {
+        const int2 c = __ldg(cp + (size_t)k * 32);
+        const typename Pair<V>::T v = __ldg(vp + (size_t)k * 32);
+        const V x0 = ldg(a.x + c.x), x1 = ldg(a.x + c.y);
+        s = fma(NEG ? -v.x : v.x, x0, s);
+        s = fma(NEG ? -v.y : v.y, x1, s);
+      }
+    }
+  }
+  if (WPS > 1) {
+    __shared__ V part[kBlock];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (g != 0) return;
+#pragma unroll
+    for (int j = 1; j < WPS; j++) s += part[threadIdx.x + 32 * j];
+  }
+  if (slice >= nslices || row < 0) return;
+  sell_store<V, EPI>(a, row, s);
+}
+
+// G y (two sign-coded entries) and A G y for one row per lane (see AgArgs).
+template <typename V, bool POST>
+__global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t* __restrict__ sptr,
+                                                     const int* __restrict__ srow, const int2* __restrict__ ci2,
+                                                     const typename Pair<V>::T* __restrict__ val2, AgArgs<V> a) {
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= nslices) return;
   const int64_t p0 = ldg(sptr + warp) >> 1;
   const int np = (int)((ldg(sptr + warp + 1) >> 1) - p0) >> 5;
   const int row = ldg(srow + (size_t)warp * 32 + lane);
+  if (row < 0) return;
+  const int2 g = ldg(a.g2 + row);
+  V gx = a.x[row];
+  gx += signed_entry<false>(a.y, g.x);
+  gx += signed_entry<false>(a.y, g.y);
+  V s = a.r[row];
   const int2* cp = ci2 + p0 + lane;
   const typename Pair<V>::T* vp = val2 + p0 + lane;
-  V s0 = V(0), s1 = V(0);
 #pragma unroll 2
   for (int k = 0; k < np; k++) {
     const int2 c = __ldg(cp + (size_t)k * 32);
     const typename Pair<V>::T v = __ldg(vp + (size_t)k * 32);
-    s0 = fma(v.x, ldg(a.x + c.x), s0);
-    s1 = fma(v.y, ldg(a.x + c.y), s1);
+    const V x0 = ldg(a.y + c.x), x1 = ldg(a.y + c.y);
+    s = fma(-v.x, x0, s);
+    s = fma(-v.y, x1, s);
   }
-  if (row < 0) return;
-  const V s = s0 + s1;
-  switch (EPI) {
-    case EPI_STORE: a.y[row] = s; break;
-    case EPI_RESID: a.y[row] = a.b[row] - s; break;
-    case EPI_SCALE: a.y[row] = a.d[row] * s; break;
-    case EPI_ADD: a.y[row] += s; break;
-    case EPI_SWEEP: a.y[row] = fma(a.d[row], a.b[row] - s, a.xin[row]); break;
+  if (POST) {
+    a.z[row] = fma(a.minv[row], s, gx);
+  } else {
+    a.x[row] = gx;
+    a.r[row] = s;
   }
 }
 
@@ -155,13 +259,19 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
-// Each block contributes `v[0..NV)`; the last block to arrive sums every block's
-// partials in index order and returns true (with the totals in `tot`, valid in all
-// threads of that block).
+// Each block contributes v[0..NV) to partial slots slot0 .. slot0+NV-1; the block
+// that completes the arrival tree returns true with the totals in tot (valid in
+// all its threads).  Group g holds blocks g, g + G, g + 2G, ... (G = min(kRedGroups,
+// gridDim.x)); sums run in index order with block_sum's fixed tree, so the totals do
+// not depend on which blocks arrive last.
 template <int NV>
 __device__ bool finish_blocks(const double* v, const RedScratch& r, int slot0, double* tot) {
   __shared__ double sh[32];
   __shared__ bool last;
+  __shared__ double res[NV];
+  const int G = min(kRedGroups, (int)gridDim.x);
+  const int grp = blockIdx.x % G;
+  unsigned* cnt = r.counters + (size_t)slot0 * (kRedGroups + 1) * kCounterStride;
   double bs[NV];
 #pragma unroll
   for (int k = 0; k < NV; k++) bs[k] = block_sum(v[k], sh);
@@ -169,78 +279,97 @@ __device__ bool finish_blocks(const double* v, const RedScratch& r, int slot0, d
 #pragma unroll
     for (int k = 0; k < NV; k++) r.partials[(slot0 + k) * kMaxRedBlocks + blockIdx.x] = bs[k];
     __threadfence();
-    const unsigned t = atomicAdd(&r.counters[slot0], 1u);
-    last = (t == gridDim.x - 1);
+    const unsigned members = (gridDim.x - grp + G - 1) / G;
+    last = (atomicAdd(cnt + grp * kCounterStride, 1u) == members - 1);
   }
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  __shared__ double res[NV];
+  // group total: members grp, grp + G, ... in index order
 #pragma unroll
   for (int k = 0; k < NV; k++) {
     double acc = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
-      acc += __ldcg(r.partials + (slot0 + k) * kMaxRedBlocks + i);
+    for (int b = grp + G * (int)threadIdx.x; b < (int)gridDim.x; b += G * (int)blockDim.x)
+      acc += __ldcg(r.partials + (slot0 + k) * kMaxRedBlocks + b);
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) res[k] = t;
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) r.gpart[(slot0 + k) * kRedGroups + grp] = res[k];
+    cnt[grp * kCounterStride] = 0u;
+    __threadfence();
+    last = (atomicAdd(cnt + kRedGroups * kCounterStride, 1u) == (unsigned)G - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    const double acc = threadIdx.x < G ? __ldcg(r.gpart + (slot0 + k) * kRedGroups + threadIdx.x) : 0.0;
     const double t = block_sum(acc, sh);
     if (threadIdx.x == 0) res[k] = t;
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NV; k++) tot[k] = res[k];
-  if (threadIdx.x == 0) r.counters[slot0] = 0u;
+  if (threadIdx.x == 0) cnt[kRedGroups * kCounterStride] = 0u;
   return true;
 }
 
-__global__ void __launch_bounds__(kBlock) k_dot(int64_t n, const double* __restrict__ x,
-                                                const double* __restrict__ y, double* out, RedScratch r) {
+__global__ void __launch_bounds__(kBlock, 8) k_dot(int64_t n, const double* __restrict__ x,
+                                                   const double* __restrict__ y, double* out, RedScratch r) {
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
     acc = fma(x[i], y[i], acc);
   double tot[1];
-  if (finish_blocks<1>(&acc, r, 0, tot) && threadIdx.x == 0) *out = tot[0];
+  if (finish_blocks<1>(&acc, r, kSlotDot, tot) && threadIdx.x == 0) *out = tot[0];
 }
 
-// q = A p with one row per lane over the slices of a grid-stride loop; each lane
-// accumulates its rows' p_i q_i and the block partials finish deterministically.
-__global__ void __launch_bounds__(kBlock) k_pcg_spmv_dot(int nslices, const int64_t* __restrict__ sptr,
-                                                         const int* __restrict__ srow,
-                                                         const int2* __restrict__ ci2,
-                                                         const double2* __restrict__ val2,
-                                                         const double* __restrict__ p, double* __restrict__ q,
-                                                         RedScratch r) {
-  double contrib = 0.0;
+// ------------------------------------------------------------ PCG kernels
+constexpr int kSpmvDotBlock = 512;  // 16 slices per block
+
+// q = A p, one sliced-ELL slice per warp, and pq = p.q; the finishing block sets
+// alpha = rho / pq.
+__global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, const int64_t* __restrict__ sptr,
+                                                                   const int* __restrict__ srow,
+                                                                   const int2* __restrict__ ci2,
+                                                                   const double2* __restrict__ val2,
+                                                                   const double* __restrict__ p,
+                                                                   double* __restrict__ q, RedScratch r) {
   const int lane = threadIdx.x & 31;
-  const int warps = gridDim.x * (kBlock / 32);
-  for (int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5; warp < nslices; warp += warps) {
-    const int64_t p0 = ldg(sptr + warp) >> 1;
-    const int np = (int)((ldg(sptr + warp + 1) >> 1) - p0) >> 5;
-    const int row = ldg(srow + (size_t)warp * 32 + lane);
+  const int slice = (blockIdx.x * kSpmvDotBlock + threadIdx.x) >> 5;
+  double contrib = 0.0;
+  if (slice < nslices) {
+    const int64_t p0 = ldg(sptr + slice) >> 1;
+    const int np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+    const int row = ldg(srow + (size_t)slice * 32 + lane);
     const int2* cp = ci2 + p0 + lane;
     const double2* vp = val2 + p0 + lane;
-    double s0 = 0.0, s1 = 0.0;
+    double acc = 0.0;
 #pragma unroll 2
     for (int k = 0; k < np; k++) {
       const int2 c = __ldg(cp + (size_t)k * 32);
       const double2 v = __ldg(vp + (size_t)k * 32);
-      s0 = fma(v.x, ldg(p + c.x), s0);
-      s1 = fma(v.y, ldg(p + c.y), s1);
+      const double x0 = ldg(p + c.x), x1 = ldg(p + c.y);
+      acc = fma(v.x, x0, acc);
+      acc = fma(v.y, x1, acc);
     }
     if (row >= 0) {
-      const double s = s0 + s1;
-      q[row] = s;
-      contrib = fma(ldg(p + row), s, contrib);
+      q[row] = acc;
+      contrib = ldg(p + row) * acc;
     }
   }
   double tot[1];
-  if (finish_blocks<1>(&contrib, r, 0, tot) && threadIdx.x == 0) {
+  if (finish_blocks<1>(&contrib, r, kSlotPQ, tot) && threadIdx.x == 0) {
     r.sc[SC_PQ] = tot[0];
     r.sc[SC_ALPHA] = r.sc[SC_RHO] / tot[0];
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_pcg_axpy_norm(int64_t n, double* __restrict__ x,
-                                                          double* __restrict__ rv, const double* __restrict__ p,
-                                                          const double* __restrict__ q, RedScratch r) {
+__global__ void __launch_bounds__(kBlock, 8) k_pcg_axpy_norm(int64_t n, double* __restrict__ x,
+                                                             double* __restrict__ rv, const double* __restrict__ p,
+                                                             const double* __restrict__ q, RedScratch r) {
   const double alpha = r.sc[SC_ALPHA];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
@@ -250,20 +379,25 @@ __global__ void __launch_bounds__(kBlock) k_pcg_axpy_norm(int64_t n, double* __r
     acc = fma(ri, ri, acc);
   }
   double tot[1];
-  if (finish_blocks<1>(&acc, r, 1, tot) && threadIdx.x == 0) r.sc[SC_RR] = tot[0];
+  if (finish_blocks<1>(&acc, r, kSlotRR, tot) && threadIdx.x == 0) r.sc[SC_RR] = tot[0];
 }
 
-__global__ void __launch_bounds__(kBlock) k_pcg_dots(int64_t n, const double* __restrict__ rv,
-                                                     const double* __restrict__ z, const double* __restrict__ q,
-                                                     int flexible, RedScratch r) {
+__global__ void __launch_bounds__(kBlock, 8) k_pcg_dots(int64_t n, const double* __restrict__ rv,
+                                                        const double* __restrict__ z, const double* __restrict__ q,
+                                                        int flexible, RedScratch r) {
   double acc[2] = {0.0, 0.0};
-  for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
-    const double zi = z[i];
-    acc[0] = fma(rv[i], zi, acc[0]);
-    acc[1] = fma(zi, q[i], acc[1]);
+  if (flexible) {
+    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
+      const double zi = z[i];
+      acc[0] = fma(rv[i], zi, acc[0]);
+      acc[1] = fma(zi, q[i], acc[1]);
+    }
+  } else {  // standard beta needs r.z only
+    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
+      acc[0] = fma(rv[i], z[i], acc[0]);
   }
   double tot[2];
-  if (finish_blocks<2>(acc, r, 2, tot) && threadIdx.x == 0) {
+  if (finish_blocks<2>(acc, r, kSlotRZ, tot) && threadIdx.x == 0) {
     const double rho = r.sc[SC_RHO];
     r.sc[SC_RHO_NEW] = tot[0];
     r.sc[SC_ZQ] = tot[1];
@@ -271,8 +405,8 @@ __global__ void __launch_bounds__(kBlock) k_pcg_dots(int64_t n, const double* __
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_pcg_update_p(int64_t n, double* __restrict__ p,
-                                                         const double* __restrict__ z, RedScratch r) {
+__global__ void __launch_bounds__(kBlock, 8) k_pcg_update_p(int64_t n, double* __restrict__ p,
+                                                            const double* __restrict__ z, RedScratch r) {
   const double beta = r.sc[SC_BETA];
   for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
     p[i] = fma(beta, p[i], z[i]);
@@ -288,31 +422,65 @@ __global__ void k_pcg_loop_cond(cudaGraphConditionalHandle hw, const double* __r
   cudaGraphSetConditional(hw, (fin && rr > sc[SC_TOL2] && it < state[1]) ? 1u : 0u);
 }
 
+// Blocks of kBlock threads that fill every SM of the current device once (2048
+// resident threads per SM; all the streaming kernels here use at most 32
+// registers).  Cached per device; the value is a property of the device only, so
+// grids built from it keep the reductions deterministic.
+int resident_blocks() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  int sms = 0, thr = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  if (cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess || thr <= 0) thr = 2048;
+  v = std::min(sms * std::max(thr / kBlock, 1), kVecRedBlocks);
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 int vec_grid(int64_t n) {
   int64_t g = (n + kBlock - 1) / kBlock;
-  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 152 * 16);
+  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), resident_blocks());
 }
 
 }  // namespace
 
 int red_blocks(int64_t n) {
   int64_t g = (n + 4 * kBlock - 1) / (4 * kBlock);
-  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), kVecRedBlocks);
+  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), resident_blocks());
 }
 
-template <typename V>
-void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
-  if (M.nslices == 0) return;
-  const int grid = (M.nslices + (kBlock / 32) - 1) / (kBlock / 32);
+template <typename V, int WPS, bool UNIT>
+static void launch_sell_t(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  const int per = (kBlock / 32) / WPS;  // slices per block
+  const int grid = (M.nslices + per - 1) / per;
   const int2* ci2 = reinterpret_cast<const int2*>(M.ci);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(M.val);
   switch (epi) {
-    case EPI_STORE: k_sell<V, EPI_STORE><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_RESID: k_sell<V, EPI_RESID><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_SCALE: k_sell<V, EPI_SCALE><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_ADD: k_sell<V, EPI_ADD><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_SWEEP: k_sell<V, EPI_SWEEP><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_STORE: k_sell<V, EPI_STORE, WPS, UNIT><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_RESID: k_sell<V, EPI_RESID, WPS, UNIT><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SCALE: k_sell<V, EPI_SCALE, WPS, UNIT><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_ADD: k_sell<V, EPI_ADD, WPS, UNIT><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SWEEP: k_sell<V, EPI_SWEEP, WPS, UNIT><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
   }
+}
+template <typename V, bool UNIT>
+static void launch_sell_u(const DevSell<V>& M, int wps, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  switch (wps) {
+    case 2: launch_sell_t<V, 2, UNIT>(M, epi, a, s); break;
+    case 4: launch_sell_t<V, 4, UNIT>(M, epi, a, s); break;
+    case 8: launch_sell_t<V, 8, UNIT>(M, epi, a, s); break;
+    default: launch_sell_t<V, 1, UNIT>(M, epi, a, s); break;
+  }
+}
+
+template <typename V>
+void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, int wps) {
+  if (M.nslices == 0) return;
+  if (M.unit) launch_sell_u<V, true>(M, wps, epi, a, s);
+  else launch_sell_u<V, false>(M, wps, epi, a, s);
 }
 template <typename V, int LANES>
 static void launch_csrv_lanes(const DevCsr<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
@@ -340,8 +508,20 @@ void launch_csrv(const DevCsr<V>& M, int lanes, int epi, const SpmvArgs<V>& a, c
 template void launch_csrv<double>(const DevCsr<double>&, int, int, const SpmvArgs<double>&, cudaStream_t);
 template void launch_csrv<float>(const DevCsr<float>&, int, int, const SpmvArgs<float>&, cudaStream_t);
 
-template void launch_sell<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t);
-template void launch_sell<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t);
+template <typename V>
+void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s) {
+  if (AG.nslices == 0) return;
+  const int grid = (AG.nslices + (kBlock / 32) - 1) / (kBlock / 32);
+  const int2* ci2 = reinterpret_cast<const int2*>(AG.ci);
+  const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(AG.val);
+  if (post) k_ag_fused<V, true><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+  else k_ag_fused<V, false><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+}
+template void launch_ag_fused<double>(const DevSell<double>&, int, const AgArgs<double>&, cudaStream_t);
+template void launch_ag_fused<float>(const DevSell<float>&, int, const AgArgs<float>&, cudaStream_t);
+
+template void launch_sell<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t, int);
+template void launch_sell<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t, int);
 
 template <typename V>
 void launch_mul(int64_t n, const V* d, const V* x, V* y, cudaStream_t s) {
@@ -375,10 +555,10 @@ void launch_dot(int64_t n, const double* x, const double* y, double* out, const 
 
 void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, const RedScratch& r,
                          cudaStream_t s) {
-  const int warps_per_block = kBlock / 32;  // one slice per warp, as in the plain sweep
-  const int grid = std::min((A.nslices + warps_per_block - 1) / warps_per_block, kMaxRedBlocks);
-  k_pcg_spmv_dot<<<std::max(grid, 1), kBlock, 0, s>>>(A.nslices, A.sptr, A.srow, reinterpret_cast<const int2*>(A.ci),
-                                                      reinterpret_cast<const double2*>(A.val), p, q, r);
+  const int per = kSpmvDotBlock / 32;
+  const int grid = std::max((A.nslices + per - 1) / per, 1);  // <= kMaxRedBlocks (checked at upload)
+  k_pcg_spmv_dot<<<grid, kSpmvDotBlock, 0, s>>>(A.nslices, A.sptr, A.srow, reinterpret_cast<const int2*>(A.ci),
+                                                reinterpret_cast<const double2*>(A.val), p, q, r);
 }
 
 void launch_pcg_axpy_norm(int64_t n, double* x, double* rv, const double* p, const double* q,

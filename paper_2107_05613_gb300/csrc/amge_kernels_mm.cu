@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kBlock) k_trimm(int n, int nrhs, const double*
 }
 
 // ---------------------------------------------------------------- per-column reductions
-constexpr size_t kColStride = (size_t)kMaxRedBlocks * kMaxRhs;
+constexpr size_t kColStride = (size_t)kMaxRedBlocksMM * kMaxRhs;
 
 // Each thread holds partials for column threadIdx.x % K.  Block sums per column (in
 // row-group order), then the last block to arrive sums the blocks in index order.
@@ -238,7 +238,7 @@ int pow2_at_least(int v) {
 int mm_red_blocks(int64_t n, int K) {
   const int64_t rows_per_block = kBlock / K;
   int64_t g = (n + 4 * rows_per_block - 1) / (4 * rows_per_block);
-  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), kVecRedBlocks);
+  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), kMaxRedBlocksMM);
 }
 
 int grid_for(int64_t tot) {

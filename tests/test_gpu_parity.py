@@ -60,26 +60,121 @@ def _coarse_tol(o):
     return max(1e-11, 10 * EPS64 * np.linalg.cond(o.A[-1].toarray()))
 
 
+class pinned_kernels:
+    """Run a block with every operator of h on one kernel (0 = sliced ELL, k = vector
+    CSR with k lanes per row); the autotuned choices are restored afterwards."""
+
+    def __init__(self, amge, h, lanes):
+        self.amge, self.h, self.lanes = amge, h, lanes
+
+    def __enter__(self):
+        self.saved = self.amge.amge_autotune_report(self.h)
+        if self.lanes != "tuned":
+            for (l, p, o), v in self.saved.items():
+                if v >= 0:
+                    self.amge.amge_set_kernel(self.h, l, p, o, self.lanes)
+        return self
+
+    def __exit__(self, *exc):
+        for (l, p, o), v in self.saved.items():
+            if v >= 0:
+                self.amge.amge_set_kernel(self.h, l, p, o, v)
+
+
 @pytest.mark.parametrize("form,n,L", CASES)
 @pytest.mark.parametrize("prec", [0, 1])
-def test_single_operators(amge, form, n, L, prec):
+@pytest.mark.parametrize("lanes", ["tuned", 0, 200, 800, 4, 32])
+def test_single_operators(amge, form, n, L, prec, lanes):
+    """Every stored product on every smoothing level, on each kernel: sliced ELL with
+    one, two and eight warps per slice (sign-coded for the +-1 incidences G), vector
+    CSR with 4 and 32 lanes per row, and the autotuned choice."""
     h = upload(amge, form, n, L)
     o = oracle_hierarchy(form, n, L, True)
     rng = np.random.default_rng(n * 7 + L)
     eps = EPS64 if prec == 0 else EPS32
-    for l in range(L - 1):
-        ops = {amge.AMGE_OP_A: o.A[l], amge.AMGE_OP_P: o.P[l], amge.AMGE_OP_PT: o.P[l].T.tocsr(),
-               amge.AMGE_OP_G: o.G[l], amge.AMGE_OP_GT: o.G[l].T.tocsr()}
-        for op, M in ops.items():
-            x = rng.uniform(-1, 1, M.shape[1])
-            y = torch.empty(M.shape[0], dtype=torch.float64, device="cuda")
-            amge.amge_apply(h, op, l, dev(x), y, prec)
-            ref = M @ x
-            bound = abs(M) @ abs(x)
-            nnz = np.diff(M.indptr)
-            slack = 2 * (nnz + 1) * eps * bound + (0 if prec == 0 else 2 * eps * bound)
-            err = np.abs(host(y) - ref)
-            assert np.all(err <= slack + 1e-300), (l, op, float((err / (bound + 1e-300)).max()))
+    rep = amge.amge_autotune_report(h)
+    with pinned_kernels(amge, h, lanes):
+        for l in range(L - 1):
+            ops = {amge.AMGE_OP_A: o.A[l], amge.AMGE_OP_P: o.P[l], amge.AMGE_OP_PT: o.P[l].T.tocsr(),
+                   amge.AMGE_OP_G: o.G[l], amge.AMGE_OP_GT: o.G[l].T.tocsr()}
+            if rep[(l, "fp64", "AG")] >= 0:
+                ops[amge.AMGE_OP_AG] = (o.A[l] @ o.G[l]).tocsr()
+            for op, M in ops.items():
+                x = rng.uniform(-1, 1, M.shape[1])
+                y = torch.empty(M.shape[0], dtype=torch.float64, device="cuda")
+                amge.amge_apply(h, op, l, dev(x), y, prec)
+                ref = M @ x
+                nnz = np.diff(M.indptr)
+                if op == amge.AMGE_OP_AG:
+                    # the stored A G carries the rounding of its entries (sums of
+                    # products of A and G) on top of the product's own
+                    bound = abs(o.A[l]) @ (abs(o.G[l]) @ abs(x))
+                    nnz = nnz + np.diff(o.A[l].indptr).max() * np.diff(o.G[l].indptr).max()
+                else:
+                    bound = abs(M) @ abs(x)
+                slack = 2 * (nnz + 1) * eps * bound + (0 if prec == 0 else 2 * eps * bound)
+                err = np.abs(host(y) - ref)
+                assert np.all(err <= slack + 1e-300), (l, op, float((err / (bound + 1e-300)).max()))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fused_aux_correction_equals_separate_products(amge, prec):
+    """H(curl): with G and A G on the one-warp sliced-ELL kernels the V-cycle forms
+    x += G y and r -= (A G) y (and the final z = x + G y + m^-1 (r - (A G) y)) in one
+    pass.  Forcing G onto the two-warp kernel runs the separate products, whose sums
+    are formed in the same order: the V-cycles must agree exactly."""
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, "hcurl", 24, 3)
+    rep = amge.amge_autotune_report(h)
+    pname = "fp64" if prec == 0 else "fp32"
+    b = dev(rhs_vector(73, h.n))
+    zf, zs = torch.empty_like(b), torch.empty_like(b)
+    levels = [l for l in range(2) if rep[(l, pname, "AG")] >= 0]
+    assert 0 in levels
+    saved = {l: (rep[(l, pname, "G")], rep[(l, pname, "AG")]) for l in levels}
+    try:
+        for l in levels:
+            amge.amge_set_kernel(h, l, pname, "G", 0)
+            amge.amge_set_kernel(h, l, pname, "AG", 0)
+        amge.amge_vcycle(h, b, zf, precision=prec)
+        for l in levels:
+            amge.amge_set_kernel(h, l, pname, "G", 200)
+        amge.amge_vcycle(h, b, zs, precision=prec)
+    finally:
+        for l, (g, ag) in saved.items():
+            amge.amge_set_kernel(h, l, pname, "G", g)
+            amge.amge_set_kernel(h, l, pname, "AG", ag)
+    torch.cuda.synchronize()
+    assert torch.isfinite(zf).all() and torch.equal(zf, zs)
+
+
+def test_set_kernel_rebuilds_graph_and_rejects_bad_input(amge):
+    """A pinned kernel choice takes effect in the captured PCG graph (rebuilt on the
+    next solve): results move by rounding only and the solve still matches the oracle."""
+    from oracle.amge_oracle import pcg
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, "hcurl", 24, 3)
+    o = oracle_hierarchy("hcurl", 24, 3, True)
+    b_np = rhs_vector(71, h.n)
+    x_ref, it_ref, _, _ = pcg(o, b_np, rtol=1e-8, maxit=500)
+    b = dev(b_np)
+    for lanes in ("tuned", 0, 400, 4):
+        with pinned_kernels(amge, h, lanes):
+            x = torch.empty_like(b)
+            st, info = amge.amge_pcg_solve(h, b, x)
+            assert st == amge.AMGE_OK and abs(info[0]["iters"] - it_ref) <= 1
+            xs = host(x)
+            assert np.linalg.norm(xs - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+    for bad in [(5, 0, 0, 0), (0, 2, 0, 0), (0, 0, 6, 0), (0, 0, 0, 3), (0, 0, 0, 64)]:
+        with pytest.raises(amge.AmgeError):
+            amge.amge_set_kernel(h, *bad)
+    hd = upload(amge, "hdiv", 24, 3)
+    with pytest.raises(amge.AmgeError):             # A G is not stored for H(div)
+        amge.amge_set_kernel(hd, 0, 0, "AG", 0)
+    with pytest.raises(amge.AmgeError):
+        amge.amge_apply(hd, amge.AMGE_OP_AG, 0, b[: 10], b[: 10], 0)
 
 
 def _hybrid_step_bound(o, b):
@@ -370,10 +465,10 @@ def test_graph_loop_maxit_and_nonfinite(amge):
 
 
 def test_autotune_report(amge):
-    """Every smoothing-level operator has a kernel choice: 0 (sliced ELL) or a
-    power-of-two lane count; the parity tests above run with whatever was chosen."""
+    """Every smoothing-level operator has a kernel choice: 0 or 100 w (sliced ELL with
+    w warps per slice) or a power-of-two lane count (vector CSR)."""
     h = upload(amge, "hcurl", 24, 3)
     rep = amge.amge_autotune_report(h)
     assert len(rep) == 2 * 2 * 6
-    assert set(rep.values()) <= {-1, 0, 2, 4, 8, 16, 32}
+    assert set(rep.values()) <= {-1, 0, 200, 400, 800, 2, 4, 8, 16, 32}
     assert rep[(0, "fp64", "AG")] >= 0          # H(curl): A G is stored (much sparser than A)
