@@ -155,6 +155,12 @@ void upload_sell(amge_hier* h, const HostCsr& M, DevSell<double>& d64, DevSell<f
   d64.nnz = d32.nnz = S.nnz;
   d64.unit = d32.unit = S.unit ? 1 : 0;
   d64.stored = d32.stored = S.sptr[S.nslices];
+  // operators well beyond L2 are streamed with the evict-first hint (32 MiB: a
+  // quarter of GB300's L2)
+  const double bytes64 = (double)d64.stored * (S.unit ? 4.0 : 12.0);
+  const double bytes32 = (double)d32.stored * (S.unit ? 4.0 : 8.0);
+  d64.stream = bytes64 > 32.0 * (1 << 20) ? 1 : 0;
+  d32.stream = bytes32 > 32.0 * (1 << 20) ? 1 : 0;
   d64.sptr = d32.sptr = upload<int64_t>(h, S.sptr.data(), S.sptr.size(), s);
   d64.srow = d32.srow = upload<int>(h, S.srow.data(), S.srow.size(), s);
   d64.ci = d32.ci = upload<int>(h, S.ci.data(), S.ci.size(), s);
@@ -274,9 +280,11 @@ void opk(amge_hier* h, int cls, const LevelDev<V>& d, int op, int epi, const Spm
   else launch_csrv<V>(op_csr(d, op), code, epi, a, s);
 }
 
-// One V-cycle at level l: z = B_l^{-1} b (Algorithm 4.1, x0 = 0).
+// One V-cycle at level l: z = B_l^{-1} b (Algorithm 4.1, x0 = 0).  x_ready: the
+// level's first point sweep from zero, x = m^-1 b, was already written into x by the
+// restriction that produced b.
 template <typename V>
-void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
+void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_ready = false) {
   auto& lv = levels<V>(h);
   if (l == h->L - 1) {
     Prof p(h, AMGE_PROF_COARSE, s, 2);
@@ -303,9 +311,16 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
     a.x = x, a.b = b, a.y = d.r;
     opk<V>(h, clsA, d, OP_A, EPI_RESID, a, s);
   };
+  LevelDev<V>& c = lv[l + 1];
+  const bool c_smooths = l + 1 < h->L - 1;  // the next level starts with x = m^-1 b
+  auto restrict_to_next = [&]() {            // b_c = P^T r (and x_c = m_c^-1 b_c)
+    SpmvArgs<V> a;
+    a.x = d.r, a.y = c.b;
+    if (c_smooths) a.d = c.minv, a.y2 = c.x;
+    opk<V>(h, AMGE_PROF_PT, d, OP_PT, c_smooths ? EPI_STORE_MUL : EPI_STORE, a, s);
+  };
   if (d.use_ag) {  // nu_pre = nu_post = 1; residual after each aux sweep by r -= (A G) y
-    LevelDev<V>& c = lv[l + 1];
-    {
+    if (!x_ready) {
       Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
       launch_mul<V>(d.n, d.minv, b, x, s);
     }
@@ -325,12 +340,8 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
       a.x = d.y, a.b = d.r, a.y = d.r;
       opk<V>(h, AMGE_PROF_AG, d, OP_AG, EPI_RESID, a, s);
     }
-    {
-      SpmvArgs<V> a;
-      a.x = d.r, a.y = c.b;
-      opk<V>(h, AMGE_PROF_PT, d, OP_PT, EPI_STORE, a, s);
-    }
-    vcycle_level<V>(h, l + 1, c.b, c.z, s);
+    restrict_to_next();
+    vcycle_level<V>(h, l + 1, c.b, c.z, s, c_smooths);
     {
       SpmvArgs<V> a;
       a.x = c.z, a.y = x;
@@ -354,7 +365,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
   // pre-relaxation: nu_pre steps of eq. 4.1
   for (int k = 0; k < h->nu_pre; k++) {
     if (k == 0) {  // from x0 = 0: x = M^{-1} b, then r = b - A x
-      {
+      if (!x_ready) {
         Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
         launch_mul<V>(d.n, d.minv, b, x, s);
       }
@@ -370,13 +381,8 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s) {
   }
   // coarse-grid correction
   residual();
-  LevelDev<V>& c = lv[l + 1];
-  {
-    SpmvArgs<V> a;
-    a.x = d.r, a.y = c.b;
-    opk<V>(h, AMGE_PROF_PT, d, OP_PT, EPI_STORE, a, s);
-  }
-  vcycle_level<V>(h, l + 1, c.b, c.z, s);
+  restrict_to_next();
+  vcycle_level<V>(h, l + 1, c.b, c.z, s, c_smooths);
   {
     SpmvArgs<V> a;
     a.x = c.z, a.y = x;
@@ -449,7 +455,7 @@ amge_status build_pcg_graph(amge_hier* h, int prec) {
   launch_pcg_update_p(n, h->pp, h->pz, h->red, h->cap);
   launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, h->cap);
   launch_pcg_axpy_norm(n, h->gx, h->pr, h->pp, h->pq, h->red, h->cap);
-  launch_pcg_loop_cond(G.hw, h->red, h->gstate, h->cap);
+  launch_pcg_loop_cond(G.hw, n, h->red, h->gstate, h->cap);
   cudaGraph_t captured = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap, &captured);
   h->prof = prof;
@@ -457,8 +463,8 @@ amge_status build_pcg_graph(amge_hier* h, int prec) {
     G.body[c] = h->launches[c] - before[c];
     h->launches[c] = before[c];
   }
-  G.body[AMGE_PROF_PCG_VEC] += 4;   // dots, update_p, axpy_norm, loop test
-  G.body[AMGE_PROF_PCG_SPMV] += 1;  // q = A p
+  G.body[AMGE_PROF_PCG_VEC] += 5;   // dots + finish, update_p, axpy_norm, loop test
+  G.body[AMGE_PROF_PCG_SPMV] += 2;  // q = A p + finish
   if (e != cudaSuccess) {
     set_error(std::string("graph capture: ") + cudaGetErrorString(e));
     return AMGE_ECUDA;
@@ -506,7 +512,7 @@ amge_status run_true_residual(PcgRun& r, int idx) {
   a.x = h->gx, a.b = r.b, a.y = h->pr;
   sell<double>(h, AMGE_PROF_PCG_SPMV, h->A0, EPI_RESID, a, r.s);
   {
-    Prof p(h, AMGE_PROF_PCG_VEC, r.s);
+    Prof p(h, AMGE_PROF_PCG_VEC, r.s, 2);
     launch_dot(h->n0, h->pr, h->pr, h->red.sc + idx, h->red, r.s);
   }
   CK(cudaMemcpyAsync(h->pinned + idx, h->red.sc + idx, sizeof(double), cudaMemcpyDeviceToHost, r.s));
@@ -570,17 +576,18 @@ amge_status run_step(PcgRun& r) {
       CK(cudaMemcpyAsync(h->pr, r.b, n * sizeof(double), cudaMemcpyDeviceToDevice, r.s));
       vcycle_fp64_iface(h, h->pr, h->pz, r.o.precision, r.s);
       {
-        Prof p(h, AMGE_PROF_PCG_VEC, r.s);
+        Prof p(h, AMGE_PROF_PCG_VEC, r.s, 2);
         launch_dot(n, h->pr, h->pz, sc + SC_RHO, h->red, r.s);
       }
       CK(cudaMemcpyAsync(h->pp, h->pz, n * sizeof(double), cudaMemcpyDeviceToDevice, r.s));
       {
-        Prof p(h, AMGE_PROF_PCG_SPMV, r.s);
+        Prof p(h, AMGE_PROF_PCG_SPMV, r.s, 2);
         launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, r.s);
       }
       {
-        Prof p(h, AMGE_PROF_PCG_VEC, r.s);
+        Prof p(h, AMGE_PROF_PCG_VEC, r.s, 2);
         launch_pcg_axpy_norm(n, h->gx, h->pr, h->pp, h->pq, h->red, r.s);
+        launch_pcg_finish_rr(n, h->red, r.s);
       }
       CK(cudaMemcpyAsync(h->pinned + SC_RR, sc + SC_RR, sizeof(double), cudaMemcpyDeviceToHost, r.s));
       r.it = 1;
@@ -636,7 +643,7 @@ amge_status amge::pcg_run_start(amge_hier* h, const double* b, double* x, const 
   r->h = h, r->b = b, r->x = x, r->o = o, r->s = s;
   r->t0 = std::chrono::steady_clock::now();
   {
-    Prof p(h, AMGE_PROF_PCG_VEC, s);
+    Prof p(h, AMGE_PROF_PCG_VEC, s, 2);
     launch_dot(h->n0, b, b, h->red.sc + SC_BB, h->red, s);
   }
   cudaError_t e = cudaMemcpyAsync(h->pinned + SC_BB, h->red.sc + SC_BB, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1043,13 +1050,10 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
     h->gx = dalloc<double>(h, n0);
     h->gstate = dalloc<int>(h, 4);
     h->red.partials = dalloc<double>(h, (size_t)kRedSlots * kMaxRedBlocks);
-    h->red.gpart = dalloc<double>(h, (size_t)kRedSlots * kRedGroups);
-    h->red.counters = dalloc<unsigned>(h, (size_t)kRedSlots * (kRedGroups + 1) * kCounterStride);
     h->red.sc = dalloc<double>(h, SC_COUNT);
   } catch (const UploadError& e) {
     return e.st;
   }
-  CK(cudaMemsetAsync(h->red.counters, 0, (size_t)kRedSlots * (kRedGroups + 1) * kCounterStride * sizeof(unsigned), s));
   CK(cudaMemsetAsync(h->red.sc, 0, SC_COUNT * sizeof(double), s));
   CK(cudaMallocHost(&h->pinned, 16 * sizeof(double)));
   CK(cudaMallocHost(&h->pinned_state, 4 * sizeof(int)));
@@ -1078,17 +1082,30 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
       if (lanes >= 100 && 2.0 * (lanes / 100) > avg + 1.0) continue;  // more warps than entry pairs
       if (lanes > 2 && lanes < 100 && lanes > 2 * avg) continue;
       d.lanes[op] = lanes;
-      for (int w = 0; w < 3; w++) opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
+      // Ten back-to-back launches captured in a graph, so the host's launch rate
+      // (which bounds small kernels launched one by one) does not flatten the
+      // comparison; best of three graph launches after a warm-up.
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      for (int r = 0; r < 10; r++) opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
+      CK(cudaStreamEndCapture(s, &g));
+      cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      CK(ie);
       float ms = 1e30f;
-      for (int trial = 0; trial < 3; trial++) {  // best of three trials of 5 launches
-        CK(cudaEventRecord(e0, s));
-        for (int r = 0; r < 5; r++) opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
+      cudaError_t le = cudaGraphLaunch(ge, s);
+      for (int trial = 0; trial < 3 && le == cudaSuccess; trial++) {
+        le = cudaEventRecord(e0, s);
+        if (le == cudaSuccess) le = cudaGraphLaunch(ge, s);
+        if (le == cudaSuccess) le = cudaEventRecord(e1, s);
+        if (le == cudaSuccess) le = cudaEventSynchronize(e1);
         float t = 0.f;
-        CK(cudaEventElapsedTime(&t, e0, e1));
+        if (le == cudaSuccess) le = cudaEventElapsedTime(&t, e0, e1);
         ms = std::min(ms, t);
       }
+      cudaGraphExecDestroy(ge);
+      CK(le);
       if (lanes == 0 || ms < 0.9f * best) best = (lanes == 0 || ms < best) ? ms : best, best_lanes = lanes;
     }
     d.lanes[op] = best_lanes;
@@ -1097,14 +1114,21 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
 }
 
 amge_status autotune(amge_hier* h, cudaStream_t s) {
+  // candidates are captured into graphs on a stream of our own (the caller's may be
+  // the legacy default stream, which cannot be captured)
+  CK(cudaStreamSynchronize(s));
+  cudaStream_t ts;
+  CK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   amge_status st = AMGE_OK;
   for (int l = 0; l + 1 < h->L && st == AMGE_OK; l++) {
-    st = autotune_level<double>(h, l, s, e0, e1);
-    if (st == AMGE_OK) st = autotune_level<float>(h, l, s, e0, e1);
+    st = autotune_level<double>(h, l, ts, e0, e1);
+    if (st == AMGE_OK) st = autotune_level<float>(h, l, ts, e0, e1);
   }
+  cudaStreamSynchronize(ts);
+  cudaStreamDestroy(ts);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   for (int c = 0; c < AMGE_PROF_CLASSES; c++) h->launches[c] = 0;
@@ -1275,11 +1299,11 @@ amge_status pcg_one(amge_hier* h, const double* b, double* x, const amge_solve_o
     SpmvArgs<double> a;
     a.x = x, a.b = b, a.y = h->pr;
     sell<double>(h, AMGE_PROF_PCG_SPMV, h->A0, EPI_RESID, a, s);
-    Prof p(h, AMGE_PROF_PCG_VEC, s);
+    Prof p(h, AMGE_PROF_PCG_VEC, s, 2);
     launch_dot(n, h->pr, h->pr, sc + SC_DOT, h->red, s);
   };
   {
-    Prof p(h, AMGE_PROF_PCG_VEC, s);
+    Prof p(h, AMGE_PROF_PCG_VEC, s, 2);
     launch_dot(n, b, b, sc + SC_BB, h->red, s);
   }
   double bb;
@@ -1298,7 +1322,7 @@ amge_status pcg_one(amge_hier* h, const double* b, double* x, const amge_solve_o
   CK(cudaMemcpyAsync(h->pr, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   vcycle_fp64_iface(h, h->pr, h->pz, o.precision, s);
   {
-    Prof p(h, AMGE_PROF_PCG_VEC, s);
+    Prof p(h, AMGE_PROF_PCG_VEC, s, 2);
     launch_dot(n, h->pr, h->pz, sc + SC_RHO, h->red, s);
   }
   CK(cudaMemcpyAsync(h->pp, h->pz, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1308,12 +1332,13 @@ amge_status pcg_one(amge_hier* h, const double* b, double* x, const amge_solve_o
   int status = AMGE_OK;
   while (it < o.maxit) {
     {
-      Prof p(h, AMGE_PROF_PCG_SPMV, s);
+      Prof p(h, AMGE_PROF_PCG_SPMV, s, 2);
       launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, s);
     }
     {
-      Prof p(h, AMGE_PROF_PCG_VEC, s);
+      Prof p(h, AMGE_PROF_PCG_VEC, s, 2);
       launch_pcg_axpy_norm(n, x, h->pr, h->pp, h->pq, h->red, s);
+      launch_pcg_finish_rr(n, h->red, s);
     }
     CK(cudaMemcpyAsync(h->pinned, sc + SC_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(h->ev, s));
@@ -1324,7 +1349,7 @@ amge_status pcg_one(amge_hier* h, const double* b, double* x, const amge_solve_o
     if (rr_prev > 0 && rr_prev2 > 0) spec = rr_prev * (rr_prev / rr_prev2) > 100.0 * tol2;
     if (spec) {
       vcycle_fp64_iface(h, h->pr, h->pz, o.precision, s);
-      Prof p(h, AMGE_PROF_PCG_VEC, s);
+      Prof p(h, AMGE_PROF_PCG_VEC, s, 2);
       launch_pcg_dots(n, h->pr, h->pz, h->pq, flexible, h->red, s);
     }
     CK(cudaEventSynchronize(h->ev));
@@ -1347,7 +1372,7 @@ amge_status pcg_one(amge_hier* h, const double* b, double* x, const amge_solve_o
     }
     if (!spec) {
       vcycle_fp64_iface(h, h->pr, h->pz, o.precision, s);
-      Prof p(h, AMGE_PROF_PCG_VEC, s);
+      Prof p(h, AMGE_PROF_PCG_VEC, s, 2);
       launch_pcg_dots(n, h->pr, h->pz, h->pq, flexible, h->red, s);
     }
     Prof p(h, AMGE_PROF_PCG_VEC, s);

@@ -50,7 +50,8 @@ HostSell build_sell(const HostCsr& M, int sigma, bool allow_unit = false);
 template <typename V>
 struct DevSell {
   int nr = 0, nc = 0, nslices = 0;
-  int unit = 0;  // sign-coded columns (val == nullptr)
+  int unit = 0;    // sign-coded columns (val == nullptr)
+  int stream = 0;  // larger than a quarter of L2: entries are read with the evict-first hint
   int64_t nnz = 0, stored = 0;
   int64_t* sptr = nullptr;
   int* srow = nullptr;
@@ -64,7 +65,8 @@ enum EpiKind : int {
   EPI_RESID = 1,  // y_i = b_i - s
   EPI_SCALE = 3,  // y_i = d_i s
   EPI_ADD = 4,    // y_i += s
-  EPI_SWEEP = 5   // y_i = xin_i + d_i (b_i - s)   (l1-Jacobi sweep into a new vector)
+  EPI_SWEEP = 5,  // y_i = xin_i + d_i (b_i - s)   (l1-Jacobi sweep into a new vector)
+  EPI_STORE_MUL = 6  // y_i = s and y2_i = d_i s   (restriction that also starts the next level's sweep)
 };
 
 template <typename V>
@@ -74,6 +76,7 @@ struct SpmvArgs {
   const V* b = nullptr;    // right-hand side (RESID / SWEEP)
   const V* xin = nullptr;  // current iterate (SWEEP)
   V* y = nullptr;
+  V* y2 = nullptr;         // second output (STORE_MUL)
 };
 
 // wps = warps per 32-row slice (1, 2, 4, 8).
@@ -168,39 +171,39 @@ constexpr int kMaxRedBlocks = 16384;  // capacity of the block-partial arrays (s
 constexpr int kMaxRedBlocksMM = 1024;  // block-partial capacity per column (blocks of vectors)
 constexpr int kVecRedBlocks = 4096;   // grid cap of the vector reductions (one resident wave is used)
 
-// Grid reductions finish in a two-level arrival tree: block b signals counter
-// b % kRedGroups (each counter on its own 128-byte line); the last block of a group
-// sums the group's partials, the last group sums the group totals.  No address sees
-// more than ~gridDim / kRedGroups arrivals: on GB300 arrivals at one address from all
-// SMs serialise at several ns each.
-constexpr int kRedGroups = 64;
-constexpr int kCounterStride = 32;  // unsigned words between counters (128 bytes)
-
+// Single-vector reductions: kernels store one partial per block in a slot, and a
+// one-block kernel sums the slot in index order (deterministic: the grid depends on
+// n and the device only).
 struct RedScratch {
   double* partials = nullptr;  // [kRedSlots][kMaxRedBlocks]
-  double* gpart = nullptr;     // [kRedSlots][kRedGroups] group totals
-  unsigned* counters = nullptr;  // [kRedSlots][kRedGroups + 1][kCounterStride]
   double* sc = nullptr;        // [SC_COUNT]
 };
 
 int red_blocks(int64_t n);
+// *out = x.y (two launches)
 void launch_dot(int64_t n, const double* x, const double* y, double* out, const RedScratch& r, cudaStream_t s);
-// PCG kernels (scalars in RedScratch::sc, reductions finished by the tree above).
-// q = A p and pq = p.q; the finishing block sets alpha = rho / pq.
+// PCG kernels (scalars in RedScratch::sc).  The streaming kernels store block
+// partials; one-block kernels sum them in index order and set the scalars.
+int pcg_spmv_blocks(const DevSell<double>& A);
+// q = A p and pq = p.q (two launches); alpha = rho / pq.
 void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, const RedScratch& r,
                          cudaStream_t s);
-// x += alpha p; r -= alpha q; ||r||^2 -> SC_RR
+// x += alpha p; r -= alpha q; block partials of ||r||^2 (summed by the loop test or
+// launch_pcg_finish_rr, which sets SC_RR)
 void launch_pcg_axpy_norm(int64_t n, double* x, double* rv, const double* p, const double* q,
                           const RedScratch& r, cudaStream_t s);
-// rho_new = r.z, zq = z.q; beta = rho_new / rho (flexible = 0) or -alpha zq / rho (flexible = 1)
+void launch_pcg_finish_rr(int64_t n, const RedScratch& r, cudaStream_t s);
+// rho_new = r.z, zq = z.q (two launches); beta = rho_new / rho (flexible = 0) or
+// -alpha zq / rho (flexible = 1)
 void launch_pcg_dots(int64_t n, const double* rv, const double* z, const double* q, int flexible,
                      const RedScratch& r, cudaStream_t s);
 // p = z + beta p; rho = rho_new
 void launch_pcg_update_p(int64_t n, double* p, const double* z, const RedScratch& r, cudaStream_t s);
-// Loop test of the graph-driven PCG: state[0] += 1 (iterations done), then the WHILE
-// condition is set to (||r||^2 finite && > SC_TOL2 && state[0] < state[1] (maxit));
-// state[2] = 1 flags a non-finite ||r||^2.
-void launch_pcg_loop_cond(cudaGraphConditionalHandle hw, const RedScratch& r, int* state, cudaStream_t s);
+// Loop test of the graph-driven PCG (one block): SC_RR from the axpy partials,
+// state[0] += 1 (iterations done), then the WHILE condition is set to (||r||^2 finite
+// && > SC_TOL2 && state[0] < state[1] (maxit)); state[2] = 1 flags a non-finite ||r||^2.
+void launch_pcg_loop_cond(cudaGraphConditionalHandle hw, int64_t n, const RedScratch& r, int* state,
+                          cudaStream_t s);
 
 // Multi-RHS PCG: per-column scalars live in sc_mm[scalar][column]; `active[c]` masks
 // columns that have converged (their alpha and beta are forced to 0).

@@ -42,6 +42,15 @@ struct Pair<float> {
   using T = float2;
 };
 
+// Loads of stored matrix entries.  CS (operators much larger than L2, read once per
+// product): the streaming hint (evict-first), so the level-0 sweeps do not push the
+// coarse levels' operators out of L2 between V-cycles.
+template <bool CS, typename T>
+__device__ __forceinline__ T ldm(const T* p) {
+  if (CS) return __ldcs(p);
+  return __ldg(p);
+}
+
 // One sliced-ELL slice per warp, one row per lane.  Each row is one FMA chain that
 // starts from the epilogue's vector (b for r = b - A x and the sweep, y for y += A x)
 // with the stored values negated where the product is subtracted, so a row of w
@@ -63,6 +72,10 @@ __device__ __forceinline__ void sell_store(const SpmvArgs<V>& a, int row, V s) {
   switch (EPI) {
     case EPI_SCALE: a.y[row] = a.d[row] * s; break;
     case EPI_SWEEP: a.y[row] = fma(a.d[row], s, a.xin[row]); break;
+    case EPI_STORE_MUL:
+      a.y[row] = s;
+      a.y2[row] = a.d[row] * s;
+      break;
     default: a.y[row] = s; break;  // STORE, RESID (s = b - A x), ADD (s = y + A x)
   }
 }
@@ -92,7 +105,7 @@ __device__ __forceinline__ float signed_entry(const float* x, int c) {
 // the first warp adds them in warp order and writes the row.  More warps per slice
 // expose more loads in flight for operators with long rows and few slices (the
 // restriction P^T, coarse-level operators); WPS = 1 needs no shared memory.
-template <typename V, int EPI, int WPS, bool UNIT>
+template <typename V, int EPI, int WPS, bool UNIT, bool CS>
 __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __restrict__ sptr,
                                                  const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                  const typename Pair<V>::T* __restrict__ val2, SpmvArgs<V> a) {
@@ -112,7 +125,7 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
     if (UNIT) {
 #pragma unroll 2
       for (int k = g; k < np; k += WPS) {
-        const int2 c = __ldg(cp + (size_t)k * 32);
+        const int2 c = ldm<CS>(cp + (size_t)k * 32);
         const V e0 = signed_entry<NEG>(a.x, c.x);
         const V e1 = signed_entry<NEG>(a.x, c.y);
         s += e0;
@@ -122,8 +135,8 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
       const typename Pair<V>::T* vp = val2 + p0 + lane;
 #pragma unroll 2
       for (int k = g; k < np; k += WPS) {
-        const int2 c = __ldg(cp + (size_t)k * 32);
-        const typename Pair<V>::T v = __ldg(vp + (size_t)k * 32);
+        const int2 c = ldm<CS>(cp + (size_t)k * 32);
+        const typename Pair<V>::T v = ldm<CS>(vp + (size_t)k * 32);
         const V x0 = ldg(a.x + c.x), x1 = ldg(a.x + c.y);
         s = fma(NEG ? -v.x : v.x, x0, s);
         s = fma(NEG ? -v.y : v.y, x1, s);
@@ -143,7 +156,7 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
 }
 
 // G y (two sign-coded entries) and A G y for one row per lane (see AgArgs).
-template <typename V, bool POST>
+template <typename V, bool POST, bool CS>
 __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t* __restrict__ sptr,
                                                      const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                      const typename Pair<V>::T* __restrict__ val2, AgArgs<V> a) {
@@ -163,8 +176,8 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
   const typename Pair<V>::T* vp = val2 + p0 + lane;
 #pragma unroll 2
   for (int k = 0; k < np; k++) {
-    const int2 c = __ldg(cp + (size_t)k * 32);
-    const typename Pair<V>::T v = __ldg(vp + (size_t)k * 32);
+    const int2 c = ldm<CS>(cp + (size_t)k * 32);
+    const typename Pair<V>::T v = ldm<CS>(vp + (size_t)k * 32);
     const V x0 = ldg(a.y + c.x), x1 = ldg(a.y + c.y);
     s = fma(-v.x, x0, s);
     s = fma(-v.y, x1, s);
@@ -209,6 +222,10 @@ __global__ void __launch_bounds__(kBlock) k_csrv(int nr, const int* __restrict__
     case EPI_SCALE: a.y[row] = a.d[row] * s; break;
     case EPI_ADD: a.y[row] += s; break;
     case EPI_SWEEP: a.y[row] = fma(a.d[row], a.b[row] - s, a.xin[row]); break;
+    case EPI_STORE_MUL:
+      a.y[row] = s;
+      a.y2[row] = a.d[row] * s;
+      break;
   }
 }
 
@@ -242,101 +259,78 @@ __global__ void __launch_bounds__(kBlock) k_trimv(int n, const double* __restric
 }
 
 // ---------------------------------------------------------------- reductions
-// Block sum in a fixed tree; result valid in thread 0.
+// Block sum in a fixed order, valid in thread 0.  On GB300 every FP64 add counts (the
+// FP64 pipe runs at 1/65 of the FP32 rate and a warp-wide add occupies it as long as
+// 32 FMAs of a sparse row), so the values go through shared memory and only warp 0
+// adds: lane l sums sh[l], sh[l + 32], ... in order, then a five-step shuffle tree.
+// That is NT/32 + 5 warp-wide adds per block instead of 5 per warp plus 5.
+// sh must hold NT doubles (NT = blockDim.x, a multiple of 32).
+template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
+  __syncthreads();  // sh may still be read by a previous call
+  sh[threadIdx.x] = v;
   __syncthreads();
   double t = 0.0;
-  if (w == 0) {
-    t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+  if (threadIdx.x < 32) {
+    t = sh[threadIdx.x];
+#pragma unroll
+    for (int k = 1; k < NT / 32; k++) t += sh[threadIdx.x + 32 * k];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
   }
   return t;
 }
 
-// Each block contributes v[0..NV) to partial slots slot0 .. slot0+NV-1; the block
-// that completes the arrival tree returns true with the totals in tot (valid in
-// all its threads).  Group g holds blocks g, g + G, g + 2G, ... (G = min(kRedGroups,
-// gridDim.x)); sums run in index order with block_sum's fixed tree, so the totals do
-// not depend on which blocks arrive last.
-template <int NV>
-__device__ bool finish_blocks(const double* v, const RedScratch& r, int slot0, double* tot) {
-  __shared__ double sh[32];
-  __shared__ bool last;
-  __shared__ double res[NV];
-  const int G = min(kRedGroups, (int)gridDim.x);
-  const int grp = blockIdx.x % G;
-  unsigned* cnt = r.counters + (size_t)slot0 * (kRedGroups + 1) * kCounterStride;
-  double bs[NV];
-#pragma unroll
-  for (int k = 0; k < NV; k++) bs[k] = block_sum(v[k], sh);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; k++) r.partials[(slot0 + k) * kMaxRedBlocks + blockIdx.x] = bs[k];
-    __threadfence();
-    const unsigned members = (gridDim.x - grp + G - 1) / G;
-    last = (atomicAdd(cnt + grp * kCounterStride, 1u) == members - 1);
-  }
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-  // group total: members grp, grp + G, ... in index order
-#pragma unroll
-  for (int k = 0; k < NV; k++) {
-    double acc = 0.0;
-    for (int b = grp + G * (int)threadIdx.x; b < (int)gridDim.x; b += G * (int)blockDim.x)
-      acc += __ldcg(r.partials + (slot0 + k) * kMaxRedBlocks + b);
-    const double t = block_sum(acc, sh);
-    if (threadIdx.x == 0) res[k] = t;
-  }
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; k++) r.gpart[(slot0 + k) * kRedGroups + grp] = res[k];
-    cnt[grp * kCounterStride] = 0u;
-    __threadfence();
-    last = (atomicAdd(cnt + kRedGroups * kCounterStride, 1u) == (unsigned)G - 1);
-  }
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-#pragma unroll
-  for (int k = 0; k < NV; k++) {
-    const double acc = threadIdx.x < G ? __ldcg(r.gpart + (slot0 + k) * kRedGroups + threadIdx.x) : 0.0;
-    const double t = block_sum(acc, sh);
-    if (threadIdx.x == 0) res[k] = t;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; k++) tot[k] = res[k];
-  if (threadIdx.x == 0) cnt[kRedGroups * kCounterStride] = 0u;
-  return true;
+// ------------------------------------------------------------ PCG kernels
+// Each PCG reduction is split in two launches: the streaming kernel stores one
+// partial per block (no fence, no atomic), and a one-block kernel sums the partials
+// in index order (thread t takes t, t + blockDim, ..., then block_sum's tree) and
+// derives the scalars.  Measured on GB300, a GPU-scope fence plus an arrival atomic
+// in every block, or every block re-reading all partials, costs more than the extra
+// launch.
+
+template <int NT>
+__device__ __forceinline__ void store_partial(double v, double* part, double* sh) {
+  const double t = block_sum<NT>(v, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
+// Sum of part[0..count) in the fixed order above; valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int count, double* sh) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += NT) acc += __ldcg(part + i);
+  return block_sum<NT>(acc, sh);
+}
+
+constexpr int kSpmvDotBlock = 512;  // 16 slices per block
+constexpr int kFinishBlock = 1024;
+
+// Dot product: block partials, then one block sums them in index order.
 __global__ void __launch_bounds__(kBlock, 8) k_dot(int64_t n, const double* __restrict__ x,
-                                                   const double* __restrict__ y, double* out, RedScratch r) {
+                                                   const double* __restrict__ y, RedScratch r) {
+  __shared__ double sh[kBlock];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
     acc = fma(x[i], y[i], acc);
-  double tot[1];
-  if (finish_blocks<1>(&acc, r, kSlotDot, tot) && threadIdx.x == 0) *out = tot[0];
+  store_partial<kBlock>(acc, r.partials + kSlotDot * kMaxRedBlocks, sh);
 }
 
-// ------------------------------------------------------------ PCG kernels
-constexpr int kSpmvDotBlock = 512;  // 16 slices per block
-
-// q = A p, one sliced-ELL slice per warp, and pq = p.q; the finishing block sets
-// alpha = rho / pq.
+// q = A p, one sliced-ELL slice per warp, and the block partials of p.q.  A warp
+// that finishes its slice leaves its row products in shared memory and exits; the
+// last warp of the block to arrive (a shared-memory counter) sums them in a fixed
+// order, so no warp idles at a block barrier behind a longer slice.
+template <bool CS>
 __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, const int64_t* __restrict__ sptr,
                                                                    const int* __restrict__ srow,
                                                                    const int2* __restrict__ ci2,
                                                                    const double2* __restrict__ val2,
                                                                    const double* __restrict__ p,
-                                                                   double* __restrict__ q, RedScratch r) {
+                                                                   double* __restrict__ q, double* part) {
+  __shared__ double sh[kSpmvDotBlock];
+  __shared__ unsigned arrived;
+  if (threadIdx.x == 0) arrived = 0u;
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int slice = (blockIdx.x * kSpmvDotBlock + threadIdx.x) >> 5;
   double contrib = 0.0;
@@ -349,8 +343,8 @@ __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, 
     double acc = 0.0;
 #pragma unroll 2
     for (int k = 0; k < np; k++) {
-      const int2 c = __ldg(cp + (size_t)k * 32);
-      const double2 v = __ldg(vp + (size_t)k * 32);
+      const int2 c = ldm<CS>(cp + (size_t)k * 32);
+      const double2 v = ldm<CS>(vp + (size_t)k * 32);
       const double x0 = ldg(p + c.x), x1 = ldg(p + c.y);
       acc = fma(v.x, x0, acc);
       acc = fma(v.y, x1, acc);
@@ -360,16 +354,42 @@ __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, 
       contrib = ldg(p + row) * acc;
     }
   }
-  double tot[1];
-  if (finish_blocks<1>(&contrib, r, kSlotPQ, tot) && threadIdx.x == 0) {
-    r.sc[SC_PQ] = tot[0];
-    r.sc[SC_ALPHA] = r.sc[SC_RHO] / tot[0];
+  sh[threadIdx.x] = contrib;
+  __threadfence_block();
+  unsigned t = 0;
+  if (lane == 0) t = atomicAdd(&arrived, 1u);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  if (t != kSpmvDotBlock / 32 - 1) return;
+  __threadfence_block();
+  double s = sh[lane];
+#pragma unroll
+  for (int k = 1; k < kSpmvDotBlock / 32; k++) s += sh[lane + 32 * k];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) part[blockIdx.x] = s;
+}
+
+// pq = p.q from the partials; alpha = rho / pq.
+__global__ void __launch_bounds__(kFinishBlock) k_pcg_finish_pq(int npq, RedScratch r) {
+  __shared__ double sh[kFinishBlock];
+  const double pq = sum_partials<kFinishBlock>(r.partials + kSlotPQ * kMaxRedBlocks, npq, sh);
+  if (threadIdx.x == 0) {
+    r.sc[SC_PQ] = pq;
+    r.sc[SC_ALPHA] = r.sc[SC_RHO] / pq;
   }
 }
 
+__global__ void __launch_bounds__(kFinishBlock) k_finish_dot(int nred, RedScratch r, double* out) {
+  __shared__ double sh[kFinishBlock];
+  const double t = sum_partials<kFinishBlock>(r.partials + kSlotDot * kMaxRedBlocks, nred, sh);
+  if (threadIdx.x == 0) *out = t;
+}
+
+// x += alpha p; r -= alpha q; block partials of ||r||^2.
 __global__ void __launch_bounds__(kBlock, 8) k_pcg_axpy_norm(int64_t n, double* __restrict__ x,
                                                              double* __restrict__ rv, const double* __restrict__ p,
                                                              const double* __restrict__ q, RedScratch r) {
+  __shared__ double sh[kBlock];
   const double alpha = r.sc[SC_ALPHA];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
@@ -378,33 +398,50 @@ __global__ void __launch_bounds__(kBlock, 8) k_pcg_axpy_norm(int64_t n, double* 
     rv[i] = ri;
     acc = fma(ri, ri, acc);
   }
-  double tot[1];
-  if (finish_blocks<1>(&acc, r, kSlotRR, tot) && threadIdx.x == 0) r.sc[SC_RR] = tot[0];
+  store_partial<kBlock>(acc, r.partials + kSlotRR * kMaxRedBlocks, sh);
 }
 
+// ||r||^2 -> SC_RR (host-driven loop).
+__global__ void __launch_bounds__(kFinishBlock) k_pcg_finish_rr(int nrr, RedScratch r) {
+  __shared__ double sh[kFinishBlock];
+  const double rr = sum_partials<kFinishBlock>(r.partials + kSlotRR * kMaxRedBlocks, nrr, sh);
+  if (threadIdx.x == 0) r.sc[SC_RR] = rr;
+}
+
+// Block partials of r.z (and z.q for the flexible beta).
 __global__ void __launch_bounds__(kBlock, 8) k_pcg_dots(int64_t n, const double* __restrict__ rv,
                                                         const double* __restrict__ z, const double* __restrict__ q,
                                                         int flexible, RedScratch r) {
-  double acc[2] = {0.0, 0.0};
+  __shared__ double sh[kBlock];
+  double acc0 = 0.0, acc1 = 0.0;
   if (flexible) {
     for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
       const double zi = z[i];
-      acc[0] = fma(rv[i], zi, acc[0]);
-      acc[1] = fma(zi, q[i], acc[1]);
+      acc0 = fma(rv[i], zi, acc0);
+      acc1 = fma(zi, q[i], acc1);
     }
   } else {  // standard beta needs r.z only
     for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
-      acc[0] = fma(rv[i], z[i], acc[0]);
+      acc0 = fma(rv[i], z[i], acc0);
   }
-  double tot[2];
-  if (finish_blocks<2>(acc, r, kSlotRZ, tot) && threadIdx.x == 0) {
+  store_partial<kBlock>(acc0, r.partials + kSlotRZ * kMaxRedBlocks, sh);
+  if (flexible) store_partial<kBlock>(acc1, r.partials + kSlotZQ * kMaxRedBlocks, sh);
+}
+
+// rho_new = r.z, zq = z.q; beta = rho_new / rho or -alpha zq / rho.
+__global__ void __launch_bounds__(kFinishBlock) k_pcg_finish_dots(int nred, int flexible, RedScratch r) {
+  __shared__ double sh[kFinishBlock];
+  const double rz = sum_partials<kFinishBlock>(r.partials + kSlotRZ * kMaxRedBlocks, nred, sh);
+  const double zq = flexible ? sum_partials<kFinishBlock>(r.partials + kSlotZQ * kMaxRedBlocks, nred, sh) : 0.0;
+  if (threadIdx.x == 0) {
     const double rho = r.sc[SC_RHO];
-    r.sc[SC_RHO_NEW] = tot[0];
-    r.sc[SC_ZQ] = tot[1];
-    r.sc[SC_BETA] = flexible ? -r.sc[SC_ALPHA] * tot[1] / rho : tot[0] / rho;
+    r.sc[SC_RHO_NEW] = rz;
+    r.sc[SC_ZQ] = zq;
+    r.sc[SC_BETA] = flexible ? -r.sc[SC_ALPHA] * zq / rho : rz / rho;
   }
 }
 
+// p = z + beta p; rho = rho_new.
 __global__ void __launch_bounds__(kBlock, 8) k_pcg_update_p(int64_t n, double* __restrict__ p,
                                                             const double* __restrict__ z, RedScratch r) {
   const double beta = r.sc[SC_BETA];
@@ -413,13 +450,18 @@ __global__ void __launch_bounds__(kBlock, 8) k_pcg_update_p(int64_t n, double* _
   if (blockIdx.x == 0 && threadIdx.x == 0) r.sc[SC_RHO] = r.sc[SC_RHO_NEW];
 }
 
-__global__ void k_pcg_loop_cond(cudaGraphConditionalHandle hw, const double* __restrict__ sc, int* state) {
-  const double rr = sc[SC_RR];
+// One block: ||r||^2 from the axpy partials, then the WHILE condition.
+__global__ void __launch_bounds__(kFinishBlock) k_pcg_loop_cond(cudaGraphConditionalHandle hw, int nrr, RedScratch r,
+                                                                int* state) {
+  __shared__ double sh[kFinishBlock];
+  const double rr = sum_partials<kFinishBlock>(r.partials + kSlotRR * kMaxRedBlocks, nrr, sh);
+  if (threadIdx.x != 0) return;
+  r.sc[SC_RR] = rr;
   const int it = state[0] + 1;
   state[0] = it;
   const bool fin = isfinite(rr);
   if (!fin) state[2] = 1;
-  cudaGraphSetConditional(hw, (fin && rr > sc[SC_TOL2] && it < state[1]) ? 1u : 0u);
+  cudaGraphSetConditional(hw, (fin && rr > r.sc[SC_TOL2] && it < state[1]) ? 1u : 0u);
 }
 
 // Blocks of kBlock threads that fill every SM of the current device once (2048
@@ -452,27 +494,37 @@ int red_blocks(int64_t n) {
   return (int)std::min<int64_t>(std::max<int64_t>(g, 1), resident_blocks());
 }
 
-template <typename V, int WPS, bool UNIT>
+template <typename V, int WPS, bool UNIT, bool CS>
 static void launch_sell_t(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
   const int per = (kBlock / 32) / WPS;  // slices per block
   const int grid = (M.nslices + per - 1) / per;
   const int2* ci2 = reinterpret_cast<const int2*>(M.ci);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(M.val);
   switch (epi) {
-    case EPI_STORE: k_sell<V, EPI_STORE, WPS, UNIT><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_RESID: k_sell<V, EPI_RESID, WPS, UNIT><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_SCALE: k_sell<V, EPI_SCALE, WPS, UNIT><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_ADD: k_sell<V, EPI_ADD, WPS, UNIT><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_SWEEP: k_sell<V, EPI_SWEEP, WPS, UNIT><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_STORE: k_sell<V, EPI_STORE, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_RESID: k_sell<V, EPI_RESID, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SCALE: k_sell<V, EPI_SCALE, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_ADD: k_sell<V, EPI_ADD, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SWEEP: k_sell<V, EPI_SWEEP, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_STORE_MUL:
+      k_sell<V, EPI_STORE_MUL, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a);
+      break;
   }
 }
 template <typename V, bool UNIT>
 static void launch_sell_u(const DevSell<V>& M, int wps, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  const bool cs = M.stream != 0;  // streaming variants for the one- and two-warp kernels
   switch (wps) {
-    case 2: launch_sell_t<V, 2, UNIT>(M, epi, a, s); break;
-    case 4: launch_sell_t<V, 4, UNIT>(M, epi, a, s); break;
-    case 8: launch_sell_t<V, 8, UNIT>(M, epi, a, s); break;
-    default: launch_sell_t<V, 1, UNIT>(M, epi, a, s); break;
+    case 2:
+      if (cs) launch_sell_t<V, 2, UNIT, true>(M, epi, a, s);
+      else launch_sell_t<V, 2, UNIT, false>(M, epi, a, s);
+      break;
+    case 4: launch_sell_t<V, 4, UNIT, false>(M, epi, a, s); break;
+    case 8: launch_sell_t<V, 8, UNIT, false>(M, epi, a, s); break;
+    default:
+      if (cs) launch_sell_t<V, 1, UNIT, true>(M, epi, a, s);
+      else launch_sell_t<V, 1, UNIT, false>(M, epi, a, s);
+      break;
   }
 }
 
@@ -492,6 +544,7 @@ static void launch_csrv_lanes(const DevCsr<V>& M, int epi, const SpmvArgs<V>& a,
     case EPI_SCALE: k_csrv<V, LANES, EPI_SCALE><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
     case EPI_ADD: k_csrv<V, LANES, EPI_ADD><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
     case EPI_SWEEP: k_csrv<V, LANES, EPI_SWEEP><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
+    case EPI_STORE_MUL: k_csrv<V, LANES, EPI_STORE_MUL><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
   }
 }
 
@@ -514,8 +567,13 @@ void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStr
   const int grid = (AG.nslices + (kBlock / 32) - 1) / (kBlock / 32);
   const int2* ci2 = reinterpret_cast<const int2*>(AG.ci);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(AG.val);
-  if (post) k_ag_fused<V, true><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
-  else k_ag_fused<V, false><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+  if (AG.stream) {
+    if (post) k_ag_fused<V, true, true><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+    else k_ag_fused<V, false, true><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+  } else {
+    if (post) k_ag_fused<V, true, false><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+    else k_ag_fused<V, false, false><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+  }
 }
 template void launch_ag_fused<double>(const DevSell<double>&, int, const AgArgs<double>&, cudaStream_t);
 template void launch_ag_fused<float>(const DevSell<float>&, int, const AgArgs<float>&, cudaStream_t);
@@ -550,15 +608,22 @@ template void launch_coarse<float, float>(int, const double*, const double*, con
                                           cudaStream_t);
 
 void launch_dot(int64_t n, const double* x, const double* y, double* out, const RedScratch& r, cudaStream_t s) {
-  k_dot<<<red_blocks(n), kBlock, 0, s>>>(n, x, y, out, r);
+  k_dot<<<red_blocks(n), kBlock, 0, s>>>(n, x, y, r);
+  k_finish_dot<<<1, kFinishBlock, 0, s>>>(red_blocks(n), r, out);
+}
+
+int pcg_spmv_blocks(const DevSell<double>& A) {
+  const int per = kSpmvDotBlock / 32;
+  return std::max((A.nslices + per - 1) / per, 1);  // <= kMaxRedBlocks (checked at upload)
 }
 
 void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, const RedScratch& r,
                          cudaStream_t s) {
-  const int per = kSpmvDotBlock / 32;
-  const int grid = std::max((A.nslices + per - 1) / per, 1);  // <= kMaxRedBlocks (checked at upload)
-  k_pcg_spmv_dot<<<grid, kSpmvDotBlock, 0, s>>>(A.nslices, A.sptr, A.srow, reinterpret_cast<const int2*>(A.ci),
-                                                reinterpret_cast<const double2*>(A.val), p, q, r);
+  const int grid = pcg_spmv_blocks(A);
+  auto k = A.stream ? k_pcg_spmv_dot<true> : k_pcg_spmv_dot<false>;
+  k<<<grid, kSpmvDotBlock, 0, s>>>(A.nslices, A.sptr, A.srow, reinterpret_cast<const int2*>(A.ci),
+                                   reinterpret_cast<const double2*>(A.val), p, q, r.partials + kSlotPQ * kMaxRedBlocks);
+  k_pcg_finish_pq<<<1, kFinishBlock, 0, s>>>(grid, r);
 }
 
 void launch_pcg_axpy_norm(int64_t n, double* x, double* rv, const double* p, const double* q,
@@ -566,17 +631,23 @@ void launch_pcg_axpy_norm(int64_t n, double* x, double* rv, const double* p, con
   k_pcg_axpy_norm<<<red_blocks(n), kBlock, 0, s>>>(n, x, rv, p, q, r);
 }
 
+void launch_pcg_finish_rr(int64_t n, const RedScratch& r, cudaStream_t s) {
+  k_pcg_finish_rr<<<1, kFinishBlock, 0, s>>>(red_blocks(n), r);
+}
+
 void launch_pcg_dots(int64_t n, const double* rv, const double* z, const double* q, int flexible,
                      const RedScratch& r, cudaStream_t s) {
   k_pcg_dots<<<red_blocks(n), kBlock, 0, s>>>(n, rv, z, q, flexible, r);
+  k_pcg_finish_dots<<<1, kFinishBlock, 0, s>>>(red_blocks(n), flexible, r);
 }
 
 void launch_pcg_update_p(int64_t n, double* p, const double* z, const RedScratch& r, cudaStream_t s) {
   k_pcg_update_p<<<vec_grid(n), kBlock, 0, s>>>(n, p, z, r);
 }
 
-void launch_pcg_loop_cond(cudaGraphConditionalHandle hw, const RedScratch& r, int* state, cudaStream_t s) {
-  k_pcg_loop_cond<<<1, 1, 0, s>>>(hw, r.sc, state);
+void launch_pcg_loop_cond(cudaGraphConditionalHandle hw, int64_t n, const RedScratch& r, int* state,
+                          cudaStream_t s) {
+  k_pcg_loop_cond<<<1, kFinishBlock, 0, s>>>(hw, red_blocks(n), r, state);
 }
 
 }  // namespace amge
