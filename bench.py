@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quick", action="store_true", help="headline loop only (for profiler runs)")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-dependent-launch", action="store_true",
+                   help="launch kernels without programmatic dependent launch (same results)")
     p.add_argument("--no-graphs", action="store_true",
                    help="host-launched PCG loop instead of the captured WHILE-node graph (same kernels)")
     p.add_argument("--precision-serve", choices=["fp32", "fp64"], default="fp32")
@@ -313,6 +315,8 @@ def run_ours(args, dist):
     hh, b = make_workload(wl)
     prec = amge.AMGE_FP32_VCYCLE if args.precision == "fp32" else amge.AMGE_FP64
     w = 4 if prec == amge.AMGE_FP32_VCYCLE else 8
+    if args.no_dependent_launch:
+        amge.amge_set_dependent_launch(False)
     h = amge.amge_setup_upload(hh)
     if args.no_graphs:
         amge.amge_set_graphs(h, False)
@@ -390,6 +394,8 @@ def run_ours(args, dist):
     line["kernels"] = kern
     tuned = amge.amge_autotune_report(h)
     line["autotune"] = {f"L{l}.{p}.{o}": v for (l, p, o), v in tuned.items() if v}
+    line["autotune_us"] = {f"L{l}.{p}.{o}": t for (l, p, o), t in amge.amge_autotune_times(h).items()
+                           if p == ("fp64" if w == 8 else "fp32")}
     line["kernel_timing"] = ("CUDA events around every launch, on the launching stream, over a second pass of the "
                              "same K steps right after the headline timed region")
     line["gpu_launches"] = int(sum(c for c, _ in launches.values()))

@@ -287,6 +287,13 @@ void amge_server_destroy(amge_server* s);
  * per-launch timing is enabled (amge_profile_enable), the host-launched loop is used. */
 amge_status amge_set_graphs(amge_hier* h, int32_t enable);
 
+/* Process-wide: launch kernels with programmatic dependent launch (default 1), so a
+ * kernel's blocks are scheduled while its predecessor in the stream finishes and
+ * wait on the device for its results; 0 launches them plainly.  Results are
+ * identical either way.  Applies to launches issued, and PCG graphs captured, after
+ * the call (call amge_set_kernel or re-upload to recapture an existing graph). */
+void amge_set_dependent_launch(int32_t enable);
+
 /* The autotuner's kernel choice for every smoothing level's single-vector products:
  * lanes[(l * 2 + p) * 6 + op] for level l < levels-1, precision p (0 FP64, 1 FP32),
  * op 0..5 = A, P, P^T, G, G^T, AG; 0 = sliced ELL (one row per lane, one warp per
@@ -297,6 +304,13 @@ amge_status amge_set_graphs(amge_hier* h, int32_t enable);
  * choice is made at upload by timing each candidate on the level's own operator.
  * lanes must hold (levels-1)*12 entries. */
 amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
+
+/* The autotuner's evidence: us[((l * 2 + p) * 6 + op) * 9 + c] = measured time per
+ * launch in microseconds (STORE epilogue, ten launches replayed from a graph, best of
+ * three) of candidate c in the order 0, 200, 400, 800, 2, 4, 8, 16, 32; -1 where a
+ * candidate was not measured (longer than the operator's rows) or the operator is
+ * not stored.  us must hold (levels-1)*108 floats. */
+amge_status amge_autotune_times(const amge_hier* h, float* us);
 
 /* Override one entry of that choice (level l < levels-1, precision 0/1, op 0..5 as
  * above; lanes = a kernel code as above: 0, 200, 400, 800 or 2, 4, 8, 16, 32).  Captured PCG graphs

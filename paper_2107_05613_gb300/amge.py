@@ -63,6 +63,7 @@ _SIGS = {
     "amge_set_graphs": [_vp, _i32],
     "amge_autotune_report": [_vp, ctypes.POINTER(_i32)],
     "amge_set_kernel": [_vp, _i32, _i32, _i32, _i32],
+    "amge_autotune_times": [_vp, ctypes.POINTER(ctypes.c_float)],
     "amge_server_create": [ctypes.c_size_t, _i32, ctypes.POINTER(_vp)],
     "amge_submit": [_vp, _vp, _vp, _vp, _i32, ctypes.POINTER(amge_solve_opts), ctypes.POINTER(ctypes.c_uint64)],
     "amge_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(amge_info)],
@@ -77,6 +78,8 @@ for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = ctypes.c_int
+_lib.amge_set_dependent_launch.argtypes = [_i32]
+_lib.amge_set_dependent_launch.restype = None
 _lib.amge_hier_free.argtypes = [_vp]
 _lib.amge_hier_free.restype = None
 _lib.amge_server_destroy.argtypes = [_vp]
@@ -231,6 +234,22 @@ def amge_autotune_report(h: Hier):
 
 
 OPS = ["A", "P", "PT", "G", "GT", "AG"]
+TUNE_CODES = [0, 200, 400, 800, 2, 4, 8, 16, 32]
+
+
+def amge_autotune_times(h: Hier):
+    """{(level, 'fp64'|'fp32', op): {code: us per launch}} as measured at upload."""
+    L = h.levels
+    buf = (ctypes.c_float * max((L - 1) * 108, 1))()
+    _check(_lib.amge_autotune_times(h.handle, buf), "amge_autotune_times")
+    out = {}
+    for l in range(L - 1):
+        for pi, p in enumerate(("fp64", "fp32")):
+            for o in range(6):
+                t = {c: round(float(buf[((l * 2 + pi) * 6 + o) * 9 + k]), 2) for k, c in enumerate(TUNE_CODES)}
+                if any(v >= 0 for v in t.values()):
+                    out[(l, p, OPS[o])] = {c: v for c, v in t.items() if v >= 0}
+    return out
 
 
 def amge_set_kernel(h: Hier, level: int, precision, op, lanes: int):
@@ -240,6 +259,11 @@ def amge_set_kernel(h: Hier, level: int, precision, op, lanes: int):
     p = {"fp64": 0, "fp32": 1}.get(precision, precision)
     o = OPS.index(op) if isinstance(op, str) else op
     _check(_lib.amge_set_kernel(h.handle, level, int(p), int(o), lanes), "amge_set_kernel")
+
+
+def amge_set_dependent_launch(enable: bool = True):
+    """Process-wide programmatic dependent launch of the library's kernels (default on)."""
+    _lib.amge_set_dependent_launch(int(enable))
 
 
 def amge_set_graphs(h: Hier, enable: bool = True):

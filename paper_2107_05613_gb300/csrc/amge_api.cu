@@ -32,6 +32,9 @@ struct LevelDev {
   // ELL, 100 w = sliced ELL with w warps per slice, 2..32 = vector CSR with that many
   // lanes per row, -1 = not stored
   int lanes[6] = {0, 0, 0, 0, 0, -1};
+  // the autotuner's measured time per launch (us) of each candidate (kTuneCodes
+  // order), -1 where not measured
+  float tune_us[6][9] = {};
   V* minv = nullptr;
   V* mauxinv = nullptr;
   V *x = nullptr, *r = nullptr, *y = nullptr, *tmp = nullptr;
@@ -155,12 +158,12 @@ void upload_sell(amge_hier* h, const HostCsr& M, DevSell<double>& d64, DevSell<f
   d64.nnz = d32.nnz = S.nnz;
   d64.unit = d32.unit = S.unit ? 1 : 0;
   d64.stored = d32.stored = S.sptr[S.nslices];
-  // operators well beyond L2 are streamed with the evict-first hint (32 MiB: a
-  // quarter of GB300's L2)
+  // operators well beyond L2 are streamed with the evict-first hint (over 64 MiB,
+  // half of GB300's L2: the finest level's; the coarser levels' stay cacheable)
   const double bytes64 = (double)d64.stored * (S.unit ? 4.0 : 12.0);
   const double bytes32 = (double)d32.stored * (S.unit ? 4.0 : 8.0);
-  d64.stream = bytes64 > 32.0 * (1 << 20) ? 1 : 0;
-  d32.stream = bytes32 > 32.0 * (1 << 20) ? 1 : 0;
+  d64.stream = bytes64 > 64.0 * (1 << 20) ? 1 : 0;
+  d32.stream = bytes32 > 64.0 * (1 << 20) ? 1 : 0;
   d64.sptr = d32.sptr = upload<int64_t>(h, S.sptr.data(), S.sptr.size(), s);
   d64.srow = d32.srow = upload<int>(h, S.srow.data(), S.srow.size(), s);
   d64.ci = d32.ci = upload<int>(h, S.ci.data(), S.ci.size(), s);
@@ -1064,6 +1067,8 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
 // Autotuner: time every candidate kernel of every level operator (sliced ELL and
 // vector CSR with 2..32 lanes per row, up to the operator's row length) on the work
 // vectors and keep the fastest; vector CSR must beat sliced ELL by 10% to be chosen.
+constexpr int kTuneCodes[9] = {0, 200, 400, 800, 2, 4, 8, 16, 32};
+
 template <typename V>
 amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   LevelDev<V>& d = levels<V>(h)[l];
@@ -1078,7 +1083,9 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
     const double avg = M.nr ? (double)M.nnz / M.nr : 0.0;
     float best = 0.f;
     int best_lanes = 0;
-    for (int lanes : {0, 200, 400, 800, 2, 4, 8, 16, 32}) {
+    for (int ci = 0; ci < 9; ci++) {
+      const int lanes = kTuneCodes[ci];
+      d.tune_us[op][ci] = -1.f;
       if (lanes >= 100 && 2.0 * (lanes / 100) > avg + 1.0) continue;  // more warps than entry pairs
       if (lanes > 2 && lanes < 100 && lanes > 2 * avg) continue;
       d.lanes[op] = lanes;
@@ -1106,6 +1113,7 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
       }
       cudaGraphExecDestroy(ge);
       CK(le);
+      d.tune_us[op][ci] = ms * 100.f;  // 10 launches: ms * 1e3 / 10
       if (lanes == 0 || ms < 0.9f * best) best = (lanes == 0 || ms < best) ? ms : best, best_lanes = lanes;
     }
     d.lanes[op] = best_lanes;
@@ -1661,6 +1669,20 @@ amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes) {
   return AMGE_OK;
 }
 
+amge_status amge_autotune_times(const amge_hier* h, float* us) {
+  if (!h || !us) {
+    set_error("NULL argument");
+    return AMGE_EINVAL;
+  }
+  for (int l = 0; l + 1 < h->L; l++)
+    for (int op = 0; op < 6; op++)
+      for (int c = 0; c < 9; c++) {
+        us[((l * 2 + 0) * 6 + op) * 9 + c] = h->lv64[l].lanes[op] < 0 ? -1.f : h->lv64[l].tune_us[op][c];
+        us[((l * 2 + 1) * 6 + op) * 9 + c] = h->lv32[l].lanes[op] < 0 ? -1.f : h->lv32[l].tune_us[op][c];
+      }
+  return AMGE_OK;
+}
+
 amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int32_t op, int32_t lanes) {
   if (!h) {
     set_error("NULL hierarchy");
@@ -1688,6 +1710,8 @@ amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int3
   }
   return AMGE_OK;
 }
+
+void amge_set_dependent_launch(int32_t enable) { set_dependent_launch(enable != 0); }
 
 amge_status amge_set_graphs(amge_hier* h, int32_t enable) {
   if (!h) {

@@ -12,6 +12,39 @@
 
 namespace amge {
 
+// Programmatic dependent launch.  Kernels are launched with programmatic stream
+// serialisation, and every kernel starts with pdl_begin(): wait until the previous
+// kernel in the stream has completed and its writes are visible (before touching
+// global memory), then allow the next kernel's blocks to be scheduled.  The next
+// kernel is therefore launched while this one's last blocks run, and its blocks fill
+// the SMs this kernel's tail leaves idle, instead of paying a launch gap and a ramp
+// per kernel; captured into a graph this becomes a programmatic edge.  Without the
+// launch attribute both instructions are no-ops.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
+// Process-wide switch (default on) read when a kernel is launched or captured.
+bool dependent_launch_enabled();
+void set_dependent_launch(bool on);
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = dependent_launch_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 void set_error(const std::string& msg);
 
 // Host CSR in FP64 (setup side).
@@ -51,7 +84,7 @@ template <typename V>
 struct DevSell {
   int nr = 0, nc = 0, nslices = 0;
   int unit = 0;    // sign-coded columns (val == nullptr)
-  int stream = 0;  // larger than a quarter of L2: entries are read with the evict-first hint
+  int stream = 0;  // larger than half of L2: entries are read with the evict-first hint
   int64_t nnz = 0, stored = 0;
   int64_t* sptr = nullptr;
   int* srow = nullptr;

@@ -109,6 +109,7 @@ template <typename V, int EPI, int WPS, bool UNIT, bool CS>
 __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __restrict__ sptr,
                                                  const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                  const typename Pair<V>::T* __restrict__ val2, SpmvArgs<V> a) {
+  pdl_begin();
   constexpr bool NEG = SellNeg<EPI>::value;
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -160,6 +161,7 @@ template <typename V, bool POST, bool CS>
 __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t* __restrict__ sptr,
                                                      const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                      const typename Pair<V>::T* __restrict__ val2, AgArgs<V> a) {
+  pdl_begin();
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= nslices) return;
@@ -196,6 +198,7 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
 template <typename V, int LANES, int EPI>
 __global__ void __launch_bounds__(kBlock) k_csrv(int nr, const int* __restrict__ rp, const int* __restrict__ ci,
                                                  const V* __restrict__ val, SpmvArgs<V> a) {
+  pdl_begin();
   const int gt = blockIdx.x * kBlock + threadIdx.x;
   const int row = gt / LANES;
   const int lane = gt & (LANES - 1);
@@ -231,12 +234,14 @@ __global__ void __launch_bounds__(kBlock) k_csrv(int nr, const int* __restrict__
 
 template <typename V>
 __global__ void k_mul(int64_t n, const V* __restrict__ d, const V* __restrict__ x, V* __restrict__ y) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = d[i] * x[i];
 }
 
 template <typename Tin, typename Tout>
 __global__ void k_cast(int64_t n, const Tin* __restrict__ in, Tout* __restrict__ out) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (Tout)in[i];
 }
@@ -245,6 +250,7 @@ __global__ void k_cast(int64_t n, const Tin* __restrict__ in, Tout* __restrict__
 template <bool LOWER, typename Tin, typename Tout>
 __global__ void __launch_bounds__(kBlock) k_trimv(int n, const double* __restrict__ M, const Tin* __restrict__ x,
                                                   Tout* __restrict__ y) {
+  pdl_begin();
   const int row = (blockIdx.x * kBlock + threadIdx.x) / 32;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;  // whole warp shares the row
@@ -309,6 +315,7 @@ constexpr int kFinishBlock = 1024;
 // Dot product: block partials, then one block sums them in index order.
 __global__ void __launch_bounds__(kBlock, 8) k_dot(int64_t n, const double* __restrict__ x,
                                                    const double* __restrict__ y, RedScratch r) {
+  pdl_begin();
   __shared__ double sh[kBlock];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
@@ -327,6 +334,7 @@ __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, 
                                                                    const double2* __restrict__ val2,
                                                                    const double* __restrict__ p,
                                                                    double* __restrict__ q, double* part) {
+  pdl_begin();
   __shared__ double sh[kSpmvDotBlock];
   __shared__ unsigned arrived;
   if (threadIdx.x == 0) arrived = 0u;
@@ -371,6 +379,7 @@ __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, 
 
 // pq = p.q from the partials; alpha = rho / pq.
 __global__ void __launch_bounds__(kFinishBlock) k_pcg_finish_pq(int npq, RedScratch r) {
+  pdl_begin();
   __shared__ double sh[kFinishBlock];
   const double pq = sum_partials<kFinishBlock>(r.partials + kSlotPQ * kMaxRedBlocks, npq, sh);
   if (threadIdx.x == 0) {
@@ -380,6 +389,7 @@ __global__ void __launch_bounds__(kFinishBlock) k_pcg_finish_pq(int npq, RedScra
 }
 
 __global__ void __launch_bounds__(kFinishBlock) k_finish_dot(int nred, RedScratch r, double* out) {
+  pdl_begin();
   __shared__ double sh[kFinishBlock];
   const double t = sum_partials<kFinishBlock>(r.partials + kSlotDot * kMaxRedBlocks, nred, sh);
   if (threadIdx.x == 0) *out = t;
@@ -389,6 +399,7 @@ __global__ void __launch_bounds__(kFinishBlock) k_finish_dot(int nred, RedScratc
 __global__ void __launch_bounds__(kBlock, 8) k_pcg_axpy_norm(int64_t n, double* __restrict__ x,
                                                              double* __restrict__ rv, const double* __restrict__ p,
                                                              const double* __restrict__ q, RedScratch r) {
+  pdl_begin();
   __shared__ double sh[kBlock];
   const double alpha = r.sc[SC_ALPHA];
   double acc = 0.0;
@@ -403,6 +414,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_pcg_axpy_norm(int64_t n, double* 
 
 // ||r||^2 -> SC_RR (host-driven loop).
 __global__ void __launch_bounds__(kFinishBlock) k_pcg_finish_rr(int nrr, RedScratch r) {
+  pdl_begin();
   __shared__ double sh[kFinishBlock];
   const double rr = sum_partials<kFinishBlock>(r.partials + kSlotRR * kMaxRedBlocks, nrr, sh);
   if (threadIdx.x == 0) r.sc[SC_RR] = rr;
@@ -412,6 +424,7 @@ __global__ void __launch_bounds__(kFinishBlock) k_pcg_finish_rr(int nrr, RedScra
 __global__ void __launch_bounds__(kBlock, 8) k_pcg_dots(int64_t n, const double* __restrict__ rv,
                                                         const double* __restrict__ z, const double* __restrict__ q,
                                                         int flexible, RedScratch r) {
+  pdl_begin();
   __shared__ double sh[kBlock];
   double acc0 = 0.0, acc1 = 0.0;
   if (flexible) {
@@ -430,6 +443,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_pcg_dots(int64_t n, const double*
 
 // rho_new = r.z, zq = z.q; beta = rho_new / rho or -alpha zq / rho.
 __global__ void __launch_bounds__(kFinishBlock) k_pcg_finish_dots(int nred, int flexible, RedScratch r) {
+  pdl_begin();
   __shared__ double sh[kFinishBlock];
   const double rz = sum_partials<kFinishBlock>(r.partials + kSlotRZ * kMaxRedBlocks, nred, sh);
   const double zq = flexible ? sum_partials<kFinishBlock>(r.partials + kSlotZQ * kMaxRedBlocks, nred, sh) : 0.0;
@@ -444,6 +458,7 @@ __global__ void __launch_bounds__(kFinishBlock) k_pcg_finish_dots(int nred, int 
 // p = z + beta p; rho = rho_new.
 __global__ void __launch_bounds__(kBlock, 8) k_pcg_update_p(int64_t n, double* __restrict__ p,
                                                             const double* __restrict__ z, RedScratch r) {
+  pdl_begin();
   const double beta = r.sc[SC_BETA];
   for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
     p[i] = fma(beta, p[i], z[i]);
@@ -453,6 +468,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_pcg_update_p(int64_t n, double* _
 // One block: ||r||^2 from the axpy partials, then the WHILE condition.
 __global__ void __launch_bounds__(kFinishBlock) k_pcg_loop_cond(cudaGraphConditionalHandle hw, int nrr, RedScratch r,
                                                                 int* state) {
+  pdl_begin();
   __shared__ double sh[kFinishBlock];
   const double rr = sum_partials<kFinishBlock>(r.partials + kSlotRR * kMaxRedBlocks, nrr, sh);
   if (threadIdx.x != 0) return;
@@ -489,6 +505,12 @@ int vec_grid(int64_t n) {
 
 }  // namespace
 
+namespace {
+std::atomic<bool> g_dependent_launch{true};
+}
+bool dependent_launch_enabled() { return g_dependent_launch.load(std::memory_order_relaxed); }
+void set_dependent_launch(bool on) { g_dependent_launch.store(on, std::memory_order_relaxed); }
+
 int red_blocks(int64_t n) {
   int64_t g = (n + 4 * kBlock - 1) / (4 * kBlock);
   return (int)std::min<int64_t>(std::max<int64_t>(g, 1), resident_blocks());
@@ -501,13 +523,13 @@ static void launch_sell_t(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cu
   const int2* ci2 = reinterpret_cast<const int2*>(M.ci);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(M.val);
   switch (epi) {
-    case EPI_STORE: k_sell<V, EPI_STORE, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_RESID: k_sell<V, EPI_RESID, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_SCALE: k_sell<V, EPI_SCALE, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_ADD: k_sell<V, EPI_ADD, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_SWEEP: k_sell<V, EPI_SWEEP, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_STORE: launch_k(k_sell<V, EPI_STORE, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_RESID: launch_k(k_sell<V, EPI_RESID, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SCALE: launch_k(k_sell<V, EPI_SCALE, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_ADD: launch_k(k_sell<V, EPI_ADD, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SWEEP: launch_k(k_sell<V, EPI_SWEEP, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
     case EPI_STORE_MUL:
-      k_sell<V, EPI_STORE_MUL, WPS, UNIT, CS><<<grid, kBlock, 0, s>>>(M.nslices, M.sptr, M.srow, ci2, v2, a);
+      launch_k(k_sell<V, EPI_STORE_MUL, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a);
       break;
   }
 }
@@ -539,12 +561,12 @@ static void launch_csrv_lanes(const DevCsr<V>& M, int epi, const SpmvArgs<V>& a,
   const int grid = (int)(((int64_t)M.nr * LANES + kBlock - 1) / kBlock);
   if (grid == 0) return;
   switch (epi) {
-    case EPI_STORE: k_csrv<V, LANES, EPI_STORE><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
-    case EPI_RESID: k_csrv<V, LANES, EPI_RESID><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
-    case EPI_SCALE: k_csrv<V, LANES, EPI_SCALE><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
-    case EPI_ADD: k_csrv<V, LANES, EPI_ADD><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
-    case EPI_SWEEP: k_csrv<V, LANES, EPI_SWEEP><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
-    case EPI_STORE_MUL: k_csrv<V, LANES, EPI_STORE_MUL><<<grid, kBlock, 0, s>>>(M.nr, M.rp, M.ci, M.val, a); break;
+    case EPI_STORE: launch_k(k_csrv<V, LANES, EPI_STORE>, grid, kBlock, s, M.nr, M.rp, M.ci, M.val, a); break;
+    case EPI_RESID: launch_k(k_csrv<V, LANES, EPI_RESID>, grid, kBlock, s, M.nr, M.rp, M.ci, M.val, a); break;
+    case EPI_SCALE: launch_k(k_csrv<V, LANES, EPI_SCALE>, grid, kBlock, s, M.nr, M.rp, M.ci, M.val, a); break;
+    case EPI_ADD: launch_k(k_csrv<V, LANES, EPI_ADD>, grid, kBlock, s, M.nr, M.rp, M.ci, M.val, a); break;
+    case EPI_SWEEP: launch_k(k_csrv<V, LANES, EPI_SWEEP>, grid, kBlock, s, M.nr, M.rp, M.ci, M.val, a); break;
+    case EPI_STORE_MUL: launch_k(k_csrv<V, LANES, EPI_STORE_MUL>, grid, kBlock, s, M.nr, M.rp, M.ci, M.val, a); break;
   }
 }
 
@@ -568,11 +590,11 @@ void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStr
   const int2* ci2 = reinterpret_cast<const int2*>(AG.ci);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(AG.val);
   if (AG.stream) {
-    if (post) k_ag_fused<V, true, true><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
-    else k_ag_fused<V, false, true><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+    if (post) launch_k(k_ag_fused<V, true, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+    else launch_k(k_ag_fused<V, false, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
   } else {
-    if (post) k_ag_fused<V, true, false><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
-    else k_ag_fused<V, false, false><<<grid, kBlock, 0, s>>>(AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+    if (post) launch_k(k_ag_fused<V, true, false>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+    else launch_k(k_ag_fused<V, false, false>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
   }
 }
 template void launch_ag_fused<double>(const DevSell<double>&, int, const AgArgs<double>&, cudaStream_t);
@@ -583,14 +605,14 @@ template void launch_sell<float>(const DevSell<float>&, int, const SpmvArgs<floa
 
 template <typename V>
 void launch_mul(int64_t n, const V* d, const V* x, V* y, cudaStream_t s) {
-  if (n > 0) k_mul<V><<<vec_grid(n), kBlock, 0, s>>>(n, d, x, y);
+  if (n > 0) launch_k(k_mul<V>, vec_grid(n), kBlock, s, n, d, x, y);
 }
 template void launch_mul<double>(int64_t, const double*, const double*, double*, cudaStream_t);
 template void launch_mul<float>(int64_t, const float*, const float*, float*, cudaStream_t);
 
 template <typename Tin, typename Tout>
 void launch_cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s) {
-  if (n > 0) k_cast<Tin, Tout><<<vec_grid(n), kBlock, 0, s>>>(n, in, out);
+  if (n > 0) launch_k(k_cast<Tin, Tout>, vec_grid(n), kBlock, s, n, in, out);
 }
 template void launch_cast<double, float>(int64_t, const double*, float*, cudaStream_t);
 template void launch_cast<float, double>(int64_t, const float*, double*, cudaStream_t);
@@ -599,8 +621,8 @@ template <typename Tin, typename Tout>
 void launch_coarse(int n, const double* Linv, const double* LinvT, const Tin* b, double* t, Tout* z,
                    cudaStream_t s) {
   const int grid = (n * 32 + kBlock - 1) / kBlock;
-  k_trimv<true, Tin, double><<<grid, kBlock, 0, s>>>(n, Linv, b, t);
-  k_trimv<false, double, Tout><<<grid, kBlock, 0, s>>>(n, LinvT, t, z);
+  launch_k(k_trimv<true, Tin, double>, grid, kBlock, s, n, Linv, b, t);
+  launch_k(k_trimv<false, double, Tout>, grid, kBlock, s, n, LinvT, t, z);
 }
 template void launch_coarse<double, double>(int, const double*, const double*, const double*, double*, double*,
                                             cudaStream_t);
@@ -608,8 +630,8 @@ template void launch_coarse<float, float>(int, const double*, const double*, con
                                           cudaStream_t);
 
 void launch_dot(int64_t n, const double* x, const double* y, double* out, const RedScratch& r, cudaStream_t s) {
-  k_dot<<<red_blocks(n), kBlock, 0, s>>>(n, x, y, r);
-  k_finish_dot<<<1, kFinishBlock, 0, s>>>(red_blocks(n), r, out);
+  launch_k(k_dot, red_blocks(n), kBlock, s, n, x, y, r);
+  launch_k(k_finish_dot, 1, kFinishBlock, s, red_blocks(n), r, out);
 }
 
 int pcg_spmv_blocks(const DevSell<double>& A) {
@@ -621,33 +643,33 @@ void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, c
                          cudaStream_t s) {
   const int grid = pcg_spmv_blocks(A);
   auto k = A.stream ? k_pcg_spmv_dot<true> : k_pcg_spmv_dot<false>;
-  k<<<grid, kSpmvDotBlock, 0, s>>>(A.nslices, A.sptr, A.srow, reinterpret_cast<const int2*>(A.ci),
+  launch_k(k, grid, kSpmvDotBlock, s, A.nslices, A.sptr, A.srow, reinterpret_cast<const int2*>(A.ci),
                                    reinterpret_cast<const double2*>(A.val), p, q, r.partials + kSlotPQ * kMaxRedBlocks);
-  k_pcg_finish_pq<<<1, kFinishBlock, 0, s>>>(grid, r);
+  launch_k(k_pcg_finish_pq, 1, kFinishBlock, s, grid, r);
 }
 
 void launch_pcg_axpy_norm(int64_t n, double* x, double* rv, const double* p, const double* q,
                           const RedScratch& r, cudaStream_t s) {
-  k_pcg_axpy_norm<<<red_blocks(n), kBlock, 0, s>>>(n, x, rv, p, q, r);
+  launch_k(k_pcg_axpy_norm, red_blocks(n), kBlock, s, n, x, rv, p, q, r);
 }
 
 void launch_pcg_finish_rr(int64_t n, const RedScratch& r, cudaStream_t s) {
-  k_pcg_finish_rr<<<1, kFinishBlock, 0, s>>>(red_blocks(n), r);
+  launch_k(k_pcg_finish_rr, 1, kFinishBlock, s, red_blocks(n), r);
 }
 
 void launch_pcg_dots(int64_t n, const double* rv, const double* z, const double* q, int flexible,
                      const RedScratch& r, cudaStream_t s) {
-  k_pcg_dots<<<red_blocks(n), kBlock, 0, s>>>(n, rv, z, q, flexible, r);
-  k_pcg_finish_dots<<<1, kFinishBlock, 0, s>>>(red_blocks(n), flexible, r);
+  launch_k(k_pcg_dots, red_blocks(n), kBlock, s, n, rv, z, q, flexible, r);
+  launch_k(k_pcg_finish_dots, 1, kFinishBlock, s, red_blocks(n), flexible, r);
 }
 
 void launch_pcg_update_p(int64_t n, double* p, const double* z, const RedScratch& r, cudaStream_t s) {
-  k_pcg_update_p<<<vec_grid(n), kBlock, 0, s>>>(n, p, z, r);
+  launch_k(k_pcg_update_p, vec_grid(n), kBlock, s, n, p, z, r);
 }
 
 void launch_pcg_loop_cond(cudaGraphConditionalHandle hw, int64_t n, const RedScratch& r, int* state,
                           cudaStream_t s) {
-  k_pcg_loop_cond<<<1, kFinishBlock, 0, s>>>(hw, red_blocks(n), r, state);
+  launch_k(k_pcg_loop_cond, 1, kFinishBlock, s, hw, red_blocks(n), r, state);
 }
 
 }  // namespace amge

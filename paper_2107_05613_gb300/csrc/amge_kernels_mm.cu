@@ -27,6 +27,7 @@ template <typename V, int K, int EPI>
 __global__ void __launch_bounds__(kBlock) k_csr_mm(int nr, int nrhs, const int* __restrict__ rp,
                                                    const int* __restrict__ ci, const V* __restrict__ val,
                                                    SpmvArgs<V> a) {
+  pdl_begin();
   const int gt = blockIdx.x * kBlock + threadIdx.x;
   const int row = gt / K;
   const int c = gt & (K - 1);
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(kBlock) k_csr_mm(int nr, int nrhs, const int* 
 
 template <typename V>
 __global__ void k_mul_mm(int64_t n, int nrhs, const V* __restrict__ d, const V* __restrict__ x, V* __restrict__ y) {
+  pdl_begin();
   const int64_t tot = n * nrhs;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x)
     y[e] = d[e / nrhs] * x[e];
@@ -63,6 +65,7 @@ __global__ void k_mul_mm(int64_t n, int nrhs, const V* __restrict__ d, const V* 
 template <bool LOWER, typename Tin, typename Tout>
 __global__ void __launch_bounds__(kBlock) k_trimm(int n, int nrhs, const double* __restrict__ M,
                                                   const Tin* __restrict__ x, Tout* __restrict__ y) {
+  pdl_begin();
   const int row = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int c = threadIdx.x & 31;
   if (row >= n || c >= nrhs) return;
@@ -134,6 +137,7 @@ __device__ __forceinline__ double* scol(const RedScratchMM& r, int idx) { return
 template <int K>
 __global__ void __launch_bounds__(kBlock) k_dot_mm(int64_t n, int nrhs, const double* __restrict__ x,
                                                    const double* __restrict__ y, int sc_index, RedScratchMM r) {
+  pdl_begin();
   const int c = threadIdx.x & (K - 1);
   const int64_t groups = (int64_t)gridDim.x * (kBlock / K);
   double acc = 0.0;
@@ -150,6 +154,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mm_spmv_dot(int nr, int nrhs, co
                                                             const double* __restrict__ val,
                                                             const double* __restrict__ p, double* __restrict__ q,
                                                             RedScratchMM r) {
+  pdl_begin();
   const int c = threadIdx.x & (K - 1);
   const int groups = gridDim.x * (kBlock / K);
   double contrib = 0.0;
@@ -179,6 +184,7 @@ template <int K>
 __global__ void __launch_bounds__(kBlock) k_pcg_mm_axpy_norm(int64_t n, int nrhs, double* __restrict__ x,
                                                              double* __restrict__ rv, const double* __restrict__ p,
                                                              const double* __restrict__ q, RedScratchMM r) {
+  pdl_begin();
   const int c = threadIdx.x & (K - 1);
   const int64_t groups = (int64_t)gridDim.x * (kBlock / K);
   double acc = 0.0;
@@ -200,6 +206,7 @@ template <int K>
 __global__ void __launch_bounds__(kBlock) k_pcg_mm_dots(int64_t n, int nrhs, const double* __restrict__ rv,
                                                         const double* __restrict__ z, const double* __restrict__ q,
                                                         int flexible, RedScratchMM r) {
+  pdl_begin();
   const int c = threadIdx.x & (K - 1);
   const int64_t groups = (int64_t)gridDim.x * (kBlock / K);
   double acc[2] = {0.0, 0.0};
@@ -223,6 +230,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mm_dots(int64_t n, int nrhs, con
 
 __global__ void __launch_bounds__(kBlock) k_pcg_mm_update_p(int64_t n, int nrhs, double* __restrict__ p,
                                                             const double* __restrict__ z, RedScratchMM r) {
+  pdl_begin();
   const int64_t tot = n * nrhs;
   for (int64_t e = blockIdx.x * (int64_t)kBlock + threadIdx.x; e < tot; e += (int64_t)gridDim.x * kBlock)
     p[e] = fma(scol(r, SC_BETA)[e % nrhs], p[e], z[e]);
@@ -269,11 +277,11 @@ void launch_csr_mm(const DevCsr<V>& M, int nrhs, int epi, const SpmvArgs<V>& a, 
   dispatch_k(K, [&](auto kk) {
     constexpr int KK = decltype(kk)::value;
     switch (epi) {
-      case EPI_STORE: k_csr_mm<V, KK, EPI_STORE><<<grid, kBlock, 0, s>>>(M.nr, nrhs, M.rp, M.ci, M.val, a); break;
-      case EPI_RESID: k_csr_mm<V, KK, EPI_RESID><<<grid, kBlock, 0, s>>>(M.nr, nrhs, M.rp, M.ci, M.val, a); break;
-      case EPI_SCALE: k_csr_mm<V, KK, EPI_SCALE><<<grid, kBlock, 0, s>>>(M.nr, nrhs, M.rp, M.ci, M.val, a); break;
-      case EPI_ADD: k_csr_mm<V, KK, EPI_ADD><<<grid, kBlock, 0, s>>>(M.nr, nrhs, M.rp, M.ci, M.val, a); break;
-      case EPI_SWEEP: k_csr_mm<V, KK, EPI_SWEEP><<<grid, kBlock, 0, s>>>(M.nr, nrhs, M.rp, M.ci, M.val, a); break;
+      case EPI_STORE: launch_k(k_csr_mm<V, KK, EPI_STORE>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, M.val, a); break;
+      case EPI_RESID: launch_k(k_csr_mm<V, KK, EPI_RESID>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, M.val, a); break;
+      case EPI_SCALE: launch_k(k_csr_mm<V, KK, EPI_SCALE>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, M.val, a); break;
+      case EPI_ADD: launch_k(k_csr_mm<V, KK, EPI_ADD>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, M.val, a); break;
+      case EPI_SWEEP: launch_k(k_csr_mm<V, KK, EPI_SWEEP>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, M.val, a); break;
     }
   });
 }
@@ -282,7 +290,7 @@ template void launch_csr_mm<float>(const DevCsr<float>&, int, int, const SpmvArg
 
 template <typename V>
 void launch_mul_mm(int64_t n, int nrhs, const V* d, const V* x, V* y, cudaStream_t s) {
-  if (n > 0) k_mul_mm<V><<<grid_for(n * nrhs), kBlock, 0, s>>>(n, nrhs, d, x, y);
+  if (n > 0) launch_k(k_mul_mm<V>, grid_for(n * nrhs), kBlock, s, n, nrhs, d, x, y);
 }
 template void launch_mul_mm<double>(int64_t, int, const double*, const double*, double*, cudaStream_t);
 template void launch_mul_mm<float>(int64_t, int, const float*, const float*, float*, cudaStream_t);
@@ -291,8 +299,8 @@ template <typename Tin, typename Tout>
 void launch_coarse_mm(int n, int nrhs, const double* Linv, const double* LinvT, const Tin* b, double* t, Tout* z,
                       cudaStream_t s) {
   const int grid = (n * 32 + kBlock - 1) / kBlock;
-  k_trimm<true, Tin, double><<<grid, kBlock, 0, s>>>(n, nrhs, Linv, b, t);
-  k_trimm<false, double, Tout><<<grid, kBlock, 0, s>>>(n, nrhs, LinvT, t, z);
+  launch_k(k_trimm<true, Tin, double>, grid, kBlock, s, n, nrhs, Linv, b, t);
+  launch_k(k_trimm<false, double, Tout>, grid, kBlock, s, n, nrhs, LinvT, t, z);
 }
 template void launch_coarse_mm<double, double>(int, int, const double*, const double*, const double*, double*,
                                                double*, cudaStream_t);
@@ -303,7 +311,7 @@ void launch_dot_mm(int64_t n, int nrhs, const double* x, const double* y, int sc
                    cudaStream_t s) {
   dispatch_k(pow2_at_least(nrhs), [&](auto kk) {
     constexpr int KK = decltype(kk)::value;
-    k_dot_mm<KK><<<mm_red_blocks(n, KK), kBlock, 0, s>>>(n, nrhs, x, y, sc_index, r);
+    launch_k(k_dot_mm<KK>, mm_red_blocks(n, KK), kBlock, s, n, nrhs, x, y, sc_index, r);
   });
 }
 
@@ -311,7 +319,7 @@ void launch_pcg_mm_spmv_dot(const DevCsr<double>& A, int nrhs, const double* p, 
                             cudaStream_t s) {
   dispatch_k(pow2_at_least(nrhs), [&](auto kk) {
     constexpr int KK = decltype(kk)::value;
-    k_pcg_mm_spmv_dot<KK><<<mm_red_blocks(A.nr, KK), kBlock, 0, s>>>(A.nr, nrhs, A.rp, A.ci, A.val, p, q, r);
+    launch_k(k_pcg_mm_spmv_dot<KK>, mm_red_blocks(A.nr, KK), kBlock, s, A.nr, nrhs, A.rp, A.ci, A.val, p, q, r);
   });
 }
 
@@ -319,7 +327,7 @@ void launch_pcg_mm_axpy_norm(int64_t n, int nrhs, double* x, double* rv, const d
                              const RedScratchMM& r, cudaStream_t s) {
   dispatch_k(pow2_at_least(nrhs), [&](auto kk) {
     constexpr int KK = decltype(kk)::value;
-    k_pcg_mm_axpy_norm<KK><<<mm_red_blocks(n, KK), kBlock, 0, s>>>(n, nrhs, x, rv, p, q, r);
+    launch_k(k_pcg_mm_axpy_norm<KK>, mm_red_blocks(n, KK), kBlock, s, n, nrhs, x, rv, p, q, r);
   });
 }
 
@@ -327,13 +335,13 @@ void launch_pcg_mm_dots(int64_t n, int nrhs, const double* rv, const double* z, 
                         const RedScratchMM& r, cudaStream_t s) {
   dispatch_k(pow2_at_least(nrhs), [&](auto kk) {
     constexpr int KK = decltype(kk)::value;
-    k_pcg_mm_dots<KK><<<mm_red_blocks(n, KK), kBlock, 0, s>>>(n, nrhs, rv, z, q, flexible, r);
+    launch_k(k_pcg_mm_dots<KK>, mm_red_blocks(n, KK), kBlock, s, n, nrhs, rv, z, q, flexible, r);
   });
 }
 
 void launch_pcg_mm_update_p(int64_t n, int nrhs, double* p, const double* z, const RedScratchMM& r,
                             cudaStream_t s) {
-  k_pcg_mm_update_p<<<grid_for(n * nrhs), kBlock, 0, s>>>(n, nrhs, p, z, r);
+  launch_k(k_pcg_mm_update_p, grid_for(n * nrhs), kBlock, s, n, nrhs, p, z, r);
 }
 
 }  // namespace amge

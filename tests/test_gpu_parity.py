@@ -149,6 +149,41 @@ def test_fused_aux_correction_equals_separate_products(amge, prec):
     assert torch.isfinite(zf).all() and torch.equal(zf, zs)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_dependent_launch_does_not_change_results(amge, prec):
+    """Programmatic dependent launch only changes when blocks are scheduled: the
+    V-cycle and the graph-driven PCG give identical results with it on and off."""
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    b = dev(rhs_vector(79, hierarchy("hcurl", 24, 3, True).A[0].shape[0]))
+    out = []
+    try:
+        for on in (True, False):
+            amge.amge_set_dependent_launch(on)
+            h = amge.amge_setup_upload(hierarchy("hcurl", 24, 3, True))
+            rep = amge.amge_autotune_report(h)
+            out.append((h, rep))
+    finally:
+        amge.amge_set_dependent_launch(True)
+    (h1, rep1), (h0, rep0) = out
+    for (l, p, o), v in rep1.items():      # same kernels on both
+        if v >= 0:
+            amge.amge_set_kernel(h0, l, p, o, v)
+    amge.amge_set_dependent_launch(False)
+    try:
+        z0, x0 = torch.empty_like(b), torch.empty_like(b)
+        amge.amge_vcycle(h0, b, z0, precision=prec)
+        st0, i0 = amge.amge_pcg_solve(h0, b, x0, precision=prec)
+    finally:
+        amge.amge_set_dependent_launch(True)
+    z1, x1 = torch.empty_like(b), torch.empty_like(b)
+    amge.amge_vcycle(h1, b, z1, precision=prec)
+    st1, i1 = amge.amge_pcg_solve(h1, b, x1, precision=prec)
+    torch.cuda.synchronize()
+    assert st0 == st1 == amge.AMGE_OK and i0[0]["iters"] == i1[0]["iters"]
+    assert torch.equal(z0, z1) and torch.equal(x0, x1)
+
+
 def test_set_kernel_rebuilds_graph_and_rejects_bad_input(amge):
     """A pinned kernel choice takes effect in the captured PCG graph (rebuilt on the
     next solve): results move by rounding only and the solve still matches the oracle."""
