@@ -46,7 +46,7 @@ WORKLOADS = {
 # dram__bytes_read.sum + dram__bytes_write.sum of one level-0 residual sweep from an
 # ncu capture (profiles/k_sell_fp64_resid_level0_hcurl64.md); only for that kernel
 # and workload, null elsewhere.
-NCU_TRAFFIC = {("hcurl64", 8): 441.7e6}
+NCU_TRAFFIC = {("hcurl64", 8): 432.5e6}
 
 HBM_FALLBACK_GBS = 6800.0
 METRIC = "PCG solves/s to 1e-8 rel residual"
@@ -66,6 +66,9 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-dependent-launch", action="store_true",
                    help="launch kernels without programmatic dependent launch (same results)")
+    p.add_argument("--kernels-from", default=None,
+                   help="pin the kernel choices recorded ('autotune') in an earlier bench JSON line, "
+                        "e.g. for a profiler run, whose timing would sway the autotuner")
     p.add_argument("--no-graphs", action="store_true",
                    help="host-launched PCG loop instead of the captured WHILE-node graph (same kernels)")
     p.add_argument("--precision-serve", choices=["fp32", "fp64"], default="fp32")
@@ -318,6 +321,12 @@ def run_ours(args, dist):
     if args.no_dependent_launch:
         amge.amge_set_dependent_launch(False)
     h = amge.amge_setup_upload(hh)
+    if args.kernels_from:
+        with open(args.kernels_from) as f:
+            chosen = json.loads(f.read().strip().splitlines()[-1])["autotune"]
+        for (l, p, o), v in amge.amge_autotune_report(h).items():
+            if v >= 0:
+                amge.amge_set_kernel(h, l, p, o, int(chosen.get(f"L{l}.{p}.{o}", 0)))
     if args.no_graphs:
         amge.amge_set_graphs(h, False)
     n = h.n
