@@ -403,17 +403,21 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
   }
 }
 
-void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, cudaStream_t s) {
+// z = B r.  x0_ready (h->L > 1 only): the level-0 sweep from zero, x = m^-1 r, is
+// already in the level-0 x (and, for the FP32 V-cycle, r already cast into the
+// level-0 b) -- written by the PCG axpy that produced r (pcg_x0_out).
+void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, cudaStream_t s,
+                       bool x0_ready = false) {
   if (precision == AMGE_FP64) {
     if (h->L == 1) {
       Prof p(h, AMGE_PROF_COARSE, s, 2);
       launch_coarse<double, double>(h->nC, h->Linv, h->LinvT, r, h->ct, z, s);
       return;
     }
-    vcycle_level<double>(h, 0, r, z, s);
+    vcycle_level<double>(h, 0, r, z, s, x0_ready);
   } else {
     LevelDev<float>& d = h->lv32[0];
-    {
+    if (!x0_ready) {
       Prof p(h, AMGE_PROF_PCG_VEC, s);
       launch_cast<double, float>(h->n0, r, d.b, s);
     }
@@ -421,10 +425,40 @@ void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, 
       Prof p(h, AMGE_PROF_COARSE, s, 2);
       launch_coarse<float, float>(h->nC, h->Linv, h->LinvT, d.b, h->ct, d.z, s);
     } else {
-      vcycle_level<float>(h, 0, d.b, d.z, s);
+      vcycle_level<float>(h, 0, d.b, d.z, s, x0_ready);
     }
     Prof p(h, AMGE_PROF_PCG_VEC, s);
     launch_cast<float, double>(h->n0, d.z, z, s);
+  }
+}
+
+// The extra outputs of the PCG axpy that start the next V-cycle (see X0Out); none for
+// a one-level hierarchy.
+X0Out pcg_x0_out(amge_hier* h, int precision) {
+  X0Out o;
+  if (h->L == 1) return o;
+  if (precision == AMGE_FP64) {
+    o.mode = 1;
+    o.minv64 = h->lv64[0].minv;
+    o.x64 = h->lv64[0].x;
+  } else {
+    o.mode = 2;
+    o.minv32 = h->lv32[0].minv;
+    o.r32 = h->lv32[0].b;
+    o.x32 = h->lv32[0].x;
+  }
+  return o;
+}
+
+// The same start computed from r alone (after the true residual replaced r).
+void pcg_x0_from_r(amge_hier* h, const double* r, int precision, cudaStream_t s) {
+  if (h->L == 1) return;
+  Prof p(h, AMGE_PROF_VCYCLE_VEC, s, precision == AMGE_FP64 ? 1 : 2);
+  if (precision == AMGE_FP64) {
+    launch_mul<double>(h->n0, h->lv64[0].minv, r, h->lv64[0].x, s);
+  } else {
+    launch_cast<double, float>(h->n0, r, h->lv32[0].b, s);
+    launch_mul<float>(h->n0, h->lv32[0].minv, h->lv32[0].b, h->lv32[0].x, s);
   }
 }
 
@@ -452,12 +486,14 @@ amge_status build_pcg_graph(amge_hier* h, int prec) {
   const bool prof = h->prof;
   h->prof = false;  // event records are not allowed inside conditional bodies
   CK(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  vcycle_fp64_iface(h, h->pr, h->pz, prec, h->cap);
+  // every body starts from an r produced by the axpy (or by the restart after a true
+  // residual), which already began the level-0 sweep
+  vcycle_fp64_iface(h, h->pr, h->pz, prec, h->cap, h->L > 1);
   const int flexible = prec == AMGE_FP32_VCYCLE ? 1 : 0;
   launch_pcg_dots(n, h->pr, h->pz, h->pq, flexible, h->red, h->cap);
   launch_pcg_update_p(n, h->pp, h->pz, h->red, h->cap);
   launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, h->cap);
-  launch_pcg_axpy_norm(n, h->gx, h->pr, h->pp, h->pq, h->red, h->cap);
+  launch_pcg_axpy_norm(n, h->gx, h->pr, h->pp, h->pq, h->red, h->cap, pcg_x0_out(h, prec));
   launch_pcg_loop_cond(G.hw, n, h->red, h->gstate, h->cap);
   cudaGraph_t captured = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap, &captured);
@@ -589,7 +625,7 @@ amge_status run_step(PcgRun& r) {
       }
       {
         Prof p(h, AMGE_PROF_PCG_VEC, r.s, 2);
-        launch_pcg_axpy_norm(n, h->gx, h->pr, h->pp, h->pq, h->red, r.s);
+        launch_pcg_axpy_norm(n, h->gx, h->pr, h->pp, h->pq, h->red, r.s, pcg_x0_out(h, r.o.precision));
         launch_pcg_finish_rr(n, h->red, r.s);
       }
       CK(cudaMemcpyAsync(h->pinned + SC_RR, sc + SC_RR, sizeof(double), cudaMemcpyDeviceToHost, r.s));
@@ -616,6 +652,7 @@ amge_status run_step(PcgRun& r) {
       r.rt = h->pinned[SC_RR];
       if (r.rt <= r.tol2) return run_tail(r, AMGE_OK);
       if (r.it >= r.o.maxit) return run_tail(r, AMGE_ENOTCONV);
+      pcg_x0_from_r(h, h->pr, r.o.precision, r.s);
       return run_graph(r);  // continue from the true residual (sc[SC_RR] holds its norm)
     }
     case PcgRun::P_FINAL:

@@ -221,10 +221,20 @@ int pcg_spmv_blocks(const DevSell<double>& A);
 // q = A p and pq = p.q (two launches); alpha = rho / pq.
 void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, const RedScratch& r,
                          cudaStream_t s);
+// Optional extra outputs of the PCG axpy: the next V-cycle's first level-0 sweep from
+// zero (mode 1: x64 = minv64 r; mode 2: r32 = (float) r, x32 = minv32 r32).
+struct X0Out {
+  int mode = 0;
+  const double* minv64 = nullptr;
+  double* x64 = nullptr;
+  const float* minv32 = nullptr;
+  float* r32 = nullptr;
+  float* x32 = nullptr;
+};
 // x += alpha p; r -= alpha q; block partials of ||r||^2 (summed by the loop test or
 // launch_pcg_finish_rr, which sets SC_RR)
 void launch_pcg_axpy_norm(int64_t n, double* x, double* rv, const double* p, const double* q,
-                          const RedScratch& r, cudaStream_t s);
+                          const RedScratch& r, cudaStream_t s, const X0Out& o = X0Out());
 void launch_pcg_finish_rr(int64_t n, const RedScratch& r, cudaStream_t s);
 // rho_new = r.z, zq = z.q (two launches); beta = rho_new / rho (flexible = 0) or
 // -alpha zq / rho (flexible = 1)

@@ -395,10 +395,14 @@ __global__ void __launch_bounds__(kFinishBlock) k_finish_dot(int nred, RedScratc
   if (threadIdx.x == 0) *out = t;
 }
 
-// x += alpha p; r -= alpha q; block partials of ||r||^2.
+// x += alpha p; r -= alpha q; block partials of ||r||^2.  X0 != 0 also starts the
+// next V-cycle's level-0 sweep from zero: X0 = 1 writes x0 = m^-1 r (FP64 V-cycle);
+// X0 = 2 writes r32 = (float) r and x0 = m32^-1 r32 (FP32 V-cycle), the same
+// roundings as the separate cast and product.
+template <int X0>
 __global__ void __launch_bounds__(kBlock, 8) k_pcg_axpy_norm(int64_t n, double* __restrict__ x,
                                                              double* __restrict__ rv, const double* __restrict__ p,
-                                                             const double* __restrict__ q, RedScratch r) {
+                                                             const double* __restrict__ q, RedScratch r, X0Out o) {
   pdl_begin();
   __shared__ double sh[kBlock];
   const double alpha = r.sc[SC_ALPHA];
@@ -408,6 +412,13 @@ __global__ void __launch_bounds__(kBlock, 8) k_pcg_axpy_norm(int64_t n, double* 
     const double ri = fma(-alpha, q[i], rv[i]);
     rv[i] = ri;
     acc = fma(ri, ri, acc);
+    if (X0 == 1) {
+      o.x64[i] = o.minv64[i] * ri;
+    } else if (X0 == 2) {
+      const float rf = (float)ri;
+      o.r32[i] = rf;
+      o.x32[i] = o.minv32[i] * rf;
+    }
   }
   store_partial<kBlock>(acc, r.partials + kSlotRR * kMaxRedBlocks, sh);
 }
@@ -649,8 +660,12 @@ void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, c
 }
 
 void launch_pcg_axpy_norm(int64_t n, double* x, double* rv, const double* p, const double* q,
-                          const RedScratch& r, cudaStream_t s) {
-  launch_k(k_pcg_axpy_norm, red_blocks(n), kBlock, s, n, x, rv, p, q, r);
+                          const RedScratch& r, cudaStream_t s, const X0Out& o) {
+  switch (o.mode) {
+    case 1: launch_k(k_pcg_axpy_norm<1>, red_blocks(n), kBlock, s, n, x, rv, p, q, r, o); break;
+    case 2: launch_k(k_pcg_axpy_norm<2>, red_blocks(n), kBlock, s, n, x, rv, p, q, r, o); break;
+    default: launch_k(k_pcg_axpy_norm<0>, red_blocks(n), kBlock, s, n, x, rv, p, q, r, o); break;
+  }
 }
 
 void launch_pcg_finish_rr(int64_t n, const RedScratch& r, cudaStream_t s) {
