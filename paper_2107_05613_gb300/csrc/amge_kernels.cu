@@ -246,22 +246,32 @@ __global__ void k_cast(int64_t n, const Tin* __restrict__ in, Tout* __restrict__
     out[i] = (Tout)in[i];
 }
 
-// y_i = sum over the stored triangle of row i of M (row-major n x n) times x.
+// y_i = sum over the stored triangle of row i of M (row-major n x n) times x.  One
+// block of kTriBlock threads per row: thread t takes entries beg + t, beg + t +
+// kTriBlock, ... (coalesced), the partial sums meet in shared memory and warp 0 adds
+// them in a fixed order.  A row of the coarsest factor has ~n/2 entries; spreading it
+// over four warps keeps enough loads in flight (a warp per row left ~13 warps per SM).
+constexpr int kTriBlock = 128;
 template <bool LOWER, typename Tin, typename Tout>
-__global__ void __launch_bounds__(kBlock) k_trimv(int n, const double* __restrict__ M, const Tin* __restrict__ x,
-                                                  Tout* __restrict__ y) {
+__global__ void __launch_bounds__(kTriBlock) k_trimv(int n, const double* __restrict__ M, const Tin* __restrict__ x,
+                                                     Tout* __restrict__ y) {
   pdl_begin();
-  const int row = (blockIdx.x * kBlock + threadIdx.x) / 32;
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;  // whole warp shares the row
+  __shared__ double part[kTriBlock];
+  const int row = blockIdx.x;
   const double* m = M + (size_t)row * n;
   const int beg = LOWER ? 0 : row;
   const int end = LOWER ? row + 1 : n;
   double s = 0.0;
-  for (int j = beg + lane; j < end; j += 32) s = fma(ldg(m + j), (double)ldg(x + j), s);
+  for (int j = beg + (int)threadIdx.x; j < end; j += kTriBlock) s = fma(ldg(m + j), (double)ldg(x + j), s);
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  double t = part[threadIdx.x];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (lane == 0) y[row] = (Tout)s;
+  for (int k = 1; k < kTriBlock / 32; k++) t += part[threadIdx.x + 32 * k];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  if (threadIdx.x == 0) y[row] = (Tout)t;
 }
 
 // ---------------------------------------------------------------- reductions
@@ -631,9 +641,9 @@ template void launch_cast<float, double>(int64_t, const float*, double*, cudaStr
 template <typename Tin, typename Tout>
 void launch_coarse(int n, const double* Linv, const double* LinvT, const Tin* b, double* t, Tout* z,
                    cudaStream_t s) {
-  const int grid = (n * 32 + kBlock - 1) / kBlock;
-  launch_k(k_trimv<true, Tin, double>, grid, kBlock, s, n, Linv, b, t);
-  launch_k(k_trimv<false, double, Tout>, grid, kBlock, s, n, LinvT, t, z);
+  if (n == 0) return;
+  launch_k(k_trimv<true, Tin, double>, n, kTriBlock, s, n, Linv, b, t);
+  launch_k(k_trimv<false, double, Tout>, n, kTriBlock, s, n, LinvT, t, z);
 }
 template void launch_coarse<double, double>(int, const double*, const double*, const double*, double*, double*,
                                             cudaStream_t);
