@@ -894,17 +894,22 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
   }
 }
 
-void vcycle_mm_iface(amge_hier* h, int nrhs, const double* r, double* z, int precision, cudaStream_t s) {
+// Z = B R for [n][nrhs] blocks.  FP32 V-cycle: r32_ready -- R was already cast into
+// the level-0 B (by the block PCG axpy); z32_only -- leave the result in the level-0 Z
+// (FP32) for kernels that widen it themselves, instead of casting it into z.
+void vcycle_mm_iface(amge_hier* h, int nrhs, const double* r, double* z, int precision, cudaStream_t s,
+                     bool r32_ready = false, bool z32_only = false) {
   const int64_t tot = (int64_t)h->n0 * nrhs;
   if (precision == AMGE_FP64) {
     vcycle_level_mm<double>(h, 0, nrhs, r, z, s);
   } else {
     LevelDev<float>& d = h->lv32[0];
-    {
+    if (!r32_ready) {
       Prof p(h, AMGE_PROF_PCG_VEC, s);
       launch_cast<double, float>(tot, r, d.B, s);
     }
     vcycle_level_mm<float>(h, 0, nrhs, d.B, d.Z, s);
+    if (z32_only) return;
     Prof p(h, AMGE_PROF_PCG_VEC, s);
     launch_cast<float, double>(tot, d.Z, z, s);
   }
@@ -967,6 +972,18 @@ amge_status pcg_mm(amge_hier* h, int nrhs, const double* b, double* x, const amg
     }
     CK(cudaMemcpyAsync(h->PP, h->PZ, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
+  // FP32 V-cycle: the axpy also writes the V-cycle's FP32 input, and the dots and the
+  // p update read its FP32 output directly (no separate casts inside the loop)
+  const bool f32 = o.precision == AMGE_FP32_VCYCLE;
+  float* r32 = f32 ? h->lv32[0].B : nullptr;
+  const float* z32 = f32 ? h->lv32[0].Z : nullptr;
+  bool r32_ready = false;
+  auto precondition = [&]() {  // Z = B R, then the dots
+    vcycle_mm_iface(h, nrhs, h->PR, h->PZ, o.precision, s, r32_ready, f32);
+    Prof p(h, AMGE_PROF_PCG_VEC, s);
+    if (f32) launch_pcg_mm_dots<float>(n, nrhs, h->PR, z32, h->PQ, flexible, r, s);
+    else launch_pcg_mm_dots<double>(n, nrhs, h->PR, h->PZ, h->PQ, flexible, r, s);
+  };
   while (nact > 0 && it < o.maxit) {
     {
       Prof p(h, AMGE_PROF_PCG_SPMV, s);
@@ -974,7 +991,8 @@ amge_status pcg_mm(amge_hier* h, int nrhs, const double* b, double* x, const amg
     }
     {
       Prof p(h, AMGE_PROF_PCG_VEC, s);
-      launch_pcg_mm_axpy_norm(n, nrhs, x, h->PR, h->PP, h->PQ, r, s);
+      launch_pcg_mm_axpy_norm(n, nrhs, x, h->PR, h->PP, h->PQ, r, s, r32);
+      r32_ready = f32;
     }
     CK(cudaMemcpyAsync(hp + SC_RR * kMaxRhs, r.sc + SC_RR * kMaxRhs, nrhs * sizeof(double), cudaMemcpyDeviceToHost,
                        s));
@@ -985,11 +1003,7 @@ amge_status pcg_mm(amge_hier* h, int nrhs, const double* b, double* x, const amg
       if (active[c] && rr_prev[c] > 0 && rr_prev2[c] > 0 &&
           rr_prev[c] * (rr_prev[c] / rr_prev2[c]) <= 100.0 * tol2[c])
         spec = false;
-    if (spec) {
-      vcycle_mm_iface(h, nrhs, h->PR, h->PZ, o.precision, s);
-      Prof p(h, AMGE_PROF_PCG_VEC, s);
-      launch_pcg_mm_dots(n, nrhs, h->PR, h->PZ, h->PQ, flexible, r, s);
-    }
+    if (spec) precondition();
     CK(cudaEventSynchronize(h->ev));
     std::memcpy(rr.data(), hp + SC_RR * kMaxRhs, nrhs * sizeof(double));
     bool check = false;
@@ -1004,6 +1018,7 @@ amge_status pcg_mm(amge_hier* h, int nrhs, const double* b, double* x, const amg
     }
     if (check) {
       resid_true();
+      r32_ready = false;
       st = read_cols(SC_DOT, rt.data());
       if (st) return st;
       for (int c = 0; c < nrhs; c++)
@@ -1015,13 +1030,10 @@ amge_status pcg_mm(amge_hier* h, int nrhs, const double* b, double* x, const amg
     st = push_active();
     if (st) return st;
     if (nact == 0) break;
-    if (!spec) {
-      vcycle_mm_iface(h, nrhs, h->PR, h->PZ, o.precision, s);
-      Prof p(h, AMGE_PROF_PCG_VEC, s);
-      launch_pcg_mm_dots(n, nrhs, h->PR, h->PZ, h->PQ, flexible, r, s);
-    }
+    if (!spec) precondition();
     Prof p(h, AMGE_PROF_PCG_VEC, s);
-    launch_pcg_mm_update_p(n, nrhs, h->PP, h->PZ, r, s);
+    if (f32) launch_pcg_mm_update_p<float>(n, nrhs, h->PP, z32, r, s);
+    else launch_pcg_mm_update_p<double>(n, nrhs, h->PP, h->PZ, r, s);
   }
   resid_true();
   st = read_cols(SC_DOT, rt.data());

@@ -262,12 +262,15 @@ void launch_dot_mm(int64_t n, int nrhs, const double* x, const double* y, int sc
 // Q = A P (FP64) and pq_c; alpha_c = active_c ? rho_c / pq_c : 0.
 void launch_pcg_mm_spmv_dot(const DevCsr<double>& A, int nrhs, const double* p, double* q, const RedScratchMM& r,
                             cudaStream_t s);
+// r32 (optional): also write (float) r, the next FP32 V-cycle's input.
 void launch_pcg_mm_axpy_norm(int64_t n, int nrhs, double* x, double* rv, const double* p, const double* q,
-                             const RedScratchMM& r, cudaStream_t s);
-void launch_pcg_mm_dots(int64_t n, int nrhs, const double* rv, const double* z, const double* q, int flexible,
+                             const RedScratchMM& r, cudaStream_t s, float* r32 = nullptr);
+// z: FP64, or FP32 as the FP32 V-cycle leaves it (widened exactly in the kernel).
+template <typename ZT>
+void launch_pcg_mm_dots(int64_t n, int nrhs, const double* rv, const ZT* z, const double* q, int flexible,
                         const RedScratchMM& r, cudaStream_t s);
-void launch_pcg_mm_update_p(int64_t n, int nrhs, double* p, const double* z, const RedScratchMM& r,
-                            cudaStream_t s);
+template <typename ZT>
+void launch_pcg_mm_update_p(int64_t n, int nrhs, double* p, const ZT* z, const RedScratchMM& r, cudaStream_t s);
 
 // Resumable single-RHS PCG on a hierarchy's (or a view's) workspace, used by the
 // blocking solve and by the request server.  advance() returns 1 when finished,

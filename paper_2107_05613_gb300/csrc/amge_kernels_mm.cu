@@ -269,10 +269,12 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mm_spmv_dot(int nr, int nrhs, co
   }
 }
 
+// r32 != nullptr: also write (float) r for the next FP32 V-cycle (its input cast).
 template <int K>
 __global__ void __launch_bounds__(kBlock) k_pcg_mm_axpy_norm(int64_t n, int nrhs, double* __restrict__ x,
                                                              double* __restrict__ rv, const double* __restrict__ p,
-                                                             const double* __restrict__ q, RedScratchMM r) {
+                                                             const double* __restrict__ q, RedScratchMM r,
+                                                             float* __restrict__ r32) {
   pdl_begin();
   const int c = threadIdx.x & (K - 1);
   const int64_t groups = (int64_t)gridDim.x * (kBlock / K);
@@ -284,6 +286,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mm_axpy_norm(int64_t n, int nrhs
       x[e] = fma(alpha, p[e], x[e]);
       const double ri = fma(-alpha, q[e], rv[e]);
       rv[e] = ri;
+      if (r32) r32[e] = (float)ri;
       acc = fma(ri, ri, acc);
     }
   }
@@ -291,9 +294,11 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mm_axpy_norm(int64_t n, int nrhs
   if (finish_cols<1>(&acc, K, nrhs, r, 1, tot) && threadIdx.x < nrhs) scol(r, SC_RR)[threadIdx.x] = tot[0][threadIdx.x];
 }
 
-template <int K>
+// z is the preconditioned residual as the V-cycle left it: FP64, or FP32 straight
+// from the FP32 V-cycle (widened exactly here instead of by a separate cast).
+template <int K, typename ZT>
 __global__ void __launch_bounds__(kBlock) k_pcg_mm_dots(int64_t n, int nrhs, const double* __restrict__ rv,
-                                                        const double* __restrict__ z, const double* __restrict__ q,
+                                                        const ZT* __restrict__ z, const double* __restrict__ q,
                                                         int flexible, RedScratchMM r) {
   pdl_begin();
   const int c = threadIdx.x & (K - 1);
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mm_dots(int64_t n, int nrhs, con
   if (c < nrhs)
     for (int64_t row = (blockIdx.x * (int64_t)kBlock + threadIdx.x) / K; row < n; row += groups) {
       const int64_t e = row * nrhs + c;
-      const double zi = z[e];
+      const double zi = (double)z[e];
       acc[0] = fma(rv[e], zi, acc[0]);
       acc[1] = fma(zi, q[e], acc[1]);
     }
@@ -317,12 +322,13 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mm_dots(int64_t n, int nrhs, con
   }
 }
 
+template <typename ZT>
 __global__ void __launch_bounds__(kBlock) k_pcg_mm_update_p(int64_t n, int nrhs, double* __restrict__ p,
-                                                            const double* __restrict__ z, RedScratchMM r) {
+                                                            const ZT* __restrict__ z, RedScratchMM r) {
   pdl_begin();
   const int64_t tot = n * nrhs;
   for (int64_t e = blockIdx.x * (int64_t)kBlock + threadIdx.x; e < tot; e += (int64_t)gridDim.x * kBlock)
-    p[e] = fma(scol(r, SC_BETA)[e % nrhs], p[e], z[e]);
+    p[e] = fma(scol(r, SC_BETA)[e % nrhs], p[e], (double)z[e]);
   if (blockIdx.x == 0 && threadIdx.x < nrhs) scol(r, SC_RHO)[threadIdx.x] = scol(r, SC_RHO_NEW)[threadIdx.x];
 }
 
@@ -431,24 +437,31 @@ void launch_pcg_mm_spmv_dot(const DevCsr<double>& A, int nrhs, const double* p, 
 }
 
 void launch_pcg_mm_axpy_norm(int64_t n, int nrhs, double* x, double* rv, const double* p, const double* q,
-                             const RedScratchMM& r, cudaStream_t s) {
+                             const RedScratchMM& r, cudaStream_t s, float* r32) {
   dispatch_k(pow2_at_least(nrhs), [&](auto kk) {
     constexpr int KK = decltype(kk)::value;
-    launch_k(k_pcg_mm_axpy_norm<KK>, mm_red_blocks(n, KK), kBlock, s, n, nrhs, x, rv, p, q, r);
+    launch_k(k_pcg_mm_axpy_norm<KK>, mm_red_blocks(n, KK), kBlock, s, n, nrhs, x, rv, p, q, r, r32);
   });
 }
 
-void launch_pcg_mm_dots(int64_t n, int nrhs, const double* rv, const double* z, const double* q, int flexible,
+template <typename ZT>
+void launch_pcg_mm_dots(int64_t n, int nrhs, const double* rv, const ZT* z, const double* q, int flexible,
                         const RedScratchMM& r, cudaStream_t s) {
   dispatch_k(pow2_at_least(nrhs), [&](auto kk) {
     constexpr int KK = decltype(kk)::value;
-    launch_k(k_pcg_mm_dots<KK>, mm_red_blocks(n, KK), kBlock, s, n, nrhs, rv, z, q, flexible, r);
+    launch_k(k_pcg_mm_dots<KK, ZT>, mm_red_blocks(n, KK), kBlock, s, n, nrhs, rv, z, q, flexible, r);
   });
 }
+template void launch_pcg_mm_dots<double>(int64_t, int, const double*, const double*, const double*, int,
+                                         const RedScratchMM&, cudaStream_t);
+template void launch_pcg_mm_dots<float>(int64_t, int, const double*, const float*, const double*, int,
+                                        const RedScratchMM&, cudaStream_t);
 
-void launch_pcg_mm_update_p(int64_t n, int nrhs, double* p, const double* z, const RedScratchMM& r,
-                            cudaStream_t s) {
-  launch_k(k_pcg_mm_update_p, grid_for(n * nrhs), kBlock, s, n, nrhs, p, z, r);
+template <typename ZT>
+void launch_pcg_mm_update_p(int64_t n, int nrhs, double* p, const ZT* z, const RedScratchMM& r, cudaStream_t s) {
+  launch_k(k_pcg_mm_update_p<ZT>, grid_for(n * nrhs), kBlock, s, n, nrhs, p, z, r);
 }
+template void launch_pcg_mm_update_p<double>(int64_t, int, double*, const double*, const RedScratchMM&, cudaStream_t);
+template void launch_pcg_mm_update_p<float>(int64_t, int, double*, const float*, const RedScratchMM&, cudaStream_t);
 
 }  // namespace amge
