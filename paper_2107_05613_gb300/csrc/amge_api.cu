@@ -795,7 +795,7 @@ amge_status ensure_mm(amge_hier* h, int nrhs, cudaStream_t s) {
 
 // One V-cycle on a [n_l][nrhs] block (Algorithm 4.1 applied to every column).
 template <typename V>
-void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream_t s) {
+void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream_t s, bool x_ready = false) {
   auto& lv = levels<V>(h);
   if (l == h->L - 1) {
     Prof p(h, AMGE_PROF_COARSE, s, 2);
@@ -823,9 +823,16 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
     a.x = x, a.b = b, a.y = d.R;
     mm(clsA, d.cA, EPI_RESID, a);
   };
+  LevelDev<V>& c = lv[l + 1];
+  const bool c_smooths = l + 1 < h->L - 1;  // the next level starts with X = m^-1 B
+  auto restrict_to_next = [&]() {            // B_c = P^T R (and X_c = m_c^-1 B_c)
+    SpmvArgs<V> a;
+    a.x = d.R, a.y = c.B;
+    if (c_smooths) a.d = c.minv, a.y2 = c.X;
+    mm(AMGE_PROF_PT, d.cPT, c_smooths ? EPI_STORE_MUL : EPI_STORE, a);
+  };
   if (d.use_ag) {  // as in vcycle_level: r -= (A G) y after each aux sweep
-    LevelDev<V>& c = lv[l + 1];
-    {
+    if (!x_ready) {
       Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
       launch_mul_mm<V>(d.n, nrhs, d.minv, b, x, s);
     }
@@ -836,12 +843,8 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
       a.x = d.Y, a.b = d.R, a.y = d.R;
       mm(AMGE_PROF_AG, d.cAG, EPI_RESID, a);
     }
-    {
-      SpmvArgs<V> a;
-      a.x = d.R, a.y = c.B;
-      mm(AMGE_PROF_PT, d.cPT, EPI_STORE, a);
-    }
-    vcycle_level_mm<V>(h, l + 1, nrhs, c.B, c.Z, s);
+    restrict_to_next();
+    vcycle_level_mm<V>(h, l + 1, nrhs, c.B, c.Z, s, c_smooths);
     {
       SpmvArgs<V> a;
       a.x = c.Z, a.y = x;
@@ -856,7 +859,7 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
   }
   for (int k = 0; k < h->nu_pre; k++) {
     if (k == 0) {
-      {
+      if (!x_ready) {
         Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
         launch_mul_mm<V>(d.n, nrhs, d.minv, b, x, s);
       }
@@ -871,13 +874,8 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
     aux_sweep();
   }
   residual();
-  LevelDev<V>& c = lv[l + 1];
-  {
-    SpmvArgs<V> a;
-    a.x = d.R, a.y = c.B;
-    mm(AMGE_PROF_PT, d.cPT, EPI_STORE, a);
-  }
-  vcycle_level_mm<V>(h, l + 1, nrhs, c.B, c.Z, s);
+  restrict_to_next();
+  vcycle_level_mm<V>(h, l + 1, nrhs, c.B, c.Z, s, c_smooths);
   {
     SpmvArgs<V> a;
     a.x = c.Z, a.y = x;
@@ -894,21 +892,22 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
   }
 }
 
-// Z = B R for [n][nrhs] blocks.  FP32 V-cycle: r32_ready -- R was already cast into
-// the level-0 B (by the block PCG axpy); z32_only -- leave the result in the level-0 Z
-// (FP32) for kernels that widen it themselves, instead of casting it into z.
+// Z = B R for [n][nrhs] blocks.  x0_ready (h->L > 1): the block PCG axpy already began
+// the level-0 sweep (X = m^-1 R; for the FP32 V-cycle also R cast into the level-0 B);
+// z32_only -- leave the FP32 V-cycle's result in the level-0 Z for kernels that widen
+// it themselves, instead of casting it into z.
 void vcycle_mm_iface(amge_hier* h, int nrhs, const double* r, double* z, int precision, cudaStream_t s,
-                     bool r32_ready = false, bool z32_only = false) {
+                     bool x0_ready = false, bool z32_only = false) {
   const int64_t tot = (int64_t)h->n0 * nrhs;
   if (precision == AMGE_FP64) {
-    vcycle_level_mm<double>(h, 0, nrhs, r, z, s);
+    vcycle_level_mm<double>(h, 0, nrhs, r, z, s, x0_ready);
   } else {
     LevelDev<float>& d = h->lv32[0];
-    if (!r32_ready) {
+    if (!x0_ready) {
       Prof p(h, AMGE_PROF_PCG_VEC, s);
       launch_cast<double, float>(tot, r, d.B, s);
     }
-    vcycle_level_mm<float>(h, 0, nrhs, d.B, d.Z, s);
+    vcycle_level_mm<float>(h, 0, nrhs, d.B, d.Z, s, x0_ready);
     if (z32_only) return;
     Prof p(h, AMGE_PROF_PCG_VEC, s);
     launch_cast<float, double>(tot, d.Z, z, s);
@@ -975,11 +974,15 @@ amge_status pcg_mm(amge_hier* h, int nrhs, const double* b, double* x, const amg
   // FP32 V-cycle: the axpy also writes the V-cycle's FP32 input, and the dots and the
   // p update read its FP32 output directly (no separate casts inside the loop)
   const bool f32 = o.precision == AMGE_FP32_VCYCLE;
-  float* r32 = f32 ? h->lv32[0].B : nullptr;
   const float* z32 = f32 ? h->lv32[0].Z : nullptr;
-  bool r32_ready = false;
+  X0Out x0;  // the axpy also starts the next block V-cycle (not for a one-level hierarchy)
+  if (h->L > 1) {
+    if (f32) x0.mode = 2, x0.minv32 = h->lv32[0].minv, x0.r32 = h->lv32[0].B, x0.x32 = h->lv32[0].X;
+    else x0.mode = 1, x0.minv64 = h->lv64[0].minv, x0.x64 = h->lv64[0].X;
+  }
+  bool x0_ready = false;
   auto precondition = [&]() {  // Z = B R, then the dots
-    vcycle_mm_iface(h, nrhs, h->PR, h->PZ, o.precision, s, r32_ready, f32);
+    vcycle_mm_iface(h, nrhs, h->PR, h->PZ, o.precision, s, x0_ready, f32);
     Prof p(h, AMGE_PROF_PCG_VEC, s);
     if (f32) launch_pcg_mm_dots<float>(n, nrhs, h->PR, z32, h->PQ, flexible, r, s);
     else launch_pcg_mm_dots<double>(n, nrhs, h->PR, h->PZ, h->PQ, flexible, r, s);
@@ -991,8 +994,8 @@ amge_status pcg_mm(amge_hier* h, int nrhs, const double* b, double* x, const amg
     }
     {
       Prof p(h, AMGE_PROF_PCG_VEC, s);
-      launch_pcg_mm_axpy_norm(n, nrhs, x, h->PR, h->PP, h->PQ, r, s, r32);
-      r32_ready = f32;
+      launch_pcg_mm_axpy_norm(n, nrhs, x, h->PR, h->PP, h->PQ, r, s, x0);
+      x0_ready = x0.mode != 0;
     }
     CK(cudaMemcpyAsync(hp + SC_RR * kMaxRhs, r.sc + SC_RR * kMaxRhs, nrhs * sizeof(double), cudaMemcpyDeviceToHost,
                        s));
@@ -1018,7 +1021,7 @@ amge_status pcg_mm(amge_hier* h, int nrhs, const double* b, double* x, const amg
     }
     if (check) {
       resid_true();
-      r32_ready = false;
+      x0_ready = false;
       st = read_cols(SC_DOT, rt.data());
       if (st) return st;
       for (int c = 0; c < nrhs; c++)

@@ -262,9 +262,10 @@ void launch_dot_mm(int64_t n, int nrhs, const double* x, const double* y, int sc
 // Q = A P (FP64) and pq_c; alpha_c = active_c ? rho_c / pq_c : 0.
 void launch_pcg_mm_spmv_dot(const DevCsr<double>& A, int nrhs, const double* p, double* q, const RedScratchMM& r,
                             cudaStream_t s);
-// r32 (optional): also write (float) r, the next FP32 V-cycle's input.
+// o (optional, X0Out with [n][nrhs] blocks, the diagonals per row): also start the
+// next block V-cycle (mode 1: x64 = minv64 r; mode 2: r32 = (float) r, x32 = minv32 r32).
 void launch_pcg_mm_axpy_norm(int64_t n, int nrhs, double* x, double* rv, const double* p, const double* q,
-                             const RedScratchMM& r, cudaStream_t s, float* r32 = nullptr);
+                             const RedScratchMM& r, cudaStream_t s, const X0Out& o = X0Out());
 // z: FP64, or FP32 as the FP32 V-cycle leaves it (widened exactly in the kernel).
 template <typename ZT>
 void launch_pcg_mm_dots(int64_t n, int nrhs, const double* rv, const ZT* z, const double* q, int flexible,

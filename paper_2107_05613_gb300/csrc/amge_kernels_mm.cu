@@ -51,6 +51,10 @@ __global__ void __launch_bounds__(kBlock) k_csr_mm(int nr, int nrhs, const int* 
     case EPI_SCALE: a.y[e] = a.d[row] * s; break;
     case EPI_ADD: a.y[e] += s; break;
     case EPI_SWEEP: a.y[e] = fma(a.d[row], a.b[e] - s, a.xin[e]); break;
+    case EPI_STORE_MUL:
+      a.y[e] = s;
+      a.y2[e] = a.d[row] * s;
+      break;
   }
 }
 
@@ -120,6 +124,14 @@ __global__ void __launch_bounds__(kBlock) k_csr_mmv(int nr, int nrhs, int lpr, c
     const VecU<V> xv = vld(xq + (size_t)c * nrhs);
 #pragma unroll
     for (int k = 0; k < W; k++) s.v[k] = fma(v, xv.v[k], s.v[k]);
+  }
+  if (EPI == EPI_STORE_MUL) {  // y = s and y2 = d s (restriction + next level's first sweep)
+    vst(a.y + e, s);
+    const V d = ldg(a.d + row);
+#pragma unroll
+    for (int k = 0; k < W; k++) s.v[k] *= d;
+    vst(a.y2 + e, s);
+    return;
   }
   if (EPI == EPI_SCALE) {
     const V d = ldg(a.d + row);
@@ -269,12 +281,12 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mm_spmv_dot(int nr, int nrhs, co
   }
 }
 
-// r32 != nullptr: also write (float) r for the next FP32 V-cycle (its input cast).
+// o.mode 1: also x64 = minv64 r (FP64 V-cycle's first level-0 sweep from zero);
+// o.mode 2: r32 = (float) r and x32 = minv32 r32 (FP32 V-cycle's input and first sweep).
 template <int K>
 __global__ void __launch_bounds__(kBlock) k_pcg_mm_axpy_norm(int64_t n, int nrhs, double* __restrict__ x,
                                                              double* __restrict__ rv, const double* __restrict__ p,
-                                                             const double* __restrict__ q, RedScratchMM r,
-                                                             float* __restrict__ r32) {
+                                                             const double* __restrict__ q, RedScratchMM r, X0Out o) {
   pdl_begin();
   const int c = threadIdx.x & (K - 1);
   const int64_t groups = (int64_t)gridDim.x * (kBlock / K);
@@ -286,7 +298,13 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mm_axpy_norm(int64_t n, int nrhs
       x[e] = fma(alpha, p[e], x[e]);
       const double ri = fma(-alpha, q[e], rv[e]);
       rv[e] = ri;
-      if (r32) r32[e] = (float)ri;
+      if (o.mode == 1) {
+        o.x64[e] = o.minv64[row] * ri;
+      } else if (o.mode == 2) {
+        const float rf = (float)ri;
+        o.r32[e] = rf;
+        o.x32[e] = o.minv32[row] * rf;
+      }
       acc = fma(ri, ri, acc);
     }
   }
@@ -373,7 +391,7 @@ template <typename V>
 void launch_csr_mm(const DevCsr<V>& M, int nrhs, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
   if (M.nr == 0) return;
   constexpr int W = VecW<V>::W;
-  if (nrhs % W == 0 && aligned16(a.x) && aligned16(a.y) && aligned16(a.b) && aligned16(a.xin)) {
+  if (nrhs % W == 0 && aligned16(a.x) && aligned16(a.y) && aligned16(a.b) && aligned16(a.xin) && aligned16(a.y2)) {
     const int lpr = nrhs / W;
     const int grid = (int)(((int64_t)M.nr * lpr + kBlock - 1) / kBlock);
     switch (epi) {
@@ -382,6 +400,9 @@ void launch_csr_mm(const DevCsr<V>& M, int nrhs, int epi, const SpmvArgs<V>& a, 
       case EPI_SCALE: launch_k(k_csr_mmv<V, EPI_SCALE>, grid, kBlock, s, M.nr, nrhs, lpr, M.rp, M.ci, M.val, a); break;
       case EPI_ADD: launch_k(k_csr_mmv<V, EPI_ADD>, grid, kBlock, s, M.nr, nrhs, lpr, M.rp, M.ci, M.val, a); break;
       case EPI_SWEEP: launch_k(k_csr_mmv<V, EPI_SWEEP>, grid, kBlock, s, M.nr, nrhs, lpr, M.rp, M.ci, M.val, a); break;
+      case EPI_STORE_MUL:
+        launch_k(k_csr_mmv<V, EPI_STORE_MUL>, grid, kBlock, s, M.nr, nrhs, lpr, M.rp, M.ci, M.val, a);
+        break;
     }
     return;
   }
@@ -395,6 +416,9 @@ void launch_csr_mm(const DevCsr<V>& M, int nrhs, int epi, const SpmvArgs<V>& a, 
       case EPI_SCALE: launch_k(k_csr_mm<V, KK, EPI_SCALE>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, M.val, a); break;
       case EPI_ADD: launch_k(k_csr_mm<V, KK, EPI_ADD>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, M.val, a); break;
       case EPI_SWEEP: launch_k(k_csr_mm<V, KK, EPI_SWEEP>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, M.val, a); break;
+      case EPI_STORE_MUL:
+        launch_k(k_csr_mm<V, KK, EPI_STORE_MUL>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, M.val, a);
+        break;
     }
   });
 }
@@ -437,10 +461,10 @@ void launch_pcg_mm_spmv_dot(const DevCsr<double>& A, int nrhs, const double* p, 
 }
 
 void launch_pcg_mm_axpy_norm(int64_t n, int nrhs, double* x, double* rv, const double* p, const double* q,
-                             const RedScratchMM& r, cudaStream_t s, float* r32) {
+                             const RedScratchMM& r, cudaStream_t s, const X0Out& o) {
   dispatch_k(pow2_at_least(nrhs), [&](auto kk) {
     constexpr int KK = decltype(kk)::value;
-    launch_k(k_pcg_mm_axpy_norm<KK>, mm_red_blocks(n, KK), kBlock, s, n, nrhs, x, rv, p, q, r, r32);
+    launch_k(k_pcg_mm_axpy_norm<KK>, mm_red_blocks(n, KK), kBlock, s, n, nrhs, x, rv, p, q, r, o);
   });
 }
 
