@@ -757,9 +757,33 @@ amge_status pcg_graph(amge_hier* h, const double* b, double* x, const amge_solve
 amge_status launch_status();
 
 // Size the block workspace for nrhs right-hand sides (grows, never shrinks).
-amge_status ensure_mm(amge_hier* h, int nrhs, cudaStream_t s) {
+}  // namespace
+
+// Bytes of the block workspace ensure_mm allocates for cap columns.
+size_t amge::hier_block_workspace_bytes(const amge_hier* h, int cap) {
+  size_t b = 0;
+  for (int l = 0; l < h->L; l++) {
+    const size_t n = (size_t)h->lv64[l].n * cap, na = (size_t)h->lv64[l].naux * cap;
+    if (l + 1 < h->L) b += 3 * n * (sizeof(double) + sizeof(float)) + na * (sizeof(double) + sizeof(float));
+    b += 2 * n * (sizeof(double) + sizeof(float));
+  }
+  const size_t n0 = (size_t)h->n0 * cap;
+  b += 6 * n0 * sizeof(double) + 2 * n0 * sizeof(float) + (size_t)h->nC * cap * sizeof(double);
+  b += (size_t)kRedSlots * kMaxRedBlocksMM * kMaxRhs * sizeof(double) + SC_COUNT * kMaxRhs * sizeof(double);
+  return b;
+}
+
+// Block workspace for up to cap columns (allocated once per hierarchy: a later call
+// needing more than the first call's cap fails with AMGE_EINVAL).  amge_pcg_solve and
+// amge_vcycle size it for 32 columns; the request server sizes its workspace views
+// for the requests they serve.
+amge_status amge::ensure_mm(amge_hier* h, int nrhs, cudaStream_t s, int cap) {
   if (nrhs <= h->mm_cap) return AMGE_OK;
-  const int k = kMaxRhs;  // size once for the largest block, so later calls never reallocate
+  if (h->mm_cap > 0 || nrhs > cap || cap > kMaxRhs) {
+    set_error("block workspace too small for this number of right-hand sides");
+    return AMGE_EINVAL;
+  }
+  const int k = cap;
   try {
     for (int l = 0; l < h->L; l++) {
       LevelDev<double>& d64 = h->lv64[l];
@@ -792,6 +816,8 @@ amge_status ensure_mm(amge_hier* h, int nrhs, cudaStream_t s) {
   h->mm_cap = k;
   return AMGE_OK;
 }
+
+namespace {
 
 // One V-cycle on a [n_l][nrhs] block (Algorithm 4.1 applied to every column).
 template <typename V>
@@ -914,147 +940,288 @@ void vcycle_mm_iface(amge_hier* h, int nrhs, const double* r, double* z, int pre
   }
 }
 
+}  // namespace
+
 // PCG on nrhs columns at once: per-column scalars, a column leaves the iteration
-// (alpha = beta = 0 from then on) once its true residual meets the tolerance.
-amge_status pcg_mm(amge_hier* h, int nrhs, const double* b, double* x, const amge_solve_opts& o, amge_info* info,
-                   cudaStream_t s) {
-  const auto t0 = std::chrono::steady_clock::now();
-  const int64_t n = h->n0;
-  const int64_t tot = n * nrhs;
-  const int flexible = (o.precision == AMGE_FP32_VCYCLE) ? 1 : 0;
-  RedScratchMM& r = h->redmm;
-  double* hp = h->pinned_mm;
-  int* act_h = reinterpret_cast<int*>(hp + SC_COUNT * kMaxRhs);
-  auto read_cols = [&](int idx, double* out) -> amge_status {
-    CK(cudaMemcpyAsync(hp + idx * kMaxRhs, r.sc + idx * kMaxRhs, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    std::memcpy(out, hp + idx * kMaxRhs, nrhs * sizeof(double));
-    return AMGE_OK;
-  };
-  std::vector<double> bb(nrhs), rr(nrhs), rt(nrhs), rr_prev(nrhs, -1), rr_prev2(nrhs, -1), tol2(nrhs);
-  std::vector<int> active(nrhs, 1), iters(nrhs, 0), status(nrhs, AMGE_OK);
-  auto push_active = [&]() -> amge_status {
-    for (int c = 0; c < nrhs; c++) act_h[c] = active[c];
-    CK(cudaMemcpyAsync(r.active, act_h, nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
-    return AMGE_OK;
-  };
-  auto resid_true = [&]() {
-    Prof p(h, AMGE_PROF_PCG_SPMV, s);
-    SpmvArgs<double> a;
-    a.x = x, a.b = b, a.y = h->PR;
-    launch_csr_mm<double>(h->cA0, nrhs, EPI_RESID, a, s);
-    launch_dot_mm(n, nrhs, h->PR, h->PR, SC_DOT, r, s);
-  };
+// (alpha = beta = 0 from then on) once its true residual meets the tolerance.  A
+// resumable state machine like PcgRun: every phase enqueues its work, copies the
+// scalars the host needs into pinned memory and records h->ev; advance() continues
+// once that event has completed, so a caller (the request server) can run many block
+// solves without blocking.  The ||r||^2 read of an iteration overlaps the next
+// V-cycle, which is enqueued speculatively unless a column is predicted to be close
+// to its tolerance.
+struct PcgRunMM {
+  enum Phase { M_BB, M_ITER, M_CHECK, M_FINAL, M_DONE };
+  amge_hier* h = nullptr;
+  int nrhs = 1;
+  const double* b = nullptr;
+  double* x = nullptr;
+  amge_solve_opts o{};
+  cudaStream_t s = nullptr;
+  Phase phase = M_BB;
+  int it = 0, nact = 0, flexible = 0;
+  bool f32 = false, x0_ready = false, spec = true;
+  X0Out x0;  // the axpy also starts the next block V-cycle (not for a one-level hierarchy)
+  std::vector<double> bb, rr, rt, rr_prev, rr_prev2, tol2;
+  std::vector<int> active, iters, status;
+  std::chrono::steady_clock::time_point t0;
+  std::vector<amge_info> info;
+  amge_status result = AMGE_OK;
+};
+
+namespace {
+
+double* mm_pinned(PcgRunMM& r, int idx) { return r.h->pinned_mm + (size_t)idx * kMaxRhs; }
+
+amge_status mm_copy_cols(PcgRunMM& r, int idx) {
+  CK(cudaMemcpyAsync(mm_pinned(r, idx), r.h->redmm.sc + (size_t)idx * kMaxRhs, r.nrhs * sizeof(double),
+                     cudaMemcpyDeviceToHost, r.s));
+  return AMGE_OK;
+}
+
+amge_status mm_record(PcgRunMM& r) {
+  CK(cudaEventRecord(r.h->ev, r.s));
+  return AMGE_OK;
+}
+
+amge_status mm_push_active(PcgRunMM& r) {
+  int* act_h = reinterpret_cast<int*>(r.h->pinned_mm + SC_COUNT * kMaxRhs);
+  for (int c = 0; c < r.nrhs; c++) act_h[c] = r.active[c];
+  CK(cudaMemcpyAsync(r.h->redmm.active, act_h, r.nrhs * sizeof(int), cudaMemcpyHostToDevice, r.s));
+  return AMGE_OK;
+}
+
+void mm_resid_true(PcgRunMM& r) {  // PR = b - A x and ||PR||^2 -> SC_DOT
+  amge_hier* h = r.h;
+  Prof p(h, AMGE_PROF_PCG_SPMV, r.s);
+  SpmvArgs<double> a;
+  a.x = r.x, a.b = r.b, a.y = h->PR;
+  launch_csr_mm<double>(h->cA0, r.nrhs, EPI_RESID, a, r.s);
+  launch_dot_mm(h->n0, r.nrhs, h->PR, h->PR, SC_DOT, h->redmm, r.s);
+}
+
+void mm_precondition(PcgRunMM& r) {  // Z = B R, then the dots
+  amge_hier* h = r.h;
+  vcycle_mm_iface(h, r.nrhs, h->PR, h->PZ, r.o.precision, r.s, r.x0_ready, r.f32);
+  Prof p(h, AMGE_PROF_PCG_VEC, r.s);
+  if (r.f32) launch_pcg_mm_dots<float>(h->n0, r.nrhs, h->PR, h->lv32[0].Z, h->PQ, r.flexible, h->redmm, r.s);
+  else launch_pcg_mm_dots<double>(h->n0, r.nrhs, h->PR, h->PZ, h->PQ, r.flexible, h->redmm, r.s);
+}
+
+amge_status mm_final(PcgRunMM& r) {
+  mm_resid_true(r);
+  amge_status st = mm_copy_cols(r, SC_DOT);
+  if (st) return st;
+  r.phase = PcgRunMM::M_FINAL;
+  return mm_record(r);
+}
+
+// q = A p, the axpy, ||r||^2 to the host, and the speculative next V-cycle.
+amge_status mm_iterate(PcgRunMM& r) {
+  amge_hier* h = r.h;
+  {
+    Prof p(h, AMGE_PROF_PCG_SPMV, r.s);
+    launch_pcg_mm_spmv_dot(h->cA0, r.nrhs, h->PP, h->PQ, h->redmm, r.s);
+  }
+  {
+    Prof p(h, AMGE_PROF_PCG_VEC, r.s);
+    launch_pcg_mm_axpy_norm(h->n0, r.nrhs, r.x, h->PR, h->PP, h->PQ, h->redmm, r.s, r.x0);
+    r.x0_ready = r.x0.mode != 0;
+  }
+  amge_status st = mm_copy_cols(r, SC_RR);
+  if (st) return st;
+  st = mm_record(r);
+  if (st) return st;
+  r.it++;
+  r.spec = true;
+  for (int c = 0; c < r.nrhs; c++)
+    if (r.active[c] && r.rr_prev[c] > 0 && r.rr_prev2[c] > 0 &&
+        r.rr_prev[c] * (r.rr_prev[c] / r.rr_prev2[c]) <= 100.0 * r.tol2[c])
+      r.spec = false;
+  if (r.spec) mm_precondition(r);
+  r.phase = PcgRunMM::M_ITER;
+  return AMGE_OK;
+}
+
+// After the iteration's scalar checks: drop finished columns, then the p update and
+// the next iteration (or the final true residual).
+amge_status mm_continue(PcgRunMM& r) {
+  amge_hier* h = r.h;
+  r.nact = 0;
+  for (int c = 0; c < r.nrhs; c++) r.nact += r.active[c];
+  amge_status st = mm_push_active(r);
+  if (st) return st;
+  if (r.nact == 0) return mm_final(r);
+  if (!r.spec) mm_precondition(r);
+  {
+    Prof p(h, AMGE_PROF_PCG_VEC, r.s);
+    if (r.f32) launch_pcg_mm_update_p<float>(h->n0, r.nrhs, h->PP, h->lv32[0].Z, h->redmm, r.s);
+    else launch_pcg_mm_update_p<double>(h->n0, r.nrhs, h->PP, h->PZ, h->redmm, r.s);
+  }
+  if (r.it >= r.o.maxit) return mm_final(r);
+  return mm_iterate(r);
+}
+
+amge_status mm_step(PcgRunMM& r) {
+  amge_hier* h = r.h;
+  const int64_t tot = h->n0 * (int64_t)r.nrhs;
+  switch (r.phase) {
+    case PcgRunMM::M_BB: {
+      std::memcpy(r.bb.data(), mm_pinned(r, SC_BB), r.nrhs * sizeof(double));
+      CK(cudaMemsetAsync(r.x, 0, tot * sizeof(double), r.s));
+      r.nact = 0;
+      for (int c = 0; c < r.nrhs; c++) {
+        r.tol2[c] = r.o.rtol * r.o.rtol * r.bb[c];
+        if (!std::isfinite(r.bb[c])) r.active[c] = 0, r.status[c] = AMGE_ENONFINITE;
+        else if (r.bb[c] == 0.0) r.active[c] = 0;
+        r.nact += r.active[c];
+      }
+      amge_status st = mm_push_active(r);
+      if (st) return st;
+      if (r.nact == 0 || r.o.maxit <= 0) return mm_final(r);
+      CK(cudaMemcpyAsync(h->PR, r.b, tot * sizeof(double), cudaMemcpyDeviceToDevice, r.s));
+      vcycle_mm_iface(h, r.nrhs, h->PR, h->PZ, r.o.precision, r.s);
+      {
+        Prof p(h, AMGE_PROF_PCG_VEC, r.s);
+        launch_dot_mm(h->n0, r.nrhs, h->PR, h->PZ, SC_RHO, h->redmm, r.s);
+      }
+      CK(cudaMemcpyAsync(h->PP, h->PZ, tot * sizeof(double), cudaMemcpyDeviceToDevice, r.s));
+      return mm_iterate(r);
+    }
+    case PcgRunMM::M_ITER: {
+      std::memcpy(r.rr.data(), mm_pinned(r, SC_RR), r.nrhs * sizeof(double));
+      bool check = false;
+      for (int c = 0; c < r.nrhs; c++) {
+        if (!r.active[c]) continue;
+        if (!std::isfinite(r.rr[c])) {
+          r.active[c] = 0, r.status[c] = AMGE_ENONFINITE, r.iters[c] = r.it;
+          continue;
+        }
+        r.rr_prev2[c] = r.rr_prev[c], r.rr_prev[c] = r.rr[c];
+        if (r.rr[c] <= r.tol2[c]) check = true;
+      }
+      if (!check) return mm_continue(r);
+      mm_resid_true(r);
+      r.x0_ready = false;
+      amge_status st = mm_copy_cols(r, SC_DOT);
+      if (st) return st;
+      r.phase = PcgRunMM::M_CHECK;
+      return mm_record(r);
+    }
+    case PcgRunMM::M_CHECK: {
+      std::memcpy(r.rt.data(), mm_pinned(r, SC_DOT), r.nrhs * sizeof(double));
+      for (int c = 0; c < r.nrhs; c++)
+        if (r.active[c] && r.rt[c] <= r.tol2[c]) r.active[c] = 0, r.iters[c] = r.it;
+      r.spec = false;  // the active columns continue from the true residual
+      return mm_continue(r);
+    }
+    case PcgRunMM::M_FINAL: {
+      std::memcpy(r.rt.data(), mm_pinned(r, SC_DOT), r.nrhs * sizeof(double));
+      amge_status st = launch_status();
+      if (st) return st;
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - r.t0).count();
+      r.result = AMGE_OK;
+      for (int c = 0; c < r.nrhs; c++) {
+        if (r.active[c]) r.iters[c] = r.it, r.status[c] = AMGE_ENOTCONV;
+        amge_info& in = r.info[c];
+        in.iters = r.iters[c];
+        in.status = r.status[c];
+        in.true_relres = r.bb[c] > 0 ? std::sqrt(r.rt[c] / r.bb[c]) : (r.bb[c] == 0 ? 0.0 : NAN);
+        in.time_ms = ms;
+        if (r.status[c] == AMGE_ENONFINITE) r.result = AMGE_ENONFINITE;
+        else if (r.status[c] == AMGE_ENOTCONV && r.result == AMGE_OK) r.result = AMGE_ENOTCONV;
+      }
+      r.phase = PcgRunMM::M_DONE;
+      return AMGE_OK;
+    }
+    default:
+      return AMGE_OK;
+  }
+}
+
+}  // namespace
+
+// Block solves need the block workspace (ensure_mm) of h for at least nrhs columns.
+amge_status amge::pcg_mm_run_start(amge_hier* h, int nrhs, const double* b, double* x, const amge_solve_opts& o,
+                                   cudaStream_t s, PcgRunMM** out) {
+  *out = nullptr;
+  PcgRunMM* r = new PcgRunMM;
+  r->h = h, r->nrhs = nrhs, r->b = b, r->x = x, r->o = o, r->s = s;
+  r->t0 = std::chrono::steady_clock::now();
+  r->flexible = (o.precision == AMGE_FP32_VCYCLE) ? 1 : 0;
+  r->f32 = o.precision == AMGE_FP32_VCYCLE;
+  if (h->L > 1) {
+    if (r->f32) r->x0.mode = 2, r->x0.minv32 = h->lv32[0].minv, r->x0.r32 = h->lv32[0].B, r->x0.x32 = h->lv32[0].X;
+    else r->x0.mode = 1, r->x0.minv64 = h->lv64[0].minv, r->x0.x64 = h->lv64[0].X;
+  }
+  r->bb.assign(nrhs, 0.0), r->rr.assign(nrhs, 0.0), r->rt.assign(nrhs, 0.0);
+  r->rr_prev.assign(nrhs, -1.0), r->rr_prev2.assign(nrhs, -1.0), r->tol2.assign(nrhs, 0.0);
+  r->active.assign(nrhs, 1), r->iters.assign(nrhs, 0), r->status.assign(nrhs, AMGE_OK);
+  r->info.assign(nrhs, amge_info{});
   {
     Prof p(h, AMGE_PROF_PCG_VEC, s);
-    launch_dot_mm(n, nrhs, b, b, SC_BB, r, s);
+    launch_dot_mm(h->n0, nrhs, b, b, SC_BB, h->redmm, s);
   }
-  amge_status st = read_cols(SC_BB, bb.data());
+  amge_status st = mm_copy_cols(*r, SC_BB);
+  if (st == AMGE_OK) st = mm_record(*r);
+  if (st) {
+    delete r;
+    return st;
+  }
+  r->phase = PcgRunMM::M_BB;
+  *out = r;
+  return AMGE_OK;
+}
+
+int amge::pcg_mm_run_advance(PcgRunMM* r, amge_status* err) {
+  *err = AMGE_OK;
+  while (r->phase != PcgRunMM::M_DONE) {
+    cudaError_t q = cudaEventQuery(r->h->ev);
+    if (q == cudaErrorNotReady) return 0;
+    if (q != cudaSuccess) {
+      set_error(std::string("block pcg event: ") + cudaGetErrorString(q));
+      *err = AMGE_ECUDA;
+      return -1;
+    }
+    amge_status st = mm_step(*r);
+    if (st) {
+      *err = st;
+      return -1;
+    }
+  }
+  return 1;
+}
+
+void amge::pcg_mm_run_wait_event(PcgRunMM* r) { cudaEventSynchronize(r->h->ev); }
+
+void amge::pcg_mm_run_free(PcgRunMM* r) { delete r; }
+
+amge_status amge::pcg_mm_run_finish(PcgRunMM* r, amge_info* info) {
+  if (info)
+    for (int c = 0; c < r->nrhs; c++) info[c] = r->info[c];
+  amge_status st = r->result;
+  delete r;
+  return st;
+}
+
+namespace {
+
+amge_status pcg_mm(amge_hier* h, int nrhs, const double* b, double* x, const amge_solve_opts& o, amge_info* info,
+                   cudaStream_t s) {
+  PcgRunMM* r = nullptr;
+  amge_status st = pcg_mm_run_start(h, nrhs, b, x, o, s, &r);
   if (st) return st;
-  CK(cudaMemsetAsync(x, 0, tot * sizeof(double), s));
-  int nact = 0;
-  for (int c = 0; c < nrhs; c++) {
-    tol2[c] = o.rtol * o.rtol * bb[c];
-    if (!std::isfinite(bb[c])) active[c] = 0, status[c] = AMGE_ENONFINITE;
-    else if (bb[c] == 0.0) active[c] = 0;
-    nact += active[c];
-  }
-  st = push_active();
-  if (st) return st;
-  int it = 0;
-  if (nact > 0) {
-    CK(cudaMemcpyAsync(h->PR, b, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    vcycle_mm_iface(h, nrhs, h->PR, h->PZ, o.precision, s);
-    {
-      Prof p(h, AMGE_PROF_PCG_VEC, s);
-      launch_dot_mm(n, nrhs, h->PR, h->PZ, SC_RHO, r, s);
+  for (;;) {
+    amge_status err;
+    const int d = pcg_mm_run_advance(r, &err);
+    if (d < 0) {
+      delete r;
+      return err;
     }
-    CK(cudaMemcpyAsync(h->PP, h->PZ, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (d == 1) break;
+    pcg_mm_run_wait_event(r);
   }
-  // FP32 V-cycle: the axpy also writes the V-cycle's FP32 input, and the dots and the
-  // p update read its FP32 output directly (no separate casts inside the loop)
-  const bool f32 = o.precision == AMGE_FP32_VCYCLE;
-  const float* z32 = f32 ? h->lv32[0].Z : nullptr;
-  X0Out x0;  // the axpy also starts the next block V-cycle (not for a one-level hierarchy)
-  if (h->L > 1) {
-    if (f32) x0.mode = 2, x0.minv32 = h->lv32[0].minv, x0.r32 = h->lv32[0].B, x0.x32 = h->lv32[0].X;
-    else x0.mode = 1, x0.minv64 = h->lv64[0].minv, x0.x64 = h->lv64[0].X;
-  }
-  bool x0_ready = false;
-  auto precondition = [&]() {  // Z = B R, then the dots
-    vcycle_mm_iface(h, nrhs, h->PR, h->PZ, o.precision, s, x0_ready, f32);
-    Prof p(h, AMGE_PROF_PCG_VEC, s);
-    if (f32) launch_pcg_mm_dots<float>(n, nrhs, h->PR, z32, h->PQ, flexible, r, s);
-    else launch_pcg_mm_dots<double>(n, nrhs, h->PR, h->PZ, h->PQ, flexible, r, s);
-  };
-  while (nact > 0 && it < o.maxit) {
-    {
-      Prof p(h, AMGE_PROF_PCG_SPMV, s);
-      launch_pcg_mm_spmv_dot(h->cA0, nrhs, h->PP, h->PQ, r, s);
-    }
-    {
-      Prof p(h, AMGE_PROF_PCG_VEC, s);
-      launch_pcg_mm_axpy_norm(n, nrhs, x, h->PR, h->PP, h->PQ, r, s, x0);
-      x0_ready = x0.mode != 0;
-    }
-    CK(cudaMemcpyAsync(hp + SC_RR * kMaxRhs, r.sc + SC_RR * kMaxRhs, nrhs * sizeof(double), cudaMemcpyDeviceToHost,
-                       s));
-    CK(cudaEventRecord(h->ev, s));
-    it++;
-    bool spec = true;
-    for (int c = 0; c < nrhs; c++)
-      if (active[c] && rr_prev[c] > 0 && rr_prev2[c] > 0 &&
-          rr_prev[c] * (rr_prev[c] / rr_prev2[c]) <= 100.0 * tol2[c])
-        spec = false;
-    if (spec) precondition();
-    CK(cudaEventSynchronize(h->ev));
-    std::memcpy(rr.data(), hp + SC_RR * kMaxRhs, nrhs * sizeof(double));
-    bool check = false;
-    for (int c = 0; c < nrhs; c++) {
-      if (!active[c]) continue;
-      if (!std::isfinite(rr[c])) {
-        active[c] = 0, status[c] = AMGE_ENONFINITE, iters[c] = it;
-        continue;
-      }
-      rr_prev2[c] = rr_prev[c], rr_prev[c] = rr[c];
-      if (rr[c] <= tol2[c]) check = true;
-    }
-    if (check) {
-      resid_true();
-      x0_ready = false;
-      st = read_cols(SC_DOT, rt.data());
-      if (st) return st;
-      for (int c = 0; c < nrhs; c++)
-        if (active[c] && rt[c] <= tol2[c]) active[c] = 0, iters[c] = it;
-      spec = false;  // the active columns continue from the true residual
-    }
-    nact = 0;
-    for (int c = 0; c < nrhs; c++) nact += active[c];
-    st = push_active();
-    if (st) return st;
-    if (nact == 0) break;
-    if (!spec) precondition();
-    Prof p(h, AMGE_PROF_PCG_VEC, s);
-    if (f32) launch_pcg_mm_update_p<float>(n, nrhs, h->PP, z32, r, s);
-    else launch_pcg_mm_update_p<double>(n, nrhs, h->PP, h->PZ, r, s);
-  }
-  resid_true();
-  st = read_cols(SC_DOT, rt.data());
-  if (st) return st;
-  st = launch_status();
-  if (st) return st;
-  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  amge_status worst = AMGE_OK;
-  for (int c = 0; c < nrhs; c++) {
-    if (active[c]) iters[c] = it, status[c] = AMGE_ENOTCONV;
-    info[c].iters = iters[c];
-    info[c].status = status[c];
-    info[c].true_relres = bb[c] > 0 ? std::sqrt(rt[c] / bb[c]) : (bb[c] == 0 ? 0.0 : NAN);
-    info[c].time_ms = ms;
-    if (status[c] == AMGE_ENONFINITE) worst = AMGE_ENONFINITE;
-    else if (status[c] == AMGE_ENOTCONV && worst == AMGE_OK) worst = AMGE_ENOTCONV;
-  }
-  return worst;
+  return pcg_mm_run_finish(r, info);
 }
 
 amge_status launch_status() {

@@ -285,6 +285,19 @@ int pcg_run_advance(PcgRun* r, amge_status* err);
 void pcg_run_wait_event(PcgRun* r);
 amge_status pcg_run_finish(PcgRun* r, amge_info* info);  // frees r
 void pcg_run_free(PcgRun* r);                            // abandons r
+// The same for a block of nrhs right-hand sides ([n][nrhs], row-major); h must have its
+// block workspace for nrhs columns (ensure_mm).  finish fills info[0..nrhs).
+}  // namespace amge
+struct PcgRunMM;
+namespace amge {
+amge_status pcg_mm_run_start(amge_hier* h, int nrhs, const double* b, double* x, const amge_solve_opts& o,
+                             cudaStream_t s, PcgRunMM** out);
+int pcg_mm_run_advance(PcgRunMM* r, amge_status* err);
+void pcg_mm_run_wait_event(PcgRunMM* r);
+amge_status pcg_mm_run_finish(PcgRunMM* r, amge_info* info);  // frees r
+void pcg_mm_run_free(PcgRunMM* r);                            // abandons r
+amge_status ensure_mm(amge_hier* h, int nrhs, cudaStream_t s, int cap = kMaxRhs);
+size_t hier_block_workspace_bytes(const amge_hier* h, int cap);
 // A view shares the level operators of `src` and owns a separate workspace (so
 // solves on different views run concurrently without interfering).
 amge_status hier_make_view(const amge_hier* src, cudaStream_t s, amge_hier** out);
