@@ -484,7 +484,7 @@ def run_ours(args, dist):
 
 
 # ------------------------------------------------------------------ serving
-def run_serving(args, amge, n_requests=1000, load=0.7, seed=2107056135, max_slots=32):
+def run_serving(args, amge, n_requests=1000, load=0.7, seed=2107056135, max_slots=128):
     """Continuous-batching request stream: problems drawn from a resident pool of
     16 hierarchies (H(curl) or H(div), n in {16, 24, 32, 48}, two beta draws each,
     beta log-uniform in [1e-2, 1e2] constant per problem, alpha = 1), 1-8 RHS per
