@@ -556,14 +556,20 @@ static void launch_sell_t(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cu
 }
 template <typename V, bool UNIT>
 static void launch_sell_u(const DevSell<V>& M, int wps, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
-  const bool cs = M.stream != 0;  // streaming variants for the one- and two-warp kernels
+  const bool cs = M.stream != 0;
   switch (wps) {
     case 2:
       if (cs) launch_sell_t<V, 2, UNIT, true>(M, epi, a, s);
       else launch_sell_t<V, 2, UNIT, false>(M, epi, a, s);
       break;
-    case 4: launch_sell_t<V, 4, UNIT, false>(M, epi, a, s); break;
-    case 8: launch_sell_t<V, 8, UNIT, false>(M, epi, a, s); break;
+    case 4:
+      if (cs) launch_sell_t<V, 4, UNIT, true>(M, epi, a, s);
+      else launch_sell_t<V, 4, UNIT, false>(M, epi, a, s);
+      break;
+    case 8:
+      if (cs) launch_sell_t<V, 8, UNIT, true>(M, epi, a, s);
+      else launch_sell_t<V, 8, UNIT, false>(M, epi, a, s);
+      break;
     default:
       if (cs) launch_sell_t<V, 1, UNIT, true>(M, epi, a, s);
       else launch_sell_t<V, 1, UNIT, false>(M, epi, a, s);
