@@ -202,7 +202,7 @@ constexpr int kRedSlots = 5;
 enum : int { kSlotPQ = 0, kSlotRR = 1, kSlotRZ = 2, kSlotZQ = 3, kSlotDot = 4 };
 constexpr int kMaxRedBlocks = 16384;  // capacity of the block-partial arrays (single vector)
 constexpr int kMaxRedBlocksMM = 1024;  // block-partial capacity per column (blocks of vectors)
-constexpr int kVecRedBlocks = 4096;   // grid cap of the vector reductions (one resident wave is used)
+constexpr int kVecRedBlocks = 4096;   // upper cap of the one-resident-wave grid of the vector kernels
 
 // Single-vector reductions: kernels store one partial per block in a slot, and a
 // one-block kernel sums the slot in index order (deterministic: the grid depends on

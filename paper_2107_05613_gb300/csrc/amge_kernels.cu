@@ -12,9 +12,10 @@
 // smoother (eq. 4.1) and of Algorithm 4.1: residuals, the l1-Jacobi sweep, diagonal
 // scaling and correction adds.
 //
-// Reductions (PCG dot products) are deterministic: a fixed grid (a function of n
-// only) writes block partials, and the last block to arrive sums them in index
-// order with a fixed tree.
+// Reductions (PCG dot products) are deterministic: a fixed grid (a function of n and
+// the device only) writes block partials, and a one-block kernel sums them in index
+// order with a fixed tree (see the PCG kernels below for why there is no in-kernel
+// grid-wide finish).
 #include <algorithm>
 #include <atomic>
 
@@ -502,8 +503,8 @@ __global__ void __launch_bounds__(kFinishBlock) k_pcg_loop_cond(cudaGraphConditi
 }
 
 // Blocks of kBlock threads that fill every SM of the current device once (2048
-// resident threads per SM; all the streaming kernels here use at most 32
-// registers).  Cached per device; the value is a property of the device only, so
+// resident threads per SM; the streaming kernels that use this grid are compiled
+// for 8 resident blocks of kBlock threads per SM, i.e. at most 32 registers).  Cached per device; the value is a property of the device only, so
 // grids built from it keep the reductions deterministic.
 int resident_blocks() {
   static std::atomic<int> cache[64];
