@@ -198,8 +198,8 @@ def a_fine_bytes_per_launch(hh, w, nrhs=1, ag=False):
 
 
 def vcycle_bytes(hh, w, ag_nnz=None):
-    """Algorithmic bytes of one V-cycle (every level's sweeps, transfers and the
-    coarsest triangular products, which always read FP64 factors)."""
+    """Algorithmic bytes of one single-vector V-cycle (every level's sweeps, transfers
+    and the coarsest solve, which always reads the FP64 inverse)."""
     import numpy as np
 
     tot = 0.0
@@ -223,7 +223,7 @@ def vcycle_bytes(hh, w, ag_nnz=None):
         tot += P.nnz * (w + 4) + 4 * (nc + 1) + w * (n + nc)          # P^T r
         tot += P.nnz * (w + 4) + 4 * (n + 1) + w * (nc + 2 * n)       # x += P e
     nL = hh.A[-1].shape[0]
-    tot += 2 * (8 * nL * (nL + 1) / 2) + 4 * w * nL
+    tot += 8 * nL * nL + 2 * w * nL   # the explicit FP64 inverse of the coarsest matrix
     return tot
 
 
@@ -425,8 +425,8 @@ def run_ours(args, dist):
                                       + ("FP32" if w == 4 else "FP64"),
                             "bytes_per_launch": bytes_launch, "peak_source": peak_src}
     vc_ms = sum(prof[k][1] for k in ("A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "vcycle_vec", "AG"))
-    n_vc = sum(iters) + len(iters)  # one V-cycle per iteration plus the initial one (speculative ones add)
-    n_vc = prof["coarse"][0] / 2          # one coarsest solve (two kernels) per V-cycle
+    # one coarsest solve per V-cycle: one kernel for a single vector, two for a block
+    n_vc = prof["coarse"][0] / (2 if nrhs > 1 else 1)
     if vc_ms > 0 and n_vc > 0:
         pname = "fp64" if w == 8 else "fp32"
         ag_nnz = [(hh.A[l].to_scipy() @ hh.G[l].to_scipy()).nnz if tuned.get((l, pname, "AG"), -1) >= 0 else None

@@ -72,6 +72,7 @@ struct amge_hier {
   DevCsr<double> cA0;  // its CSR copy (multi-RHS products)
   int nC = 0;
   double *Linv = nullptr, *LinvT = nullptr, *ct = nullptr;
+  double* Ainv = nullptr;  // explicit coarsest inverse (single-vector V-cycles)
   double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
   double *stage_b = nullptr, *stage_x = nullptr;
   float *s32_in = nullptr, *s32_out = nullptr;
@@ -290,8 +291,8 @@ template <typename V>
 void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_ready = false) {
   auto& lv = levels<V>(h);
   if (l == h->L - 1) {
-    Prof p(h, AMGE_PROF_COARSE, s, 2);
-    launch_coarse<V, V>(h->nC, h->Linv, h->LinvT, b, h->ct, z, s);
+    Prof p(h, AMGE_PROF_COARSE, s);
+    launch_coarse_inv<V, V>(h->nC, h->Ainv, b, z, s);
     return;
   }
   LevelDev<V>& d = lv[l];
@@ -410,8 +411,8 @@ void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, 
                        bool x0_ready = false) {
   if (precision == AMGE_FP64) {
     if (h->L == 1) {
-      Prof p(h, AMGE_PROF_COARSE, s, 2);
-      launch_coarse<double, double>(h->nC, h->Linv, h->LinvT, r, h->ct, z, s);
+      Prof p(h, AMGE_PROF_COARSE, s);
+      launch_coarse_inv<double, double>(h->nC, h->Ainv, r, z, s);
       return;
     }
     vcycle_level<double>(h, 0, r, z, s, x0_ready);
@@ -422,8 +423,8 @@ void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, 
       launch_cast<double, float>(h->n0, r, d.b, s);
     }
     if (h->L == 1) {
-      Prof p(h, AMGE_PROF_COARSE, s, 2);
-      launch_coarse<float, float>(h->nC, h->Linv, h->LinvT, d.b, h->ct, d.z, s);
+      Prof p(h, AMGE_PROF_COARSE, s);
+      launch_coarse_inv<float, float>(h->nC, h->Ainv, d.b, d.z, s);
     } else {
       vcycle_level<float>(h, 0, d.b, d.z, s, x0_ready);
     }
@@ -1476,6 +1477,12 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
         h->nC = n[l];
         keepd.push_back(std::move(Li));
         h->Linv = upload<double>(h, keepd.back().data(), (size_t)n[l] * n[l], s);
+        {
+          std::vector<double> Ai;
+          coarse_inverse(n[l], LiT, Ai);
+          keepd.push_back(std::move(Ai));
+          h->Ainv = upload<double>(h, keepd.back().data(), (size_t)n[l] * n[l], s);
+        }
         keepd.push_back(std::move(LiT));
         h->LinvT = upload<double>(h, keepd.back().data(), (size_t)n[l] * n[l], s);
         if (L == 1) {
@@ -1628,7 +1635,7 @@ amge_status amge::hier_make_view(const amge_hier* src, cudaStream_t s, amge_hier
   v->lv64 = src->lv64;  // operator pointers shared; alloc_work replaces the work pointers
   v->lv32 = src->lv32;
   v->A0 = src->A0, v->cA0 = src->cA0;
-  v->nC = src->nC, v->Linv = src->Linv, v->LinvT = src->LinvT;
+  v->nC = src->nC, v->Linv = src->Linv, v->LinvT = src->LinvT, v->Ainv = src->Ainv;
   v->use_graphs = src->use_graphs;
   v->base = src->base ? src->base : src;
   amge_status st = alloc_work(v, s);

@@ -195,6 +195,24 @@ bool coarse_factor(const HostCsr& Ac, std::vector<double>& Linv, std::vector<dou
   return true;
 }
 
+// A^{-1} = L^{-T} L^{-1} (symmetric, full n x n row-major): entry (i, j) sums
+// Linv[k][i] Linv[k][j] over k >= max(i, j) (Linv is lower triangular), read along
+// rows i and j of LinvT.
+void coarse_inverse(int n, const std::vector<double>& LinvT, std::vector<double>& Ainv) {
+  Ainv.assign((size_t)n * n, 0.0);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int i = 0; i < n; i++) {
+    const double* ri = &LinvT[(size_t)i * n];
+    for (int j = i; j < n; j++) {
+      const double* rj = &LinvT[(size_t)j * n];
+      double s = 0.0;
+      for (int k = j; k < n; k++) s += ri[k] * rj[k];
+      Ainv[(size_t)i * n + j] = s;
+      Ainv[(size_t)j * n + i] = s;
+    }
+  }
+}
+
 HostSell build_sell(const HostCsr& M, int sigma, bool allow_unit) {
   constexpr int C = 32;
   HostSell S;

@@ -182,6 +182,9 @@ void launch_cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s);
 template <typename Tin, typename Tout>
 void launch_coarse(int n, const double* Linv, const double* LinvT, const Tin* b, double* t, Tout* z,
                    cudaStream_t s);
+// The same solve as one dense product z = A^{-1} b with the explicit inverse.
+template <typename Tin, typename Tout>
+void launch_coarse_inv(int n, const double* Ainv, const Tin* b, Tout* z, cudaStream_t s);
 
 // Reduction scratch: block partials + an arrival counter per slot, and scalars.
 enum Scalar : int {
@@ -316,6 +319,8 @@ std::vector<double> aux_l1_row_sums(const HostCsr& A, const HostCsr& G, const Ho
 // Dense Cholesky of the coarsest matrix; returns false if not SPD.  Linv = L^{-1}
 // (row-major, lower triangle), LinvT its transpose (row-major, upper triangle).
 bool coarse_factor(const HostCsr& A, std::vector<double>& Linv, std::vector<double>& LinvT);
+// A^{-1} = L^{-T} L^{-1} from the transposed inverse factor (full n x n, row-major).
+void coarse_inverse(int n, const std::vector<double>& LinvT, std::vector<double>& Ainv);
 
 // Read-only view of a hierarchy's coarsest factor (defined in amge_api.cu).
 void coarse_factor_view(const amge_hier* h, int* n, const double** Linv, const double** LinvT);

@@ -275,6 +275,29 @@ __global__ void __launch_bounds__(kTriBlock) k_trimv(int n, const double* __rest
   if (threadIdx.x == 0) y[row] = (Tout)t;
 }
 
+// z = A^{-1} b with the explicit symmetric inverse (full rows): one kTriBlock-thread
+// block per row, the same partial-sum scheme as k_trimv.  One launch and one pass over
+// n^2 entries replace the two triangular products (no intermediate vector).
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kTriBlock) k_densemv(int n, const double* __restrict__ M, const Tin* __restrict__ x,
+                                                       Tout* __restrict__ y) {
+  pdl_begin();
+  __shared__ double part[kTriBlock];
+  const int row = blockIdx.x;
+  const double* m = M + (size_t)row * n;
+  double s = 0.0;
+  for (int j = (int)threadIdx.x; j < n; j += kTriBlock) s = fma(ldg(m + j), (double)ldg(x + j), s);
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  double t = part[threadIdx.x];
+#pragma unroll
+  for (int k = 1; k < kTriBlock / 32; k++) t += part[threadIdx.x + 32 * k];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  if (threadIdx.x == 0) y[row] = (Tout)t;
+}
+
 // ---------------------------------------------------------------- reductions
 // Block sum in a fixed order, valid in thread 0.  On GB300 every FP64 add counts (the
 // FP64 pipe runs at 1/65 of the FP32 rate and a warp-wide add occupies it as long as
@@ -652,6 +675,13 @@ void launch_coarse(int n, const double* Linv, const double* LinvT, const Tin* b,
   launch_k(k_trimv<true, Tin, double>, n, kTriBlock, s, n, Linv, b, t);
   launch_k(k_trimv<false, double, Tout>, n, kTriBlock, s, n, LinvT, t, z);
 }
+template <typename Tin, typename Tout>
+void launch_coarse_inv(int n, const double* Ainv, const Tin* b, Tout* z, cudaStream_t s) {
+  if (n > 0) launch_k(k_densemv<Tin, Tout>, n, kTriBlock, s, n, Ainv, b, z);
+}
+template void launch_coarse_inv<double, double>(int, const double*, const double*, double*, cudaStream_t);
+template void launch_coarse_inv<float, float>(int, const double*, const float*, float*, cudaStream_t);
+
 template void launch_coarse<double, double>(int, const double*, const double*, const double*, double*, double*,
                                             cudaStream_t);
 template void launch_coarse<float, float>(int, const double*, const double*, const float*, double*, float*,
