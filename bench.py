@@ -425,8 +425,8 @@ def run_ours(args, dist):
                                       + ("FP32" if w == 4 else "FP64"),
                             "bytes_per_launch": bytes_launch, "peak_source": peak_src}
     vc_ms = sum(prof[k][1] for k in ("A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "vcycle_vec", "AG"))
-    # one coarsest solve per V-cycle: one kernel for a single vector, two for a block
-    n_vc = prof["coarse"][0] / (2 if nrhs > 1 else 1)
+    # one coarsest solve per V-cycle: one kernel (FP32 V-cycle: widening + product)
+    n_vc = prof["coarse"][0] / (2 if w == 4 else 1)
     if vc_ms > 0 and n_vc > 0:
         pname = "fp64" if w == 8 else "fp32"
         ag_nnz = [(hh.A[l].to_scipy() @ hh.G[l].to_scipy()).nnz if tuned.get((l, pname, "AG"), -1) >= 0 else None

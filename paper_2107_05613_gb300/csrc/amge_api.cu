@@ -291,8 +291,8 @@ template <typename V>
 void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_ready = false) {
   auto& lv = levels<V>(h);
   if (l == h->L - 1) {
-    Prof p(h, AMGE_PROF_COARSE, s);
-    launch_coarse_inv<V, V>(h->nC, h->Ainv, b, z, s);
+    Prof p(h, AMGE_PROF_COARSE, s, std::is_same<V, float>::value ? 2 : 1);  // FP32: + the widening
+    launch_coarse_inv<V, V>(h->nC, h->Ainv, b, h->ct, z, s);
     return;
   }
   LevelDev<V>& d = lv[l];
@@ -412,7 +412,7 @@ void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, 
   if (precision == AMGE_FP64) {
     if (h->L == 1) {
       Prof p(h, AMGE_PROF_COARSE, s);
-      launch_coarse_inv<double, double>(h->nC, h->Ainv, r, z, s);
+      launch_coarse_inv<double, double>(h->nC, h->Ainv, r, h->ct, z, s);
       return;
     }
     vcycle_level<double>(h, 0, r, z, s, x0_ready);
@@ -423,8 +423,8 @@ void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, 
       launch_cast<double, float>(h->n0, r, d.b, s);
     }
     if (h->L == 1) {
-      Prof p(h, AMGE_PROF_COARSE, s);
-      launch_coarse_inv<float, float>(h->nC, h->Ainv, d.b, d.z, s);
+      Prof p(h, AMGE_PROF_COARSE, s, 2);
+      launch_coarse_inv<float, float>(h->nC, h->Ainv, d.b, h->ct, d.z, s);
     } else {
       vcycle_level<float>(h, 0, d.b, d.z, s, x0_ready);
     }
@@ -825,8 +825,8 @@ template <typename V>
 void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream_t s, bool x_ready = false) {
   auto& lv = levels<V>(h);
   if (l == h->L - 1) {
-    Prof p(h, AMGE_PROF_COARSE, s, 2);
-    launch_coarse_mm<V, V>(h->nC, nrhs, h->Linv, h->LinvT, b, h->CT, z, s);
+    Prof p(h, AMGE_PROF_COARSE, s, std::is_same<V, float>::value ? 2 : 1);  // FP32: + the widening
+    launch_coarse_inv_mm<V, V>(h->nC, nrhs, h->Ainv, b, h->CT, z, s);
     return;
   }
   LevelDev<V>& d = lv[l];

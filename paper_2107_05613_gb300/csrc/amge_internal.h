@@ -170,6 +170,9 @@ void launch_mul_mm(int64_t n, int nrhs, const V* d, const V* x, V* y, cudaStream
 template <typename Tin, typename Tout>
 void launch_coarse_mm(int n, int nrhs, const double* Linv, const double* LinvT, const Tin* b, double* t, Tout* z,
                       cudaStream_t s);
+// Z = A^{-1} B with the explicit inverse (one launch).
+template <typename Tin, typename Tout>
+void launch_coarse_inv_mm(int n, int nrhs, const double* Ainv, const Tin* b, double* t, Tout* z, cudaStream_t s);
 // y = d .* x (elementwise)
 template <typename V>
 void launch_mul(int64_t n, const V* d, const V* x, V* y, cudaStream_t s);
@@ -184,7 +187,7 @@ void launch_coarse(int n, const double* Linv, const double* LinvT, const Tin* b,
                    cudaStream_t s);
 // The same solve as one dense product z = A^{-1} b with the explicit inverse.
 template <typename Tin, typename Tout>
-void launch_coarse_inv(int n, const double* Ainv, const Tin* b, Tout* z, cudaStream_t s);
+void launch_coarse_inv(int n, const double* Ainv, const Tin* b, double* t, Tout* z, cudaStream_t s);
 
 // Reduction scratch: block partials + an arrival counter per slot, and scalars.
 enum Scalar : int {

@@ -18,6 +18,7 @@
 // grid-wide finish).
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "amge_internal.h"
 
@@ -675,12 +676,20 @@ void launch_coarse(int n, const double* Linv, const double* LinvT, const Tin* b,
   launch_k(k_trimv<true, Tin, double>, n, kTriBlock, s, n, Linv, b, t);
   launch_k(k_trimv<false, double, Tout>, n, kTriBlock, s, n, LinvT, t, z);
 }
+// An FP32 input is widened once into t (each entry is read by every row, and a
+// float-to-double conversion issues on GB300's scarce FP64 pipe).
 template <typename Tin, typename Tout>
-void launch_coarse_inv(int n, const double* Ainv, const Tin* b, Tout* z, cudaStream_t s) {
-  if (n > 0) launch_k(k_densemv<Tin, Tout>, n, kTriBlock, s, n, Ainv, b, z);
+void launch_coarse_inv(int n, const double* Ainv, const Tin* b, double* t, Tout* z, cudaStream_t s) {
+  if (n <= 0) return;
+  if (std::is_same<Tin, double>::value) {
+    launch_k(k_densemv<Tin, Tout>, n, kTriBlock, s, n, Ainv, b, z);
+  } else {
+    launch_cast<Tin, double>(n, b, t, s);
+    launch_k(k_densemv<double, Tout>, n, kTriBlock, s, n, Ainv, (const double*)t, z);
+  }
 }
-template void launch_coarse_inv<double, double>(int, const double*, const double*, double*, cudaStream_t);
-template void launch_coarse_inv<float, float>(int, const double*, const float*, float*, cudaStream_t);
+template void launch_coarse_inv<double, double>(int, const double*, const double*, double*, double*, cudaStream_t);
+template void launch_coarse_inv<float, float>(int, const double*, const float*, double*, float*, cudaStream_t);
 
 template void launch_coarse<double, double>(int, const double*, const double*, const double*, double*, double*,
                                             cudaStream_t);

@@ -158,7 +158,8 @@ __global__ void k_mul_mm(int64_t n, int nrhs, const V* __restrict__ d, const V* 
 // per column; warp w takes the triangle's entries j = beg + w, beg + w + 8, ... and the
 // eight partial sums per column meet in shared memory (added in warp order), so a row
 // of ~n/2 entries runs as eight short chains instead of one long one.
-template <bool LOWER, typename Tin, typename Tout>
+// TRI: 1 the lower triangle, 2 the upper one, 0 the full row (explicit inverse).
+template <int TRI, typename Tin, typename Tout>
 __global__ void __launch_bounds__(kBlock) k_trimm(int n, int nrhs, const double* __restrict__ M,
                                                   const Tin* __restrict__ x, Tout* __restrict__ y) {
   pdl_begin();
@@ -170,8 +171,8 @@ __global__ void __launch_bounds__(kBlock) k_trimm(int n, int nrhs, const double*
   double s0 = 0.0, s1 = 0.0;
   if (c < nrhs) {
     const double* m = M + (size_t)row * n;
-    const int beg = LOWER ? 0 : row;
-    const int end = LOWER ? row + 1 : n;
+    const int beg = TRI == 2 ? row : 0;
+    const int end = TRI == 1 ? row + 1 : n;
     int j = beg + w;
     for (; j + NW < end; j += 2 * NW) {
       s0 = fma(ldg(m + j), (double)ldg(x + (size_t)j * nrhs + c), s0);
@@ -436,9 +437,26 @@ template <typename Tin, typename Tout>
 void launch_coarse_mm(int n, int nrhs, const double* Linv, const double* LinvT, const Tin* b, double* t, Tout* z,
                       cudaStream_t s) {
   if (n == 0) return;
-  launch_k(k_trimm<true, Tin, double>, n, kBlock, s, n, nrhs, Linv, b, t);
-  launch_k(k_trimm<false, double, Tout>, n, kBlock, s, n, nrhs, LinvT, t, z);
+  launch_k(k_trimm<1, Tin, double>, n, kBlock, s, n, nrhs, Linv, b, t);
+  launch_k(k_trimm<2, double, Tout>, n, kBlock, s, n, nrhs, LinvT, t, z);
 }
+
+// An FP32 block is widened once into t (float-to-double conversions issue on the FP64
+// pipe, and every entry would otherwise be converted once per row).
+template <typename Tin, typename Tout>
+void launch_coarse_inv_mm(int n, int nrhs, const double* Ainv, const Tin* b, double* t, Tout* z, cudaStream_t s) {
+  if (n <= 0) return;
+  if (std::is_same<Tin, double>::value) {
+    launch_k(k_trimm<0, Tin, Tout>, n, kBlock, s, n, nrhs, Ainv, b, z);
+  } else {
+    launch_cast<Tin, double>((int64_t)n * nrhs, b, t, s);
+    launch_k(k_trimm<0, double, Tout>, n, kBlock, s, n, nrhs, Ainv, (const double*)t, z);
+  }
+}
+template void launch_coarse_inv_mm<double, double>(int, int, const double*, const double*, double*, double*,
+                                                   cudaStream_t);
+template void launch_coarse_inv_mm<float, float>(int, int, const double*, const float*, double*, float*,
+                                                 cudaStream_t);
 template void launch_coarse_mm<double, double>(int, int, const double*, const double*, const double*, double*,
                                                double*, cudaStream_t);
 template void launch_coarse_mm<float, float>(int, int, const double*, const double*, const float*, double*, float*,
