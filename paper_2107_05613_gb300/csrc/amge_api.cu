@@ -760,24 +760,9 @@ amge_status launch_status();
 // Size the block workspace for nrhs right-hand sides (grows, never shrinks).
 }  // namespace
 
-// Bytes of the block workspace ensure_mm allocates for cap columns.
-size_t amge::hier_block_workspace_bytes(const amge_hier* h, int cap) {
-  size_t b = 0;
-  for (int l = 0; l < h->L; l++) {
-    const size_t n = (size_t)h->lv64[l].n * cap, na = (size_t)h->lv64[l].naux * cap;
-    if (l + 1 < h->L) b += 3 * n * (sizeof(double) + sizeof(float)) + na * (sizeof(double) + sizeof(float));
-    b += 2 * n * (sizeof(double) + sizeof(float));
-  }
-  const size_t n0 = (size_t)h->n0 * cap;
-  b += 6 * n0 * sizeof(double) + 2 * n0 * sizeof(float) + (size_t)h->nC * cap * sizeof(double);
-  b += (size_t)kRedSlots * kMaxRedBlocksMM * kMaxRhs * sizeof(double) + SC_COUNT * kMaxRhs * sizeof(double);
-  return b;
-}
-
 // Block workspace for up to cap columns (allocated once per hierarchy: a later call
 // needing more than the first call's cap fails with AMGE_EINVAL).  amge_pcg_solve and
-// amge_vcycle size it for 32 columns; the request server sizes its workspace views
-// for the requests they serve.
+// amge_vcycle size it for 32 columns.
 amge_status amge::ensure_mm(amge_hier* h, int nrhs, cudaStream_t s, int cap) {
   if (nrhs <= h->mm_cap) return AMGE_OK;
   if (h->mm_cap > 0 || nrhs > cap || cap > kMaxRhs) {

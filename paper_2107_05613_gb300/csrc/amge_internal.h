@@ -303,7 +303,6 @@ void pcg_mm_run_wait_event(PcgRunMM* r);
 amge_status pcg_mm_run_finish(PcgRunMM* r, amge_info* info);  // frees r
 void pcg_mm_run_free(PcgRunMM* r);                            // abandons r
 amge_status ensure_mm(amge_hier* h, int nrhs, cudaStream_t s, int cap = kMaxRhs);
-size_t hier_block_workspace_bytes(const amge_hier* h, int cap);
 // A view shares the level operators of `src` and owns a separate workspace (so
 // solves on different views run concurrently without interfering).
 amge_status hier_make_view(const amge_hier* src, cudaStream_t s, amge_hier** out);
