@@ -111,23 +111,42 @@ template <typename V, int EPI, int WPS, bool UNIT, bool CS>
 __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __restrict__ sptr,
                                                  const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                  const typename Pair<V>::T* __restrict__ val2, SpmvArgs<V> a) {
-  pdl_begin();
+  using PV = typename Pair<V>::T;
   constexpr bool NEG = SellNeg<EPI>::value;
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int g = wib % WPS;
   const int slice = (blockIdx.x * (kBlock / 32) + wib) / WPS;
-  V s = V(0);
-  int row = -1;
-  if (slice < nslices) {
+  const bool live = slice < nslices;
+  // The operator is read-only for the life of the hierarchy, so the slice header and
+  // this warp's first entry pair are loaded before waiting for the previous kernel.
+  int row = -1, np = 0;
+  const int2* cp = ci2;
+  const PV* vp = val2;
+  int2 c0 = make_int2(kSellPad, kSellPad);
+  PV v0{};
+  if (live) {
     const int64_t p0 = ldg(sptr + slice) >> 1;
-    const int np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+    np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
     row = ldg(srow + (size_t)slice * 32 + lane);
+    cp += p0 + lane;
+    if (!UNIT) vp += p0 + lane;
+    if (g < np) {
+      c0 = ldm<CS>(cp + (size_t)g * 32);
+      if (!UNIT) v0 = ldm<CS>(vp + (size_t)g * 32);
+    }
+  }
+  pdl_begin();
+  V s = V(0);
+  if (live) {
     if (g == 0) s = sell_init<V, EPI>(a, row);
-    const int2* cp = ci2 + p0 + lane;
     if (UNIT) {
+      if (g < np) {
+        s += signed_entry<NEG>(a.x, c0.x);
+        s += signed_entry<NEG>(a.x, c0.y);
+      }
 #pragma unroll 2
-      for (int k = g; k < np; k += WPS) {
+      for (int k = g + WPS; k < np; k += WPS) {
         const int2 c = ldm<CS>(cp + (size_t)k * 32);
         const V e0 = signed_entry<NEG>(a.x, c.x);
         const V e1 = signed_entry<NEG>(a.x, c.y);
@@ -135,11 +154,15 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
         s += e1;
       }
     } else {
-      const typename Pair<V>::T* vp = val2 + p0 + lane;
+      if (g < np) {
+        const V x0 = ldg(a.x + c0.x), x1 = ldg(a.x + c0.y);
+        s = fma(NEG ? -v0.x : v0.x, x0, s);
+        s = fma(NEG ? -v0.y : v0.y, x1, s);
+      }
 #pragma unroll 2
-      for (int k = g; k < np; k += WPS) {
+      for (int k = g + WPS; k < np; k += WPS) {
         const int2 c = ldm<CS>(cp + (size_t)k * 32);
-        const typename Pair<V>::T v = ldm<CS>(vp + (size_t)k * 32);
+        const PV v = ldm<CS>(vp + (size_t)k * 32);
         const V x0 = ldg(a.x + c.x), x1 = ldg(a.x + c.y);
         s = fma(NEG ? -v.x : v.x, x0, s);
         s = fma(NEG ? -v.y : v.y, x1, s);
@@ -154,34 +177,52 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
 #pragma unroll
     for (int j = 1; j < WPS; j++) s += part[threadIdx.x + 32 * j];
   }
-  if (slice >= nslices || row < 0) return;
+  if (!live || row < 0) return;
   sell_store<V, EPI>(a, row, s);
 }
 
-// G y (two sign-coded entries) and A G y for one row per lane (see AgArgs).
+// G y (two sign-coded entries) and A G y for one row per lane (see AgArgs).  As in
+// k_sell, the constant slice header, G's row and the first entry pair are loaded
+// before waiting for the previous kernel.
 template <typename V, bool POST, bool CS>
 __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t* __restrict__ sptr,
                                                      const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                      const typename Pair<V>::T* __restrict__ val2, AgArgs<V> a) {
-  pdl_begin();
+  using PV = typename Pair<V>::T;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= nslices) return;
-  const int64_t p0 = ldg(sptr + warp) >> 1;
-  const int np = (int)((ldg(sptr + warp + 1) >> 1) - p0) >> 5;
-  const int row = ldg(srow + (size_t)warp * 32 + lane);
+  int row = -1, np = 0;
+  const int2* cp = ci2;
+  const PV* vp = val2;
+  int2 g = make_int2(kSellPad, kSellPad), c0 = g;
+  PV v0{};
+  if (warp < nslices) {
+    const int64_t p0 = ldg(sptr + warp) >> 1;
+    np = (int)((ldg(sptr + warp + 1) >> 1) - p0) >> 5;
+    row = ldg(srow + (size_t)warp * 32 + lane);
+    cp += p0 + lane;
+    vp += p0 + lane;
+    if (row >= 0) g = ldg(a.g2 + row);
+    if (np > 0) {
+      c0 = ldm<CS>(cp);
+      v0 = ldm<CS>(vp);
+    }
+  }
+  pdl_begin();
   if (row < 0) return;
-  const int2 g = ldg(a.g2 + row);
   V gx = a.x[row];
   gx += signed_entry<false>(a.y, g.x);
   gx += signed_entry<false>(a.y, g.y);
   V s = a.r[row];
-  const int2* cp = ci2 + p0 + lane;
-  const typename Pair<V>::T* vp = val2 + p0 + lane;
+  if (np > 0) {
+    const V x0 = ldg(a.y + c0.x), x1 = ldg(a.y + c0.y);
+    s = fma(-v0.x, x0, s);
+    s = fma(-v0.y, x1, s);
+  }
 #pragma unroll 2
-  for (int k = 0; k < np; k++) {
+  for (int k = 1; k < np; k++) {
     const int2 c = ldm<CS>(cp + (size_t)k * 32);
-    const typename Pair<V>::T v = ldm<CS>(vp + (size_t)k * 32);
+    const PV v = ldm<CS>(vp + (size_t)k * 32);
     const V x0 = ldg(a.y + c.x), x1 = ldg(a.y + c.y);
     s = fma(-v.x, x0, s);
     s = fma(-v.y, x1, s);
@@ -278,16 +319,31 @@ __global__ void __launch_bounds__(kTriBlock) k_trimv(int n, const double* __rest
 
 // z = A^{-1} b with the explicit symmetric inverse (full rows): one kTriBlock-thread
 // block per row, the same partial-sum scheme as k_trimv.  One launch and one pass over
-// n^2 entries replace the two triangular products (no intermediate vector).
+// n^2 entries replace the two triangular products (no intermediate vector).  The
+// inverse is constant, so each thread loads its first kDensePre entries of the row
+// before waiting for the kernel that produces x.
+constexpr int kDensePre = 8;
 template <typename Tin, typename Tout>
-__global__ void __launch_bounds__(kTriBlock) k_densemv(int n, const double* __restrict__ M, const Tin* __restrict__ x,
+__global__ void __launch_bounds__(kTriBlock, 16) k_densemv(int n, const double* __restrict__ M, const Tin* __restrict__ x,
                                                        Tout* __restrict__ y) {
-  pdl_begin();
   __shared__ double part[kTriBlock];
   const int row = blockIdx.x;
   const double* m = M + (size_t)row * n;
+  double mr[kDensePre];
+#pragma unroll
+  for (int i = 0; i < kDensePre; i++) {
+    const int j = (int)threadIdx.x + i * kTriBlock;
+    mr[i] = j < n ? ldg(m + j) : 0.0;
+  }
+  pdl_begin();
   double s = 0.0;
-  for (int j = (int)threadIdx.x; j < n; j += kTriBlock) s = fma(ldg(m + j), (double)ldg(x + j), s);
+#pragma unroll
+  for (int i = 0; i < kDensePre; i++) {
+    const int j = (int)threadIdx.x + i * kTriBlock;
+    if (j < n) s = fma(mr[i], (double)ldg(x + j), s);
+  }
+  for (int j = (int)threadIdx.x + kDensePre * kTriBlock; j < n; j += kTriBlock)
+    s = fma(ldg(m + j), (double)ldg(x + j), s);
   part[threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.x >= 32) return;
@@ -369,23 +425,40 @@ __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, 
                                                                    const double2* __restrict__ val2,
                                                                    const double* __restrict__ p,
                                                                    double* __restrict__ q, double* part) {
-  pdl_begin();
   __shared__ double sh[kSpmvDotBlock];
   __shared__ unsigned arrived;
   if (threadIdx.x == 0) arrived = 0u;
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int slice = (blockIdx.x * kSpmvDotBlock + threadIdx.x) >> 5;
-  double contrib = 0.0;
+  // constant slice header and first entry pair before waiting (see k_sell)
+  int row = -1, np = 0;
+  const int2* cp = ci2;
+  const double2* vp = val2;
+  int2 c0 = make_int2(0, 0);
+  double2 v0 = make_double2(0.0, 0.0);
   if (slice < nslices) {
     const int64_t p0 = ldg(sptr + slice) >> 1;
-    const int np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
-    const int row = ldg(srow + (size_t)slice * 32 + lane);
-    const int2* cp = ci2 + p0 + lane;
-    const double2* vp = val2 + p0 + lane;
+    np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+    row = ldg(srow + (size_t)slice * 32 + lane);
+    cp += p0 + lane;
+    vp += p0 + lane;
+    if (np > 0) {
+      c0 = ldm<CS>(cp);
+      v0 = ldm<CS>(vp);
+    }
+  }
+  pdl_begin();
+  __syncthreads();
+  double contrib = 0.0;
+  if (slice < nslices) {
     double acc = 0.0;
+    if (np > 0) {
+      const double x0 = ldg(p + c0.x), x1 = ldg(p + c0.y);
+      acc = fma(v0.x, x0, acc);
+      acc = fma(v0.y, x1, acc);
+    }
 #pragma unroll 2
-    for (int k = 0; k < np; k++) {
+    for (int k = 1; k < np; k++) {
       const int2 c = ldm<CS>(cp + (size_t)k * 32);
       const double2 v = ldm<CS>(vp + (size_t)k * 32);
       const double x0 = ldg(p + c.x), x1 = ldg(p + c.y);
