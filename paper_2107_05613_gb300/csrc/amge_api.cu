@@ -329,15 +329,17 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
       launch_mul<V>(d.n, d.minv, b, x, s);
     }
     // G y and (A G) y in one pass where G is the two-entry gradient and both
-    // products run the one-warp sliced-ELL kernels (identical results)
-    const bool fused = d.g2 && d.lanes[OP_AG] == 0 && d.lanes[OP_G] == 0;
+    // products run sliced-ELL kernels (identical results to the separate products)
+    const int ag = d.lanes[OP_AG];
+    const bool fused = d.g2 && (ag == 0 || ag >= 100) && d.lanes[OP_G] == 0;
+    const int ag_wps = ag >= 100 ? ag / 100 : 1;
     residual();
     if (fused) {
       aux_gt();
       Prof p(h, AMGE_PROF_AG, s);
       AgArgs<V> f;  // x += G y; r -= (A G) y
       f.y = d.y, f.g2 = d.g2, f.x = x, f.r = d.r;
-      launch_ag_fused<V>(d.AG, 0, f, s);
+      launch_ag_fused<V>(d.AG, 0, f, s, ag_wps);
     } else {
       aux_sweep();
       SpmvArgs<V> a;  // r = r - (A G) y (in place: row i reads and writes r_i only)
@@ -357,7 +359,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
       Prof p(h, AMGE_PROF_AG, s);
       AgArgs<V> f;  // z = x + G y + M^{-1} (r - (A G) y)
       f.y = d.y, f.g2 = d.g2, f.x = x, f.r = d.r, f.minv = d.minv, f.z = z;
-      launch_ag_fused<V>(d.AG, 1, f, s);
+      launch_ag_fused<V>(d.AG, 1, f, s, ag_wps);
       return;
     }
     aux_sweep();
@@ -1272,10 +1274,58 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
 // Autotuner: time every candidate kernel of every level operator (sliced ELL and
 // vector CSR with 2..32 lanes per row, up to the operator's row length) on the work
 // vectors and keep the fastest; vector CSR must beat sliced ELL by 10% to be chosen.
+// Operators that fit in L2 but do not stay there between two uses inside a V-cycle
+// are timed cold: each launch follows a read of twice L2's capacity (whose own time is
+// subtracted), and the kernel that is fastest on a warm L2 (fewest warps) is often not
+// the fastest from HBM.  A level's operators are taken to be evicted when those of
+// that level and all coarser ones (coarsest inverse included) take more than half of
+// L2: they are read cyclically and evict one another, as measured on H(curl) 64^3
+// (115 MB below level 0); a smaller working set stays resident and is timed warm.
+// Streamed operators (much larger than L2) come from HBM either way and are timed back
+// to back, where each launch overlaps the previous one's tail as it does behind its
+// predecessor in the V-cycle.
 constexpr int kTuneCodes[9] = {0, 200, 400, 800, 2, 4, 8, 16, 32};
+constexpr int kTuneReps = 10;
+
+struct TuneFlush {
+  void* buf = nullptr;
+  size_t bytes = 0;  // 2 x L2
+  double l2 = 0.0;   // L2 bytes
+  float ms = 0.f;    // kTuneReps flushes alone
+};
+
+// Best of three launches of a graph (after one warm-up launch), in ms.
+cudaError_t time_graph(cudaGraphExec_t ge, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float* best) {
+  *best = 1e30f;
+  cudaError_t le = cudaGraphLaunch(ge, s);
+  for (int trial = 0; trial < 3 && le == cudaSuccess; trial++) {
+    le = cudaEventRecord(e0, s);
+    if (le == cudaSuccess) le = cudaGraphLaunch(ge, s);
+    if (le == cudaSuccess) le = cudaEventRecord(e1, s);
+    if (le == cudaSuccess) le = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (le == cudaSuccess) le = cudaEventElapsedTime(&t, e0, e1);
+    *best = std::min(*best, t);
+  }
+  return le;
+}
+
+// Bytes of the operators a V-cycle reads on levels l0 and below (one precision's
+// copies, the coarsest inverse included).
+template <typename V>
+double coarse_bytes(const amge_hier* h, const std::vector<LevelDev<V>>& lv, int l0) {
+  auto sb = [](const DevSell<V>& M) { return (double)M.stored * (M.unit ? 4.0 : 4.0 + sizeof(V)); };
+  double b = 8.0 * h->nC * h->nC;
+  for (int l = l0; l + 1 < h->L; l++) {
+    const LevelDev<V>& d = lv[l];
+    b += sb(d.A) + sb(d.P) + sb(d.PT) + sb(d.G) + sb(d.GT) + (d.use_ag ? sb(d.AG) : 0.0);
+  }
+  return b;
+}
 
 template <typename V>
-amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                           const TuneFlush& fl) {
   LevelDev<V>& d = levels<V>(h)[l];
   LevelDev<V>& c = levels<V>(h)[l + 1];
   for (int op = 0; op < 6; op++) {
@@ -1286,6 +1336,7 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
     SpmvArgs<V> a;
     a.x = in, a.y = out;
     const double avg = M.nr ? (double)M.nnz / M.nr : 0.0;
+    const bool cold = fl.buf && !op_sell(d, op).stream && coarse_bytes<V>(h, levels<V>(h), l) > 0.5 * fl.l2;
     float best = 0.f;
     int best_lanes = 0;
     for (int ci = 0; ci < 9; ci++) {
@@ -1294,31 +1345,25 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
       if (lanes >= 100 && 2.0 * (lanes / 100) > avg + 1.0) continue;  // more warps than entry pairs
       if (lanes > 2 && lanes < 100 && lanes > 2 * avg) continue;
       d.lanes[op] = lanes;
-      // Ten back-to-back launches captured in a graph, so the host's launch rate
-      // (which bounds small kernels launched one by one) does not flatten the
-      // comparison; best of three graph launches after a warm-up.
+      // kTuneReps launches (each after an L2 flush if cold) captured in a graph, so
+      // the host's launch rate does not flatten the comparison of small kernels.
       cudaGraph_t g = nullptr;
       cudaGraphExec_t ge = nullptr;
       CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      for (int r = 0; r < 10; r++) opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
+      for (int r = 0; r < kTuneReps; r++) {
+        if (cold) launch_l2_flush(fl.buf, fl.bytes, s);
+        opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
+      }
       CK(cudaStreamEndCapture(s, &g));
       cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
       cudaGraphDestroy(g);
       CK(ie);
-      float ms = 1e30f;
-      cudaError_t le = cudaGraphLaunch(ge, s);
-      for (int trial = 0; trial < 3 && le == cudaSuccess; trial++) {
-        le = cudaEventRecord(e0, s);
-        if (le == cudaSuccess) le = cudaGraphLaunch(ge, s);
-        if (le == cudaSuccess) le = cudaEventRecord(e1, s);
-        if (le == cudaSuccess) le = cudaEventSynchronize(e1);
-        float t = 0.f;
-        if (le == cudaSuccess) le = cudaEventElapsedTime(&t, e0, e1);
-        ms = std::min(ms, t);
-      }
+      float ms = 0.f;
+      cudaError_t le = time_graph(ge, s, e0, e1, &ms);
       cudaGraphExecDestroy(ge);
       CK(le);
-      d.tune_us[op][ci] = ms * 100.f;  // 10 launches: ms * 1e3 / 10
+      if (cold) ms = std::max(ms - fl.ms, 1e-4f);
+      d.tune_us[op][ci] = ms * (1e3f / kTuneReps);
       if (lanes == 0 || ms < 0.9f * best) best = (lanes == 0 || ms < best) ? ms : best, best_lanes = lanes;
     }
     d.lanes[op] = best_lanes;
@@ -1336,14 +1381,45 @@ amge_status autotune(amge_hier* h, cudaStream_t s) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   amge_status st = AMGE_OK;
+  // flush scratch (temporary; without it the candidates are timed on a warm L2)
+  TuneFlush fl;
+  int dev = 0, l2 = 0;
+  if (h->L > 1 && cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess && l2 > 0) {
+    fl.l2 = (double)l2;
+    fl.bytes = 2 * (size_t)l2;
+    if (cudaMalloc(&fl.buf, fl.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      fl.buf = nullptr;
+    } else if (cudaMemsetAsync(fl.buf, 0, fl.bytes, ts) != cudaSuccess) {
+      set_error("autotune: cudaMemsetAsync failed");
+      st = AMGE_ECUDA;
+    }
+  }
+  if (fl.buf && st == AMGE_OK) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal);
+    for (int r = 0; r < kTuneReps && e == cudaSuccess; r++) launch_l2_flush(fl.buf, fl.bytes, ts);
+    if (e == cudaSuccess) e = cudaStreamEndCapture(ts, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e == cudaSuccess) e = time_graph(ge, ts, e0, e1, &fl.ms);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (e != cudaSuccess) {
+      set_error(std::string("autotune flush: ") + cudaGetErrorString(e));
+      st = AMGE_ECUDA;
+    }
+  }
   for (int l = 0; l + 1 < h->L && st == AMGE_OK; l++) {
-    st = autotune_level<double>(h, l, ts, e0, e1);
-    if (st == AMGE_OK) st = autotune_level<float>(h, l, ts, e0, e1);
+    st = autotune_level<double>(h, l, ts, e0, e1, fl);
+    if (st == AMGE_OK) st = autotune_level<float>(h, l, ts, e0, e1, fl);
   }
   cudaStreamSynchronize(ts);
   cudaStreamDestroy(ts);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (fl.buf) cudaFree(fl.buf);
   for (int c = 0; c < AMGE_PROF_CLASSES; c++) h->launches[c] = 0;
   return st;
 }

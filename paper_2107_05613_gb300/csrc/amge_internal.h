@@ -123,7 +123,8 @@ void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_
 //   pre  (post = 0): x_i += (G y)_i and r_i -= ((A G) y)_i
 //   post (post = 1): z_i = x_i + (G y)_i + m_i^-1 (r_i - ((A G) y)_i)
 // g2[i] holds row i of G sign-coded (see kSellPad); the sums are formed in the same
-// order as the separate G and A G products, so the results are identical.
+// order as the separate G and A G products with the same number of warps per slice
+// (wps = 1, 2, 4, 8), so the results are identical.
 template <typename V>
 struct AgArgs {
   const V* y = nullptr;    // aux vector
@@ -134,7 +135,7 @@ struct AgArgs {
   V* z = nullptr;          // post form output
 };
 template <typename V>
-void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s);
+void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, int wps = 1);
 
 template <typename V>
 struct DevCsr {
@@ -180,6 +181,8 @@ void launch_mul(int64_t n, const V* d, const V* x, V* y, cudaStream_t s);
 // Elementwise helpers.
 template <typename Tin, typename Tout>
 void launch_cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s);
+// Read `bytes` of buf (16-byte aligned, zero-filled), evicting L2's previous contents.
+void launch_l2_flush(void* buf, size_t bytes, cudaStream_t s);
 
 // Coarsest solve z = Linv^T (Linv b): two dense triangular products, FP64 accumulation.
 template <typename Tin, typename Tout>
