@@ -32,12 +32,23 @@ bool check_csr(const amge_csr& c, int nr, int nc, const char* what, std::string&
   return true;
 }
 
+// Stored zeros are dropped (the prolongators carry some: 6% of P_0's entries on the
+// H(curl) 64^3 hierarchy, 16% of P_1's): a term 0 * x adds nothing to a product with
+// finite x, and every kernel would spend an FP64 FMA and 12 bytes on it.
 HostCsr to_host(const amge_csr& c) {
   HostCsr h;
   h.nr = c.n_rows, h.nc = c.n_cols;
-  h.rp.assign(c.row_ptr, c.row_ptr + c.n_rows + 1);
-  h.ci.assign(c.col, c.col + c.nnz);
-  h.v.assign(c.val, c.val + c.nnz);
+  h.rp.assign(c.n_rows + 1, 0);
+  h.ci.reserve(c.nnz);
+  h.v.reserve(c.nnz);
+  for (int i = 0; i < c.n_rows; i++) {
+    for (int64_t p = c.row_ptr[i]; p < c.row_ptr[i + 1]; p++)
+      if (c.val[p] != 0.0) {
+        h.ci.push_back(c.col[p]);
+        h.v.push_back(c.val[p]);
+      }
+    h.rp[i + 1] = (int)h.ci.size();
+  }
   return h;
 }
 
@@ -66,13 +77,21 @@ std::vector<double> l1_row_sums(const HostCsr& A) {
   return m;
 }
 
+// C = A B in FP64.  An entry whose computed value is within 64 eps of the sum of its
+// terms' magnitudes, |c_ij| <= 64 eps (|A||B|)_ij, is dropped: it is cancellation
+// residue (for A G, of the discrete identity curl grad = 0, which A's assembly in
+// floating point leaves at about eps (|A||G|)_ij), below the product's own rounding
+// bound, so dropping it perturbs (A B) y by no more than rounding does.  On the H(curl)
+// 64^3 hierarchy the genuine entries of A_0 G_0 sit at 4e-9 of their term magnitudes
+// and above, the residue at 1.2e-16 and below; the residue is 19% of the entries.
 HostCsr sparse_product(const HostCsr& A, const HostCsr& B) {
   HostCsr C;
   C.nr = A.nr, C.nc = B.nc;
+  constexpr double kResidue = 64.0 * 2.220446049250313e-16;
   std::vector<std::vector<std::pair<int, double>>> rows(A.nr);
 #pragma omp parallel
   {
-    std::vector<double> acc(B.nc, 0.0);
+    std::vector<double> acc(B.nc, 0.0), mag(B.nc, 0.0);
     std::vector<char> seen(B.nc, 0);
     std::vector<int> touched;
 #pragma omp for schedule(dynamic, 512)
@@ -85,12 +104,14 @@ HostCsr sparse_product(const HostCsr& A, const HostCsr& B) {
           const int j = B.ci[q];
           if (!seen[j]) seen[j] = 1, touched.push_back(j);
           acc[j] += a * B.v[q];
+          mag[j] += std::fabs(a * B.v[q]);
         }
       }
       std::sort(touched.begin(), touched.end());
       for (int j : touched) {
-        if (acc[j] != 0.0) rows[i].push_back({j, acc[j]});
+        if (std::fabs(acc[j]) > kResidue * mag[j]) rows[i].push_back({j, acc[j]});
         acc[j] = 0.0;
+        mag[j] = 0.0;
         seen[j] = 0;
       }
     }
