@@ -44,6 +44,15 @@ struct Pair<float> {
   using T = float2;
 };
 
+// One bulk request that brings [p, p + bytes) into L2 (p and bytes multiples of 16).
+// A warp of an L2-sized operator's product issues it for its whole slice before
+// waiting for the previous kernel: its entry loads then find L2 instead of paying a
+// DRAM round trip per entry pair in the loop (the coarse levels' operators are
+// evicted between uses, and their few warps cannot hide that latency).
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Loads of stored matrix entries.  CS (operators much larger than L2, read once per
 // product): the streaming hint (evict-first), so the level-0 sweeps do not push the
 // coarse levels' operators out of L2 between V-cycles.
@@ -129,6 +138,10 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
     const int64_t p0 = ldg(sptr + slice) >> 1;
     np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
     row = ldg(srow + (size_t)slice * 32 + lane);
+    if (!CS && g == 0 && lane == 0 && np > 0) {
+      prefetch_l2_bulk(ci2 + p0, (uint32_t)np * 32u * sizeof(int2));
+      if (!UNIT) prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(PV));
+    }
     cp += p0 + lane;
     if (!UNIT) vp += p0 + lane;
     if (g < np) {
@@ -204,6 +217,10 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
     const int64_t p0 = ldg(sptr + slice) >> 1;
     np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
     row = ldg(srow + (size_t)slice * 32 + lane);
+    if (!CS && g == 0 && lane == 0 && np > 0) {
+      prefetch_l2_bulk(ci2 + p0, (uint32_t)np * 32u * sizeof(int2));
+      prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(PV));
+    }
     cp += p0 + lane;
     vp += p0 + lane;
     if (row >= 0 && g == 0) g2 = ldg(a.g2 + row);
