@@ -302,16 +302,19 @@ void amge_set_dependent_launch(int32_t enable);
  * A G = A_l G_l is much sparser than A_l, i.e. for H(curl): there the residual after
  * an aux sweep is updated as r - (A G) y instead of recomputed as b - A x).  The
  * choice is made at upload by timing each candidate on the level's own operator
- * (see amge_autotune_times for how).
+ * (see amge_autotune_times for how): the fastest sliced-ELL kernel, unless a vector
+ * CSR kernel is at least 10% faster.
  * lanes must hold (levels-1)*12 entries. */
 amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
 
 /* The autotuner's evidence: us[((l * 2 + p) * 6 + op) * 9 + c] = measured time per
- * launch in microseconds (STORE epilogue, ten launches replayed from a graph, best of
- * three; for an operator that fits in L2 each launch follows a read of twice L2's
- * capacity, whose time is subtracted, so the operator comes from HBM as it does inside
- * a V-cycle -- on a warm L2 if that scratch cannot be allocated; streamed operators
- * larger than L2 back to back) of candidate c in the order 0,
+ * launch in microseconds (STORE epilogue, ten launches replayed from a graph).  Where
+ * a level's operators and the coarser ones take more than half of L2, so that a
+ * V-cycle finds them evicted, each launch follows a read of twice L2's capacity and is
+ * timed by its own pair of event records (best of five replays): the operator comes
+ * from HBM as it does inside a V-cycle.  Otherwise, and for streamed operators larger
+ * than L2, the ten launches run back to back and are timed as a whole (best of
+ * three) -- also where the 2x L2 scratch cannot be allocated.  Candidate c in the order 0,
  * 200, 400, 800, 2, 4, 8, 16, 32; -1 where a
  * candidate was not measured (longer than the operator's rows) or the operator is
  * not stored.  us must hold (levels-1)*108 floats. */

@@ -1275,9 +1275,9 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
 // vector CSR with 2..32 lanes per row, up to the operator's row length) on the work
 // vectors and keep the fastest; vector CSR must beat sliced ELL by 10% to be chosen.
 // Operators that fit in L2 but do not stay there between two uses inside a V-cycle
-// are timed cold: each launch follows a read of twice L2's capacity (whose own time is
-// subtracted), and the kernel that is fastest on a warm L2 (fewest warps) is often not
-// the fastest from HBM.  A level's operators are taken to be evicted when those of
+// are timed cold: each launch follows a read of twice L2's capacity and is timed by
+// its own event records, and the kernel that is fastest on a warm L2 (fewest warps) is
+// often not the fastest from HBM.  A level's operators are taken to be evicted when those of
 // that level and all coarser ones (coarsest inverse included) take more than half of
 // L2: they are read cyclically and evict one another, as measured on H(curl) 64^3
 // (115 MB below level 0); a smaller working set stays resident and is timed warm.
@@ -1291,7 +1291,8 @@ struct TuneFlush {
   void* buf = nullptr;
   size_t bytes = 0;  // 2 x L2
   double l2 = 0.0;   // L2 bytes
-  float ms = 0.f;    // kTuneReps flushes alone
+  // external event records around each cold launch (the flush stays outside)
+  cudaEvent_t ea[kTuneReps] = {}, eb[kTuneReps] = {};
 };
 
 // Best of three launches of a graph (after one warm-up launch), in ms.
@@ -1323,6 +1324,25 @@ double coarse_bytes(const amge_hier* h, const std::vector<LevelDev<V>>& lv, int 
   return b;
 }
 
+// Cold timing: best of five graph launches (after one warm-up) of the sum of the
+// launches' own event intervals, in ms.
+cudaError_t time_graph_events(cudaGraphExec_t ge, cudaStream_t s, const TuneFlush& fl, float* best) {
+  *best = 1e30f;
+  cudaError_t le = cudaGraphLaunch(ge, s);
+  for (int trial = 0; trial < 5 && le == cudaSuccess; trial++) {
+    le = cudaGraphLaunch(ge, s);
+    if (le == cudaSuccess) le = cudaStreamSynchronize(s);
+    float sum = 0.f;
+    for (int r = 0; r < kTuneReps && le == cudaSuccess; r++) {
+      float t = 0.f;
+      le = cudaEventElapsedTime(&t, fl.ea[r], fl.eb[r]);
+      sum += t;
+    }
+    if (le == cudaSuccess) *best = std::min(*best, sum);
+  }
+  return le;
+}
+
 template <typename V>
 amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
                            const TuneFlush& fl) {
@@ -1337,36 +1357,45 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
     a.x = in, a.y = out;
     const double avg = M.nr ? (double)M.nnz / M.nr : 0.0;
     const bool cold = fl.buf && !op_sell(d, op).stream && coarse_bytes<V>(h, levels<V>(h), l) > 0.5 * fl.l2;
-    float best = 0.f;
-    int best_lanes = 0;
+    float best_sell = -1.f, best_vec = -1.f;
+    int sell_lanes = 0, vec_lanes = 0;
     for (int ci = 0; ci < 9; ci++) {
       const int lanes = kTuneCodes[ci];
       d.tune_us[op][ci] = -1.f;
       if (lanes >= 100 && 2.0 * (lanes / 100) > avg + 1.0) continue;  // more warps than entry pairs
       if (lanes > 2 && lanes < 100 && lanes > 2 * avg) continue;
       d.lanes[op] = lanes;
-      // kTuneReps launches (each after an L2 flush if cold) captured in a graph, so
-      // the host's launch rate does not flatten the comparison of small kernels.
+      // kTuneReps launches captured in a graph, so the host's launch rate does not
+      // flatten the comparison of small kernels.  Cold: each launch after an L2 flush,
+      // bracketed by its own event records (the flush is not timed); warm: the
+      // launches back to back, timed as a whole.
       cudaGraph_t g = nullptr;
       cudaGraphExec_t ge = nullptr;
       CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
       for (int r = 0; r < kTuneReps; r++) {
-        if (cold) launch_l2_flush(fl.buf, fl.bytes, s);
+        if (cold) {
+          launch_l2_flush(fl.buf, fl.bytes, s);
+          CK(cudaEventRecordWithFlags(fl.ea[r], s, cudaEventRecordExternal));
+        }
         opk<V>(h, AMGE_PROF_A_COARSE, d, op, EPI_STORE, a, s);
+        if (cold) CK(cudaEventRecordWithFlags(fl.eb[r], s, cudaEventRecordExternal));
       }
       CK(cudaStreamEndCapture(s, &g));
       cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
       cudaGraphDestroy(g);
       CK(ie);
       float ms = 0.f;
-      cudaError_t le = time_graph(ge, s, e0, e1, &ms);
+      cudaError_t le = cold ? time_graph_events(ge, s, fl, &ms) : time_graph(ge, s, e0, e1, &ms);
       cudaGraphExecDestroy(ge);
       CK(le);
-      if (cold) ms = std::max(ms - fl.ms, 1e-4f);
       d.tune_us[op][ci] = ms * (1e3f / kTuneReps);
-      if (lanes == 0 || ms < 0.9f * best) best = (lanes == 0 || ms < best) ? ms : best, best_lanes = lanes;
+      const bool sell = lanes == 0 || lanes >= 100;
+      float& b = sell ? best_sell : best_vec;
+      int& bl = sell ? sell_lanes : vec_lanes;
+      if (b < 0.f || ms < b) b = ms, bl = lanes;
     }
-    d.lanes[op] = best_lanes;
+    // the fastest sliced-ELL kernel, unless a vector CSR kernel beats it by 10%
+    d.lanes[op] = (best_vec >= 0.f && best_vec < 0.9f * best_sell) ? vec_lanes : sell_lanes;
   }
   return AMGE_OK;
 }
@@ -1396,18 +1425,9 @@ amge_status autotune(amge_hier* h, cudaStream_t s) {
       st = AMGE_ECUDA;
     }
   }
-  if (fl.buf && st == AMGE_OK) {
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ge = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal);
-    for (int r = 0; r < kTuneReps && e == cudaSuccess; r++) launch_l2_flush(fl.buf, fl.bytes, ts);
-    if (e == cudaSuccess) e = cudaStreamEndCapture(ts, &g);
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
-    if (g) cudaGraphDestroy(g);
-    if (e == cudaSuccess) e = time_graph(ge, ts, e0, e1, &fl.ms);
-    if (ge) cudaGraphExecDestroy(ge);
-    if (e != cudaSuccess) {
-      set_error(std::string("autotune flush: ") + cudaGetErrorString(e));
+  for (int r = 0; r < kTuneReps && fl.buf && st == AMGE_OK; r++) {
+    if (cudaEventCreate(&fl.ea[r]) != cudaSuccess || cudaEventCreate(&fl.eb[r]) != cudaSuccess) {
+      set_error("autotune: cudaEventCreate failed");
       st = AMGE_ECUDA;
     }
   }
@@ -1420,6 +1440,10 @@ amge_status autotune(amge_hier* h, cudaStream_t s) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (fl.buf) cudaFree(fl.buf);
+  for (int r = 0; r < kTuneReps; r++) {
+    if (fl.ea[r]) cudaEventDestroy(fl.ea[r]);
+    if (fl.eb[r]) cudaEventDestroy(fl.eb[r]);
+  }
   for (int c = 0; c < AMGE_PROF_CLASSES; c++) h->launches[c] = 0;
   return st;
 }
