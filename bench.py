@@ -46,7 +46,7 @@ WORKLOADS = {
 # dram__bytes_read.sum + dram__bytes_write.sum of one level-0 residual sweep from an
 # ncu capture (profiles/k_sell_fp64_resid_level0_hcurl64.md); only for that kernel
 # and workload, null elsewhere.
-NCU_TRAFFIC = {("hcurl64", 8): 432.5e6}
+NCU_TRAFFIC = {("hcurl64", 8): 431.0e6}
 
 HBM_FALLBACK_GBS = 6800.0
 METRIC = "PCG solves/s to 1e-8 rel residual"
