@@ -1277,10 +1277,10 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
 // Operators that fit in L2 but do not stay there between two uses inside a V-cycle
 // are timed cold: each launch follows a read of twice L2's capacity and is timed by
 // its own event records, and the kernel that is fastest on a warm L2 (fewest warps) is
-// often not the fastest from HBM.  A level's operators are taken to be evicted when those of
-// that level and all coarser ones (coarsest inverse included) take more than half of
-// L2: they are read cyclically and evict one another, as measured on H(curl) 64^3
-// (115 MB below level 0); a smaller working set stays resident and is timed warm.
+// often not the fastest from HBM.  A level's operators are taken to be evicted when
+// those of that level and all coarser ones (coarsest inverse included) take more than
+// half of L2: they are read cyclically and evict one another, as measured on H(curl)
+// 64^3 (115 MB below level 0); a smaller working set stays resident and is timed warm.
 // Streamed operators (much larger than L2) come from HBM either way and are timed back
 // to back, where each launch overlaps the previous one's tail as it does behind its
 // predecessor in the V-cycle.
@@ -1356,7 +1356,8 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
     SpmvArgs<V> a;
     a.x = in, a.y = out;
     const double avg = M.nr ? (double)M.nnz / M.nr : 0.0;
-    const bool cold = fl.buf && !op_sell(d, op).stream && coarse_bytes<V>(h, levels<V>(h), l) > 0.5 * fl.l2;
+    const bool cold =
+        fl.buf && !op_sell(d, op).stream && coarse_bytes<V>(h, levels<V>(h), l) > 0.5 * fl.l2;
     float best_sell = -1.f, best_vec = -1.f;
     int sell_lanes = 0, vec_lanes = 0;
     for (int ci = 0; ci < 9; ci++) {
