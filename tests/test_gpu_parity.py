@@ -118,11 +118,13 @@ def test_single_operators(amge, form, n, L, prec, lanes):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_fused_aux_correction_equals_separate_products(amge, prec):
-    """H(curl): with G and A G on the one-warp sliced-ELL kernels the V-cycle forms
-    x += G y and r -= (A G) y (and the final z = x + G y + m^-1 (r - (A G) y)) in one
-    pass.  Forcing G onto the two-warp kernel runs the separate products, whose sums
-    are formed in the same order: the V-cycles must agree exactly."""
+@pytest.mark.parametrize("ag", [0, 200, 400, 800])
+def test_fused_aux_correction_equals_separate_products(amge, prec, ag):
+    """H(curl): with G on the one-warp and A G on a sliced-ELL kernel (1, 2, 4 or 8
+    warps per slice) the V-cycle forms x += G y and r -= (A G) y (and the final
+    z = x + G y + m^-1 (r - (A G) y)) in one pass with that many warps per slice.
+    Forcing G onto the two-warp kernel runs the separate products, whose sums are
+    formed in the same order: the V-cycles must agree exactly."""
     from paper_2107_05613_gb300.inputs import rhs_vector
 
     h = upload(amge, "hcurl", 24, 3)
@@ -136,7 +138,7 @@ def test_fused_aux_correction_equals_separate_products(amge, prec):
     try:
         for l in levels:
             amge.amge_set_kernel(h, l, pname, "G", 0)
-            amge.amge_set_kernel(h, l, pname, "AG", 0)
+            amge.amge_set_kernel(h, l, pname, "AG", ag)
         amge.amge_vcycle(h, b, zf, precision=prec)
         for l in levels:
             amge.amge_set_kernel(h, l, pname, "G", 200)
