@@ -49,6 +49,9 @@ WORKLOADS = {
 NCU_TRAFFIC = {("hcurl64", 8): 431.0e6}
 
 HBM_FALLBACK_GBS = 6800.0
+# FP64 FMA rate of this GB300 pool, measured with an independent-chain FMA loop on the
+# box (TFMA/s); ncu's nominal peak is 2 FMA per cycle per SM, 0.63 TFMA/s at 2.07 GHz.
+FP64_TFMA_MEASURED = 0.503
 METRIC = "PCG solves/s to 1e-8 rel residual"
 
 
@@ -447,6 +450,14 @@ def run_ours(args, dist):
                                        "k_sell level-0 A sweeps (three residuals, final l1 sweep)") + ", "
                                       + ("FP32" if w == 4 else "FP64"),
                             "bytes_per_launch": bytes_launch, "peak_source": peak_src}
+        if w == 8 and nrhs == 1:
+            # the same launches against the FP64 pipe: one FMA per stored nonzero (the
+            # chain starts from b), the kernel's other bound on GB300
+            fma = float(hh.A[0].nnz)
+            tfma = fma / (m / c / 1e3) / 1e12
+            line["roofline"]["fp64"] = {"achieved": tfma, "peak": FP64_TFMA_MEASURED, "unit": "TFMA/s",
+                                        "frac": tfma / FP64_TFMA_MEASURED, "fma_per_launch": fma,
+                                        "peak_source": "FMA-loop probe on this GPU pool (of measured)"}
     vc_ms = sum(prof[k][1] for k in ("A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "vcycle_vec", "AG"))
     # one coarsest solve per V-cycle: one kernel (FP32 V-cycle: widening + product)
     n_vc = prof["coarse"][0] / (2 if w == 4 else 1)
