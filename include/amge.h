@@ -111,8 +111,13 @@ typedef struct {
  * l1 sums of G_l^T A_l G_l (eq. 4.1, second line), the transposes P_l^T and G_l^T,
  * FP32 copies of every level operator, and the Cholesky factor of the dense
  * coarsest matrix together with its triangular inverse (the coarsest solve that
- * replaces the paper's AMS/ADS, Section 4.2).  The library owns the device memory
- * until amge_hier_free.
+ * replaces the paper's AMS/ADS, Section 4.2).  Stored zeros of the input operators
+ * are dropped.  For H(curl) with one pre- and one post-smoothing step it also forms
+ * A_l G_l where that product is much sparser than A_l, dropping its cancellation
+ * residue (entries at most 64 eps times the sum of their terms' magnitudes), and
+ * times every candidate kernel of every operator (amge_autotune_report), for which
+ * it allocates twice the GPU's L2 capacity for the duration of the call.  The
+ * library owns the device memory until amge_hier_free.
  * Errors: AMGE_EINVAL for malformed CSR data, mismatched sizes, a coarsest matrix
  * that is not SPD, or a level too large for 32-bit indices; AMGE_ENOMEM;
  * AMGE_ECUDA.  On error *out is NULL. */
