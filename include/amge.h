@@ -8,8 +8,9 @@
  * an l1-Jacobi sweep on the auxiliary matrix G^T A_l G reached through the exterior
  * derivative G, corrected back through G) on every level and a dense direct solve
  * on the coarsest level.  The hierarchy itself (Sections 2-3: prolongators P_l,
- * coarse exterior derivatives, Galerkin A_l) is input data built on the host and
- * handed over as plain CSR arrays.
+ * coarse exterior derivatives, Galerkin A_l) is built on the host in FP64 from the
+ * problem's coefficients (amge_setup_upload) or handed over as plain CSR arrays
+ * (amge_upload_levels) or as a serialized blob (amge_upload_blob).
  *
  * Conventions
  *   - Every pointer argument documented as "device" must point to memory the
@@ -47,13 +48,22 @@ typedef enum {
   AMGE_ECANCELED = 8
 } amge_status;
 
-typedef enum { AMGE_HCURL = 1, AMGE_HDIV = 2 } amge_form;
+/* The problem's space, numbered by the exterior derivative that defines its
+ * bilinear form: D_2 = curl (H(curl), Nedelec edge dofs, aux space H1 reached
+ * through the discrete gradient) and D_3 = div (H(div), Raviart-Thomas face dofs,
+ * aux space H(curl) reached through the discrete curl), Section 2 of the paper. */
+typedef enum { AMGE_HCURL = 2, AMGE_HDIV = 3 } amge_form;
 
 /* AMGE_FP64: every step in double precision.
- * AMGE_FP32_VCYCLE: the V-cycle (level matrices, prolongators, smoother data and
- * vectors) runs in single precision with single-precision accumulation; the
- * coarsest-level triangular solves, the outer PCG dot products, AXPYs and the
- * true-residual recomputation stay in double precision. */
+ * AMGE_FP32_VCYCLE: the V-cycle's vectors are single precision, and so are its
+ * prolongators, incidences, smoother data and the level products with single-
+ * precision accumulation, except the residuals b - A_l x of iterates that carry a
+ * correction through G or P: those read the FP64 copy of A_l and sum in double
+ * (rounded once to single), because on such iterates most of A_l x cancels and
+ * single-precision rounding would swamp the residual's gradient (curl) part that
+ * the aux sweep and the coarse solve divide by small mass-only diagonals.  The
+ * coarsest-level solve, the outer PCG dot products, AXPYs and the true-residual
+ * recomputation stay in double precision. */
 typedef enum { AMGE_FP64 = 0, AMGE_FP32_VCYCLE = 1 } amge_precision;
 
 /* A CSR matrix in host memory: row_ptr[n_rows+1], col[nnz] (0-based, each row's
@@ -67,7 +77,7 @@ typedef struct {
   const double* val;
 } amge_csr;
 
-/* The generated hierarchy (host memory, copied during amge_setup_upload).
+/* A generated hierarchy (host memory, copied during amge_upload_levels).
  *   form        AMGE_HCURL (edge dofs; G_l = discrete gradient D_0 at level l) or
  *               AMGE_HDIV (face dofs; G_l = discrete curl D_1 at level l)
  *   num_levels  >= 1
@@ -87,6 +97,37 @@ typedef struct {
 
 typedef struct amge_hier amge_hier; /* opaque, device-resident hierarchy */
 
+/* The problem the paper states (eq. 2.2, Section 5.1 setting), on the unit cube
+ * split into n^3 cubes, each cut into the 6 Kuhn tetrahedra along its
+ * (0,0,0)-(1,1,1) diagonal, lowest-order Whitney elements, natural boundary
+ * conditions (every edge / face is a dof):
+ *   H(curl): a(u, v) = (beta curl u, curl v) + (alpha u, v)
+ *   H(div):  a(u, v) = (beta div u, div v) + (alpha u, v)
+ *   form        AMGE_HCURL or AMGE_HDIV
+ *   n           cubes per side, 1 .. 256
+ *   num_levels  levels of the AMGe hierarchy, 1 .. 16, or 0 = agglomerate 2x2x2
+ *               cells while the cell grid side m is even and > 8 (so n = 64 gives
+ *               4 levels: 64^3 -> 32^3 -> 16^3 -> 8^3 cells)
+ *   beta        host double [6 n^3], coefficient of the derivative term per
+ *               tetrahedron (the paper's alpha), > 0 and finite; NULL = all ones
+ *   alpha       host double [6 n^3], coefficient of the mass term (the paper's
+ *               beta), > 0 and finite; NULL = all ones
+ *   nu_pre, nu_post  hybrid smoothing steps before / after the coarse correction,
+ *               1 .. 8
+ * Tetrahedron t = 6 ((i n + j) n + k) + p lies in cube (i, j, k) (i, j, k the x, y, z
+ * cube indices), p = 0 .. 5 the Kuhn permutation index in the order
+ * (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y), (z,y,x) of the monotone path from the
+ * cube's (0,0,0) corner to its (1,1,1) corner. */
+typedef struct {
+  int32_t form;
+  int32_t n;
+  int32_t num_levels;
+  const double* beta;
+  const double* alpha;
+  int32_t nu_pre;
+  int32_t nu_post;
+} amge_problem;
+
 /* Options of a PCG solve.  rtol: stop when the true FP64 relative residual
  * ||b - A x||_2 / ||b||_2 <= rtol (x0 = 0); maxit >= 1; precision: amge_precision. */
 typedef struct {
@@ -105,6 +146,38 @@ typedef struct {
   double time_ms;
 } amge_info;
 
+/* Build the problem's AMGe hierarchy on the host and upload it to the current
+ * device (Sections 2-3 of the paper, then the preparation of amge_upload_levels).
+ * The host FP64 setup forms the fine Whitney-form operator, agglomerates 2x2x2
+ * cells per level, builds the coarse topology (Section 3.1), the PV traces
+ * (eq. 3.5) and their local extensions (eqs. 3.6, 3.8) into the prolongators P_l,
+ * the integer coarse exterior derivatives, and the Galerkin operators
+ * A_{l+1} = P_l^T A_l P_l (Section 3.2.1), then hands them to amge_upload_levels.
+ * Host memory of the setup is released before return; the caller's arrays are
+ * only read.
+ * Errors: AMGE_EINVAL for a NULL problem or out, a form, n, level count or
+ * smoothing count out of range, a coefficient that is not positive and finite, or
+ * a setup failure; AMGE_ECUDA if no CUDA device is current (checked first);
+ * otherwise as amge_upload_levels.  On error *out is NULL. */
+amge_status amge_setup_upload(const amge_problem* problem, void* stream, amge_hier** out);
+
+/* Upload a hierarchy serialized in the blob format below (the same bytes the CPU
+ * oracle reads).  The blob is only read; it may be freed after return.  Little-
+ * endian, every section starting at a multiple of 8 bytes from the blob's start:
+ *   header, 32 bytes: char magic[8] = "AMGEBLOB"; uint32 version = 1; int32 form
+ *     (amge_form); int32 num_levels L (1 .. 16); int32 nu_pre; int32 nu_post;
+ *     int32 reserved = 0
+ *   then 3L - 2 matrices in the order A_0 .. A_{L-1}, P_0 .. P_{L-2}, G_0 .. G_{L-2}
+ *   (meanings as in amge_hierarchy_desc), each as
+ *     int32 n_rows; int32 n_cols; int64 nnz;
+ *     int32 row_ptr[n_rows + 1], zero-padded to a multiple of 8 bytes;
+ *     int32 col[nnz], zero-padded to a multiple of 8 bytes;
+ *     double val[nnz]
+ *   and nothing after the last matrix (`bytes` must equal the layout's size).
+ * Errors: AMGE_EINVAL for a NULL argument or a blob that does not follow the layout
+ * (checked before any device work); otherwise as amge_upload_levels. */
+amge_status amge_upload_blob(const void* blob, size_t bytes, void* stream, amge_hier** out);
+
 /* Upload a generated hierarchy to the current device and prepare the solve data.
  * The host setup run here derives, in FP64, the l1-Jacobi diagonals m_l = sum_j
  * |(A_l)_ij| (Section 4.1 point smoother), the auxiliary diagonals m_aux,l = row
@@ -121,7 +194,7 @@ typedef struct {
  * Errors: AMGE_EINVAL for malformed CSR data, mismatched sizes, a coarsest matrix
  * that is not SPD, or a level too large for 32-bit indices; AMGE_ENOMEM;
  * AMGE_ECUDA.  On error *out is NULL. */
-amge_status amge_setup_upload(const amge_hierarchy_desc* desc, void* stream, amge_hier** out);
+amge_status amge_upload_levels(const amge_hierarchy_desc* desc, void* stream, amge_hier** out);
 
 /* Size of the finest level, number of levels and device bytes held. */
 amge_status amge_hier_info(const amge_hier* h, int32_t* n_dofs, int32_t* levels, size_t* device_bytes);
@@ -166,6 +239,10 @@ amge_status amge_pcg_solve_host(amge_hier* h, const double* b_host, double* x_ho
  *      AMGE_OP_COARSE:      y = A_L^{-1} x on the coarsest level (level ignored)
  *      AMGE_OP_AG: y = (A_l G_l) x, where that product is stored (see
  *                  amge_autotune_report; AMGE_EINVAL elsewhere)
+ *      AMGE_OP_A_WIDE (AMGE_FP32_VCYCLE only): y = A_l x with x rounded to FP32,
+ *                  FP64 values and FP64 sums, the result rounded to FP32 -- the
+ *                  product the FP32 V-cycle uses for residuals of iterates that
+ *                  carry a correction through G or P (amge_vcycle)
  * Products run the kernel chosen for the operator (amge_autotune_report,
  * amge_set_kernel). */
 enum {
@@ -176,7 +253,8 @@ enum {
   AMGE_OP_GT = 4,
   AMGE_OP_SMOOTH_PRE = 5,
   AMGE_OP_COARSE = 6,
-  AMGE_OP_AG = 7
+  AMGE_OP_AG = 7,
+  AMGE_OP_A_WIDE = 8
 };
 amge_status amge_apply(amge_hier* h, int32_t op, int32_t level, const double* x_dev, double* y_dev,
                        int32_t precision, void* stream);
@@ -206,7 +284,8 @@ enum {
   AMGE_PROF_PCG_VEC = 8,   /* PCG vector updates, dots, casts */
   AMGE_PROF_VCYCLE_VEC = 9, /* V-cycle elementwise products (x = m^-1 b on entry to a level) */
   AMGE_PROF_AG = 10,        /* residual updates r -= (A G) y after an aux sweep (H(curl)) */
-  AMGE_PROF_CLASSES = 11
+  AMGE_PROF_A_WIDE = 11,    /* FP32 V-cycle, level 0: products on the FP64 operator (AMGE_OP_A_WIDE) */
+  AMGE_PROF_CLASSES = 12
 };
 amge_status amge_profile_enable(amge_hier* h, int32_t enable);
 amge_status amge_profile_read(amge_hier* h, int64_t* count, double* ms);
@@ -222,8 +301,9 @@ amge_status amge_profile_read(amge_hier* h, int64_t* count, double* ms);
  * held by every GPU that loads the library until the process exits).
  *   h             hierarchy uploaded on the current device
  *   b_dev, z_dev  device double [n_L] (n_L = coarsest dofs); must not overlap
- * Errors: AMGE_EINVAL for NULL arguments or a coarsest level larger than 4096
- * dofs; AMGE_ECUDA if the device address of the array cannot be obtained.
+ * Errors: AMGE_EINVAL for NULL arguments, a coarsest level larger than 4096 dofs,
+ * or a hierarchy uploaded on another device than the current one; AMGE_ECUDA if the
+ * device address of the array cannot be obtained.
  * The first call on each device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  Every call
  * shares the one array, so calls whose kernels overlap on the GPU (different

@@ -51,6 +51,33 @@ class OracleHierarchy:
         self.coarse_factor = sla.cho_factor(Ac, lower=True)
 
     @classmethod
+    def from_blob(cls, blob: bytes):
+        """Read a serialized hierarchy: a 32-byte header ("AMGEBLOB", version 1, form,
+        levels L, nu_pre, nu_post, 0), then A_0..A_{L-1}, P_0..P_{L-2}, G_0..G_{L-2},
+        each as int32 rows, int32 cols, int64 nnz, int32 row_ptr, int32 col, float64
+        values; little-endian, sections padded to multiples of 8 bytes."""
+        buf = memoryview(blob)
+        if bytes(buf[:8]) != b"AMGEBLOB" or np.frombuffer(buf[8:12], "<u4")[0] != 1:
+            raise ValueError("not a version-1 hierarchy blob")
+        form, L, nu_pre, nu_post, _ = (int(v) for v in np.frombuffer(buf[12:32], "<i4"))
+        off = 32
+        mats = []
+        for _ in range(3 * L - 2):
+            nr, nc = (int(v) for v in np.frombuffer(buf[off:off + 8], "<i4"))
+            nnz = int(np.frombuffer(buf[off + 8:off + 16], "<i8")[0])
+            off += 16
+            rp = np.frombuffer(buf[off:off + 4 * (nr + 1)], "<i4")
+            off += 4 * (nr + 1) + (-4 * (nr + 1)) % 8
+            ci = np.frombuffer(buf[off:off + 4 * nnz], "<i4")
+            off += 4 * nnz + (-4 * nnz) % 8
+            v = np.frombuffer(buf[off:off + 8 * nnz], "<f8")
+            off += 8 * nnz
+            mats.append(sp.csr_matrix((v, ci, rp), shape=(nr, nc)))
+        if off != len(buf):
+            raise ValueError("trailing bytes after the last matrix")
+        return cls(mats[:L], mats[L:2 * L - 1], mats[2 * L - 1:], nu_pre, nu_post)
+
+    @classmethod
     def from_hierarchy(cls, h, nu_pre: int = 1, nu_post: int = 1):
         return cls([a.to_scipy() for a in h.A], [p.to_scipy() for p in h.P],
                    [g.to_scipy() for g in h.G], nu_pre, nu_post)

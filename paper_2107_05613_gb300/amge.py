@@ -21,10 +21,11 @@ _lib = ctypes.CDLL(AMGE_SO)
 
 AMGE_OK, AMGE_EINVAL, AMGE_ENOMEM, AMGE_ECUDA, AMGE_ENOTCONV, AMGE_ENONFINITE = 0, 1, 2, 3, 4, 5
 AMGE_EAGAIN, AMGE_ETIMEOUT, AMGE_ECANCELED = 6, 7, 8
-AMGE_HCURL, AMGE_HDIV = 1, 2
+AMGE_HCURL, AMGE_HDIV = 2, 3
 AMGE_FP64, AMGE_FP32_VCYCLE = 0, 1
-AMGE_OP_A, AMGE_OP_P, AMGE_OP_PT, AMGE_OP_G, AMGE_OP_GT, AMGE_OP_SMOOTH_PRE, AMGE_OP_COARSE, AMGE_OP_AG = range(8)
-PROF_CLASSES = ["A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "pcg_spmv", "pcg_vec", "vcycle_vec", "AG"]
+AMGE_OP_A, AMGE_OP_P, AMGE_OP_PT, AMGE_OP_G, AMGE_OP_GT, AMGE_OP_SMOOTH_PRE, AMGE_OP_COARSE, AMGE_OP_AG, AMGE_OP_A_WIDE = range(9)
+PROF_CLASSES = ["A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "pcg_spmv", "pcg_vec", "vcycle_vec", "AG",
+                "A_wide"]
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENONFINITE",
                 6: "EAGAIN", 7: "ETIMEOUT", 8: "ECANCELED"}
 
@@ -40,6 +41,12 @@ class amge_hierarchy_desc(ctypes.Structure):
                 ("G", ctypes.POINTER(amge_csr)), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32)]
 
 
+class amge_problem(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int32), ("n", ctypes.c_int32), ("num_levels", ctypes.c_int32),
+                ("beta", ctypes.c_void_p), ("alpha", ctypes.c_void_p), ("nu_pre", ctypes.c_int32),
+                ("nu_post", ctypes.c_int32)]
+
+
 class amge_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
@@ -51,7 +58,9 @@ class amge_info(ctypes.Structure):
 
 _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 _SIGS = {
-    "amge_setup_upload": [ctypes.POINTER(amge_hierarchy_desc), _vp, ctypes.POINTER(_vp)],
+    "amge_setup_upload": [ctypes.POINTER(amge_problem), _vp, ctypes.POINTER(_vp)],
+    "amge_upload_blob": [_vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)],
+    "amge_upload_levels": [ctypes.POINTER(amge_hierarchy_desc), _vp, ctypes.POINTER(_vp)],
     "amge_hier_info": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_size_t)],
     "amge_vcycle": [_vp, _vp, _vp, _i32, _i32, _vp],
     "amge_pcg_solve": [_vp, _vp, _vp, _i32, ctypes.POINTER(amge_solve_opts), ctypes.POINTER(amge_info), _vp],
@@ -152,7 +161,43 @@ def _csr_struct(m, keep):
     return amge_csr(m.shape[0], m.shape[1], int(rp[-1]), rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
 
 
-def amge_setup_upload(hierarchy, stream=None, nu_pre: int = 1, nu_post: int = 1) -> Hier:
+def _hier_from(h):
+    n, lv, nb = amge_hier_info(h)
+    return Hier(h, n, lv)
+
+
+def amge_setup_upload(form: str, n: int, num_levels: int = 0, beta=None, alpha=None, nu_pre: int = 1,
+                      nu_post: int = 1, stream=None) -> Hier:
+    """Build the hierarchy of the problem (eq. 2.2 on n^3 Kuhn-split cubes) on the host
+    and upload it.  form: 'hcurl' or 'hdiv'; beta / alpha: per-tet coefficients of the
+    derivative / mass term (6 n^3 values, None = 1)."""
+    keep = []
+
+    def coef(c):
+        if c is None:
+            return None
+        a = np.ascontiguousarray(c, dtype=np.float64)
+        if a.size != 6 * n ** 3:
+            raise ValueError(f"coefficient array must have {6 * n ** 3} entries")
+        keep.append(a)
+        return a.ctypes.data
+
+    prob = amge_problem({"hcurl": AMGE_HCURL, "hdiv": AMGE_HDIV}[form], n, num_levels, coef(beta), coef(alpha),
+                        nu_pre, nu_post)
+    h = ctypes.c_void_p()
+    _check(_lib.amge_setup_upload(ctypes.byref(prob), _stream(stream), ctypes.byref(h)), "amge_setup_upload")
+    return _hier_from(h)
+
+
+def amge_upload_blob(blob: bytes, stream=None) -> Hier:
+    """Upload a hierarchy serialized in the blob format of include/amge.h."""
+    buf = np.frombuffer(blob, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    _check(_lib.amge_upload_blob(buf.ctypes.data, buf.size, _stream(stream), ctypes.byref(h)), "amge_upload_blob")
+    return _hier_from(h)
+
+
+def amge_upload_levels(hierarchy, stream=None, nu_pre: int = 1, nu_post: int = 1) -> Hier:
     """Upload an inputs.Hierarchy (or any object with form, A, P, G lists of CSR)."""
     keep = []
     L = len(hierarchy.A)
@@ -162,9 +207,8 @@ def amge_setup_upload(hierarchy, stream=None, nu_pre: int = 1, nu_post: int = 1)
     form = {"hcurl": AMGE_HCURL, "hdiv": AMGE_HDIV}[hierarchy.form]
     desc = amge_hierarchy_desc(form, L, A, P, G, nu_pre, nu_post)
     h = ctypes.c_void_p()
-    _check(_lib.amge_setup_upload(ctypes.byref(desc), _stream(stream), ctypes.byref(h)), "amge_setup_upload")
-    n, lv, nb = amge_hier_info(h)
-    return Hier(h, n, lv)
+    _check(_lib.amge_upload_levels(ctypes.byref(desc), _stream(stream), ctypes.byref(h)), "amge_upload_levels")
+    return _hier_from(h)
 
 
 def amge_hier_info(h):

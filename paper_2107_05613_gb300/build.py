@@ -1,6 +1,7 @@
 """In-tree builds of the native libraries.
 
-libamge.so            the C-ABI solve library (CUDA, sm_103a only)
+libamge.so            the C-ABI solve library (CUDA, sm_103a only; it also holds the
+                      host hierarchy generator, for the problem-level setup entry)
 libamge_hierarchy.so  the host FP64 hierarchy generator (input data)
 
 Both are compiled with explicit nvcc / g++ command lines, in parallel, into the
@@ -21,7 +22,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CUDA_SOURCES = ["amge_api.cu", "amge_kernels.cu", "amge_kernels_mm.cu", "amge_server.cu", "amge_host_setup.cpp",
-                "amge_noalloc.cu"]
+                "amge_noalloc.cu", "amge_setup.cpp", "../inputs/amge_hierarchy.cpp"]
+INPUTS = os.path.join(PKG, "inputs")
 
 
 def _run(cmds):
@@ -50,10 +52,10 @@ def build_amge_lib(verbose_ptxas=False):
     cmds, objs = [], []
     for s in CUDA_SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(objdir, s + ".o")
+        obj = os.path.join(objdir, os.path.basename(s) + ".o")
         objs.append(obj)
         cmd = [NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-fopenmp",
-               "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+               "-I", INCLUDE, "-I", CSRC, "-I", INPUTS, "-c", src, "-o", obj]
         if verbose_ptxas and s.endswith(".cu"):
             cmd.insert(1, "-Xptxas=-v")
         cmds.append(cmd)

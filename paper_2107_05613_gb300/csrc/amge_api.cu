@@ -66,6 +66,7 @@ struct GraphPcg {
 struct amge_hier {
   int form = 0, L = 0, nu_pre = 1, nu_post = 1;
   int n0 = 0;
+  int device = -1;  // CUDA device the operators live on (current at upload)
   std::vector<LevelDev<double>> lv64;
   std::vector<LevelDev<float>> lv32;
   DevSell<double> A0;  // finest operator for the outer PCG
@@ -284,6 +285,39 @@ void opk(amge_hier* h, int cls, const LevelDev<V>& d, int op, int epi, const Spm
   else launch_csrv<V>(op_csr(d, op), code, epi, a, s);
 }
 
+// Warps per slice of the FP32 V-cycle's FP64-operator products on level l: those
+// autotuned for the FP64 operator when it runs sliced ELL (the same loads and FP64
+// work), else four.
+int wide_wps(const amge_hier* h, int l) {
+  const int code = h->lv64[l].lanes[OP_A];
+  return code >= 100 ? code / 100 : (code == 0 ? 1 : 4);
+}
+
+// A product with A_l in a residual form (EPI_RESID / EPI_SWEEP).  `corrected`: the
+// iterate x has received a correction through G or P since the level's first sweep
+// from zero.  In the FP32 V-cycle such products run on the level's FP64 operator
+// with FP64 sums (launch_sell_wide): for such x most of A x cancels (K G = 0 for the
+// large-coefficient part), and the FP32 rounding of A's values and of the sums, of
+// order eps_32 |A| |x|, is then far larger than the gradient (curl) components of
+// the residual that the aux sweep and the coarse solve divide by their mass-only
+// diagonals.  Under the 1e6 coefficient contrast of the 64^3 workloads an all-FP32
+// V-cycle stops reducing the PCG residual near 1e-1; with these products on the FP64
+// operators it needs one iteration more than the FP64 V-cycle.  The FP64 copies
+// are resident anyway (FP64 mode).
+template <typename V>
+void a_product(amge_hier* h, int l, const LevelDev<V>& d, bool corrected, int epi, const SpmvArgs<V>& a,
+               cudaStream_t s) {
+  const int clsA = l == 0 ? AMGE_PROF_A_FINE : AMGE_PROF_A_COARSE;
+  if constexpr (std::is_same<V, float>::value) {
+    if (corrected) {
+      Prof p(h, l == 0 ? AMGE_PROF_A_WIDE : AMGE_PROF_A_COARSE, s);
+      launch_sell_wide(h->lv64[l].A, epi, a, s, wide_wps(h, l));
+      return;
+    }
+  }
+  opk<V>(h, clsA, d, OP_A, epi, a, s);
+}
+
 // One V-cycle at level l: z = B_l^{-1} b (Algorithm 4.1, x0 = 0).  x_ready: the
 // level's first point sweep from zero, x = m^-1 b, was already written into x by the
 // restriction that produced b.
@@ -296,7 +330,6 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
     return;
   }
   LevelDev<V>& d = lv[l];
-  const int clsA = l == 0 ? AMGE_PROF_A_FINE : AMGE_PROF_A_COARSE;
   V* x = d.x;
   V* xt = d.tmp;
   auto aux_gt = [&]() {  // y = M_aux^{-1} G^T r   (r = b - A x already formed)
@@ -310,10 +343,10 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
     c.x = d.y, c.y = x;
     opk<V>(h, AMGE_PROF_G, d, OP_G, EPI_ADD, c, s);
   };
-  auto residual = [&]() {
+  auto residual = [&](bool corrected) {
     SpmvArgs<V> a;
     a.x = x, a.b = b, a.y = d.r;
-    opk<V>(h, clsA, d, OP_A, EPI_RESID, a, s);
+    a_product<V>(h, l, d, corrected, EPI_RESID, a, s);
   };
   LevelDev<V>& c = lv[l + 1];
   const bool c_smooths = l + 1 < h->L - 1;  // the next level starts with x = m^-1 b
@@ -333,7 +366,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
     const int ag = d.lanes[OP_AG];
     const bool fused = d.g2 && (ag == 0 || ag >= 100) && d.lanes[OP_G] == 0;
     const int ag_wps = ag >= 100 ? ag / 100 : 1;
-    residual();
+    residual(false);
     if (fused) {
       aux_gt();
       Prof p(h, AMGE_PROF_AG, s);
@@ -353,7 +386,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
       a.x = c.z, a.y = x;
       opk<V>(h, AMGE_PROF_P, d, OP_P, EPI_ADD, a, s);
     }
-    residual();
+    residual(true);
     if (fused) {
       aux_gt();
       Prof p(h, AMGE_PROF_AG, s);
@@ -375,18 +408,18 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
         Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
         launch_mul<V>(d.n, d.minv, b, x, s);
       }
-      residual();
+      residual(false);
     } else {
       SpmvArgs<V> a;  // x <- x + M^{-1} (b - A x)
       a.x = x, a.xin = x, a.d = d.minv, a.b = b, a.y = xt;
-      opk<V>(h, clsA, d, OP_A, EPI_SWEEP, a, s);
+      a_product<V>(h, l, d, true, EPI_SWEEP, a, s);
       std::swap(x, xt);
-      residual();
+      residual(true);
     }
     aux_sweep();
   }
   // coarse-grid correction
-  residual();
+  residual(true);
   restrict_to_next();
   vcycle_level<V>(h, l + 1, c.b, c.z, s, c_smooths);
   {
@@ -396,12 +429,12 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
   }
   // post-relaxation with the transposed step: aux sweep first, then the point sweep
   for (int k = 0; k < h->nu_post; k++) {
-    residual();
+    residual(true);
     aux_sweep();
     const bool last = (k == h->nu_post - 1);
     SpmvArgs<V> a;
     a.x = x, a.xin = x, a.d = d.minv, a.b = b, a.y = last ? z : xt;
-    opk<V>(h, clsA, d, OP_A, EPI_SWEEP, a, s);
+    a_product<V>(h, l, d, true, EPI_SWEEP, a, s);
     if (!last) std::swap(x, xt);
   }
 }
@@ -1723,6 +1756,7 @@ amge_status amge::hier_make_view(const amge_hier* src, cudaStream_t s, amge_hier
   v->A0 = src->A0, v->cA0 = src->cA0;
   v->nC = src->nC, v->Linv = src->Linv, v->LinvT = src->LinvT, v->Ainv = src->Ainv;
   v->use_graphs = src->use_graphs;
+  v->device = src->device;
   v->base = src->base ? src->base : src;
   amge_status st = alloc_work(v, s);
   if (st == AMGE_OK) {
@@ -1744,7 +1778,9 @@ size_t amge::hier_workspace_bytes(const amge_hier* h) { return h->bytes - h->op_
 int amge::hier_dofs(const amge_hier* h) { return h->n0; }
 const amge_hier* amge::hier_base(const amge_hier* h) { return h->base ? h->base : h; }
 
-void amge::coarse_factor_view(const amge_hier* h, int* n, const double** Linv, const double** LinvT) {
+void amge::coarse_factor_view(const amge_hier* h, int* n, const double** Linv, const double** LinvT,
+                              int* device) {
+  *device = h->device;
   *n = h->nC;
   *Linv = h->Linv;
   *LinvT = h->LinvT;
@@ -1754,7 +1790,7 @@ extern "C" {
 
 const char* amge_last_error(void) { return g_last_error.c_str(); }
 
-amge_status amge_setup_upload(const amge_hierarchy_desc* desc, void* stream, amge_hier** out) {
+amge_status amge_upload_levels(const amge_hierarchy_desc* desc, void* stream, amge_hier** out) {
   if (!out) {
     set_error("out is NULL");
     return AMGE_EINVAL;
@@ -1774,6 +1810,12 @@ amge_status amge_setup_upload(const amge_hierarchy_desc* desc, void* stream, amg
     return AMGE_EINVAL;
   }
   amge_hier* h = new amge_hier;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    set_error("cudaGetDevice failed");
+    return AMGE_ECUDA;
+  }
   amge_status st = do_upload(desc, as_stream(stream), h);
   if (st != AMGE_OK) {
     amge_hier_free(h);
@@ -1902,9 +1944,22 @@ amge_status amge_apply(amge_hier* h, int32_t op, int32_t level, const double* x_
     set_error("level must index a smoothing level (0 .. levels-2)");
     return AMGE_EINVAL;
   }
-  if ((op < AMGE_OP_A || op > AMGE_OP_SMOOTH_PRE) && op != AMGE_OP_AG) {
+  if ((op < AMGE_OP_A || op > AMGE_OP_SMOOTH_PRE) && op != AMGE_OP_AG && op != AMGE_OP_A_WIDE) {
     set_error("unknown op");
     return AMGE_EINVAL;
+  }
+  if (op == AMGE_OP_A_WIDE) {
+    if (precision != AMGE_FP32_VCYCLE) {
+      set_error("AMGE_OP_A_WIDE is a product of the FP32 V-cycle");
+      return AMGE_EINVAL;
+    }
+    const DevSell<double>& M = h->lv64[level].A;
+    launch_cast<double, float>(M.nc, x_dev, h->s32_in, s);
+    SpmvArgs<float> a;
+    a.x = h->s32_in, a.y = h->s32_out;
+    launch_sell_wide(M, EPI_STORE, a, s, wide_wps(h, level));
+    launch_cast<float, double>(M.nr, h->s32_out, y_dev, s);
+    return launch_status();
   }
   if (op == AMGE_OP_AG && !h->lv64[level].use_ag) {
     set_error("A G is not stored on this level");

@@ -116,6 +116,12 @@ struct SpmvArgs {
 template <typename V>
 void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, int wps = 1);
 
+// FP32 vectors through the FP64 sliced-ELL operator M (FP64 values, FP64 FMA chain,
+// result rounded once to FP32); epi = EPI_STORE (y = M x), EPI_RESID (y = b - M x) or
+// EPI_SWEEP (y = xin + d (b - M x)).  Same row order and warp split as
+// launch_sell<double>.
+void launch_sell_wide(const DevSell<double>& M, int epi, const SpmvArgs<float>& a, cudaStream_t s, int wps = 1);
+
 // CSR copy of an operator for the multi-right-hand-side products (row pointers and
 // columns shared by both precisions).
 // Fused correction of the hybrid smoother's aux sweep where G has two +-1 entries per
@@ -327,7 +333,8 @@ bool coarse_factor(const HostCsr& A, std::vector<double>& Linv, std::vector<doub
 // A^{-1} = L^{-T} L^{-1} from the transposed inverse factor (full n x n, row-major).
 void coarse_inverse(int n, const std::vector<double>& LinvT, std::vector<double>& Ainv);
 
-// Read-only view of a hierarchy's coarsest factor (defined in amge_api.cu).
-void coarse_factor_view(const amge_hier* h, int* n, const double** Linv, const double** LinvT);
+// Read-only view of a hierarchy's coarsest factor and the device it lives on
+// (defined in amge_api.cu).
+void coarse_factor_view(const amge_hier* h, int* n, const double** Linv, const double** LinvT, int* device);
 
 }  // namespace amge

@@ -194,6 +194,97 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
   sell_store<V, EPI>(a, row, s);
 }
 
+// FP32 -> FP64 without a conversion instruction: a normal float's exponent is
+// rebiased (+896 = 1023 - 127) and its 23-bit mantissa moved to the top of the 52-bit
+// field, both with integer operations, exact (every float is a double).  On GB300 the
+// F2F conversion issues on the FP64 pipe, which the FMA of every stored entry
+// already keeps busy.  Zero is built the same way; subnormals, infinities and NaN
+// (never produced by these solves, but possible inputs) take the conversion.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e - 1u < 254u) {
+    const unsigned hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(u << 29));
+  }
+  if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return (double)f;
+}
+
+// Product of the FP32 V-cycle with a level's FP64 operator: FP32 vectors in and out,
+// FP64 values and an FP64 FMA chain per row (the chain, entry order and warp split of
+// k_sell<double>, so the result is that kernel's on the widened inputs, rounded once
+// to FP32).  Used where the iterate carries a correction through G or P: there most
+// of A x cancels (curl grad = 0, div curl = 0 on the large-coefficient part), and
+// FP32 values or FP32 sums leave a rounding error of order eps_32 |A| |x| in the
+// gradient (curl) components of r that the aux sweep and the coarse solve then
+// divide by their small mass-only diagonals.
+//   EPI_STORE: y = A x
+//   EPI_RESID: y = b - A x
+//   EPI_SWEEP: y = xin + d (float)(b - A x)
+template <int EPI, int WPS, bool CS>
+__global__ void __launch_bounds__(kBlock) k_sell_wide(int nslices, const int64_t* __restrict__ sptr,
+                                                      const int* __restrict__ srow, const int2* __restrict__ ci2,
+                                                      const double2* __restrict__ val2, SpmvArgs<float> a) {
+  static_assert(EPI == EPI_STORE || EPI == EPI_RESID || EPI == EPI_SWEEP, "unsupported epilogue");
+  constexpr bool NEG = EPI != EPI_STORE;
+  const int wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int g = wib % WPS;
+  const int slice = (blockIdx.x * (kBlock / 32) + wib) / WPS;
+  const bool live = slice < nslices;
+  int row = -1, np = 0;
+  const int2* cp = ci2;
+  const double2* vp = val2;
+  int2 c0 = make_int2(0, 0);
+  double2 v0{};
+  if (live) {  // constant operator data before the dependent-launch wait (as k_sell)
+    const int64_t p0 = ldg(sptr + slice) >> 1;
+    np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+    row = ldg(srow + (size_t)slice * 32 + lane);
+    if (!CS && g == 0 && lane == 0 && np > 0) {
+      prefetch_l2_bulk(ci2 + p0, (uint32_t)np * 32u * sizeof(int2));
+      prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(double2));
+    }
+    cp += p0 + lane;
+    vp += p0 + lane;
+    if (g < np) {
+      c0 = ldm<CS>(cp + (size_t)g * 32);
+      v0 = ldm<CS>(vp + (size_t)g * 32);
+    }
+  }
+  pdl_begin();
+  double s = 0.0;
+  if (live) {
+    if (NEG && g == 0 && row >= 0) s = widen(a.b[row]);
+    if (g < np) {
+      const double x0 = widen(ldg(a.x + c0.x)), x1 = widen(ldg(a.x + c0.y));
+      s = fma(NEG ? -v0.x : v0.x, x0, s);
+      s = fma(NEG ? -v0.y : v0.y, x1, s);
+    }
+#pragma unroll 2
+    for (int k = g + WPS; k < np; k += WPS) {
+      const int2 c = ldm<CS>(cp + (size_t)k * 32);
+      const double2 v = ldm<CS>(vp + (size_t)k * 32);
+      const double x0 = widen(ldg(a.x + c.x)), x1 = widen(ldg(a.x + c.y));
+      s = fma(NEG ? -v.x : v.x, x0, s);
+      s = fma(NEG ? -v.y : v.y, x1, s);
+    }
+  }
+  if (WPS > 1) {
+    __shared__ double part[kBlock];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (g != 0) return;
+#pragma unroll
+    for (int j = 1; j < WPS; j++) s += part[threadIdx.x + 32 * j];
+  }
+  if (!live || row < 0) return;
+  const float r = (float)s;
+  if (EPI == EPI_SWEEP) a.y[row] = fmaf(a.d[row], r, a.xin[row]);
+  else a.y[row] = r;
+}
+
 // G y (two sign-coded entries) and A G y for one row per lane (see AgArgs).  WPS warps
 // share a slice as in k_sell (the first warp starts from r and adds the others'
 // partial sums in warp order, then applies G y and the epilogue).  As in k_sell, the
@@ -726,6 +817,31 @@ void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_
   if (M.unit) launch_sell_u<V, true>(M, wps, epi, a, s);
   else launch_sell_u<V, false>(M, wps, epi, a, s);
 }
+template <int EPI, int WPS>
+static void launch_sell_wide_t(const DevSell<double>& M, const SpmvArgs<float>& a, cudaStream_t s) {
+  const int per = (kBlock / 32) / WPS;
+  const int grid = (M.nslices + per - 1) / per;
+  const int2* ci2 = reinterpret_cast<const int2*>(M.ci);
+  const auto* v2 = reinterpret_cast<const double2*>(M.val);
+  if (M.stream) launch_k(k_sell_wide<EPI, WPS, true>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a);
+  else launch_k(k_sell_wide<EPI, WPS, false>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a);
+}
+template <int EPI>
+static void launch_sell_wide_e(const DevSell<double>& M, const SpmvArgs<float>& a, cudaStream_t s, int wps) {
+  switch (wps) {
+    case 2: launch_sell_wide_t<EPI, 2>(M, a, s); break;
+    case 4: launch_sell_wide_t<EPI, 4>(M, a, s); break;
+    case 8: launch_sell_wide_t<EPI, 8>(M, a, s); break;
+    default: launch_sell_wide_t<EPI, 1>(M, a, s); break;
+  }
+}
+void launch_sell_wide(const DevSell<double>& M, int epi, const SpmvArgs<float>& a, cudaStream_t s, int wps) {
+  if (M.nslices == 0) return;
+  if (epi == EPI_SWEEP) launch_sell_wide_e<EPI_SWEEP>(M, a, s, wps);
+  else if (epi == EPI_RESID) launch_sell_wide_e<EPI_RESID>(M, a, s, wps);
+  else launch_sell_wide_e<EPI_STORE>(M, a, s, wps);
+}
+
 template <typename V, int LANES>
 static void launch_csrv_lanes(const DevCsr<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
   const int grid = (int)(((int64_t)M.nr * LANES + kBlock - 1) / kBlock);

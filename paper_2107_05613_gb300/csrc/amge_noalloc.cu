@@ -30,9 +30,9 @@ extern "C" amge_status amge_coarse_solve_noalloc(const amge_hier* h, const doubl
     amge::set_error("NULL argument");
     return AMGE_EINVAL;
   }
-  int n = 0;
+  int n = 0, hdev = -1;
   const double *Linv = nullptr, *LinvT = nullptr;
-  amge::coarse_factor_view(h, &n, &Linv, &LinvT);
+  amge::coarse_factor_view(h, &n, &Linv, &LinvT, &hdev);
   if (n > kStaticCoarseMax) {
     amge::set_error("coarsest level has " + std::to_string(n) +
                     " dofs; the no-allocation solve holds at most " + std::to_string(kStaticCoarseMax));
@@ -46,6 +46,12 @@ extern "C" amge_status amge_coarse_solve_noalloc(const amge_hier* h, const doubl
   }
   if (dev < 0 || dev >= kMaxDevices) {
     amge::set_error("device ordinal out of range");
+    return AMGE_EINVAL;
+  }
+  // the factor's pointers are only valid on the device the hierarchy was uploaded on
+  if (dev != hdev) {
+    amge::set_error("hierarchy was uploaded on device " + std::to_string(hdev) + ", current device is " +
+                    std::to_string(dev));
     return AMGE_EINVAL;
   }
   double* t = nullptr;

@@ -6,7 +6,7 @@ hierarchy built once on the host in FP64 (Sections 2-3 of the paper, as input
 data), per-element coefficients, and right-hand sides from SplitMix64.
 """
 from .rng import splitmix64_uniform, block_coefficients, rhs_vector, workload_coefficients
-from .hierarchy import build_hierarchy, Hierarchy, CSR
+from .hierarchy import build_hierarchy, hierarchy_to_blob, Hierarchy, CSR
 
 __all__ = [
     "splitmix64_uniform",
@@ -16,4 +16,5 @@ __all__ = [
     "build_hierarchy",
     "Hierarchy",
     "CSR",
+    "hierarchy_to_blob",
 ]

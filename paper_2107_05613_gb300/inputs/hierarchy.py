@@ -148,3 +148,28 @@ def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=Non
     finally:
         lib.amgh_free(h)
     return Hierarchy(form, n, A, P, G, counts, P_all, D_all, diag)
+
+
+BLOB_MAGIC = b"AMGEBLOB"
+BLOB_FORMS = {"hcurl": 2, "hdiv": 3}   # amge_form values (D_2 = curl, D_3 = div)
+
+
+def _pad8(b: bytes) -> bytes:
+    return b + b"\0" * (-len(b) % 8)
+
+
+def hierarchy_to_blob(h: Hierarchy, nu_pre: int = 1, nu_post: int = 1) -> bytes:
+    """Serialize the solve-phase data of a hierarchy (A_l, P_l, G_l) in the blob
+    layout of the library's amge_upload_blob: a 32-byte header (magic, version 1,
+    form, levels, nu_pre, nu_post, 0), then A_0..A_{L-1}, P_0..P_{L-2}, G_0..G_{L-2},
+    each as (int32 rows, int32 cols, int64 nnz, int32 row_ptr, int32 col, float64
+    val), little-endian, every section padded to a multiple of 8 bytes."""
+    L = h.num_levels
+    out = [BLOB_MAGIC, np.array([1], "<u4").tobytes(),
+           np.array([BLOB_FORMS[h.form], L, nu_pre, nu_post, 0], "<i4").tobytes()]
+    for m in list(h.A) + list(h.P) + list(h.G):
+        out.append(np.array(m.shape, "<i4").tobytes() + np.array([m.nnz], "<i8").tobytes())
+        out.append(_pad8(np.ascontiguousarray(m.indptr, "<i4").tobytes()))
+        out.append(_pad8(np.ascontiguousarray(m.indices, "<i4").tobytes()))
+        out.append(np.ascontiguousarray(m.data, "<f8").tobytes())
+    return b"".join(out)

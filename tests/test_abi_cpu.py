@@ -40,10 +40,10 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_validation_without_gpu(lib):
-    lib.amge_setup_upload.restype = ctypes.c_int
+    lib.amge_upload_levels.restype = ctypes.c_int
     lib.amge_last_error.restype = ctypes.c_char_p
     out = ctypes.c_void_p(1)
-    assert lib.amge_setup_upload(None, None, ctypes.byref(out)) == 1      # AMGE_EINVAL
+    assert lib.amge_upload_levels(None, None, ctypes.byref(out)) == 1      # AMGE_EINVAL
     assert out.value is None
     assert b"descriptor" in lib.amge_last_error()
     assert lib.amge_hier_info(None, None, None, None) == 1

@@ -7,10 +7,19 @@ streamed level-0 operators, the captured PCG loop.
   last slice) of y = M x against the oracle's rows, within the bound of one CSR
   product, 2 (nnz_i + 1) eps (|M||x|)_i; for A G the stored product's entry rounding
   and its dropped cancellation residue (64 eps (|A||G||x|)_i) come on top;
+* the same samples for the FP32 copies (streamed FP32 kernels), with the FP32 bound of
+  the small cases, and for the FP32 V-cycle's FP64-operator product (AMGE_OP_A_WIDE)
+  on gradient (curl) fields, with its bound (eps32/2 |y|_i + 2 (nnz_i + 1) eps64
+  (|A||x|)_i against the exact product of the FP32-rounded input);
 * one FP64 V-cycle, whole vector, against the oracle's: relative L2 within the bound
-  of the small cases, max(1e-11, 10 eps kappa(A_L));
-* the FP64 PCG solve of the benchmark: iterations within +-1 of the oracle's and the
-  true relative residual of the GPU solution, recomputed on the host, <= 1e-8.
+  of the small cases, max(1e-11, 10 eps kappa(A_L)); one FP32 V-cycle within 1e-3 in
+  the energy norm;
+* the FP64 PCG solve of the benchmark: iterations within +-1 of the oracle's, the
+  true relative residual of the GPU solution, recomputed on the host, <= 1e-8, and the
+  solution within 1e-9 (relative L2) of the oracle's;
+* the FP32-V-cycle PCG solve of the benchmark: true relative residual <= 1e-8,
+  iterations within 3 of the FP64 oracle's, solution within 1e-7 of the oracle's
+  (the distance is printed).
 """
 import numpy as np
 import pytest
@@ -19,6 +28,7 @@ import torch
 pytestmark = pytest.mark.gpu
 
 EPS64 = np.finfo(np.float64).eps
+EPS32 = np.finfo(np.float32).eps
 
 
 @pytest.fixture(scope="module")
@@ -31,6 +41,7 @@ def amge():
 
 
 _cache = {}
+_oracle_solutions = {}
 
 
 def workload(amge, name):
@@ -43,7 +54,7 @@ def workload(amge, name):
             del _cache[k]
         torch.cuda.synchronize()
         hh, b = bench.make_workload(bench.WORKLOADS[name])
-        _cache[name] = (amge.amge_setup_upload(hh), OracleHierarchy.from_hierarchy(hh), np.asarray(b).ravel())
+        _cache[name] = (amge.amge_upload_levels(hh), OracleHierarchy.from_hierarchy(hh), np.asarray(b).ravel())
     return _cache[name]
 
 
@@ -61,10 +72,12 @@ def sample_rows(n, rng):
 
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
-def test_level0_products_sampled(amge, name):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_level0_products_sampled(amge, name, prec):
     h, o, _ = workload(amge, name)
     rep = amge.amge_autotune_report(h)
-    rng = np.random.default_rng(7)
+    rng = np.random.default_rng(7 + prec)
+    eps = EPS64 if prec == 0 else EPS32
     A, P, G = o.A[0], o.P[0], o.G[0]
     ops = {amge.AMGE_OP_A: A, amge.AMGE_OP_P: P, amge.AMGE_OP_PT: P.T.tocsr(), amge.AMGE_OP_G: G,
            amge.AMGE_OP_GT: G.T.tocsr()}
@@ -75,7 +88,7 @@ def test_level0_products_sampled(amge, name):
         nrows = A.shape[0] if op == amge.AMGE_OP_AG else M.shape[0]
         x = rng.uniform(-1, 1, ncols)
         y = torch.empty(nrows, dtype=torch.float64, device="cuda")
-        amge.amge_apply(h, op, 0, dev(x), y, amge.AMGE_FP64)
+        amge.amge_apply(h, op, 0, dev(x), y, prec)
         rows = sample_rows(nrows, rng)
         if op == amge.AMGE_OP_AG:
             Ar = A[rows]
@@ -87,8 +100,27 @@ def test_level0_products_sampled(amge, name):
             ref = Mr @ x
             bound = abs(Mr) @ abs(x)
             k = np.diff(Mr.indptr) + 1
+        # FP32: the rounding of operator entries and input on top of the product's own
+        slack = 2 * k * eps * bound + (0 if prec == 0 else 2 * eps * bound)
         err = np.abs(host(y)[rows] - ref)
-        assert np.all(err <= 2 * k * EPS64 * bound + 1e-300), (name, op, float((err / (bound + 1e-300)).max()))
+        assert np.all(err <= slack + 1e-300), (name, prec, op, float((err / (bound + 1e-300)).max()))
+
+
+@pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
+def test_level0_wide_product_sampled(amge, name):
+    h, o, _ = workload(amge, name)
+    rng = np.random.default_rng(9)
+    A, G = o.A[0], o.G[0]
+    x = G @ rng.uniform(-1, 1, G.shape[1]) + 1e-3 * rng.uniform(-1, 1, A.shape[1])
+    x32 = x.astype(np.float32).astype(np.float64)
+    y = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+    amge.amge_apply(h, amge.AMGE_OP_A_WIDE, 0, dev(x), y, amge.AMGE_FP32_VCYCLE)
+    rows = sample_rows(A.shape[0], rng)
+    Ar = A[rows]
+    ref = Ar @ x32
+    bound = 0.5 * EPS32 * np.abs(ref) + 2 * (np.diff(Ar.indptr) + 1) * EPS64 * (abs(Ar) @ abs(x32))
+    err = np.abs(host(y)[rows] - ref)
+    assert np.all(err <= bound + 1e-300), (name, float((err / (bound + 1e-300)).max()))
 
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
@@ -100,17 +132,48 @@ def test_vcycle_full_size(amge, name):
     tol = max(1e-11, 10 * EPS64 * np.linalg.cond(o.A[-1].toarray()))
     rel = np.linalg.norm(host(z) - ref) / np.linalg.norm(ref)
     assert rel <= tol, (name, rel, tol)
+    amge.amge_vcycle(h, dev(b), z, 1, amge.AMGE_FP32_VCYCLE)
+    d = host(z) - ref
+    A = o.A[0]
+    err = np.sqrt((d @ (A @ d)) / (ref @ (A @ ref)))
+    print(f"{name}: FP32 V-cycle energy-norm distance to the FP64 oracle cycle {err:.2e}")
+    assert err <= 1e-3, (name, err)
+
+
+def oracle_solution(name, o, b):
+    from oracle import pcg
+
+    if name not in _oracle_solutions:
+        _oracle_solutions[name] = pcg(o, b, rtol=1e-8)
+    return _oracle_solutions[name]
 
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 def test_pcg_full_size(amge, name):
-    from oracle import pcg
-
     h, o, b = workload(amge, name)
     x = torch.empty(b.size, dtype=torch.float64, device="cuda")
     st, info = amge.amge_pcg_solve(h, dev(b), x, rtol=1e-8, precision=amge.AMGE_FP64)
-    xo, it_o, rr_o, ok_o = pcg(o, b, rtol=1e-8)
+    xo, it_o, rr_o, ok_o = oracle_solution(name, o, b)
     assert st == amge.AMGE_OK and ok_o
     assert abs(info[0]["iters"] - it_o) <= 1, (info[0]["iters"], it_o)
     xg = host(x)
     assert np.linalg.norm(b - o.A[0] @ xg) <= 1e-8 * np.linalg.norm(b)
+    rel = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    print(f"{name}: FP64 solution vs oracle, relative L2 {rel:.2e}")
+    assert rel <= 1e-9, (name, rel)
+
+
+@pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
+def test_pcg_full_size_fp32_vcycle(amge, name):
+    h, o, b = workload(amge, name)
+    x = torch.empty(b.size, dtype=torch.float64, device="cuda")
+    st, info = amge.amge_pcg_solve(h, dev(b), x, rtol=1e-8, precision=amge.AMGE_FP32_VCYCLE)
+    xo, it_o, _, ok_o = oracle_solution(name, o, b)
+    assert st == amge.AMGE_OK and ok_o, (st, info)
+    assert info[0]["iters"] <= it_o + 3, (info[0]["iters"], it_o)
+    xg = host(x)
+    assert np.linalg.norm(b - o.A[0] @ xg) <= 1e-8 * np.linalg.norm(b)
+    rel = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    print(f"{name}: FP32-V-cycle solution vs FP64 oracle, relative L2 {rel:.2e}, "
+          f"{info[0]['iters']} iterations (oracle {it_o})")
+    assert rel <= 1e-7, (name, rel)

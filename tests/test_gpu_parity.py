@@ -10,8 +10,16 @@ Tolerances (derived from the arithmetic):
     substitutes); the other steps add O(nnz eps64).
   * PCG (FP64): iterations within +-1 of the oracle, solution relative L2 <= 1e-9,
     true relative residual <= 1e-8.
-  * PCG with the FP32 V-cycle: true FP64 relative residual <= 1e-8; the difference
-    from the FP64 oracle solution is bounded by kappa(A) * 1e-8 and reported.
+  * the FP32 V-cycle's FP64-operator product (AMGE_OP_A_WIDE): against the exact
+    product of the FP32-rounded input, eps32/2 |y_ref|_i (the final rounding) plus
+    2 (nnz_i + 1) eps64 (|M||x|)_i -- tight enough to catch a product that sums in
+    FP32 on inputs whose product cancels (gradient fields).
+  * one FP32 V-cycle: energy-norm distance to the FP64 oracle cycle <= 1e-3 (a fixed
+    bound; the CPU emulation of the same steps measures 5e-5 at 32^3 and 9e-5 at 64^3
+    under the 1e6 coefficient contrast).
+  * PCG with the FP32 V-cycle: true FP64 relative residual <= 1e-8, iterations within
+    3 of the FP64 oracle's, and the solution within 1e-7 (relative L2) of the FP64
+    oracle's.
 """
 import numpy as np
 import pytest
@@ -40,7 +48,7 @@ _uploaded = {}
 def upload(amge, form, n, L, contrast=True):
     key = (form, n, L, contrast)
     if key not in _uploaded:
-        _uploaded[key] = amge.amge_setup_upload(hierarchy(form, n, L, contrast))
+        _uploaded[key] = amge.amge_upload_levels(hierarchy(form, n, L, contrast))
     return _uploaded[key]
 
 
@@ -162,7 +170,7 @@ def test_dependent_launch_does_not_change_results(amge, prec):
     try:
         for on in (True, False):
             amge.amge_set_dependent_launch(on)
-            h = amge.amge_setup_upload(hierarchy("hcurl", 24, 3, True))
+            h = amge.amge_upload_levels(hierarchy("hcurl", 24, 3, True))
             rep = amge.amge_autotune_report(h)
             out.append((h, rep))
     finally:
@@ -265,13 +273,14 @@ def test_vcycle_fp64_matches_oracle(amge, form, n, L):
     assert np.linalg.norm(host(z) - ref) <= _coarse_tol(o) * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("form,n,L", CASES)
+FP32_CASES = CASES + [("hcurl", 32, 3), ("hdiv", 32, 3)]
+
+
+@pytest.mark.parametrize("form,n,L", FP32_CASES)
 def test_vcycle_fp32_close_to_oracle(amge, form, n, L):
-    """FP32 V-cycle vs the FP64 oracle in the energy norm.  The FP32 residual
-    b - A x on the finest level carries a rounding error of order
-    eps32 (|A||x|)_i, which the aux sweep and the coarse correction propagate; the
-    bound is eps32 * c_A with c_A = || |A||z| || / ||A z|| the cancellation factor
-    of the fine operator on the cycle's output (measured ratio 0.05-0.11 of it)."""
+    """FP32 V-cycle vs the FP64 oracle in the energy norm, under the 1e6 coefficient
+    contrast: within 1e-3 (the residuals of corrected iterates run on the FP64
+    operators; an all-FP32 cycle is 3e-2 off at 32^3 and 1.3e-1 at 64^3)."""
     h = upload(amge, form, n, L)
     o = oracle_hierarchy(form, n, L, True)
     from paper_2107_05613_gb300.inputs import rhs_vector
@@ -281,10 +290,34 @@ def test_vcycle_fp32_close_to_oracle(amge, form, n, L):
     amge.amge_vcycle(h, dev(r), z, 1, amge.AMGE_FP32_VCYCLE)
     ref = o.apply(r)
     A = o.A[0]
-    c_A = np.linalg.norm(abs(A) @ abs(ref)) / np.linalg.norm(A @ ref)
     d = host(z) - ref
     err = np.sqrt((d @ (A @ d)) / (ref @ (A @ ref)))
-    assert err <= EPS32 * c_A, (err, EPS32 * c_A)
+    assert err <= 1e-3, err
+
+
+@pytest.mark.parametrize("form,n,L", FP32_CASES)
+@pytest.mark.parametrize("field", ["random", "gradient"])
+def test_wide_product(amge, form, n, L, field):
+    """AMGE_OP_A_WIDE on every smoothing level: FP32 input, FP64 values and sums, FP32
+    output.  On gradient (curl) fields, where the large-coefficient part of A x
+    cancels, only FP64 sums meet the bound."""
+    h = upload(amge, form, n, L)
+    o = oracle_hierarchy(form, n, L, True)
+    rng = np.random.default_rng(n + 3 * L)
+    for l in range(L - 1):
+        A = o.A[l]
+        x = rng.uniform(-1, 1, A.shape[1])
+        if field == "gradient":
+            x = o.G[l] @ rng.uniform(-1, 1, o.G[l].shape[1]) + 1e-3 * x
+        x32 = x.astype(np.float32).astype(np.float64)
+        y = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+        amge.amge_apply(h, amge.AMGE_OP_A_WIDE, l, dev(x), y, amge.AMGE_FP32_VCYCLE)
+        ref = A @ x32
+        bound = 0.5 * EPS32 * np.abs(ref) + 2 * (np.diff(A.indptr) + 1) * EPS64 * (abs(A) @ abs(x32))
+        err = np.abs(host(y) - ref)
+        assert np.all(err <= bound + 1e-300), (l, float((err / (bound + 1e-300)).max()))
+    with pytest.raises(amge.AmgeError):             # FP32 V-cycle product only
+        amge.amge_apply(h, amge.AMGE_OP_A_WIDE, 0, dev(x), y, amge.AMGE_FP64)
 
 
 @pytest.mark.parametrize("form,n,L", CASES)
@@ -306,7 +339,7 @@ def test_pcg_fp64_matches_oracle(amge, form, n, L):
     assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("form,n,L", CASES)
+@pytest.mark.parametrize("form,n,L", FP32_CASES)
 def test_pcg_fp32_vcycle_reaches_fp64_tolerance(amge, form, n, L):
     from oracle import pcg
     from paper_2107_05613_gb300.inputs import rhs_vector
@@ -320,9 +353,9 @@ def test_pcg_fp32_vcycle_reaches_fp64_tolerance(amge, form, n, L):
     xg = host(x)
     assert np.linalg.norm(b - o.A[0] @ xg) <= 1e-8 * np.linalg.norm(b)
     xo, it_o, _, _ = pcg(o, b, rtol=1e-8)
-    assert info[0]["iters"] <= it_o + 5
+    assert info[0]["iters"] <= it_o + 3, (info[0]["iters"], it_o)
     err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
-    assert err <= 1e-5, err
+    assert err <= 1e-7, err
 
 
 def test_pcg_host_buffers(amge):
@@ -375,7 +408,7 @@ def test_one_level_hierarchy_is_direct(amge):
     from paper_2107_05613_gb300.inputs import rhs_vector
 
     hh = hierarchy("hcurl", 4, 1, False)
-    h = amge.amge_setup_upload(hh)
+    h = amge.amge_upload_levels(hh)
     A = hh.A[0].to_scipy()
     b = rhs_vector(2, A.shape[0])
     x = torch.empty_like(dev(b))

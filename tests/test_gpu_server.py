@@ -26,7 +26,7 @@ def amge():
 
 @pytest.fixture(scope="module")
 def hiers(amge):
-    return {key: amge.amge_setup_upload(hierarchy(*key, True))
+    return {key: amge.amge_upload_levels(hierarchy(*key, True))
             for key in [("hcurl", 16, 2), ("hdiv", 24, 3), ("hcurl", 24, 3)]}
 
 

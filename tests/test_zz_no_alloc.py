@@ -38,20 +38,26 @@ def _hier(form, n, levels):
 
 def test_noalloc_matches_regular_coarse_solve_on_consecutive_calls(amge):
     hh = _hier("hcurl", 16, 2)                      # coarsest level: 1,944 edge dofs
-    h = amge.amge_setup_upload(hh)
+    h = amge.amge_upload_levels(hh)
     Ac = hh.A[-1].to_scipy().toarray()
     nc = Ac.shape[0]
     # same tolerance as the coarsest-solve parity tests: the solve's forward error scale
     tol = max(1e-11, 10 * EPS64 * np.linalg.cond(Ac))
     rng = np.random.default_rng(11)
-    for call in range(2):                           # two calls in a row share the static array
-        b = torch.from_numpy(rng.uniform(-1, 1, nc)).cuda()
-        z_ref = torch.empty_like(b)
-        z_new = torch.full_like(b, float("nan"))
-        amge.amge_apply(h, amge.AMGE_OP_COARSE, 0, b, z_ref, amge.AMGE_FP64)
-        amge.amge_coarse_solve_noalloc(h, b, z_new)
-        torch.cuda.synchronize()
-        zr, zn = z_ref.cpu().numpy(), z_new.cpu().numpy()
+    bs = [torch.from_numpy(rng.uniform(-1, 1, nc)).cuda() for _ in range(2)]
+    z_ref = [torch.empty_like(b) for b in bs]
+    z_new = [torch.full_like(b, float("nan")) for b in bs]
+    for b, z in zip(bs, z_ref):
+        amge.amge_apply(h, amge.AMGE_OP_COARSE, 0, b, z, amge.AMGE_FP64)
+    torch.cuda.synchronize()
+    # two calls in a row on one stream with no synchronisation between them: the
+    # second call's first product overwrites the shared array only after the first
+    # call's second product has read it (stream order)
+    for b, z in zip(bs, z_new):
+        amge.amge_coarse_solve_noalloc(h, b, z)
+    torch.cuda.synchronize()
+    for call in range(2):
+        zr, zn = z_ref[call].cpu().numpy(), z_new[call].cpu().numpy()
         assert np.all(np.isfinite(zn)), call
         assert np.linalg.norm(zn - zr) <= tol * np.linalg.norm(zr), call
     h.free()
@@ -59,7 +65,7 @@ def test_noalloc_matches_regular_coarse_solve_on_consecutive_calls(amge):
 
 def test_noalloc_rejects_coarse_levels_beyond_its_array(amge):
     hh = _hier("hcurl", 8, 1)                       # one level: 4,184 dofs > 4,096
-    h = amge.amge_setup_upload(hh)
+    h = amge.amge_upload_levels(hh)
     b = torch.zeros(hh.A[0].shape[0], dtype=torch.float64, device="cuda")
     z = torch.empty_like(b)
     with pytest.raises(amge.AmgeError) as e:
