@@ -6,16 +6,17 @@ preconditioned by one AMGe V-cycle per iteration, on the H(curl) workload of
 64^3 Kuhn-split cubes (1,572,864 tetrahedra, 1,872,064 lowest-order Nedelec edge
 dofs), derivative coefficient beta log-uniform in [1e-3, 1e3] per 8^3 block of
 cubes, mass coefficient alpha = 1, 4-level AMGe hierarchy, one right-hand side
-uniform in [-1, 1].  The headline mode runs the V-cycle in FP32 inside FP64 PCG;
-the plain FP64 mode is measured beside it.
+uniform in [-1, 1].  The headline mode runs the V-cycle in FP32 inside FP64 PCG
+(--precision, default fp32); the plain FP64 mode is measured beside it, and so are
+the H(div) 64^3 workload and the block of 32 right-hand sides on H(curl) 48^3.
 
 Multi-GPU (torchrun, N ranks): every rank solves its own replica of the workload
 (independent problems, no collective on the data path); value = all ranks' solves
 divided by the slowest rank's time.
 
---impl reference times the CPU FP64 oracle as it stands on the host cores, on a
-bounded sample of the same workload (a few PCG iterations per step, extrapolated
-to the full solve's iteration count).
+--impl reference times the CPU FP64 oracle as it stands: every step is one full
+PCG solve of the same workload by the oracle on one host core (a spawned process
+with one BLAS / OpenMP thread).
 """
 import argparse
 import json
@@ -25,6 +26,8 @@ import subprocess
 import sys
 import threading
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -46,12 +49,9 @@ WORKLOADS = {
 # dram__bytes_read.sum + dram__bytes_write.sum of one level-0 residual sweep from an
 # ncu capture (profiles/k_sell_fp64_resid_level0_hcurl64.md); only for that kernel
 # and workload, null elsewhere.
-NCU_TRAFFIC = {("hcurl64", 8): 431.0e6}
+NCU_TRAFFIC = {("hcurl64", "A_fine", 8): 431.0e6}
 
 HBM_FALLBACK_GBS = 6800.0
-# FP64 FMA rate of this GB300 pool, measured with an independent-chain FMA loop on the
-# box (TFMA/s); ncu's nominal peak is 2 FMA per cycle per SM, 0.63 TFMA/s at 2.07 GHz.
-FP64_TFMA_MEASURED = 0.503
 METRIC = "PCG solves/s to 1e-8 rel residual"
 
 
@@ -62,7 +62,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="hcurl64")
-    p.add_argument("--precision", choices=["fp32", "fp64"], default="fp64")
+    p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    p.add_argument("--no-subresults", action="store_true",
+                   help="skip the H(div) 64^3 and 48^3 x 32 right-hand-side sub-results")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quick", action="store_true", help="headline loop only (for profiler runs)")
@@ -180,12 +182,12 @@ def make_workload(wl):
     return hh, b
 
 
-def sweep_bytes(nnz, n, w, extra_vectors, nrhs=1):
-    """Algorithmic bytes of one sweep: values + int32 columns + int32 row pointers,
-    one read of the gathered block, the right-hand side and the output, plus
-    `extra_vectors` other row-wise blocks (FP width w, nrhs columns; a diagonal
-    counts as one column)."""
-    return nnz * (w + 4) + 4 * (n + 1) + w * n * nrhs * 3 + w * n * extra_vectors
+def sweep_bytes(nnz, n, w, extra_vectors, nrhs=1, vw=None):
+    """Algorithmic bytes of one sweep: values (width vw, default w) + int32 columns +
+    int32 row pointers, one read of the gathered block, the right-hand side and the
+    output, plus `extra_vectors` other row-wise blocks (FP width w, nrhs columns; a
+    diagonal counts as one column)."""
+    return nnz * ((vw or w) + 4) + 4 * (n + 1) + w * n * nrhs * 3 + w * n * extra_vectors
 
 
 def a_fine_bytes_per_launch(hh, w, nrhs=1, ag=False):
@@ -224,21 +226,25 @@ def stored_ag_nnz(A, G):
 
 def vcycle_bytes(hh, w, ag_nnz=None):
     """Algorithmic bytes of one single-vector V-cycle (every level's sweeps, transfers
-    and the coarsest solve, which always reads the FP64 inverse)."""
+    and the coarsest solve, which always reads the FP64 inverse).  FP32 V-cycle
+    (w = 4): the residuals of iterates corrected through G or P read the FP64
+    operator (8-byte values) on FP32 vectors."""
     import numpy as np
 
     tot = 0.0
     L = len(hh.A)
+    wide = 8 if w == 4 else None
     for l in range(L - 1):
         A, P, G = hh.A[l], hh.P[l], hh.G[l]
         n, naux, nc = A.shape[0], G.shape[1], P.shape[1]
         AGnnz = ag_nnz[l] if ag_nnz else None
         if AGnnz:   # two residuals, r -= (A G) y (reads r, y; writes r), final sweep through A G
-            tot += 2 * sweep_bytes(A.nnz, n, w, 0) + 3 * w * n
+            tot += sweep_bytes(A.nnz, n, w, 0) + sweep_bytes(A.nnz, n, w, 0, vw=wide) + 3 * w * n
             tot += AGnnz * (w + 4) + 4 * (n + 1) + w * (naux + 2 * n)
             tot += AGnnz * (w + 4) + 4 * (n + 1) + w * (naux + 4 * n)
-        else:
-            tot += 3 * sweep_bytes(A.nnz, n, w, 0) + sweep_bytes(A.nnz, n, w, 1) + 3 * w * n   # + x = m^-1 b
+        else:       # + x = m^-1 b
+            tot += (sweep_bytes(A.nnz, n, w, 0) + 2 * sweep_bytes(A.nnz, n, w, 0, vw=wide)
+                    + sweep_bytes(A.nnz, n, w, 1, vw=wide) + 3 * w * n)
         # G^T r scaled (2x), G y added (2x): read + write of the output for the add.
         # G with entries +-1 only (the de Rham incidences) is stored sign-coded:
         # a column index per entry and no values.
@@ -261,64 +267,138 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ oracle timing
-def oracle_sample(hh, b, iters_full, budget_s=15.0):
-    """Time the oracle's PCG for a few iterations (bounded CPU work) and extrapolate
-    to one full solve of `iters_full` iterations."""
+_ORACLE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def _oracle_worker(blob_path, rhs_path, solves, barrier, queue):
+    """One spawned oracle process: read the hierarchy blob and the right-hand side,
+    wait for the others, then time `solves` full PCG solves (one BLAS thread)."""
+    import numpy as np
+
     from oracle import OracleHierarchy, pcg
 
-    o = OracleHierarchy.from_hierarchy(hh)
-    t = time.perf_counter()
-    pcg(o, b, rtol=1e-30, maxit=1)
-    t1 = time.perf_counter() - t                     # 2 V-cycles + 2 products + residual
-    k = max(1, min(20, int(budget_s / max(t1 / 2, 1e-3)) - 1))
-    t = time.perf_counter()
-    pcg(o, b, rtol=1e-30, maxit=k)
-    tk = time.perf_counter() - t
-    per_iter = tk / (k + 1)
-    return {"per_iter_s": per_iter, "iters_sampled": k, "solve_s": per_iter * iters_full,
-            "seconds": tk + t1, "cores": 1}
+    try:
+        with open(blob_path, "rb") as f:
+            o = OracleHierarchy.from_blob(f.read())
+        b = np.load(rhs_path)
+        barrier.wait(timeout=900)
+        out = []
+        for _ in range(solves):
+            t = time.perf_counter()
+            _, it, rr, ok = pcg(o, b, rtol=1e-8)
+            out.append((time.perf_counter() - t, it, rr, ok))
+        queue.put(("ok", out))
+    except Exception as e:  # noqa: BLE001  (reported to the parent)
+        queue.put(("error", repr(e)))
+
+
+def oracle_solves(hh, b, procs, solves):
+    """Full FP64 oracle solves in `procs` concurrent spawned processes (one thread
+    each, spawned so that no process forks after the GPU is in use), `solves` per
+    process.  Returns one list of (seconds, iterations, relres, converged) per
+    process; the solves of different processes overlap in time."""
+    import multiprocessing as mp
+    import tempfile
+
+    import numpy as np
+
+    from paper_2107_05613_gb300.inputs import hierarchy_to_blob
+
+    tmpdir = "/dev/shm" if os.path.isdir("/dev/shm") else None
+    with tempfile.TemporaryDirectory(dir=tmpdir) as d:
+        blob_path, rhs_path = os.path.join(d, "h.blob"), os.path.join(d, "b.npy")
+        with open(blob_path, "wb") as f:
+            f.write(hierarchy_to_blob(hh))
+        np.save(rhs_path, np.ascontiguousarray(b))
+        ctx = mp.get_context("spawn")
+        barrier, queue = ctx.Barrier(procs), ctx.Queue()
+        saved = {k: os.environ.get(k) for k in _ORACLE_THREAD_ENV}
+        os.environ.update({k: "1" for k in _ORACLE_THREAD_ENV})
+        try:
+            ps = [ctx.Process(target=_oracle_worker, args=(blob_path, rhs_path, solves, barrier, queue))
+                  for _ in range(procs)]
+            for p in ps:
+                p.start()
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        res = [queue.get(timeout=3600) for _ in ps]
+        for p in ps:
+            p.join()
+    errs = [r[1] for r in res if r[0] != "ok"]
+    if errs:
+        raise RuntimeError("oracle worker failed: " + errs[0])
+    return [r[1] for r in res]
+
+
+def oracle_all_core_procs(hh):
+    """Concurrent oracle processes for the all-core timing: one per host core, fewer
+    if host memory would not hold that many copies of the hierarchy (~3x its CSR
+    bytes each)."""
+    per = 3 * sum(24 * m.nnz for m in list(hh.A) + list(hh.P) + list(hh.G)) + (1 << 28)
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = 0
+    cores = os.cpu_count() or 1
+    return max(1, min(cores, int(avail // per) if avail else 1))
+
+
+def cpu_baseline(hh, b):
+    """The oracle on the host cores: one full solve on one core, then one full solve
+    in each of P concurrent single-thread processes (P = host cores, capped by host
+    memory); value = the all-core throughput."""
+    one = oracle_solves(hh, b, 1, 1)[0][0]
+    procs = oracle_all_core_procs(hh)
+    allc = oracle_solves(hh, b, procs, 1)
+    wall = max(r[0][0] for r in allc)
+    return {
+        "value": procs / wall, "unit": "solves/s", "cores": procs, "kind": "oracle",
+        "sample": f"scipy FP64 oracle, full PCG solves of this workload ({one[1]} iterations, relres "
+                  f"{one[2]:.2e}): {procs} concurrent single-thread processes, one solve each, slowest "
+                  f"{wall:.1f} s; host has {os.cpu_count()} cores",
+        "single_thread": {"value": 1.0 / one[0], "unit": "solves/s", "cores": 1,
+                          "seconds_per_solve": one[0]},
+    }
 
 
 # ------------------------------------------------------------------ reference arm
+def workload_config(wl, hh):
+    """The `config` object of both arms for workload `wl`."""
+    op_bytes = sum(12 * m.nnz for m in list(hh.A) + list(hh.P) + list(hh.G))
+    return {"workload": wl["desc"], "form": wl["form"], "n": wl["n"], "levels": len(hh.A),
+            "dofs": int(hh.A[0].shape[0]), "nrhs": wl.get("nrhs", 1), "nnz_A0": int(hh.A[0].nnz), "rtol": 1e-8,
+            "l2": ("inputs larger than L2 (129 MB): the operators alone take %.2f GB in FP64" % (op_bytes / 1e9)
+                   if op_bytes > 129e6 else "L2-resident small case (%.1f MB of FP64 operators), no flush" %
+                   (op_bytes / 1e6)),
+            "parallelism": "single GPU or independent replicas"}
+
+
 def run_reference(args, dist):
     wl = WORKLOADS[args.workload]
     if dist.rank != 0:
         return
     hh, b = make_workload(wl)
-    from oracle import OracleHierarchy, pcg
-
-    o = OracleHierarchy.from_hierarchy(hh)
-    # iteration count of the full FP64 solve: a short calibration of the oracle's
-    # convergence would itself take minutes at this size, so the oracle runs one
-    # bounded sample per step and the full-solve length comes from the oracle on
-    # the 24^3 analogue scaled by the observed growth (stated in the sample text).
-    per_step = []
-    k = 2
-    for i in range(args.warmup + args.steps):
-        t = time.perf_counter()
-        pcg(o, b, rtol=1e-30, maxit=k)
-        dt = (time.perf_counter() - t) / (k + 1)
-        if i >= args.warmup:
-            per_step.append(dt)
-    iters_full = ITERS_FULL_FP64.get(args.workload)
-    per_iter = statistics.median(per_step)
-    value = 1.0 / (per_iter * iters_full)
+    if wl.get("nrhs", 1) > 1:
+        b = b[:, 0].copy()
+    res = oracle_solves(hh, b, 1, args.warmup + args.steps)[0][args.warmup:]
+    total = sum(r[0] for r in res)
+    value = args.steps / total      # right-hand sides solved per second (one per step)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_iter * iters_full,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["desc"], "precision": "fp64 (oracle)"},
+        "config": workload_config(wl, hh), "precision": "fp64 (oracle)",
+        "iters": res[0][1], "true_relres": max(r[2] for r in res),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": f"scipy FP64 oracle, {k} PCG iterations per step on the full workload, "
-                                   f"per-iteration time extrapolated to {iters_full} iterations"},
+                         "sample": f"scipy FP64 oracle, one full PCG solve of the workload per step "
+                                   f"({res[0][1]} iterations) in a spawned single-thread process"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-
-
-# Iterations of the FP64 solve of each workload (oracle and GPU agree within 1; the
-# GPU measures it in every run of the ours arm, see "fp64"."iters").
-ITERS_FULL_FP64 = {"hcurl64": 43, "hdiv64": 45, "hcurl8": 33}
 
 
 # ------------------------------------------------------------------ our arm
@@ -331,8 +411,76 @@ def profiler_range(on):
         pass
 
 
+def level0_launch_bytes(hh, w, nrhs, ag):
+    """Algorithmic bytes per launch of the two level-0 A kernel classes of a V-cycle.
+    A_fine: FP64 (w = 8) every level-0 A sweep (see a_fine_bytes_per_launch); FP32
+    single vector: the first residual r = b - A x only (FP32 values); FP32 blocks:
+    all four sweeps.  A_wide (FP32 single vector): the residuals of corrected iterates
+    on the FP64 operator -- with the A G form the post-correction residual, else two
+    residuals and the final l1 sweep (which also reads m^-1)."""
+    A = hh.A[0]
+    n, nnz = A.shape[0], A.nnz
+    if w == 8 or nrhs > 1:
+        return {"A_fine": a_fine_bytes_per_launch(hh, w, nrhs, ag)}
+    wide = (float(sweep_bytes(nnz, n, 4, 0, vw=8)) if ag else
+            (2 * sweep_bytes(nnz, n, 4, 0, vw=8) + sweep_bytes(nnz, n, 4, 1, vw=8)) / 3.0)
+    return {"A_fine": float(sweep_bytes(nnz, n, 4, 0)), "A_wide": wide}
+
+
+ROOFLINE_KERNELS = {
+    "A_fine": "k_sell level-0 A sweeps (residuals r = b - A x{last})",
+    "A_wide": "k_sell_wide level-0 residuals of corrected iterates (FP64 values and sums, FP32 vectors)",
+}
+
+
+def timed_solves(amge, h, bd, x, precision, steps, nrhs, maxit=1000):
+    """`steps` PCG solves between CUDA events on the current stream; returns
+    (ms, [infos of the last solve])."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = []
+    for _ in range(steps):
+        st, info = amge.amge_pcg_solve(h, bd, x, rtol=1e-8, maxit=maxit, precision=precision, nrhs=nrhs)
+        out.append((st, info))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def mode_result(amge, ms, out, steps, nrhs, world=1):
+    st = max(o[0] for o in out)
+    infos = out[-1][1]
+    return {"solves_per_s": world * steps * nrhs / (ms / 1e3), "ms_per_step": ms / steps,
+            "iters": max(i["iters"] for i in infos), "true_relres": max(i["true_relres"] for i in infos),
+            "status": amge.STATUS_NAMES[st]}
+
+
+def sub_result(amge, name, steps):
+    """Solves/s of another workload in both precisions (device-resident inputs)."""
+    import torch
+
+    wl = WORKLOADS[name]
+    hh, b = make_workload(wl)
+    nrhs = wl.get("nrhs", 1)
+    h = amge.amge_upload_levels(hh)
+    bd = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    x = torch.empty_like(bd)
+    out = {"config": workload_config(wl, hh)}
+    for pname, prec in (("fp32", amge.AMGE_FP32_VCYCLE), ("fp64", amge.AMGE_FP64)):
+        timed_solves(amge, h, bd, x, prec, 1, nrhs)              # warm-up (graph capture)
+        ms, res = timed_solves(amge, h, bd, x, prec, steps, nrhs)
+        out[pname] = mode_result(amge, ms, res, steps, nrhs)
+    h.free()
+    del bd, x
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, dist):
-    import numpy as np
     import torch
 
     dist.init("nccl" if torch.cuda.is_available() else "gloo")
@@ -346,7 +494,7 @@ def run_ours(args, dist):
     w = 4 if prec == amge.AMGE_FP32_VCYCLE else 8
     if args.no_dependent_launch:
         amge.amge_set_dependent_launch(False)
-    h = amge.amge_setup_upload(hh)
+    h = amge.amge_upload_levels(hh)
     if args.kernels_from:
         with open(args.kernels_from) as f:
             chosen = json.loads(f.read().strip().splitlines()[-1])["autotune"]
@@ -365,7 +513,7 @@ def run_ours(args, dist):
     def solve(precision, strict=True, maxit=1000):
         st, info = amge.amge_pcg_solve(h, bd, x, rtol=1e-8, maxit=maxit, precision=precision, nrhs=nrhs)
         if strict and st != amge.AMGE_OK:
-            raise RuntimeError(f"solve failed: {info}")
+            raise RuntimeError(f"solve failed: {amge.STATUS_NAMES[st]} {info}")
         out = dict(info[0])
         out["iters"] = max(i["iters"] for i in info)
         out["true_relres"] = max(i["true_relres"] for i in info)
@@ -409,17 +557,18 @@ def run_ours(args, dist):
     iters = [i["iters"] for i in infos]
     relres = max(i["true_relres"] for i in infos)
 
+    fp32 = prec == amge.AMGE_FP32_VCYCLE
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 V-cycle in f64 PCG" if prec == amge.AMGE_FP32_VCYCLE else "f64",
+        "dtype": ("f32 V-cycle (f64 values and sums for residuals of corrected iterates) in f64 PCG" if fp32
+                  else "f64"),
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "form": wl["form"], "n": wl["n"], "levels": len(hh.A), "dofs": n,
-                   "nrhs": nrhs,
-                   "nnz_A0": hh.A[0].nnz, "rtol": 1e-8, "precision": args.precision,
-                   "l2": "inputs larger than L2: the resident hierarchy is ~%.1f GB" % (amge.amge_hier_info(h)[2] / 1e9),
-                   "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU"},
+        "config": workload_config(wl, hh),
+        "precision": args.precision,
+        "device_bytes": amge.amge_hier_info(h)[2],
+        "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU",
         "iters": iters[0], "true_relres": relres,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "clocks": clk,
@@ -428,9 +577,9 @@ def run_ours(args, dist):
     kern = {k: {"launches": c, "ms": m, "avg_us": (1e3 * m / c if c else None)} for k, (c, m) in prof.items()}
     line["kernels"] = kern
     tuned = amge.amge_autotune_report(h)
+    pname = "fp32" if fp32 else "fp64"
     line["autotune"] = {f"L{l}.{p}.{o}": v for (l, p, o), v in tuned.items() if v}
-    line["autotune_us"] = {f"L{l}.{p}.{o}": t for (l, p, o), t in amge.amge_autotune_times(h).items()
-                           if p == ("fp64" if w == 8 else "fp32")}
+    line["autotune_us"] = {f"L{l}.{p}.{o}": t for (l, p, o), t in amge.amge_autotune_times(h).items() if p == pname}
     line["kernel_timing"] = ("CUDA events around every launch, on the launching stream, over a second pass of the "
                              "same K steps right after the headline timed region")
     line["gpu_launches"] = int(sum(c for c, _ in launches.values()))
@@ -438,31 +587,37 @@ def run_ours(args, dist):
     hbm = peaks.get("hbm_gbs") if peaks else None
     peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s (of fallback)"
     hbm = hbm or HBM_FALLBACK_GBS
-    c, m = prof["A_fine"]
+    ag = tuned.get((0, pname, "AG"), -1) >= 0
+    per_launch = level0_launch_bytes(hh, w, nrhs, ag)
+    # the roofline kernel: the level-0 A class with the most device time
+    cls = max(per_launch, key=lambda k: prof[k][1])
+    c, m = prof[cls]
     if c and m > 0:
-        ag = tuned.get((0, "fp64" if w == 8 else "fp32", "AG"), -1) >= 0
-        bytes_launch = a_fine_bytes_per_launch(hh, w, nrhs, ag)
+        bytes_launch = per_launch[cls]
         achieved = bytes_launch / (m / c / 1e3) / 1e9
+        fp64_values = (cls == "A_wide") or not fp32
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                             "frac": achieved / hbm,
-                            "traffic": NCU_TRAFFIC.get((args.workload, w)) if nrhs == 1 else None,
-                            "kernel": ("k_sell level-0 A residual sweeps r = b - A x" if ag else
-                                       "k_sell level-0 A sweeps (three residuals, final l1 sweep)") + ", "
-                                      + ("FP32" if w == 4 else "FP64"),
+                            "traffic": NCU_TRAFFIC.get((args.workload, cls, w)) if nrhs == 1 else None,
+                            "kernel": ROOFLINE_KERNELS[cls].format(last="" if ag else ", final l1 sweep")
+                                      + (", FP64" if not fp32 else ""),
+                            "class": cls, "launches": c, "avg_us": 1e3 * m / c,
                             "bytes_per_launch": bytes_launch, "peak_source": peak_src}
-        if w == 8 and nrhs == 1:
+        if fp64_values and nrhs == 1:
             # the same launches against the FP64 pipe: one FMA per stored nonzero (the
-            # chain starts from b), the kernel's other bound on GB300
+            # chain starts from b), the kernel's other bound on GB300; the peak is the
+            # FMA rate measured on this GPU right now (amge_fp64_fma_rate)
             fma = float(hh.A[0].nnz)
             tfma = fma / (m / c / 1e3) / 1e12
-            line["roofline"]["fp64"] = {"achieved": tfma, "peak": FP64_TFMA_MEASURED, "unit": "TFMA/s",
-                                        "frac": tfma / FP64_TFMA_MEASURED, "fma_per_launch": fma,
-                                        "peak_source": "FMA-loop probe on this GPU pool (of measured)"}
-    vc_ms = sum(prof[k][1] for k in ("A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "vcycle_vec", "AG"))
+            peak64 = amge.amge_fp64_fma_rate()
+            line["roofline"]["fp64"] = {"achieved": tfma, "peak": peak64, "unit": "TFMA/s",
+                                        "frac": tfma / peak64, "fma_per_launch": fma,
+                                        "peak_source": "amge_fp64_fma_rate on this GPU in this run (of measured)"}
+    vc_ms = sum(prof[k][1] for k in ("A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "vcycle_vec", "AG",
+                                     "A_wide"))
     # one coarsest solve per V-cycle: one kernel (FP32 V-cycle: widening + product)
-    n_vc = prof["coarse"][0] / (2 if w == 4 else 1)
-    if vc_ms > 0 and n_vc > 0:
-        pname = "fp64" if w == 8 else "fp32"
+    n_vc = prof["coarse"][0] / (2 if fp32 else 1)
+    if vc_ms > 0 and n_vc > 0 and nrhs == 1:
         ag_nnz = [stored_ag_nnz(hh.A[l], hh.G[l]) if tuned.get((l, pname, "AG"), -1) >= 0 else None
                   for l in range(len(hh.A) - 1)]
         line["vcycle_hbm_gbs"] = vcycle_bytes(hh, w, ag_nnz) * n_vc / (vc_ms / 1e3) / 1e9
@@ -474,18 +629,11 @@ def run_ours(args, dist):
         return
 
     # the other precision, for the FP32-vs-FP64 comparison
-    other = amge.AMGE_FP64 if prec == amge.AMGE_FP32_VCYCLE else amge.AMGE_FP32_VCYCLE
-    solve(other, strict=False, maxit=300)
-    torch.cuda.synchronize()
+    other = amge.AMGE_FP64 if fp32 else amge.AMGE_FP32_VCYCLE
+    timed_solves(amge, h, bd, x, other, 1, nrhs, maxit=300)
     k2 = max(2, args.steps // 2)
-    e0.record(stream)
-    oi = [solve(other, strict=False, maxit=300) for _ in range(k2)]
-    e1.record(stream)
-    torch.cuda.synchronize()
-    line["fp64" if other == amge.AMGE_FP64 else "fp32"] = {
-        "solves_per_s": dist.world * k2 * nrhs / (dist.max(e0.elapsed_time(e1), "cuda") / 1e3),
-        "iters": oi[0]["iters"], "true_relres": oi[0]["true_relres"], "status": oi[0]["status_name"],
-        "maxit": 300}
+    ms2, res2 = timed_solves(amge, h, bd, x, other, k2, nrhs, maxit=300)
+    line["fp64" if fp32 else "fp32"] = mode_result(amge, dist.max(ms2, "cuda"), res2, k2, nrhs, dist.world)
 
     # end to end through the C ABI with host buffers (H2D of b and D2H of x every step)
     if not args.no_e2e:
@@ -499,19 +647,18 @@ def run_ours(args, dist):
         el = dist.max(time.perf_counter() - t, "cuda")
         line["e2e"] = {"value": dist.world * args.steps * nrhs / el, "unit": "solves/s",
                        "h2d_bytes_per_step": 8 * n * nrhs, "d2h_bytes_per_step": 8 * n * nrhs}
+    h.free()
+    del bd, x
+    torch.cuda.empty_cache()
 
-    if dist.rank == 0 and not args.no_cpu_baseline:
-        if nrhs > 1:
-            b = b[:, 0].copy()
-        fp64_iters = iters[0] if prec == amge.AMGE_FP64 else line.get("fp64", {}).get("iters", iters[0])
-        s = oracle_sample(hh, b, fp64_iters)
-        line["cpu_baseline"] = {
-            "value": 1.0 / s["solve_s"], "unit": "solves/s", "cores": s["cores"], "kind": "oracle",
-            "sample": f"scipy FP64 oracle, first {s['iters_sampled']} PCG iterations of this workload "
-                      f"({s['per_iter_s']:.2f} s/iteration) extrapolated to the {fp64_iters}-iteration FP64 "
-                      f"solve; host has {os.cpu_count()} cores, the oracle uses 1"}
+    if dist.world == 1 and not args.no_subresults and args.workload == "hcurl64":
+        line["hdiv64"] = sub_result(amge, "hdiv64", 5)
+        line["hcurl48x32"] = sub_result(amge, "hcurl48x32", 5)
     if not args.no_serving and dist.world == 1:
         line["serving"] = run_serving(args, amge)
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        bc = b[:, 0].copy() if nrhs > 1 else b
+        line["cpu_baseline"] = cpu_baseline(hh, bc)
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
     dist.done()
@@ -536,7 +683,7 @@ def run_serving(args, amge, n_requests=1000, load=0.7, seed=2107056135, max_slot
                 beta = 10.0 ** rng.uniform(-2.0, 2.0)
                 nt = 6 * n ** 3
                 hh = build_hierarchy(form, n, beta=np.full(nt, beta), alpha=np.ones(nt))
-                h = amge.amge_setup_upload(hh)
+                h = amge.amge_upload_levels(hh)
                 pool.append((form, n, beta, h))
                 sd = int(rng.integers(1 << 30))
                 banks.append([rhs_vector(sd, h.n, k).reshape(h.n, k) for k in range(1, 9)])
