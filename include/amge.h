@@ -290,6 +290,12 @@ enum {
 amge_status amge_profile_enable(amge_hier* h, int32_t enable);
 amge_status amge_profile_read(amge_hier* h, int64_t* count, double* ms);
 
+/* FP64 FMA issue rate of the current device in TFMA/s (*tfma, host): a kernel of
+ * independent FMA chains filling every SM, best of five timed launches on `stream`
+ * (synchronised).  The second roofline of the FP64 sparse products, which issue one
+ * FMA per stored 12-byte entry.  Errors: AMGE_EINVAL for NULL, AMGE_ECUDA. */
+amge_status amge_fp64_fma_rate(double* tfma, void* stream);
+
 /* Coarsest-level solve z = A_L^{-1} b without any device allocation.
  * The paper has no counterpart.  It serves callers that may not have the library
  * allocate device memory while they solve (a latency-critical loop that must not
@@ -413,6 +419,21 @@ amge_status amge_autotune_times(const amge_hier* h, float* us);
  * while a call on h is in flight.  AMGE_EINVAL for an index out of range, an
  * operator that is not stored (-1 in the report) or another lane count. */
 amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int32_t op, int32_t lanes);
+
+/* Kernel choice of the block (multi-right-hand-side) products for nrhs columns (2 ..
+ * 32) and one precision, per smoothing level and operator (op order as above):
+ * codes[l * 6 + op] = 0 CSR (a lane group per row), 1 / 2 sliced ELL with one / two
+ * 16-byte vectors of columns per lane, -1 not stored or not tuned yet.  The library
+ * times the forms per operator on the first block call with that nrhs and keeps the
+ * fastest; us (optional, [levels-1][6][3]) receives the measured time per launch
+ * (microseconds) of each form, -1 where not measured. */
+amge_status amge_autotune_report_mm(amge_hier* h, int32_t nrhs, int32_t precision, int32_t* codes, float* us);
+
+/* Pin one block kernel choice (code as above); AMGE_EINVAL where the sliced-ELL form
+ * does not apply to nrhs (nrhs must be a multiple of code * 16 / sizeof(value), at
+ * most 8 lanes per row).  Pinned choices are not re-tuned. */
+amge_status amge_set_kernel_mm(amge_hier* h, int32_t level, int32_t precision, int32_t op, int32_t nrhs,
+                               int32_t code);
 
 /* Release the hierarchy and all device memory it holds (NULL is ignored). */
 void amge_hier_free(amge_hier* h);

@@ -82,6 +82,9 @@ _SIGS = {
                           ctypes.POINTER(_i32)],
     "amge_profile_read": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)],
     "amge_coarse_solve_noalloc": [_vp, _vp, _vp, _vp],
+    "amge_fp64_fma_rate": [ctypes.POINTER(ctypes.c_double), _vp],
+    "amge_autotune_report_mm": [_vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)],
+    "amge_set_kernel_mm": [_vp, _i32, _i32, _i32, _i32, _i32],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -416,3 +419,30 @@ kMaxRhs = 32
 def lib_handle():
     """The loaded ctypes library (tests inspect its exports)."""
     return _lib
+
+
+def amge_fp64_fma_rate(stream=None) -> float:
+    """FP64 FMA issue rate of the current device, TFMA/s."""
+    v = ctypes.c_double()
+    _check(_lib.amge_fp64_fma_rate(ctypes.byref(v), _stream(stream)), "amge_fp64_fma_rate")
+    return v.value
+
+
+_OPS = ["A", "P", "PT", "G", "GT", "AG"]
+
+
+def amge_autotune_report_mm(h: Hier, nrhs: int, precision: int = AMGE_FP32_VCYCLE):
+    """({(level, op): code}, {(level, op): [us CSR, us sliced ELL x1, us x2]}) of the block
+    products for nrhs columns: 0 = CSR, 1 / 2 = sliced ELL with 1 / 2 vectors per lane,
+    -1 = not stored / not tuned yet."""
+    L = h.levels
+    codes = (_i32 * max((L - 1) * 6, 1))()
+    us = (ctypes.c_float * max((L - 1) * 18, 1))()
+    _check(_lib.amge_autotune_report_mm(h.handle, nrhs, precision, codes, us), "amge_autotune_report_mm")
+    return ({(l, _OPS[o]): int(codes[l * 6 + o]) for l in range(L - 1) for o in range(6)},
+            {(l, _OPS[o]): [float(us[(l * 6 + o) * 3 + k]) for k in range(3)] for l in range(L - 1) for o in range(6)})
+
+
+def amge_set_kernel_mm(h: Hier, level: int, precision: int, op, nrhs: int, code: int):
+    o = _OPS.index(op) if isinstance(op, str) else op
+    _check(_lib.amge_set_kernel_mm(h.handle, level, precision, o, nrhs, code), "amge_set_kernel_mm")

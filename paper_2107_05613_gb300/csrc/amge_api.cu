@@ -35,12 +35,17 @@ struct LevelDev {
   // the autotuner's measured time per launch (us) of each candidate (kTuneCodes
   // order), -1 where not measured
   float tune_us[6][9] = {};
+  // block (multi-right-hand-side) kernel per operator and column count: -1 = not
+  // tuned yet, 0 = CSR, 1 / 2 = sliced ELL with 1 / 2 vectors of 16 bytes per lane
+  int8_t mmk[6][kMaxRhs + 1];
+  float mm_us[6][3] = {};  // the block tuner's time per launch (us) of each form, last tuned nrhs
   V* minv = nullptr;
   V* mauxinv = nullptr;
   V *x = nullptr, *r = nullptr, *y = nullptr, *tmp = nullptr;
   V *b = nullptr, *z = nullptr;
   // block workspace ([n][nrhs] / [naux][nrhs]), allocated on the first multi-RHS call
   V *X = nullptr, *R = nullptr, *Y = nullptr, *T = nullptr, *B = nullptr, *Z = nullptr;
+  LevelDev() { std::memset(mmk, -1, sizeof(mmk)); }
 };
 
 }  // namespace amge
@@ -80,6 +85,7 @@ struct amge_hier {
   RedScratch red;
   RedScratchMM redmm;
   int mm_cap = 0;  // nrhs the block workspace was sized for
+  bool mm_tuned[2][kMaxRhs + 1] = {};  // block kernels timed for (precision, nrhs)
   double *PR = nullptr, *PZ = nullptr, *PP = nullptr, *PQ = nullptr, *SB = nullptr, *SX = nullptr;
   float *S32in = nullptr, *S32out = nullptr;
   double* CT = nullptr;
@@ -840,6 +846,17 @@ amge_status amge::ensure_mm(amge_hier* h, int nrhs, cudaStream_t s, int cap) {
 
 namespace {
 
+// Block product with the kernel chosen for operator `op` and nrhs columns (CSR where
+// none was chosen or the sliced-ELL form does not apply).
+template <typename V>
+void opk_mm(amge_hier* h, int cls, const LevelDev<V>& d, int op, int nrhs, int epi, const SpmvArgs<V>& a,
+            cudaStream_t s) {
+  Prof p(h, cls, s);
+  const int code = d.mmk[op][nrhs];
+  if (code > 0 && launch_sell_mm<V>(op_sell(d, op), nrhs, code, epi, a, s)) return;
+  launch_csr_mm<V>(op_csr(d, op), nrhs, epi, a, s);
+}
+
 // One V-cycle on a [n_l][nrhs] block (Algorithm 4.1 applied to every column).
 template <typename V>
 void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream_t s, bool x_ready = false) {
@@ -853,22 +870,19 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
   const int clsA = l == 0 ? AMGE_PROF_A_FINE : AMGE_PROF_A_COARSE;
   V* x = d.X;
   V* xt = d.T;
-  auto mm = [&](int cls, const DevCsr<V>& M, int epi, const SpmvArgs<V>& a) {
-    Prof p(h, cls, s);
-    launch_csr_mm<V>(M, nrhs, epi, a, s);
-  };
+  auto mm = [&](int cls, int op, int epi, const SpmvArgs<V>& a) { opk_mm<V>(h, cls, d, op, nrhs, epi, a, s); };
   auto aux_sweep = [&]() {
     SpmvArgs<V> g;
     g.x = d.R, g.d = d.mauxinv, g.y = d.Y;
-    mm(AMGE_PROF_GT, d.cGT, EPI_SCALE, g);
+    mm(AMGE_PROF_GT, OP_GT, EPI_SCALE, g);
     SpmvArgs<V> c;
     c.x = d.Y, c.y = x;
-    mm(AMGE_PROF_G, d.cG, EPI_ADD, c);
+    mm(AMGE_PROF_G, OP_G, EPI_ADD, c);
   };
   auto residual = [&]() {
     SpmvArgs<V> a;
     a.x = x, a.b = b, a.y = d.R;
-    mm(clsA, d.cA, EPI_RESID, a);
+    mm(clsA, OP_A, EPI_RESID, a);
   };
   LevelDev<V>& c = lv[l + 1];
   const bool c_smooths = l + 1 < h->L - 1;  // the next level starts with X = m^-1 B
@@ -876,7 +890,7 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
     SpmvArgs<V> a;
     a.x = d.R, a.y = c.B;
     if (c_smooths) a.d = c.minv, a.y2 = c.X;
-    mm(AMGE_PROF_PT, d.cPT, c_smooths ? EPI_STORE_MUL : EPI_STORE, a);
+    mm(AMGE_PROF_PT, OP_PT, c_smooths ? EPI_STORE_MUL : EPI_STORE, a);
   };
   if (d.use_ag) {  // as in vcycle_level: r -= (A G) y after each aux sweep
     if (!x_ready) {
@@ -888,20 +902,20 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
     {
       SpmvArgs<V> a;
       a.x = d.Y, a.b = d.R, a.y = d.R;
-      mm(AMGE_PROF_AG, d.cAG, EPI_RESID, a);
+      mm(AMGE_PROF_AG, OP_AG, EPI_RESID, a);
     }
     restrict_to_next();
     vcycle_level_mm<V>(h, l + 1, nrhs, c.B, c.Z, s, c_smooths);
     {
       SpmvArgs<V> a;
       a.x = c.Z, a.y = x;
-      mm(AMGE_PROF_P, d.cP, EPI_ADD, a);
+      mm(AMGE_PROF_P, OP_P, EPI_ADD, a);
     }
     residual();
     aux_sweep();
     SpmvArgs<V> a;
     a.x = d.Y, a.xin = x, a.d = d.minv, a.b = d.R, a.y = z;
-    mm(AMGE_PROF_AG, d.cAG, EPI_SWEEP, a);
+    mm(AMGE_PROF_AG, OP_AG, EPI_SWEEP, a);
     return;
   }
   for (int k = 0; k < h->nu_pre; k++) {
@@ -914,7 +928,7 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
     } else {
       SpmvArgs<V> a;
       a.x = x, a.xin = x, a.d = d.minv, a.b = b, a.y = xt;
-      mm(clsA, d.cA, EPI_SWEEP, a);
+      mm(clsA, OP_A, EPI_SWEEP, a);
       std::swap(x, xt);
       residual();
     }
@@ -926,7 +940,7 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
   {
     SpmvArgs<V> a;
     a.x = c.Z, a.y = x;
-    mm(AMGE_PROF_P, d.cP, EPI_ADD, a);
+    mm(AMGE_PROF_P, OP_P, EPI_ADD, a);
   }
   for (int k = 0; k < h->nu_post; k++) {
     residual();
@@ -934,7 +948,7 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
     const bool last = (k == h->nu_post - 1);
     SpmvArgs<V> a;
     a.x = x, a.xin = x, a.d = d.minv, a.b = b, a.y = last ? z : xt;
-    mm(clsA, d.cA, EPI_SWEEP, a);
+    mm(clsA, OP_A, EPI_SWEEP, a);
     if (!last) std::swap(x, xt);
   }
 }
@@ -1434,6 +1448,65 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
   return AMGE_OK;
 }
 
+// Block kernels for nrhs columns, per operator of every smoothing level: CSR (lane
+// groups per row) against the sliced-ELL forms with one and two 16-byte vectors per
+// lane, each timed as kTuneReps launches replayed from a graph on the level's own
+// block vectors (warm; a level's block vectors and operators are read as a whole);
+// the fastest is kept.  Run once per (precision, nrhs) on the first block call.
+template <typename V>
+amge_status autotune_mm_level(amge_hier* h, int l, int nrhs, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  LevelDev<V>& d = levels<V>(h)[l];
+  LevelDev<V>& c = levels<V>(h)[l + 1];
+  for (int op = 0; op < 6; op++) {
+    if (op == OP_AG && !d.use_ag) continue;
+    const V* in = op == OP_A ? d.X : op == OP_P ? c.Z : op == OP_PT ? d.R : op == OP_G ? d.Y : op == OP_GT ? d.R : d.Y;
+    V* out = op == OP_A ? d.T : op == OP_P ? d.T : op == OP_PT ? c.B : op == OP_G ? d.T : op == OP_GT ? d.Y : d.T;
+    SpmvArgs<V> a;
+    a.x = in, a.y = out;
+    float best = -1.f;
+    int best_code = 0;
+    for (int code = 0; code <= 2; code++) {
+      d.mm_us[op][code] = -1.f;
+      if (code > 0 && !sell_mm_applies<V>(nrhs, code)) continue;
+      d.mmk[op][nrhs] = (int8_t)code;
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      for (int r = 0; r < kTuneReps; r++) opk_mm<V>(h, AMGE_PROF_A_COARSE, d, op, nrhs, EPI_STORE, a, s);
+      CK(cudaStreamEndCapture(s, &g));
+      cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      CK(ie);
+      float ms = 0.f;
+      cudaError_t le = time_graph(ge, s, e0, e1, &ms);
+      cudaGraphExecDestroy(ge);
+      CK(le);
+      d.mm_us[op][code] = ms * (1e3f / kTuneReps);
+      if (best < 0.f || ms < best) best = ms, best_code = code;
+    }
+    d.mmk[op][nrhs] = (int8_t)best_code;
+  }
+  return AMGE_OK;
+}
+
+amge_status tune_mm(amge_hier* h, int nrhs, int precision, cudaStream_t s) {
+  const int p = precision == AMGE_FP64 ? 0 : 1;
+  if (nrhs < 2 || nrhs > kMaxRhs || h->mm_tuned[p][nrhs]) return AMGE_OK;
+  const bool prof = h->prof;
+  h->prof = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  amge_status st = AMGE_OK;
+  for (int l = 0; l + 1 < h->L && st == AMGE_OK; l++)
+    st = p == 0 ? autotune_mm_level<double>(h, l, nrhs, s, e0, e1) : autotune_mm_level<float>(h, l, nrhs, s, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->prof = prof;
+  if (st == AMGE_OK) h->mm_tuned[p][nrhs] = true;
+  return st;
+}
+
 amge_status autotune(amge_hier* h, cudaStream_t s) {
   // candidates are captured into graphs on a stream of our own (the caller's may be
   // the legacy default stream, which cannot be captured)
@@ -1858,6 +1931,7 @@ amge_status amge_vcycle(amge_hier* h, const double* r_dev, double* z_dev, int32_
     vcycle_fp64_iface(h, r_dev, z_dev, precision, as_stream(stream));
   } else {
     amge_status st = ensure_mm(h, nrhs, as_stream(stream));
+    if (st == AMGE_OK) st = tune_mm(h, nrhs, precision, as_stream(stream));
     if (st) return st;
     vcycle_mm_iface(h, nrhs, r_dev, z_dev, precision, as_stream(stream));
   }
@@ -1886,6 +1960,7 @@ amge_status amge_pcg_solve(amge_hier* h, const double* b_dev, double* x_dev, int
     return pcg_one(h, b_dev, x_dev, *opts, info[0], as_stream(stream));
   }
   amge_status st = ensure_mm(h, nrhs, as_stream(stream));
+  if (st == AMGE_OK) st = tune_mm(h, nrhs, opts->precision, as_stream(stream));
   if (st) return st;
   return pcg_mm(h, nrhs, b_dev, x_dev, *opts, info, as_stream(stream));
 }
@@ -2079,6 +2154,47 @@ amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int3
 }
 
 void amge_set_dependent_launch(int32_t enable) { set_dependent_launch(enable != 0); }
+
+amge_status amge_autotune_report_mm(amge_hier* h, int32_t nrhs, int32_t precision, int32_t* codes, float* us) {
+  if (!h || !codes || nrhs < 2 || nrhs > kMaxRhs || (precision != AMGE_FP64 && precision != AMGE_FP32_VCYCLE)) {
+    set_error("NULL argument, nrhs outside [2, 32] or unknown precision");
+    return AMGE_EINVAL;
+  }
+  for (int l = 0; l + 1 < h->L; l++)
+    for (int op = 0; op < 6; op++) {
+      const bool stored = op != OP_AG || h->lv64[l].use_ag;
+      const int code = precision == AMGE_FP64 ? h->lv64[l].mmk[op][nrhs] : h->lv32[l].mmk[op][nrhs];
+      codes[l * 6 + op] = stored ? code : -1;
+      if (us)
+        for (int k = 0; k < 3; k++)
+          us[(l * 6 + op) * 3 + k] = precision == AMGE_FP64 ? h->lv64[l].mm_us[op][k] : h->lv32[l].mm_us[op][k];
+    }
+  return AMGE_OK;
+}
+
+amge_status amge_set_kernel_mm(amge_hier* h, int32_t level, int32_t precision, int32_t op, int32_t nrhs,
+                               int32_t code) {
+  if (!h || level < 0 || level >= h->L - 1 || op < 0 || op > 5 || nrhs < 2 || nrhs > kMaxRhs || code < 0 ||
+      code > 2 || (precision != AMGE_FP64 && precision != AMGE_FP32_VCYCLE)) {
+    set_error("invalid level, op, nrhs, code or precision");
+    return AMGE_EINVAL;
+  }
+  if (op == OP_AG && !h->lv64[level].use_ag) {
+    set_error("A G is not stored on this level");
+    return AMGE_EINVAL;
+  }
+  const bool ok = precision == AMGE_FP64 ? (code == 0 || sell_mm_applies<double>(nrhs, code))
+                                         : (code == 0 || sell_mm_applies<float>(nrhs, code));
+  if (!ok) {
+    set_error("the sliced-ELL block form does not apply to this nrhs");
+    return AMGE_EINVAL;
+  }
+  const int p = precision == AMGE_FP64 ? 0 : 1;
+  if (p == 0) h->lv64[level].mmk[op][nrhs] = (int8_t)code;
+  else h->lv32[level].mmk[op][nrhs] = (int8_t)code;
+  h->mm_tuned[p][nrhs] = true;  // a pinned choice is not re-tuned
+  return AMGE_OK;
+}
 
 amge_status amge_set_graphs(amge_hier* h, int32_t enable) {
   if (!h) {

@@ -170,6 +170,15 @@ struct DevOp {
 constexpr int kMaxRhs = 32;
 template <typename V>
 void launch_csr_mm(const DevCsr<V>& M, int nrhs, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+// The same products on the sliced-ELL layout of the single-vector kernels (see
+// k_sell_mm): ct = 1 or 2 vectors of 16 bytes per lane.  Returns false (and launches
+// nothing) where that form does not apply to nrhs / the vectors' alignment.
+template <typename V>
+bool launch_sell_mm(const DevSell<V>& M, int nrhs, int ct, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+// Whether that form applies to nrhs columns with ct vectors per lane (16-byte aligned
+// vectors assumed, as every workspace block is).
+template <typename V>
+bool sell_mm_applies(int nrhs, int ct);
 // Y[i][c] = d[i] X[i][c]
 template <typename V>
 void launch_mul_mm(int64_t n, int nrhs, const V* d, const V* x, V* y, cudaStream_t s);

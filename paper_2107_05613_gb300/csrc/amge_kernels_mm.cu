@@ -146,6 +146,113 @@ __global__ void __launch_bounds__(kBlock) k_csr_mmv(int nr, int nrhs, int lpr, c
   vst(a.y + e, s);
 }
 
+// Block product on the single-vector sliced-ELL layout.  lpr lanes share a row (lane
+// q owns CT vectors of W columns: columns (q CT + t) W .. + W - 1, t < CT), a warp
+// takes rpw = 32 / lpr consecutive rows of a 32-row slice, and lpr warps cover the
+// slice.  The rpw rows' entry pairs at one step are adjacent in the layout (pair k of
+// slice row t at sptr/2 + 32 k + t), so the warp's index and value loads hit one
+// 8 rpw-byte segment instead of rpw CSR rows' separate lines: on the FP32 block
+// products, bound by the L1 load path, those loads cost as many wavefronts as the
+// gathers of X.  Sign-coded (unit) operators apply the sign to the gathered values.
+template <typename V>
+struct PairMM;
+template <>
+struct PairMM<double> {
+  using T = double2;
+};
+template <>
+struct PairMM<float> {
+  using T = float2;
+};
+
+template <typename V, int CT>
+__device__ __forceinline__ void fma_row(VecU<V> (&s)[CT], V v, const V* xr) {
+#pragma unroll
+  for (int t = 0; t < CT; t++) {
+    const VecU<V> xv = vld(xr + t * VecW<V>::W);
+#pragma unroll
+    for (int k = 0; k < VecW<V>::W; k++) s[t].v[k] = fma(v, xv.v[k], s[t].v[k]);
+  }
+}
+
+template <typename V, int EPI, int CT, bool UNIT>
+__global__ void __launch_bounds__(kBlock) k_sell_mm(int nslices, int nrhs, int lpr, const int64_t* __restrict__ sptr,
+                                                    const int* __restrict__ srow, const int2* __restrict__ ci2,
+                                                    const typename PairMM<V>::T* __restrict__ val2, SpmvArgs<V> a) {
+  pdl_begin();
+  constexpr int W = VecW<V>::W;
+  constexpr bool NEG = (EPI == EPI_RESID || EPI == EPI_SWEEP);
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);  // global warp
+  const int slice = gw / lpr;
+  if (slice >= nslices) return;
+  const int rpw = 32 / lpr;
+  const int t = (gw - slice * lpr) * rpw + lane / lpr;  // row of the slice
+  const int q = lane % lpr;
+  const int row = __ldg(srow + (size_t)slice * 32 + t);
+  if (row < 0) return;
+  const int64_t p0 = __ldg(sptr + slice) >> 1;
+  const int np = (int)((__ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+  const int col0 = q * CT * W;
+  const size_t e = (size_t)row * nrhs + col0;
+  VecU<V> s[CT];
+#pragma unroll
+  for (int u = 0; u < CT; u++) {
+    if (EPI == EPI_RESID || EPI == EPI_SWEEP) s[u] = vld(a.b + e + u * W);
+    else if (EPI == EPI_ADD) s[u] = vld(a.y + e + u * W);
+    else
+#pragma unroll
+      for (int k = 0; k < W; k++) s[u].v[k] = V(0);
+  }
+  const int2* cp = ci2 + p0 + t;
+  const V* xq = a.x + col0;
+  if (UNIT) {
+#pragma unroll 2
+    for (int k = 0; k < np; k++) {
+      const int2 c = __ldg(cp + (size_t)k * 32);
+      if (c.x != kSellPad) fma_row<V, CT>(s, (c.x < 0) != NEG ? V(-1) : V(1), xq + (size_t)(c.x ^ (c.x >> 31)) * nrhs);
+      if (c.y != kSellPad) fma_row<V, CT>(s, (c.y < 0) != NEG ? V(-1) : V(1), xq + (size_t)(c.y ^ (c.y >> 31)) * nrhs);
+    }
+  } else {
+    const typename PairMM<V>::T* vp = val2 + p0 + t;
+#pragma unroll 2
+    for (int k = 0; k < np; k++) {
+      const int2 c = __ldg(cp + (size_t)k * 32);
+      const typename PairMM<V>::T v = __ldg(vp + (size_t)k * 32);
+      fma_row<V, CT>(s, NEG ? -v.x : v.x, xq + (size_t)c.x * nrhs);
+      fma_row<V, CT>(s, NEG ? -v.y : v.y, xq + (size_t)c.y * nrhs);
+    }
+  }
+  if (EPI == EPI_STORE_MUL) {
+    const V d = __ldg(a.d + row);
+#pragma unroll
+    for (int u = 0; u < CT; u++) {
+      vst(a.y + e + u * W, s[u]);
+#pragma unroll
+      for (int k = 0; k < W; k++) s[u].v[k] *= d;
+      vst(a.y2 + e + u * W, s[u]);
+    }
+    return;
+  }
+  if (EPI == EPI_SCALE) {
+    const V d = __ldg(a.d + row);
+#pragma unroll
+    for (int u = 0; u < CT; u++)
+#pragma unroll
+      for (int k = 0; k < W; k++) s[u].v[k] *= d;
+  } else if (EPI == EPI_SWEEP) {
+    const V d = __ldg(a.d + row);
+#pragma unroll
+    for (int u = 0; u < CT; u++) {
+      const VecU<V> xi = vld(a.xin + e + u * W);
+#pragma unroll
+      for (int k = 0; k < W; k++) s[u].v[k] = fma(d, s[u].v[k], xi.v[k]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < CT; u++) vst(a.y + e + u * W, s[u]);
+}
+
 template <typename V>
 __global__ void k_mul_mm(int64_t n, int nrhs, const V* __restrict__ d, const V* __restrict__ x, V* __restrict__ y) {
   pdl_begin();
@@ -425,6 +532,63 @@ void launch_csr_mm(const DevCsr<V>& M, int nrhs, int epi, const SpmvArgs<V>& a, 
 }
 template void launch_csr_mm<double>(const DevCsr<double>&, int, int, const SpmvArgs<double>&, cudaStream_t);
 template void launch_csr_mm<float>(const DevCsr<float>&, int, int, const SpmvArgs<float>&, cudaStream_t);
+
+// Lanes per row of the sliced-ELL block kernel with CT vectors per lane, or 0 where
+// it does not apply (nrhs not a multiple of CT W, more than 8 lanes per row, or
+// vectors not 16-byte aligned).
+template <typename V>
+int sell_mm_lpr(int nrhs, int ct, const SpmvArgs<V>& a) {
+  constexpr int W = VecW<V>::W;
+  if (nrhs % (ct * W) != 0) return 0;
+  const int lpr = nrhs / (ct * W);
+  if (lpr < 1 || lpr > 8 || (lpr & (lpr - 1)) != 0) return 0;
+  if (!(aligned16(a.x) && aligned16(a.y) && aligned16(a.b) && aligned16(a.xin) && aligned16(a.y2))) return 0;
+  return lpr;
+}
+
+template <typename V, int CT, bool UNIT>
+void launch_sell_mm_t(const DevSell<V>& M, int nrhs, int lpr, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  const int warps = M.nslices * lpr;
+  const int grid = (warps + (kBlock / 32) - 1) / (kBlock / 32);
+  const int2* ci2 = reinterpret_cast<const int2*>(M.ci);
+  const auto* v2 = reinterpret_cast<const typename PairMM<V>::T*>(M.val);
+  switch (epi) {
+    case EPI_STORE: launch_k(k_sell_mm<V, EPI_STORE, CT, UNIT>, grid, kBlock, s, M.nslices, nrhs, lpr, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_RESID: launch_k(k_sell_mm<V, EPI_RESID, CT, UNIT>, grid, kBlock, s, M.nslices, nrhs, lpr, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SCALE: launch_k(k_sell_mm<V, EPI_SCALE, CT, UNIT>, grid, kBlock, s, M.nslices, nrhs, lpr, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_ADD: launch_k(k_sell_mm<V, EPI_ADD, CT, UNIT>, grid, kBlock, s, M.nslices, nrhs, lpr, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SWEEP: launch_k(k_sell_mm<V, EPI_SWEEP, CT, UNIT>, grid, kBlock, s, M.nslices, nrhs, lpr, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_STORE_MUL: launch_k(k_sell_mm<V, EPI_STORE_MUL, CT, UNIT>, grid, kBlock, s, M.nslices, nrhs, lpr, M.sptr, M.srow, ci2, v2, a); break;
+  }
+}
+
+template <typename V>
+bool sell_mm_applies(int nrhs, int ct) {
+  constexpr int W = VecW<V>::W;
+  if (ct != 1 && ct != 2) return false;
+  if (nrhs % (ct * W) != 0) return false;
+  const int lpr = nrhs / (ct * W);
+  return lpr >= 1 && lpr <= 8 && (lpr & (lpr - 1)) == 0;
+}
+template bool sell_mm_applies<double>(int, int);
+template bool sell_mm_applies<float>(int, int);
+
+template <typename V>
+bool launch_sell_mm(const DevSell<V>& M, int nrhs, int ct, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  const int lpr = sell_mm_lpr<V>(nrhs, ct, a);
+  if (lpr == 0 || (ct != 1 && ct != 2)) return false;
+  if (M.nslices == 0) return true;
+  if (ct == 2) {
+    if (M.unit) launch_sell_mm_t<V, 2, true>(M, nrhs, lpr, epi, a, s);
+    else launch_sell_mm_t<V, 2, false>(M, nrhs, lpr, epi, a, s);
+  } else {
+    if (M.unit) launch_sell_mm_t<V, 1, true>(M, nrhs, lpr, epi, a, s);
+    else launch_sell_mm_t<V, 1, false>(M, nrhs, lpr, epi, a, s);
+  }
+  return true;
+}
+template bool launch_sell_mm<double>(const DevSell<double>&, int, int, int, const SpmvArgs<double>&, cudaStream_t);
+template bool launch_sell_mm<float>(const DevSell<float>&, int, int, int, const SpmvArgs<float>&, cudaStream_t);
 
 template <typename V>
 void launch_mul_mm(int64_t n, int nrhs, const V* d, const V* x, V* y, cudaStream_t s) {

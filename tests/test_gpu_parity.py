@@ -446,6 +446,81 @@ def test_vcycle_block_matches_oracle_per_column(amge, form, n, L, nrhs):
         assert np.linalg.norm(Zg[:, c] - ref[:, c]) <= tol * np.linalg.norm(ref[:, c]), c
 
 
+def _pin_block_forms(amge, h, nrhs, code):
+    """Pin every stored block product of h to one form for nrhs columns, both
+    precisions (where the sliced-ELL form applies); returns the number pinned."""
+    pinned = 0
+    for prec in (amge.AMGE_FP64, amge.AMGE_FP32_VCYCLE):
+        codes, _ = amge.amge_autotune_report_mm(h, nrhs, prec)
+        for (l, op), c in codes.items():
+            if op == "AG" and amge.amge_autotune_report(h)[(l, "fp64", "AG")] < 0:
+                continue
+            try:
+                amge.amge_set_kernel_mm(h, l, prec, op, nrhs, code)
+                pinned += 1
+            except amge.AmgeError:
+                assert code > 0       # only the sliced-ELL forms can be inapplicable
+    return pinned
+
+
+@pytest.mark.parametrize("form,n,L", [("hcurl", 16, 2), ("hdiv", 24, 3), ("hcurl", 8, 4)])
+@pytest.mark.parametrize("nrhs", [4, 8, 32])
+@pytest.mark.parametrize("code", [0, 1, 2])
+def test_block_kernel_forms_match_oracle(amge, form, n, L, nrhs, code):
+    """Every block product on one form -- CSR lane groups, sliced ELL with one or two
+    16-byte vectors per lane -- through the FP64 block V-cycle, per column against the
+    oracle's V-cycle (the single-vector bound); the FP32 block V-cycle on the
+    constant-coefficient hierarchy within 1e-3 in the energy norm."""
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    for contrast in (True, False):
+        hh = hierarchy(form, n, L, contrast)
+        h = amge.amge_upload_levels(hh)
+        o = oracle_hierarchy(form, n, L, contrast)
+        R = rhs_vector(67, o.A[0].shape[0], nrhs)
+        Z = torch.empty_like(dev(R))
+        amge.amge_vcycle(h, dev(R), Z, nrhs, amge.AMGE_FP64)      # sizes the block workspace
+        assert _pin_block_forms(amge, h, nrhs, code) > 0
+        ref = o.apply(R)
+        if contrast:
+            amge.amge_vcycle(h, dev(R), Z, nrhs, amge.AMGE_FP64)
+            Zg = host(Z)
+            tol = _coarse_tol(o)
+            for c in range(nrhs):
+                assert np.linalg.norm(Zg[:, c] - ref[:, c]) <= tol * np.linalg.norm(ref[:, c]), (c, code)
+        else:
+            amge.amge_vcycle(h, dev(R), Z, nrhs, amge.AMGE_FP32_VCYCLE)
+            Zg = host(Z)
+            A = o.A[0]
+            for c in range(nrhs):
+                d = Zg[:, c] - ref[:, c]
+                err = np.sqrt((d @ (A @ d)) / (ref[:, c] @ (A @ ref[:, c])))
+                assert err <= 1e-3, (c, code, err)
+        h.free()
+
+
+def test_block_autotune_report(amge):
+    """The block tuner runs on the first block call with a column count and reports a
+    choice for every stored operator, with its measured times."""
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = amge.amge_upload_levels(hierarchy("hcurl", 16, 3, True))
+    codes, _ = amge.amge_autotune_report_mm(h, 16, amge.AMGE_FP32_VCYCLE)
+    assert set(codes.values()) == {-1}
+    R = dev(rhs_vector(71, h.n, 16))
+    Z = torch.empty_like(R)
+    amge.amge_vcycle(h, R, Z, 16, amge.AMGE_FP32_VCYCLE)
+    codes, us = amge.amge_autotune_report_mm(h, 16, amge.AMGE_FP32_VCYCLE)
+    for (l, op), c in codes.items():
+        if op == "AG" and c == -1:
+            continue
+        assert c in (0, 1, 2), (l, op)
+        assert us[(l, op)][c] > 0
+    with pytest.raises(amge.AmgeError):             # FP32: 4 floats per vector, 12 is not a multiple of 8
+        amge.amge_set_kernel_mm(h, 0, amge.AMGE_FP32_VCYCLE, "A", 12, 2)
+    h.free()
+
+
 @pytest.mark.parametrize("form,n,L,nrhs", [("hcurl", 16, 2, 4), ("hdiv", 24, 3, 5), ("hcurl", 8, 4, 32)])
 def test_pcg_block_fp64_matches_oracle_per_column(amge, form, n, L, nrhs):
     from oracle import pcg
