@@ -7,8 +7,11 @@ generated hierarchy arrays (paper_2107_05613_gb300.inputs) and nothing else.
 """
 from .amge_oracle import (
     OracleHierarchy,
+    SymmetricGaussSeidel,
+    colour_order,
+    greedy_colours,
     l1_row_sums,
     pcg,
 )
 
-__all__ = ["OracleHierarchy", "l1_row_sums", "pcg"]
+__all__ = ["OracleHierarchy", "SymmetricGaussSeidel", "colour_order", "greedy_colours", "l1_row_sums", "pcg"]

@@ -12,7 +12,13 @@ dense Cholesky factorisation) serve as single steps, with no fusion or reorderin
     derivative G (D_0 for H(curl), D_1 for H(div)), corrected back through G.  The
     transposed step runs the two sweeps in the reverse order.
   * Point smoother: l1-Jacobi, M = diag(sum_j |a_ij|) (the l1-scaled point variant
-    the paper cites in Section 4.1; this build's smoother choice).
+    the paper cites in Section 4.1; this build's default), or the smoother of the
+    paper's runs (Section 5.1): symmetric Gauss-Seidel, two sweeps for the primary
+    and for the auxiliary smoothing, here in a multicolour ordering (rows sorted by
+    the colour of a greedy colouring of the matrix graph, then by index).  The l1
+    term of the paper's l1-scaled block variant adds, to a row's diagonal, its
+    couplings to rows outside the row's processor block; with the whole matrix as
+    one block it is zero, and the smoother is plain symmetric Gauss-Seidel.
   * Coarsest level: dense FP64 Cholesky solve (in place of the paper's AMS/ADS).
   * PCG (Sections 4 and 5.1): preconditioned conjugate gradients with x0 = 0 and
     one V-cycle per iteration; stop on the true FP64 relative residual
@@ -22,11 +28,62 @@ dense Cholesky factorisation) serve as single steps, with no fusion or reorderin
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 
 def l1_row_sums(A) -> np.ndarray:
     """m_i = sum_j |a_ij|: the l1-Jacobi diagonal (Section 4.1 point smoother)."""
     return np.asarray(abs(A).sum(axis=1)).ravel()
+
+
+def greedy_colours(S) -> np.ndarray:
+    """Colour of every row of the symmetric sparsity pattern S: rows in index order,
+    each taking the smallest colour no already-coloured neighbour has."""
+    S = sp.csr_matrix(S)
+    n = S.shape[0]
+    colour = np.full(n, -1, dtype=np.int64)
+    for i in range(n):
+        used = {int(colour[j]) for j in S.indices[S.indptr[i]:S.indptr[i + 1]] if j != i and colour[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        colour[i] = c
+    return colour
+
+
+def colour_order(S) -> np.ndarray:
+    """The multicolour ordering: rows sorted by colour, then by index."""
+    colour = greedy_colours(S)
+    return np.lexsort((np.arange(colour.size), colour))
+
+
+class SymmetricGaussSeidel:
+    """Symmetric Gauss-Seidel for M x = b in a given row ordering: one step is a
+    forward sweep (rows in order, each x_i <- x_i + (b_i - M_i x) / m_ii with the
+    rows before it already updated) then a backward sweep (reverse order).  Written
+    with the ordering's triangular parts: forward x <- x + (D + L)^{-1} (b - M x),
+    backward x <- x + (D + U)^{-1} (b - M x), L / U the couplings to rows earlier /
+    later in the ordering."""
+
+    def __init__(self, M, order):
+        M = sp.csr_matrix(M)
+        self.M = M
+        self.order = np.asarray(order)
+        Mp = M[self.order][:, self.order].tocsr()
+        self.lower = sp.tril(Mp, format="csr")
+        self.upper = sp.triu(Mp, format="csr")
+
+    def _solve(self, T, v, lower):
+        return spla.spsolve_triangular(T, v, lower=lower)
+
+    def step(self, x, b):
+        o = self.order
+        r = (b - self.M @ x)[o]
+        x = x.copy()
+        x[o] += self._solve(self.lower, r, True)           # forward sweep
+        r = (b - self.M @ x)[o]
+        x[o] += self._solve(self.upper, r, False)          # backward sweep
+        return x
 
 
 class OracleHierarchy:
@@ -36,7 +93,8 @@ class OracleHierarchy:
     G[l]: exterior derivative into the problem space at level l (aux transition).
     """
 
-    def __init__(self, A, P, G, nu_pre: int = 1, nu_post: int = 1):
+    def __init__(self, A, P, G, nu_pre: int = 1, nu_post: int = 1, smoother: str = "l1jacobi",
+                 sweeps: int = 2):
         self.A = [sp.csr_matrix(a, dtype=np.float64) for a in A]
         self.P = [sp.csr_matrix(p, dtype=np.float64) for p in P]
         self.G = [sp.csr_matrix(g, dtype=np.float64) for g in G]
@@ -46,6 +104,20 @@ class OracleHierarchy:
         self.m = [l1_row_sums(self.A[l]) for l in range(self.L - 1)]
         self.A_aux = [(self.G[l].T @ self.A[l] @ self.G[l]).tocsr() for l in range(self.L - 1)]
         self.m_aux = [l1_row_sums(self.A_aux[l]) for l in range(self.L - 1)]
+        self.smoother = smoother
+        self.sweeps = sweeps
+        if smoother == "gs":
+            # orderings from the sparsity patterns (the aux pattern symbolic: entries
+            # that cancel numerically still couple)
+            self.gs = []
+            self.gs_aux = []
+            for l in range(self.L - 1):
+                pa = abs(self.A[l])
+                pg = abs(self.G[l])
+                self.gs.append(SymmetricGaussSeidel(self.A[l], colour_order(pa)))
+                self.gs_aux.append(SymmetricGaussSeidel(self.A_aux[l], colour_order((pg.T @ pa @ pg).tocsr())))
+        elif smoother != "l1jacobi":
+            raise ValueError("smoother must be 'l1jacobi' or 'gs'")
         # coarsest level: dense Cholesky factor
         Ac = self.A[-1].toarray()
         self.coarse_factor = sla.cho_factor(Ac, lower=True)
@@ -78,19 +150,31 @@ class OracleHierarchy:
         return cls(mats[:L], mats[L:2 * L - 1], mats[2 * L - 1:], nu_pre, nu_post)
 
     @classmethod
-    def from_hierarchy(cls, h, nu_pre: int = 1, nu_post: int = 1):
+    def from_hierarchy(cls, h, nu_pre: int = 1, nu_post: int = 1, smoother: str = "l1jacobi", sweeps: int = 2):
         return cls([a.to_scipy() for a in h.A], [p.to_scipy() for p in h.P],
-                   [g.to_scipy() for g in h.G], nu_pre, nu_post)
+                   [g.to_scipy() for g in h.G], nu_pre, nu_post, smoother, sweeps)
 
     # ---------------------------------------------------------------- smoothers
     def _point(self, l, x, b):
-        """x <- x + M^{-1} (b - A x), M = l1 diagonal (symmetric, so M^{-T} = M^{-1})."""
+        """x <- x + M^{-1} (b - A x).  l1-Jacobi: M = l1 diagonal (symmetric, so
+        M^{-T} = M^{-1}); Gauss-Seidel: `sweeps` symmetric steps (symmetric as well)."""
+        if self.smoother == "gs":
+            for _ in range(self.sweeps):
+                x = self.gs[l].step(x, b)
+            return x
         return x + _div(b - self.A[l] @ x, self.m[l])
 
     def _aux(self, l, x, b):
-        """x <- x + G M_aux^{-1} G^T (b - A x) (second line of eq. 4.1)."""
+        """x <- x + G M_aux^{-1} G^T (b - A x) (second line of eq. 4.1); with
+        Gauss-Seidel, M_aux^{-1} t is `sweeps` symmetric steps on A_aux y = t from y = 0."""
         G = self.G[l]
-        return x + G @ _div(G.T @ (b - self.A[l] @ x), self.m_aux[l])
+        t = G.T @ (b - self.A[l] @ x)
+        if self.smoother == "gs":
+            y = np.zeros_like(t)
+            for _ in range(self.sweeps):
+                y = self.gs_aux[l].step(y, t)
+            return x + G @ y
+        return x + G @ _div(t, self.m_aux[l])
 
     def hybrid(self, l, x, b):
         """One step of eq. 4.1: point sweep on A_l, then the auxiliary sweep."""
