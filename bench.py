@@ -63,6 +63,9 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="hcurl64")
     p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    p.add_argument("--smoother", choices=["l1jacobi", "gs"], default="l1jacobi",
+                   help="hybrid smoother: l1-Jacobi (default) or two symmetric Gauss-Seidel steps (FP64 only)")
+    p.add_argument("--gs-levels", type=int, default=64, help="finest smoothing levels that use Gauss-Seidel")
     p.add_argument("--no-subresults", action="store_true",
                    help="skip the H(div) 64^3 and 48^3 x 32 right-hand-side sub-results")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -495,6 +498,8 @@ def run_ours(args, dist):
     if args.no_dependent_launch:
         amge.amge_set_dependent_launch(False)
     h = amge.amge_upload_levels(hh)
+    if args.smoother == "gs":
+        amge.amge_set_smoother(h, amge.AMGE_SMOOTHER_SYM_GS, 2, args.gs_levels)
     if args.kernels_from:
         with open(args.kernels_from) as f:
             chosen = json.loads(f.read().strip().splitlines()[-1])["autotune"]
@@ -567,6 +572,7 @@ def run_ours(args, dist):
         "data": "synthetic",
         "config": workload_config(wl, hh),
         "precision": args.precision,
+        "smoother": args.smoother if args.smoother == "l1jacobi" else f"gs x2, {args.gs_levels} finest levels",
         "device_bytes": amge.amge_hier_info(h)[2],
         "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU",
         "iters": iters[0], "true_relres": relres,
@@ -628,12 +634,13 @@ def run_ours(args, dist):
         dist.done()
         return
 
-    # the other precision, for the FP32-vs-FP64 comparison
-    other = amge.AMGE_FP64 if fp32 else amge.AMGE_FP32_VCYCLE
-    timed_solves(amge, h, bd, x, other, 1, nrhs, maxit=300)
-    k2 = max(2, args.steps // 2)
-    ms2, res2 = timed_solves(amge, h, bd, x, other, k2, nrhs, maxit=300)
-    line["fp64" if fp32 else "fp32"] = mode_result(amge, dist.max(ms2, "cuda"), res2, k2, nrhs, dist.world)
+    # the other precision, for the FP32-vs-FP64 comparison (Gauss-Seidel runs FP64 only)
+    if args.smoother == "l1jacobi":
+        other = amge.AMGE_FP64 if fp32 else amge.AMGE_FP32_VCYCLE
+        timed_solves(amge, h, bd, x, other, 1, nrhs, maxit=300)
+        k2 = max(2, args.steps // 2)
+        ms2, res2 = timed_solves(amge, h, bd, x, other, k2, nrhs, maxit=300)
+        line["fp64" if fp32 else "fp32"] = mode_result(amge, dist.max(ms2, "cuda"), res2, k2, nrhs, dist.world)
 
     # end to end through the C ABI with host buffers (H2D of b and D2H of x every step)
     if not args.no_e2e:
@@ -651,7 +658,7 @@ def run_ours(args, dist):
     del bd, x
     torch.cuda.empty_cache()
 
-    if dist.world == 1 and not args.no_subresults and args.workload == "hcurl64":
+    if dist.world == 1 and not args.no_subresults and args.workload == "hcurl64" and args.smoother == "l1jacobi":
         line["hdiv64"] = sub_result(amge, "hdiv64", 5)
         line["hcurl48x32"] = sub_result(amge, "hcurl48x32", 5)
     if not args.no_serving and dist.world == 1:
