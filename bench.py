@@ -589,6 +589,10 @@ def run_ours(args, dist):
     line["kernel_timing"] = ("CUDA events around every launch, on the launching stream, over a second pass of the "
                              "same K steps right after the headline timed region")
     line["gpu_launches"] = int(sum(c for c, _ in launches.values()))
+    if nrhs > 1:  # the block products' tuned forms: 0 CSR, 1 / 2 sliced ELL (1 / 2 vectors per lane)
+        codes, us = amge.amge_autotune_report_mm(h, nrhs, prec)
+        line["autotune_mm"] = {f"L{l}.{o}": {"code": c, "us": [round(t, 2) for t in us[(l, o)]]}
+                               for (l, o), c in codes.items() if c >= 0}
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs") if peaks else None
     peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s (of fallback)"

@@ -266,6 +266,28 @@ amge_status amge_apply(amge_hier* h, int32_t op, int32_t level, const double* x_
 amge_status amge_dot(amge_hier* h, const double* x_dev, const double* y_dev, int64_t n, double* result_dev,
                      void* stream);
 
+/* Hybrid-smoother choice (eq. 4.1 with either point smoother; Section 4.1):
+ *   AMGE_SMOOTHER_L1_JACOBI  the default: one l1-Jacobi sweep, m_i = sum_j |a_ij|,
+ *                            for the primary and for the auxiliary smoothing
+ *   AMGE_SMOOTHER_SYM_GS     the smoother of the paper's runs (Section 5.1): `sweeps`
+ *                            symmetric Gauss-Seidel steps (a forward then a backward
+ *                            pass) for the primary and for the auxiliary smoothing,
+ *                            on the gs_levels finest smoothing levels (l1-Jacobi on the
+ *                            coarser ones); rows are visited in a multicolour order --
+ *                            a greedy colouring of the pattern of A_l (of the symbolic
+ *                            pattern of G^T A_l G for the aux matrix) in row order,
+ *                            rows sorted by colour, one launch per colour.  The l1 term
+ *                            of the paper's l1-scaled block variant couples a row to
+ *                            rows outside its processor block and vanishes on one GPU.
+ * The first selection of Gauss-Seidel on a level builds its data (a host pass over the
+ * level's operators, the explicit G^T A_l G, device allocation) and synchronises; it
+ * is kept for later selections.  Gauss-Seidel V-cycles run in FP64 on single vectors:
+ * AMGE_FP32_VCYCLE solves and blocks of right-hand sides then fail with AMGE_EINVAL.
+ * Errors: AMGE_EINVAL for an unknown smoother, sweeps outside [1, 8], gs_levels < 0,
+ * or a workspace view; AMGE_ENOMEM, AMGE_ECUDA. */
+enum { AMGE_SMOOTHER_L1_JACOBI = 0, AMGE_SMOOTHER_SYM_GS = 1 };
+amge_status amge_set_smoother(amge_hier* h, int32_t smoother, int32_t sweeps, int32_t gs_levels);
+
 /* Per-kernel launch counts and timing.  Every kernel launch of the solve path is
  * counted per kernel class; while timing is enabled each launch is also bracketed
  * by CUDA events on its stream.  amge_profile_read synchronises, and returns for
@@ -285,7 +307,8 @@ enum {
   AMGE_PROF_VCYCLE_VEC = 9, /* V-cycle elementwise products (x = m^-1 b on entry to a level) */
   AMGE_PROF_AG = 10,        /* residual updates r -= (A G) y after an aux sweep (H(curl)) */
   AMGE_PROF_A_WIDE = 11,    /* FP32 V-cycle, level 0: products on the FP64 operator (AMGE_OP_A_WIDE) */
-  AMGE_PROF_CLASSES = 12
+  AMGE_PROF_GS = 12,        /* Gauss-Seidel colour sweeps (amge_set_smoother) */
+  AMGE_PROF_CLASSES = 13
 };
 amge_status amge_profile_enable(amge_hier* h, int32_t enable);
 amge_status amge_profile_read(amge_hier* h, int64_t* count, double* ms);
@@ -389,6 +412,9 @@ void amge_set_dependent_launch(int32_t enable);
  * lanes[(l * 2 + p) * 6 + op] for level l < levels-1, precision p (0 FP64, 1 FP32),
  * op 0..5 = A, P, P^T, G, G^T, AG; 0 = sliced ELL (one row per lane, one warp per
  * 32-row slice), 100 w (200, 400, 800) = sliced ELL with w warps sharing each slice,
+ * 1000 / 1200 = sliced ELL with one / two warps per slice where each warp first issues
+ * a bulk L2 prefetch of its slice's entries (candidates only for streamed operators,
+ * those larger than half of L2; the others always prefetch),
  * 2..32 = vector CSR with that many lanes per row, -1 = operator not used (AG is stored only where
  * A G = A_l G_l is much sparser than A_l, i.e. for H(curl): there the residual after
  * an aux sweep is updated as r - (A G) y instead of recomputed as b - A x).  The
@@ -398,7 +424,7 @@ void amge_set_dependent_launch(int32_t enable);
  * lanes must hold (levels-1)*12 entries. */
 amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
 
-/* The autotuner's evidence: us[((l * 2 + p) * 6 + op) * 9 + c] = measured time per
+/* The autotuner's evidence: us[((l * 2 + p) * 6 + op) * 11 + c] = measured time per
  * launch in microseconds (STORE epilogue, ten launches replayed from a graph).  Where
  * a level's operators and the coarser ones take more than half of L2, so that a
  * V-cycle finds them evicted, each launch follows a read of twice L2's capacity and is
@@ -406,13 +432,15 @@ amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
  * from HBM as it does inside a V-cycle.  Otherwise, and for streamed operators larger
  * than L2, the ten launches run back to back and are timed as a whole (best of
  * three) -- also where the 2x L2 scratch cannot be allocated.  Candidate c in the order 0,
- * 200, 400, 800, 2, 4, 8, 16, 32; -1 where a
- * candidate was not measured (longer than the operator's rows) or the operator is
- * not stored.  us must hold (levels-1)*108 floats. */
+ * 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200; -1 where a candidate was not measured
+ * (more warps than the operator's rows have entry pairs, or a prefetch variant of an
+ * operator that is not streamed) or the operator is not stored.  us must hold
+ * (levels-1)*132 floats. */
 amge_status amge_autotune_times(const amge_hier* h, float* us);
 
 /* Override one entry of that choice (level l < levels-1, precision 0/1, op 0..5 as
- * above; lanes = a kernel code as above: 0, 200, 400, 800 or 2, 4, 8, 16, 32).  Captured PCG graphs
+ * above; lanes = a kernel code as above: 0, 200, 400, 800, 1000, 1200 or 2, 4, 8, 16,
+ * 32; the prefetch codes act as 0 / 200 on operators that are not streamed).  Captured PCG graphs
  * of h are rebuilt on the next solve.  Every kernel computes the same products (in a
  * different summation order), so a choice changes rounding, not results beyond it;
  * pinning the choices makes results reproducible across uploads.  Not to be called

@@ -37,9 +37,11 @@ def l1_row_sums(A) -> np.ndarray:
 
 
 def greedy_colours(S) -> np.ndarray:
-    """Colour of every row of the symmetric sparsity pattern S: rows in index order,
-    each taking the smallest colour no already-coloured neighbour has."""
+    """Colour of every row of the symmetric sparsity pattern S (its nonzero entries):
+    rows in index order, each taking the smallest colour no already-coloured
+    neighbour has."""
     S = sp.csr_matrix(S)
+    S.eliminate_zeros()
     n = S.shape[0]
     colour = np.full(n, -1, dtype=np.int64)
     for i in range(n):
@@ -94,7 +96,7 @@ class OracleHierarchy:
     """
 
     def __init__(self, A, P, G, nu_pre: int = 1, nu_post: int = 1, smoother: str = "l1jacobi",
-                 sweeps: int = 2):
+                 sweeps: int = 2, gs_levels: int = None):
         self.A = [sp.csr_matrix(a, dtype=np.float64) for a in A]
         self.P = [sp.csr_matrix(p, dtype=np.float64) for p in P]
         self.G = [sp.csr_matrix(g, dtype=np.float64) for g in G]
@@ -106,12 +108,15 @@ class OracleHierarchy:
         self.m_aux = [l1_row_sums(self.A_aux[l]) for l in range(self.L - 1)]
         self.smoother = smoother
         self.sweeps = sweeps
+        # Gauss-Seidel on the gs_levels finest smoothing levels (all by default),
+        # l1-Jacobi on the coarser ones
+        self.gs_levels = (self.L - 1) if gs_levels is None else min(gs_levels, self.L - 1)
         if smoother == "gs":
             # orderings from the sparsity patterns (the aux pattern symbolic: entries
             # that cancel numerically still couple)
             self.gs = []
             self.gs_aux = []
-            for l in range(self.L - 1):
+            for l in range(self.gs_levels):
                 pa = abs(self.A[l])
                 pg = abs(self.G[l])
                 self.gs.append(SymmetricGaussSeidel(self.A[l], colour_order(pa)))
@@ -150,15 +155,16 @@ class OracleHierarchy:
         return cls(mats[:L], mats[L:2 * L - 1], mats[2 * L - 1:], nu_pre, nu_post)
 
     @classmethod
-    def from_hierarchy(cls, h, nu_pre: int = 1, nu_post: int = 1, smoother: str = "l1jacobi", sweeps: int = 2):
+    def from_hierarchy(cls, h, nu_pre: int = 1, nu_post: int = 1, smoother: str = "l1jacobi", sweeps: int = 2,
+                       gs_levels: int = None):
         return cls([a.to_scipy() for a in h.A], [p.to_scipy() for p in h.P],
-                   [g.to_scipy() for g in h.G], nu_pre, nu_post, smoother, sweeps)
+                   [g.to_scipy() for g in h.G], nu_pre, nu_post, smoother, sweeps, gs_levels)
 
     # ---------------------------------------------------------------- smoothers
     def _point(self, l, x, b):
         """x <- x + M^{-1} (b - A x).  l1-Jacobi: M = l1 diagonal (symmetric, so
         M^{-T} = M^{-1}); Gauss-Seidel: `sweeps` symmetric steps (symmetric as well)."""
-        if self.smoother == "gs":
+        if self.smoother == "gs" and l < self.gs_levels:
             for _ in range(self.sweeps):
                 x = self.gs[l].step(x, b)
             return x
@@ -169,7 +175,7 @@ class OracleHierarchy:
         Gauss-Seidel, M_aux^{-1} t is `sweeps` symmetric steps on A_aux y = t from y = 0."""
         G = self.G[l]
         t = G.T @ (b - self.A[l] @ x)
-        if self.smoother == "gs":
+        if self.smoother == "gs" and l < self.gs_levels:
             y = np.zeros_like(t)
             for _ in range(self.sweeps):
                 y = self.gs_aux[l].step(y, t)

@@ -25,7 +25,8 @@ AMGE_HCURL, AMGE_HDIV = 2, 3
 AMGE_FP64, AMGE_FP32_VCYCLE = 0, 1
 AMGE_OP_A, AMGE_OP_P, AMGE_OP_PT, AMGE_OP_G, AMGE_OP_GT, AMGE_OP_SMOOTH_PRE, AMGE_OP_COARSE, AMGE_OP_AG, AMGE_OP_A_WIDE = range(9)
 PROF_CLASSES = ["A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "pcg_spmv", "pcg_vec", "vcycle_vec", "AG",
-                "A_wide"]
+                "A_wide", "gs"]
+AMGE_SMOOTHER_L1_JACOBI, AMGE_SMOOTHER_SYM_GS = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENONFINITE",
                 6: "EAGAIN", 7: "ETIMEOUT", 8: "ECANCELED"}
 
@@ -85,6 +86,7 @@ _SIGS = {
     "amge_fp64_fma_rate": [ctypes.POINTER(ctypes.c_double), _vp],
     "amge_autotune_report_mm": [_vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)],
     "amge_set_kernel_mm": [_vp, _i32, _i32, _i32, _i32, _i32],
+    "amge_set_smoother": [_vp, _i32, _i32, _i32],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -281,19 +283,19 @@ def amge_autotune_report(h: Hier):
 
 
 OPS = ["A", "P", "PT", "G", "GT", "AG"]
-TUNE_CODES = [0, 200, 400, 800, 2, 4, 8, 16, 32]
+TUNE_CODES = [0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200]
 
 
 def amge_autotune_times(h: Hier):
     """{(level, 'fp64'|'fp32', op): {code: us per launch}} as measured at upload."""
     L = h.levels
-    buf = (ctypes.c_float * max((L - 1) * 108, 1))()
+    buf = (ctypes.c_float * max((L - 1) * 132, 1))()
     _check(_lib.amge_autotune_times(h.handle, buf), "amge_autotune_times")
     out = {}
     for l in range(L - 1):
         for pi, p in enumerate(("fp64", "fp32")):
             for o in range(6):
-                t = {c: round(float(buf[((l * 2 + pi) * 6 + o) * 9 + k]), 2) for k, c in enumerate(TUNE_CODES)}
+                t = {c: round(float(buf[((l * 2 + pi) * 6 + o) * 11 + k]), 2) for k, c in enumerate(TUNE_CODES)}
                 if any(v >= 0 for v in t.values()):
                     out[(l, p, OPS[o])] = {c: v for c, v in t.items() if v >= 0}
     return out
@@ -446,3 +448,9 @@ def amge_autotune_report_mm(h: Hier, nrhs: int, precision: int = AMGE_FP32_VCYCL
 def amge_set_kernel_mm(h: Hier, level: int, precision: int, op, nrhs: int, code: int):
     o = _OPS.index(op) if isinstance(op, str) else op
     _check(_lib.amge_set_kernel_mm(h.handle, level, precision, o, nrhs, code), "amge_set_kernel_mm")
+
+
+def amge_set_smoother(h: Hier, smoother: int, sweeps: int = 2, gs_levels: int = 64):
+    """AMGE_SMOOTHER_L1_JACOBI, or AMGE_SMOOTHER_SYM_GS (`sweeps` symmetric Gauss-Seidel
+    steps per smoothing) on the gs_levels finest smoothing levels."""
+    _check(_lib.amge_set_smoother(h.handle, smoother, sweeps, gs_levels), "amge_set_smoother")

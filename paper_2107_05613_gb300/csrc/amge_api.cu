@@ -15,6 +15,8 @@ namespace amge {
 thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+constexpr int kNumTuneCodes = 11;  // candidates of the single-vector autotuner (kTuneCodes)
+
 template <typename V>
 struct LevelDev {
   int n = 0, naux = 0;
@@ -34,11 +36,17 @@ struct LevelDev {
   int lanes[6] = {0, 0, 0, 0, 0, -1};
   // the autotuner's measured time per launch (us) of each candidate (kTuneCodes
   // order), -1 where not measured
-  float tune_us[6][9] = {};
+  float tune_us[6][kNumTuneCodes] = {};
   // block (multi-right-hand-side) kernel per operator and column count: -1 = not
   // tuned yet, 0 = CSR, 1 / 2 = sliced ELL with 1 / 2 vectors of 16 bytes per lane
   int8_t mmk[6][kMaxRhs + 1];
   float mm_us[6][3] = {};  // the block tuner's time per launch (us) of each form, last tuned nrhs
+  // Gauss-Seidel smoother (amge_set_smoother; FP64): A_l and A_aux = G^T A_l G with
+  // rows grouped by colour (colour k: slices [cs[k], cs[k+1])), 1 / diagonal
+  DevSell<V> gsA, gsX;
+  std::vector<int> gsA_cs, gsX_cs;
+  V *gsA_dinv = nullptr, *gsX_dinv = nullptr;
+  V* t = nullptr;  // aux right-hand side G^T r of the Gauss-Seidel aux smoothing
   V* minv = nullptr;
   V* mauxinv = nullptr;
   V *x = nullptr, *r = nullptr, *y = nullptr, *tmp = nullptr;
@@ -70,6 +78,9 @@ struct GraphPcg {
 
 struct amge_hier {
   int form = 0, L = 0, nu_pre = 1, nu_post = 1;
+  // smoother: AMGE_SMOOTHER_L1_JACOBI, or AMGE_SMOOTHER_SYM_GS on the gs_levels finest
+  // smoothing levels (sweeps symmetric steps per smoothing; l1-Jacobi below them)
+  int smoother = AMGE_SMOOTHER_L1_JACOBI, sweeps = 2, gs_levels = 0, gs_built = 0;
   int n0 = 0;
   int device = -1;  // CUDA device the operators live on (current at upload)
   std::vector<LevelDev<double>> lv64;
@@ -86,6 +97,10 @@ struct amge_hier {
   RedScratchMM redmm;
   int mm_cap = 0;  // nrhs the block workspace was sized for
   bool mm_tuned[2][kMaxRhs + 1] = {};  // block kernels timed for (precision, nrhs)
+  GraphPcg gmm[2][kMaxRhs + 1];        // captured block PCG loops per (precision, nrhs)
+  int* gstate_mm = nullptr;            // device: iterations done, maxit, non-finite flag
+  int* pinned_state_mm = nullptr;
+  double* GX = nullptr;                // block iterate of the graph-driven loop
   double *PR = nullptr, *PZ = nullptr, *PP = nullptr, *PQ = nullptr, *SB = nullptr, *SX = nullptr;
   float *S32in = nullptr, *S32out = nullptr;
   double* CT = nullptr;
@@ -286,8 +301,8 @@ const DevCsr<V>& op_csr(const LevelDev<V>& d, int op) {
 template <typename V>
 void opk(amge_hier* h, int cls, const LevelDev<V>& d, int op, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
   Prof p(h, cls, s);
-  const int code = d.lanes[op];  // 0 / 100 w: sliced ELL (w warps per slice); 2..32: vector CSR lanes
-  if (code == 0 || code >= 100) launch_sell<V>(op_sell(d, op), epi, a, s, code >= 100 ? code / 100 : 1);
+  const int code = d.lanes[op];  // sliced ELL (code_wps warps per slice, code_pf) or vector CSR lanes
+  if (code_is_sell(code)) launch_sell<V>(op_sell(d, op), epi, a, s, code_wps(code), code_pf(code));
   else launch_csrv<V>(op_csr(d, op), code, epi, a, s);
 }
 
@@ -296,7 +311,7 @@ void opk(amge_hier* h, int cls, const LevelDev<V>& d, int op, int epi, const Spm
 // work), else four.
 int wide_wps(const amge_hier* h, int l) {
   const int code = h->lv64[l].lanes[OP_A];
-  return code >= 100 ? code / 100 : (code == 0 ? 1 : 4);
+  return code_is_sell(code) ? code_wps(code) : 4;
 }
 
 // A product with A_l in a residual form (EPI_RESID / EPI_SWEEP).  `corrected`: the
@@ -317,23 +332,118 @@ void a_product(amge_hier* h, int l, const LevelDev<V>& d, bool corrected, int ep
   if constexpr (std::is_same<V, float>::value) {
     if (corrected) {
       Prof p(h, l == 0 ? AMGE_PROF_A_WIDE : AMGE_PROF_A_COARSE, s);
-      launch_sell_wide(h->lv64[l].A, epi, a, s, wide_wps(h, l));
+      launch_sell_wide(h->lv64[l].A, epi, a, s, wide_wps(h, l), code_pf(h->lv64[l].lanes[OP_A]));
       return;
     }
   }
   opk<V>(h, clsA, d, OP_A, epi, a, s);
 }
 
+template <typename V>
+void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_ready);
+
+bool gs_level(const amge_hier* h, int l) {
+  return h->smoother == AMGE_SMOOTHER_SYM_GS && l < h->gs_levels && l + 1 < h->L;
+}
+
+// Gauss-Seidel V-cycles run in FP64 on single vectors.
+bool gs_refuses(const amge_hier* h, int precision, int nrhs) {
+  if (!gs_level(h, 0) || (precision == AMGE_FP64 && nrhs == 1)) return false;
+  set_error("the Gauss-Seidel smoother runs FP64 V-cycles on single vectors");
+  return true;
+}
+
+// One V-cycle at level l with the Gauss-Seidel hybrid smoother (FP64; Algorithm 4.1
+// with eq. 4.1, the smoother of the paper's runs, Section 5.1): the iterate is z
+// itself, from zero.  Primary smoothing: `sweeps` symmetric steps on A_l z = b, each
+// a forward pass over the colours and a backward one; aux smoothing: t = G^T (b - A z),
+// `sweeps` symmetric steps on A_aux y = t from y = 0, z += G y.  Pre-smoothing runs
+// primary then aux, post-smoothing aux then primary (the transposed step; every
+// factor is symmetric).
+void vcycle_level_gs(amge_hier* h, int l, const double* b, double* z, cudaStream_t s) {
+  LevelDev<double>& d = h->lv64[l];
+  LevelDev<double>& c = h->lv64[l + 1];
+  const int code = d.lanes[OP_A];
+  const int wps = code_is_sell(code) ? code_wps(code) : 1;
+  auto sweeps = [&](const DevSell<double>& M, const std::vector<int>& cs, const double* dinv, const double* rhs,
+                    double* v, int w) {
+    const int C = (int)cs.size() - 1;
+    for (int t = 0; t < h->sweeps; t++) {
+      for (int k = 0; k < C; k++) {
+        Prof p(h, AMGE_PROF_GS, s);
+        launch_gs_colour(M, cs[k], cs[k + 1], dinv, rhs, v, s, w);
+      }
+      for (int k = C - 1; k >= 0; k--) {
+        Prof p(h, AMGE_PROF_GS, s);
+        launch_gs_colour(M, cs[k], cs[k + 1], dinv, rhs, v, s, w);
+      }
+    }
+  };
+  auto residual = [&]() {
+    SpmvArgs<double> a;
+    a.x = z, a.b = b, a.y = d.r;
+    opk<double>(h, l == 0 ? AMGE_PROF_A_FINE : AMGE_PROF_A_COARSE, d, OP_A, EPI_RESID, a, s);
+  };
+  auto primary = [&]() { sweeps(d.gsA, d.gsA_cs, d.gsA_dinv, b, z, wps); };
+  auto aux = [&]() {
+    residual();
+    SpmvArgs<double> g;
+    g.x = d.r, g.y = d.t;
+    opk<double>(h, AMGE_PROF_GT, d, OP_GT, EPI_STORE, g, s);
+    {
+      Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
+      launch_zero<double>(d.naux, d.y, s);
+    }
+    sweeps(d.gsX, d.gsX_cs, d.gsX_dinv, d.t, d.y, 1);
+    SpmvArgs<double> a;
+    a.x = d.y, a.y = z;
+    opk<double>(h, AMGE_PROF_G, d, OP_G, EPI_ADD, a, s);
+  };
+  {
+    Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
+    launch_zero<double>(d.n, z, s);
+  }
+  for (int k = 0; k < h->nu_pre; k++) {
+    primary();
+    aux();
+  }
+  residual();
+  // restriction; a next level smoothed by l1-Jacobi starts its sweep from it
+  const bool c_jac = l + 2 < h->L && !gs_level(h, l + 1);
+  {
+    SpmvArgs<double> a;
+    a.x = d.r, a.y = c.b;
+    if (c_jac) a.d = c.minv, a.y2 = c.x;
+    opk<double>(h, AMGE_PROF_PT, d, OP_PT, c_jac ? EPI_STORE_MUL : EPI_STORE, a, s);
+  }
+  vcycle_level<double>(h, l + 1, c.b, c.z, s, c_jac);
+  {
+    SpmvArgs<double> a;
+    a.x = c.z, a.y = z;
+    opk<double>(h, AMGE_PROF_P, d, OP_P, EPI_ADD, a, s);
+  }
+  for (int k = 0; k < h->nu_post; k++) {
+    aux();
+    primary();
+  }
+}
+
 // One V-cycle at level l: z = B_l^{-1} b (Algorithm 4.1, x0 = 0).  x_ready: the
 // level's first point sweep from zero, x = m^-1 b, was already written into x by the
 // restriction that produced b.
 template <typename V>
-void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_ready = false) {
+void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_ready) {
   auto& lv = levels<V>(h);
   if (l == h->L - 1) {
     Prof p(h, AMGE_PROF_COARSE, s, std::is_same<V, float>::value ? 2 : 1);  // FP32: + the widening
     launch_coarse_inv<V, V>(h->nC, h->Ainv, b, h->ct, z, s);
     return;
+  }
+  if constexpr (std::is_same<V, double>::value) {
+    if (gs_level(h, l)) {
+      vcycle_level_gs(h, l, b, z, s);
+      return;
+    }
   }
   LevelDev<V>& d = lv[l];
   V* x = d.x;
@@ -370,15 +480,16 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
     // G y and (A G) y in one pass where G is the two-entry gradient and both
     // products run sliced-ELL kernels (identical results to the separate products)
     const int ag = d.lanes[OP_AG];
-    const bool fused = d.g2 && (ag == 0 || ag >= 100) && d.lanes[OP_G] == 0;
-    const int ag_wps = ag >= 100 ? ag / 100 : 1;
+    const bool fused = d.g2 && code_is_sell(ag) && d.lanes[OP_G] == 0;
+    const int ag_wps = code_wps(ag);
+    const bool ag_pf = code_pf(ag);
     residual(false);
     if (fused) {
       aux_gt();
       Prof p(h, AMGE_PROF_AG, s);
       AgArgs<V> f;  // x += G y; r -= (A G) y
       f.y = d.y, f.g2 = d.g2, f.x = x, f.r = d.r;
-      launch_ag_fused<V>(d.AG, 0, f, s, ag_wps);
+      launch_ag_fused<V>(d.AG, 0, f, s, ag_wps, ag_pf);
     } else {
       aux_sweep();
       SpmvArgs<V> a;  // r = r - (A G) y (in place: row i reads and writes r_i only)
@@ -398,7 +509,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
       Prof p(h, AMGE_PROF_AG, s);
       AgArgs<V> f;  // z = x + G y + M^{-1} (r - (A G) y)
       f.y = d.y, f.g2 = d.g2, f.x = x, f.r = d.r, f.minv = d.minv, f.z = z;
-      launch_ag_fused<V>(d.AG, 1, f, s, ag_wps);
+      launch_ag_fused<V>(d.AG, 1, f, s, ag_wps, ag_pf);
       return;
     }
     aux_sweep();
@@ -456,7 +567,7 @@ void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, 
       launch_coarse_inv<double, double>(h->nC, h->Ainv, r, h->ct, z, s);
       return;
     }
-    vcycle_level<double>(h, 0, r, z, s, x0_ready);
+    vcycle_level<double>(h, 0, r, z, s, x0_ready && !gs_level(h, 0));
   } else {
     LevelDev<float>& d = h->lv32[0];
     if (!x0_ready) {
@@ -478,7 +589,7 @@ void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, 
 // a one-level hierarchy.
 X0Out pcg_x0_out(amge_hier* h, int precision) {
   X0Out o;
-  if (h->L == 1) return o;
+  if (h->L == 1 || gs_level(h, 0)) return o;  // Gauss-Seidel starts the level from zero itself
   if (precision == AMGE_FP64) {
     o.mode = 1;
     o.minv64 = h->lv64[0].minv;
@@ -494,7 +605,7 @@ X0Out pcg_x0_out(amge_hier* h, int precision) {
 
 // The same start computed from r alone (after the true residual replaced r).
 void pcg_x0_from_r(amge_hier* h, const double* r, int precision, cudaStream_t s) {
-  if (h->L == 1) return;
+  if (h->L == 1 || gs_level(h, 0)) return;
   Prof p(h, AMGE_PROF_VCYCLE_VEC, s, precision == AMGE_FP64 ? 1 : 2);
   if (precision == AMGE_FP64) {
     launch_mul<double>(h->n0, h->lv64[0].minv, r, h->lv64[0].x, s);
@@ -717,6 +828,7 @@ amge_status run_step(PcgRun& r) {
 amge_status amge::pcg_run_start(amge_hier* h, const double* b, double* x, const amge_solve_opts& o,
                                 cudaStream_t s, PcgRun** out) {
   *out = nullptr;
+  if (gs_refuses(h, o.precision, 1)) return AMGE_EINVAL;
   if (!h->gpcg[o.precision].built) {
     amge_status st = build_pcg_graph(h, o.precision);
     if (st) return st;
@@ -834,9 +946,12 @@ amge_status amge::ensure_mm(amge_hier* h, int nrhs, cudaStream_t s, int cap) {
     h->redmm.counters = dalloc<unsigned>(h, kRedSlots);
     h->redmm.sc = dalloc<double>(h, (size_t)SC_COUNT * kMaxRhs);
     h->redmm.active = dalloc<int>(h, kMaxRhs);
+    h->GX = dalloc<double>(h, n0);
+    h->gstate_mm = dalloc<int>(h, 4);
   } catch (const UploadError& e) {
     return e.st;
   }
+  CK(cudaMallocHost(&h->pinned_state_mm, 4 * sizeof(int)));
   CK(cudaMemsetAsync(h->redmm.counters, 0, kRedSlots * sizeof(unsigned), s));
   CK(cudaMemsetAsync(h->redmm.sc, 0, SC_COUNT * kMaxRhs * sizeof(double), s));
   CK(cudaMallocHost(&h->pinned_mm, (SC_COUNT * kMaxRhs + kMaxRhs) * sizeof(double)));
@@ -996,6 +1111,11 @@ struct PcgRunMM {
   Phase phase = M_BB;
   int it = 0, nact = 0, flexible = 0;
   bool f32 = false, x0_ready = false, spec = true;
+  // graph: iterations after the first run in the captured WHILE loop (in_graph: one is
+  // in flight); xw is the iterate the kernels update (the loop's own block, GX, copied
+  // to x at the end, or x itself)
+  bool graph = false, in_graph = false;
+  double* xw = nullptr;
   X0Out x0;  // the axpy also starts the next block V-cycle (not for a one-level hierarchy)
   std::vector<double> bb, rr, rt, rr_prev, rr_prev2, tol2;
   std::vector<int> active, iters, status;
@@ -1030,9 +1150,24 @@ void mm_resid_true(PcgRunMM& r) {  // PR = b - A x and ||PR||^2 -> SC_DOT
   amge_hier* h = r.h;
   Prof p(h, AMGE_PROF_PCG_SPMV, r.s);
   SpmvArgs<double> a;
-  a.x = r.x, a.b = r.b, a.y = h->PR;
+  a.x = r.xw, a.b = r.b, a.y = h->PR;
   launch_csr_mm<double>(h->cA0, r.nrhs, EPI_RESID, a, r.s);
   launch_dot_mm(h->n0, r.nrhs, h->PR, h->PR, SC_DOT, h->redmm, r.s);
+}
+
+// The level-0 sweep from zero of the next block V-cycle, from PR (after the true
+// residual replaced it): the same operations vcycle_mm_iface runs when not x0_ready.
+void mm_x0_from_r(PcgRunMM& r) {
+  amge_hier* h = r.h;
+  if (r.x0.mode == 0) return;
+  Prof p(h, AMGE_PROF_VCYCLE_VEC, r.s, r.f32 ? 2 : 1);
+  if (r.f32) {
+    launch_cast<double, float>((int64_t)h->n0 * r.nrhs, h->PR, h->lv32[0].B, r.s);
+    launch_mul_mm<float>(h->n0, r.nrhs, h->lv32[0].minv, h->lv32[0].B, h->lv32[0].X, r.s);
+  } else {
+    launch_mul_mm<double>(h->n0, r.nrhs, h->lv64[0].minv, h->PR, h->lv64[0].X, r.s);
+  }
+  r.x0_ready = true;
 }
 
 void mm_precondition(PcgRunMM& r) {  // Z = B R, then the dots
@@ -1045,6 +1180,8 @@ void mm_precondition(PcgRunMM& r) {  // Z = B R, then the dots
 
 amge_status mm_final(PcgRunMM& r) {
   mm_resid_true(r);
+  if (r.xw != r.x)
+    CK(cudaMemcpyAsync(r.x, r.xw, (size_t)r.h->n0 * r.nrhs * sizeof(double), cudaMemcpyDeviceToDevice, r.s));
   amge_status st = mm_copy_cols(r, SC_DOT);
   if (st) return st;
   r.phase = PcgRunMM::M_FINAL;
@@ -1060,7 +1197,7 @@ amge_status mm_iterate(PcgRunMM& r) {
   }
   {
     Prof p(h, AMGE_PROF_PCG_VEC, r.s);
-    launch_pcg_mm_axpy_norm(h->n0, r.nrhs, r.x, h->PR, h->PP, h->PQ, h->redmm, r.s, r.x0);
+    launch_pcg_mm_axpy_norm(h->n0, r.nrhs, r.xw, h->PR, h->PP, h->PQ, h->redmm, r.s, r.x0);
     r.x0_ready = r.x0.mode != 0;
   }
   amge_status st = mm_copy_cols(r, SC_RR);
@@ -1068,7 +1205,7 @@ amge_status mm_iterate(PcgRunMM& r) {
   st = mm_record(r);
   if (st) return st;
   r.it++;
-  r.spec = true;
+  r.spec = !r.graph;
   for (int c = 0; c < r.nrhs; c++)
     if (r.active[c] && r.rr_prev[c] > 0 && r.rr_prev2[c] > 0 &&
         r.rr_prev[c] * (r.rr_prev[c] / r.rr_prev2[c]) <= 100.0 * r.tol2[c])
@@ -1076,6 +1213,25 @@ amge_status mm_iterate(PcgRunMM& r) {
   if (r.spec) mm_precondition(r);
   r.phase = PcgRunMM::M_ITER;
   return AMGE_OK;
+}
+
+// Iterations in the captured loop until a column's ||r|| meets its tolerance, a value
+// is not finite, or maxit: the operations and their order are those of mm_continue
+// and mm_iterate (z = B r, dots, p update, q = A p, axpy).
+amge_status mm_graph(PcgRunMM& r) {
+  amge_hier* h = r.h;
+  if (!r.x0_ready) mm_x0_from_r(r);
+  int* ps = h->pinned_state_mm;
+  ps[0] = r.it, ps[1] = r.o.maxit, ps[2] = 0, ps[3] = 0;
+  CK(cudaMemcpyAsync(h->gstate_mm, ps, 4 * sizeof(int), cudaMemcpyHostToDevice, r.s));
+  CK(cudaGraphLaunch(h->gmm[r.f32 ? 1 : 0][r.nrhs].exec, r.s));
+  CK(cudaMemcpyAsync(ps, h->gstate_mm, 4 * sizeof(int), cudaMemcpyDeviceToHost, r.s));
+  amge_status st = mm_copy_cols(r, SC_RR);
+  if (st) return st;
+  r.x0_ready = r.x0.mode != 0;
+  r.in_graph = true;
+  r.phase = PcgRunMM::M_ITER;
+  return mm_record(r);
 }
 
 // After the iteration's scalar checks: drop finished columns, then the p update and
@@ -1087,6 +1243,10 @@ amge_status mm_continue(PcgRunMM& r) {
   amge_status st = mm_push_active(r);
   if (st) return st;
   if (r.nact == 0) return mm_final(r);
+  if (r.graph) {
+    if (r.it >= r.o.maxit) return mm_final(r);
+    return mm_graph(r);
+  }
   if (!r.spec) mm_precondition(r);
   {
     Prof p(h, AMGE_PROF_PCG_VEC, r.s);
@@ -1103,13 +1263,18 @@ amge_status mm_step(PcgRunMM& r) {
   switch (r.phase) {
     case PcgRunMM::M_BB: {
       std::memcpy(r.bb.data(), mm_pinned(r, SC_BB), r.nrhs * sizeof(double));
-      CK(cudaMemsetAsync(r.x, 0, tot * sizeof(double), r.s));
+      CK(cudaMemsetAsync(r.xw, 0, tot * sizeof(double), r.s));
       r.nact = 0;
       for (int c = 0; c < r.nrhs; c++) {
         r.tol2[c] = r.o.rtol * r.o.rtol * r.bb[c];
         if (!std::isfinite(r.bb[c])) r.active[c] = 0, r.status[c] = AMGE_ENONFINITE;
         else if (r.bb[c] == 0.0) r.active[c] = 0;
         r.nact += r.active[c];
+      }
+      if (r.graph) {  // the loop test reads each column's tolerance on the device
+        std::memcpy(mm_pinned(r, SC_TOL2), r.tol2.data(), r.nrhs * sizeof(double));
+        CK(cudaMemcpyAsync(h->redmm.sc + (size_t)SC_TOL2 * kMaxRhs, mm_pinned(r, SC_TOL2), r.nrhs * sizeof(double),
+                           cudaMemcpyHostToDevice, r.s));
       }
       amge_status st = mm_push_active(r);
       if (st) return st;
@@ -1124,6 +1289,13 @@ amge_status mm_step(PcgRunMM& r) {
       return mm_iterate(r);
     }
     case PcgRunMM::M_ITER: {
+      if (r.in_graph) {
+        const int it_new = h->pinned_state_mm[0];
+        const GraphPcg& G = h->gmm[r.f32 ? 1 : 0][r.nrhs];
+        for (int c = 0; c < AMGE_PROF_CLASSES; c++) h->launches[c] += G.body[c] * (it_new - r.it);
+        r.it = it_new;
+        r.in_graph = false;
+      }
       std::memcpy(r.rr.data(), mm_pinned(r, SC_RR), r.nrhs * sizeof(double));
       bool check = false;
       for (int c = 0; c < r.nrhs; c++) {
@@ -1176,6 +1348,73 @@ amge_status mm_step(PcgRunMM& r) {
 
 }  // namespace
 
+namespace {
+
+// The block PCG loop for (precision, nrhs), captured once like build_pcg_graph: a
+// WHILE node whose body is one rotated iteration (block V-cycle from the axpy's
+// start, dots, p update, q = A p, axpy, loop test) on the hierarchy's block vectors
+// and its own iterate GX.
+amge_status build_pcg_graph_mm(amge_hier* h, int prec, int nrhs, const X0Out& x0) {
+  GraphPcg& G = h->gmm[prec][nrhs];
+  const int64_t n = h->n0;
+  const bool f32 = prec == AMGE_FP32_VCYCLE;
+  if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  CK(cudaGraphCreate(&G.g, 0));
+  CK(cudaGraphConditionalHandleCreate(&G.hw, G.g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = G.hw;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  CK(cudaGraphAddNode(&wnode, G.g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  int64_t before[AMGE_PROF_CLASSES];
+  std::memcpy(before, h->launches, sizeof(before));
+  const bool prof = h->prof;
+  h->prof = false;  // event records are not allowed inside conditional bodies
+  CK(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  vcycle_mm_iface(h, nrhs, h->PR, h->PZ, prec, h->cap, h->L > 1, f32);
+  const int flexible = f32 ? 1 : 0;
+  if (f32) {
+    launch_pcg_mm_dots<float>(n, nrhs, h->PR, h->lv32[0].Z, h->PQ, flexible, h->redmm, h->cap);
+    launch_pcg_mm_update_p<float>(n, nrhs, h->PP, h->lv32[0].Z, h->redmm, h->cap);
+  } else {
+    launch_pcg_mm_dots<double>(n, nrhs, h->PR, h->PZ, h->PQ, flexible, h->redmm, h->cap);
+    launch_pcg_mm_update_p<double>(n, nrhs, h->PP, h->PZ, h->redmm, h->cap);
+  }
+  launch_pcg_mm_spmv_dot(h->cA0, nrhs, h->PP, h->PQ, h->redmm, h->cap);
+  launch_pcg_mm_axpy_norm(n, nrhs, h->GX, h->PR, h->PP, h->PQ, h->redmm, h->cap, x0);
+  launch_pcg_mm_loop_cond(G.hw, nrhs, h->redmm, h->gstate_mm, h->cap);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap, &captured);
+  h->prof = prof;
+  for (int c = 0; c < AMGE_PROF_CLASSES; c++) {
+    G.body[c] = h->launches[c] - before[c];
+    h->launches[c] = before[c];
+  }
+  G.body[AMGE_PROF_PCG_VEC] += 4;   // dots, update_p, axpy_norm, loop test
+  G.body[AMGE_PROF_PCG_SPMV] += 1;  // q = A p with p.q
+  if (e != cudaSuccess) {
+    set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+    return AMGE_ECUDA;
+  }
+  CK(cudaGraphInstantiate(&G.exec, G.g, 0));
+  G.built = true;
+  return AMGE_OK;
+}
+
+void drop_graphs_mm(amge_hier* h) {
+  for (auto& row : h->gmm)
+    for (GraphPcg& G : row) {
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      if (G.g) cudaGraphDestroy(G.g);
+      G = GraphPcg{};
+    }
+}
+
+}  // namespace
+
 // Block solves need the block workspace (ensure_mm) of h for at least nrhs columns.
 amge_status amge::pcg_mm_run_start(amge_hier* h, int nrhs, const double* b, double* x, const amge_solve_opts& o,
                                    cudaStream_t s, PcgRunMM** out) {
@@ -1189,6 +1428,17 @@ amge_status amge::pcg_mm_run_start(amge_hier* h, int nrhs, const double* b, doub
     if (r->f32) r->x0.mode = 2, r->x0.minv32 = h->lv32[0].minv, r->x0.r32 = h->lv32[0].B, r->x0.x32 = h->lv32[0].X;
     else r->x0.mode = 1, r->x0.minv64 = h->lv64[0].minv, r->x0.x64 = h->lv64[0].X;
   }
+  // per-launch event timing (profiling) uses the directly launched loop, as for single
+  // vectors (event records cannot sit inside the captured loop's body)
+  r->graph = h->use_graphs && !h->prof;
+  if (r->graph && !h->gmm[r->f32 ? 1 : 0][nrhs].built) {
+    amge_status st = build_pcg_graph_mm(h, r->f32 ? 1 : 0, nrhs, r->x0);
+    if (st) {
+      delete r;
+      return st;
+    }
+  }
+  r->xw = r->graph ? h->GX : x;
   r->bb.assign(nrhs, 0.0), r->rr.assign(nrhs, 0.0), r->rt.assign(nrhs, 0.0);
   r->rr_prev.assign(nrhs, -1.0), r->rr_prev2.assign(nrhs, -1.0), r->tol2.assign(nrhs, 0.0);
   r->active.assign(nrhs, 1), r->iters.assign(nrhs, 0), r->status.assign(nrhs, AMGE_OK);
@@ -1280,11 +1530,11 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
       const int n = d64.n;
       if (l + 1 < L) {
         d64.x = dalloc<double>(h, n), d64.r = dalloc<double>(h, n), d64.tmp = dalloc<double>(h, n);
-        d64.y = dalloc<double>(h, d64.naux);
+        d64.y = dalloc<double>(h, d64.naux), d64.t = dalloc<double>(h, d64.naux);
         d32.x = dalloc<float>(h, n), d32.r = dalloc<float>(h, n), d32.tmp = dalloc<float>(h, n);
         d32.y = dalloc<float>(h, d32.naux);
       } else {
-        d64.x = d64.r = d64.tmp = d64.y = nullptr;
+        d64.x = d64.r = d64.tmp = d64.y = d64.t = nullptr;
         d32.x = d32.r = d32.tmp = d32.y = nullptr;
       }
       d64.b = (l >= 1 || L == 1) ? dalloc<double>(h, n) : nullptr;
@@ -1331,7 +1581,7 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
 // Streamed operators (much larger than L2) come from HBM either way and are timed back
 // to back, where each launch overlaps the previous one's tail as it does behind its
 // predecessor in the V-cycle.
-constexpr int kTuneCodes[9] = {0, 200, 400, 800, 2, 4, 8, 16, 32};
+constexpr int kTuneCodes[kNumTuneCodes] = {0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200};
 constexpr int kTuneReps = 10;
 
 struct TuneFlush {
@@ -1407,10 +1657,11 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
         fl.buf && !op_sell(d, op).stream && coarse_bytes<V>(h, levels<V>(h), l) > 0.5 * fl.l2;
     float best_sell = -1.f, best_vec = -1.f;
     int sell_lanes = 0, vec_lanes = 0;
-    for (int ci = 0; ci < 9; ci++) {
+    for (int ci = 0; ci < kNumTuneCodes; ci++) {
       const int lanes = kTuneCodes[ci];
       d.tune_us[op][ci] = -1.f;
-      if (lanes >= 100 && 2.0 * (lanes / 100) > avg + 1.0) continue;  // more warps than entry pairs
+      if (code_pf(lanes) && (!op_sell(d, op).stream || op_sell(d, op).unit)) continue;  // prefetch: streamed only
+      if (code_is_sell(lanes) && code_wps(lanes) > 1 && 2.0 * code_wps(lanes) > avg + 1.0) continue;  // more warps than entry pairs
       if (lanes > 2 && lanes < 100 && lanes > 2 * avg) continue;
       d.lanes[op] = lanes;
       // kTuneReps launches captured in a graph, so the host's launch rate does not
@@ -1437,7 +1688,7 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
       cudaGraphExecDestroy(ge);
       CK(le);
       d.tune_us[op][ci] = ms * (1e3f / kTuneReps);
-      const bool sell = lanes == 0 || lanes >= 100;
+      const bool sell = code_is_sell(lanes);
       float& b = sell ? best_sell : best_vec;
       int& bl = sell ? sell_lanes : vec_lanes;
       if (b < 0.f || ms < b) b = ms, bl = lanes;
@@ -1492,17 +1743,30 @@ amge_status autotune_mm_level(amge_hier* h, int l, int nrhs, cudaStream_t s, cud
 amge_status tune_mm(amge_hier* h, int nrhs, int precision, cudaStream_t s) {
   const int p = precision == AMGE_FP64 ? 0 : 1;
   if (nrhs < 2 || nrhs > kMaxRhs || h->mm_tuned[p][nrhs]) return AMGE_OK;
+  // candidates are captured on a stream of our own (the caller's may be the legacy
+  // default stream, which cannot be captured); their launches are not the caller's
+  CK(cudaStreamSynchronize(s));
+  cudaStream_t ts = nullptr;
+  CK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+  int64_t launches[AMGE_PROF_CLASSES];
+  std::memcpy(launches, h->launches, sizeof(launches));
   const bool prof = h->prof;
   h->prof = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
   amge_status st = AMGE_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("block tuner: cudaEventCreate failed");
+    st = AMGE_ECUDA;
+  }
   for (int l = 0; l + 1 < h->L && st == AMGE_OK; l++)
-    st = p == 0 ? autotune_mm_level<double>(h, l, nrhs, s, e0, e1) : autotune_mm_level<float>(h, l, nrhs, s, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+    st = p == 0 ? autotune_mm_level<double>(h, l, nrhs, ts, e0, e1) : autotune_mm_level<float>(h, l, nrhs, ts, e0, e1);
+  cudaStreamSynchronize(ts);
+  cudaStreamDestroy(ts);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   h->prof = prof;
+  std::memcpy(h->launches, launches, sizeof(launches));
   if (st == AMGE_OK) h->mm_tuned[p][nrhs] = true;
   return st;
 }
@@ -1830,6 +2094,7 @@ amge_status amge::hier_make_view(const amge_hier* src, cudaStream_t s, amge_hier
   v->nC = src->nC, v->Linv = src->Linv, v->LinvT = src->LinvT, v->Ainv = src->Ainv;
   v->use_graphs = src->use_graphs;
   v->device = src->device;
+  v->smoother = src->smoother, v->sweeps = src->sweeps, v->gs_levels = src->gs_levels, v->gs_built = src->gs_built;
   v->base = src->base ? src->base : src;
   amge_status st = alloc_work(v, s);
   if (st == AMGE_OK) {
@@ -1923,6 +2188,7 @@ amge_status amge_vcycle(amge_hier* h, const double* r_dev, double* z_dev, int32_
     set_error("unknown precision");
     return AMGE_EINVAL;
   }
+  if (gs_refuses(h, precision, nrhs)) return AMGE_EINVAL;
   if (r_dev == z_dev) {
     set_error("r and z must not overlap");
     return AMGE_EINVAL;
@@ -1953,6 +2219,7 @@ amge_status amge_pcg_solve(amge_hier* h, const double* b_dev, double* x_dev, int
     set_error("invalid solve options");
     return AMGE_EINVAL;
   }
+  if (gs_refuses(h, opts->precision, nrhs)) return AMGE_EINVAL;
   if (nrhs == 1) {
     // the captured loop needs no per-iteration host round trip; per-launch event
     // timing (profiling) uses the directly launched loop with the same kernels
@@ -2118,9 +2385,10 @@ amge_status amge_autotune_times(const amge_hier* h, float* us) {
   }
   for (int l = 0; l + 1 < h->L; l++)
     for (int op = 0; op < 6; op++)
-      for (int c = 0; c < 9; c++) {
-        us[((l * 2 + 0) * 6 + op) * 9 + c] = h->lv64[l].lanes[op] < 0 ? -1.f : h->lv64[l].tune_us[op][c];
-        us[((l * 2 + 1) * 6 + op) * 9 + c] = h->lv32[l].lanes[op] < 0 ? -1.f : h->lv32[l].tune_us[op][c];
+      for (int c = 0; c < kNumTuneCodes; c++) {
+        const size_t k = ((size_t)(l * 2) * 6 + op) * kNumTuneCodes + c;
+        us[k] = h->lv64[l].lanes[op] < 0 ? -1.f : h->lv64[l].tune_us[op][c];
+        us[k + 6 * kNumTuneCodes] = h->lv32[l].lanes[op] < 0 ? -1.f : h->lv32[l].tune_us[op][c];
       }
   return AMGE_OK;
 }
@@ -2135,8 +2403,8 @@ amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int3
     return AMGE_EINVAL;
   }
   if (lanes != 0 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32 && lanes != 200 &&
-      lanes != 400 && lanes != 800) {
-    set_error("kernel code must be 0, 200, 400, 800 (sliced ELL) or 2, 4, 8, 16, 32 (vector CSR)");
+      lanes != 400 && lanes != 800 && lanes != 1000 && lanes != 1200) {
+    set_error("kernel code must be 0, 200, 400, 800, 1000, 1200 (sliced ELL) or 2, 4, 8, 16, 32 (vector CSR)");
     return AMGE_EINVAL;
   }
   int& cur = precision == 0 ? h->lv64[level].lanes[op] : h->lv32[level].lanes[op];
@@ -2193,6 +2461,111 @@ amge_status amge_set_kernel_mm(amge_hier* h, int32_t level, int32_t precision, i
   if (p == 0) h->lv64[level].mmk[op][nrhs] = (int8_t)code;
   else h->lv32[level].mmk[op][nrhs] = (int8_t)code;
   h->mm_tuned[p][nrhs] = true;  // a pinned choice is not re-tuned
+  drop_graphs_mm(h);            // the captured launches name the old kernels
+  return AMGE_OK;
+}
+
+namespace {
+
+// Copy a device CSR (FP64 values) back to the host.
+amge_status download_csr(const DevCsr<double>& M, HostCsr& out) {
+  out.nr = M.nr, out.nc = M.nc;
+  out.rp.resize((size_t)M.nr + 1);
+  out.ci.resize((size_t)M.nnz);
+  out.v.resize((size_t)M.nnz);
+  CK(cudaMemcpy(out.rp.data(), M.rp, out.rp.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  if (M.nnz) {
+    CK(cudaMemcpy(out.ci.data(), M.ci, out.ci.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out.v.data(), M.val, out.v.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  return AMGE_OK;
+}
+
+// Gauss-Seidel data of smoothing level l: A_l and A_aux = G^T A_l G (FP64, the
+// product's cancellation residue dropped as for A G), each with rows grouped by the
+// colours of a greedy colouring of its pattern (for A_aux the symbolic pattern of
+// G^T A G: entries that cancel numerically still couple), and 1 / diagonal.
+amge_status build_gs_level(amge_hier* h, int l, cudaStream_t s) {
+  LevelDev<double>& d = h->lv64[l];
+  HostCsr A, G;
+  amge_status st = download_csr(d.cA, A);
+  if (st == AMGE_OK) st = download_csr(d.cG, G);
+  if (st) return st;
+  const HostCsr GT = transpose(G);
+  const HostCsr Aaux = sparse_product(GT, sparse_product(A, G));
+  const HostCsr pattern_aux = symbolic_product(GT, symbolic_product(A, G));
+  std::vector<std::vector<double>> keepd;
+  std::vector<std::vector<float>> keep;
+  try {
+    auto one = [&](const HostCsr& M, const HostCsr& pattern, DevSell<double>& out, std::vector<int>& cs,
+                   double*& dinv) -> amge_status {
+      std::vector<int> colour;
+      const int nc = greedy_colours(pattern, colour);
+      HostSell S = build_sell_coloured(M, colour, nc, kSellSigma, cs);
+      std::vector<double> di(M.nr, 0.0);
+      for (int i = 0; i < M.nr; i++)
+        for (int p = M.rp[i]; p < M.rp[i + 1]; p++)
+          if (M.ci[p] == i) di[i] = M.v[p];
+      for (int i = 0; i < M.nr; i++) {
+        if (!(di[i] > 0)) {
+          set_error("Gauss-Seidel: non-positive diagonal at level " + std::to_string(l));
+          return AMGE_EINVAL;
+        }
+        di[i] = 1.0 / di[i];
+      }
+      out.nr = S.nr, out.nc = S.nc, out.nslices = S.nslices, out.nnz = S.nnz, out.unit = 0;
+      out.stored = S.sptr[S.nslices];
+      out.stream = (double)out.stored * 12.0 > 64.0 * (1 << 20) ? 1 : 0;
+      out.sptr = upload<int64_t>(h, S.sptr.data(), S.sptr.size(), s);
+      out.srow = upload<int>(h, S.srow.data(), S.srow.size(), s);
+      out.ci = upload<int>(h, S.ci.data(), S.ci.size(), s);
+      keepd.push_back(std::move(S.v));
+      out.val = upload<double>(h, keepd.back().data(), keepd.back().size(), s);
+      keepd.push_back(std::move(di));
+      dinv = upload<double>(h, keepd.back().data(), keepd.back().size(), s);
+      CK(cudaStreamSynchronize(s));  // the host vectors die with this call
+      keepd.clear();
+      return AMGE_OK;
+    };
+    st = one(A, A, d.gsA, d.gsA_cs, d.gsA_dinv);
+    if (st == AMGE_OK) st = one(Aaux, pattern_aux, d.gsX, d.gsX_cs, d.gsX_dinv);
+  } catch (const UploadError& e) {
+    return e.st;
+  }
+  return st;
+}
+
+void drop_graphs(amge_hier* h) {
+  for (GraphPcg& G : h->gpcg) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.g) cudaGraphDestroy(G.g);
+    G = GraphPcg{};
+  }
+}
+
+}  // namespace
+
+amge_status amge_set_smoother(amge_hier* h, int32_t smoother, int32_t sweeps, int32_t gs_levels) {
+  if (!h || (smoother != AMGE_SMOOTHER_L1_JACOBI && smoother != AMGE_SMOOTHER_SYM_GS) || sweeps < 1 ||
+      sweeps > 8 || gs_levels < 0) {
+    set_error("invalid smoother, sweeps (1 .. 8) or gs_levels (>= 0)");
+    return AMGE_EINVAL;
+  }
+  if (h->base) {
+    set_error("a workspace view takes the smoother of its hierarchy");
+    return AMGE_EINVAL;
+  }
+  const int want = smoother == AMGE_SMOOTHER_SYM_GS ? std::min(gs_levels, h->L - 1) : 0;
+  cudaStream_t s = nullptr;
+  for (int l = h->gs_built; l < want; l++) {  // built once per level, kept
+    amge_status st = build_gs_level(h, l, s);
+    if (st) return st;
+    h->gs_built = l + 1;
+  }
+  h->smoother = smoother;
+  h->sweeps = sweeps;
+  h->gs_levels = want;
+  drop_graphs(h);  // the captured V-cycle changes
   return AMGE_OK;
 }
 
@@ -2239,8 +2612,10 @@ void amge_hier_free(amge_hier* h) {
     if (G.exec) cudaGraphExecDestroy(G.exec);
     if (G.g) cudaGraphDestroy(G.g);
   }
+  drop_graphs_mm(h);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->pinned_state) cudaFreeHost(h->pinned_state);
+  if (h->pinned_state_mm) cudaFreeHost(h->pinned_state_mm);
   if (h->pinned) cudaFreeHost(h->pinned);
   if (h->pinned_mm) cudaFreeHost(h->pinned_mm);
   if (h->ev) cudaEventDestroy(h->ev);

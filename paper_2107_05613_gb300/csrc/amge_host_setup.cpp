@@ -285,3 +285,81 @@ HostSell build_sell(const HostCsr& M, int sigma, bool allow_unit) {
 }
 
 }  // namespace amge
+
+namespace amge {
+
+int greedy_colours(const HostCsr& S, std::vector<int>& colour) {
+  colour.assign(S.nr, -1);
+  std::vector<int> mark;  // mark[c] == i: colour c is taken by a neighbour of row i
+  int ncol = 0;
+  for (int i = 0; i < S.nr; i++) {
+    for (int p = S.rp[i]; p < S.rp[i + 1]; p++) {
+      const int j = S.ci[p];
+      if (j != i && colour[j] >= 0) {
+        if ((int)mark.size() <= colour[j]) mark.resize(colour[j] + 1, -1);
+        mark[colour[j]] = i;
+      }
+    }
+    int c = 0;
+    while (c < (int)mark.size() && mark[c] == i) c++;
+    colour[i] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  return ncol;
+}
+
+HostSell build_sell_coloured(const HostCsr& M, const std::vector<int>& colour, int ncolours, int sigma,
+                             std::vector<int>& cslice) {
+  HostSell out;
+  out.nr = M.nr, out.nc = M.nc, out.nnz = M.nnz();
+  out.sptr.assign(1, 0);
+  cslice.assign(ncolours + 1, 0);
+  std::vector<std::vector<int>> rows(ncolours);
+  for (int i = 0; i < M.nr; i++) rows[colour[i]].push_back(i);
+  for (int c = 0; c < ncolours; c++) {
+    HostCsr sub;  // the colour's rows, columns unchanged
+    sub.nr = (int)rows[c].size(), sub.nc = M.nc;
+    sub.rp.assign(sub.nr + 1, 0);
+    for (int k = 0; k < sub.nr; k++) {
+      const int r = rows[c][k];
+      sub.rp[k + 1] = sub.rp[k] + (M.rp[r + 1] - M.rp[r]);
+      sub.ci.insert(sub.ci.end(), M.ci.begin() + M.rp[r], M.ci.begin() + M.rp[r + 1]);
+      sub.v.insert(sub.v.end(), M.v.begin() + M.rp[r], M.v.begin() + M.rp[r + 1]);
+    }
+    HostSell S = build_sell(sub, sigma, false);
+    const int64_t base = out.sptr.back();
+    for (int s = 0; s < S.nslices; s++) out.sptr.push_back(base + S.sptr[s + 1]);
+    for (int r : S.srow) out.srow.push_back(r >= 0 ? rows[c][r] : -1);
+    out.ci.insert(out.ci.end(), S.ci.begin(), S.ci.end());
+    out.v.insert(out.v.end(), S.v.begin(), S.v.end());
+    out.nslices += S.nslices;
+    cslice[c + 1] = out.nslices;
+  }
+  return out;
+}
+
+HostCsr symbolic_product(const HostCsr& A, const HostCsr& B) {
+  HostCsr C;
+  C.nr = A.nr, C.nc = B.nc;
+  C.rp.assign(A.nr + 1, 0);
+  std::vector<char> seen(B.nc, 0);
+  std::vector<int> touched;
+  for (int i = 0; i < A.nr; i++) {
+    touched.clear();
+    for (int p = A.rp[i]; p < A.rp[i + 1]; p++)
+      for (int q = B.rp[A.ci[p]]; q < B.rp[A.ci[p] + 1]; q++) {
+        const int j = B.ci[q];
+        if (!seen[j]) seen[j] = 1, touched.push_back(j);
+      }
+    std::sort(touched.begin(), touched.end());
+    for (int j : touched) {
+      C.ci.push_back(j);
+      C.v.push_back(1.0);
+      seen[j] = 0;
+    }
+    C.rp[i + 1] = (int)C.ci.size();
+  }
+  return C;
+}
+
+}  // namespace amge

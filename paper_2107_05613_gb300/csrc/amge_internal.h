@@ -112,15 +112,37 @@ struct SpmvArgs {
   V* y2 = nullptr;         // second output (STORE_MUL)
 };
 
-// wps = warps per 32-row slice (1, 2, 4, 8).
+// Single-vector kernel codes of the autotuner: 0 = sliced ELL with one warp per
+// slice, 100 w = w warps per slice (w = 2, 4, 8), 1000 / 1200 = one / two warps per
+// slice with a bulk L2 prefetch of each slice's entries for streamed operators (those
+// read with the evict-first hint; the others always prefetch), 2 .. 32 = vector CSR
+// with that many lanes per row.
+inline bool code_is_sell(int c) { return c == 0 || c >= 100; }
+inline int code_wps(int c) {
+  const int w = c >= 1000 ? (c - 1000) / 100 : c / 100;
+  return w < 1 ? 1 : w;
+}
+inline bool code_pf(int c) { return c >= 1000; }
+
+// wps = warps per 32-row slice (1, 2, 4, 8); pf: a streamed operator's slices are
+// also prefetched into L2 in bulk (wps 1 or 2).
 template <typename V>
-void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, int wps = 1);
+void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, int wps = 1, bool pf = false);
 
 // FP32 vectors through the FP64 sliced-ELL operator M (FP64 values, FP64 FMA chain,
 // result rounded once to FP32); epi = EPI_STORE (y = M x), EPI_RESID (y = b - M x) or
 // EPI_SWEEP (y = xin + d (b - M x)).  Same row order and warp split as
 // launch_sell<double>.
-void launch_sell_wide(const DevSell<double>& M, int epi, const SpmvArgs<float>& a, cudaStream_t s, int wps = 1);
+void launch_sell_wide(const DevSell<double>& M, int epi, const SpmvArgs<float>& a, cudaStream_t s, int wps = 1,
+                      bool pf = false);
+
+// Gauss-Seidel update of one colour's rows: slices [s0, s1) of a colour-grouped
+// sliced-ELL operator, x_i += dinv_i (b_i - (M x)_i) in place (FP64).
+void launch_gs_colour(const DevSell<double>& M, int s0, int s1, const double* dinv, const double* b, double* x,
+                      cudaStream_t s, int wps = 1);
+// x = 0
+template <typename V>
+void launch_zero(int64_t n, V* x, cudaStream_t s);
 
 // CSR copy of an operator for the multi-right-hand-side products (row pointers and
 // columns shared by both precisions).
@@ -141,7 +163,8 @@ struct AgArgs {
   V* z = nullptr;          // post form output
 };
 template <typename V>
-void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, int wps = 1);
+void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, int wps = 1,
+                     bool pf = false);
 
 template <typename V>
 struct DevCsr {
@@ -297,6 +320,12 @@ void launch_pcg_mm_dots(int64_t n, int nrhs, const double* rv, const ZT* z, cons
 template <typename ZT>
 void launch_pcg_mm_update_p(int64_t n, int nrhs, double* p, const ZT* z, const RedScratchMM& r, cudaStream_t s);
 
+// Loop test of the graph-driven block PCG (one warp): state[0] += 1; the WHILE
+// condition is set while every active column's SC_RR is finite and above its SC_TOL2
+// and state[0] < state[1]; state[2] = 1 flags a non-finite active column.
+void launch_pcg_mm_loop_cond(cudaGraphConditionalHandle hw, int nrhs, const RedScratchMM& r, int* state,
+                             cudaStream_t s);
+
 // Resumable single-RHS PCG on a hierarchy's (or a view's) workspace, used by the
 // blocking solve and by the request server.  advance() returns 1 when finished,
 // 0 while the GPU is still working on the current phase, -1 on error.
@@ -341,6 +370,16 @@ std::vector<double> aux_l1_row_sums(const HostCsr& A, const HostCsr& G, const Ho
 bool coarse_factor(const HostCsr& A, std::vector<double>& Linv, std::vector<double>& LinvT);
 // A^{-1} = L^{-T} L^{-1} from the transposed inverse factor (full n x n, row-major).
 void coarse_inverse(int n, const std::vector<double>& LinvT, std::vector<double>& Ainv);
+
+// Greedy colouring of the symmetric sparsity pattern S (rows in index order, each
+// taking the smallest colour no coloured neighbour has); returns the colour count.
+int greedy_colours(const HostCsr& S, std::vector<int>& colour);
+// Sliced ELL of the rows of M grouped by colour: the rows of colour c fill slices
+// [cslice[c], cslice[c+1]) (each a sliced-ELL layout of those rows alone).
+HostSell build_sell_coloured(const HostCsr& M, const std::vector<int>& colour, int ncolours, int sigma,
+                             std::vector<int>& cslice);
+// Pattern of A B (structural: every product term counts, whatever its value).
+HostCsr symbolic_product(const HostCsr& A, const HostCsr& B);
 
 // Read-only view of a hierarchy's coarsest factor and the device it lives on
 // (defined in amge_api.cu).

@@ -116,7 +116,7 @@ __device__ __forceinline__ float signed_entry(const float* x, int c) {
 // the first warp adds them in warp order and writes the row.  More warps per slice
 // expose more loads in flight for operators with long rows and few slices (the
 // restriction P^T, coarse-level operators); WPS = 1 needs no shared memory.
-template <typename V, int EPI, int WPS, bool UNIT, bool CS>
+template <typename V, int EPI, int WPS, bool UNIT, bool CS, bool PF = false>
 __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __restrict__ sptr,
                                                  const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                  const typename Pair<V>::T* __restrict__ val2, SpmvArgs<V> a) {
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
     const int64_t p0 = ldg(sptr + slice) >> 1;
     np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
     row = ldg(srow + (size_t)slice * 32 + lane);
-    if (!CS && g == 0 && lane == 0 && np > 0) {
+    if ((!CS || PF) && g == 0 && lane == 0 && np > 0) {
       prefetch_l2_bulk(ci2 + p0, (uint32_t)np * 32u * sizeof(int2));
       if (!UNIT) prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(PV));
     }
@@ -222,7 +222,7 @@ __device__ __forceinline__ double widen(float f) {
 //   EPI_STORE: y = A x
 //   EPI_RESID: y = b - A x
 //   EPI_SWEEP: y = xin + d (float)(b - A x)
-template <int EPI, int WPS, bool CS>
+template <int EPI, int WPS, bool CS, bool PF = false>
 __global__ void __launch_bounds__(kBlock) k_sell_wide(int nslices, const int64_t* __restrict__ sptr,
                                                       const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                       const double2* __restrict__ val2, SpmvArgs<float> a) {
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kBlock) k_sell_wide(int nslices, const int64_t
     const int64_t p0 = ldg(sptr + slice) >> 1;
     np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
     row = ldg(srow + (size_t)slice * 32 + lane);
-    if (!CS && g == 0 && lane == 0 && np > 0) {
+    if ((!CS || PF) && g == 0 && lane == 0 && np > 0) {
       prefetch_l2_bulk(ci2 + p0, (uint32_t)np * 32u * sizeof(int2));
       prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(double2));
     }
@@ -285,12 +285,70 @@ __global__ void __launch_bounds__(kBlock) k_sell_wide(int nslices, const int64_t
   else a.y[row] = r;
 }
 
+// One Gauss-Seidel update of the rows of one colour: slices [s0, s1) of a
+// colour-grouped sliced-ELL operator (every slice holds rows of a single colour),
+// x_i <- x_i + dinv_i (b_i - (M x)_i).  Rows of one colour are not coupled, so
+// updating them all at once in place is the sequential sweep over them; the sum
+// includes the diagonal term a_ii x_i, read before this thread writes x_i, and no
+// other thread of the launch reads x_i.  x is read with plain loads (it is written
+// in the launch).  WPS warps per slice as in k_sell.
+template <int WPS, bool CS>
+__global__ void __launch_bounds__(kBlock) k_gs(int s0, int s1, const int64_t* __restrict__ sptr,
+                                               const int* __restrict__ srow, const int2* __restrict__ ci2,
+                                               const double2* __restrict__ val2, const double* __restrict__ dinv,
+                                               const double* __restrict__ b, double* x) {
+  const int wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int g = wib % WPS;
+  const int slice = s0 + (blockIdx.x * (kBlock / 32) + wib) / WPS;
+  const bool live = slice < s1;
+  int row = -1, np = 0;
+  const int2* cp = ci2;
+  const double2* vp = val2;
+  if (live) {
+    const int64_t p0 = ldg(sptr + slice) >> 1;
+    np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+    row = ldg(srow + (size_t)slice * 32 + lane);
+    cp += p0 + lane;
+    vp += p0 + lane;
+  }
+  pdl_begin();
+  double s = 0.0;
+  if (live) {
+    if (g == 0 && row >= 0) s = b[row];
+#pragma unroll 2
+    for (int k = g; k < np; k += WPS) {
+      const int2 c = ldm<CS>(cp + (size_t)k * 32);
+      const double2 v = ldm<CS>(vp + (size_t)k * 32);
+      s = fma(-v.x, x[c.x], s);
+      s = fma(-v.y, x[c.y], s);
+    }
+  }
+  if (WPS > 1) {
+    __shared__ double part[kBlock];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (g != 0) return;
+#pragma unroll
+    for (int j = 1; j < WPS; j++) s += part[threadIdx.x + 32 * j];
+  }
+  if (!live || row < 0) return;
+  x[row] = fma(dinv[row], s, x[row]);
+}
+
+template <typename V>
+__global__ void k_zero(int64_t n, V* __restrict__ x) {
+  pdl_begin();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = V(0);
+}
+
 // G y (two sign-coded entries) and A G y for one row per lane (see AgArgs).  WPS warps
 // share a slice as in k_sell (the first warp starts from r and adds the others'
 // partial sums in warp order, then applies G y and the epilogue).  As in k_sell, the
 // constant slice header, G's row and the first entry pair are loaded before waiting
 // for the previous kernel.
-template <typename V, bool POST, bool CS, int WPS>
+template <typename V, bool POST, bool CS, int WPS, bool PF = false>
 __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t* __restrict__ sptr,
                                                      const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                      const typename Pair<V>::T* __restrict__ val2, AgArgs<V> a) {
@@ -308,7 +366,7 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
     const int64_t p0 = ldg(sptr + slice) >> 1;
     np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
     row = ldg(srow + (size_t)slice * 32 + lane);
-    if (!CS && g == 0 && lane == 0 && np > 0) {
+    if ((!CS || PF) && g == 0 && lane == 0 && np > 0) {
       prefetch_l2_bulk(ci2 + p0, (uint32_t)np * 32u * sizeof(int2));
       prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(PV));
     }
@@ -771,20 +829,20 @@ int red_blocks(int64_t n) {
   return (int)std::min<int64_t>(std::max<int64_t>(g, 1), resident_blocks());
 }
 
-template <typename V, int WPS, bool UNIT, bool CS>
+template <typename V, int WPS, bool UNIT, bool CS, bool PF = false>
 static void launch_sell_t(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
   const int per = (kBlock / 32) / WPS;  // slices per block
   const int grid = (M.nslices + per - 1) / per;
   const int2* ci2 = reinterpret_cast<const int2*>(M.ci);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(M.val);
   switch (epi) {
-    case EPI_STORE: launch_k(k_sell<V, EPI_STORE, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_RESID: launch_k(k_sell<V, EPI_RESID, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_SCALE: launch_k(k_sell<V, EPI_SCALE, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_ADD: launch_k(k_sell<V, EPI_ADD, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
-    case EPI_SWEEP: launch_k(k_sell<V, EPI_SWEEP, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_STORE: launch_k(k_sell<V, EPI_STORE, WPS, UNIT, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_RESID: launch_k(k_sell<V, EPI_RESID, WPS, UNIT, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SCALE: launch_k(k_sell<V, EPI_SCALE, WPS, UNIT, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_ADD: launch_k(k_sell<V, EPI_ADD, WPS, UNIT, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
+    case EPI_SWEEP: launch_k(k_sell<V, EPI_SWEEP, WPS, UNIT, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a); break;
     case EPI_STORE_MUL:
-      launch_k(k_sell<V, EPI_STORE_MUL, WPS, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a);
+      launch_k(k_sell<V, EPI_STORE_MUL, WPS, UNIT, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a);
       break;
   }
 }
@@ -812,35 +870,73 @@ static void launch_sell_u(const DevSell<V>& M, int wps, int epi, const SpmvArgs<
 }
 
 template <typename V>
-void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, int wps) {
+void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, int wps, bool pf) {
   if (M.nslices == 0) return;
+  if (pf && M.stream && !M.unit && wps <= 2) {  // streamed, prefetched slice by slice
+    if (wps == 2) launch_sell_t<V, 2, false, true, true>(M, epi, a, s);
+    else launch_sell_t<V, 1, false, true, true>(M, epi, a, s);
+    return;
+  }
   if (M.unit) launch_sell_u<V, true>(M, wps, epi, a, s);
   else launch_sell_u<V, false>(M, wps, epi, a, s);
 }
 template <int EPI, int WPS>
-static void launch_sell_wide_t(const DevSell<double>& M, const SpmvArgs<float>& a, cudaStream_t s) {
+static void launch_sell_wide_t(const DevSell<double>& M, const SpmvArgs<float>& a, cudaStream_t s, bool pf) {
   const int per = (kBlock / 32) / WPS;
   const int grid = (M.nslices + per - 1) / per;
   const int2* ci2 = reinterpret_cast<const int2*>(M.ci);
   const auto* v2 = reinterpret_cast<const double2*>(M.val);
-  if (M.stream) launch_k(k_sell_wide<EPI, WPS, true>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a);
+  if (M.stream && pf && WPS <= 2)
+    launch_k(k_sell_wide<EPI, WPS, true, true>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a);
+  else if (M.stream)
+    launch_k(k_sell_wide<EPI, WPS, true>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a);
   else launch_k(k_sell_wide<EPI, WPS, false>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a);
 }
 template <int EPI>
-static void launch_sell_wide_e(const DevSell<double>& M, const SpmvArgs<float>& a, cudaStream_t s, int wps) {
+static void launch_sell_wide_e(const DevSell<double>& M, const SpmvArgs<float>& a, cudaStream_t s, int wps,
+                               bool pf) {
   switch (wps) {
-    case 2: launch_sell_wide_t<EPI, 2>(M, a, s); break;
-    case 4: launch_sell_wide_t<EPI, 4>(M, a, s); break;
-    case 8: launch_sell_wide_t<EPI, 8>(M, a, s); break;
-    default: launch_sell_wide_t<EPI, 1>(M, a, s); break;
+    case 2: launch_sell_wide_t<EPI, 2>(M, a, s, pf); break;
+    case 4: launch_sell_wide_t<EPI, 4>(M, a, s, pf); break;
+    case 8: launch_sell_wide_t<EPI, 8>(M, a, s, pf); break;
+    default: launch_sell_wide_t<EPI, 1>(M, a, s, pf); break;
   }
 }
-void launch_sell_wide(const DevSell<double>& M, int epi, const SpmvArgs<float>& a, cudaStream_t s, int wps) {
+void launch_sell_wide(const DevSell<double>& M, int epi, const SpmvArgs<float>& a, cudaStream_t s, int wps,
+                      bool pf) {
   if (M.nslices == 0) return;
-  if (epi == EPI_SWEEP) launch_sell_wide_e<EPI_SWEEP>(M, a, s, wps);
-  else if (epi == EPI_RESID) launch_sell_wide_e<EPI_RESID>(M, a, s, wps);
-  else launch_sell_wide_e<EPI_STORE>(M, a, s, wps);
+  if (epi == EPI_SWEEP) launch_sell_wide_e<EPI_SWEEP>(M, a, s, wps, pf);
+  else if (epi == EPI_RESID) launch_sell_wide_e<EPI_RESID>(M, a, s, wps, pf);
+  else launch_sell_wide_e<EPI_STORE>(M, a, s, wps, pf);
 }
+
+template <int WPS>
+static void launch_gs_t(const DevSell<double>& M, int s0, int s1, const double* dinv, const double* b, double* x,
+                        cudaStream_t s) {
+  const int per = (kBlock / 32) / WPS;
+  const int grid = (s1 - s0 + per - 1) / per;
+  const int2* ci2 = reinterpret_cast<const int2*>(M.ci);
+  const auto* v2 = reinterpret_cast<const double2*>(M.val);
+  if (M.stream) launch_k(k_gs<WPS, true>, grid, kBlock, s, s0, s1, M.sptr, M.srow, ci2, v2, dinv, b, x);
+  else launch_k(k_gs<WPS, false>, grid, kBlock, s, s0, s1, M.sptr, M.srow, ci2, v2, dinv, b, x);
+}
+void launch_gs_colour(const DevSell<double>& M, int s0, int s1, const double* dinv, const double* b, double* x,
+                      cudaStream_t s, int wps) {
+  if (s1 <= s0) return;
+  switch (wps) {
+    case 2: launch_gs_t<2>(M, s0, s1, dinv, b, x, s); break;
+    case 4: launch_gs_t<4>(M, s0, s1, dinv, b, x, s); break;
+    case 8: launch_gs_t<8>(M, s0, s1, dinv, b, x, s); break;
+    default: launch_gs_t<1>(M, s0, s1, dinv, b, x, s); break;
+  }
+}
+
+template <typename V>
+void launch_zero(int64_t n, V* x, cudaStream_t s) {
+  if (n > 0) launch_k(k_zero<V>, vec_grid(n), kBlock, s, n, x);
+}
+template void launch_zero<double>(int64_t, double*, cudaStream_t);
+template void launch_zero<float>(int64_t, float*, cudaStream_t);
 
 template <typename V, int LANES>
 static void launch_csrv_lanes(const DevCsr<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
@@ -870,11 +966,14 @@ template void launch_csrv<double>(const DevCsr<double>&, int, int, const SpmvArg
 template void launch_csrv<float>(const DevCsr<float>&, int, int, const SpmvArgs<float>&, cudaStream_t);
 
 template <typename V, int WPS>
-void launch_ag_fused_t(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s) {
+void launch_ag_fused_t(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, bool pf) {
   const int grid = (int)(((int64_t)AG.nslices * WPS + (kBlock / 32) - 1) / (kBlock / 32));
   const int2* ci2 = reinterpret_cast<const int2*>(AG.ci);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(AG.val);
-  if (AG.stream) {
+  if (AG.stream && pf && WPS <= 2) {
+    if (post) launch_k(k_ag_fused<V, true, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+    else launch_k(k_ag_fused<V, false, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+  } else if (AG.stream) {
     if (post) launch_k(k_ag_fused<V, true, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
     else launch_k(k_ag_fused<V, false, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
   } else {
@@ -884,20 +983,20 @@ void launch_ag_fused_t(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaS
 }
 
 template <typename V>
-void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, int wps) {
+void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, int wps, bool pf) {
   if (AG.nslices == 0) return;
   switch (wps) {
-    case 2: launch_ag_fused_t<V, 2>(AG, post, a, s); break;
-    case 4: launch_ag_fused_t<V, 4>(AG, post, a, s); break;
-    case 8: launch_ag_fused_t<V, 8>(AG, post, a, s); break;
-    default: launch_ag_fused_t<V, 1>(AG, post, a, s); break;
+    case 2: launch_ag_fused_t<V, 2>(AG, post, a, s, pf); break;
+    case 4: launch_ag_fused_t<V, 4>(AG, post, a, s, pf); break;
+    case 8: launch_ag_fused_t<V, 8>(AG, post, a, s, pf); break;
+    default: launch_ag_fused_t<V, 1>(AG, post, a, s, pf); break;
   }
 }
-template void launch_ag_fused<double>(const DevSell<double>&, int, const AgArgs<double>&, cudaStream_t, int);
-template void launch_ag_fused<float>(const DevSell<float>&, int, const AgArgs<float>&, cudaStream_t, int);
+template void launch_ag_fused<double>(const DevSell<double>&, int, const AgArgs<double>&, cudaStream_t, int, bool);
+template void launch_ag_fused<float>(const DevSell<float>&, int, const AgArgs<float>&, cudaStream_t, int, bool);
 
-template void launch_sell<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t, int);
-template void launch_sell<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t, int);
+template void launch_sell<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t, int, bool);
+template void launch_sell<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t, int, bool);
 
 template <typename V>
 void launch_mul(int64_t n, const V* d, const V* x, V* y, cudaStream_t s) {

@@ -458,6 +458,31 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mm_update_p(int64_t n, int nrhs,
   if (blockIdx.x == 0 && threadIdx.x < nrhs) scol(r, SC_RHO)[threadIdx.x] = scol(r, SC_RHO_NEW)[threadIdx.x];
 }
 
+// One block: the WHILE condition of the captured block PCG loop.  state[0] += 1
+// (iterations done); the loop goes on while every active column's recursive ||r||^2
+// (SC_RR, summed by the axpy) is finite and above its tolerance (SC_TOL2) and
+// state[0] < state[1] (maxit); state[2] = 1 flags a non-finite active column.  A
+// column whose ||r|| met its tolerance stops the loop: the host then checks the true
+// residuals, as the host-driven loop does after every iteration.
+__global__ void __launch_bounds__(kMaxRhs) k_pcg_mm_loop_cond(cudaGraphConditionalHandle hw, int nrhs,
+                                                              RedScratchMM r, int* state) {
+  pdl_begin();
+  const int c = threadIdx.x;
+  bool stop = false, bad = false;
+  if (c < nrhs && r.active[c]) {
+    const double rr = scol(r, SC_RR)[c];
+    bad = !isfinite(rr);
+    stop = bad || rr <= scol(r, SC_TOL2)[c];
+  }
+  stop = __any_sync(0xffffffffu, stop);
+  bad = __any_sync(0xffffffffu, bad);
+  if (c != 0) return;
+  const int it = state[0] + 1;
+  state[0] = it;
+  if (bad) state[2] = 1;
+  cudaGraphSetConditional(hw, (!stop && it < state[1]) ? 1u : 0u);
+}
+
 int pow2_at_least(int v) {
   int k = 1;
   while (k < v) k <<= 1;
@@ -662,6 +687,11 @@ template void launch_pcg_mm_dots<double>(int64_t, int, const double*, const doub
                                          const RedScratchMM&, cudaStream_t);
 template void launch_pcg_mm_dots<float>(int64_t, int, const double*, const float*, const double*, int,
                                         const RedScratchMM&, cudaStream_t);
+
+void launch_pcg_mm_loop_cond(cudaGraphConditionalHandle hw, int nrhs, const RedScratchMM& r, int* state,
+                             cudaStream_t s) {
+  launch_k(k_pcg_mm_loop_cond, 1, kMaxRhs, s, hw, nrhs, r, state);
+}
 
 template <typename ZT>
 void launch_pcg_mm_update_p(int64_t n, int nrhs, double* p, const ZT* z, const RedScratchMM& r, cudaStream_t s) {

@@ -71,10 +71,38 @@ def sample_rows(n, rng):
     return np.unique(np.concatenate([rng.choice(n, size=min(n, 4096), replace=False), np.arange(max(n - 64, 0), n)]))
 
 
+class pinned_level0:
+    """Pin every sliced-ELL level-0 operator of h (both precisions) to one kernel code
+    for the block, restoring the autotuned choices afterwards."""
+
+    def __init__(self, amge, h, code):
+        self.amge, self.h, self.code = amge, h, code
+
+    def __enter__(self):
+        self.saved = self.amge.amge_autotune_report(self.h)
+        if self.code != "tuned":
+            for (l, p, o), v in self.saved.items():
+                if l == 0 and (v == 0 or v >= 100):
+                    self.amge.amge_set_kernel(self.h, l, p, o, self.code)
+
+    def __exit__(self, *exc):
+        for (l, p, o), v in self.saved.items():
+            if v >= 0:
+                self.amge.amge_set_kernel(self.h, l, p, o, v)
+
+
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_level0_products_sampled(amge, name, prec):
+@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200])
+def test_level0_products_sampled(amge, name, prec, kernels):
+    """The level-0 products on the autotuned kernels, and on the sliced-ELL kernels that
+    prefetch each slice into L2 with one and two warps per slice."""
     h, o, _ = workload(amge, name)
+    with pinned_level0(amge, h, kernels):
+        _level0_products(amge, h, o, name, prec)
+
+
+def _level0_products(amge, h, o, name, prec):
     rep = amge.amge_autotune_report(h)
     rng = np.random.default_rng(7 + prec)
     eps = EPS64 if prec == 0 else EPS32
@@ -107,8 +135,14 @@ def test_level0_products_sampled(amge, name, prec):
 
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
-def test_level0_wide_product_sampled(amge, name):
+@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200])
+def test_level0_wide_product_sampled(amge, name, kernels):
     h, o, _ = workload(amge, name)
+    with pinned_level0(amge, h, kernels):
+        _level0_wide(amge, h, o, name)
+
+
+def _level0_wide(amge, h, o, name):
     rng = np.random.default_rng(9)
     A, G = o.A[0], o.G[0]
     x = G @ rng.uniform(-1, 1, G.shape[1]) + 1e-3 * rng.uniform(-1, 1, A.shape[1])

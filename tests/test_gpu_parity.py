@@ -592,6 +592,35 @@ def test_graph_loop_equals_host_loop(amge, form, n, L, prec):
     assert torch.equal(xg, xh)
 
 
+@pytest.mark.parametrize("form,n,L,nrhs", [("hcurl", 16, 2, 8), ("hdiv", 24, 3, 5), ("hcurl", 8, 4, 32)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_block_graph_loop_equals_host_loop(amge, form, n, L, nrhs, prec):
+    """The block PCG's WHILE-node graph runs the kernels of the host-driven block loop
+    in the same order: identical iterates, per-column iteration counts and residuals
+    (a zero column stays out of the iteration in both)."""
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, form, n, L)
+    B = rhs_vector(83, h.n, nrhs)
+    B[:, 1] = 0.0
+    B = dev(B)
+    Xg, Xh = torch.empty_like(B), torch.empty_like(B)
+    amge.amge_set_graphs(h, True)
+    st_g, ig = amge.amge_pcg_solve(h, B, Xg, precision=prec, nrhs=nrhs)
+    amge.amge_set_graphs(h, False)
+    st_h, ih = amge.amge_pcg_solve(h, B, Xh, precision=prec, nrhs=nrhs)
+    amge.amge_set_graphs(h, True)
+    assert st_g == st_h == amge.AMGE_OK
+    assert [i["iters"] for i in ig] == [i["iters"] for i in ih]
+    assert [i["true_relres"] for i in ig] == [i["true_relres"] for i in ih]
+    assert ig[1]["iters"] == 0 and max(i["true_relres"] for i in ig) <= 1e-8
+    assert torch.equal(Xg, Xh)
+    for maxit in (1, 3):
+        st, info = amge.amge_pcg_solve(h, B, Xg, rtol=1e-14, maxit=maxit, precision=prec, nrhs=nrhs)
+        assert st == amge.AMGE_ENOTCONV
+        assert all(i["iters"] == maxit for c, i in enumerate(info) if c != 1)
+
+
 def test_graph_loop_maxit_and_nonfinite(amge):
     from paper_2107_05613_gb300.inputs import rhs_vector
 
@@ -615,5 +644,5 @@ def test_autotune_report(amge):
     h = upload(amge, "hcurl", 24, 3)
     rep = amge.amge_autotune_report(h)
     assert len(rep) == 2 * 2 * 6
-    assert set(rep.values()) <= {-1, 0, 200, 400, 800, 2, 4, 8, 16, 32}
+    assert set(rep.values()) <= {-1, 0, 200, 400, 800, 1000, 1200, 2, 4, 8, 16, 32}
     assert rep[(0, "fp64", "AG")] >= 0          # H(curl): A G is stored (much sparser than A)

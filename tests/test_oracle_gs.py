@@ -88,9 +88,11 @@ def _dense_B(o):
     return np.column_stack([o.apply(e) for e in np.eye(n)])
 
 
-@pytest.mark.parametrize("form,n,L", [("hcurl", 2, 2), ("hdiv", 2, 2), ("hcurl", 4, 3)])
-def test_vcycle_with_gs_is_spd_and_contractive(form, n, L):
-    o = OracleHierarchy.from_hierarchy(hierarchy(form, n, L, True), smoother="gs")
+@pytest.mark.parametrize("form,n,L,gs_levels", [("hcurl", 2, 2, None), ("hdiv", 2, 2, None), ("hcurl", 4, 3, None),
+                                                 ("hdiv", 4, 3, 1)])
+def test_vcycle_with_gs_is_spd_and_contractive(form, n, L, gs_levels):
+    """All smoothing levels with Gauss-Seidel, or the finest only (l1-Jacobi below)."""
+    o = OracleHierarchy.from_hierarchy(hierarchy(form, n, L, True), smoother="gs", gs_levels=gs_levels)
     B = _dense_B(o)
     assert np.abs(B - B.T).max() <= 1e-10 * np.abs(B).max()
     ev = np.linalg.eigvals(B @ o.A[0].toarray())
