@@ -161,6 +161,23 @@ typedef struct {
  * otherwise as amge_upload_levels.  On error *out is NULL. */
 amge_status amge_setup_upload(const amge_problem* problem, void* stream, amge_hier** out);
 
+/* New coefficients for a hierarchy made by amge_setup_upload, re-set up on the GPU.
+ * The prolongators P_l and exterior derivatives G_l do not depend on the coefficients
+ * (the local extensions of eqs. 3.6/3.8 use unweighted masses), so only the Galerkin
+ * operators change: A_0 is re-assembled on the device from the per-tetrahedron beta
+ * and alpha (host double [6 n^3] each as in amge_problem, NULL = ones), then
+ * A_{l+1} = P_l^T A_l P_l (Section 3.2.1), the l1 diagonals of A_l and of
+ * G_l^T A_l G_l, the stored A_l G_l, the FP32 copies and the sliced-ELL values are
+ * recomputed on the device, and the coarsest Cholesky factor and inverse on the host
+ * from the new A_L.  Kernel choices and captured graphs are kept; Gauss-Seidel data
+ * (amge_set_smoother) are rebuilt.  Synchronises `stream`; no solve on h or on a
+ * server slot of h may be in flight.  Results equal a fresh amge_setup_upload with
+ * these coefficients up to the summation order of the products.
+ * Errors: AMGE_EINVAL for NULL h, a hierarchy not made by amge_setup_upload (or with
+ * fewer than two levels), a view, or a coefficient that is not positive and finite;
+ * AMGE_EINVAL if the new coarsest matrix is not SPD; AMGE_ECUDA. */
+amge_status amge_update_coefficients(amge_hier* h, const double* beta, const double* alpha, void* stream);
+
 /* Upload a hierarchy serialized in the blob format below (the same bytes the CPU
  * oracle reads).  The blob is only read; it may be freed after return.  Little-
  * endian, every section starting at a multiple of 8 bytes from the blob's start:

@@ -87,6 +87,7 @@ _SIGS = {
     "amge_autotune_report_mm": [_vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)],
     "amge_set_kernel_mm": [_vp, _i32, _i32, _i32, _i32, _i32],
     "amge_set_smoother": [_vp, _i32, _i32, _i32],
+    "amge_update_coefficients": [_vp, _vp, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -454,3 +455,19 @@ def amge_set_smoother(h: Hier, smoother: int, sweeps: int = 2, gs_levels: int = 
     """AMGE_SMOOTHER_L1_JACOBI, or AMGE_SMOOTHER_SYM_GS (`sweeps` symmetric Gauss-Seidel
     steps per smoothing) on the gs_levels finest smoothing levels."""
     _check(_lib.amge_set_smoother(h.handle, smoother, sweeps, gs_levels), "amge_set_smoother")
+
+
+def amge_update_coefficients(h: Hier, beta=None, alpha=None, stream=None):
+    """New per-tetrahedron coefficients for a hierarchy made by amge_setup_upload (GPU
+    re-setup of the Galerkin operators; see include/amge.h)."""
+    keep = []
+
+    def ptr(c):
+        if c is None:
+            return None
+        a = np.ascontiguousarray(c, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data
+
+    _check(_lib.amge_update_coefficients(h.handle, ptr(beta), ptr(alpha), _stream(stream)),
+           "amge_update_coefficients")

@@ -22,7 +22,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CUDA_SOURCES = ["amge_api.cu", "amge_kernels.cu", "amge_kernels_mm.cu", "amge_server.cu", "amge_host_setup.cpp",
-                "amge_noalloc.cu", "amge_setup.cpp", "amge_probe.cu", "../inputs/amge_hierarchy.cpp"]
+                "amge_noalloc.cu", "amge_setup.cpp", "amge_probe.cu", "amge_update.cu", "../inputs/amge_hierarchy.cpp"]
 INPUTS = os.path.join(PKG, "inputs")
 
 

@@ -8,122 +8,16 @@
 #include <type_traits>
 #include <utility>
 
-#include "amge_internal.h"
+#include "amge_hier.h"
 
 namespace amge {
 
 thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
-constexpr int kNumTuneCodes = 11;  // candidates of the single-vector autotuner (kTuneCodes)
-
-template <typename V>
-struct LevelDev {
-  int n = 0, naux = 0;
-  DevSell<V> A, P, PT, G, GT;
-  DevCsr<V> cA, cP, cPT, cG, cGT;  // CSR copies for the multi-RHS products
-  // A G (n x naux), stored where it is much sparser than A: the residual after an aux
-  // sweep is then updated as r - (A G) y instead of recomputed as b - A x
-  DevSell<V> AG;
-  DevCsr<V> cAG;
-  bool use_ag = false;
-  // G sign-coded with two entries per row in row order (the discrete gradient), for
-  // the fused aux correction (launch_ag_fused); null where G has another shape
-  int2* g2 = nullptr;
-  // autotuned single-vector kernel per operator (A, P, PT, G, GT, AG): 0 = sliced
-  // ELL, 100 w = sliced ELL with w warps per slice, 2..32 = vector CSR with that many
-  // lanes per row, -1 = not stored
-  int lanes[6] = {0, 0, 0, 0, 0, -1};
-  // the autotuner's measured time per launch (us) of each candidate (kTuneCodes
-  // order), -1 where not measured
-  float tune_us[6][kNumTuneCodes] = {};
-  // block (multi-right-hand-side) kernel per operator and column count: -1 = not
-  // tuned yet, 0 = CSR, 1 / 2 = sliced ELL with 1 / 2 vectors of 16 bytes per lane
-  int8_t mmk[6][kMaxRhs + 1];
-  float mm_us[6][3] = {};  // the block tuner's time per launch (us) of each form, last tuned nrhs
-  // Gauss-Seidel smoother (amge_set_smoother; FP64): A_l and A_aux = G^T A_l G with
-  // rows grouped by colour (colour k: slices [cs[k], cs[k+1])), 1 / diagonal
-  DevSell<V> gsA, gsX;
-  std::vector<int> gsA_cs, gsX_cs;
-  V *gsA_dinv = nullptr, *gsX_dinv = nullptr;
-  V* t = nullptr;  // aux right-hand side G^T r of the Gauss-Seidel aux smoothing
-  V* minv = nullptr;
-  V* mauxinv = nullptr;
-  V *x = nullptr, *r = nullptr, *y = nullptr, *tmp = nullptr;
-  V *b = nullptr, *z = nullptr;
-  // block workspace ([n][nrhs] / [naux][nrhs]), allocated on the first multi-RHS call
-  V *X = nullptr, *R = nullptr, *Y = nullptr, *T = nullptr, *B = nullptr, *Z = nullptr;
-  LevelDev() { std::memset(mmk, -1, sizeof(mmk)); }
-};
-
 }  // namespace amge
 
 using namespace amge;
-
-struct ProfRec {
-  int cls;
-  cudaEvent_t a, b;
-};
-
-// PCG loop captured once per precision: a WHILE conditional node whose body is one
-// rotated iteration (z = B r, beta, p = z + beta p, q = A p, alpha, x and r updates,
-// loop test), so a whole run of iterations needs no host round trip.
-struct GraphPcg {
-  bool built = false;
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraphConditionalHandle hw{};
-  int64_t body[AMGE_PROF_CLASSES] = {};  // kernel launches of one body replay, per class
-};
-
-struct amge_hier {
-  int form = 0, L = 0, nu_pre = 1, nu_post = 1;
-  // smoother: AMGE_SMOOTHER_L1_JACOBI, or AMGE_SMOOTHER_SYM_GS on the gs_levels finest
-  // smoothing levels (sweeps symmetric steps per smoothing; l1-Jacobi below them)
-  int smoother = AMGE_SMOOTHER_L1_JACOBI, sweeps = 2, gs_levels = 0, gs_built = 0;
-  int n0 = 0;
-  int device = -1;  // CUDA device the operators live on (current at upload)
-  std::vector<LevelDev<double>> lv64;
-  std::vector<LevelDev<float>> lv32;
-  DevSell<double> A0;  // finest operator for the outer PCG
-  DevCsr<double> cA0;  // its CSR copy (multi-RHS products)
-  int nC = 0;
-  double *Linv = nullptr, *LinvT = nullptr, *ct = nullptr;
-  double* Ainv = nullptr;  // explicit coarsest inverse (single-vector V-cycles)
-  double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
-  double *stage_b = nullptr, *stage_x = nullptr;
-  float *s32_in = nullptr, *s32_out = nullptr;
-  RedScratch red;
-  RedScratchMM redmm;
-  int mm_cap = 0;  // nrhs the block workspace was sized for
-  bool mm_tuned[2][kMaxRhs + 1] = {};  // block kernels timed for (precision, nrhs)
-  GraphPcg gmm[2][kMaxRhs + 1];        // captured block PCG loops per (precision, nrhs)
-  int* gstate_mm = nullptr;            // device: iterations done, maxit, non-finite flag
-  int* pinned_state_mm = nullptr;
-  double* GX = nullptr;                // block iterate of the graph-driven loop
-  double *PR = nullptr, *PZ = nullptr, *PP = nullptr, *PQ = nullptr, *SB = nullptr, *SX = nullptr;
-  float *S32in = nullptr, *S32out = nullptr;
-  double* CT = nullptr;
-  double* pinned_mm = nullptr;  // [SC_COUNT][kMaxRhs]
-  double* pinned = nullptr;
-  cudaEvent_t ev = nullptr;
-  GraphPcg gpcg[2];
-  cudaStream_t cap = nullptr;  // capture stream of the graphs
-  int* gstate = nullptr;       // device: iterations done, maxit, non-finite flag
-  double* gx = nullptr;        // device: iterate of the graph-driven loop
-  int* pinned_state = nullptr;
-  bool use_graphs = true;
-  std::vector<void*> allocs;
-  size_t bytes = 0;     // device bytes this object allocated
-  size_t op_bytes = 0;  // of which level operators (0 for a view)
-  const amge_hier* base = nullptr;  // the hierarchy whose operators a view shares
-  bool prof = false;
-  std::vector<ProfRec> prof_pending;
-  std::vector<cudaEvent_t> prof_free;
-  int64_t prof_count[AMGE_PROF_CLASSES] = {};
-  int64_t launches[AMGE_PROF_CLASSES] = {};  // launches of each class, counted always
-  double prof_ms[AMGE_PROF_CLASSES] = {};
-};
 
 namespace {
 
@@ -2545,6 +2439,36 @@ void drop_graphs(amge_hier* h) {
 
 }  // namespace
 
+amge_status amge_update_coefficients(amge_hier* h, const double* beta, const double* alpha, void* stream) {
+  if (!h) {
+    set_error("NULL hierarchy");
+    return AMGE_EINVAL;
+  }
+  if (!h->upd || h->base) {
+    set_error("coefficient updates need a hierarchy made by amge_setup_upload (not a view)");
+    return AMGE_EINVAL;
+  }
+  for (const double* c : {beta, alpha})
+    if (c)
+      for (int i = 0; i < h->ncell; i++)
+        if (!(c[i] > 0.0) || !std::isfinite(c[i])) {
+          set_error("coefficients must be positive and finite");
+          return AMGE_EINVAL;
+        }
+  cudaStream_t s = as_stream(stream);
+  amge_status st = update_coefficients(h, beta, alpha, s);
+  if (st) return st;
+  // the Gauss-Seidel data hold copies of A_l and G^T A_l G: rebuild the levels built
+  const int built = h->gs_built;
+  h->gs_built = 0;
+  for (int l = 0; l < built; l++) {
+    st = build_gs_level(h, l, s);
+    if (st) return st;
+    h->gs_built = l + 1;
+  }
+  return AMGE_OK;
+}
+
 amge_status amge_set_smoother(amge_hier* h, int32_t smoother, int32_t sweeps, int32_t gs_levels) {
   if (!h || (smoother != AMGE_SMOOTHER_L1_JACOBI && smoother != AMGE_SMOOTHER_SYM_GS) || sweeps < 1 ||
       sweeps > 8 || gs_levels < 0) {
@@ -2613,6 +2537,7 @@ void amge_hier_free(amge_hier* h) {
     if (G.g) cudaGraphDestroy(G.g);
   }
   drop_graphs_mm(h);
+  if (h->upd) free_update_plan(h->upd);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->pinned_state) cudaFreeHost(h->pinned_state);
   if (h->pinned_state_mm) cudaFreeHost(h->pinned_state_mm);

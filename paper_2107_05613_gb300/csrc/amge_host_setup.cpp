@@ -341,24 +341,27 @@ HostSell build_sell_coloured(const HostCsr& M, const std::vector<int>& colour, i
 HostCsr symbolic_product(const HostCsr& A, const HostCsr& B) {
   HostCsr C;
   C.nr = A.nr, C.nc = B.nc;
-  C.rp.assign(A.nr + 1, 0);
-  std::vector<char> seen(B.nc, 0);
-  std::vector<int> touched;
-  for (int i = 0; i < A.nr; i++) {
-    touched.clear();
-    for (int p = A.rp[i]; p < A.rp[i + 1]; p++)
-      for (int q = B.rp[A.ci[p]]; q < B.rp[A.ci[p] + 1]; q++) {
-        const int j = B.ci[q];
-        if (!seen[j]) seen[j] = 1, touched.push_back(j);
-      }
-    std::sort(touched.begin(), touched.end());
-    for (int j : touched) {
-      C.ci.push_back(j);
-      C.v.push_back(1.0);
-      seen[j] = 0;
+  std::vector<std::vector<int>> rows(A.nr);
+#pragma omp parallel
+  {
+    std::vector<char> seen(B.nc, 0);
+#pragma omp for schedule(dynamic, 512)
+    for (int i = 0; i < A.nr; i++) {
+      std::vector<int>& touched = rows[i];
+      for (int p = A.rp[i]; p < A.rp[i + 1]; p++)
+        for (int q = B.rp[A.ci[p]]; q < B.rp[A.ci[p] + 1]; q++) {
+          const int j = B.ci[q];
+          if (!seen[j]) seen[j] = 1, touched.push_back(j);
+        }
+      std::sort(touched.begin(), touched.end());
+      for (int j : touched) seen[j] = 0;
     }
-    C.rp[i + 1] = (int)C.ci.size();
   }
+  C.rp.assign(A.nr + 1, 0);
+  for (int i = 0; i < A.nr; i++) C.rp[i + 1] = C.rp[i] + (int)rows[i].size();
+  C.ci.resize(C.rp[A.nr]);
+  C.v.assign(C.rp[A.nr], 1.0);
+  for (int i = 0; i < A.nr; i++) std::copy(rows[i].begin(), rows[i].end(), C.ci.begin() + C.rp[i]);
   return C;
 }
 

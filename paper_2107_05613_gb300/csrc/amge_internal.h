@@ -381,6 +381,22 @@ HostSell build_sell_coloured(const HostCsr& M, const std::vector<int>& colour, i
 // Pattern of A B (structural: every product term counts, whatever its value).
 HostCsr symbolic_product(const HostCsr& A, const HostCsr& B);
 
+// Fine-level assembly of A_0 as a gather (see amgh_fine_assembly_copy): element
+// matrices K (derivative term) and M (mass term) of the six Kuhn shapes, s x s each,
+// and per stored entry of A_0 its contributions (cell, local entry index).
+struct FineAssembly {
+  int ncell = 0, s = 0;
+  std::vector<double> K, M;
+  std::vector<int32_t> coff, ccell;
+  std::vector<uint8_t> cidx;
+};
+struct UpdatePlan;
+// Device data for amge_update_coefficients (patterns of the Galerkin products, the
+// sliced-ELL maps, the assembly gather); kept in h->upd.
+amge_status prepare_update(amge_hier* h, const FineAssembly& fa, cudaStream_t s);
+amge_status update_coefficients(amge_hier* h, const double* beta, const double* alpha, cudaStream_t s);
+void free_update_plan(UpdatePlan* p);
+
 // Read-only view of a hierarchy's coarsest factor and the device it lives on
 // (defined in amge_api.cu).
 void coarse_factor_view(const amge_hier* h, int* n, const double** Linv, const double** LinvT, int* device);

@@ -144,7 +144,33 @@ extern "C" amge_status amge_setup_upload(const amge_problem* p, void* stream, am
   d.G = gg.data();
   d.nu_pre = p->nu_pre;
   d.nu_post = p->nu_post;
-  return amge_upload_levels(&d, stream, out);
+  amge_status st = amge_upload_levels(&d, stream, out);
+  if (st != AMGE_OK || L < 2) return st;
+  // data for amge_update_coefficients: the fine assembly as a gather (the upload
+  // keeps every stored entry of A_l: the generator stores no zeros in them)
+  bool zeros = false;
+  for (int l = 0; l < L; l++)
+    for (double v : A[l].v) zeros |= (v == 0.0);
+  if (zeros) return AMGE_OK;  // updates stay unavailable (amge_update_coefficients: AMGE_EINVAL)
+  amge::FineAssembly fa;
+  int64_t nct = 0;
+  int s = 0;
+  if (amgh_fine_assembly_info(g.h, &nct, &s) != 0) return AMGE_OK;
+  fa.ncell = (int)ntet, fa.s = s;
+  fa.K.resize(6 * s * s), fa.M.resize(6 * s * s);
+  fa.coff.resize(A[0].v.size() + 1), fa.ccell.resize(nct), fa.cidx.resize(nct);
+  if (amgh_fine_assembly_copy(g.h, fa.K.data(), fa.M.data(), fa.coff.data(), fa.ccell.data(), fa.cidx.data()) != 0) {
+    amge::set_error(std::string("fine assembly map: ") + amgh_error());
+    amge_hier_free(*out);
+    *out = nullptr;
+    return AMGE_EINVAL;
+  }
+  st = amge::prepare_update(*out, fa, static_cast<cudaStream_t>(stream));
+  if (st != AMGE_OK) {
+    amge_hier_free(*out);
+    *out = nullptr;
+  }
+  return st;
 }
 
 extern "C" amge_status amge_upload_blob(const void* blob, size_t bytes, void* stream, amge_hier** out) {

@@ -1358,6 +1358,76 @@ int amgh_diagnostics(const void* h, double out[4]) {
   return 0;
 }
 
+// Fine-level assembly of A_0 as a gather: for every stored entry of A_0 (the CSR order
+// of amgh_matrix_copy) the cells that add to it and the local entry each adds, in the
+// order assemble_global adds them (cells ascending), and the element matrices of the
+// six Kuhn shapes (cell c has shape c % 6).
+int amgh_fine_assembly_info(const void* h, int64_t* ncontrib, int* local_size) {
+  if (!h) return 1;
+  const Hier* H = (const Hier*)h;
+  const Level& L = H->levels[0];
+  const int kf = H->form_k;
+  const Adj& cl = L.clo[3][kf];
+  int64_t n = 0;
+  for (int c = 0; c < cl.rows(); c++) n += (int64_t)cl.len(c) * cl.len(c);
+  *ncontrib = n;
+  *local_size = kf == 1 ? 6 : 4;
+  return 0;
+}
+
+int amgh_fine_assembly_copy(const void* h, double* K, double* M, int32_t* coff, int32_t* ccell, uint8_t* cidx) {
+  try {
+    if (!h) return 1;
+    const Hier* H = (const Hier*)h;
+    const Level& L = H->levels[0];
+    const int kf = H->form_k;
+    const int s2 = kf == 1 ? 36 : 16;
+    for (int sh = 0; sh < 6; sh++) {
+      const TetMats& t = L.perm_mats[sh];
+      std::copy(kf == 1 ? t.K1 : t.K2, (kf == 1 ? t.K1 : t.K2) + s2, K + sh * s2);
+      std::copy(kf == 1 ? t.M1 : t.M2, (kf == 1 ? t.M1 : t.M2) + s2, M + sh * s2);
+    }
+    const int nr = (int)L.cnt[kf];
+    const Adj& cl = L.clo[3][kf];
+    Adj tr = transpose_adj(cl, nr);
+    const DCsr& A = H->A[0];
+    // contributions per row, then stably by column, as in assemble_global
+    std::vector<int64_t> rowoff(nr + 1, 0);
+    for (int r = 0; r < nr; r++) {
+      int64_t k = 0;
+      for (int64_t p = tr.rp[r]; p < tr.rp[r + 1]; p++) k += cl.len(tr.ci[p]);
+      rowoff[r + 1] = rowoff[r] + k;
+    }
+    REQUIRE(rowoff[nr] < (int64_t)INT32_MAX, "too many assembly contributions for 32-bit offsets");
+    std::vector<int32_t> count(A.a.rp[nr], 0);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int r = 0; r < nr; r++) {
+      struct C { int col, cell, idx; };
+      std::vector<C> acc;
+      for (int64_t p = tr.rp[r]; p < tr.rp[r + 1]; p++) {
+        const int c = tr.ci[p];
+        const int sz = cl.len(c);
+        const int li = cl.find(c, r);
+        for (int j = 0; j < sz; j++) acc.push_back({cl.row(c)[j], c, li * sz + j});
+      }
+      std::stable_sort(acc.begin(), acc.end(), [](const C& a, const C& b) { return a.col < b.col; });
+      int64_t q = A.a.rp[r];
+      for (size_t i = 0; i < acc.size(); i++) {
+        if (i > 0 && acc[i].col != acc[i - 1].col) q++;
+        count[q]++;
+        ccell[rowoff[r] + i] = acc[i].cell;
+        cidx[rowoff[r] + i] = (uint8_t)acc[i].idx;
+      }
+    }
+    coff[0] = 0;
+    for (int64_t q = 0; q < A.a.rp[nr]; q++) coff[q + 1] = coff[q] + count[q];
+    return 0;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return 1;
+  }
+}
+
 void amgh_free(void* h) { delete (Hier*)h; }
 
 }  // extern "C"

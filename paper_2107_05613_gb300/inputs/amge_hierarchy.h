@@ -56,6 +56,17 @@ int amgh_matrix_copy(const void* h, int kind, int level, int k, int32_t* row_ptr
  *              [2] max disagreement of coarse incidence over constituent choices,
  *              [3] setup seconds */
 int amgh_diagnostics(const void* h, double out[4]);
+/* Fine-level assembly of the problem matrix A_0 written as a gather, for re-assembling
+ * it from new coefficients: every stored entry q of A_0 (the CSR order of
+ * amgh_matrix_copy) is the sum, in order, of
+ *   beta[c] K[(c % 6) * s*s + idx] + alpha[c] M[(c % 6) * s*s + idx]
+ * over its contributions t = coff[q] .. coff[q+1]-1 with c = ccell[t], idx = cidx[t]
+ * (s = local_size: 6 edges (H(curl)) or 4 faces (H(div)) per cell; K = the derivative
+ * term's element matrix, M = the mass term's, of the six Kuhn shapes).
+ * info: *ncontrib = total contributions.  copy: K, M [6*s*s]; coff [nnz+1];
+ * ccell, cidx [ncontrib]. */
+int amgh_fine_assembly_info(const void* h, int64_t* ncontrib, int* local_size);
+int amgh_fine_assembly_copy(const void* h, double* K, double* M, int32_t* coff, int32_t* ccell, uint8_t* cidx);
 void amgh_free(void* h);
 
 #ifdef __cplusplus

@@ -45,6 +45,8 @@ def _load():
     lib.amgh_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
     lib.amgh_free.argtypes = [ctypes.c_void_p]
     lib.amgh_free.restype = None
+    lib.amgh_fine_assembly_info.argtypes = [ctypes.c_void_p, i64p, ctypes.POINTER(ctypes.c_int)]
+    lib.amgh_fine_assembly_copy.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 5
     _lib = lib
     return lib
 
@@ -110,11 +112,13 @@ def _copy(lib, h, kind, level, k):
 
 
 def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=None,
-                    all_spaces: bool = False, nthreads: int = 0) -> Hierarchy:
+                    all_spaces: bool = False, nthreads: int = 0, assembly: bool = False) -> Hierarchy:
     """Build the hierarchy on an n^3 Kuhn-split cube (6 n^3 tetrahedra).
 
     beta, alpha: per-tet coefficients of (Du, Dv) and (u, v) (None = 1).
     num_levels: 0 = coarsen 2x2x2 while the cell grid side m > 8.
+    assembly: also return the fine assembly of A_0 as a gather (diagnostics
+    "assembly": dict of K, M [6, s, s], coff, ccell, cidx; see amge_hierarchy.h).
     """
     lib = _load()
     kf = FORMS[form]
@@ -145,6 +149,19 @@ def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=Non
         d = (ctypes.c_double * 4)()
         lib.amgh_diagnostics(h, d)
         diag = {"lambda_dev": d[0], "local_residual": d[1], "incidence_dev": d[2], "seconds": d[3]}
+        if assembly:
+            nct, sz = ctypes.c_int64(), ctypes.c_int()
+            assert lib.amgh_fine_assembly_info(h, ctypes.byref(nct), ctypes.byref(sz)) == 0
+            s_ = sz.value
+            K = np.empty((6, s_, s_)); M = np.empty((6, s_, s_))
+            coff = np.empty(A[0].nnz + 1, np.int32)
+            ccell = np.empty(nct.value, np.int32)
+            cidx = np.empty(nct.value, np.uint8)
+            rc = lib.amgh_fine_assembly_copy(h, K.ctypes.data, M.ctypes.data, coff.ctypes.data, ccell.ctypes.data,
+                                             cidx.ctypes.data)
+            if rc != 0:
+                raise RuntimeError("fine assembly map: " + lib.amgh_error().decode())
+            diag["assembly"] = dict(K=K, M=M, coff=coff, ccell=ccell, cidx=cidx, s=s_)
     finally:
         lib.amgh_free(h)
     return Hierarchy(form, n, A, P, G, counts, P_all, D_all, diag)
