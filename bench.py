@@ -739,32 +739,42 @@ def run_serving(args, amge, n_requests=1000, load=0.7, seed=2107056135, max_slot
     for t, _ in warm:
         amge.amge_wait(sv, t)
     cap = len(warm) / (time.perf_counter() - t0)
-    # open loop: Poisson arrivals at load x capacity
-    lam = load * cap
-    gaps = rng.exponential(1.0 / lam, n_requests)
-    t_start = time.perf_counter()
-    t_next = t_start
-    live, lat, nrhs_tot, bad = [], [], 0, 0
-    for (j, k), g in zip(reqs, gaps):
-        t_next += g
-        while time.perf_counter() < t_next:
-            pass
-        live.append(submit(j, k))
-        nrhs_tot += k
-    for t, _ in live:
-        st, infos = amge.amge_wait(sv, t)
-        lat.append(infos[0]["time_ms"])
-        bad += st != amge.AMGE_OK
-    t_end = time.perf_counter()
+    def open_loop(ld):
+        """Poisson arrivals at ld x capacity; latency = submit to result."""
+        lam = ld * cap
+        gaps = rng.exponential(1.0 / lam, n_requests)
+        t_start = time.perf_counter()
+        t_next = t_start
+        live, lat, nrhs_tot, bad = [], [], 0, 0
+        for (j, k), g in zip(reqs, gaps):
+            t_next += g
+            while time.perf_counter() < t_next:
+                pass
+            live.append(submit(j, k))
+            nrhs_tot += k
+        for t, _ in live:
+            st, infos = amge.amge_wait(sv, t)
+            lat.append(infos[0]["time_ms"])
+            bad += st != amge.AMGE_OK
+        t_end = time.perf_counter()
+        return {"arrival_rate_req_per_s": lam, "load": ld, "rhs_total": nrhs_tot,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "mean": float(np.mean(lat))},
+                "solves_per_s": nrhs_tot / (t_end - t_start), "requests_per_s": n_requests / (t_end - t_start),
+                "failed": int(bad)}
+
+    main = open_loop(load)
+    # overload: arrivals faster than the closed-loop capacity; queues grow, latency
+    # with them, every request still completes
+    over = open_loop(1.2)
     stats = amge.amge_server_stats(sv)
     sv.destroy()
     return {
-        "requests": n_requests, "rhs_total": nrhs_tot, "precision": args.precision_serve,
-        "arrival_rate_req_per_s": lam, "closed_loop_capacity_req_per_s": cap, "load": load,
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "mean": float(np.mean(lat))},
-        "solves_per_s": nrhs_tot / (t_end - t_start), "requests_per_s": n_requests / (t_end - t_start),
-        "failed": int(bad), "max_slots": max_slots, "slots_at_end": stats["slots"],
+        "requests": n_requests, "rhs_total": main["rhs_total"], "precision": args.precision_serve,
+        "arrival_rate_req_per_s": main["arrival_rate_req_per_s"], "closed_loop_capacity_req_per_s": cap,
+        "load": load, "latency_ms": main["latency_ms"], "solves_per_s": main["solves_per_s"],
+        "requests_per_s": main["requests_per_s"], "failed": main["failed"], "overload": over,
+        "max_slots": max_slots, "slots_at_end": stats["slots"],
         "slot_bytes_at_end": stats["bytes_in_use"], "pool_setup_s": t_setup,
         "workload": "1000 requests, Poisson arrivals; each an H(curl) or H(div) problem on an n^3 Kuhn mesh, "
                     "n in {16,24,32,48}, beta constant per problem log-uniform [1e-2,1e2] (16-problem resident "

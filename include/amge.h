@@ -468,13 +468,17 @@ amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int3
 /* Kernel choice of the block (multi-right-hand-side) products for nrhs columns (2 ..
  * 32) and one precision, per smoothing level and operator (op order as above):
  * codes[l * 6 + op] = 0 CSR (a lane group per row), 1 / 2 sliced ELL with one / two
- * 16-byte vectors of columns per lane, -1 not stored or not tuned yet.  The library
- * times the forms per operator on the first block call with that nrhs and keeps the
- * fastest; us (optional, [levels-1][6][3]) receives the measured time per launch
- * (microseconds) of each form, -1 where not measured. */
+ * 16-byte vectors of columns per lane, -1 not stored or not tuned yet; and for the
+ * coarsest product Z = A_L^{-1} B, codes[(levels-1) * 6] = 0 CUDA cores, 1 the FP64
+ * tensor cores (mma.sync m8n8k4; nrhs a multiple of 8).  The library times the forms
+ * per operator on the first block call with that nrhs and keeps the fastest; us
+ * (optional) receives the measured time per launch (microseconds) of each form,
+ * us[(l * 6 + op) * 3 + form], and the coarsest's two at us[(levels-1) * 18 + 0 / 1];
+ * -1 where not measured.  codes holds (levels-1)*6 + 1 entries, us 3 times as many. */
 amge_status amge_autotune_report_mm(amge_hier* h, int32_t nrhs, int32_t precision, int32_t* codes, float* us);
 
-/* Pin one block kernel choice (code as above); AMGE_EINVAL where the sliced-ELL form
+/* Pin one block kernel choice (code as above); op = 6 pins the coarsest product (level
+ * ignored; code 1 needs nrhs a multiple of 8).  AMGE_EINVAL where the sliced-ELL form
  * does not apply to nrhs (nrhs must be a multiple of code * 16 / sizeof(value), at
  * most 8 lanes per row).  Pinned choices are not re-tuned. */
 amge_status amge_set_kernel_mm(amge_hier* h, int32_t level, int32_t precision, int32_t op, int32_t nrhs,

@@ -437,17 +437,22 @@ _OPS = ["A", "P", "PT", "G", "GT", "AG"]
 def amge_autotune_report_mm(h: Hier, nrhs: int, precision: int = AMGE_FP32_VCYCLE):
     """({(level, op): code}, {(level, op): [us CSR, us sliced ELL x1, us x2]}) of the block
     products for nrhs columns: 0 = CSR, 1 / 2 = sliced ELL with 1 / 2 vectors per lane,
-    -1 = not stored / not tuned yet."""
+    -1 = not stored / not tuned yet; key (levels-1, "coarse"): the coarsest product, 0 =
+    CUDA cores, 1 = FP64 tensor cores, with [us CUDA cores, us tensor cores]."""
     L = h.levels
-    codes = (_i32 * max((L - 1) * 6, 1))()
-    us = (ctypes.c_float * max((L - 1) * 18, 1))()
+    codes = (_i32 * ((L - 1) * 6 + 1))()
+    us = (ctypes.c_float * ((L - 1) * 18 + 3))()
     _check(_lib.amge_autotune_report_mm(h.handle, nrhs, precision, codes, us), "amge_autotune_report_mm")
-    return ({(l, _OPS[o]): int(codes[l * 6 + o]) for l in range(L - 1) for o in range(6)},
-            {(l, _OPS[o]): [float(us[(l * 6 + o) * 3 + k]) for k in range(3)] for l in range(L - 1) for o in range(6)})
+    c = {(l, _OPS[o]): int(codes[l * 6 + o]) for l in range(L - 1) for o in range(6)}
+    t = {(l, _OPS[o]): [float(us[(l * 6 + o) * 3 + k]) for k in range(3)] for l in range(L - 1) for o in range(6)}
+    c[(L - 1, "coarse")] = int(codes[(L - 1) * 6])      # 0 CUDA cores, 1 FP64 tensor cores
+    t[(L - 1, "coarse")] = [float(us[(L - 1) * 18 + k]) for k in range(2)]
+    return c, t
 
 
 def amge_set_kernel_mm(h: Hier, level: int, precision: int, op, nrhs: int, code: int):
-    o = _OPS.index(op) if isinstance(op, str) else op
+    """op "coarse" (6): the coarsest product, code 0 CUDA cores / 1 FP64 tensor cores."""
+    o = (6 if op == "coarse" else _OPS.index(op)) if isinstance(op, str) else op
     _check(_lib.amge_set_kernel_mm(h.handle, level, precision, o, nrhs, code), "amge_set_kernel_mm")
 
 

@@ -454,7 +454,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
 // already in the level-0 x (and, for the FP32 V-cycle, r already cast into the
 // level-0 b) -- written by the PCG axpy that produced r (pcg_x0_out).
 void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, cudaStream_t s,
-                       bool x0_ready = false) {
+                       bool x0_ready = false, bool z32_only = false) {
   if (precision == AMGE_FP64) {
     if (h->L == 1) {
       Prof p(h, AMGE_PROF_COARSE, s);
@@ -474,6 +474,7 @@ void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, 
     } else {
       vcycle_level<float>(h, 0, d.b, d.z, s, x0_ready);
     }
+    if (z32_only) return;  // the PCG kernels widen the level-0 z themselves
     Prof p(h, AMGE_PROF_PCG_VEC, s);
     launch_cast<float, double>(h->n0, d.z, z, s);
   }
@@ -535,10 +536,16 @@ amge_status build_pcg_graph(amge_hier* h, int prec) {
   CK(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   // every body starts from an r produced by the axpy (or by the restart after a true
   // residual), which already began the level-0 sweep
-  vcycle_fp64_iface(h, h->pr, h->pz, prec, h->cap, h->L > 1);
-  const int flexible = prec == AMGE_FP32_VCYCLE ? 1 : 0;
-  launch_pcg_dots(n, h->pr, h->pz, h->pq, flexible, h->red, h->cap);
-  launch_pcg_update_p(n, h->pp, h->pz, h->red, h->cap);
+  const bool f32 = prec == AMGE_FP32_VCYCLE;
+  vcycle_fp64_iface(h, h->pr, h->pz, prec, h->cap, h->L > 1, f32);
+  const int flexible = f32 ? 1 : 0;
+  if (f32) {
+    launch_pcg_dots<float>(n, h->pr, h->lv32[0].z, h->pq, flexible, h->red, h->cap);
+    launch_pcg_update_p<float>(n, h->pp, h->lv32[0].z, h->red, h->cap);
+  } else {
+    launch_pcg_dots<double>(n, h->pr, h->pz, h->pq, flexible, h->red, h->cap);
+    launch_pcg_update_p<double>(n, h->pp, h->pz, h->red, h->cap);
+  }
   launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, h->cap);
   launch_pcg_axpy_norm(n, h->gx, h->pr, h->pp, h->pq, h->red, h->cap, pcg_x0_out(h, prec));
   launch_pcg_loop_cond(G.hw, n, h->red, h->gstate, h->cap);
@@ -549,7 +556,7 @@ amge_status build_pcg_graph(amge_hier* h, int prec) {
     G.body[c] = h->launches[c] - before[c];
     h->launches[c] = before[c];
   }
-  G.body[AMGE_PROF_PCG_VEC] += 5;   // dots + finish, update_p, axpy_norm, loop test
+  G.body[AMGE_PROF_PCG_VEC] += 5;   // dots + finish, update_p, axpy_norm, loop test (FP32: no cast)
   G.body[AMGE_PROF_PCG_SPMV] += 2;  // q = A p + finish
   if (e != cudaSuccess) {
     set_error(std::string("graph capture: ") + cudaGetErrorString(e));
@@ -872,7 +879,9 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
   auto& lv = levels<V>(h);
   if (l == h->L - 1) {
     Prof p(h, AMGE_PROF_COARSE, s, std::is_same<V, float>::value ? 2 : 1);  // FP32: + the widening
-    launch_coarse_inv_mm<V, V>(h->nC, nrhs, h->Ainv, b, h->CT, z, s);
+    const int pi = std::is_same<V, double>::value ? 0 : 1;
+    if (!(h->coarse_mm[pi][nrhs] == 1 && launch_coarse_inv_mm_dmma<V, V>(h->nC, nrhs, h->Ainv, b, h->CT, z, s)))
+      launch_coarse_inv_mm<V, V>(h->nC, nrhs, h->Ainv, b, h->CT, z, s);
     return;
   }
   LevelDev<V>& d = lv[l];
@@ -1655,6 +1664,44 @@ amge_status tune_mm(amge_hier* h, int nrhs, int precision, cudaStream_t s) {
   }
   for (int l = 0; l + 1 < h->L && st == AMGE_OK; l++)
     st = p == 0 ? autotune_mm_level<double>(h, l, nrhs, ts, e0, e1) : autotune_mm_level<float>(h, l, nrhs, ts, e0, e1);
+  // coarsest product: CUDA cores against the FP64 tensor cores (nrhs a multiple of 8)
+  for (int code = 0; code <= 1 && st == AMGE_OK; code++) {
+    h->coarse_mm_us[p][nrhs][code] = -1.f;
+    if (code == 1 && nrhs % 8 != 0) break;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      st = launch_status();
+      break;
+    }
+    for (int r = 0; r < kTuneReps; r++) {
+      if (p == 0) {
+        LevelDev<double>& c = h->lv64[h->L - 1];
+        if (!(code == 1 && launch_coarse_inv_mm_dmma<double, double>(h->nC, nrhs, h->Ainv, c.B, h->CT, c.Z, ts)))
+          launch_coarse_inv_mm<double, double>(h->nC, nrhs, h->Ainv, c.B, h->CT, c.Z, ts);
+      } else {
+        LevelDev<float>& c = h->lv32[h->L - 1];
+        if (!(code == 1 && launch_coarse_inv_mm_dmma<float, float>(h->nC, nrhs, h->Ainv, c.B, h->CT, c.Z, ts)))
+          launch_coarse_inv_mm<float, float>(h->nC, nrhs, h->Ainv, c.B, h->CT, c.Z, ts);
+      }
+    }
+    cudaError_t ce = cudaStreamEndCapture(ts, &g);
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = time_graph(ge, ts, e0, e1, &ms);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (ce != cudaSuccess) {
+      set_error(std::string("block tuner (coarsest): ") + cudaGetErrorString(ce));
+      st = AMGE_ECUDA;
+      break;
+    }
+    h->coarse_mm_us[p][nrhs][code] = ms * (1e3f / kTuneReps);
+  }
+  if (st == AMGE_OK) {
+    const float* t = h->coarse_mm_us[p][nrhs];
+    h->coarse_mm[p][nrhs] = (t[1] > 0.f && t[1] < t[0]) ? 1 : 0;
+  }
   cudaStreamSynchronize(ts);
   cudaStreamDestroy(ts);
   if (e0) cudaEventDestroy(e0);
@@ -1931,11 +1978,14 @@ amge_status pcg_one(amge_hier* h, const double* b, double* x, const amge_solve_o
     // unless the recursive residual is predicted to be near the tolerance.
     bool spec = true;
     if (rr_prev > 0 && rr_prev2 > 0) spec = rr_prev * (rr_prev / rr_prev2) > 100.0 * tol2;
-    if (spec) {
-      vcycle_fp64_iface(h, h->pr, h->pz, o.precision, s);
+    const bool f32 = o.precision == AMGE_FP32_VCYCLE;
+    auto precondition = [&]() {  // z = B r and the dots (FP32: the level-0 z, widened by the kernels)
+      vcycle_fp64_iface(h, h->pr, h->pz, o.precision, s, false, f32);
       Prof p(h, AMGE_PROF_PCG_VEC, s, 2);
-      launch_pcg_dots(n, h->pr, h->pz, h->pq, flexible, h->red, s);
-    }
+      if (f32) launch_pcg_dots<float>(n, h->pr, h->lv32[0].z, h->pq, flexible, h->red, s);
+      else launch_pcg_dots<double>(n, h->pr, h->pz, h->pq, flexible, h->red, s);
+    };
+    if (spec) precondition();
     CK(cudaEventSynchronize(h->ev));
     const double rr = h->pinned[0];
     if (!finite(rr)) {
@@ -1954,13 +2004,10 @@ amge_status pcg_one(amge_hier* h, const double* b, double* x, const amge_solve_o
       }
       spec = false;  // continue from the true residual
     }
-    if (!spec) {
-      vcycle_fp64_iface(h, h->pr, h->pz, o.precision, s);
-      Prof p(h, AMGE_PROF_PCG_VEC, s, 2);
-      launch_pcg_dots(n, h->pr, h->pz, h->pq, flexible, h->red, s);
-    }
+    if (!spec) precondition();
     Prof p(h, AMGE_PROF_PCG_VEC, s);
-    launch_pcg_update_p(n, h->pp, h->pz, h->red, s);
+    if (f32) launch_pcg_update_p<float>(n, h->pp, h->lv32[0].z, h->red, s);
+    else launch_pcg_update_p<double>(n, h->pp, h->pz, h->red, s);
   }
   if (!converged) {
     resid_true();
@@ -2331,11 +2378,27 @@ amge_status amge_autotune_report_mm(amge_hier* h, int32_t nrhs, int32_t precisio
         for (int k = 0; k < 3; k++)
           us[(l * 6 + op) * 3 + k] = precision == AMGE_FP64 ? h->lv64[l].mm_us[op][k] : h->lv32[l].mm_us[op][k];
     }
+  const int p = precision == AMGE_FP64 ? 0 : 1;
+  const int last = (h->L - 1) * 6;
+  codes[last] = h->mm_tuned[p][nrhs] ? h->coarse_mm[p][nrhs] : -1;
+  if (us) {
+    us[last * 3] = h->coarse_mm_us[p][nrhs][0];
+    us[last * 3 + 1] = h->coarse_mm_us[p][nrhs][1];
+    us[last * 3 + 2] = -1.f;
+  }
   return AMGE_OK;
 }
 
 amge_status amge_set_kernel_mm(amge_hier* h, int32_t level, int32_t precision, int32_t op, int32_t nrhs,
                                int32_t code) {
+  if (h && op == 6 && nrhs >= 2 && nrhs <= kMaxRhs && (code == 0 || (code == 1 && nrhs % 8 == 0)) &&
+      (precision == AMGE_FP64 || precision == AMGE_FP32_VCYCLE)) {  // the coarsest product
+    const int p = precision == AMGE_FP64 ? 0 : 1;
+    h->coarse_mm[p][nrhs] = (int8_t)code;
+    h->mm_tuned[p][nrhs] = true;
+    drop_graphs_mm(h);
+    return AMGE_OK;
+  }
   if (!h || level < 0 || level >= h->L - 1 || op < 0 || op > 5 || nrhs < 2 || nrhs > kMaxRhs || code < 0 ||
       code > 2 || (precision != AMGE_FP64 && precision != AMGE_FP32_VCYCLE)) {
     set_error("invalid level, op, nrhs, code or precision");

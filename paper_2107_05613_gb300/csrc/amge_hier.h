@@ -93,6 +93,10 @@ struct amge_hier {
   RedScratchMM redmm;
   int mm_cap = 0;  // nrhs the block workspace was sized for
   bool mm_tuned[2][kMaxRhs + 1] = {};  // block kernels timed for (precision, nrhs)
+  // block coarsest product Z = A_L^{-1} B per (precision, nrhs): 0 CUDA cores, 1 FP64
+  // tensor cores (DMMA); the tuner's times (us) of both
+  int8_t coarse_mm[2][kMaxRhs + 1] = {};
+  float coarse_mm_us[2][kMaxRhs + 1][2] = {};
   GraphPcg gmm[2][kMaxRhs + 1];        // captured block PCG loops per (precision, nrhs)
   int* gstate_mm = nullptr;            // device: iterations done, maxit, non-finite flag
   int* pinned_state_mm = nullptr;

@@ -212,6 +212,11 @@ void launch_coarse_mm(int n, int nrhs, const double* Linv, const double* LinvT, 
 // Z = A^{-1} B with the explicit inverse (one launch).
 template <typename Tin, typename Tout>
 void launch_coarse_inv_mm(int n, int nrhs, const double* Ainv, const Tin* b, double* t, Tout* z, cudaStream_t s);
+// The same on the FP64 tensor cores (mma.sync m8n8k4); false where nrhs is not a
+// multiple of 8.
+template <typename Tin, typename Tout>
+bool launch_coarse_inv_mm_dmma(int n, int nrhs, const double* Ainv, const Tin* b, double* t, Tout* z,
+                               cudaStream_t s);
 // y = d .* x (elementwise)
 template <typename V>
 void launch_mul(int64_t n, const V* d, const V* x, V* y, cudaStream_t s);
@@ -284,11 +289,14 @@ void launch_pcg_axpy_norm(int64_t n, double* x, double* rv, const double* p, con
                           const RedScratch& r, cudaStream_t s, const X0Out& o = X0Out());
 void launch_pcg_finish_rr(int64_t n, const RedScratch& r, cudaStream_t s);
 // rho_new = r.z, zq = z.q (two launches); beta = rho_new / rho (flexible = 0) or
-// -alpha zq / rho (flexible = 1)
-void launch_pcg_dots(int64_t n, const double* rv, const double* z, const double* q, int flexible,
+// -alpha zq / rho (flexible = 1).  z: FP64, or the FP32 V-cycle's output (widened in
+// the kernel, exactly).
+template <typename ZT>
+void launch_pcg_dots(int64_t n, const double* rv, const ZT* z, const double* q, int flexible,
                      const RedScratch& r, cudaStream_t s);
 // p = z + beta p; rho = rho_new
-void launch_pcg_update_p(int64_t n, double* p, const double* z, const RedScratch& r, cudaStream_t s);
+template <typename ZT>
+void launch_pcg_update_p(int64_t n, double* p, const ZT* z, const RedScratch& r, cudaStream_t s);
 // Loop test of the graph-driven PCG (one block): SC_RR from the axpy partials,
 // state[0] += 1 (iterations done), then the WHILE condition is set to (||r||^2 finite
 // && > SC_TOL2 && state[0] < state[1] (maxit)); state[2] = 1 flags a non-finite ||r||^2.

@@ -733,22 +733,27 @@ __global__ void __launch_bounds__(kFinishBlock) k_pcg_finish_rr(int nrr, RedScra
   if (threadIdx.x == 0) r.sc[SC_RR] = rr;
 }
 
-// Block partials of r.z (and z.q for the flexible beta).
+// Block partials of r.z (and z.q for the flexible beta).  z: FP64, or the FP32 V-cycle's
+// output widened here (exactly, by integer operations) instead of by a separate cast.
+__device__ __forceinline__ double zval(const double* z, int64_t i) { return z[i]; }
+__device__ __forceinline__ double zval(const float* z, int64_t i) { return widen(z[i]); }
+
+template <typename ZT>
 __global__ void __launch_bounds__(kBlock, 8) k_pcg_dots(int64_t n, const double* __restrict__ rv,
-                                                        const double* __restrict__ z, const double* __restrict__ q,
+                                                        const ZT* __restrict__ z, const double* __restrict__ q,
                                                         int flexible, RedScratch r) {
   pdl_begin();
   __shared__ double sh[kBlock];
   double acc0 = 0.0, acc1 = 0.0;
   if (flexible) {
     for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
-      const double zi = z[i];
+      const double zi = zval(z, i);
       acc0 = fma(rv[i], zi, acc0);
       acc1 = fma(zi, q[i], acc1);
     }
   } else {  // standard beta needs r.z only
     for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
-      acc0 = fma(rv[i], z[i], acc0);
+      acc0 = fma(rv[i], zval(z, i), acc0);
   }
   store_partial<kBlock>(acc0, r.partials + kSlotRZ * kMaxRedBlocks, sh);
   if (flexible) store_partial<kBlock>(acc1, r.partials + kSlotZQ * kMaxRedBlocks, sh);
@@ -769,12 +774,13 @@ __global__ void __launch_bounds__(kFinishBlock) k_pcg_finish_dots(int nred, int 
 }
 
 // p = z + beta p; rho = rho_new.
+template <typename ZT>
 __global__ void __launch_bounds__(kBlock, 8) k_pcg_update_p(int64_t n, double* __restrict__ p,
-                                                            const double* __restrict__ z, RedScratch r) {
+                                                            const ZT* __restrict__ z, RedScratch r) {
   pdl_begin();
   const double beta = r.sc[SC_BETA];
   for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
-    p[i] = fma(beta, p[i], z[i]);
+    p[i] = fma(beta, p[i], zval(z, i));
   if (blockIdx.x == 0 && threadIdx.x == 0) r.sc[SC_RHO] = r.sc[SC_RHO_NEW];
 }
 
@@ -1076,15 +1082,24 @@ void launch_pcg_finish_rr(int64_t n, const RedScratch& r, cudaStream_t s) {
   launch_k(k_pcg_finish_rr, 1, kFinishBlock, s, red_blocks(n), r);
 }
 
-void launch_pcg_dots(int64_t n, const double* rv, const double* z, const double* q, int flexible,
+template <typename ZT>
+void launch_pcg_dots(int64_t n, const double* rv, const ZT* z, const double* q, int flexible,
                      const RedScratch& r, cudaStream_t s) {
-  launch_k(k_pcg_dots, red_blocks(n), kBlock, s, n, rv, z, q, flexible, r);
+  launch_k(k_pcg_dots<ZT>, red_blocks(n), kBlock, s, n, rv, z, q, flexible, r);
   launch_k(k_pcg_finish_dots, 1, kFinishBlock, s, red_blocks(n), flexible, r);
 }
 
-void launch_pcg_update_p(int64_t n, double* p, const double* z, const RedScratch& r, cudaStream_t s) {
-  launch_k(k_pcg_update_p, vec_grid(n), kBlock, s, n, p, z, r);
+template void launch_pcg_dots<double>(int64_t, const double*, const double*, const double*, int,
+                                      const RedScratch&, cudaStream_t);
+template void launch_pcg_dots<float>(int64_t, const double*, const float*, const double*, int, const RedScratch&,
+                                     cudaStream_t);
+
+template <typename ZT>
+void launch_pcg_update_p(int64_t n, double* p, const ZT* z, const RedScratch& r, cudaStream_t s) {
+  launch_k(k_pcg_update_p<ZT>, vec_grid(n), kBlock, s, n, p, z, r);
 }
+template void launch_pcg_update_p<double>(int64_t, double*, const double*, const RedScratch&, cudaStream_t);
+template void launch_pcg_update_p<float>(int64_t, double*, const float*, const RedScratch&, cudaStream_t);
 
 void launch_pcg_loop_cond(cudaGraphConditionalHandle hw, int64_t n, const RedScratch& r, int* state,
                           cudaStream_t s) {

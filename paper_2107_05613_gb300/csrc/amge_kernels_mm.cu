@@ -296,6 +296,60 @@ __global__ void __launch_bounds__(kBlock) k_trimm(int n, int nrhs, const double*
   y[(size_t)row * nrhs + c] = (Tout)t;
 }
 
+// Z = M X for [n][nrhs] blocks (nrhs a multiple of 8, at most 32) on the FP64 tensor
+// cores: mma.sync m8n8k4 (DMMA; the tcgen05 MMA has no FP64 kind).  A block of eight
+// warps computes one 8-row tile of Z: warp w accumulates the k-steps (of 4) in its
+// eighth of [0, n) into NT = nrhs/8 accumulator tiles of 8 x 8, and the eight partial
+// tiles are added in warp order through shared memory (deterministic).  Fragments
+// (PTX m8n8k4 .f64): A row-major, lane l holds A[l/4][l%4]; B column-major, lane l
+// holds B[l%4][l/4]; C/D lane l holds row l/4, columns 2(l%4) and 2(l%4)+1.
+constexpr int kDmmaWarps = 8;
+template <int NT, typename Tout>
+__global__ void __launch_bounds__(kDmmaWarps * 32) k_densemm_dmma(int n, const double* __restrict__ M,
+                                                                  const double* __restrict__ X, Tout* __restrict__ Z) {
+  pdl_begin();
+  constexpr int nrhs = NT * 8;
+  __shared__ double part[kDmmaWarps][8][nrhs];
+  const int row0 = blockIdx.x * 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ar = row0 + (lane >> 2), ak = lane & 3;
+  const int bk = lane & 3, bn = lane >> 2;
+  double acc[NT][2];
+#pragma unroll
+  for (int t = 0; t < NT; t++) acc[t][0] = acc[t][1] = 0.0;
+  const int ksteps = (n + 3) / 4;
+  const int per = (ksteps + kDmmaWarps - 1) / kDmmaWarps;
+  const int s0 = warp * per, s1 = min(ksteps, s0 + per);
+  const double* mrow = M + (size_t)min(ar, n - 1) * n;
+  for (int st = s0; st < s1; st++) {
+    const int k = st * 4;
+    const double a = (ar < n && k + ak < n) ? __ldg(mrow + k + ak) : 0.0;
+    const bool bin = k + bk < n;
+    const double* xr = X + (size_t)(bin ? k + bk : 0) * nrhs + bn;
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+      const double b = bin ? __ldg(xr + t * 8) : 0.0;
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                   : "+d"(acc[t][0]), "+d"(acc[t][1])
+                   : "d"(a), "d"(b));
+    }
+  }
+  const int r = lane >> 2, c = (lane & 3) * 2;
+#pragma unroll
+  for (int t = 0; t < NT; t++) {
+    part[warp][r][t * 8 + c] = acc[t][0];
+    part[warp][r][t * 8 + c + 1] = acc[t][1];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 8 * nrhs; e += kDmmaWarps * 32) {
+    const int rr = e / nrhs, cc = e % nrhs;
+    double sum = part[0][rr][cc];
+#pragma unroll
+    for (int w = 1; w < kDmmaWarps; w++) sum += part[w][rr][cc];
+    if (row0 + rr < n) Z[(size_t)(row0 + rr) * nrhs + cc] = (Tout)sum;
+  }
+}
+
 // ---------------------------------------------------------------- per-column reductions
 constexpr size_t kColStride = (size_t)kMaxRedBlocksMM * kMaxRhs;
 
@@ -642,6 +696,32 @@ void launch_coarse_inv_mm(int n, int nrhs, const double* Ainv, const Tin* b, dou
     launch_k(k_trimm<0, double, Tout>, n, kBlock, s, n, nrhs, Ainv, (const double*)t, z);
   }
 }
+// The same product on the FP64 tensor cores (nrhs a multiple of 8, at most 32); an FP32
+// block is widened into t first, as above.  Returns false (nothing launched) where it
+// does not apply.
+template <typename Tin, typename Tout>
+bool launch_coarse_inv_mm_dmma(int n, int nrhs, const double* Ainv, const Tin* b, double* t, Tout* z,
+                               cudaStream_t s) {
+  if (nrhs % 8 != 0 || nrhs > 32 || nrhs <= 0) return false;
+  if (n <= 0) return true;
+  const double* x = reinterpret_cast<const double*>(b);
+  if (!std::is_same<Tin, double>::value) {
+    launch_cast<Tin, double>((int64_t)n * nrhs, b, t, s);
+    x = t;
+  }
+  const int grid = (n + 7) / 8;
+  switch (nrhs / 8) {
+    case 1: launch_k(k_densemm_dmma<1, Tout>, grid, kDmmaWarps * 32, s, n, Ainv, x, z); break;
+    case 2: launch_k(k_densemm_dmma<2, Tout>, grid, kDmmaWarps * 32, s, n, Ainv, x, z); break;
+    case 3: launch_k(k_densemm_dmma<3, Tout>, grid, kDmmaWarps * 32, s, n, Ainv, x, z); break;
+    default: launch_k(k_densemm_dmma<4, Tout>, grid, kDmmaWarps * 32, s, n, Ainv, x, z); break;
+  }
+  return true;
+}
+template bool launch_coarse_inv_mm_dmma<double, double>(int, int, const double*, const double*, double*, double*,
+                                                        cudaStream_t);
+template bool launch_coarse_inv_mm_dmma<float, float>(int, int, const double*, const float*, double*, float*,
+                                                      cudaStream_t);
 template void launch_coarse_inv_mm<double, double>(int, int, const double*, const double*, double*, double*,
                                                    cudaStream_t);
 template void launch_coarse_inv_mm<float, float>(int, int, const double*, const float*, double*, float*,

@@ -453,7 +453,7 @@ def _pin_block_forms(amge, h, nrhs, code):
     for prec in (amge.AMGE_FP64, amge.AMGE_FP32_VCYCLE):
         codes, _ = amge.amge_autotune_report_mm(h, nrhs, prec)
         for (l, op), c in codes.items():
-            if op == "AG" and amge.amge_autotune_report(h)[(l, "fp64", "AG")] < 0:
+            if op == "coarse" or (op == "AG" and amge.amge_autotune_report(h)[(l, "fp64", "AG")] < 0):
                 continue
             try:
                 amge.amge_set_kernel_mm(h, l, prec, op, nrhs, code)
@@ -519,6 +519,32 @@ def test_block_autotune_report(amge):
     with pytest.raises(amge.AmgeError):             # FP32: 4 floats per vector, 12 is not a multiple of 8
         amge.amge_set_kernel_mm(h, 0, amge.AMGE_FP32_VCYCLE, "A", 12, 2)
     h.free()
+
+
+@pytest.mark.parametrize("nrhs", [8, 16, 24, 32])
+@pytest.mark.parametrize("code", [0, 1])
+def test_block_coarse_solve_on_tensor_cores(amge, nrhs, code):
+    """The coarsest product Z = A_L^{-1} B of block V-cycles on CUDA cores (code 0) and on
+    the FP64 tensor cores (mma.sync m8n8k4, code 1): per column within the single-vector
+    V-cycle bound of the oracle (coarsest 1,944 dofs)."""
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, "hcurl", 16, 2)
+    o = oracle_hierarchy("hcurl", 16, 2, True)
+    R = rhs_vector(89, o.A[0].shape[0], nrhs)
+    Z = torch.empty_like(dev(R))
+    amge.amge_vcycle(h, dev(R), Z, nrhs, amge.AMGE_FP64)
+    amge.amge_set_kernel_mm(h, 0, amge.AMGE_FP64, "coarse", nrhs, code)
+    amge.amge_vcycle(h, dev(R), Z, nrhs, amge.AMGE_FP64)
+    codes, us = amge.amge_autotune_report_mm(h, nrhs, amge.AMGE_FP64)
+    assert codes[(1, "coarse")] == code and us[(1, "coarse")][0] > 0 and us[(1, "coarse")][1] > 0
+    Zg = host(Z)
+    ref = o.apply(R)
+    tol = _coarse_tol(o)
+    for c in range(nrhs):
+        assert np.linalg.norm(Zg[:, c] - ref[:, c]) <= tol * np.linalg.norm(ref[:, c]), (c, code)
+    with pytest.raises(amge.AmgeError):
+        amge.amge_set_kernel_mm(h, 0, amge.AMGE_FP64, "coarse", 4, 1)   # not a multiple of 8
 
 
 @pytest.mark.parametrize("form,n,L,nrhs", [("hcurl", 16, 2, 4), ("hdiv", 24, 3, 5), ("hcurl", 8, 4, 32)])

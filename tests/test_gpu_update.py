@@ -6,7 +6,8 @@ the re-assembled A_0, the Galerkin chain A_{l+1} = P_l^T A_l P_l (Section 3.2.1)
 derived smoother data on the GPU must give the V-cycle and PCG solve of a fresh setup
 with the new field: one V-cycle within the single-vector bound, PCG within one
 iteration and 1e-9 of the oracle's solution; the FP32 V-cycle reaches 1e-8.  Updating
-back to the first field restores its results.  Hierarchies uploaded as CSR levels have
+back to the first field restores its solution to that tolerance (the first operators
+came from the host's Galerkin products, the restored ones from the GPU's).  Hierarchies uploaded as CSR levels have
 no assembly data and are refused.
 """
 import numpy as np
@@ -73,7 +74,9 @@ def test_update_coefficients_matches_fresh_setup(amge, form, n):
     _check_solves(amge, h, build_hierarchy(form, n, 0, b2, a2), rhs, "updated field")
     amge.amge_update_coefficients(h, b1, a1)
     x1b = _check_solves(amge, h, build_hierarchy(form, n, 0, b1, a1), rhs, "first field again")
-    assert np.linalg.norm(x1b - x1) <= 1e-12 * np.linalg.norm(x1)
+    # the first operators came from the host's Galerkin products, these from the GPU's
+    # (another summation order): the solutions agree to the parity tolerance
+    assert np.linalg.norm(x1b - x1) <= 1e-9 * np.linalg.norm(x1)
     h.free()
 
 
