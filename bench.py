@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--smoother", choices=["l1jacobi", "gs"], default="l1jacobi",
                    help="hybrid smoother: l1-Jacobi (default) or two symmetric Gauss-Seidel steps (FP64 only)")
     p.add_argument("--gs-levels", type=int, default=64, help="finest smoothing levels that use Gauss-Seidel")
+    p.add_argument("--wide-arith", choices=["df", "fp64"], default="df",
+                   help="FP32 V-cycle: residuals of corrected iterates in double-float or FP64 arithmetic")
     p.add_argument("--no-subresults", action="store_true",
                    help="skip the H(div) 64^3 and 48^3 x 32 right-hand-side sub-results")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -438,6 +440,8 @@ def level0_launch_bytes(hh, w, nrhs, ag):
 ROOFLINE_KERNELS = {
     "A_fine": "k_sell level-0 A sweeps (residuals r = b - A x{last})",
     "A_wide": "k_sell_wide level-0 residuals of corrected iterates (FP64 values and sums, FP32 vectors)",
+    "A_wide_df": "k_sell_df level-0 residuals of corrected iterates (double-float values and sums on the FP32 "
+                 "pipe, FP32 vectors)",
 }
 
 
@@ -505,6 +509,7 @@ def run_ours(args, dist):
     # the problem-level setup entry (host hierarchy + upload), as a user calls it
     beta, alpha = workload_coeffs(wl)
     h = amge.amge_setup_upload(wl["form"], wl["n"], wl["levels"], beta, alpha)
+    amge.amge_set_wide_arith(h, amge.AMGE_WIDE_DF if args.wide_arith == "df" else amge.AMGE_WIDE_FP64)
     if args.smoother == "gs":
         amge.amge_set_smoother(h, amge.AMGE_SMOOTHER_SYM_GS, 2, args.gs_levels)
     if args.kernels_from:
@@ -580,6 +585,7 @@ def run_ours(args, dist):
         "config": workload_config(wl, hh),
         "precision": args.precision,
         "smoother": args.smoother if args.smoother == "l1jacobi" else f"gs x2, {args.gs_levels} finest levels",
+        "wide_arith": args.wide_arith,
         "device_bytes": amge.amge_hier_info(h)[2],
         "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU",
         "iters": iters[0], "true_relres": relres,
@@ -612,21 +618,25 @@ def run_ours(args, dist):
     if c and m > 0:
         bytes_launch = per_launch[cls]
         achieved = bytes_launch / (m / c / 1e3) / 1e9
-        fp64_values = (cls == "A_wide") or not fp32
+        df = cls == "A_wide" and args.wide_arith == "df"
+        fp64_values = (cls == "A_wide" and not df) or not fp32
+        kname = "A_wide_df" if df else cls
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                             "frac": achieved / hbm,
-                            "traffic": NCU_TRAFFIC.get((args.workload, cls, w)) if nrhs == 1 else None,
-                            "kernel": ROOFLINE_KERNELS[cls].format(last="" if ag else ", final l1 sweep")
+                            "traffic": NCU_TRAFFIC.get((args.workload, kname, w)) if nrhs == 1 else None,
+                            "kernel": ROOFLINE_KERNELS[kname].format(last="" if ag else ", final l1 sweep")
                                       + (", FP64" if not fp32 else ""),
                             "class": cls, "launches": c, "avg_us": 1e3 * m / c,
                             "bytes_per_launch": bytes_launch, "peak_source": peak_src}
+        peak64 = amge.amge_fp64_fma_rate()
+        line["fp64_rates"] = {"cuda_core_tfma": peak64, "tensor_core_tflops": amge.amge_fp64_mma_rate(),
+                              "how": "amge_fp64_fma_rate / amge_fp64_mma_rate on this GPU in this run"}
         if fp64_values and nrhs == 1:
             # the same launches against the FP64 pipe: one FMA per stored nonzero (the
             # chain starts from b), the kernel's other bound on GB300; the peak is the
             # FMA rate measured on this GPU right now (amge_fp64_fma_rate)
             fma = float(hh.A[0].nnz)
             tfma = fma / (m / c / 1e3) / 1e12
-            peak64 = amge.amge_fp64_fma_rate()
             line["roofline"]["fp64"] = {"achieved": tfma, "peak": peak64, "unit": "TFMA/s",
                                         "frac": tfma / peak64, "fma_per_launch": fma,
                                         "peak_source": "amge_fp64_fma_rate on this GPU in this run (of measured)"}

@@ -58,10 +58,12 @@ typedef enum { AMGE_HCURL = 2, AMGE_HDIV = 3 } amge_form;
  * AMGE_FP32_VCYCLE: the V-cycle's vectors are single precision, and so are its
  * prolongators, incidences, smoother data and the level products with single-
  * precision accumulation, except the residuals b - A_l x of iterates that carry a
- * correction through G or P: those read the FP64 copy of A_l and sum in double
- * (rounded once to single), because on such iterates most of A_l x cancels and
- * single-precision rounding would swamp the residual's gradient (curl) part that
- * the aux sweep and the coarse solve divide by small mass-only diagonals.  The
+ * correction through G or P: those use A_l's values to about 48 bits and sum to
+ * about that precision (double-float pairs on the FP32 pipe by default, or FP64
+ * values and sums, see amge_set_wide_arith), rounded once to single, because on
+ * such iterates most of A_l x cancels and single-precision rounding would swamp the
+ * residual's gradient (curl) part that the aux sweep and the coarse solve divide by
+ * small mass-only diagonals.  The
  * coarsest-level solve, the outer PCG dot products, AXPYs and the true-residual
  * recomputation stay in double precision. */
 typedef enum { AMGE_FP64 = 0, AMGE_FP32_VCYCLE = 1 } amge_precision;
@@ -305,6 +307,24 @@ amge_status amge_dot(amge_hier* h, const double* x_dev, const double* y_dev, int
 enum { AMGE_SMOOTHER_L1_JACOBI = 0, AMGE_SMOOTHER_SYM_GS = 1 };
 amge_status amge_set_smoother(amge_hier* h, int32_t smoother, int32_t sweeps, int32_t gs_levels);
 
+/* Arithmetic of the FP32 V-cycle's residuals of corrected iterates (and of
+ * AMGE_OP_A_WIDE):
+ *   AMGE_WIDE_DF    the default: each value of A_l as the float pair hi + lo
+ *                   (hi = fl32(a), lo = fl32(a - hi): 48 significant bits), each
+ *                   product hi x formed exactly as a float pair (product and FMA
+ *                   remainder), lo x added to the remainder, the row's sum kept as a
+ *                   float pair (two-sum of the high parts); all on the FP32 pipe.
+ *                   Error: a few multiples of 2^-48 |A_l| |x| per stored entry.
+ *   AMGE_WIDE_FP64  FP64 values and an FP64 FMA chain per row on the FP32 vectors
+ *                   widened exactly (error of FP64 recursive summation).
+ * Both read 8 value bytes per entry (the double-float pairs are a resident copy of
+ * A_l beside the FP64 and FP32 ones) and round the result once to single.  On GB300
+ * the FP64 form is co-limited by the FP64 FMA rate (one FMA per entry), the
+ * double-float form by HBM.  Captured PCG graphs of h are rebuilt on the next
+ * solve.  AMGE_EINVAL for another value or a NULL h. */
+enum { AMGE_WIDE_FP64 = 0, AMGE_WIDE_DF = 1 };
+amge_status amge_set_wide_arith(amge_hier* h, int32_t arith);
+
 /* Per-kernel launch counts and timing.  Every kernel launch of the solve path is
  * counted per kernel class; while timing is enabled each launch is also bracketed
  * by CUDA events on its stream.  amge_profile_read synchronises, and returns for
@@ -335,6 +355,14 @@ amge_status amge_profile_read(amge_hier* h, int64_t* count, double* ms);
  * (synchronised).  The second roofline of the FP64 sparse products, which issue one
  * FMA per stored 12-byte entry.  Errors: AMGE_EINVAL for NULL, AMGE_ECUDA. */
 amge_status amge_fp64_fma_rate(double* tfma, void* stream);
+
+/* FP64 tensor-core rate of the current device in TFLOP/s (*tflops, host): independent
+ * mma.sync m8n8k4 FP64 tiles (512 FLOP each, operands in registers) in every warp of a
+ * grid filling every SM, best of five timed launches on `stream` (synchronised).  The
+ * ceiling of an FP64 GEMM on the tensor cores (the coarsest solve of a block of
+ * right-hand sides); compare 2 x amge_fp64_fma_rate for the CUDA cores.
+ * Errors: AMGE_EINVAL for NULL, AMGE_ECUDA. */
+amge_status amge_fp64_mma_rate(double* tflops, void* stream);
 
 /* Coarsest-level solve z = A_L^{-1} b without any device allocation.
  * The paper has no counterpart.  It serves callers that may not have the library
@@ -425,13 +453,24 @@ amge_status amge_set_graphs(amge_hier* h, int32_t enable);
  * the call (call amge_set_kernel or re-upload to recapture an existing graph). */
 void amge_set_dependent_launch(int32_t enable);
 
+/* Wait status of h's kernels with bounded waits (the bulk-staged product, kernel code
+ * 3000): synchronizes `stream`, then *timed_out = 1 if such a kernel's wait for its
+ * staged copy ran out (about one second) since the previous call, else 0, and clears
+ * the flag.  A kernel that timed out stops early, so the results of the calls on h
+ * since the previous check are then not valid; the CUDA context stays usable.
+ * AMGE_EINVAL for NULL arguments, AMGE_ECUDA if the copy or the synchronization fails. */
+amge_status amge_wait_status(amge_hier* h, void* stream, int32_t* timed_out);
+
 /* The autotuner's kernel choice for every smoothing level's single-vector products:
  * lanes[(l * 2 + p) * 6 + op] for level l < levels-1, precision p (0 FP64, 1 FP32),
  * op 0..5 = A, P, P^T, G, G^T, AG; 0 = sliced ELL (one row per lane, one warp per
  * 32-row slice), 100 w (200, 400, 800) = sliced ELL with w warps sharing each slice,
  * 1000 / 1200 = sliced ELL with one / two warps per slice where each warp first issues
  * a bulk L2 prefetch of its slice's entries (candidates only for streamed operators,
- * those larger than half of L2; the others always prefetch),
+ * those larger than half of L2; the others always prefetch), 3000 = sliced ELL with one
+ * warp per slice whose entries are staged into shared memory by bulk asynchronous
+ * copies two slices ahead (candidate only for streamed operators with stored values;
+ * its waits are bounded, see amge_wait_status),
  * 2..32 = vector CSR with that many lanes per row, -1 = operator not used (AG is stored only where
  * A G = A_l G_l is much sparser than A_l, i.e. for H(curl): there the residual after
  * an aux sweep is updated as r - (A G) y instead of recomputed as b - A x).  The
@@ -449,15 +488,16 @@ amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
  * from HBM as it does inside a V-cycle.  Otherwise, and for streamed operators larger
  * than L2, the ten launches run back to back and are timed as a whole (best of
  * three) -- also where the 2x L2 scratch cannot be allocated.  Candidate c in the order 0,
- * 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200; -1 where a candidate was not measured
- * (more warps than the operator's rows have entry pairs, or a prefetch variant of an
- * operator that is not streamed) or the operator is not stored.  us must hold
- * (levels-1)*132 floats. */
+ * 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000; -1 where a candidate was not measured
+ * (more warps than the operator's rows have entry pairs, or a prefetch or staging
+ * variant of an operator that is not streamed) or the operator is not stored.  us must
+ * hold (levels-1)*144 floats. */
 amge_status amge_autotune_times(const amge_hier* h, float* us);
 
 /* Override one entry of that choice (level l < levels-1, precision 0/1, op 0..5 as
- * above; lanes = a kernel code as above: 0, 200, 400, 800, 1000, 1200 or 2, 4, 8, 16,
- * 32; the prefetch codes act as 0 / 200 on operators that are not streamed).  Captured PCG graphs
+ * above; lanes = a kernel code as above: 0, 200, 400, 800, 1000, 1200, 3000 or 2, 4, 8,
+ * 16, 32; the prefetch codes act as 0 / 200 on operators that are not streamed, 3000 as 0
+ * on sign-coded operators and on those whose longest slice does not fit the stages).  Captured PCG graphs
  * of h are rebuilt on the next solve.  Every kernel computes the same products (in a
  * different summation order), so a choice changes rounding, not results beyond it;
  * pinning the choices makes results reproducible across uploads.  Not to be called

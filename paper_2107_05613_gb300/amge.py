@@ -27,6 +27,7 @@ AMGE_OP_A, AMGE_OP_P, AMGE_OP_PT, AMGE_OP_G, AMGE_OP_GT, AMGE_OP_SMOOTH_PRE, AMG
 PROF_CLASSES = ["A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "pcg_spmv", "pcg_vec", "vcycle_vec", "AG",
                 "A_wide", "gs"]
 AMGE_SMOOTHER_L1_JACOBI, AMGE_SMOOTHER_SYM_GS = 0, 1
+AMGE_WIDE_FP64, AMGE_WIDE_DF = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENONFINITE",
                 6: "EAGAIN", 7: "ETIMEOUT", 8: "ECANCELED"}
 
@@ -84,10 +85,13 @@ _SIGS = {
     "amge_profile_read": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)],
     "amge_coarse_solve_noalloc": [_vp, _vp, _vp, _vp],
     "amge_fp64_fma_rate": [ctypes.POINTER(ctypes.c_double), _vp],
+    "amge_fp64_mma_rate": [ctypes.POINTER(ctypes.c_double), _vp],
     "amge_autotune_report_mm": [_vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)],
     "amge_set_kernel_mm": [_vp, _i32, _i32, _i32, _i32, _i32],
     "amge_set_smoother": [_vp, _i32, _i32, _i32],
     "amge_update_coefficients": [_vp, _vp, _vp, _vp],
+    "amge_wait_status": [_vp, _vp, ctypes.POINTER(_i32)],
+    "amge_set_wide_arith": [_vp, _i32],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -284,19 +288,19 @@ def amge_autotune_report(h: Hier):
 
 
 OPS = ["A", "P", "PT", "G", "GT", "AG"]
-TUNE_CODES = [0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200]
+TUNE_CODES = [0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000]
 
 
 def amge_autotune_times(h: Hier):
     """{(level, 'fp64'|'fp32', op): {code: us per launch}} as measured at upload."""
     L = h.levels
-    buf = (ctypes.c_float * max((L - 1) * 132, 1))()
+    buf = (ctypes.c_float * max((L - 1) * 144, 1))()
     _check(_lib.amge_autotune_times(h.handle, buf), "amge_autotune_times")
     out = {}
     for l in range(L - 1):
         for pi, p in enumerate(("fp64", "fp32")):
             for o in range(6):
-                t = {c: round(float(buf[((l * 2 + pi) * 6 + o) * 11 + k]), 2) for k, c in enumerate(TUNE_CODES)}
+                t = {c: round(float(buf[((l * 2 + pi) * 6 + o) * 12 + k]), 2) for k, c in enumerate(TUNE_CODES)}
                 if any(v >= 0 for v in t.values()):
                     out[(l, p, OPS[o])] = {c: v for c, v in t.items() if v >= 0}
     return out
@@ -314,6 +318,20 @@ def amge_set_kernel(h: Hier, level: int, precision, op, lanes: int):
 def amge_set_dependent_launch(enable: bool = True):
     """Process-wide programmatic dependent launch of the library's kernels (default on)."""
     _lib.amge_set_dependent_launch(int(enable))
+
+
+def amge_set_wide_arith(h: Hier, arith: int):
+    """Arithmetic of the FP32 V-cycle's residuals of corrected iterates:
+    AMGE_WIDE_DF (double-float on the FP32 pipe, default) or AMGE_WIDE_FP64."""
+    _check(_lib.amge_set_wide_arith(h.handle, int(arith)), "amge_set_wide_arith")
+
+
+def amge_wait_status(h: Hier, stream=None) -> bool:
+    """True if a kernel of h with bounded waits (the bulk-staged product) ran out of
+    time since the previous check (the results since then are not valid); clears it."""
+    v = _i32()
+    _check(_lib.amge_wait_status(h.handle, _stream(stream), ctypes.byref(v)), "amge_wait_status")
+    return bool(v.value)
 
 
 def amge_set_graphs(h: Hier, enable: bool = True):
@@ -476,3 +494,10 @@ def amge_update_coefficients(h: Hier, beta=None, alpha=None, stream=None):
 
     _check(_lib.amge_update_coefficients(h.handle, ptr(beta), ptr(alpha), _stream(stream)),
            "amge_update_coefficients")
+
+
+def amge_fp64_mma_rate(stream=None) -> float:
+    """FP64 tensor-core (mma.sync m8n8k4) rate of the current device, TFLOP/s."""
+    v = ctypes.c_double()
+    _check(_lib.amge_fp64_mma_rate(ctypes.byref(v), _stream(stream)), "amge_fp64_mma_rate")
+    return v.value

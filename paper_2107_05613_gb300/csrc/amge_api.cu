@@ -75,6 +75,9 @@ void upload_sell(amge_hier* h, const HostCsr& M, DevSell<double>& d64, DevSell<f
   d64.nnz = d32.nnz = S.nnz;
   d64.unit = d32.unit = S.unit ? 1 : 0;
   d64.stored = d32.stored = S.sptr[S.nslices];
+  int64_t mp = 0;
+  for (int i = 0; i < S.nslices; i++) mp = std::max(mp, (S.sptr[i + 1] - S.sptr[i]) / 64);
+  d64.max_pairs = d32.max_pairs = (int)mp;
   // operators well beyond L2 are streamed with the evict-first hint (over 64 MiB,
   // half of GB300's L2: the finest level's; the coarser levels' stay cacheable)
   const double bytes64 = (double)d64.stored * (S.unit ? 4.0 : 12.0);
@@ -196,6 +199,7 @@ template <typename V>
 void opk(amge_hier* h, int cls, const LevelDev<V>& d, int op, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
   Prof p(h, cls, s);
   const int code = d.lanes[op];  // sliced ELL (code_wps warps per slice, code_pf) or vector CSR lanes
+  if (code_bulk(code) && launch_sell_bulk<V>(op_sell(d, op), epi, a, s, h->kwait)) return;
   if (code_is_sell(code)) launch_sell<V>(op_sell(d, op), epi, a, s, code_wps(code), code_pf(code));
   else launch_csrv<V>(op_csr(d, op), code, epi, a, s);
 }
@@ -206,6 +210,16 @@ void opk(amge_hier* h, int cls, const LevelDev<V>& d, int op, int epi, const Spm
 int wide_wps(const amge_hier* h, int l) {
   const int code = h->lv64[l].lanes[OP_A];
   return code_is_sell(code) ? code_wps(code) : 4;
+}
+
+// A_l x of the FP32 V-cycle on level l's FP64 operator: FP64 values and sums
+// (launch_sell_wide) or double-float values and sums on the FP32 pipe
+// (launch_sell_df), per amge_set_wide_arith.
+void wide_product(amge_hier* h, int l, int epi, const SpmvArgs<float>& a, cudaStream_t s) {
+  const DevSell<double>& M = h->lv64[l].A;
+  const bool pf = code_pf(h->lv64[l].lanes[OP_A]);
+  if (h->wide_arith == AMGE_WIDE_DF && h->lv32[l].Adf) launch_sell_df(M, h->lv32[l].Adf, epi, a, s, wide_wps(h, l), pf);
+  else launch_sell_wide(M, epi, a, s, wide_wps(h, l), pf);
 }
 
 // A product with A_l in a residual form (EPI_RESID / EPI_SWEEP).  `corrected`: the
@@ -226,7 +240,7 @@ void a_product(amge_hier* h, int l, const LevelDev<V>& d, bool corrected, int ep
   if constexpr (std::is_same<V, float>::value) {
     if (corrected) {
       Prof p(h, l == 0 ? AMGE_PROF_A_WIDE : AMGE_PROF_A_COARSE, s);
-      launch_sell_wide(h->lv64[l].A, epi, a, s, wide_wps(h, l), code_pf(h->lv64[l].lanes[OP_A]));
+      wide_product(h, l, epi, a, s);
       return;
     }
   }
@@ -1459,12 +1473,14 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
     h->s32_out = dalloc<float>(h, n0);
     h->gx = dalloc<double>(h, n0);
     h->gstate = dalloc<int>(h, 4);
+    h->kwait = dalloc<int>(h, 1);
     h->red.partials = dalloc<double>(h, (size_t)kRedSlots * kMaxRedBlocks);
     h->red.sc = dalloc<double>(h, SC_COUNT);
   } catch (const UploadError& e) {
     return e.st;
   }
   CK(cudaMemsetAsync(h->red.sc, 0, SC_COUNT * sizeof(double), s));
+  CK(cudaMemsetAsync(h->kwait, 0, sizeof(int), s));
   CK(cudaMallocHost(&h->pinned, 16 * sizeof(double)));
   CK(cudaMallocHost(&h->pinned_state, 4 * sizeof(int)));
   CK(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
@@ -1484,7 +1500,7 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
 // Streamed operators (much larger than L2) come from HBM either way and are timed back
 // to back, where each launch overlaps the previous one's tail as it does behind its
 // predecessor in the V-cycle.
-constexpr int kTuneCodes[kNumTuneCodes] = {0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200};
+constexpr int kTuneCodes[kNumTuneCodes] = {0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000};
 constexpr int kTuneReps = 10;
 
 struct TuneFlush {
@@ -1564,6 +1580,9 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
       const int lanes = kTuneCodes[ci];
       d.tune_us[op][ci] = -1.f;
       if (code_pf(lanes) && (!op_sell(d, op).stream || op_sell(d, op).unit)) continue;  // prefetch: streamed only
+      if (code_bulk(lanes) && (!op_sell(d, op).stream || op_sell(d, op).unit || !sell_bulk_fits(op_sell(d, op)) ||
+                               (op == OP_AG && d.g2)))
+        continue;  // bulk staging: streamed operators with stored values (AG runs fused with G where it can)
       if (code_is_sell(lanes) && code_wps(lanes) > 1 && 2.0 * code_wps(lanes) > avg + 1.0) continue;  // more warps than entry pairs
       if (lanes > 2 && lanes < 100 && lanes > 2 * avg) continue;
       d.lanes[op] = lanes;
@@ -1716,6 +1735,7 @@ amge_status autotune(amge_hier* h, cudaStream_t s) {
   // candidates are captured into graphs on a stream of our own (the caller's may be
   // the legacy default stream, which cannot be captured)
   CK(cudaStreamSynchronize(s));
+  sell_bulk_prepare();
   cudaStream_t ts;
   CK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
   cudaEvent_t e0, e1;
@@ -1825,6 +1845,8 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
         }
         d64.naux = d32.naux = G.nc;
         upload_sell(h, A, d64.A, d32.A, s, keep, keeps);
+        d32.Adf = dalloc<float4>(h, (size_t)(d64.A.stored / 2));
+        launch_df_split(d64.A.stored / 2, d64.A.val, d32.Adf, s);
         upload_sell(h, P, d64.P, d32.P, s, keep, keeps);
         upload_sell(h, PT, d64.PT, d32.PT, s, keep, keeps);
         upload_sell(h, G, d64.G, d32.G, s, keep, keeps, true);
@@ -2240,7 +2262,7 @@ amge_status amge_apply(amge_hier* h, int32_t op, int32_t level, const double* x_
     launch_cast<double, float>(M.nc, x_dev, h->s32_in, s);
     SpmvArgs<float> a;
     a.x = h->s32_in, a.y = h->s32_out;
-    launch_sell_wide(M, EPI_STORE, a, s, wide_wps(h, level));
+    wide_product(h, level, EPI_STORE, a, s);
     launch_cast<float, double>(M.nr, h->s32_out, y_dev, s);
     return launch_status();
   }
@@ -2344,8 +2366,8 @@ amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int3
     return AMGE_EINVAL;
   }
   if (lanes != 0 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32 && lanes != 200 &&
-      lanes != 400 && lanes != 800 && lanes != 1000 && lanes != 1200) {
-    set_error("kernel code must be 0, 200, 400, 800, 1000, 1200 (sliced ELL) or 2, 4, 8, 16, 32 (vector CSR)");
+      lanes != 400 && lanes != 800 && lanes != 1000 && lanes != 1200 && lanes != 3000) {
+    set_error("kernel code must be 0, 200, 400, 800, 1000, 1200, 3000 (sliced ELL) or 2, 4, 8, 16, 32 (vector CSR)");
     return AMGE_EINVAL;
   }
   int& cur = precision == 0 ? h->lv64[level].lanes[op] : h->lv32[level].lanes[op];
@@ -2353,6 +2375,7 @@ amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int3
     set_error("operator not stored on this level");
     return AMGE_EINVAL;
   }
+  if (code_bulk(lanes)) sell_bulk_prepare();
   cur = lanes;
   for (GraphPcg& G : h->gpcg) {  // the captured launches name the old kernels
     if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -2363,6 +2386,20 @@ amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int3
 }
 
 void amge_set_dependent_launch(int32_t enable) { set_dependent_launch(enable != 0); }
+
+amge_status amge_wait_status(amge_hier* h, void* stream, int32_t* timed_out) {
+  if (!h || !timed_out) {
+    set_error("NULL argument");
+    return AMGE_EINVAL;
+  }
+  cudaStream_t s = as_stream(stream);
+  int v = 0;
+  CK(cudaMemcpyAsync(&v, h->kwait, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (v) CK(cudaMemsetAsync(h->kwait, 0, sizeof(int), s));
+  *timed_out = v;
+  return AMGE_OK;
+}
 
 amge_status amge_autotune_report_mm(amge_hier* h, int32_t nrhs, int32_t precision, int32_t* codes, float* us) {
   if (!h || !codes || nrhs < 2 || nrhs > kMaxRhs || (precision != AMGE_FP64 && precision != AMGE_FP32_VCYCLE)) {
@@ -2553,6 +2590,21 @@ amge_status amge_set_smoother(amge_hier* h, int32_t smoother, int32_t sweeps, in
   h->sweeps = sweeps;
   h->gs_levels = want;
   drop_graphs(h);  // the captured V-cycle changes
+  return AMGE_OK;
+}
+
+amge_status amge_set_wide_arith(amge_hier* h, int32_t arith) {
+  if (!h) {
+    set_error("NULL hierarchy");
+    return AMGE_EINVAL;
+  }
+  if (arith != AMGE_WIDE_FP64 && arith != AMGE_WIDE_DF) {
+    set_error("arith must be AMGE_WIDE_FP64 or AMGE_WIDE_DF");
+    return AMGE_EINVAL;
+  }
+  h->wide_arith = arith;
+  drop_graphs(h);  // the captured V-cycle changes
+  drop_graphs_mm(h);
   return AMGE_OK;
 }
 

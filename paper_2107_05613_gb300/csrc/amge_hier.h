@@ -11,7 +11,7 @@
 
 namespace amge {
 
-constexpr int kNumTuneCodes = 11;  // candidates of the single-vector autotuner (kTuneCodes)
+constexpr int kNumTuneCodes = 12;  // candidates of the single-vector autotuner (kTuneCodes)
 
 template <typename V>
 struct LevelDev {
@@ -43,6 +43,9 @@ struct LevelDev {
   std::vector<int> gsA_cs, gsX_cs;
   V *gsA_dinv = nullptr, *gsX_dinv = nullptr;
   V* t = nullptr;  // aux right-hand side G^T r of the Gauss-Seidel aux smoothing
+  // FP32 V-cycle (lv32): A_l's values as double-float pairs {hi0, hi1, lo0, lo1} per
+  // entry pair of the FP64 sliced-ELL copy (launch_sell_df)
+  float4* Adf = nullptr;
   V* minv = nullptr;
   V* mauxinv = nullptr;
   V *x = nullptr, *r = nullptr, *y = nullptr, *tmp = nullptr;
@@ -77,6 +80,8 @@ struct amge_hier {
   // smoother: AMGE_SMOOTHER_L1_JACOBI, or AMGE_SMOOTHER_SYM_GS on the gs_levels finest
   // smoothing levels (sweeps symmetric steps per smoothing; l1-Jacobi below them)
   int smoother = AMGE_SMOOTHER_L1_JACOBI, sweeps = 2, gs_levels = 0, gs_built = 0;
+  // arithmetic of the FP32 V-cycle's residuals of corrected iterates (amge_set_wide_arith)
+  int wide_arith = AMGE_WIDE_DF;
   int n0 = 0;
   int device = -1;  // CUDA device the operators live on (current at upload)
   std::vector<LevelDev<double>> lv64;
@@ -114,6 +119,7 @@ struct amge_hier {
   GraphPcg gpcg[2];
   cudaStream_t cap = nullptr;  // capture stream of the graphs
   int* gstate = nullptr;       // device: iterations done, maxit, non-finite flag
+  int* kwait = nullptr;        // device: set by a bounded wait that ran out (amge_wait_status)
   double* gx = nullptr;        // device: iterate of the graph-driven loop
   int* pinned_state = nullptr;
   bool use_graphs = true;

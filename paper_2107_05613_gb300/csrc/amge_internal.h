@@ -85,6 +85,7 @@ struct DevSell {
   int nr = 0, nc = 0, nslices = 0;
   int unit = 0;    // sign-coded columns (val == nullptr)
   int stream = 0;  // larger than half of L2: entries are read with the evict-first hint
+  int max_pairs = 0;  // entry pairs of the longest slice (bulk-staged kernel's stage size)
   int64_t nnz = 0, stored = 0;
   int64_t* sptr = nullptr;
   int* srow = nullptr;
@@ -119,15 +120,31 @@ struct SpmvArgs {
 // with that many lanes per row.
 inline bool code_is_sell(int c) { return c == 0 || c >= 100; }
 inline int code_wps(int c) {
-  const int w = c >= 1000 ? (c - 1000) / 100 : c / 100;
-  return w < 1 ? 1 : w;
+  if (c == 200 || c == 1200) return 2;
+  if (c == 400) return 4;
+  if (c == 800) return 8;
+  return 1;
 }
-inline bool code_pf(int c) { return c >= 1000; }
+inline bool code_pf(int c) { return c == 1000 || c == 1200; }
+// 3000: one warp per slice with the slice's entries staged into shared memory by bulk
+// asynchronous copies (streamed operators with stored values; see k_sell_bulk).
+inline bool code_bulk(int c) { return c == 3000; }
 
 // wps = warps per 32-row slice (1, 2, 4, 8); pf: a streamed operator's slices are
 // also prefetched into L2 in bulk (wps 1 or 2).
 template <typename V>
 void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, int wps = 1, bool pf = false);
+
+// The bulk-staged form of launch_sell (one warp per slice; false, nothing launched,
+// for sign-coded operators or slices too long for the stages); err: a device int set
+// to 1 if a stage's copy did not arrive in time (the launch then stops early).
+template <typename V>
+bool launch_sell_bulk(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, int* err);
+template <typename V>
+bool sell_bulk_fits(const DevSell<V>& M);
+// Raises the bulk-staged kernels' shared-memory limit on the current device (once;
+// outside any stream capture).  Until it has run there, launch_sell_bulk returns false.
+void sell_bulk_prepare();
 
 // FP32 vectors through the FP64 sliced-ELL operator M (FP64 values, FP64 FMA chain,
 // result rounded once to FP32); epi = EPI_STORE (y = M x), EPI_RESID (y = b - M x) or
@@ -135,6 +152,12 @@ void launch_sell(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_
 // launch_sell<double>.
 void launch_sell_wide(const DevSell<double>& M, int epi, const SpmvArgs<float>& a, cudaStream_t s, int wps = 1,
                       bool pf = false);
+// The same products in double-float arithmetic on the FP32 pipe (k_sell_df): M's
+// indices and layout with the values v4 = {hi0, hi1, lo0, lo1} per entry pair.
+void launch_sell_df(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a, cudaStream_t s,
+                    int wps = 1, bool pf = false);
+// v4 from the FP64 sliced-ELL values v (npairs = stored entries / 2).
+void launch_df_split(int64_t npairs, const double* v, float4* out, cudaStream_t s);
 
 // Gauss-Seidel update of one colour's rows: slices [s0, s1) of a colour-grouped
 // sliced-ELL operator, x_i += dinv_i (b_i - (M x)_i) in place (FP64).

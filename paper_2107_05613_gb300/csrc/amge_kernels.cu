@@ -285,6 +285,114 @@ __global__ void __launch_bounds__(kBlock) k_sell_wide(int nslices, const int64_t
   else a.y[row] = r;
 }
 
+// The same products in double-float arithmetic on the FP32 pipe.  Each stored value
+// a is kept as the float pair hi + lo (hi = fl(a), lo = fl(a - hi)), a pair of
+// entries as one float4 {hi0, hi1, lo0, lo1} (8 bytes per entry, as an FP64 value).
+// Per entry: p = fl(hi x), e = fma(hi, x, -p) (the exact remainder of the product),
+// t = fma(lo, x, e); the running sum is an unnormalized pair (sh, sl): sh <- sh + p
+// by a two-sum whose exact rounding error, plus t, is added to sl.  The result is
+// fl(sh + sl).  Its error is a few multiples of 2^-48 |A| |x| per stored entry, so
+// the cancellation the FP64 form guards against is resolved as well (c_A eps_32
+// ~ 1 at the 1e6 contrast, c_A 2^-43 ~ 1e-6), while the FP64 pipe, which the FP64
+// form keeps busy at one FMA per entry, stays idle.  All steps use
+// round-to-nearest intrinsics, which the compiler does not contract.
+struct DfSum {
+  float h, l;
+};
+__device__ __forceinline__ void df_add_entry(DfSum& s, float hi, float lo, float x) {
+  const float p = __fmul_rn(hi, x);
+  const float e = __fmaf_rn(hi, x, -p);
+  const float t = __fmaf_rn(lo, x, e);
+  const float sh = __fadd_rn(s.h, p);
+  const float bp = __fsub_rn(sh, s.h);
+  const float err = __fadd_rn(__fsub_rn(s.h, __fsub_rn(sh, bp)), __fsub_rn(p, bp));
+  s.h = sh;
+  s.l = __fadd_rn(s.l, __fadd_rn(err, t));
+}
+__device__ __forceinline__ void df_add(DfSum& s, const DfSum& o) {
+  const float sh = __fadd_rn(s.h, o.h);
+  const float bp = __fsub_rn(sh, s.h);
+  const float err = __fadd_rn(__fsub_rn(s.h, __fsub_rn(sh, bp)), __fsub_rn(o.h, bp));
+  s.h = sh;
+  s.l = __fadd_rn(s.l, __fadd_rn(err, o.l));
+}
+
+template <int EPI, int WPS, bool CS, bool PF = false>
+__global__ void __launch_bounds__(kBlock) k_sell_df(int nslices, const int64_t* __restrict__ sptr,
+                                                    const int* __restrict__ srow, const int2* __restrict__ ci2,
+                                                    const float4* __restrict__ val4, SpmvArgs<float> a) {
+  static_assert(EPI == EPI_STORE || EPI == EPI_RESID || EPI == EPI_SWEEP, "unsupported epilogue");
+  constexpr bool NEG = EPI != EPI_STORE;
+  const int wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int g = wib % WPS;
+  const int slice = (blockIdx.x * (kBlock / 32) + wib) / WPS;
+  const bool live = slice < nslices;
+  int row = -1, np = 0;
+  const int2* cp = ci2;
+  const float4* vp = val4;
+  int2 c0 = make_int2(0, 0);
+  float4 v0{};
+  if (live) {  // constant operator data before the dependent-launch wait (as k_sell)
+    const int64_t p0 = ldg(sptr + slice) >> 1;
+    np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+    row = ldg(srow + (size_t)slice * 32 + lane);
+    if ((!CS || PF) && g == 0 && lane == 0 && np > 0) {
+      prefetch_l2_bulk(ci2 + p0, (uint32_t)np * 32u * sizeof(int2));
+      prefetch_l2_bulk(val4 + p0, (uint32_t)np * 32u * sizeof(float4));
+    }
+    cp += p0 + lane;
+    vp += p0 + lane;
+    if (g < np) {
+      c0 = ldm<CS>(cp + (size_t)g * 32);
+      v0 = ldm<CS>(vp + (size_t)g * 32);
+    }
+  }
+  pdl_begin();
+  DfSum s{0.f, 0.f};
+  if (live) {
+    if (NEG && g == 0 && row >= 0) s.h = a.b[row];
+    if (g < np) {
+      const float x0 = ldg(a.x + c0.x), x1 = ldg(a.x + c0.y);
+      df_add_entry(s, NEG ? -v0.x : v0.x, NEG ? -v0.z : v0.z, x0);
+      df_add_entry(s, NEG ? -v0.y : v0.y, NEG ? -v0.w : v0.w, x1);
+    }
+#pragma unroll 2
+    for (int k = g + WPS; k < np; k += WPS) {
+      const int2 c = ldm<CS>(cp + (size_t)k * 32);
+      const float4 v = ldm<CS>(vp + (size_t)k * 32);
+      const float x0 = ldg(a.x + c.x), x1 = ldg(a.x + c.y);
+      df_add_entry(s, NEG ? -v.x : v.x, NEG ? -v.z : v.z, x0);
+      df_add_entry(s, NEG ? -v.y : v.y, NEG ? -v.w : v.w, x1);
+    }
+  }
+  if (WPS > 1) {
+    __shared__ float2 part[kBlock];
+    part[threadIdx.x] = make_float2(s.h, s.l);
+    __syncthreads();
+    if (g != 0) return;
+#pragma unroll
+    for (int j = 1; j < WPS; j++) {
+      const float2 o = part[threadIdx.x + 32 * j];
+      df_add(s, DfSum{o.x, o.y});
+    }
+  }
+  if (!live || row < 0) return;
+  const float r = __fadd_rn(s.h, s.l);
+  if (EPI == EPI_SWEEP) a.y[row] = fmaf(a.d[row], r, a.xin[row]);
+  else a.y[row] = r;
+}
+
+// Double-float values of a sliced-ELL operator: pair q of entries (2q, 2q + 1) as
+// {hi0, hi1, lo0, lo1}.
+__global__ void k_df_split(int64_t npairs, const double2* __restrict__ v, float4* out) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npairs; q += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = v[q];
+    const float h0 = __double2float_rn(a.x), h1 = __double2float_rn(a.y);
+    out[q] = make_float4(h0, h1, __double2float_rn(a.x - (double)h0), __double2float_rn(a.y - (double)h1));
+  }
+}
+
 // One Gauss-Seidel update of the rows of one colour: slices [s0, s1) of a
 // colour-grouped sliced-ELL operator (every slice holds rows of a single colour),
 // x_i <- x_i + dinv_i (b_i - (M x)_i).  Rows of one colour are not coupled, so
@@ -341,6 +449,182 @@ __global__ void k_zero(int64_t n, V* __restrict__ x) {
   pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = V(0);
+}
+
+// ---------------------------------------------------------------- bulk-staged sliced ELL
+// For operators streamed from HBM (the finest level's), each warp stages its slices'
+// column and value arrays into shared memory with bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier), kBulkStages slices ahead, then reads
+// them from shared memory.  The loads of a slice's entries no longer sit in front of
+// its gathers (every gather address is in shared memory when the slice starts, so
+// all of a lane's gathers are independent), and the operator streams in a few large
+// requests per slice.  The FMA chain per row is that of k_sell with one warp per
+// slice, so the results are identical.  Waits are bounded: on a timeout the warp
+// sets *err, waits (bounded) for its copies in flight and returns.
+constexpr int kBulkWarps = 8;
+constexpr int kBulkStages = 2;
+constexpr int kBulkBatch = 6;
+constexpr int kBulkSpinLimit = 1 << 22;
+constexpr uint64_t kBulkWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// policy: an L2 cache policy (evict-first for operators streamed once per product, so
+// that they do not push the coarse levels' operators out of L2)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded both in tries and in time (one second): every try returns after at most a
+// system-dependent suspension, so the wait ends whether or not the phase completes.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (int i = 0; i < kBulkSpinLimit; i++) {
+    if (mbar_try(bar, parity)) return true;
+    if (global_ns() - t0 > kBulkWaitNs) return false;
+  }
+  return false;
+}
+
+// Shared memory of one warp: kBulkStages barriers (16 bytes each), then the stages,
+// each [stage_pairs * 32] int2 columns followed by as many value pairs.
+template <typename PV>
+__host__ __device__ __forceinline__ size_t bulk_stage_bytes(int stage_pairs) {
+  return (size_t)stage_pairs * 32 * (sizeof(int2) + sizeof(PV));
+}
+
+template <typename V, int EPI>
+__global__ void __launch_bounds__(kBulkWarps * 32) k_sell_bulk(int nslices, const int64_t* __restrict__ sptr,
+                                                               const int* __restrict__ srow,
+                                                               const int2* __restrict__ ci2,
+                                                               const typename Pair<V>::T* __restrict__ val2,
+                                                               SpmvArgs<V> a, int stage_pairs, int* err) {
+  using PV = typename Pair<V>::T;
+  constexpr bool NEG = SellNeg<EPI>::value;
+  extern __shared__ __align__(128) unsigned char bulk_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t sb = bulk_stage_bytes<PV>(stage_pairs);
+  unsigned char* base = bulk_smem + (size_t)warp * (16 * kBulkStages + kBulkStages * sb);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base);  // barrier j at bar[2 j]
+  auto cols = [&](int st) { return reinterpret_cast<int2*>(base + 16 * kBulkStages + st * sb); };
+  auto vals = [&](int st) {
+    return reinterpret_cast<PV*>(base + 16 * kBulkStages + st * sb + (size_t)stage_pairs * 32 * sizeof(int2));
+  };
+  const int gw = blockIdx.x * kBulkWarps + warp, nw = gridDim.x * kBulkWarps;
+  const uint64_t pol = policy_evict_first();
+  auto issue = [&](int k) {  // lane 0: stage the k-th slice of this warp
+    const int slice = gw + k * nw;
+    if (slice >= nslices) return;
+    const int64_t p0 = ldg(sptr + slice) >> 1;
+    const int np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+    const int st = k % kBulkStages;
+    const uint32_t bc = (uint32_t)np * 32u * sizeof(int2), bv = (uint32_t)np * 32u * sizeof(PV);
+    mbar_expect_tx(&bar[2 * st], bc + bv);
+    if (np > 0) {
+      bulk_g2s(cols(st), ci2 + p0, bc, &bar[2 * st], pol);
+      bulk_g2s(vals(st), val2 + p0, bv, &bar[2 * st], pol);
+    }
+  };
+  if (lane == 0) {
+    for (int st = 0; st < kBulkStages; st++) mbar_init1(&bar[2 * st]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  // the operator is read-only: its first slices are requested before the wait
+  if (lane == 0)
+    for (int k = 0; k < kBulkStages; k++) issue(k);
+  pdl_begin();
+  int k = 0;
+  bool ok = true;
+  for (;; k++) {
+    const int slice = gw + k * nw;
+    if (slice >= nslices) break;
+    const int st = k % kBulkStages;
+    const bool arrived = mbar_wait_bounded(&bar[2 * st], (uint32_t)(k / kBulkStages) & 1u);
+    if (!__all_sync(0xffffffffu, arrived)) {  // the warp leaves together
+      ok = false;
+      break;
+    }
+    const int64_t p0 = ldg(sptr + slice) >> 1;
+    const int np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+    const int row = ldg(srow + (size_t)slice * 32 + lane);
+    V s = sell_init<V, EPI>(a, row);
+    const int2* cs = cols(st) + lane;
+    const PV* vs = vals(st) + lane;
+    // batches of kBulkBatch entry pairs: the batch's gathers are issued together,
+    // then summed in entry order (the chain of k_sell)
+    int kk = 0;
+    for (; kk + kBulkBatch <= np; kk += kBulkBatch) {
+      int2 c[kBulkBatch];
+      V x0[kBulkBatch], x1[kBulkBatch];
+#pragma unroll
+      for (int j = 0; j < kBulkBatch; j++) c[j] = cs[(kk + j) * 32];
+#pragma unroll
+      for (int j = 0; j < kBulkBatch; j++) x0[j] = ldg(a.x + c[j].x), x1[j] = ldg(a.x + c[j].y);
+#pragma unroll
+      for (int j = 0; j < kBulkBatch; j++) {
+        const PV v = vs[(kk + j) * 32];
+        s = fma(NEG ? -v.x : v.x, x0[j], s);
+        s = fma(NEG ? -v.y : v.y, x1[j], s);
+      }
+    }
+    for (; kk < np; kk++) {
+      const int2 c = cs[kk * 32];
+      const PV v = vs[kk * 32];
+      const V x0 = ldg(a.x + c.x), x1 = ldg(a.x + c.y);
+      s = fma(NEG ? -v.x : v.x, x0, s);
+      s = fma(NEG ? -v.y : v.y, x1, s);
+    }
+    if (row >= 0) sell_store<V, EPI>(a, row, s);
+    __syncwarp();  // every lane is done with this stage before it is refilled
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(k + kBulkStages);
+    }
+  }
+  if (!ok && lane == 0) {
+    atomicExch(err, 1);
+    for (int j = 0; j < kBulkStages; j++) {  // copies in flight land before the memory is released
+      const int kk = k + j;
+      if (gw + kk * nw < nslices) mbar_wait_bounded(&bar[2 * (kk % kBulkStages)], (uint32_t)(kk / kBulkStages) & 1u);
+    }
+  }
+  __syncwarp();
+  if (lane == 0)
+    for (int st = 0; st < kBulkStages; st++) mbar_inval(&bar[2 * st]);
 }
 
 // G y (two sign-coded entries) and A G y for one row per lane (see AgArgs).  WPS warps
@@ -898,6 +1182,41 @@ static void launch_sell_wide_t(const DevSell<double>& M, const SpmvArgs<float>& 
     launch_k(k_sell_wide<EPI, WPS, true>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a);
   else launch_k(k_sell_wide<EPI, WPS, false>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v2, a);
 }
+template <int EPI, int WPS>
+static void launch_sell_df_t(const DevSell<double>& M, const float4* v4, const SpmvArgs<float>& a, cudaStream_t s,
+                             bool pf) {
+  const int per = (kBlock / 32) / WPS;
+  const int grid = (M.nslices + per - 1) / per;
+  const int2* ci2 = reinterpret_cast<const int2*>(M.ci);
+  if (M.stream && pf && WPS <= 2)
+    launch_k(k_sell_df<EPI, WPS, true, true>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v4, a);
+  else if (M.stream)
+    launch_k(k_sell_df<EPI, WPS, true>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v4, a);
+  else launch_k(k_sell_df<EPI, WPS, false>, grid, kBlock, s, M.nslices, M.sptr, M.srow, ci2, v4, a);
+}
+template <int EPI>
+static void launch_sell_df_e(const DevSell<double>& M, const float4* v4, const SpmvArgs<float>& a, cudaStream_t s,
+                             int wps, bool pf) {
+  switch (wps) {
+    case 2: launch_sell_df_t<EPI, 2>(M, v4, a, s, pf); break;
+    case 4: launch_sell_df_t<EPI, 4>(M, v4, a, s, pf); break;
+    case 8: launch_sell_df_t<EPI, 8>(M, v4, a, s, pf); break;
+    default: launch_sell_df_t<EPI, 1>(M, v4, a, s, pf); break;
+  }
+}
+void launch_sell_df(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a, cudaStream_t s,
+                    int wps, bool pf) {
+  if (M.nslices == 0) return;
+  if (epi == EPI_RESID) launch_sell_df_e<EPI_RESID>(M, v4, a, s, wps, pf);
+  else if (epi == EPI_SWEEP) launch_sell_df_e<EPI_SWEEP>(M, v4, a, s, wps, pf);
+  else launch_sell_df_e<EPI_STORE>(M, v4, a, s, wps, pf);
+}
+void launch_df_split(int64_t npairs, const double* v, float4* out, cudaStream_t s) {
+  if (npairs <= 0) return;
+  const int grid = (int)std::min<int64_t>((npairs + kBlock - 1) / kBlock, 152 * 16);
+  k_df_split<<<grid, kBlock, 0, s>>>(npairs, reinterpret_cast<const double2*>(v), out);
+}
+
 template <int EPI>
 static void launch_sell_wide_e(const DevSell<double>& M, const SpmvArgs<float>& a, cudaStream_t s, int wps,
                                bool pf) {
@@ -943,6 +1262,94 @@ void launch_zero(int64_t n, V* x, cudaStream_t s) {
 }
 template void launch_zero<double>(int64_t, double*, cudaStream_t);
 template void launch_zero<float>(int64_t, float*, cudaStream_t);
+
+// Dynamic shared memory of a bulk-staged launch, or 0 where the operator's longest
+// slice does not fit (the caller then uses k_sell).
+template <typename V>
+size_t sell_bulk_smem(const DevSell<V>& M) {
+  if (M.max_pairs <= 0) return 0;
+  const size_t b = (size_t)kBulkWarps * (16 * kBulkStages + kBulkStages * bulk_stage_bytes<typename Pair<V>::T>(M.max_pairs));
+  return b <= 200 * 1024 ? b : 0;
+}
+
+// Per device: SM count once the kernels' shared-memory limit is raised (0: not yet).
+int g_bulk_sms[64] = {};
+
+template <typename V, int EPI>
+static void launch_sell_bulk_e(const DevSell<V>& M, const SpmvArgs<V>& a, cudaStream_t s, int* err, size_t smem,
+                               int sms) {
+  int per_sm = (int)((227 * 1024) / (smem + 1024));
+  per_sm = std::max(1, std::min(per_sm, 4));
+  const int need = (M.nslices + kBulkWarps - 1) / kBulkWarps;
+  const int grid = std::max(1, std::min(need, sms * per_sm));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = kBulkWarps * 32;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = dependent_launch_enabled() ? 1 : 0;
+  const int2* ci2 = reinterpret_cast<const int2*>(M.ci);
+  const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(M.val);
+  cudaLaunchKernelEx(&cfg, k_sell_bulk<V, EPI>, M.nslices, (const int64_t*)M.sptr, (const int*)M.srow, ci2, v2, a,
+                     M.max_pairs, err);
+}
+
+template <typename V>
+static void bulk_allow_smem() {
+  constexpr int b = 200 * 1024;
+  cudaFuncSetAttribute(k_sell_bulk<V, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaFuncSetAttribute(k_sell_bulk<V, EPI_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaFuncSetAttribute(k_sell_bulk<V, EPI_SCALE>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaFuncSetAttribute(k_sell_bulk<V, EPI_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaFuncSetAttribute(k_sell_bulk<V, EPI_SWEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaFuncSetAttribute(k_sell_bulk<V, EPI_STORE_MUL>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+}
+
+template <typename V>
+bool launch_sell_bulk(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, int* err) {
+  const size_t smem = sell_bulk_smem(M);
+  int dev = 0;
+  if (M.unit || smem == 0 || !err || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  const int sms = g_bulk_sms[dev];
+  if (sms <= 0) return false;  // sell_bulk_prepare has not run on this device
+  if (M.nslices == 0) return true;
+  switch (epi) {
+    case EPI_STORE: launch_sell_bulk_e<V, EPI_STORE>(M, a, s, err, smem, sms); break;
+    case EPI_RESID: launch_sell_bulk_e<V, EPI_RESID>(M, a, s, err, smem, sms); break;
+    case EPI_SCALE: launch_sell_bulk_e<V, EPI_SCALE>(M, a, s, err, smem, sms); break;
+    case EPI_ADD: launch_sell_bulk_e<V, EPI_ADD>(M, a, s, err, smem, sms); break;
+    case EPI_SWEEP: launch_sell_bulk_e<V, EPI_SWEEP>(M, a, s, err, smem, sms); break;
+    case EPI_STORE_MUL: launch_sell_bulk_e<V, EPI_STORE_MUL>(M, a, s, err, smem, sms); break;
+    default: return false;
+  }
+  return true;
+}
+
+void sell_bulk_prepare() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  if (g_bulk_sms[dev] > 0) return;
+  bulk_allow_smem<double>();
+  bulk_allow_smem<float>();
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return;
+  g_bulk_sms[dev] = sms;
+}
+template <typename V>
+bool sell_bulk_fits(const DevSell<V>& M) {
+  return !M.unit && sell_bulk_smem(M) > 0;
+}
+template bool sell_bulk_fits<double>(const DevSell<double>&);
+template bool sell_bulk_fits<float>(const DevSell<float>&);
+template bool launch_sell_bulk<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t, int*);
+template bool launch_sell_bulk<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t, int*);
 
 template <typename V, int LANES>
 static void launch_csrv_lanes(const DevCsr<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {

@@ -17,7 +17,8 @@ of the sums swamps it).  Step names:
   'post'  residual after the coarse-grid correction x += P e
   'post2' final point sweep after the post-smoothing aux sweep (no A G form)
   'gt', 'g', 'ag', 'pt', 'p'  the other products
-A policy maps (step, level) to 32 (all FP32) or 64 (FP64 values and sums).  `vec`
+A policy maps (step, level) to 32 (all FP32), 64 (FP64 values and sums) or 48
+(double-float: FP32 pairs for values and sums, see resid_df).  `vec`
 is the vector type between steps (float32 as on the GPU; float64 with policy_fp64
 makes the emulation an FP64 V-cycle, which pins its step order to the oracle).
 """
@@ -43,6 +44,49 @@ def policy_wide(step, level):
 
 def policy_fp64(step, level):
     return 64
+
+
+def policy_df(step, level):
+    """Residuals of corrected iterates in double-float arithmetic (below), the rest FP32."""
+    return 48 if step in CORRECTED else 32
+
+
+def split_df(v):
+    """A value as the float32 pair hi + lo (hi = fl32(v), lo = fl32(v - hi))."""
+    hi = v.astype(f32)
+    lo = (v - hi.astype(f64)).astype(f32)
+    return hi, lo
+
+
+def resid_df(A, x, b):
+    """b - A x in double-float arithmetic on float32 data, row by row in stored
+    order: each entry's hi x exactly as a float32 pair (product and its FMA
+    remainder), lo x added to the remainder, the running sum kept as an unnormalized
+    pair (two-sum of the high parts, the low parts summed), rounded once at the end.
+    The float32 steps are numpy float32 operations; the exact remainder of a float32
+    product is formed in float64 (where the product is exact) and is a float32."""
+    A = A.tocsr()
+    n = A.shape[0]
+    lens = np.diff(A.indptr)
+    w = int(lens.max()) if n else 0
+    x = x.astype(f32)
+    sh = b.astype(f32).copy()
+    sl = np.zeros(n, dtype=f32)
+    hi_all, lo_all = split_df(A.data)
+    for k in range(w):
+        rows = np.nonzero(lens > k)[0]
+        pos = A.indptr[rows] + k
+        hi, lo = -hi_all[pos], -lo_all[pos]
+        xv = x[A.indices[pos]]
+        p = hi * xv
+        e = (hi.astype(f64) * xv.astype(f64) - p.astype(f64)).astype(f32)
+        t = (lo.astype(f64) * xv.astype(f64) + e.astype(f64)).astype(f32)
+        s = sh[rows] + p
+        bp = s - sh[rows]
+        err = (sh[rows] - (s - bp)) + (p - bp)
+        sh[rows] = s
+        sl[rows] = sl[rows] + (err + t)
+    return sh + sl
 
 
 class EmulatedVcycle:
@@ -80,6 +124,8 @@ class EmulatedVcycle:
 
     def _resid(self, l, step, x, b):
         A = self.A[l]
+        if self.policy(step, l) == 48:
+            return resid_df(A, x, b).astype(self.vec)
         if self.policy(step, l) == 64:
             return (b.astype(f64) - A @ x.astype(f64)).astype(self.vec)
         return (b.astype(f32) - self._f32[id(A)] @ x.astype(f32)).astype(self.vec)

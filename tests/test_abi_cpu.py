@@ -49,6 +49,7 @@ def test_validation_without_gpu(lib):
     assert lib.amge_hier_info(None, None, None, None) == 1
     assert lib.amge_vcycle(None, None, None, 1, 0, None) == 1
     assert lib.amge_pcg_solve(None, None, None, 1, None, None, None) == 1
+    assert lib.amge_wait_status(None, None, None) == 1
     lib.amge_hier_free(None)
 
 

@@ -93,10 +93,11 @@ class pinned_level0:
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200])
+@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200, 3000])
 def test_level0_products_sampled(amge, name, prec, kernels):
-    """The level-0 products on the autotuned kernels, and on the sliced-ELL kernels that
-    prefetch each slice into L2 with one and two warps per slice."""
+    """The level-0 products on the autotuned kernels, on the sliced-ELL kernels that
+    prefetch each slice into L2 with one and two warps per slice, and on the one that
+    stages each warp's slices into shared memory by bulk copies."""
     h, o, _ = workload(amge, name)
     with pinned_level0(amge, h, kernels):
         _level0_products(amge, h, o, name, prec)
@@ -136,13 +137,20 @@ def _level0_products(amge, h, o, name, prec):
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 @pytest.mark.parametrize("kernels", ["tuned", 1000, 1200])
-def test_level0_wide_product_sampled(amge, name, kernels):
+@pytest.mark.parametrize("arith", [1, 0])
+def test_level0_wide_product_sampled(amge, name, kernels, arith):
+    """The level-0 product of the FP32 V-cycle's corrected residuals, in double-float
+    (1) and FP64 (0) arithmetic, on a near-gradient field (most of A x cancels)."""
     h, o, _ = workload(amge, name)
-    with pinned_level0(amge, h, kernels):
-        _level0_wide(amge, h, o, name)
+    try:
+        amge.amge_set_wide_arith(h, arith)
+        with pinned_level0(amge, h, kernels):
+            _level0_wide(amge, h, o, name, arith)
+    finally:
+        amge.amge_set_wide_arith(h, amge.AMGE_WIDE_DF)
 
 
-def _level0_wide(amge, h, o, name):
+def _level0_wide(amge, h, o, name, arith):
     rng = np.random.default_rng(9)
     A, G = o.A[0], o.G[0]
     x = G @ rng.uniform(-1, 1, G.shape[1]) + 1e-3 * rng.uniform(-1, 1, A.shape[1])
@@ -152,9 +160,33 @@ def _level0_wide(amge, h, o, name):
     rows = sample_rows(A.shape[0], rng)
     Ar = A[rows]
     ref = Ar @ x32
-    bound = 0.5 * EPS32 * np.abs(ref) + 2 * (np.diff(Ar.indptr) + 1) * EPS64 * (abs(Ar) @ abs(x32))
+    w = np.diff(Ar.indptr)
+    if arith == amge.AMGE_WIDE_FP64:
+        bound = 0.5 * EPS32 * np.abs(ref) + 2 * (w + 1) * EPS64 * (abs(Ar) @ abs(x32))
+    else:  # double-float: 48-bit values, pair sums (see the parity test's wide_bound)
+        bound = 0.5 * EPS32 * np.abs(ref) + (w * w + 4 * w + 8) * 2.0 ** -48 * (abs(Ar) @ abs(x32))
     err = np.abs(host(y)[rows] - ref)
     assert np.all(err <= bound + 1e-300), (name, float((err / (bound + 1e-300)).max()))
+
+
+@pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_level0_bulk_staged_equals_one_warp(amge, name, prec):
+    """At full size, in the launch configuration of the timed solves: the level-0
+    operators on the bulk-staged kernel (code 3000) give the V-cycle and the PCG solve
+    of the one-warp sliced-ELL kernel (code 0) bit for bit."""
+    h, o, b = workload(amge, name)
+    bd = dev(b)
+    res = []
+    for code in (0, 3000):
+        with pinned_level0(amge, h, code):
+            z, x = torch.empty_like(bd), torch.empty_like(bd)
+            amge.amge_vcycle(h, bd, z, 1, prec)
+            st, info = amge.amge_pcg_solve(h, bd, x, rtol=1e-8, precision=prec)
+            assert st == amge.AMGE_OK and not amge.amge_wait_status(h)
+            res.append((z, x, info[0]["iters"]))
+    (z0, x0, i0), (z1, x1, i1) = res
+    assert torch.equal(z0, z1) and torch.equal(x0, x1) and i0 == i1
 
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])

@@ -91,11 +91,12 @@ class pinned_kernels:
 
 @pytest.mark.parametrize("form,n,L", CASES)
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("lanes", ["tuned", 0, 200, 800, 4, 32])
+@pytest.mark.parametrize("lanes", ["tuned", 0, 200, 800, 4, 32, 3000])
 def test_single_operators(amge, form, n, L, prec, lanes):
     """Every stored product on every smoothing level, on each kernel: sliced ELL with
-    one, two and eight warps per slice (sign-coded for the +-1 incidences G), vector
-    CSR with 4 and 32 lanes per row, and the autotuned choice."""
+    one, two and eight warps per slice (sign-coded for the +-1 incidences G), with the
+    slices staged into shared memory by bulk copies (3000), vector CSR with 4 and 32
+    lanes per row, and the autotuned choice."""
     h = upload(amge, form, n, L)
     o = oracle_hierarchy(form, n, L, True)
     rng = np.random.default_rng(n * 7 + L)
@@ -157,6 +158,42 @@ def test_fused_aux_correction_equals_separate_products(amge, prec, ag):
             amge.amge_set_kernel(h, l, pname, "AG", ag)
     torch.cuda.synchronize()
     assert torch.isfinite(zf).all() and torch.equal(zf, zs)
+
+
+@pytest.mark.parametrize("form,n,L", [("hcurl", 8, 2), ("hdiv", 24, 3), ("hcurl", 24, 3)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bulk_staged_equals_one_warp_kernel(amge, form, n, L, prec):
+    """The bulk-staged product (code 3000: each warp's slices copied into shared memory
+    two ahead) forms every row's sum in the order of the one-warp sliced-ELL kernel
+    (code 0): products, V-cycles and graph-driven PCG solves are identical, and no
+    staged copy's wait runs out."""
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, form, n, L)
+    o = oracle_hierarchy(form, n, L, True)
+    b = dev(rhs_vector(83, h.n))
+    res = {}
+    for code in (0, 3000):
+        with pinned_kernels(amge, h, code):
+            out = []
+            for l in range(L - 1):
+                shapes = {amge.AMGE_OP_A: o.A[l].shape, amge.AMGE_OP_P: o.P[l].shape,
+                          amge.AMGE_OP_PT: o.P[l].T.shape, amge.AMGE_OP_G: o.G[l].shape,
+                          amge.AMGE_OP_GT: o.G[l].T.shape}
+                for op, (nr, nc) in shapes.items():
+                    x = dev(np.random.default_rng(l * 10 + op).uniform(-1, 1, nc))
+                    y = torch.empty(nr, dtype=torch.float64, device="cuda")
+                    amge.amge_apply(h, op, l, x, y, prec)
+                    out.append(y)
+            z, x = torch.empty_like(b), torch.empty_like(b)
+            amge.amge_vcycle(h, b, z, precision=prec)
+            st, info = amge.amge_pcg_solve(h, b, x, precision=prec)
+            assert st == amge.AMGE_OK
+            res[code] = (out, z, x, info[0]["iters"])
+            assert not amge.amge_wait_status(h)
+    (o0, z0, x0, i0), (o1, z1, x1, i1) = res[0], res[3000]
+    assert all(torch.equal(a, c) for a, c in zip(o0, o1))
+    assert torch.equal(z0, z1) and torch.equal(x0, x1) and i0 == i1
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -295,29 +332,79 @@ def test_vcycle_fp32_close_to_oracle(amge, form, n, L):
     assert err <= 1e-3, err
 
 
+def wide_bound(amge, arith, A, x32, ref):
+    """Error bound of AMGE_OP_A_WIDE (y = fl32(A x) with x in FP32): the final
+    rounding plus the sum's own error -- FP64 recursive summation for AMGE_WIDE_FP64;
+    for AMGE_WIDE_DF the 48-bit value split, the product remainders and the
+    unnormalized pair sum, at most (w^2 + 4 w + 8) 2^-48 |A| |x| for rows of w entries."""
+    w = np.diff(A.indptr)
+    ax = abs(A) @ abs(x32)
+    if arith == amge.AMGE_WIDE_FP64:
+        return 0.5 * EPS32 * np.abs(ref) + 2 * (w + 1) * EPS64 * ax
+    return 0.5 * EPS32 * np.abs(ref) + (w * w + 4 * w + 8) * 2.0 ** -48 * ax
+
+
 @pytest.mark.parametrize("form,n,L", FP32_CASES)
 @pytest.mark.parametrize("field", ["random", "gradient"])
-def test_wide_product(amge, form, n, L, field):
-    """AMGE_OP_A_WIDE on every smoothing level: FP32 input, FP64 values and sums, FP32
-    output.  On gradient (curl) fields, where the large-coefficient part of A x
-    cancels, only FP64 sums meet the bound."""
+@pytest.mark.parametrize("arith", [1, 0])
+def test_wide_product(amge, form, n, L, field, arith):
+    """AMGE_OP_A_WIDE on every smoothing level: FP32 input and output, values and sums
+    in double-float pairs (arith 1, the default) or FP64 (0).  On gradient (curl)
+    fields, where the large-coefficient part of A x cancels, only sums carried well
+    beyond FP32 meet the bound (the CPU emulation tests show FP32 failing it)."""
     h = upload(amge, form, n, L)
     o = oracle_hierarchy(form, n, L, True)
     rng = np.random.default_rng(n + 3 * L)
-    for l in range(L - 1):
-        A = o.A[l]
-        x = rng.uniform(-1, 1, A.shape[1])
-        if field == "gradient":
-            x = o.G[l] @ rng.uniform(-1, 1, o.G[l].shape[1]) + 1e-3 * x
-        x32 = x.astype(np.float32).astype(np.float64)
-        y = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
-        amge.amge_apply(h, amge.AMGE_OP_A_WIDE, l, dev(x), y, amge.AMGE_FP32_VCYCLE)
-        ref = A @ x32
-        bound = 0.5 * EPS32 * np.abs(ref) + 2 * (np.diff(A.indptr) + 1) * EPS64 * (abs(A) @ abs(x32))
-        err = np.abs(host(y) - ref)
-        assert np.all(err <= bound + 1e-300), (l, float((err / (bound + 1e-300)).max()))
+    try:
+        amge.amge_set_wide_arith(h, arith)
+        for l in range(L - 1):
+            A = o.A[l]
+            x = rng.uniform(-1, 1, A.shape[1])
+            if field == "gradient":
+                x = o.G[l] @ rng.uniform(-1, 1, o.G[l].shape[1]) + 1e-3 * x
+            x32 = x.astype(np.float32).astype(np.float64)
+            y = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+            amge.amge_apply(h, amge.AMGE_OP_A_WIDE, l, dev(x), y, amge.AMGE_FP32_VCYCLE)
+            ref = A @ x32
+            bound = wide_bound(amge, arith, A, x32, ref)
+            err = np.abs(host(y) - ref)
+            assert np.all(err <= bound + 1e-300), (l, float((err / (bound + 1e-300)).max()))
+    finally:
+        amge.amge_set_wide_arith(h, amge.AMGE_WIDE_DF)
     with pytest.raises(amge.AmgeError):             # FP32 V-cycle product only
         amge.amge_apply(h, amge.AMGE_OP_A_WIDE, 0, dev(x), y, amge.AMGE_FP64)
+    with pytest.raises(amge.AmgeError):
+        amge.amge_set_wide_arith(h, 2)
+
+
+@pytest.mark.parametrize("form,n,L", [("hcurl", 16, 2), ("hdiv", 24, 3)])
+def test_wide_arith_modes_in_the_fp32_solve(amge, form, n, L):
+    """Both arithmetics of the residuals of corrected iterates give FP32-V-cycle PCG
+    solves that reach the FP64 tolerance in the FP64 iteration count (+3), and the
+    V-cycles agree to the FP32 rounding level."""
+    from oracle.amge_oracle import pcg
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h = upload(amge, form, n, L)
+    o = oracle_hierarchy(form, n, L, True)
+    b = rhs_vector(89, h.n)
+    _, it_o, _, _ = pcg(o, b, rtol=1e-8)
+    z = {}
+    try:
+        for arith in (amge.AMGE_WIDE_FP64, amge.AMGE_WIDE_DF):
+            amge.amge_set_wide_arith(h, arith)
+            x = torch.empty(h.n, dtype=torch.float64, device="cuda")
+            st, info = amge.amge_pcg_solve(h, dev(b), x, precision=amge.AMGE_FP32_VCYCLE)
+            assert st == amge.AMGE_OK and info[0]["iters"] <= it_o + 3, (arith, info[0]["iters"], it_o)
+            assert np.linalg.norm(b - o.A[0] @ host(x)) <= 1e-8 * np.linalg.norm(b)
+            z[arith] = torch.empty_like(x)
+            amge.amge_vcycle(h, dev(b), z[arith], precision=amge.AMGE_FP32_VCYCLE)
+    finally:
+        amge.amge_set_wide_arith(h, amge.AMGE_WIDE_DF)
+    d = host(z[0]) - host(z[1])
+    A = o.A[0]
+    ref = host(z[0])
+    assert np.sqrt(d @ (A @ d)) <= 1e-4 * np.sqrt(ref @ (A @ ref))
 
 
 @pytest.mark.parametrize("form,n,L", CASES)
@@ -670,5 +757,5 @@ def test_autotune_report(amge):
     h = upload(amge, "hcurl", 24, 3)
     rep = amge.amge_autotune_report(h)
     assert len(rep) == 2 * 2 * 6
-    assert set(rep.values()) <= {-1, 0, 200, 400, 800, 1000, 1200, 2, 4, 8, 16, 32}
+    assert set(rep.values()) <= {-1, 0, 200, 400, 800, 1000, 1200, 3000, 2, 4, 8, 16, 32}
     assert rep[(0, "fp64", "AG")] >= 0          # H(curl): A G is stored (much sparser than A)
