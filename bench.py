@@ -579,7 +579,8 @@ def run_ours(args, dist):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("f32 V-cycle (f64 values and sums for residuals of corrected iterates) in f64 PCG" if fp32
+        "dtype": (f"f32 V-cycle ({'double-float' if args.wide_arith == 'df' else 'f64'} values and sums for "
+                  "residuals of corrected iterates) in f64 PCG" if fp32
                   else "f64"),
         "data": "synthetic",
         "config": workload_config(wl, hh),
@@ -642,8 +643,9 @@ def run_ours(args, dist):
                                         "peak_source": "amge_fp64_fma_rate on this GPU in this run (of measured)"}
     vc_ms = sum(prof[k][1] for k in ("A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "vcycle_vec", "AG",
                                      "A_wide"))
-    # one coarsest solve per V-cycle: one kernel (FP32 V-cycle: widening + product)
-    n_vc = prof["coarse"][0] / (2 if fp32 else 1)
+    # one coarsest solve per V-cycle: one kernel (FP32 V-cycle with FP64 arithmetic:
+    # widening + product)
+    n_vc = prof["coarse"][0] / (2 if fp32 and args.wide_arith == "fp64" else 1)
     if vc_ms > 0 and n_vc > 0 and nrhs == 1:
         ag_nnz = [stored_ag_nnz(hh.A[l], hh.G[l]) if tuned.get((l, pname, "AG"), -1) >= 0 else None
                   for l in range(len(hh.A) - 1)]

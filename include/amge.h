@@ -63,9 +63,9 @@ typedef enum { AMGE_HCURL = 2, AMGE_HDIV = 3 } amge_form;
  * values and sums, see amge_set_wide_arith), rounded once to single, because on
  * such iterates most of A_l x cancels and single-precision rounding would swamp the
  * residual's gradient (curl) part that the aux sweep and the coarse solve divide by
- * small mass-only diagonals.  The
- * coarsest-level solve, the outer PCG dot products, AXPYs and the true-residual
- * recomputation stay in double precision. */
+ * small mass-only diagonals.  The coarsest-level solve runs in the same ~48-bit
+ * arithmetic (rounded to single); the outer PCG dot products, AXPYs and the
+ * true-residual recomputation stay in double precision. */
 typedef enum { AMGE_FP64 = 0, AMGE_FP32_VCYCLE = 1 } amge_precision;
 
 /* A CSR matrix in host memory: row_ptr[n_rows+1], col[nnz] (0-based, each row's
@@ -318,7 +318,10 @@ amge_status amge_set_smoother(amge_hier* h, int32_t smoother, int32_t sweeps, in
  *   AMGE_WIDE_FP64  FP64 values and an FP64 FMA chain per row on the FP32 vectors
  *                   widened exactly (error of FP64 recursive summation).
  * Both read 8 value bytes per entry (the double-float pairs are a resident copy of
- * A_l beside the FP64 and FP32 ones) and round the result once to single.  On GB300
+ * A_l beside the FP64 and FP32 ones) and round the result once to single.  The same
+ * switch selects the arithmetic of the FP32 V-cycle's coarsest solve z = A_L^{-1} b
+ * (the explicit inverse as double-float pairs with pair sums, or in FP64 with the
+ * input widened first); its result is rounded to single either way.  On GB300
  * the FP64 form is co-limited by the FP64 FMA rate (one FMA per entry), the
  * double-float form by HBM.  Captured PCG graphs of h are rebuilt on the next
  * solve.  AMGE_EINVAL for another value or a NULL h. */

@@ -339,12 +339,28 @@ void vcycle_level_gs(amge_hier* h, int l, const double* b, double* z, cudaStream
 // One V-cycle at level l: z = B_l^{-1} b (Algorithm 4.1, x0 = 0).  x_ready: the
 // level's first point sweep from zero, x = m^-1 b, was already written into x by the
 // restriction that produced b.
+// The FP32 V-cycle's coarsest solve: double-float (one launch) or FP64 with the
+// input widened first (two), per amge_set_wide_arith.
+void coarse_solve_f32(amge_hier* h, const float* b, float* z, cudaStream_t s) {
+  if (h->wide_arith == AMGE_WIDE_DF && h->Ainv_df) {
+    Prof p(h, AMGE_PROF_COARSE, s);
+    launch_coarse_inv_df(h->nC, h->Ainv_df, b, z, s);
+    return;
+  }
+  Prof p(h, AMGE_PROF_COARSE, s, 2);
+  launch_coarse_inv<float, float>(h->nC, h->Ainv, b, h->ct, z, s);
+}
+
 template <typename V>
 void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_ready) {
   auto& lv = levels<V>(h);
   if (l == h->L - 1) {
-    Prof p(h, AMGE_PROF_COARSE, s, std::is_same<V, float>::value ? 2 : 1);  // FP32: + the widening
-    launch_coarse_inv<V, V>(h->nC, h->Ainv, b, h->ct, z, s);
+    if constexpr (std::is_same<V, float>::value) {
+      coarse_solve_f32(h, b, z, s);
+    } else {
+      Prof p(h, AMGE_PROF_COARSE, s);
+      launch_coarse_inv<V, V>(h->nC, h->Ainv, b, h->ct, z, s);
+    }
     return;
   }
   if constexpr (std::is_same<V, double>::value) {
@@ -483,8 +499,7 @@ void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, 
       launch_cast<double, float>(h->n0, r, d.b, s);
     }
     if (h->L == 1) {
-      Prof p(h, AMGE_PROF_COARSE, s, 2);
-      launch_coarse_inv<float, float>(h->nC, h->Ainv, d.b, h->ct, d.z, s);
+      coarse_solve_f32(h, d.b, d.z, s);
     } else {
       vcycle_level<float>(h, 0, d.b, d.z, s, x0_ready);
     }
@@ -1901,6 +1916,8 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
           coarse_inverse(n[l], LiT, Ai);
           keepd.push_back(std::move(Ai));
           h->Ainv = upload<double>(h, keepd.back().data(), (size_t)n[l] * n[l], s);
+          h->Ainv_df = dalloc<float2>(h, (size_t)n[l] * n[l]);
+          launch_df_split_entries((int64_t)n[l] * n[l], h->Ainv, h->Ainv_df, s);
         }
         keepd.push_back(std::move(LiT));
         h->LinvT = upload<double>(h, keepd.back().data(), (size_t)n[l] * n[l], s);

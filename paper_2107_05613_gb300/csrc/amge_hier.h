@@ -91,6 +91,7 @@ struct amge_hier {
   int nC = 0;
   double *Linv = nullptr, *LinvT = nullptr, *ct = nullptr;
   double* Ainv = nullptr;  // explicit coarsest inverse (single-vector V-cycles)
+  float2* Ainv_df = nullptr;  // the same as double-float pairs (FP32 V-cycles, AMGE_WIDE_DF)
   double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
   double *stage_b = nullptr, *stage_x = nullptr;
   float *s32_in = nullptr, *s32_out = nullptr;

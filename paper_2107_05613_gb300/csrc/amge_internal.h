@@ -158,6 +158,10 @@ void launch_sell_df(const DevSell<double>& M, const float4* v4, int epi, const S
                     int wps = 1, bool pf = false);
 // v4 from the FP64 sliced-ELL values v (npairs = stored entries / 2).
 void launch_df_split(int64_t npairs, const double* v, float4* out, cudaStream_t s);
+// Coarsest solve of the FP32 V-cycle in double-float arithmetic: z = A^{-1} b with
+// the inverse as {hi, lo} float pairs (launch_df_split_entries of the FP64 inverse).
+void launch_coarse_inv_df(int n, const float2* Ainv_df, const float* b, float* z, cudaStream_t s);
+void launch_df_split_entries(int64_t n, const double* v, float2* out, cudaStream_t s);
 
 // Gauss-Seidel update of one colour's rows: slices [s0, s1) of a colour-grouped
 // sliced-ELL operator, x_i += dinv_i (b_i - (M x)_i) in place (FP64).

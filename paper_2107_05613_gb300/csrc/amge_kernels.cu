@@ -833,6 +833,68 @@ __global__ void __launch_bounds__(kTriBlock, 16) k_densemv(int n, const double* 
   if (threadIdx.x == 0) y[row] = (Tout)t;
 }
 
+// The FP32 V-cycle's coarsest solve z = A^{-1} b in double-float arithmetic: the
+// inverse as float pairs {hi, lo} per entry (8 bytes, as FP64), FP32 b read as is,
+// each thread's column sum as a float pair (df_add_entry), the block's partial pairs
+// combined in a fixed order by warp 0 (df_add), z = fl(hi + lo).  No FP64 work and no
+// widening pass: the FP64 form spends one FP64 FMA per entry of the n^2 inverse.
+template <int NT>
+__device__ __forceinline__ DfSum df_block_sum(DfSum v, float2* sh) {
+  sh[threadIdx.x] = make_float2(v.h, v.l);
+  __syncthreads();
+  DfSum t{0.f, 0.f};
+  if (threadIdx.x < 32) {
+    const float2 a = sh[threadIdx.x];
+    t = DfSum{a.x, a.y};
+#pragma unroll
+    for (int k = 1; k < NT / 32; k++) {
+      const float2 o = sh[threadIdx.x + 32 * k];
+      df_add(t, DfSum{o.x, o.y});
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const DfSum o{__shfl_xor_sync(0xffffffffu, t.h, off), __shfl_xor_sync(0xffffffffu, t.l, off)};
+      df_add(t, o);
+    }
+  }
+  return t;
+}
+
+__global__ void __launch_bounds__(kTriBlock, 16) k_densemv_df(int n, const float2* __restrict__ M,
+                                                             const float* __restrict__ x, float* __restrict__ y) {
+  __shared__ float2 part[kTriBlock];
+  const int row = blockIdx.x;
+  const float2* m = M + (size_t)row * n;
+  float2 mr[kDensePre];
+#pragma unroll
+  for (int i = 0; i < kDensePre; i++) {
+    const int j = (int)threadIdx.x + i * kTriBlock;
+    mr[i] = j < n ? ldg(m + j) : make_float2(0.f, 0.f);
+  }
+  pdl_begin();
+  DfSum s{0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < kDensePre; i++) {
+    const int j = (int)threadIdx.x + i * kTriBlock;
+    if (j < n) df_add_entry(s, mr[i].x, mr[i].y, ldg(x + j));
+  }
+  for (int j = (int)threadIdx.x + kDensePre * kTriBlock; j < n; j += kTriBlock) {
+    const float2 v = ldg(m + j);
+    df_add_entry(s, v.x, v.y, ldg(x + j));
+  }
+  const DfSum t = df_block_sum<kTriBlock>(s, part);
+  if (threadIdx.x == 0) y[row] = __fadd_rn(t.h, t.l);
+}
+
+// Double-float copy {hi, lo} of n doubles.
+__global__ void k_df_split_entries(int64_t n, const double* __restrict__ v, float2* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = v[i];
+    const float h = __double2float_rn(a);
+    out[i] = make_float2(h, __double2float_rn(a - (double)h));
+  }
+}
+
 // ---------------------------------------------------------------- reductions
 // Block sum in a fixed order, valid in thread 0.  On GB300 every FP64 add counts (the
 // FP64 pipe runs at 1/65 of the FP32 rate and a warp-wide add occupies it as long as
@@ -1448,6 +1510,15 @@ void launch_coarse_inv(int n, const double* Ainv, const Tin* b, double* t, Tout*
     launch_cast<Tin, double>(n, b, t, s);
     launch_k(k_densemv<double, Tout>, n, kTriBlock, s, n, Ainv, (const double*)t, z);
   }
+}
+void launch_coarse_inv_df(int n, const float2* Ainv_df, const float* b, float* z, cudaStream_t s) {
+  if (n <= 0) return;
+  launch_k(k_densemv_df, n, kTriBlock, s, n, Ainv_df, b, z);
+}
+void launch_df_split_entries(int64_t n, const double* v, float2* out, cudaStream_t s) {
+  if (n <= 0) return;
+  const int grid = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, 152 * 16);
+  k_df_split_entries<<<grid, kBlock, 0, s>>>(n, v, out);
 }
 template void launch_coarse_inv<double, double>(int, const double*, const double*, double*, double*, cudaStream_t);
 template void launch_coarse_inv<float, float>(int, const double*, const float*, double*, float*, cudaStream_t);

@@ -307,6 +307,11 @@ amge_status update_coefficients(amge_hier* h, const double* beta, const double* 
   UCK(cudaMemcpy(h->Linv, Li.data(), nn, cudaMemcpyHostToDevice));
   UCK(cudaMemcpy(h->LinvT, LiT.data(), nn, cudaMemcpyHostToDevice));
   UCK(cudaMemcpy(h->Ainv, Ai.data(), nn, cudaMemcpyHostToDevice));
+  if (h->Ainv_df) {
+    launch_df_split_entries((int64_t)h->nC * h->nC, h->Ainv, h->Ainv_df, s);
+    UCK(cudaGetLastError());
+    UCK(cudaStreamSynchronize(s));
+  }
   return AMGE_OK;
 }
 

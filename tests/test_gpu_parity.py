@@ -504,6 +504,38 @@ def test_one_level_hierarchy_is_direct(amge):
     assert np.linalg.norm(host(x) - np.linalg.solve(A.toarray(), b)) <= 1e-10 * np.linalg.norm(host(x))
 
 
+@pytest.mark.parametrize("arith", [1, 0])
+def test_fp32_coarsest_solve(amge, arith):
+    """The FP32 V-cycle's coarsest solve (one-level hierarchy: the V-cycle is the
+    coarsest solve): FP32 input and output, the explicit inverse in double-float pairs
+    with pair sums (1) or in FP64 (0), against the FP64 direct solution of the FP32
+    input: within the final rounding plus the sum's error bound over n terms."""
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    hh = hierarchy("hcurl", 6, 1, True)
+    h = amge.amge_upload_levels(hh)
+    A = hh.A[0].to_scipy().toarray()
+    Ainv = np.linalg.inv(A)
+    b32 = rhs_vector(3, A.shape[0]).astype(np.float32).astype(np.float64)
+    ref = Ainv @ b32
+    n = A.shape[0]
+    scale = np.abs(Ainv) @ np.abs(b32)
+    # the explicit inverse itself carries the Cholesky rounding: kappa eps_64 |A^-1||b|
+    kappa = np.linalg.cond(A)
+    if arith == 1:
+        bound = 0.5 * EPS32 * np.abs(ref) + ((n / 128 + 8) ** 2 + 300) * 2.0 ** -48 * scale + 10 * kappa * EPS64 * scale
+    else:
+        bound = 0.5 * EPS32 * np.abs(ref) + 2 * n * EPS64 * scale + 10 * kappa * EPS64 * scale
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    try:
+        amge.amge_set_wide_arith(h, arith)
+        amge.amge_vcycle(h, dev(b32), z, 1, amge.AMGE_FP32_VCYCLE)
+        err = np.abs(host(z) - ref)
+        assert np.all(err <= bound), float((err / bound).max())
+    finally:
+        h.free()
+
+
 def test_solve_is_deterministic(amge):
     from paper_2107_05613_gb300.inputs import rhs_vector
 
