@@ -926,10 +926,22 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
     c.x = d.Y, c.y = x;
     mm(AMGE_PROF_G, OP_G, EPI_ADD, c);
   };
-  auto residual = [&]() {
+  // A products; `corrected`: x carries a correction through G or P (FP32: double-float
+  // values and sums, as in a_product)
+  auto a_mm = [&](bool corrected, int epi, const SpmvArgs<V>& a) {
+    if constexpr (std::is_same<V, float>::value) {
+      if (corrected && d.cAdf) {
+        Prof p(h, l == 0 ? AMGE_PROF_A_WIDE : AMGE_PROF_A_COARSE, s);
+        launch_csr_mm_df(d.cA, d.cAdf, nrhs, epi, a, s);
+        return;
+      }
+    }
+    mm(clsA, OP_A, epi, a);
+  };
+  auto residual = [&](bool corrected) {
     SpmvArgs<V> a;
     a.x = x, a.b = b, a.y = d.R;
-    mm(clsA, OP_A, EPI_RESID, a);
+    a_mm(corrected, EPI_RESID, a);
   };
   LevelDev<V>& c = lv[l + 1];
   const bool c_smooths = l + 1 < h->L - 1;  // the next level starts with X = m^-1 B
@@ -944,7 +956,7 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
       Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
       launch_mul_mm<V>(d.n, nrhs, d.minv, b, x, s);
     }
-    residual();
+    residual(false);
     aux_sweep();
     {
       SpmvArgs<V> a;
@@ -958,7 +970,7 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
       a.x = c.Z, a.y = x;
       mm(AMGE_PROF_P, OP_P, EPI_ADD, a);
     }
-    residual();
+    residual(true);
     aux_sweep();
     SpmvArgs<V> a;
     a.x = d.Y, a.xin = x, a.d = d.minv, a.b = d.R, a.y = z;
@@ -971,17 +983,17 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
         Prof p(h, AMGE_PROF_VCYCLE_VEC, s);
         launch_mul_mm<V>(d.n, nrhs, d.minv, b, x, s);
       }
-      residual();
+      residual(false);
     } else {
       SpmvArgs<V> a;
       a.x = x, a.xin = x, a.d = d.minv, a.b = b, a.y = xt;
-      mm(clsA, OP_A, EPI_SWEEP, a);
+      a_mm(true, EPI_SWEEP, a);
       std::swap(x, xt);
-      residual();
+      residual(true);
     }
     aux_sweep();
   }
-  residual();
+  residual(true);
   restrict_to_next();
   vcycle_level_mm<V>(h, l + 1, nrhs, c.B, c.Z, s, c_smooths);
   {
@@ -990,12 +1002,12 @@ void vcycle_level_mm(amge_hier* h, int l, int nrhs, const V* b, V* z, cudaStream
     mm(AMGE_PROF_P, OP_P, EPI_ADD, a);
   }
   for (int k = 0; k < h->nu_post; k++) {
-    residual();
+    residual(true);
     aux_sweep();
     const bool last = (k == h->nu_post - 1);
     SpmvArgs<V> a;
     a.x = x, a.xin = x, a.d = d.minv, a.b = b, a.y = last ? z : xt;
-    mm(clsA, OP_A, EPI_SWEEP, a);
+    a_mm(true, EPI_SWEEP, a);
     if (!last) std::swap(x, xt);
   }
 }
@@ -1867,6 +1879,8 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
         upload_sell(h, G, d64.G, d32.G, s, keep, keeps, true);
         upload_sell(h, GT, d64.GT, d32.GT, s, keep, keeps, true);
         upload_csr(h, A, d64.cA, d32.cA, s, keep);
+        d32.cAdf = dalloc<float2>(h, (size_t)d64.cA.nnz);
+        launch_df_split_entries(d64.cA.nnz, d64.cA.val, d32.cAdf, s);
         upload_csr(h, P, d64.cP, d32.cP, s, keep);
         upload_csr(h, PT, d64.cPT, d32.cPT, s, keep);
         upload_csr(h, G, d64.cG, d32.cG, s, keep);

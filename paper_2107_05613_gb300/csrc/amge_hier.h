@@ -46,6 +46,7 @@ struct LevelDev {
   // FP32 V-cycle (lv32): A_l's values as double-float pairs {hi0, hi1, lo0, lo1} per
   // entry pair of the FP64 sliced-ELL copy (launch_sell_df)
   float4* Adf = nullptr;
+  float2* cAdf = nullptr;  // the same for the CSR copy (block V-cycles)
   V* minv = nullptr;
   V* mauxinv = nullptr;
   V *x = nullptr, *r = nullptr, *y = nullptr, *tmp = nullptr;

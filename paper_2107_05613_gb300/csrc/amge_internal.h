@@ -25,6 +25,38 @@ __device__ __forceinline__ void pdl_begin() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+
+// Double-float arithmetic on the FP32 pipe, for the FP32 V-cycle's products that
+// need more than single precision (GB300's FP64 pipe issues at 1/64 of the FP32
+// rate).  A value a is kept as the float pair hi + lo (hi = fl(a), lo = fl(a - hi):
+// 48 significant bits).  Per entry: p = fl(hi x), e = fma(hi, x, -p) (the exact
+// remainder of the product), t = fma(lo, x, e); the running sum is an unnormalized
+// pair (h, l): h <- h + p by a two-sum whose exact rounding error, plus t, is added to
+// l.  The result is fl(h + l).  The error is a few multiples of 2^-48 |A| |x| per
+// summed entry: under the 1e6 coefficient contrast, where most of A x cancels on
+// corrected iterates (c_A eps_32 ~ 1), c_A 2^-43 ~ 1e-6.  Round-to-nearest
+// intrinsics throughout, which the compiler does not contract.
+struct DfSum {
+  float h, l;
+};
+__device__ __forceinline__ void df_add_entry(DfSum& s, float hi, float lo, float x) {
+  const float p = __fmul_rn(hi, x);
+  const float e = __fmaf_rn(hi, x, -p);
+  const float t = __fmaf_rn(lo, x, e);
+  const float sh = __fadd_rn(s.h, p);
+  const float bp = __fsub_rn(sh, s.h);
+  const float err = __fadd_rn(__fsub_rn(s.h, __fsub_rn(sh, bp)), __fsub_rn(p, bp));
+  s.h = sh;
+  s.l = __fadd_rn(s.l, __fadd_rn(err, t));
+}
+// s += o for two pair sums (two-sum of the high parts, low parts and error added).
+__device__ __forceinline__ void df_add(DfSum& s, const DfSum& o) {
+  const float sh = __fadd_rn(s.h, o.h);
+  const float bp = __fsub_rn(sh, s.h);
+  const float err = __fadd_rn(__fsub_rn(s.h, __fsub_rn(sh, bp)), __fsub_rn(o.h, bp));
+  s.h = sh;
+  s.l = __fadd_rn(s.l, __fadd_rn(err, o.l));
+}
 #endif
 // Process-wide switch (default on) read when a kernel is launched or captured.
 bool dependent_launch_enabled();
@@ -220,6 +252,10 @@ struct DevOp {
 constexpr int kMaxRhs = 32;
 template <typename V>
 void launch_csr_mm(const DevCsr<V>& M, int nrhs, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+// Block form of the FP32 V-cycle's double-float products (EPI_STORE, EPI_RESID,
+// EPI_SWEEP): M's CSR pattern with the values vdf = {hi, lo} per entry.
+void launch_csr_mm_df(const DevCsr<float>& M, const float2* vdf, int nrhs, int epi, const SpmvArgs<float>& a,
+                      cudaStream_t s);
 // The same products on the sliced-ELL layout of the single-vector kernels (see
 // k_sell_mm): ct = 1 or 2 vectors of 16 bytes per lane.  Returns false (and launches
 // nothing) where that form does not apply to nrhs / the vectors' alignment.

@@ -285,38 +285,9 @@ __global__ void __launch_bounds__(kBlock) k_sell_wide(int nslices, const int64_t
   else a.y[row] = r;
 }
 
-// The same products in double-float arithmetic on the FP32 pipe.  Each stored value
-// a is kept as the float pair hi + lo (hi = fl(a), lo = fl(a - hi)), a pair of
-// entries as one float4 {hi0, hi1, lo0, lo1} (8 bytes per entry, as an FP64 value).
-// Per entry: p = fl(hi x), e = fma(hi, x, -p) (the exact remainder of the product),
-// t = fma(lo, x, e); the running sum is an unnormalized pair (sh, sl): sh <- sh + p
-// by a two-sum whose exact rounding error, plus t, is added to sl.  The result is
-// fl(sh + sl).  Its error is a few multiples of 2^-48 |A| |x| per stored entry, so
-// the cancellation the FP64 form guards against is resolved as well (c_A eps_32
-// ~ 1 at the 1e6 contrast, c_A 2^-43 ~ 1e-6), while the FP64 pipe, which the FP64
-// form keeps busy at one FMA per entry, stays idle.  All steps use
-// round-to-nearest intrinsics, which the compiler does not contract.
-struct DfSum {
-  float h, l;
-};
-__device__ __forceinline__ void df_add_entry(DfSum& s, float hi, float lo, float x) {
-  const float p = __fmul_rn(hi, x);
-  const float e = __fmaf_rn(hi, x, -p);
-  const float t = __fmaf_rn(lo, x, e);
-  const float sh = __fadd_rn(s.h, p);
-  const float bp = __fsub_rn(sh, s.h);
-  const float err = __fadd_rn(__fsub_rn(s.h, __fsub_rn(sh, bp)), __fsub_rn(p, bp));
-  s.h = sh;
-  s.l = __fadd_rn(s.l, __fadd_rn(err, t));
-}
-__device__ __forceinline__ void df_add(DfSum& s, const DfSum& o) {
-  const float sh = __fadd_rn(s.h, o.h);
-  const float bp = __fsub_rn(sh, s.h);
-  const float err = __fadd_rn(__fsub_rn(s.h, __fsub_rn(sh, bp)), __fsub_rn(o.h, bp));
-  s.h = sh;
-  s.l = __fadd_rn(s.l, __fadd_rn(err, o.l));
-}
-
+// The same products in double-float arithmetic on the FP32 pipe (DfSum, df_add_entry:
+// a pair of entries as one float4 {hi0, hi1, lo0, lo1}, 8 bytes per entry as in FP64).
+// The FP64 pipe, which the FP64 form keeps busy at one FMA per entry, stays idle.
 template <int EPI, int WPS, bool CS, bool PF = false>
 __global__ void __launch_bounds__(kBlock) k_sell_df(int nslices, const int64_t* __restrict__ sptr,
                                                     const int* __restrict__ srow, const int2* __restrict__ ci2,

@@ -146,6 +146,80 @@ __global__ void __launch_bounds__(kBlock) k_csr_mmv(int nr, int nrhs, int lpr, c
   vst(a.y + e, s);
 }
 
+// The FP32 block V-cycle's residuals of corrected iterates in double-float
+// arithmetic (DfSum): A's values as CSR float pairs {hi, lo}, each lane's columns as
+// pair sums started from the epilogue's vector, rounded once.  As in the
+// single-vector path, on iterates corrected through G or P most of A x cancels and
+// FP32 values or sums would swamp the residual's gradient (curl) part.
+//   EPI_STORE: y = A x;  EPI_RESID: y = b - A x;  EPI_SWEEP: y = xin + d fl(b - A x)
+// Vector form: W = 4 consecutive columns per lane (nrhs % 4 == 0, 16-byte aligned).
+template <int EPI>
+__global__ void __launch_bounds__(kBlock) k_csr_mmv_df(int nr, int nrhs, int lpr, const int* __restrict__ rp,
+                                                       const int* __restrict__ ci, const float2* __restrict__ val,
+                                                       SpmvArgs<float> a) {
+  static_assert(EPI == EPI_STORE || EPI == EPI_RESID || EPI == EPI_SWEEP, "unsupported epilogue");
+  pdl_begin();
+  constexpr bool NEG = EPI != EPI_STORE;
+  const int gt = blockIdx.x * kBlock + threadIdx.x;
+  const int row = gt / lpr;
+  if (row >= nr) return;
+  const int q = gt - row * lpr;
+  const size_t e = (size_t)row * nrhs + (size_t)q * 4;
+  DfSum s[4];
+  if (NEG) {
+    const float4 b = __ldg(reinterpret_cast<const float4*>(a.b + e));
+    s[0] = DfSum{b.x, 0.f}, s[1] = DfSum{b.y, 0.f}, s[2] = DfSum{b.z, 0.f}, s[3] = DfSum{b.w, 0.f};
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; k++) s[k] = DfSum{0.f, 0.f};
+  }
+  const int beg = ldg(rp + row), end = ldg(rp + row + 1);
+  const float* xq = a.x + (size_t)q * 4;
+#pragma unroll 2
+  for (int j = beg; j < end; j++) {
+    const int c = ldg(ci + j);
+    float2 v = ldg(val + j);
+    if (NEG) v.x = -v.x, v.y = -v.y;
+    const float4 xv = __ldg(reinterpret_cast<const float4*>(xq + (size_t)c * nrhs));
+    df_add_entry(s[0], v.x, v.y, xv.x);
+    df_add_entry(s[1], v.x, v.y, xv.y);
+    df_add_entry(s[2], v.x, v.y, xv.z);
+    df_add_entry(s[3], v.x, v.y, xv.w);
+  }
+  float4 r = make_float4(__fadd_rn(s[0].h, s[0].l), __fadd_rn(s[1].h, s[1].l), __fadd_rn(s[2].h, s[2].l),
+                         __fadd_rn(s[3].h, s[3].l));
+  if (EPI == EPI_SWEEP) {
+    const float d = ldg(a.d + row);
+    const float4 xi = __ldg(reinterpret_cast<const float4*>(a.xin + e));
+    r = make_float4(fmaf(d, r.x, xi.x), fmaf(d, r.y, xi.y), fmaf(d, r.z, xi.z), fmaf(d, r.w, xi.w));
+  }
+  *reinterpret_cast<float4*>(a.y + e) = r;
+}
+
+// Scalar form: one lane per column, K lanes (a power of two >= nrhs) per row.
+template <int K, int EPI>
+__global__ void __launch_bounds__(kBlock) k_csr_mm_df(int nr, int nrhs, const int* __restrict__ rp,
+                                                      const int* __restrict__ ci, const float2* __restrict__ val,
+                                                      SpmvArgs<float> a) {
+  static_assert(EPI == EPI_STORE || EPI == EPI_RESID || EPI == EPI_SWEEP, "unsupported epilogue");
+  pdl_begin();
+  constexpr bool NEG = EPI != EPI_STORE;
+  const int gt = blockIdx.x * kBlock + threadIdx.x;
+  const int row = gt / K;
+  const int c = gt & (K - 1);
+  if (row >= nr || c >= nrhs) return;
+  const size_t e = (size_t)row * nrhs + c;
+  DfSum s{NEG ? a.b[e] : 0.f, 0.f};
+  const int beg = ldg(rp + row), end = ldg(rp + row + 1);
+  for (int j = beg; j < end; j++) {
+    float2 v = ldg(val + j);
+    if (NEG) v.x = -v.x, v.y = -v.y;
+    df_add_entry(s, v.x, v.y, ldg(a.x + (size_t)ldg(ci + j) * nrhs + c));
+  }
+  const float r = __fadd_rn(s.h, s.l);
+  a.y[e] = EPI == EPI_SWEEP ? fmaf(a.d[row], r, a.xin[e]) : r;
+}
+
 // Block product on the single-vector sliced-ELL layout.  lpr lanes share a row (lane
 // q owns CT vectors of W columns: columns (q CT + t) W .. + W - 1, t < CT), a warp
 // takes rpw = 32 / lpr consecutive rows of a 32-row slice, and lpr warps cover the
@@ -611,6 +685,31 @@ void launch_csr_mm(const DevCsr<V>& M, int nrhs, int epi, const SpmvArgs<V>& a, 
 }
 template void launch_csr_mm<double>(const DevCsr<double>&, int, int, const SpmvArgs<double>&, cudaStream_t);
 template void launch_csr_mm<float>(const DevCsr<float>&, int, int, const SpmvArgs<float>&, cudaStream_t);
+
+void launch_csr_mm_df(const DevCsr<float>& M, const float2* vdf, int nrhs, int epi, const SpmvArgs<float>& a,
+                      cudaStream_t s) {
+  if (M.nr == 0) return;
+  if (nrhs % 4 == 0 && aligned16(a.x) && aligned16(a.y) && aligned16(a.b) && aligned16(a.xin)) {
+    const int lpr = nrhs / 4;
+    const int grid = (int)(((int64_t)M.nr * lpr + kBlock - 1) / kBlock);
+    switch (epi) {
+      case EPI_RESID: launch_k(k_csr_mmv_df<EPI_RESID>, grid, kBlock, s, M.nr, nrhs, lpr, M.rp, M.ci, vdf, a); break;
+      case EPI_SWEEP: launch_k(k_csr_mmv_df<EPI_SWEEP>, grid, kBlock, s, M.nr, nrhs, lpr, M.rp, M.ci, vdf, a); break;
+      default: launch_k(k_csr_mmv_df<EPI_STORE>, grid, kBlock, s, M.nr, nrhs, lpr, M.rp, M.ci, vdf, a); break;
+    }
+    return;
+  }
+  const int K = pow2_at_least(nrhs);
+  const int grid = (int)(((int64_t)M.nr * K + kBlock - 1) / kBlock);
+  dispatch_k(K, [&](auto kk) {
+    constexpr int KK = decltype(kk)::value;
+    switch (epi) {
+      case EPI_RESID: launch_k(k_csr_mm_df<KK, EPI_RESID>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, vdf, a); break;
+      case EPI_SWEEP: launch_k(k_csr_mm_df<KK, EPI_SWEEP>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, vdf, a); break;
+      default: launch_k(k_csr_mm_df<KK, EPI_STORE>, grid, kBlock, s, M.nr, nrhs, M.rp, M.ci, vdf, a); break;
+    }
+  });
+}
 
 // Lanes per row of the sliced-ELL block kernel with CT vectors per lane, or 0 where
 // it does not apply (nrhs not a multiple of CT W, more than 8 lanes per row, or

@@ -275,6 +275,7 @@ amge_status update_coefficients(amge_hier* h, const double* beta, const double* 
     };
     // copies of A_l: FP32 CSR, sliced ELL (both precisions)
     k_to_f32<<<grid_of(A.nnz), kUpdBlock, 0, s>>>(A.nnz, A.val, f.cA.val);
+    if (f.cAdf) launch_df_split_entries(A.nnz, A.val, f.cAdf, s);
     k_sell_fill<<<grid_of(d.A.stored), kUpdBlock, 0, s>>>(d.A.stored, u.mapA, A.val, d.A.val, f.A.val);
     if (f.Adf) launch_df_split(d.A.stored / 2, d.A.val, f.Adf, s);
     // l1 diagonals of A_l and of G^T A_l G

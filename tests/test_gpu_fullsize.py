@@ -243,3 +243,29 @@ def test_pcg_full_size_fp32_vcycle(amge, name):
     print(f"{name}: FP32-V-cycle solution vs FP64 oracle, relative L2 {rel:.2e}, "
           f"{info[0]['iters']} iterations (oracle {it_o})")
     assert rel <= 1e-7, (name, rel)
+
+
+@pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
+def test_pcg_full_size_fp32_vcycle_block(amge, name):
+    """Blocks of right-hand sides under the 1e6 contrast with the FP32 V-cycle: its
+    corrected residuals in double-float arithmetic (an all-FP32 block cycle stagnates
+    here, as the single-vector one did).  Four columns: the workload's right-hand side
+    (checked against the oracle's solution) and three more; every column reaches the
+    FP64 tolerance within the oracle's iteration count + 3."""
+    from paper_2107_05613_gb300.inputs import rhs_vector
+
+    h, o, b = workload(amge, name)
+    nrhs = 4
+    B = np.stack([b] + [rhs_vector(900 + k, b.size) for k in range(1, nrhs)], axis=1)
+    X = torch.empty((b.size, nrhs), dtype=torch.float64, device="cuda")
+    st, info = amge.amge_pcg_solve(h, dev(B), X, rtol=1e-8, precision=amge.AMGE_FP32_VCYCLE, nrhs=nrhs)
+    xo, it_o, _, ok_o = oracle_solution(name, o, b)
+    assert st == amge.AMGE_OK and ok_o, (st, info)
+    Xg = host(X)
+    for k in range(nrhs):
+        assert info[k]["status"] == amge.AMGE_OK and info[k]["iters"] <= it_o + 3, (k, info[k], it_o)
+        assert np.linalg.norm(B[:, k] - o.A[0] @ Xg[:, k]) <= 1e-8 * np.linalg.norm(B[:, k]), k
+    rel = np.linalg.norm(Xg[:, 0] - xo) / np.linalg.norm(xo)
+    print(f"{name}: FP32-V-cycle block solve, column 0 vs FP64 oracle, relative L2 {rel:.2e}, "
+          f"iterations {[i['iters'] for i in info]} (oracle {it_o})")
+    assert rel <= 1e-7, (name, rel)
