@@ -6,12 +6,15 @@ falls back to it.  It shares no code with the CUDA path: both read the same
 generated hierarchy arrays (paper_2107_05613_gb300.inputs) and nothing else.
 """
 from .amge_oracle import (
+    AuxSpaceCoarseSolver,
     OracleHierarchy,
     SymmetricGaussSeidel,
+    coarse_interpolation,
     colour_order,
     greedy_colours,
     l1_row_sums,
     pcg,
 )
 
-__all__ = ["OracleHierarchy", "SymmetricGaussSeidel", "colour_order", "greedy_colours", "l1_row_sums", "pcg"]
+__all__ = ["AuxSpaceCoarseSolver", "OracleHierarchy", "SymmetricGaussSeidel", "coarse_interpolation", "colour_order",
+           "greedy_colours", "l1_row_sums", "pcg"]

@@ -19,7 +19,9 @@ dense Cholesky factorisation) serve as single steps, with no fusion or reorderin
     term of the paper's l1-scaled block variant adds, to a row's diagonal, its
     couplings to rows outside the row's processor block; with the whole matrix as
     one block it is zero, and the smoother is plain symmetric Gauss-Seidel.
-  * Coarsest level: dense FP64 Cholesky solve (in place of the paper's AMS/ADS).
+  * Coarsest level: dense FP64 Cholesky solve (the default), or the paper's solver
+    (Sections 4.2 and 5.1): a fixed number of PCG iterations preconditioned by the
+    additive auxiliary-space preconditioner of eq. 4.2 (AuxSpaceCoarseSolver).
   * PCG (Sections 4 and 5.1): preconditioned conjugate gradients with x0 = 0 and
     one V-cycle per iteration; stop on the true FP64 relative residual
     ||b - A x|| / ||b|| <= rtol (residual replaced by the true one when the
@@ -88,6 +90,95 @@ class SymmetricGaussSeidel:
         return x
 
 
+def coarse_interpolation(h, k: int):
+    """The interpolation of vector H1 into space k (1 edges, 2 faces) at the coarsest
+    level of generated hierarchy h (built with all spaces), by the recursion of
+    Section 4.2 from the finest level's: pihat^{l+1} = Pi^l pihat^l (P_0^l (x) I_3),
+    with Pi^l the co-chain projector of space k and P_0^l the H1 prolongator."""
+    M = h.pihat[0][k].to_scipy()
+    for l in range(h.num_levels - 1):
+        Pv = sp.kron(h.P_all[l][0].to_scipy(), sp.eye(3), format="csr")
+        M = (h.Pi[l][k].to_scipy() @ M @ Pv).tocsr()
+    return M
+
+
+class AuxSpaceCoarseSolver:
+    """Coarsest-level solver of the paper's runs (Sections 4.2 and 5.1): `iters` PCG
+    iterations (five) from x0 = 0 on A, preconditioned by the additive
+    auxiliary-space preconditioner of eq. 4.2,
+
+      B^{-1} = M^{-1} + Pihat S_v^{-1} Pihat^T + D B_D D^T,   S_v = Pihat^T A Pihat,
+
+    with M the l1-Jacobi point smoother (Section 4.1) and D the exterior derivative
+    into the problem space.  H(curl) (AMS): D = D_0, B_D = S_g^{-1}, S_g = D_0^T A D_0.
+    H(div) (ADS): D = D_1 and B_D is the same construction for the curl-curl matrix
+    A_c = D_1^T A D_1 with the edge interpolation Pihat_1: B_D = M_c^{-1} + Pihat_1
+    S_c^{-1} Pihat_1^T, S_c = Pihat_1^T A_c Pihat_1 (A_c annihilates gradients, so its
+    gradient term is void).  The auxiliary solves are exact: S^{-1} := the
+    pseudo-inverse of S, because with natural boundary conditions S_g and S_c are
+    singular (constants; gradients of quadratics); their right-hand sides D^T r and
+    Pihat^T t have no component in those kernels, which D and Pihat map to zero again."""
+
+    def __init__(self, A, pihat, D, pihat_inner=None, iters: int = 5):
+        self.A = sp.csr_matrix(A)
+        self.iters = iters
+        self.m = l1_row_sums(self.A)
+        self.Pv = sp.csr_matrix(pihat)
+        self.D = sp.csr_matrix(D)
+        self.Sv_inv = self._reg_inverse((self.Pv.T @ self.A @ self.Pv).toarray())
+        if pihat_inner is None:                      # AMS: gradient term
+            self.Sg_inv = self._reg_inverse((self.D.T @ self.A @ self.D).toarray())
+            self.inner = None
+        else:                                        # ADS: AMS of the curl-curl matrix
+            Ac = (self.D.T @ self.A @ self.D).tocsr()
+            Pi1 = sp.csr_matrix(pihat_inner)
+            self.inner = (l1_row_sums(Ac), Pi1, self._reg_inverse((Pi1.T @ Ac @ Pi1).toarray()))
+
+    @staticmethod
+    def _reg_inverse(S):
+        """The pseudo-inverse of the symmetric positive semi-definite S: its eigenvalues
+        below 1e-12 of the largest (the kernel, zero up to rounding) dropped."""
+        if not S.size:
+            return S.copy()
+        lam, V = np.linalg.eigh(S)
+        keep = lam > 1e-12 * lam.max()
+        return (V[:, keep] / lam[keep]) @ V[:, keep].T
+
+    def precondition(self, r):
+        """Eq. 4.2 (additive): the three terms summed."""
+        z = _div(r, self.m) + self.Pv @ (self.Sv_inv @ (self.Pv.T @ r))
+        t = self.D.T @ r
+        if self.inner is None:
+            y = self.Sg_inv @ t
+        else:
+            mc, Pi1, Sc_inv = self.inner
+            y = _div(t, mc) + Pi1 @ (Sc_inv @ (Pi1.T @ t))
+        return z + self.D @ y
+
+    def solve(self, b):
+        """`iters` PCG iterations from x0 = 0 (fixed count, no tolerance)."""
+        x = np.zeros_like(b)
+        r = b.copy()
+        z = self.precondition(r)
+        p = z.copy()
+        rho = r @ z
+        for it in range(self.iters):
+            q = self.A @ p
+            pq = p @ q
+            if pq == 0.0:
+                break
+            alpha = rho / pq
+            x = x + alpha * p
+            r = r - alpha * q
+            if it + 1 == self.iters:
+                break
+            z = self.precondition(r)
+            rho_new = r @ z
+            p = z + (rho_new / rho) * p
+            rho = rho_new
+        return x
+
+
 class OracleHierarchy:
     """The solve-phase operators of an AMGe hierarchy, in scipy FP64.
 
@@ -96,7 +187,7 @@ class OracleHierarchy:
     """
 
     def __init__(self, A, P, G, nu_pre: int = 1, nu_post: int = 1, smoother: str = "l1jacobi",
-                 sweeps: int = 2, gs_levels: int = None):
+                 sweeps: int = 2, gs_levels: int = None, coarse_aux: AuxSpaceCoarseSolver = None):
         self.A = [sp.csr_matrix(a, dtype=np.float64) for a in A]
         self.P = [sp.csr_matrix(p, dtype=np.float64) for p in P]
         self.G = [sp.csr_matrix(g, dtype=np.float64) for g in G]
@@ -123,9 +214,10 @@ class OracleHierarchy:
                 self.gs_aux.append(SymmetricGaussSeidel(self.A_aux[l], colour_order((pg.T @ pa @ pg).tocsr())))
         elif smoother != "l1jacobi":
             raise ValueError("smoother must be 'l1jacobi' or 'gs'")
-        # coarsest level: dense Cholesky factor
+        # coarsest level: dense Cholesky factor, or the auxiliary-space solver
         Ac = self.A[-1].toarray()
         self.coarse_factor = sla.cho_factor(Ac, lower=True)
+        self.coarse_aux = coarse_aux
 
     @classmethod
     def from_blob(cls, blob: bytes):
@@ -156,9 +248,23 @@ class OracleHierarchy:
 
     @classmethod
     def from_hierarchy(cls, h, nu_pre: int = 1, nu_post: int = 1, smoother: str = "l1jacobi", sweeps: int = 2,
-                       gs_levels: int = None):
+                       gs_levels: int = None, coarse: str = "dense", coarse_iters: int = 5):
+        """coarse: 'dense' (Cholesky) or 'aux' (AuxSpaceCoarseSolver; h built with all
+        spaces)."""
+        aux = None
+        if coarse == "aux":
+            L = h.num_levels
+            A = h.A[-1].to_scipy()
+            if h.form == "hcurl":
+                aux = AuxSpaceCoarseSolver(A, coarse_interpolation(h, 1), h.D_all[L - 1][0].to_scipy(),
+                                           iters=coarse_iters)
+            else:
+                aux = AuxSpaceCoarseSolver(A, coarse_interpolation(h, 2), h.D_all[L - 1][1].to_scipy(),
+                                           coarse_interpolation(h, 1), iters=coarse_iters)
+        elif coarse != "dense":
+            raise ValueError("coarse must be 'dense' or 'aux'")
         return cls([a.to_scipy() for a in h.A], [p.to_scipy() for p in h.P],
-                   [g.to_scipy() for g in h.G], nu_pre, nu_post, smoother, sweeps, gs_levels)
+                   [g.to_scipy() for g in h.G], nu_pre, nu_post, smoother, sweeps, gs_levels, aux)
 
     # ---------------------------------------------------------------- smoothers
     def _point(self, l, x, b):
@@ -194,6 +300,8 @@ class OracleHierarchy:
 
     # ---------------------------------------------------------------- V-cycle
     def coarse_solve(self, b):
+        if self.coarse_aux is not None:
+            return self.coarse_aux.solve(b)
         return sla.cho_solve(self.coarse_factor, b)
 
     def vcycle(self, b, l: int = 0, x0=None):

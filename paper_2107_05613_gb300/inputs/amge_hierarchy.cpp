@@ -1208,8 +1208,142 @@ struct Hier {
   std::vector<Level> levels;
   std::vector<Transfer> transfers;
   std::vector<DCsr> A;
+  // with all spaces: co-chain projectors Pi[l][k] (level l -> l+1, space k) and the
+  // interpolations pihat[l][k] of vector H1 into space k = 1, 2 at level l
+  std::vector<std::array<DCsr, 4>> Pi;
+  std::vector<std::array<DCsr, 3>> pihat;
   double diag[4] = {0, 0, 0, 0};
 };
+
+// ------------------------------------------------------------ auxiliary-space data
+// Sparse product C = A B, rows formed independently (entries summed in the order of
+// A's row, then B's row; columns sorted).
+DCsr spgemm(const DCsr& A, const DCsr& B) {
+  REQUIRE(A.nc == B.nr, "spgemm shapes");
+  DCsr C;
+  C.nr = A.nr, C.nc = B.nc;
+  std::vector<std::vector<std::pair<int, double>>> rows(A.nr);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int i = 0; i < A.nr; i++) {
+    std::vector<std::pair<int, double>>& r = rows[i];
+    for (int64_t p = A.a.rp[i]; p < A.a.rp[i + 1]; p++) {
+      const int k = A.a.ci[p];
+      const double a = A.v[p];
+      for (int64_t q = B.a.rp[k]; q < B.a.rp[k + 1]; q++) r.emplace_back(B.a.ci[q], a * B.v[q]);
+    }
+    std::stable_sort(r.begin(), r.end(), [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
+      return x.first < y.first;
+    });
+    size_t w = 0;
+    for (size_t t = 0; t < r.size(); t++) {
+      if (w > 0 && r[w - 1].first == r[t].first) r[w - 1].second += r[t].second;
+      else r[w++] = r[t];
+    }
+    r.resize(w);
+  }
+  C.a.rp.assign(C.nr + 1, 0);
+  for (int i = 0; i < C.nr; i++) C.a.rp[i + 1] = C.a.rp[i] + (int64_t)rows[i].size();
+  C.a.ci.resize(C.a.rp[C.nr]);
+  C.v.resize(C.a.rp[C.nr]);
+  for (int i = 0; i < C.nr; i++)
+    for (size_t t = 0; t < rows[i].size(); t++) {
+      C.a.ci[C.a.rp[i] + t] = rows[i][t].first;
+      C.v[C.a.rp[i] + t] = rows[i][t].second;
+    }
+  return C;
+}
+
+// Co-chain projector of the lowest-order space k from a level to the next coarser one
+// (Section 3.2.2): the coarse dof of entity X is the integral functional over X's
+// chain, sum over the constituents y of X of phi_y v_y.  The PV traces of eq. 3.5 put
+// phi_y / |cons(X)| on X's constituents, so Pi P = I (eq. 3.3); by Stokes' theorem on
+// the oriented chains Pi_{k+1} D_k = D_k^H Pi_k.  Built entity by entity.
+DCsr cochain(const Transfer& T, int k, int nfine) {
+  DCsr M;
+  M.nr = T.cons[k].rows(), M.nc = nfine;
+  M.a = T.cons[k];
+  M.v.resize(T.phi[k].size());
+  for (size_t p = 0; p < T.phi[k].size(); p++) M.v[p] = (double)T.phi[k][p];
+  return M;
+}
+
+// Interpolation of continuous piecewise-linear vector fields (three components per
+// vertex, column 3 v + c) into the lowest-order space k of the finest level: k = 1 the
+// edge integrals of the tangential component, k = 2 the face fluxes, both exact for
+// such fields (the finite element interpolant of Section 4.2's auxiliary space).
+// Edge (a < b): (x_b - x_a) . (r_a + r_b) / 2.  Face (a < b < c), oriented like its
+// boundary chain [a,b] + [b,c] - [a,c]: n . (r_a + r_b + r_c) / 3 with the area normal
+// n = (x_b - x_a) x (x_c - x_a) / 2.
+DCsr fine_pihat(const Level& L, int k) {
+  const int ne = (int)L.cnt[k];
+  DCsr M;
+  M.nr = ne, M.nc = 3 * (int)L.cnt[0];
+  M.a.rp.assign(ne + 1, 0);
+  std::vector<std::vector<std::pair<int, double>>> rows(ne);
+#pragma omp parallel for schedule(static)
+  for (int e = 0; e < ne; e++) {
+    const int* vv = L.clo[k][0].row(e);
+    const int nv = k + 1;
+    double x[3][3], w[3];
+    for (int a = 0; a < nv; a++) vert_coord(L, vv[a], x[a]);
+    if (k == 1) {
+      for (int c = 0; c < 3; c++) w[c] = 0.5 * (x[1][c] - x[0][c]);
+    } else {
+      double e1[3], e2[3], nr[3];
+      for (int c = 0; c < 3; c++) e1[c] = x[1][c] - x[0][c], e2[c] = x[2][c] - x[0][c];
+      cross3(e1, e2, nr);
+      for (int c = 0; c < 3; c++) w[c] = nr[c] / 6.0;
+    }
+    for (int a = 0; a < nv; a++)
+      for (int c = 0; c < 3; c++)
+        if (w[c] != 0.0) rows[e].emplace_back(3 * vv[a] + c, w[c]);
+  }
+  for (int e = 0; e < ne; e++) M.a.rp[e + 1] = M.a.rp[e] + (int64_t)rows[e].size();
+  M.a.ci.resize(M.a.rp[ne]);
+  M.v.resize(M.a.rp[ne]);
+  for (int e = 0; e < ne; e++)
+    for (size_t t = 0; t < rows[e].size(); t++) {
+      M.a.ci[M.a.rp[e] + t] = rows[e][t].first;
+      M.v[M.a.rp[e] + t] = rows[e][t].second;
+    }
+  return M;
+}
+
+// Vector form of the H1 prolongator: (P0 (x) I_3), entry (3 i + c, 3 j + c) = P0(i, j).
+DCsr vector_prolongator(const DCsr& P0) {
+  DCsr M;
+  M.nr = 3 * P0.nr, M.nc = 3 * P0.nc;
+  M.a.rp.assign(M.nr + 1, 0);
+  for (int i = 0; i < P0.nr; i++)
+    for (int c = 0; c < 3; c++) M.a.rp[3 * i + c + 1] = M.a.rp[3 * i + c] + P0.a.len(i);
+  M.a.ci.resize(M.a.rp[M.nr]);
+  M.v.resize(M.a.rp[M.nr]);
+  for (int i = 0; i < P0.nr; i++)
+    for (int c = 0; c < 3; c++) {
+      int64_t o = M.a.rp[3 * i + c];
+      for (int64_t p = P0.a.rp[i]; p < P0.a.rp[i + 1]; p++, o++) {
+        M.a.ci[o] = 3 * P0.a.ci[p] + c;
+        M.v[o] = P0.v[p];
+      }
+    }
+  return M;
+}
+
+// Co-chain projectors on every level and the interpolations on every level by the
+// recursion of Section 4.2: pihat^{l+1}_k = Pi_k^{l} pihat^l_k (P0 (x) I_3).
+void build_aux(Hier* H) {
+  const int nl = (int)H->levels.size();
+  H->Pi.resize(nl > 1 ? nl - 1 : 0);
+  H->pihat.resize(nl);
+  for (int l = 0; l + 1 < nl; l++)
+    for (int k = 0; k < 4; k++) H->Pi[l][k] = cochain(H->transfers[l], k, (int)H->levels[l].cnt[k]);
+  for (int k = 1; k <= 2; k++) H->pihat[0][k] = fine_pihat(H->levels[0], k);
+  for (int l = 0; l + 1 < nl; l++) {
+    REQUIRE(H->transfers[l].built[0], "auxiliary-space data needs the H1 prolongators");
+    const DCsr Pv = vector_prolongator(H->transfers[l].P[0]);
+    for (int k = 1; k <= 2; k++) H->pihat[l + 1][k] = spgemm(H->Pi[l][k], spgemm(H->pihat[l][k], Pv));
+  }
+}
 
 Hier* build(int form, int n, int num_levels, const double* beta, const double* alpha, int all_spaces) {
   auto t0 = std::chrono::steady_clock::now();
@@ -1262,6 +1396,10 @@ Hier* build(int form, int n, int num_levels, const double* beta, const double* a
           T.fclo[d][k] = Adj();
           std::vector<uint8_t>().swap(T.fint[d][k]);
         }
+    }
+    if (all_spaces) {
+      Stage s("auxiliary-space data");
+      build_aux(H);
     }
     H->diag[0] = st.lam_dev;
     H->diag[1] = st.resid;
@@ -1330,6 +1468,14 @@ int amgh_matrix_info(const void* h, int kind, int level, int k, int64_t info[3])
     if (k < 0 || k > 2) return 1;
     const ICsr& M = H->levels[level].D[k];
     info[0] = M.nr, info[1] = M.nc, info[2] = (int64_t)M.v.size();
+  } else if (kind == AMGH_KIND_PI) {
+    if (level + 1 >= (int)H->levels.size() || k < 0 || k > 3 || H->Pi.empty()) return 1;
+    const DCsr& M = H->Pi[level][k];
+    info[0] = M.nr, info[1] = M.nc, info[2] = (int64_t)M.v.size();
+  } else if (kind == AMGH_KIND_PIHAT) {
+    if (k < 1 || k > 2 || H->pihat.empty()) return 1;
+    const DCsr& M = H->pihat[level][k];
+    info[0] = M.nr, info[1] = M.nc, info[2] = (int64_t)M.v.size();
   } else {
     return 1;
   }
@@ -1342,6 +1488,8 @@ int amgh_matrix_copy(const void* h, int kind, int level, int k, int32_t* rp, int
   const Hier* H = (const Hier*)h;
   if (kind == AMGH_KIND_A) copy_dcsr(H->A[level], rp, ci, v);
   else if (kind == AMGH_KIND_P) copy_dcsr(H->transfers[level].P[k], rp, ci, v);
+  else if (kind == AMGH_KIND_PI) copy_dcsr(H->Pi[level][k], rp, ci, v);
+  else if (kind == AMGH_KIND_PIHAT) copy_dcsr(H->pihat[level][k], rp, ci, v);
   else {
     const ICsr& M = H->levels[level].D[k];
     for (int i = 0; i <= M.nr; i++) rp[i] = (int32_t)M.a.rp[i];

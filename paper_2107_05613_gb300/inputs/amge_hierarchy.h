@@ -28,7 +28,7 @@ extern "C" {
 #endif
 
 enum { AMGH_FORM_HCURL = 1, AMGH_FORM_HDIV = 2 };
-enum { AMGH_KIND_A = 0, AMGH_KIND_P = 1, AMGH_KIND_D = 2 };
+enum { AMGH_KIND_A = 0, AMGH_KIND_P = 1, AMGH_KIND_D = 2, AMGH_KIND_PI = 3, AMGH_KIND_PIHAT = 4 };
 
 /* Build the hierarchy on an n^3 Kuhn-split unit cube.
  *   form        AMGH_FORM_HCURL (Nedelec edges) or AMGH_FORM_HDIV (Raviart-Thomas faces)
@@ -47,7 +47,13 @@ int amgh_num_levels(const void* h);
 /* entity counts V, E, F, T at a level */
 int amgh_level_counts(const void* h, int level, int64_t counts[4]);
 /* kind A: problem matrix at `level` (k ignored); kind P: prolongator of space k from
- * level+1 to level; kind D: signed incidence D_k at `level`.  info = {rows, cols, nnz}. */
+ * level+1 to level; kind D: signed incidence D_k at `level`.  With all_spaces also
+ * kind PI: co-chain projector of space k from `level` to level+1 (coarse rows; the
+ * signed sum over each coarse entity's constituents, Pi P = I) and kind PIHAT: the
+ * interpolation of vector H1 (column 3 v + c = component c at vertex v) into space
+ * k = 1 (edges) or 2 (faces) at `level` (finest: exact for linear fields; coarser:
+ * the recursion pihat^{l+1} = Pi^l pihat^l (P_0 (x) I_3) of Section 4.2).
+ * info = {rows, cols, nnz}. */
 int amgh_matrix_info(const void* h, int kind, int level, int k, int64_t info[3]);
 int amgh_matrix_copy(const void* h, int kind, int level, int k, int32_t* row_ptr, int32_t* col,
                      double* val);

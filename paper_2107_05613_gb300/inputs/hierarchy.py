@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libamge_hierarchy.so")
 
 FORMS = {"hcurl": 1, "hdiv": 2}
-KIND_A, KIND_P, KIND_D = 0, 1, 2
+KIND_A, KIND_P, KIND_D, KIND_PI, KIND_PIHAT = 0, 1, 2, 3, 4
 
 _lib = None
 
@@ -81,6 +81,9 @@ class Hierarchy:
     G[l]      aux transition at level l: D_0 (H(curl)) or D_1 (H(div)), integer values
     counts[l] entity counts (vertices, edges, faces, cells)
     P_all[l][k], D_all[l][k]: prolongators / incidences of every space built
+    Pi[l][k]  (all_spaces) co-chain projector of space k from level l to l+1
+    pihat[l][k] (all_spaces) interpolation of vector H1 (column 3 v + c) into space
+              k = 1, 2 at level l (index 0 unused)
     """
 
     form: str
@@ -92,6 +95,8 @@ class Hierarchy:
     P_all: list
     D_all: list
     diagnostics: dict
+    Pi: list = None
+    pihat: list = None
 
     @property
     def num_levels(self) -> int:
@@ -146,6 +151,10 @@ def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=Non
                 P_all.append([_copy(lib, h, KIND_P, l, k) for k in range(4)])
                 P.append(P_all[-1][kf])
                 G.append(D_all[-1][kf - 1])
+        Pi = pihat = None
+        if all_spaces:
+            Pi = [[_copy(lib, h, KIND_PI, l, k) for k in range(4)] for l in range(L - 1)]
+            pihat = [[None] + [_copy(lib, h, KIND_PIHAT, l, k) for k in (1, 2)] for l in range(L)]
         d = (ctypes.c_double * 4)()
         lib.amgh_diagnostics(h, d)
         diag = {"lambda_dev": d[0], "local_residual": d[1], "incidence_dev": d[2], "seconds": d[3]}
@@ -164,7 +173,7 @@ def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=Non
             diag["assembly"] = dict(K=K, M=M, coff=coff, ccell=ccell, cidx=cidx, s=s_)
     finally:
         lib.amgh_free(h)
-    return Hierarchy(form, n, A, P, G, counts, P_all, D_all, diag)
+    return Hierarchy(form, n, A, P, G, counts, P_all, D_all, diag, Pi, pihat)
 
 
 BLOB_MAGIC = b"AMGEBLOB"
