@@ -608,6 +608,7 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
                                                      const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                      const typename Pair<V>::T* __restrict__ val2, AgArgs<V> a) {
   using PV = typename Pair<V>::T;
+  constexpr int kPre = 2;  // entry pairs per lane loaded before the dependent-launch wait
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int g = wib % WPS;
@@ -615,8 +616,11 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
   int row = -1, np = 0;
   const int2* cp = ci2;
   const PV* vp = val2;
-  int2 g2 = make_int2(kSellPad, kSellPad), c0 = g2;
-  PV v0{};
+  int2 g2 = make_int2(kSellPad, kSellPad);
+  int2 cpre[kPre];
+  PV vpre[kPre];
+#pragma unroll
+  for (int t = 0; t < kPre; t++) cpre[t] = make_int2(0, 0), vpre[t] = PV{};
   if (slice < nslices) {
     const int64_t p0 = ldg(sptr + slice) >> 1;
     np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
@@ -628,22 +632,39 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
     cp += p0 + lane;
     vp += p0 + lane;
     if (row >= 0 && g == 0) g2 = ldg(a.g2 + row);
-    if (g < np) {
-      c0 = ldm<CS>(cp + (size_t)g * 32);
-      v0 = ldm<CS>(vp + (size_t)g * 32);
-    }
+    // rows of A G are short (5.4 entries on the H(curl) finest level): the first kPre
+    // pairs hold most of a row's entries, so their gathers below go out at once
+#pragma unroll
+    for (int t = 0; t < kPre; t++)
+      if (g + t * WPS < np) {
+        cpre[t] = ldm<CS>(cp + (size_t)(g + t * WPS) * 32);
+        vpre[t] = ldm<CS>(vp + (size_t)(g + t * WPS) * 32);
+      }
   }
   pdl_begin();
-  V s = V(0);
+  V s = V(0), gx = V(0), ge0 = V(0), ge1 = V(0);
   if (row >= 0) {
-    if (g == 0) s = a.r[row];
-    if (g < np) {
-      const V x0 = ldg(a.y + c0.x), x1 = ldg(a.y + c0.y);
-      s = fma(-v0.x, x0, s);
-      s = fma(-v0.y, x1, s);
+    // every load that does not depend on another goes out before the first sum
+    if (g == 0) {
+      s = a.r[row];
+      gx = a.x[row];
+      ge0 = signed_entry<false>(a.y, g2.x);
+      ge1 = signed_entry<false>(a.y, g2.y);
     }
+    V xv[2 * kPre];
+#pragma unroll
+    for (int t = 0; t < kPre; t++) {
+      xv[2 * t] = V(0), xv[2 * t + 1] = V(0);
+      if (g + t * WPS < np) xv[2 * t] = ldg(a.y + cpre[t].x), xv[2 * t + 1] = ldg(a.y + cpre[t].y);
+    }
+#pragma unroll
+    for (int t = 0; t < kPre; t++)
+      if (g + t * WPS < np) {
+        s = fma(-vpre[t].x, xv[2 * t], s);
+        s = fma(-vpre[t].y, xv[2 * t + 1], s);
+      }
 #pragma unroll 2
-    for (int k = g + WPS; k < np; k += WPS) {
+    for (int k = g + kPre * WPS; k < np; k += WPS) {
       const int2 c = ldm<CS>(cp + (size_t)k * 32);
       const PV v = ldm<CS>(vp + (size_t)k * 32);
       const V x0 = ldg(a.y + c.x), x1 = ldg(a.y + c.y);
@@ -660,9 +681,8 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
     for (int j = 1; j < WPS; j++) s += part[threadIdx.x + 32 * j];
   }
   if (row < 0) return;
-  V gx = a.x[row];
-  gx += signed_entry<false>(a.y, g2.x);
-  gx += signed_entry<false>(a.y, g2.y);
+  gx += ge0;
+  gx += ge1;
   if (POST) {
     a.z[row] = fma(a.minv[row], s, gx);
   } else {
