@@ -192,12 +192,14 @@ def make_workload(wl):
     return hh, b
 
 
-def sweep_bytes(nnz, n, w, extra_vectors, nrhs=1, vw=None):
-    """Algorithmic bytes of one sweep: values (width vw, default w) + int32 columns +
-    int32 row pointers, one read of the gathered block, the right-hand side and the
-    output, plus `extra_vectors` other row-wise blocks (FP width w, nrhs columns; a
-    diagonal counts as one column)."""
-    return nnz * ((vw or w) + 4) + 4 * (n + 1) + w * n * nrhs * 3 + w * n * extra_vectors
+def sweep_bytes(nnz, n, w, extra_vectors, nrhs=1, vw=None, c16=False):
+    """Algorithmic bytes of one sweep: values (width vw, default w) + int32 columns
+    (c16: 16-bit column offsets and one int32 base per 32-row slice) + int32 row
+    pointers, one read of the gathered block, the right-hand side and the output, plus
+    `extra_vectors` other row-wise blocks (FP width w, nrhs columns; a diagonal counts
+    as one column)."""
+    cols = nnz * 2 + 4 * ((n + 31) // 32) if c16 else nnz * 4
+    return nnz * (vw or w) + cols + 4 * (n + 1) + w * n * nrhs * 3 + w * n * extra_vectors
 
 
 def a_fine_bytes_per_launch(hh, w, nrhs=1, ag=False):
@@ -421,27 +423,31 @@ def profiler_range(on):
         pass
 
 
-def level0_launch_bytes(hh, w, nrhs, ag):
+def level0_launch_bytes(hh, w, nrhs, ag, c16=False, c16_wide=False):
     """Algorithmic bytes per launch of the two level-0 A kernel classes of a V-cycle.
     A_fine: FP64 (w = 8) every level-0 A sweep (see a_fine_bytes_per_launch); FP32
     single vector: the first residual r = b - A x only (FP32 values); FP32 blocks:
     all four sweeps.  A_wide (FP32 single vector): the residuals of corrected iterates
     on the FP64 operator -- with the A G form the post-correction residual, else two
-    residuals and the final l1 sweep (which also reads m^-1)."""
+    residuals and the final l1 sweep (which also reads m^-1).  c16 / c16_wide: the
+    FP32 / double-float products read 16-bit column offsets (kernel code 1600)."""
     A = hh.A[0]
     n, nnz = A.shape[0], A.nnz
     if w == 8 or nrhs > 1:
         return {"A_fine": a_fine_bytes_per_launch(hh, w, nrhs, ag)}
-    wide = (float(sweep_bytes(nnz, n, 4, 0, vw=8)) if ag else
-            (2 * sweep_bytes(nnz, n, 4, 0, vw=8) + sweep_bytes(nnz, n, 4, 1, vw=8)) / 3.0)
-    return {"A_fine": float(sweep_bytes(nnz, n, 4, 0)), "A_wide": wide}
+    wide = (float(sweep_bytes(nnz, n, 4, 0, vw=8, c16=c16_wide)) if ag else
+            (2 * sweep_bytes(nnz, n, 4, 0, vw=8, c16=c16_wide) + sweep_bytes(nnz, n, 4, 1, vw=8, c16=c16_wide)) / 3.0)
+    return {"A_fine": float(sweep_bytes(nnz, n, 4, 0, c16=c16)), "A_wide": wide}
 
 
 ROOFLINE_KERNELS = {
     "A_fine": "k_sell level-0 A sweeps (residuals r = b - A x{last})",
+    "A_fine16": "k_sell16 level-0 A sweeps with 16-bit column offsets (residuals r = b - A x{last})",
     "A_wide": "k_sell_wide level-0 residuals of corrected iterates (FP64 values and sums, FP32 vectors)",
     "A_wide_df": "k_sell_df level-0 residuals of corrected iterates (double-float values and sums on the FP32 "
                  "pipe, FP32 vectors)",
+    "A_wide_df16": "k_sell_df16 level-0 residuals of corrected iterates (double-float values and sums on the "
+                   "FP32 pipe, 16-bit column offsets, FP32 vectors)",
 }
 
 
@@ -612,7 +618,10 @@ def run_ours(args, dist):
     peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s (of fallback)"
     hbm = hbm or HBM_FALLBACK_GBS
     ag = tuned.get((0, pname, "AG"), -1) >= 0
-    per_launch = level0_launch_bytes(hh, w, nrhs, ag)
+    c16 = tuned.get((0, pname, "A"), -1) == 1600
+    per_launch = level0_launch_bytes(hh, w, nrhs, ag, c16=c16,
+                                     c16_wide=fp32 and args.wide_arith == "df" and
+                                     tuned.get((0, "fp32", "A"), -1) == 1600)
     # the roofline kernel: the level-0 A class with the most device time
     cls = max(per_launch, key=lambda k: prof[k][1])
     c, m = prof[cls]
@@ -621,7 +630,9 @@ def run_ours(args, dist):
         achieved = bytes_launch / (m / c / 1e3) / 1e9
         df = cls == "A_wide" and args.wide_arith == "df"
         fp64_values = (cls == "A_wide" and not df) or not fp32
-        kname = "A_wide_df" if df else cls
+        kname = ("A_wide_df16" if tuned.get((0, "fp32", "A"), -1) == 1600 else "A_wide_df") if df else cls
+        if cls == "A_fine" and c16:
+            kname = "A_fine16"
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                             "frac": achieved / hbm,
                             "traffic": NCU_TRAFFIC.get((args.workload, kname, w)) if nrhs == 1 else None,

@@ -68,7 +68,7 @@ constexpr int kSellSigma = 1024;
 void upload_sell(amge_hier* h, const HostCsr& M, DevSell<double>& d64, DevSell<float>& d32, cudaStream_t s,
                  std::vector<std::vector<float>>& keep, std::vector<HostSell>& keeps, bool allow_unit = false) {
   keeps.push_back(build_sell(M, kSellSigma, allow_unit));
-  const HostSell& S = keeps.back();
+  HostSell& S = keeps.back();
   d64.nr = d32.nr = S.nr;
   d64.nc = d32.nc = S.nc;
   d64.nslices = d32.nslices = S.nslices;
@@ -87,6 +87,10 @@ void upload_sell(amge_hier* h, const HostCsr& M, DevSell<double>& d64, DevSell<f
   d64.sptr = d32.sptr = upload<int64_t>(h, S.sptr.data(), S.sptr.size(), s);
   d64.srow = d32.srow = upload<int>(h, S.srow.data(), S.srow.size(), s);
   d64.ci = d32.ci = upload<int>(h, S.ci.data(), S.ci.size(), s);
+  if (build_sell16(S, S.sbase16, S.c16)) {  // kept alive in `keeps` until the copies finish
+    d64.sbase = d32.sbase = upload<int>(h, S.sbase16.data(), S.sbase16.size(), s);
+    d64.c16 = d32.c16 = upload<uint32_t>(h, S.c16.data(), S.c16.size(), s);
+  }
   if (S.unit) {  // sign-coded: the columns carry the +-1 entries
     d64.val = nullptr;
     d32.val = nullptr;
@@ -200,6 +204,7 @@ void opk(amge_hier* h, int cls, const LevelDev<V>& d, int op, int epi, const Spm
   Prof p(h, cls, s);
   const int code = d.lanes[op];  // sliced ELL (code_wps warps per slice, code_pf) or vector CSR lanes
   if (code_bulk(code) && launch_sell_bulk<V>(op_sell(d, op), epi, a, s, h->kwait)) return;
+  if (code_c16(code) && launch_sell16<V>(op_sell(d, op), epi, a, s)) return;
   if (code_is_sell(code)) launch_sell<V>(op_sell(d, op), epi, a, s, code_wps(code), code_pf(code));
   else launch_csrv<V>(op_csr(d, op), code, epi, a, s);
 }
@@ -218,8 +223,13 @@ int wide_wps(const amge_hier* h, int l) {
 void wide_product(amge_hier* h, int l, int epi, const SpmvArgs<float>& a, cudaStream_t s) {
   const DevSell<double>& M = h->lv64[l].A;
   const bool pf = code_pf(h->lv64[l].lanes[OP_A]);
-  if (h->wide_arith == AMGE_WIDE_DF && h->lv32[l].Adf) launch_sell_df(M, h->lv32[l].Adf, epi, a, s, wide_wps(h, l), pf);
-  else launch_sell_wide(M, epi, a, s, wide_wps(h, l), pf);
+  if (h->wide_arith == AMGE_WIDE_DF && h->lv32[l].Adf) {
+    // the 16-bit columns where the FP32 product of A_l uses them
+    if (code_c16(h->lv32[l].lanes[OP_A]) && launch_sell_df16(M, h->lv32[l].Adf, epi, a, s)) return;
+    launch_sell_df(M, h->lv32[l].Adf, epi, a, s, wide_wps(h, l), pf);
+  } else {
+    launch_sell_wide(M, epi, a, s, wide_wps(h, l), pf);
+  }
 }
 
 // A product with A_l in a residual form (EPI_RESID / EPI_SWEEP).  `corrected`: the
@@ -1527,7 +1537,7 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
 // Streamed operators (much larger than L2) come from HBM either way and are timed back
 // to back, where each launch overlaps the previous one's tail as it does behind its
 // predecessor in the V-cycle.
-constexpr int kTuneCodes[kNumTuneCodes] = {0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000};
+constexpr int kTuneCodes[kNumTuneCodes] = {0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000, 1600};
 constexpr int kTuneReps = 10;
 
 struct TuneFlush {
@@ -1610,6 +1620,8 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
       if (code_bulk(lanes) && (!op_sell(d, op).stream || op_sell(d, op).unit || !sell_bulk_fits(op_sell(d, op)) ||
                                (op == OP_AG && d.g2)))
         continue;  // bulk staging: streamed operators with stored values (AG runs fused with G where it can)
+      if (code_c16(lanes) && (!op_sell(d, op).c16 || (op == OP_AG && d.g2)))
+        continue;  // 16-bit columns: where built (AG runs fused with G where it can)
       if (code_is_sell(lanes) && code_wps(lanes) > 1 && 2.0 * code_wps(lanes) > avg + 1.0) continue;  // more warps than entry pairs
       if (lanes > 2 && lanes < 100 && lanes > 2 * avg) continue;
       d.lanes[op] = lanes;
@@ -2397,8 +2409,9 @@ amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int3
     return AMGE_EINVAL;
   }
   if (lanes != 0 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32 && lanes != 200 &&
-      lanes != 400 && lanes != 800 && lanes != 1000 && lanes != 1200 && lanes != 3000) {
-    set_error("kernel code must be 0, 200, 400, 800, 1000, 1200, 3000 (sliced ELL) or 2, 4, 8, 16, 32 (vector CSR)");
+      lanes != 400 && lanes != 800 && lanes != 1000 && lanes != 1200 && lanes != 1600 && lanes != 3000) {
+    set_error(
+        "kernel code must be 0, 200, 400, 800, 1000, 1200, 1600, 3000 (sliced ELL) or 2, 4, 8, 16, 32 (vector CSR)");
     return AMGE_EINVAL;
   }
   int& cur = precision == 0 ? h->lv64[level].lanes[op] : h->lv32[level].lanes[op];

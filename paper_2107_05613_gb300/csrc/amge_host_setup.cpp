@@ -234,6 +234,38 @@ void coarse_inverse(int n, const std::vector<double>& LinvT, std::vector<double>
   }
 }
 
+// Lanes past the last row (srow < 0) gather at offset 0, the slice's smallest column:
+// their sums are never stored.
+bool build_sell16(const HostSell& S, std::vector<int>& sbase, std::vector<uint32_t>& c16) {
+  constexpr int C = 32;
+  if (S.unit) return false;
+  sbase.assign(S.nslices, 0);
+  c16.assign(S.sptr[S.nslices] / 2, 0u);
+  for (int s = 0; s < S.nslices; s++) {
+    const int np = (int)((S.sptr[s + 1] - S.sptr[s]) / (2 * C));
+    int lo = INT32_MAX, hi = INT32_MIN;
+    for (int j = 0; j < C; j++) {
+      if (S.srow[(size_t)s * C + j] < 0) continue;
+      for (int k = 0; k < np; k++)
+        for (int e = 0; e < 2; e++) {
+          const int c = S.ci[S.sptr[s] + (int64_t)k * 2 * C + 2 * j + e];
+          lo = std::min(lo, c), hi = std::max(hi, c);
+        }
+    }
+    if (lo > hi) lo = hi = 0;
+    if ((int64_t)hi - lo > 65535) return false;
+    sbase[s] = lo;
+    for (int j = 0; j < C; j++) {
+      const bool live = S.srow[(size_t)s * C + j] >= 0;
+      for (int k = 0; k < np; k++) {
+        const int64_t p = S.sptr[s] + (int64_t)k * 2 * C + 2 * j;
+        c16[p / 2] = live ? (uint32_t)(S.ci[p] - lo) | ((uint32_t)(S.ci[p + 1] - lo) << 16) : 0u;
+      }
+    }
+  }
+  return true;
+}
+
 HostSell build_sell(const HostCsr& M, int sigma, bool allow_unit) {
   constexpr int C = 32;
   HostSell S;

@@ -108,6 +108,8 @@ struct HostSell {
   std::vector<int> srow;          // [nslices * 32]
   std::vector<int> ci;            // [sptr[nslices]]
   std::vector<double> v;          // [sptr[nslices]] (empty when unit)
+  std::vector<int> sbase16;       // 16-bit column form (build_sell16), empty if not built
+  std::vector<uint32_t> c16;
 };
 // Sliced ELL of M; with allow_unit, an operator whose entries are all +-1 is sign-coded.
 HostSell build_sell(const HostCsr& M, int sigma, bool allow_unit = false);
@@ -123,6 +125,11 @@ struct DevSell {
   int* srow = nullptr;
   int* ci = nullptr;
   V* val = nullptr;
+  // 16-bit column offsets (k_sell16): per slice its smallest column, per entry pair the
+  // two offsets from it packed low | high << 16; null where a slice spans 65,536
+  // columns or more, or the operator is sign-coded
+  int* sbase = nullptr;
+  uint32_t* c16 = nullptr;
 };
 
 // Epilogues of the sliced-ELL product (s = row i of M times the gathered vector).
@@ -161,6 +168,8 @@ inline bool code_pf(int c) { return c == 1000 || c == 1200; }
 // 3000: one warp per slice with the slice's entries staged into shared memory by bulk
 // asynchronous copies (streamed operators with stored values; see k_sell_bulk).
 inline bool code_bulk(int c) { return c == 3000; }
+// 1600: one warp per slice with 16-bit column offsets (see k_sell16).
+inline bool code_c16(int c) { return c == 1600; }
 
 // wps = warps per 32-row slice (1, 2, 4, 8); pf: a streamed operator's slices are
 // also prefetched into L2 in bulk (wps 1 or 2).
@@ -174,6 +183,13 @@ template <typename V>
 bool launch_sell_bulk(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, int* err);
 template <typename V>
 bool sell_bulk_fits(const DevSell<V>& M);
+// The 16-bit-column forms (false, nothing launched, where M has no 16-bit columns).
+template <typename V>
+bool launch_sell16(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+bool launch_sell_df16(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a, cudaStream_t s);
+// Host construction of the 16-bit columns of a sliced-ELL operator (false if a slice
+// spans too many columns or the operator is sign-coded).
+bool build_sell16(const HostSell& S, std::vector<int>& sbase, std::vector<uint32_t>& c16);
 // Raises the bulk-staged kernels' shared-memory limit on the current device (once;
 // outside any stream capture).  Until it has run there, launch_sell_bulk returns false.
 void sell_bulk_prepare();

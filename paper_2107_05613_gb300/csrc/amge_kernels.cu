@@ -194,6 +194,55 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
   sell_store<V, EPI>(a, row, s);
 }
 
+// Sliced ELL with 16-bit column offsets (autotuner code 1600): one warp per slice as
+// k_sell, but each entry pair's columns are two 16-bit offsets from the slice's
+// smallest column (sbase), 4 bytes per pair instead of 8, so a stored entry costs
+// 6 (FP32) or 10 (FP64) bytes instead of 8 or 12; built where every slice spans fewer
+// than 65,536 columns (the H(curl) finest operators, banded by the mesh numbering).
+// Same FMA chain as k_sell with one warp per slice: identical results.
+template <typename V, int EPI, bool CS>
+__global__ void __launch_bounds__(kBlock) k_sell16(int nslices, const int64_t* __restrict__ sptr,
+                                                   const int* __restrict__ srow, const int* __restrict__ sbase,
+                                                   const uint32_t* __restrict__ c16,
+                                                   const typename Pair<V>::T* __restrict__ val2, SpmvArgs<V> a) {
+  using PV = typename Pair<V>::T;
+  constexpr bool NEG = SellNeg<EPI>::value;
+  const int lane = threadIdx.x & 31;
+  const int slice = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+  if (slice >= nslices) {
+    pdl_begin();
+    return;
+  }
+  const int64_t p0 = ldg(sptr + slice) >> 1;
+  const int np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+  const int row = ldg(srow + (size_t)slice * 32 + lane);
+  const V* xb = a.x + ldg(sbase + slice);
+  const uint32_t* cp = c16 + p0 + lane;
+  const PV* vp = val2 + p0 + lane;
+  uint32_t u0 = 0;
+  PV v0{};
+  if (np > 0) {
+    u0 = ldm<CS>(cp);
+    v0 = ldm<CS>(vp);
+  }
+  pdl_begin();
+  V s = sell_init<V, EPI>(a, row);
+  if (np > 0) {
+    const V x0 = ldg(xb + (u0 & 0xffffu)), x1 = ldg(xb + (u0 >> 16));
+    s = fma(NEG ? -v0.x : v0.x, x0, s);
+    s = fma(NEG ? -v0.y : v0.y, x1, s);
+  }
+#pragma unroll 2
+  for (int k = 1; k < np; k++) {
+    const uint32_t u = ldm<CS>(cp + (size_t)k * 32);
+    const PV v = ldm<CS>(vp + (size_t)k * 32);
+    const V x0 = ldg(xb + (u & 0xffffu)), x1 = ldg(xb + (u >> 16));
+    s = fma(NEG ? -v.x : v.x, x0, s);
+    s = fma(NEG ? -v.y : v.y, x1, s);
+  }
+  if (row >= 0) sell_store<V, EPI>(a, row, s);
+}
+
 // FP32 -> FP64 without a conversion instruction: a normal float's exponent is
 // rebiased (+896 = 1023 - 127) and its 23-bit mantissa moved to the top of the 52-bit
 // field, both with integer operations, exact (every float is a double).  On GB300 the
@@ -349,6 +398,55 @@ __global__ void __launch_bounds__(kBlock) k_sell_df(int nslices, const int64_t* 
     }
   }
   if (!live || row < 0) return;
+  const float r = __fadd_rn(s.h, s.l);
+  if (EPI == EPI_SWEEP) a.y[row] = fmaf(a.d[row], r, a.xin[row]);
+  else a.y[row] = r;
+}
+
+// k_sell_df with the 16-bit column offsets of k_sell16 (one warp per slice; the
+// same sums, identical results).
+template <int EPI, bool CS>
+__global__ void __launch_bounds__(kBlock) k_sell_df16(int nslices, const int64_t* __restrict__ sptr,
+                                                      const int* __restrict__ srow, const int* __restrict__ sbase,
+                                                      const uint32_t* __restrict__ c16,
+                                                      const float4* __restrict__ val4, SpmvArgs<float> a) {
+  static_assert(EPI == EPI_STORE || EPI == EPI_RESID || EPI == EPI_SWEEP, "unsupported epilogue");
+  constexpr bool NEG = EPI != EPI_STORE;
+  const int lane = threadIdx.x & 31;
+  const int slice = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+  if (slice >= nslices) {
+    pdl_begin();
+    return;
+  }
+  const int64_t p0 = ldg(sptr + slice) >> 1;
+  const int np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+  const int row = ldg(srow + (size_t)slice * 32 + lane);
+  const float* xb = a.x + ldg(sbase + slice);
+  const uint32_t* cp = c16 + p0 + lane;
+  const float4* vp = val4 + p0 + lane;
+  uint32_t u0 = 0;
+  float4 v0{};
+  if (np > 0) {
+    u0 = ldm<CS>(cp);
+    v0 = ldm<CS>(vp);
+  }
+  pdl_begin();
+  DfSum s{0.f, 0.f};
+  if (NEG && row >= 0) s.h = a.b[row];
+  if (np > 0) {
+    const float x0 = ldg(xb + (u0 & 0xffffu)), x1 = ldg(xb + (u0 >> 16));
+    df_add_entry(s, NEG ? -v0.x : v0.x, NEG ? -v0.z : v0.z, x0);
+    df_add_entry(s, NEG ? -v0.y : v0.y, NEG ? -v0.w : v0.w, x1);
+  }
+#pragma unroll 2
+  for (int k = 1; k < np; k++) {
+    const uint32_t u = ldm<CS>(cp + (size_t)k * 32);
+    const float4 v = ldm<CS>(vp + (size_t)k * 32);
+    const float x0 = ldg(xb + (u & 0xffffu)), x1 = ldg(xb + (u >> 16));
+    df_add_entry(s, NEG ? -v.x : v.x, NEG ? -v.z : v.z, x0);
+    df_add_entry(s, NEG ? -v.y : v.y, NEG ? -v.w : v.w, x1);
+  }
+  if (row < 0) return;
   const float r = __fadd_rn(s.h, s.l);
   if (EPI == EPI_SWEEP) a.y[row] = fmaf(a.d[row], r, a.xin[row]);
   else a.y[row] = r;
@@ -1210,6 +1308,50 @@ static void launch_sell_u(const DevSell<V>& M, int wps, int epi, const SpmvArgs<
       else launch_sell_t<V, 1, UNIT, false>(M, epi, a, s);
       break;
   }
+}
+
+template <typename V, bool CS>
+static void launch_sell16_t(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  const int grid = (M.nslices + (kBlock / 32) - 1) / (kBlock / 32);
+  const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(M.val);
+  switch (epi) {
+    case EPI_STORE: launch_k(k_sell16<V, EPI_STORE, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
+    case EPI_RESID: launch_k(k_sell16<V, EPI_RESID, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
+    case EPI_SCALE: launch_k(k_sell16<V, EPI_SCALE, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
+    case EPI_ADD: launch_k(k_sell16<V, EPI_ADD, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
+    case EPI_SWEEP: launch_k(k_sell16<V, EPI_SWEEP, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
+    case EPI_STORE_MUL:
+      launch_k(k_sell16<V, EPI_STORE_MUL, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a);
+      break;
+  }
+}
+template <typename V>
+bool launch_sell16(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  if (!M.c16 || M.unit) return false;
+  if (M.nslices == 0) return true;
+  if (M.stream) launch_sell16_t<V, true>(M, epi, a, s);
+  else launch_sell16_t<V, false>(M, epi, a, s);
+  return true;
+}
+template bool launch_sell16<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t);
+template bool launch_sell16<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t);
+
+template <bool CS>
+static void launch_sell_df16_t(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a,
+                               cudaStream_t s) {
+  const int grid = (M.nslices + (kBlock / 32) - 1) / (kBlock / 32);
+  if (epi == EPI_RESID)
+    launch_k(k_sell_df16<EPI_RESID, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
+  else if (epi == EPI_SWEEP)
+    launch_k(k_sell_df16<EPI_SWEEP, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
+  else launch_k(k_sell_df16<EPI_STORE, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
+}
+bool launch_sell_df16(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a, cudaStream_t s) {
+  if (!M.c16 || M.unit) return false;
+  if (M.nslices == 0) return true;
+  if (M.stream) launch_sell_df16_t<true>(M, v4, epi, a, s);
+  else launch_sell_df16_t<false>(M, v4, epi, a, s);
+  return true;
 }
 
 template <typename V>

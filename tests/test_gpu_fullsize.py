@@ -93,7 +93,7 @@ class pinned_level0:
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200, 3000])
+@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200, 3000, 1600])
 def test_level0_products_sampled(amge, name, prec, kernels):
     """The level-0 products on the autotuned kernels, on the sliced-ELL kernels that
     prefetch each slice into L2 with one and two warps per slice, and on the one that
@@ -171,15 +171,17 @@ def _level0_wide(amge, h, o, name, arith):
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_level0_bulk_staged_equals_one_warp(amge, name, prec):
+@pytest.mark.parametrize("code", [3000, 1600])
+def test_level0_bulk_staged_equals_one_warp(amge, name, prec, code):
     """At full size, in the launch configuration of the timed solves: the level-0
-    operators on the bulk-staged kernel (code 3000) give the V-cycle and the PCG solve
-    of the one-warp sliced-ELL kernel (code 0) bit for bit."""
+    operators on the bulk-staged kernel (code 3000) or with 16-bit column offsets
+    (1600, where built: H(curl)) give the V-cycle and the PCG solve of the one-warp
+    sliced-ELL kernel (code 0) bit for bit."""
     h, o, b = workload(amge, name)
     bd = dev(b)
     res = []
-    for code in (0, 3000):
-        with pinned_level0(amge, h, code):
+    for c in (0, code):
+        with pinned_level0(amge, h, c):
             z, x = torch.empty_like(bd), torch.empty_like(bd)
             amge.amge_vcycle(h, bd, z, 1, prec)
             st, info = amge.amge_pcg_solve(h, bd, x, rtol=1e-8, precision=prec)
