@@ -618,10 +618,10 @@ def run_ours(args, dist):
     peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s (of fallback)"
     hbm = hbm or HBM_FALLBACK_GBS
     ag = tuned.get((0, pname, "AG"), -1) >= 0
-    c16 = tuned.get((0, pname, "A"), -1) == 1600
-    per_launch = level0_launch_bytes(hh, w, nrhs, ag, c16=c16,
-                                     c16_wide=fp32 and args.wide_arith == "df" and
-                                     tuned.get((0, "fp32", "A"), -1) == 1600)
+    C16_CODES = (1600, 1700)  # kernel codes with 16-bit column offsets
+    c16 = tuned.get((0, pname, "A"), -1) in C16_CODES
+    c16_wide = fp32 and args.wide_arith == "df" and tuned.get((0, "fp32", "A"), -1) in C16_CODES
+    per_launch = level0_launch_bytes(hh, w, nrhs, ag, c16=c16, c16_wide=c16_wide)
     # the roofline kernel: the level-0 A class with the most device time
     cls = max(per_launch, key=lambda k: prof[k][1])
     c, m = prof[cls]
@@ -630,7 +630,7 @@ def run_ours(args, dist):
         achieved = bytes_launch / (m / c / 1e3) / 1e9
         df = cls == "A_wide" and args.wide_arith == "df"
         fp64_values = (cls == "A_wide" and not df) or not fp32
-        kname = ("A_wide_df16" if tuned.get((0, "fp32", "A"), -1) == 1600 else "A_wide_df") if df else cls
+        kname = ("A_wide_df16" if c16_wide else "A_wide_df") if df else cls
         if cls == "A_fine" and c16:
             kname = "A_fine16"
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

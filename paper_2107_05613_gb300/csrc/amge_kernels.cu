@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
 // 6 (FP32) or 10 (FP64) bytes instead of 8 or 12; built where every slice spans fewer
 // than 65,536 columns (the H(curl) finest operators, banded by the mesh numbering).
 // Same FMA chain as k_sell with one warp per slice: identical results.
-template <typename V, int EPI, bool CS>
+template <typename V, int EPI, bool CS, bool PF = false>
 __global__ void __launch_bounds__(kBlock) k_sell16(int nslices, const int64_t* __restrict__ sptr,
                                                    const int* __restrict__ srow, const int* __restrict__ sbase,
                                                    const uint32_t* __restrict__ c16,
@@ -219,6 +219,10 @@ __global__ void __launch_bounds__(kBlock) k_sell16(int nslices, const int64_t* _
   const V* xb = a.x + ldg(sbase + slice);
   const uint32_t* cp = c16 + p0 + lane;
   const PV* vp = val2 + p0 + lane;
+  if (PF && lane == 0 && np > 0) {  // code 1700: the slice's entries into L2 first
+    prefetch_l2_bulk(c16 + p0, (uint32_t)np * 32u * sizeof(uint32_t));
+    prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(PV));
+  }
   uint32_t u0 = 0;
   PV v0{};
   if (np > 0) {
@@ -405,7 +409,7 @@ __global__ void __launch_bounds__(kBlock) k_sell_df(int nslices, const int64_t* 
 
 // k_sell_df with the 16-bit column offsets of k_sell16 (one warp per slice; the
 // same sums, identical results).
-template <int EPI, bool CS>
+template <int EPI, bool CS, bool PF = false>
 __global__ void __launch_bounds__(kBlock) k_sell_df16(int nslices, const int64_t* __restrict__ sptr,
                                                       const int* __restrict__ srow, const int* __restrict__ sbase,
                                                       const uint32_t* __restrict__ c16,
@@ -424,6 +428,10 @@ __global__ void __launch_bounds__(kBlock) k_sell_df16(int nslices, const int64_t
   const float* xb = a.x + ldg(sbase + slice);
   const uint32_t* cp = c16 + p0 + lane;
   const float4* vp = val4 + p0 + lane;
+  if (PF && lane == 0 && np > 0) {
+    prefetch_l2_bulk(c16 + p0, (uint32_t)np * 32u * sizeof(uint32_t));
+    prefetch_l2_bulk(val4 + p0, (uint32_t)np * 32u * sizeof(float4));
+  }
   uint32_t u0 = 0;
   float4 v0{};
   if (np > 0) {
@@ -701,19 +709,31 @@ __global__ void __launch_bounds__(kBulkWarps * 32) k_sell_bulk(int nslices, cons
 // partial sums in warp order, then applies G y and the epilogue).  As in k_sell, the
 // constant slice header, G's row and the first entry pair are loaded before waiting
 // for the previous kernel.
-template <typename V, bool POST, bool CS, int WPS, bool PF = false>
+// C16: the columns as 16-bit offsets from the slice's smallest column (k_sell16).
+template <typename V, bool POST, bool CS, int WPS, bool PF = false, bool C16 = false>
 __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t* __restrict__ sptr,
                                                      const int* __restrict__ srow, const int2* __restrict__ ci2,
-                                                     const typename Pair<V>::T* __restrict__ val2, AgArgs<V> a) {
+                                                     const typename Pair<V>::T* __restrict__ val2, AgArgs<V> a,
+                                                     const int* __restrict__ sbase, const uint32_t* __restrict__ c16) {
   using PV = typename Pair<V>::T;
   constexpr int kPre = 2;  // entry pairs per lane loaded before the dependent-launch wait
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int g = wib % WPS;
   const int slice = (blockIdx.x * (kBlock / 32) + wib) / WPS;
-  int row = -1, np = 0;
+  int row = -1, np = 0, base = 0;
   const int2* cp = ci2;
+  const uint32_t* up = c16;
   const PV* vp = val2;
+  // the entry pair k's two columns (C16: decoded from the 16-bit offsets)
+  auto cols = [&](int k) -> int2 {
+    if constexpr (C16) {
+      const uint32_t u = ldm<CS>(up + (size_t)k * 32);
+      return make_int2(base + (int)(u & 0xffffu), base + (int)(u >> 16));
+    } else {
+      return ldm<CS>(cp + (size_t)k * 32);
+    }
+  };
   int2 g2 = make_int2(kSellPad, kSellPad);
   int2 cpre[kPre];
   PV vpre[kPre];
@@ -724,10 +744,12 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
     np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
     row = ldg(srow + (size_t)slice * 32 + lane);
     if ((!CS || PF) && g == 0 && lane == 0 && np > 0) {
-      prefetch_l2_bulk(ci2 + p0, (uint32_t)np * 32u * sizeof(int2));
+      if (C16) prefetch_l2_bulk(c16 + p0, (uint32_t)np * 32u * sizeof(uint32_t));
+      else prefetch_l2_bulk(ci2 + p0, (uint32_t)np * 32u * sizeof(int2));
       prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(PV));
     }
-    cp += p0 + lane;
+    if (C16) base = ldg(sbase + slice), up += p0 + lane;
+    else cp += p0 + lane;
     vp += p0 + lane;
     if (row >= 0 && g == 0) g2 = ldg(a.g2 + row);
     // rows of A G are short (5.4 entries on the H(curl) finest level): the first kPre
@@ -735,7 +757,7 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
 #pragma unroll
     for (int t = 0; t < kPre; t++)
       if (g + t * WPS < np) {
-        cpre[t] = ldm<CS>(cp + (size_t)(g + t * WPS) * 32);
+        cpre[t] = cols(g + t * WPS);
         vpre[t] = ldm<CS>(vp + (size_t)(g + t * WPS) * 32);
       }
   }
@@ -763,7 +785,7 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
       }
 #pragma unroll 2
     for (int k = g + kPre * WPS; k < np; k += WPS) {
-      const int2 c = ldm<CS>(cp + (size_t)k * 32);
+      const int2 c = cols(k);
       const PV v = ldm<CS>(vp + (size_t)k * 32);
       const V x0 = ldg(a.y + c.x), x1 = ldg(a.y + c.y);
       s = fma(-v.x, x0, s);
@@ -1310,47 +1332,50 @@ static void launch_sell_u(const DevSell<V>& M, int wps, int epi, const SpmvArgs<
   }
 }
 
-template <typename V, bool CS>
+template <typename V, bool CS, bool PF>
 static void launch_sell16_t(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
   const int grid = (M.nslices + (kBlock / 32) - 1) / (kBlock / 32);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(M.val);
   switch (epi) {
-    case EPI_STORE: launch_k(k_sell16<V, EPI_STORE, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
-    case EPI_RESID: launch_k(k_sell16<V, EPI_RESID, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
-    case EPI_SCALE: launch_k(k_sell16<V, EPI_SCALE, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
-    case EPI_ADD: launch_k(k_sell16<V, EPI_ADD, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
-    case EPI_SWEEP: launch_k(k_sell16<V, EPI_SWEEP, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
+    case EPI_STORE: launch_k(k_sell16<V, EPI_STORE, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
+    case EPI_RESID: launch_k(k_sell16<V, EPI_RESID, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
+    case EPI_SCALE: launch_k(k_sell16<V, EPI_SCALE, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
+    case EPI_ADD: launch_k(k_sell16<V, EPI_ADD, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
+    case EPI_SWEEP: launch_k(k_sell16<V, EPI_SWEEP, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
     case EPI_STORE_MUL:
-      launch_k(k_sell16<V, EPI_STORE_MUL, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a);
+      launch_k(k_sell16<V, EPI_STORE_MUL, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a);
       break;
   }
 }
 template <typename V>
-bool launch_sell16(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+bool launch_sell16(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, bool pf) {
   if (!M.c16 || M.unit) return false;
   if (M.nslices == 0) return true;
-  if (M.stream) launch_sell16_t<V, true>(M, epi, a, s);
-  else launch_sell16_t<V, false>(M, epi, a, s);
+  if (M.stream && pf) launch_sell16_t<V, true, true>(M, epi, a, s);
+  else if (M.stream) launch_sell16_t<V, true, false>(M, epi, a, s);
+  else launch_sell16_t<V, false, false>(M, epi, a, s);
   return true;
 }
-template bool launch_sell16<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t);
-template bool launch_sell16<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t);
+template bool launch_sell16<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t, bool);
+template bool launch_sell16<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t, bool);
 
-template <bool CS>
+template <bool CS, bool PF>
 static void launch_sell_df16_t(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a,
                                cudaStream_t s) {
   const int grid = (M.nslices + (kBlock / 32) - 1) / (kBlock / 32);
   if (epi == EPI_RESID)
-    launch_k(k_sell_df16<EPI_RESID, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
+    launch_k(k_sell_df16<EPI_RESID, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
   else if (epi == EPI_SWEEP)
-    launch_k(k_sell_df16<EPI_SWEEP, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
-  else launch_k(k_sell_df16<EPI_STORE, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
+    launch_k(k_sell_df16<EPI_SWEEP, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
+  else launch_k(k_sell_df16<EPI_STORE, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
 }
-bool launch_sell_df16(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a, cudaStream_t s) {
+bool launch_sell_df16(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a, cudaStream_t s,
+                      bool pf) {
   if (!M.c16 || M.unit) return false;
   if (M.nslices == 0) return true;
-  if (M.stream) launch_sell_df16_t<true>(M, v4, epi, a, s);
-  else launch_sell_df16_t<false>(M, v4, epi, a, s);
+  if (M.stream && pf) launch_sell_df16_t<true, true>(M, v4, epi, a, s);
+  else if (M.stream) launch_sell_df16_t<true, false>(M, v4, epi, a, s);
+  else launch_sell_df16_t<false, false>(M, v4, epi, a, s);
   return true;
 }
 
@@ -1578,17 +1603,45 @@ void launch_ag_fused_t(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaS
   const int grid = (int)(((int64_t)AG.nslices * WPS + (kBlock / 32) - 1) / (kBlock / 32));
   const int2* ci2 = reinterpret_cast<const int2*>(AG.ci);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(AG.val);
+  const int* sb = nullptr;
+  const uint32_t* c16 = nullptr;
   if (AG.stream && pf && WPS <= 2) {
-    if (post) launch_k(k_ag_fused<V, true, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
-    else launch_k(k_ag_fused<V, false, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+    if (post) launch_k(k_ag_fused<V, true, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
+    else launch_k(k_ag_fused<V, false, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
   } else if (AG.stream) {
-    if (post) launch_k(k_ag_fused<V, true, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
-    else launch_k(k_ag_fused<V, false, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+    if (post) launch_k(k_ag_fused<V, true, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
+    else launch_k(k_ag_fused<V, false, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
   } else {
-    if (post) launch_k(k_ag_fused<V, true, false, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
-    else launch_k(k_ag_fused<V, false, false, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a);
+    if (post) launch_k(k_ag_fused<V, true, false, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
+    else launch_k(k_ag_fused<V, false, false, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
   }
 }
+
+// The fused pass with the 16-bit columns (one warp per slice; pf: the slice's entries
+// prefetched into L2 as with code 1000).
+template <typename V, bool CS, bool PF>
+void launch_ag_fused16_t(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s) {
+  const int grid = (AG.nslices + (kBlock / 32) - 1) / (kBlock / 32);
+  const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(AG.val);
+  const int2* ci2 = reinterpret_cast<const int2*>(AG.ci);
+  if (post)
+    launch_k(k_ag_fused<V, true, CS, 1, PF, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a,
+             (const int*)AG.sbase, (const uint32_t*)AG.c16);
+  else
+    launch_k(k_ag_fused<V, false, CS, 1, PF, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a,
+             (const int*)AG.sbase, (const uint32_t*)AG.c16);
+}
+template <typename V>
+bool launch_ag_fused16(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, bool pf) {
+  if (!AG.c16) return false;
+  if (AG.nslices == 0) return true;
+  if (AG.stream && pf) launch_ag_fused16_t<V, true, true>(AG, post, a, s);
+  else if (AG.stream) launch_ag_fused16_t<V, true, false>(AG, post, a, s);
+  else launch_ag_fused16_t<V, false, false>(AG, post, a, s);
+  return true;
+}
+template bool launch_ag_fused16<double>(const DevSell<double>&, int, const AgArgs<double>&, cudaStream_t, bool);
+template bool launch_ag_fused16<float>(const DevSell<float>&, int, const AgArgs<float>&, cudaStream_t, bool);
 
 template <typename V>
 void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, int wps, bool pf) {

@@ -93,7 +93,7 @@ class pinned_level0:
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200, 3000, 1600])
+@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200, 3000, 1600, 1700])
 def test_level0_products_sampled(amge, name, prec, kernels):
     """The level-0 products on the autotuned kernels, on the sliced-ELL kernels that
     prefetch each slice into L2 with one and two warps per slice, and on the one that

@@ -91,7 +91,7 @@ class pinned_kernels:
 
 @pytest.mark.parametrize("form,n,L", CASES)
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("lanes", ["tuned", 0, 200, 800, 4, 32, 3000, 1600])
+@pytest.mark.parametrize("lanes", ["tuned", 0, 200, 800, 4, 32, 3000, 1600, 1700])
 def test_single_operators(amge, form, n, L, prec, lanes):
     """Every stored product on every smoothing level, on each kernel: sliced ELL with
     one, two and eight warps per slice (sign-coded for the +-1 incidences G), with the
@@ -127,10 +127,10 @@ def test_single_operators(amge, form, n, L, prec, lanes):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("ag", [0, 200, 400, 800])
+@pytest.mark.parametrize("ag", [0, 200, 400, 800, 1600])
 def test_fused_aux_correction_equals_separate_products(amge, prec, ag):
     """H(curl): with G on the one-warp and A G on a sliced-ELL kernel (1, 2, 4 or 8
-    warps per slice) the V-cycle forms x += G y and r -= (A G) y (and the final
+    warps per slice, or 16-bit columns) the V-cycle forms x += G y and r -= (A G) y (and the final
     z = x + G y + m^-1 (r - (A G) y)) in one pass with that many warps per slice.
     Forcing G onto the two-warp kernel runs the separate products, whose sums are
     formed in the same order: the V-cycles must agree exactly."""
@@ -791,5 +791,5 @@ def test_autotune_report(amge):
     h = upload(amge, "hcurl", 24, 3)
     rep = amge.amge_autotune_report(h)
     assert len(rep) == 2 * 2 * 6
-    assert set(rep.values()) <= {-1, 0, 200, 400, 800, 1000, 1200, 1600, 3000, 2, 4, 8, 16, 32}
+    assert set(rep.values()) <= {-1, 0, 200, 400, 800, 1000, 1200, 1600, 1700, 3000, 2, 4, 8, 16, 32}
     assert rep[(0, "fp64", "AG")] >= 0          # H(curl): A G is stored (much sparser than A)
