@@ -515,6 +515,16 @@ amge_status amge_autotune_times(const amge_hier* h, float* us);
  * operator that is not stored (-1 in the report) or another lane count. */
 amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int32_t op, int32_t lanes);
 
+/* The PCG product q = A_0 p (FP64, with the p.q partials): code 0 = 32-bit columns,
+ * 1700 = 16-bit column offsets with each slice's entries prefetched into L2 (where
+ * A_0's slices span fewer than 65,536 columns).  Chosen at upload by timing both
+ * (us[0], us[1]: time per launch, -1 where not measured); both form the same sums.
+ * set = 0: report the choice in *code; set = 1: take *code as the choice (1700 acts
+ * as 0 without 16-bit columns) and report what is used.  us may be NULL.  Captured
+ * PCG graphs are rebuilt on the next solve.  AMGE_EINVAL for NULL h or code, or
+ * another code. */
+amge_status amge_pcg_kernel(amge_hier* h, int32_t set, int32_t* code, float* us);
+
 /* Kernel choice of the block (multi-right-hand-side) products for nrhs columns (2 ..
  * 32) and one precision, per smoothing level and operator (op order as above):
  * codes[l * 6 + op] = 0 CSR (a lane group per row), 1 / 2 sliced ELL with one / two

@@ -92,6 +92,7 @@ _SIGS = {
     "amge_update_coefficients": [_vp, _vp, _vp, _vp],
     "amge_wait_status": [_vp, _vp, ctypes.POINTER(_i32)],
     "amge_set_wide_arith": [_vp, _i32],
+    "amge_pcg_kernel": [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -324,6 +325,15 @@ def amge_set_wide_arith(h: Hier, arith: int):
     """Arithmetic of the FP32 V-cycle's residuals of corrected iterates:
     AMGE_WIDE_DF (double-float on the FP32 pipe, default) or AMGE_WIDE_FP64."""
     _check(_lib.amge_set_wide_arith(h.handle, int(arith)), "amge_set_wide_arith")
+
+
+def amge_pcg_kernel(h: Hier, code=None):
+    """The PCG product's kernel (0 or 1700) and the upload-time timings [us, us];
+    with `code`, set it first."""
+    c = _i32(0 if code is None else int(code))
+    us = (ctypes.c_float * 2)()
+    _check(_lib.amge_pcg_kernel(h.handle, 0 if code is None else 1, ctypes.byref(c), us), "amge_pcg_kernel")
+    return c.value, [round(float(us[0]), 2), round(float(us[1]), 2)]
 
 
 def amge_wait_status(h: Hier, stream=None) -> bool:

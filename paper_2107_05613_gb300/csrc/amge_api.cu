@@ -586,7 +586,7 @@ amge_status build_pcg_graph(amge_hier* h, int prec) {
     launch_pcg_dots<double>(n, h->pr, h->pz, h->pq, flexible, h->red, h->cap);
     launch_pcg_update_p<double>(n, h->pp, h->pz, h->red, h->cap);
   }
-  launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, h->cap);
+  launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, h->cap, h->pcg_c16);
   launch_pcg_axpy_norm(n, h->gx, h->pr, h->pp, h->pq, h->red, h->cap, pcg_x0_out(h, prec));
   launch_pcg_loop_cond(G.hw, n, h->red, h->gstate, h->cap);
   cudaGraph_t captured = nullptr;
@@ -715,7 +715,7 @@ amge_status run_step(PcgRun& r) {
       CK(cudaMemcpyAsync(h->pp, h->pz, n * sizeof(double), cudaMemcpyDeviceToDevice, r.s));
       {
         Prof p(h, AMGE_PROF_PCG_SPMV, r.s, 2);
-        launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, r.s);
+        launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, r.s, h->pcg_c16);
       }
       {
         Prof p(h, AMGE_PROF_PCG_VEC, r.s, 2);
@@ -1770,6 +1770,34 @@ amge_status tune_mm(amge_hier* h, int nrhs, int precision, cudaStream_t s) {
   return st;
 }
 
+// The PCG product q = A_0 p (with the p.q partials) in its two forms, 32-bit columns
+// and 16-bit columns with per-slice L2 prefetch (where A_0 has them): kTuneReps
+// launches back to back from a graph, best of three; the faster is kept.  Both form
+// the same sums.
+amge_status autotune_pcg_spmv(amge_hier* h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  h->pcg_c16 = false;
+  h->pcg_spmv_us[0] = h->pcg_spmv_us[1] = -1.f;
+  if (!h->A0.c16 || !h->pp) return AMGE_OK;
+  CK(cudaMemsetAsync(h->pp, 0, (size_t)h->n0 * sizeof(double), s));
+  for (int c = 0; c <= 1; c++) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int r = 0; r < kTuneReps; r++) launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, s, c == 1);
+    CK(cudaStreamEndCapture(s, &g));
+    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CK(ie);
+    float ms = 0.f;
+    cudaError_t le = time_graph(ge, s, e0, e1, &ms);
+    cudaGraphExecDestroy(ge);
+    CK(le);
+    h->pcg_spmv_us[c] = ms * (1e3f / kTuneReps);
+  }
+  h->pcg_c16 = h->pcg_spmv_us[1] < h->pcg_spmv_us[0];
+  return AMGE_OK;
+}
+
 amge_status autotune(amge_hier* h, cudaStream_t s) {
   // candidates are captured into graphs on a stream of our own (the caller's may be
   // the legacy default stream, which cannot be captured)
@@ -1806,6 +1834,7 @@ amge_status autotune(amge_hier* h, cudaStream_t s) {
     st = autotune_level<double>(h, l, ts, e0, e1, fl);
     if (st == AMGE_OK) st = autotune_level<float>(h, l, ts, e0, e1, fl);
   }
+  if (st == AMGE_OK) st = autotune_pcg_spmv(h, ts, e0, e1);
   cudaStreamSynchronize(ts);
   cudaStreamDestroy(ts);
   cudaEventDestroy(e0);
@@ -2029,7 +2058,7 @@ amge_status pcg_one(amge_hier* h, const double* b, double* x, const amge_solve_o
   while (it < o.maxit) {
     {
       Prof p(h, AMGE_PROF_PCG_SPMV, s, 2);
-      launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, s);
+      launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, s, h->pcg_c16);
     }
     {
       Prof p(h, AMGE_PROF_PCG_VEC, s, 2);
@@ -2097,7 +2126,8 @@ amge_status amge::hier_make_view(const amge_hier* src, cudaStream_t s, amge_hier
   v->lv64 = src->lv64;  // operator pointers shared; alloc_work replaces the work pointers
   v->lv32 = src->lv32;
   v->A0 = src->A0, v->cA0 = src->cA0;
-  v->nC = src->nC, v->Linv = src->Linv, v->LinvT = src->LinvT, v->Ainv = src->Ainv;
+  v->nC = src->nC, v->Linv = src->Linv, v->LinvT = src->LinvT, v->Ainv = src->Ainv, v->Ainv_df = src->Ainv_df;
+  v->wide_arith = src->wide_arith, v->pcg_c16 = src->pcg_c16;
   v->use_graphs = src->use_graphs;
   v->device = src->device;
   v->smoother = src->smoother, v->sweeps = src->sweeps, v->gs_levels = src->gs_levels, v->gs_built = src->gs_built;
@@ -2396,6 +2426,28 @@ amge_status amge_autotune_times(const amge_hier* h, float* us) {
         us[k] = h->lv64[l].lanes[op] < 0 ? -1.f : h->lv64[l].tune_us[op][c];
         us[k + 6 * kNumTuneCodes] = h->lv32[l].lanes[op] < 0 ? -1.f : h->lv32[l].tune_us[op][c];
       }
+  return AMGE_OK;
+}
+
+amge_status amge_pcg_kernel(amge_hier* h, int32_t set, int32_t* code, float* us) {
+  if (!h || !code) {
+    set_error("NULL argument");
+    return AMGE_EINVAL;
+  }
+  if (set) {
+    if (*code != 0 && *code != 1700) {
+      set_error("PCG product code must be 0 or 1700");
+      return AMGE_EINVAL;
+    }
+    h->pcg_c16 = (*code == 1700) && h->A0.c16;
+    for (GraphPcg& G : h->gpcg) {  // the captured loop names the old kernel
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      if (G.g) cudaGraphDestroy(G.g);
+      G = GraphPcg{};
+    }
+  }
+  *code = h->pcg_c16 ? 1700 : 0;
+  if (us) us[0] = h->pcg_spmv_us[0], us[1] = h->pcg_spmv_us[1];
   return AMGE_OK;
 }
 

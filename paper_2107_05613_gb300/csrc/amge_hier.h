@@ -122,6 +122,9 @@ struct amge_hier {
   cudaStream_t cap = nullptr;  // capture stream of the graphs
   int* gstate = nullptr;       // device: iterations done, maxit, non-finite flag
   int* kwait = nullptr;        // device: set by a bounded wait that ran out (amge_wait_status)
+  // PCG q = A p with the 16-bit columns and per-slice L2 prefetch (timed at upload)
+  bool pcg_c16 = false;
+  float pcg_spmv_us[2] = {-1.f, -1.f};
   double* gx = nullptr;        // device: iterate of the graph-driven loop
   int* pinned_state = nullptr;
   bool use_graphs = true;

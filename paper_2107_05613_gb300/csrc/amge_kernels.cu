@@ -1069,32 +1069,54 @@ __global__ void __launch_bounds__(kBlock, 8) k_dot(int64_t n, const double* __re
 // that finishes its slice leaves its row products in shared memory and exits; the
 // last warp of the block to arrive (a shared-memory counter) sums them in a fixed
 // order, so no warp idles at a block barrier behind a longer slice.
-template <bool CS>
+template <bool CS, bool C16 = false>
 __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, const int64_t* __restrict__ sptr,
                                                                    const int* __restrict__ srow,
                                                                    const int2* __restrict__ ci2,
                                                                    const double2* __restrict__ val2,
                                                                    const double* __restrict__ p,
-                                                                   double* __restrict__ q, double* part) {
+                                                                   double* __restrict__ q, double* part,
+                                                                   const int* __restrict__ sbase,
+                                                                   const uint32_t* __restrict__ c16) {
   __shared__ double sh[kSpmvDotBlock];
   __shared__ unsigned arrived;
   if (threadIdx.x == 0) arrived = 0u;
   const int lane = threadIdx.x & 31;
   const int slice = (blockIdx.x * kSpmvDotBlock + threadIdx.x) >> 5;
   // constant slice header and first entry pair before waiting (see k_sell)
-  int row = -1, np = 0;
+  // C16: 16-bit column offsets from the slice's smallest column, and each slice's
+  // entries prefetched into L2 first (the 1700 form of k_sell16; same sums)
+  int row = -1, np = 0, base = 0;
   const int2* cp = ci2;
+  const uint32_t* up = c16;
   const double2* vp = val2;
+  auto cols = [&](int k) -> int2 {
+    if constexpr (C16) {
+      const uint32_t u = ldm<CS>(up + (size_t)k * 32);
+      return make_int2(base + (int)(u & 0xffffu), base + (int)(u >> 16));
+    } else {
+      return ldm<CS>(cp + (size_t)k * 32);
+    }
+  };
   int2 c0 = make_int2(0, 0);
   double2 v0 = make_double2(0.0, 0.0);
   if (slice < nslices) {
     const int64_t p0 = ldg(sptr + slice) >> 1;
     np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
     row = ldg(srow + (size_t)slice * 32 + lane);
-    cp += p0 + lane;
+    if (C16) {
+      if (lane == 0 && np > 0) {
+        prefetch_l2_bulk(c16 + p0, (uint32_t)np * 32u * sizeof(uint32_t));
+        prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(double2));
+      }
+      base = ldg(sbase + slice);
+      up += p0 + lane;
+    } else {
+      cp += p0 + lane;
+    }
     vp += p0 + lane;
     if (np > 0) {
-      c0 = ldm<CS>(cp);
+      c0 = cols(0);
       v0 = ldm<CS>(vp);
     }
   }
@@ -1110,7 +1132,7 @@ __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, 
     }
 #pragma unroll 2
     for (int k = 1; k < np; k++) {
-      const int2 c = ldm<CS>(cp + (size_t)k * 32);
+      const int2 c = cols(k);
       const double2 v = ldm<CS>(vp + (size_t)k * 32);
       const double x0 = ldg(p + c.x), x1 = ldg(p + c.y);
       acc = fma(v.x, x0, acc);
@@ -1725,11 +1747,14 @@ int pcg_spmv_blocks(const DevSell<double>& A) {
 }
 
 void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, const RedScratch& r,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool c16) {
   const int grid = pcg_spmv_blocks(A);
-  auto k = A.stream ? k_pcg_spmv_dot<true> : k_pcg_spmv_dot<false>;
+  const bool use16 = c16 && A.c16 && !A.unit;
+  auto k = use16 ? (A.stream ? k_pcg_spmv_dot<true, true> : k_pcg_spmv_dot<false, true>)
+                 : (A.stream ? k_pcg_spmv_dot<true> : k_pcg_spmv_dot<false>);
   launch_k(k, grid, kSpmvDotBlock, s, A.nslices, A.sptr, A.srow, reinterpret_cast<const int2*>(A.ci),
-                                   reinterpret_cast<const double2*>(A.val), p, q, r.partials + kSlotPQ * kMaxRedBlocks);
+           reinterpret_cast<const double2*>(A.val), p, q, r.partials + kSlotPQ * kMaxRedBlocks,
+           (const int*)A.sbase, (const uint32_t*)A.c16);
   launch_k(k_pcg_finish_pq, 1, kFinishBlock, s, grid, r);
 }
 
