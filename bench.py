@@ -49,7 +49,9 @@ WORKLOADS = {
 # dram__bytes_read.sum + dram__bytes_write.sum of one level-0 residual sweep from an
 # ncu capture (profiles/k_sell_fp64_resid_level0_hcurl64.md); only for that kernel
 # and workload, null elsewhere.
-NCU_TRAFFIC = {("hcurl64", "A_fine", 8): 431.0e6}
+NCU_TRAFFIC = {("hcurl64", "A_fine", 8): 431.0e6,
+               # profiles/k_sell_df16_resid_level0_hcurl64.md
+               ("hcurl64", "A_wide_df16", 4): 354.4e6}
 
 HBM_FALLBACK_GBS = 6800.0
 METRIC = "PCG solves/s to 1e-8 rel residual"
