@@ -87,9 +87,10 @@ void upload_sell(amge_hier* h, const HostCsr& M, DevSell<double>& d64, DevSell<f
   d64.sptr = d32.sptr = upload<int64_t>(h, S.sptr.data(), S.sptr.size(), s);
   d64.srow = d32.srow = upload<int>(h, S.srow.data(), S.srow.size(), s);
   d64.ci = d32.ci = upload<int>(h, S.ci.data(), S.ci.size(), s);
-  if (build_sell16(S, S.sbase16, S.c16)) {  // kept alive in `keeps` until the copies finish
+  if (build_sell16(S, S.sbase16, S.c16, &S.c16_rb)) {  // kept alive in `keeps` until the copies finish
     d64.sbase = d32.sbase = upload<int>(h, S.sbase16.data(), S.sbase16.size(), s);
     d64.c16 = d32.c16 = upload<uint32_t>(h, S.c16.data(), S.c16.size(), s);
+    d64.c16_rb = d32.c16_rb = S.c16_rb ? 1 : 0;
   }
   if (S.unit) {  // sign-coded: the columns carry the +-1 entries
     d64.val = nullptr;

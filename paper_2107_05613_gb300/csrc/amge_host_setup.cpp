@@ -234,35 +234,55 @@ void coarse_inverse(int n, const std::vector<double>& LinvT, std::vector<double>
   }
 }
 
-// Lanes past the last row (srow < 0) gather at offset 0, the slice's smallest column:
-// their sums are never stored.
-bool build_sell16(const HostSell& S, std::vector<int>& sbase, std::vector<uint32_t>& c16) {
+// Lanes past the last row (srow < 0) gather at offset 0 from their base (a valid
+// column): their sums are never stored.
+bool build_sell16(const HostSell& S, std::vector<int>& sbase, std::vector<uint32_t>& c16, bool* rowbase) {
   constexpr int C = 32;
+  *rowbase = false;
   if (S.unit) return false;
-  sbase.assign(S.nslices, 0);
-  c16.assign(S.sptr[S.nslices] / 2, 0u);
+  auto entry = [&](int s, int j, int k, int e) { return S.ci[S.sptr[s] + (int64_t)k * 2 * C + 2 * j + e]; };
+  auto npairs = [&](int s) { return (int)((S.sptr[s + 1] - S.sptr[s]) / (2 * C)); };
+  // the smallest and largest column of every live row (lane) and slice
+  std::vector<int> rlo((size_t)S.nslices * C, 0), rhi((size_t)S.nslices * C, 0);
+  bool slice_fit = true, row_fit = true;
   for (int s = 0; s < S.nslices; s++) {
-    const int np = (int)((S.sptr[s + 1] - S.sptr[s]) / (2 * C));
     int lo = INT32_MAX, hi = INT32_MIN;
     for (int j = 0; j < C; j++) {
       if (S.srow[(size_t)s * C + j] < 0) continue;
-      for (int k = 0; k < np; k++)
-        for (int e = 0; e < 2; e++) {
-          const int c = S.ci[S.sptr[s] + (int64_t)k * 2 * C + 2 * j + e];
-          lo = std::min(lo, c), hi = std::max(hi, c);
-        }
+      int l = INT32_MAX, h = INT32_MIN;
+      for (int k = 0; k < npairs(s); k++)
+        for (int e = 0; e < 2; e++) l = std::min(l, entry(s, j, k, e)), h = std::max(h, entry(s, j, k, e));
+      if (l > h) l = h = 0;
+      rlo[(size_t)s * C + j] = l, rhi[(size_t)s * C + j] = h;
+      row_fit = row_fit && (int64_t)h - l <= 65535;
+      lo = std::min(lo, l), hi = std::max(hi, h);
     }
     if (lo > hi) lo = hi = 0;
-    if ((int64_t)hi - lo > 65535) return false;
-    sbase[s] = lo;
+    slice_fit = slice_fit && (int64_t)hi - lo <= 65535;
+  }
+  if (!slice_fit && !row_fit) return false;
+  *rowbase = !slice_fit;
+  if (slice_fit) {
+    sbase.assign(S.nslices, 0);
+    for (int s = 0; s < S.nslices; s++) {
+      int lo = INT32_MAX;
+      for (int j = 0; j < C; j++)
+        if (S.srow[(size_t)s * C + j] >= 0) lo = std::min(lo, rlo[(size_t)s * C + j]);
+      sbase[s] = lo == INT32_MAX ? 0 : lo;
+    }
+  } else {
+    sbase = rlo;
+  }
+  c16.assign(S.sptr[S.nslices] / 2, 0u);
+  for (int s = 0; s < S.nslices; s++)
     for (int j = 0; j < C; j++) {
-      const bool live = S.srow[(size_t)s * C + j] >= 0;
-      for (int k = 0; k < np; k++) {
+      if (S.srow[(size_t)s * C + j] < 0) continue;
+      const int base = slice_fit ? sbase[s] : sbase[(size_t)s * C + j];
+      for (int k = 0; k < npairs(s); k++) {
         const int64_t p = S.sptr[s] + (int64_t)k * 2 * C + 2 * j;
-        c16[p / 2] = live ? (uint32_t)(S.ci[p] - lo) | ((uint32_t)(S.ci[p + 1] - lo) << 16) : 0u;
+        c16[p / 2] = (uint32_t)(S.ci[p] - base) | ((uint32_t)(S.ci[p + 1] - base) << 16);
       }
     }
-  }
   return true;
 }
 

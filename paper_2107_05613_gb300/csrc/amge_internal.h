@@ -110,6 +110,7 @@ struct HostSell {
   std::vector<double> v;          // [sptr[nslices]] (empty when unit)
   std::vector<int> sbase16;       // 16-bit column form (build_sell16), empty if not built
   std::vector<uint32_t> c16;
+  bool c16_rb = false;            // sbase16 holds one base per row
 };
 // Sliced ELL of M; with allow_unit, an operator whose entries are all +-1 is sign-coded.
 HostSell build_sell(const HostCsr& M, int sigma, bool allow_unit = false);
@@ -130,6 +131,7 @@ struct DevSell {
   // columns or more, or the operator is sign-coded
   int* sbase = nullptr;
   uint32_t* c16 = nullptr;
+  int c16_rb = 0;  // 1: sbase holds one base per row ([nslices * 32], see build_sell16)
 };
 
 // Epilogues of the sliced-ELL product (s = row i of M times the gathered vector).
@@ -189,9 +191,10 @@ template <typename V>
 bool launch_sell16(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, bool pf = false);
 bool launch_sell_df16(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a, cudaStream_t s,
                       bool pf = false);
-// Host construction of the 16-bit columns of a sliced-ELL operator (false if a slice
-// spans too many columns or the operator is sign-coded).
-bool build_sell16(const HostSell& S, std::vector<int>& sbase, std::vector<uint32_t>& c16);
+// Host construction of the 16-bit columns of a sliced-ELL operator: one base per slice
+// where every slice spans fewer than 65,536 columns, else one per row where every row
+// does (*rowbase = true); false if neither, or the operator is sign-coded.
+bool build_sell16(const HostSell& S, std::vector<int>& sbase, std::vector<uint32_t>& c16, bool* rowbase);
 // Raises the bulk-staged kernels' shared-memory limit on the current device (once;
 // outside any stream capture).  Until it has run there, launch_sell_bulk returns false.
 void sell_bulk_prepare();

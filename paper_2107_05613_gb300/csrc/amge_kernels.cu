@@ -194,6 +194,13 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
   sell_store<V, EPI>(a, row, s);
 }
 
+// The column base of the 16-bit offsets of lane `lane` in slice `slice`: the slice's
+// smallest column (rb = 0), or, where a slice spans too many columns, the lane's row's
+// smallest column (rb = 1, one base per row).
+__device__ __forceinline__ int col_base(const int* __restrict__ base, int rb, int slice, int lane) {
+  return rb ? __ldg(base + (size_t)slice * 32 + lane) : __ldg(base + slice);
+}
+
 // Sliced ELL with 16-bit column offsets (autotuner code 1600): one warp per slice as
 // k_sell, but each entry pair's columns are two 16-bit offsets from the slice's
 // smallest column (sbase), 4 bytes per pair instead of 8, so a stored entry costs
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslices, const int64_t* __r
 // Same FMA chain as k_sell with one warp per slice: identical results.
 template <typename V, int EPI, bool CS, bool PF = false>
 __global__ void __launch_bounds__(kBlock) k_sell16(int nslices, const int64_t* __restrict__ sptr,
-                                                   const int* __restrict__ srow, const int* __restrict__ sbase,
+                                                   const int* __restrict__ srow, const int* __restrict__ sbase, int rb,
                                                    const uint32_t* __restrict__ c16,
                                                    const typename Pair<V>::T* __restrict__ val2, SpmvArgs<V> a) {
   using PV = typename Pair<V>::T;
@@ -216,7 +223,7 @@ __global__ void __launch_bounds__(kBlock) k_sell16(int nslices, const int64_t* _
   const int64_t p0 = ldg(sptr + slice) >> 1;
   const int np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
   const int row = ldg(srow + (size_t)slice * 32 + lane);
-  const V* xb = a.x + ldg(sbase + slice);
+  const V* xb = a.x + col_base(sbase, rb, slice, lane);
   const uint32_t* cp = c16 + p0 + lane;
   const PV* vp = val2 + p0 + lane;
   if (PF && lane == 0 && np > 0) {  // code 1700: the slice's entries into L2 first
@@ -411,7 +418,7 @@ __global__ void __launch_bounds__(kBlock) k_sell_df(int nslices, const int64_t* 
 // same sums, identical results).
 template <int EPI, bool CS, bool PF = false>
 __global__ void __launch_bounds__(kBlock) k_sell_df16(int nslices, const int64_t* __restrict__ sptr,
-                                                      const int* __restrict__ srow, const int* __restrict__ sbase,
+                                                      const int* __restrict__ srow, const int* __restrict__ sbase, int rb,
                                                       const uint32_t* __restrict__ c16,
                                                       const float4* __restrict__ val4, SpmvArgs<float> a) {
   static_assert(EPI == EPI_STORE || EPI == EPI_RESID || EPI == EPI_SWEEP, "unsupported epilogue");
@@ -425,7 +432,7 @@ __global__ void __launch_bounds__(kBlock) k_sell_df16(int nslices, const int64_t
   const int64_t p0 = ldg(sptr + slice) >> 1;
   const int np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
   const int row = ldg(srow + (size_t)slice * 32 + lane);
-  const float* xb = a.x + ldg(sbase + slice);
+  const float* xb = a.x + col_base(sbase, rb, slice, lane);
   const uint32_t* cp = c16 + p0 + lane;
   const float4* vp = val4 + p0 + lane;
   if (PF && lane == 0 && np > 0) {
@@ -714,7 +721,8 @@ template <typename V, bool POST, bool CS, int WPS, bool PF = false, bool C16 = f
 __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t* __restrict__ sptr,
                                                      const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                      const typename Pair<V>::T* __restrict__ val2, AgArgs<V> a,
-                                                     const int* __restrict__ sbase, const uint32_t* __restrict__ c16) {
+                                                     const int* __restrict__ sbase, int rb,
+                                                     const uint32_t* __restrict__ c16) {
   using PV = typename Pair<V>::T;
   constexpr int kPre = 2;  // entry pairs per lane loaded before the dependent-launch wait
   const int wib = threadIdx.x >> 5;
@@ -748,7 +756,7 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
       else prefetch_l2_bulk(ci2 + p0, (uint32_t)np * 32u * sizeof(int2));
       prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(PV));
     }
-    if (C16) base = ldg(sbase + slice), up += p0 + lane;
+    if (C16) base = col_base(sbase, rb, slice, lane), up += p0 + lane;
     else cp += p0 + lane;
     vp += p0 + lane;
     if (row >= 0 && g == 0) g2 = ldg(a.g2 + row);
@@ -1076,7 +1084,7 @@ __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, 
                                                                    const double2* __restrict__ val2,
                                                                    const double* __restrict__ p,
                                                                    double* __restrict__ q, double* part,
-                                                                   const int* __restrict__ sbase,
+                                                                   const int* __restrict__ sbase, int rb,
                                                                    const uint32_t* __restrict__ c16) {
   __shared__ double sh[kSpmvDotBlock];
   __shared__ unsigned arrived;
@@ -1109,7 +1117,7 @@ __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, 
         prefetch_l2_bulk(c16 + p0, (uint32_t)np * 32u * sizeof(uint32_t));
         prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(double2));
       }
-      base = ldg(sbase + slice);
+      base = col_base(sbase, rb, slice, lane);
       up += p0 + lane;
     } else {
       cp += p0 + lane;
@@ -1359,13 +1367,13 @@ static void launch_sell16_t(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, 
   const int grid = (M.nslices + (kBlock / 32) - 1) / (kBlock / 32);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(M.val);
   switch (epi) {
-    case EPI_STORE: launch_k(k_sell16<V, EPI_STORE, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
-    case EPI_RESID: launch_k(k_sell16<V, EPI_RESID, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
-    case EPI_SCALE: launch_k(k_sell16<V, EPI_SCALE, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
-    case EPI_ADD: launch_k(k_sell16<V, EPI_ADD, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
-    case EPI_SWEEP: launch_k(k_sell16<V, EPI_SWEEP, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a); break;
+    case EPI_STORE: launch_k(k_sell16<V, EPI_STORE, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a); break;
+    case EPI_RESID: launch_k(k_sell16<V, EPI_RESID, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a); break;
+    case EPI_SCALE: launch_k(k_sell16<V, EPI_SCALE, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a); break;
+    case EPI_ADD: launch_k(k_sell16<V, EPI_ADD, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a); break;
+    case EPI_SWEEP: launch_k(k_sell16<V, EPI_SWEEP, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a); break;
     case EPI_STORE_MUL:
-      launch_k(k_sell16<V, EPI_STORE_MUL, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v2, a);
+      launch_k(k_sell16<V, EPI_STORE_MUL, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a);
       break;
   }
 }
@@ -1386,10 +1394,10 @@ static void launch_sell_df16_t(const DevSell<double>& M, const float4* v4, int e
                                cudaStream_t s) {
   const int grid = (M.nslices + (kBlock / 32) - 1) / (kBlock / 32);
   if (epi == EPI_RESID)
-    launch_k(k_sell_df16<EPI_RESID, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
+    launch_k(k_sell_df16<EPI_RESID, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v4, a);
   else if (epi == EPI_SWEEP)
-    launch_k(k_sell_df16<EPI_SWEEP, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
-  else launch_k(k_sell_df16<EPI_STORE, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16, v4, a);
+    launch_k(k_sell_df16<EPI_SWEEP, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v4, a);
+  else launch_k(k_sell_df16<EPI_STORE, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v4, a);
 }
 bool launch_sell_df16(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a, cudaStream_t s,
                       bool pf) {
@@ -1628,14 +1636,14 @@ void launch_ag_fused_t(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaS
   const int* sb = nullptr;
   const uint32_t* c16 = nullptr;
   if (AG.stream && pf && WPS <= 2) {
-    if (post) launch_k(k_ag_fused<V, true, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
-    else launch_k(k_ag_fused<V, false, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
+    if (post) launch_k(k_ag_fused<V, true, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
+    else launch_k(k_ag_fused<V, false, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
   } else if (AG.stream) {
-    if (post) launch_k(k_ag_fused<V, true, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
-    else launch_k(k_ag_fused<V, false, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
+    if (post) launch_k(k_ag_fused<V, true, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
+    else launch_k(k_ag_fused<V, false, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
   } else {
-    if (post) launch_k(k_ag_fused<V, true, false, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
-    else launch_k(k_ag_fused<V, false, false, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, c16);
+    if (post) launch_k(k_ag_fused<V, true, false, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
+    else launch_k(k_ag_fused<V, false, false, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
   }
 }
 
@@ -1648,10 +1656,10 @@ void launch_ag_fused16_t(const DevSell<V>& AG, int post, const AgArgs<V>& a, cud
   const int2* ci2 = reinterpret_cast<const int2*>(AG.ci);
   if (post)
     launch_k(k_ag_fused<V, true, CS, 1, PF, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a,
-             (const int*)AG.sbase, (const uint32_t*)AG.c16);
+             (const int*)AG.sbase, AG.c16_rb, (const uint32_t*)AG.c16);
   else
     launch_k(k_ag_fused<V, false, CS, 1, PF, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a,
-             (const int*)AG.sbase, (const uint32_t*)AG.c16);
+             (const int*)AG.sbase, AG.c16_rb, (const uint32_t*)AG.c16);
 }
 template <typename V>
 bool launch_ag_fused16(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, bool pf) {
@@ -1754,7 +1762,7 @@ void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, c
                  : (A.stream ? k_pcg_spmv_dot<true> : k_pcg_spmv_dot<false>);
   launch_k(k, grid, kSpmvDotBlock, s, A.nslices, A.sptr, A.srow, reinterpret_cast<const int2*>(A.ci),
            reinterpret_cast<const double2*>(A.val), p, q, r.partials + kSlotPQ * kMaxRedBlocks,
-           (const int*)A.sbase, (const uint32_t*)A.c16);
+           (const int*)A.sbase, A.c16_rb, (const uint32_t*)A.c16);
   launch_k(k_pcg_finish_pq, 1, kFinishBlock, s, grid, r);
 }
 

@@ -101,4 +101,18 @@ void shim_sell_copy(const void* s, int64_t* sptr, int* srow, int* ci, double* v)
   if (!S->unit) std::memcpy(v, S->v.data(), S->v.size() * sizeof(double));
 }
 
+// 16-bit columns of a sliced ELL: returns 0 (not built), 1 (per-slice base), 2 (per-row
+// base); bases / c16 sized by the caller (nslices * 32 and stored / 2).
+int shim_sell16(const void* s, int* bases, uint32_t* c16, int64_t* nbases) {
+  const HostSell* S = static_cast<const HostSell*>(s);
+  std::vector<int> b;
+  std::vector<uint32_t> c;
+  bool rb = false;
+  if (!amge::build_sell16(*S, b, c, &rb)) return 0;
+  std::memcpy(bases, b.data(), b.size() * sizeof(int));
+  std::memcpy(c16, c.data(), c.size() * sizeof(uint32_t));
+  *nbases = (int64_t)b.size();
+  return rb ? 2 : 1;
+}
+
 }  // extern "C"

@@ -55,6 +55,7 @@ def lib(tmp_path_factory):
         ("shim_sell_free", [vp], None),
         ("shim_sell_info", [vp, ip], None),
         ("shim_sell_copy", [vp, ip, ip, ip, dp], None),
+        ("shim_sell16", [vp, ip, ip, ip], i32),
         ("shim_error", [], ctypes.c_char_p),
     ]:
         f = getattr(L, name)
@@ -283,3 +284,63 @@ def test_sliced_ell_sign_coded(lib):
     G2 = G.copy()
     G2.data[0] = 2.0
     assert not sell_rows(lib, G2, 1024, True)[5]
+
+
+def _sell16(lib, M, sigma=1024):
+    h = to_shim(lib, M)
+    s = lib.shim_sell(h, sigma, 0)
+    lib.shim_csr_free(h)
+    info = np.zeros(3, np.int64)
+    lib.shim_sell_info(s, _ptr(info))
+    ns, stored = int(info[0]), int(info[1])
+    sptr, srow = np.zeros(ns + 1, np.int64), np.zeros(ns * 32, np.int32)
+    ci, v = np.zeros(max(stored, 1), np.int32), np.zeros(max(stored, 1))
+    lib.shim_sell_copy(s, _ptr(sptr), _ptr(srow), _ptr(ci), _ptr(v))
+    bases = np.zeros(ns * 32, np.int32)
+    c16 = np.zeros(max(stored // 2, 1), np.uint32)
+    nb = np.zeros(1, np.int64)
+    mode = lib.shim_sell16(s, _ptr(bases), _ptr(c16), _ptr(nb))
+    lib.shim_sell_free(s)
+    return mode, ns, sptr, srow, ci, bases[:nb[0]], c16
+
+
+def _check16(mode, ns, sptr, srow, ci, bases, c16):
+    """Every live lane's decoded columns equal the 32-bit ones."""
+    for s in range(ns):
+        w = (sptr[s + 1] - sptr[s]) // 64
+        for j in range(32):
+            if srow[s * 32 + j] < 0:
+                continue
+            base = bases[s] if mode == 1 else bases[s * 32 + j]
+            for k in range(w):
+                p = sptr[s] + k * 64 + 2 * j
+                u = int(c16[p // 2])
+                assert (base + (u & 0xFFFF), base + (u >> 16)) == (ci[p], ci[p + 1])
+
+
+def test_sliced_ell_16bit_columns(lib):
+    """16-bit column offsets: one base per slice where every slice spans fewer than
+    65,536 columns; one per row where only the rows do (a slice gathering rows far
+    apart); none where a row spans more."""
+    rng = np.random.default_rng(8)
+    n = 200_000
+    # banded rows: every slice narrow
+    rows = np.repeat(np.arange(3000), 5)
+    cols = np.minimum(rows * 10 + rng.integers(0, 5000, rows.size), n - 1)
+    M = sp.csr_matrix((np.ones(rows.size), (rows, cols)), shape=(3000, n))
+    M.sum_duplicates()
+    mode, *rest = _sell16(lib, M)
+    assert mode == 1
+    _check16(mode, *rest)
+    # rows narrow, but row i starts at column 6,000 (i mod 32): every 32-row slice spans
+    # about 246,000 columns
+    rows = np.repeat(np.arange(3000), 4)
+    cols = (rows % 32) * 6000 + rng.integers(0, 60000, rows.size)
+    M = sp.csr_matrix((np.ones(rows.size), (rows, cols)), shape=(3000, 260_000))
+    M.sum_duplicates()
+    mode, *rest = _sell16(lib, M)
+    assert mode == 2
+    _check16(mode, *rest)
+    # a row spanning more than 65,535 columns: not built
+    M = sp.csr_matrix((np.ones(2), ([0, 0], [0, 70000])), shape=(40, n))
+    assert _sell16(lib, M)[0] == 0
