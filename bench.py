@@ -194,13 +194,13 @@ def make_workload(wl):
     return hh, b
 
 
-def sweep_bytes(nnz, n, w, extra_vectors, nrhs=1, vw=None, c16=False):
+def sweep_bytes(nnz, n, w, extra_vectors, nrhs=1, vw=None, c16=0):
     """Algorithmic bytes of one sweep: values (width vw, default w) + int32 columns
-    (c16: 16-bit column offsets and one int32 base per 32-row slice) + int32 row
-    pointers, one read of the gathered block, the right-hand side and the output, plus
-    `extra_vectors` other row-wise blocks (FP width w, nrhs columns; a diagonal counts
-    as one column)."""
-    cols = nnz * 2 + 4 * ((n + 31) // 32) if c16 else nnz * 4
+    (c16: 16-bit column offsets with one int32 base per 32-row slice (1) or per row
+    (2)) + int32 row pointers, one read of the gathered block, the right-hand side and
+    the output, plus `extra_vectors` other row-wise blocks (FP width w, nrhs columns; a
+    diagonal counts as one column)."""
+    cols = (nnz * 2 + 4 * (((n + 31) // 32) if c16 == 1 else n)) if c16 else nnz * 4
     return nnz * (vw or w) + cols + 4 * (n + 1) + w * n * nrhs * 3 + w * n * extra_vectors
 
 
@@ -425,7 +425,7 @@ def profiler_range(on):
         pass
 
 
-def level0_launch_bytes(hh, w, nrhs, ag, c16=False, c16_wide=False):
+def level0_launch_bytes(hh, w, nrhs, ag, c16=0, c16_wide=0):
     """Algorithmic bytes per launch of the two level-0 A kernel classes of a V-cycle.
     A_fine: FP64 (w = 8) every level-0 A sweep (see a_fine_bytes_per_launch); FP32
     single vector: the first residual r = b - A x only (FP32 values); FP32 blocks:
@@ -621,8 +621,9 @@ def run_ours(args, dist):
     hbm = hbm or HBM_FALLBACK_GBS
     ag = tuned.get((0, pname, "AG"), -1) >= 0
     C16_CODES = (1600, 1700)  # kernel codes with 16-bit column offsets
-    c16 = tuned.get((0, pname, "A"), -1) in C16_CODES
-    c16_wide = fp32 and args.wide_arith == "df" and tuned.get((0, "fp32", "A"), -1) in C16_CODES
+    df_form, _, layout16 = amge.amge_df_form(h, 0, layout=True)
+    c16 = layout16 if tuned.get((0, pname, "A"), -1) in C16_CODES else 0
+    c16_wide = layout16 if (fp32 and args.wide_arith == "df" and df_form > 0) else 0
     per_launch = level0_launch_bytes(hh, w, nrhs, ag, c16=c16, c16_wide=c16_wide)
     # the roofline kernel: the level-0 A class with the most device time
     cls = max(per_launch, key=lambda k: prof[k][1])

@@ -525,6 +525,18 @@ amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int3
  * another code. */
 amge_status amge_pcg_kernel(amge_hier* h, int32_t set, int32_t* code, float* us);
 
+/* Form of the FP32 V-cycle's double-float product on smoothing level `level`
+ * (AMGE_WIDE_DF): 0 = 32-bit columns, 1 = 16-bit column offsets, 2 = 16-bit offsets
+ * with each slice's entries prefetched into L2 (1 and 2 where the 16-bit columns are
+ * built).  Chosen at upload by timing (us[0..2]: time per launch, -1 where not
+ * measured).  set = 0: report it in *form; set = 1: take *form (1 and 2 act as 0
+ * without 16-bit columns) and report what is used.  The forms sum each row's entries
+ * in the same order (the 32-bit form with one warp per slice).  us may be NULL.
+ * layout (may be NULL): the level's 16-bit columns of A_l, 0 = not built, 1 = one base
+ * column per slice, 2 = one per row.
+ * AMGE_EINVAL for NULL h or form, a level out of range or another form. */
+amge_status amge_df_form(amge_hier* h, int32_t level, int32_t set, int32_t* form, float* us, int32_t* layout);
+
 /* Kernel choice of the block (multi-right-hand-side) products for nrhs columns (2 ..
  * 32) and one precision, per smoothing level and operator (op order as above):
  * codes[l * 6 + op] = 0 CSR (a lane group per row), 1 / 2 sliced ELL with one / two

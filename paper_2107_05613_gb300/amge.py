@@ -93,6 +93,7 @@ _SIGS = {
     "amge_wait_status": [_vp, _vp, ctypes.POINTER(_i32)],
     "amge_set_wide_arith": [_vp, _i32],
     "amge_pcg_kernel": [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)],
+    "amge_df_form": [_vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_i32)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -334,6 +335,19 @@ def amge_pcg_kernel(h: Hier, code=None):
     us = (ctypes.c_float * 2)()
     _check(_lib.amge_pcg_kernel(h.handle, 0 if code is None else 1, ctypes.byref(c), us), "amge_pcg_kernel")
     return c.value, [round(float(us[0]), 2), round(float(us[1]), 2)]
+
+
+def amge_df_form(h: Hier, level: int, form=None, layout: bool = False):
+    """The double-float product's form on a smoothing level (0 32-bit columns, 1 16-bit,
+    2 16-bit with L2 prefetch) and the upload-time timings; with `form`, set it first.
+    layout=True also returns the 16-bit column layout (0 none, 1 per-slice base, 2 per-row)."""
+    f = _i32(0 if form is None else int(form))
+    us = (ctypes.c_float * 3)()
+    lay = _i32(0)
+    _check(_lib.amge_df_form(h.handle, level, 0 if form is None else 1, ctypes.byref(f), us, ctypes.byref(lay)),
+           "amge_df_form")
+    out = (f.value, [round(float(u), 2) for u in us])
+    return out + (lay.value,) if layout else out
 
 
 def amge_wait_status(h: Hier, stream=None) -> bool:

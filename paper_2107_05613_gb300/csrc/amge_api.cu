@@ -225,9 +225,8 @@ void wide_product(amge_hier* h, int l, int epi, const SpmvArgs<float>& a, cudaSt
   const DevSell<double>& M = h->lv64[l].A;
   const bool pf = code_pf(h->lv64[l].lanes[OP_A]);
   if (h->wide_arith == AMGE_WIDE_DF && h->lv32[l].Adf) {
-    // the 16-bit columns where the FP32 product of A_l uses them
-    const int c32 = h->lv32[l].lanes[OP_A];
-    if (code_c16(c32) && launch_sell_df16(M, h->lv32[l].Adf, epi, a, s, code_pf(c32))) return;
+    const int f = h->lv32[l].df_form;  // the form timed fastest at upload
+    if (f > 0 && launch_sell_df16(M, h->lv32[l].Adf, epi, a, s, f == 2)) return;
     launch_sell_df(M, h->lv32[l].Adf, epi, a, s, wide_wps(h, l), pf);
   } else {
     launch_sell_wide(M, epi, a, s, wide_wps(h, l), pf);
@@ -1771,6 +1770,45 @@ amge_status tune_mm(amge_hier* h, int nrhs, int precision, cudaStream_t s) {
   return st;
 }
 
+// The double-float product of the FP32 V-cycle on level l in its forms (32-bit
+// columns with the FP64 operator's warps per slice; 16-bit columns without and with
+// the per-slice L2 prefetch, where built): kTuneReps launches back to back from a
+// graph, best of three; the fastest is kept (all form the same sums per row up to the
+// warp split of the 32-bit form).
+amge_status autotune_df(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  LevelDev<float>& d = h->lv32[l];
+  d.df_form = 0;
+  d.df_us[0] = d.df_us[1] = d.df_us[2] = -1.f;
+  if (!d.Adf || !d.x || !d.tmp) return AMGE_OK;
+  const DevSell<double>& M = h->lv64[l].A;
+  SpmvArgs<float> a;
+  a.x = d.x, a.y = d.tmp;
+  const bool pf = code_pf(h->lv64[l].lanes[OP_A]);
+  float best = -1.f;
+  for (int f = 0; f <= 2; f++) {
+    if (f > 0 && !M.c16) break;
+    if (f == 2 && !M.stream) break;  // the prefetch form is for streamed operators
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int r = 0; r < kTuneReps; r++) {
+      if (f == 0) launch_sell_df(M, d.Adf, EPI_STORE, a, s, wide_wps(h, l), pf);
+      else launch_sell_df16(M, d.Adf, EPI_STORE, a, s, f == 2);
+    }
+    CK(cudaStreamEndCapture(s, &g));
+    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CK(ie);
+    float ms = 0.f;
+    cudaError_t le = time_graph(ge, s, e0, e1, &ms);
+    cudaGraphExecDestroy(ge);
+    CK(le);
+    d.df_us[f] = ms * (1e3f / kTuneReps);
+    if (best < 0.f || ms < best) best = ms, d.df_form = f;
+  }
+  return AMGE_OK;
+}
+
 // The PCG product q = A_0 p (with the p.q partials) in its two forms, 32-bit columns
 // and 16-bit columns with per-slice L2 prefetch (where A_0 has them): kTuneReps
 // launches back to back from a graph, best of three; the faster is kept.  Both form
@@ -1835,6 +1873,7 @@ amge_status autotune(amge_hier* h, cudaStream_t s) {
     st = autotune_level<double>(h, l, ts, e0, e1, fl);
     if (st == AMGE_OK) st = autotune_level<float>(h, l, ts, e0, e1, fl);
   }
+  for (int l = 0; l + 1 < h->L && st == AMGE_OK; l++) st = autotune_df(h, l, ts, e0, e1);
   if (st == AMGE_OK) st = autotune_pcg_spmv(h, ts, e0, e1);
   cudaStreamSynchronize(ts);
   cudaStreamDestroy(ts);
@@ -2427,6 +2466,34 @@ amge_status amge_autotune_times(const amge_hier* h, float* us) {
         us[k] = h->lv64[l].lanes[op] < 0 ? -1.f : h->lv64[l].tune_us[op][c];
         us[k + 6 * kNumTuneCodes] = h->lv32[l].lanes[op] < 0 ? -1.f : h->lv32[l].tune_us[op][c];
       }
+  return AMGE_OK;
+}
+
+amge_status amge_df_form(amge_hier* h, int32_t level, int32_t set, int32_t* form, float* us, int32_t* layout) {
+  if (!h || !form) {
+    set_error("NULL argument");
+    return AMGE_EINVAL;
+  }
+  if (level < 0 || level + 1 >= h->L) {
+    set_error("level must index a smoothing level");
+    return AMGE_EINVAL;
+  }
+  LevelDev<float>& d = h->lv32[level];
+  if (set) {
+    if (*form < 0 || *form > 2) {
+      set_error("double-float form must be 0, 1 or 2");
+      return AMGE_EINVAL;
+    }
+    d.df_form = h->lv64[level].A.c16 ? *form : 0;
+    for (GraphPcg& G : h->gpcg) {  // the captured V-cycle names the old kernel
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      if (G.g) cudaGraphDestroy(G.g);
+      G = GraphPcg{};
+    }
+  }
+  *form = d.df_form;
+  if (us) us[0] = d.df_us[0], us[1] = d.df_us[1], us[2] = d.df_us[2];
+  if (layout) *layout = !h->lv64[level].A.c16 ? 0 : h->lv64[level].A.c16_rb ? 2 : 1;
   return AMGE_OK;
 }
 

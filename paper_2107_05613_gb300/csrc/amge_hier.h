@@ -47,6 +47,11 @@ struct LevelDev {
   // entry pair of the FP64 sliced-ELL copy (launch_sell_df)
   float4* Adf = nullptr;
   float2* cAdf = nullptr;  // the same for the CSR copy (block V-cycles)
+  // form of the double-float product (timed at upload): 0 = 32-bit columns (warps per
+  // slice of the FP64 A_l's code), 1 = 16-bit columns, 2 = 16-bit columns with the
+  // per-slice L2 prefetch; us: time per launch of each, -1 where not measured
+  int df_form = 0;
+  float df_us[3] = {-1.f, -1.f, -1.f};
   V* minv = nullptr;
   V* mauxinv = nullptr;
   V *x = nullptr, *r = nullptr, *y = nullptr, *tmp = nullptr;

@@ -292,3 +292,30 @@ def test_pcg_product_forms_equal(amge, name):
         amge.amge_pcg_kernel(h, saved)
     print(f"{name}: PCG product {us[0]} us (32-bit columns) / {us[1]} us (16-bit + prefetch), kept {saved}")
     assert torch.equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+
+
+@pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
+def test_double_float_forms_equal(amge, name):
+    """The FP32 V-cycle's double-float product with 32-bit columns (one warp per slice)
+    and with 16-bit column offsets, without and with the L2 prefetch, form the same
+    sums: identical V-cycles and FP32-V-cycle solves."""
+    h, o, b = workload(amge, name)
+    bd = dev(b)
+    saved, us = amge.amge_df_form(h, 0)
+    rep = amge.amge_autotune_report(h)
+    res = []
+    try:
+        amge.amge_set_kernel(h, 0, "fp64", "A", 0)     # the 32-bit form's warps per slice: one
+        for form in (0, 1, 2):
+            got, _ = amge.amge_df_form(h, 0, form)
+            z, x = torch.empty_like(bd), torch.empty_like(bd)
+            amge.amge_vcycle(h, bd, z, 1, amge.AMGE_FP32_VCYCLE)
+            st, info = amge.amge_pcg_solve(h, bd, x, rtol=1e-8, precision=amge.AMGE_FP32_VCYCLE)
+            assert st == amge.AMGE_OK
+            res.append((got, z, x, info[0]["iters"]))
+    finally:
+        amge.amge_df_form(h, 0, saved)
+        amge.amge_set_kernel(h, 0, "fp64", "A", rep[(0, "fp64", "A")])
+    print(f"{name}: double-float level-0 product {us} us (32-bit / 16-bit / 16-bit + prefetch), kept {saved}")
+    for got, z, x, it in res[1:]:
+        assert torch.equal(z, res[0][1]) and torch.equal(x, res[0][2]) and it == res[0][3], got

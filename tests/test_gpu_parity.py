@@ -165,10 +165,9 @@ def test_fused_aux_correction_equals_separate_products(amge, prec, ag):
 @pytest.mark.parametrize("code", [3000, 1600])
 def test_bulk_staged_equals_one_warp_kernel(amge, form, n, L, prec, code):
     """The bulk-staged product (code 3000: each warp's slices copied into shared memory
-    two ahead) and the 16-bit-column product (1600; in the FP32 V-cycle also its
-    double-float residuals) form every row's sum in the order of the one-warp
-    sliced-ELL kernel (code 0): products, V-cycles and graph-driven PCG solves are
-    identical, and no staged copy's wait runs out."""
+    two ahead) and the 16-bit-column product (1600) form every row's sum in the order
+    of the one-warp sliced-ELL kernel (code 0): products, V-cycles and graph-driven
+    PCG solves are identical, and no staged copy's wait runs out."""
     from paper_2107_05613_gb300.inputs import rhs_vector
 
     h = upload(amge, form, n, L)
