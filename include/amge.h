@@ -515,6 +515,34 @@ amge_status amge_autotune_times(const amge_hier* h, float* us);
  * operator that is not stored (-1 in the report) or another lane count. */
 amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int32_t op, int32_t lanes);
 
+/* Coarsest-level solver of single-vector V-cycles:
+ *   AMGE_COARSE_DENSE  the default: a product with the explicit FP64 inverse of A_L
+ *                      (double-float pairs in the FP32 V-cycle)
+ *   AMGE_COARSE_AUX    the paper's (Sections 4.2, 5.1): `iters` PCG iterations (five in
+ *                      the paper) from zero on A_L, preconditioned by the additive
+ *                      auxiliary-space preconditioner of eq. 4.2,
+ *                        B^{-1} = M^{-1} + Pihat S_v^+ Pihat^T + D B_D D^T,
+ *                      M the l1-Jacobi diagonal, S_v = Pihat^T A_L Pihat; H(curl) (AMS):
+ *                      D = D_0 at level L, B_D = S_g^+ with S_g = D^T A_L D; H(div) (ADS):
+ *                      D = D_1 at level L and B_D the same construction for the curl-curl
+ *                      matrix A_c = D^T A_L D with the edge interpolation pihat_inner (no
+ *                      gradient term: A_c annihilates gradients).  S^+ is a symmetric
+ *                      generalized inverse (pivoted Cholesky; the auxiliary matrices of
+ *                      natural-boundary problems are singular), computed on the host
+ *                      here, in FP64 (the paper solves these problems with BoomerAMG).
+ *                      Runs in FP64 (the FP32 V-cycle widens its input and rounds the
+ *                      result).  Blocks of right-hand sides keep the dense solve.
+ * pihat: the interpolation of vector H1 into the problem space at the coarsest level
+ * (n_L rows, 3 columns per vertex: column 3 v + c); D: the exterior derivative into the
+ * problem space at the coarsest level; pihat_inner: (H(div) only) the interpolation into
+ * the edge space.  Host CSR, read during the call.  Synchronises `stream`; captured PCG
+ * graphs are rebuilt on the next solve.  AMGE_EINVAL for an unknown solver, iters
+ * outside [1, 64], missing or mis-sized matrices, or a workspace view; AMGE_ENOMEM,
+ * AMGE_ECUDA. */
+enum { AMGE_COARSE_DENSE = 0, AMGE_COARSE_AUX = 1 };
+amge_status amge_set_coarse_solver(amge_hier* h, int32_t solver, int32_t iters, const amge_csr* pihat,
+                                   const amge_csr* D, const amge_csr* pihat_inner, void* stream);
+
 /* The PCG product q = A_0 p (FP64, with the p.q partials): code 0 = 32-bit columns,
  * 1700 = 16-bit column offsets with each slice's entries prefetched into L2 (where
  * A_0's slices span fewer than 65,536 columns).  Chosen at upload by timing both

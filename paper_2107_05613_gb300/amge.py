@@ -28,6 +28,7 @@ PROF_CLASSES = ["A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "pcg_spmv"
                 "A_wide", "gs"]
 AMGE_SMOOTHER_L1_JACOBI, AMGE_SMOOTHER_SYM_GS = 0, 1
 AMGE_WIDE_FP64, AMGE_WIDE_DF = 0, 1
+AMGE_COARSE_DENSE, AMGE_COARSE_AUX = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENONFINITE",
                 6: "EAGAIN", 7: "ETIMEOUT", 8: "ECANCELED"}
 
@@ -93,6 +94,8 @@ _SIGS = {
     "amge_wait_status": [_vp, _vp, ctypes.POINTER(_i32)],
     "amge_set_wide_arith": [_vp, _i32],
     "amge_pcg_kernel": [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)],
+    "amge_set_coarse_solver": [_vp, _i32, _i32, ctypes.POINTER(amge_csr), ctypes.POINTER(amge_csr),
+                               ctypes.POINTER(amge_csr), _vp],
     "amge_df_form": [_vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_i32)],
 }
 for _name, _args in _SIGS.items():
@@ -348,6 +351,29 @@ def amge_df_form(h: Hier, level: int, form=None, layout: bool = False):
            "amge_df_form")
     out = (f.value, [round(float(u), 2) for u in us])
     return out + (lay.value,) if layout else out
+
+
+def amge_set_coarse_solver(h: Hier, solver: int, iters: int = 5, pihat=None, D=None, pihat_inner=None,
+                           stream=None):
+    """Coarsest solver: AMGE_COARSE_DENSE or AMGE_COARSE_AUX (iters PCG iterations with
+    the auxiliary-space preconditioner of eq. 4.2; pihat, D, pihat_inner: CSR matrices
+    of the coarsest level, see amge_coarse_aux_inputs)."""
+    keep = []
+    ptr = lambda m: None if m is None else ctypes.pointer(_csr_struct(m, keep))
+    _check(_lib.amge_set_coarse_solver(h.handle, int(solver), int(iters), ptr(pihat), ptr(D), ptr(pihat_inner),
+                                       _stream(stream)), "amge_set_coarse_solver")
+
+
+def amge_coarse_aux_inputs(hierarchy):
+    """(pihat, D, pihat_inner) of the coarsest level of a generated hierarchy built with
+    all spaces: the vector-H1 interpolation into the problem space, the exterior
+    derivative into it, and (H(div)) the interpolation into the edge space."""
+    L = hierarchy.num_levels
+    if hierarchy.pihat is None:
+        raise ValueError("the hierarchy was built without all spaces")
+    if hierarchy.form == "hcurl":
+        return hierarchy.pihat[L - 1][1], hierarchy.D_all[L - 1][0], None
+    return hierarchy.pihat[L - 1][2], hierarchy.D_all[L - 1][1], hierarchy.pihat[L - 1][1]
 
 
 def amge_wait_status(h: Hier, stream=None) -> bool:

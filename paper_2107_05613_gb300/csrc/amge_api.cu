@@ -350,9 +350,74 @@ void vcycle_level_gs(amge_hier* h, int l, const double* b, double* z, cudaStream
 // One V-cycle at level l: z = B_l^{-1} b (Algorithm 4.1, x0 = 0).  x_ready: the
 // level's first point sweep from zero, x = m^-1 b, was already written into x by the
 // restriction that produced b.
+// ---------------------------------------------------------------- auxiliary-space coarsest solver
+// Additive preconditioner of eq. 4.2 on the coarsest level: z = M^-1 r + Pihat Gv
+// Pihat^T r + D B_D D^T r, with B_D = Gd (AMS) or M_c^-1 + Pi1 Gc Pi1^T (ADS, on the
+// curl-curl matrix D^T A D); G* the generalized inverses of the auxiliary matrices.
+void coarse_aux_precondition(amge_hier* h, const double* r, double* z, cudaStream_t s) {
+  CoarseAux& c = *h->aux;
+  auto csr = [&](const DevCsr<double>& M, int epi, const double* x, double* y) {
+    SpmvArgs<double> a;
+    a.x = x, a.y = y;
+    launch_csrv<double>(M, 4, epi, a, s);
+  };
+  launch_mul<double>(c.A.nr, c.minv, r, z, s);
+  csr(c.PvT, EPI_STORE, r, c.u);
+  launch_coarse_inv<double, double>(c.nv, c.Gv, c.u, c.tmp, c.w, s);
+  csr(c.Pv, EPI_ADD, c.w, z);
+  csr(c.DT, EPI_STORE, r, c.t);
+  if (!c.ads) {
+    launch_coarse_inv<double, double>(c.nd, c.Gd, c.t, c.tmp, c.y, s);
+  } else {
+    launch_mul<double>(c.nd, c.mcinv, c.t, c.y, s);
+    csr(c.Pi1T, EPI_STORE, c.t, c.u2);
+    launch_coarse_inv<double, double>(c.nv1, c.Gc, c.u2, c.tmp, c.w2, s);
+    csr(c.Pi1, EPI_ADD, c.w2, c.y);
+  }
+  csr(c.D, EPI_ADD, c.y, z);
+}
+int coarse_aux_precondition_launches(const CoarseAux& c) { return c.ads ? 10 : 7; }
+
+// The paper's coarsest solver (Sections 4.2, 5.1): `iters` PCG iterations from x = 0
+// with the preconditioner above; scalars rho_k at sc[2 k], p.q at sc[2 k + 1].
+void coarse_aux_solve(amge_hier* h, const double* b, double* out, cudaStream_t s) {
+  CoarseAux& c = *h->aux;
+  const int n = c.A.nr;
+  const int nb = coarse_aux_precondition_launches(c);
+  // kernel launches (the memset and copies are not kernels)
+  Prof pr(h, AMGE_PROF_COARSE, s, nb + 2 + c.iters * 4 + (c.iters - 1) * (nb + 3));
+  cudaMemsetAsync(c.x, 0, (size_t)n * sizeof(double), s);
+  cudaMemcpyAsync(c.r, b, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  coarse_aux_precondition(h, c.r, c.z, s);
+  cudaMemcpyAsync(c.p, c.z, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  launch_dot(n, c.r, c.z, c.red.sc + 0, c.red, s);
+  for (int k = 0; k < c.iters; k++) {
+    SpmvArgs<double> a;
+    a.x = c.p, a.y = c.q;
+    launch_csrv<double>(c.A, 8, EPI_STORE, a, s);
+    launch_dot(n, c.p, c.q, c.red.sc + 2 * k + 1, c.red, s);
+    launch_aux_xr(n, c.x, c.r, c.p, c.q, c.red.sc, 2 * k, 2 * k + 1, s);
+    if (k + 1 == c.iters) break;
+    coarse_aux_precondition(h, c.r, c.z, s);
+    launch_dot(n, c.r, c.z, c.red.sc + 2 * (k + 1), c.red, s);
+    launch_aux_p(n, c.p, c.z, c.red.sc, 2 * (k + 1), 2 * k, s);
+  }
+  cudaMemcpyAsync(out, c.x, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
 // The FP32 V-cycle's coarsest solve: double-float (one launch) or FP64 with the
 // input widened first (two), per amge_set_wide_arith.
 void coarse_solve_f32(amge_hier* h, const float* b, float* z, cudaStream_t s) {
+  if (h->aux) {  // the auxiliary-space solver runs in FP64
+    {
+      Prof p(h, AMGE_PROF_COARSE, s);
+      launch_cast<float, double>(h->nC, b, h->aux->bd, s);
+    }
+    coarse_aux_solve(h, h->aux->bd, h->aux->zd, s);
+    Prof p(h, AMGE_PROF_COARSE, s);
+    launch_cast<double, float>(h->nC, h->aux->zd, z, s);
+    return;
+  }
   if (h->wide_arith == AMGE_WIDE_DF && h->Ainv_df) {
     Prof p(h, AMGE_PROF_COARSE, s);
     launch_coarse_inv_df(h->nC, h->Ainv_df, b, z, s);
@@ -368,6 +433,8 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
   if (l == h->L - 1) {
     if constexpr (std::is_same<V, float>::value) {
       coarse_solve_f32(h, b, z, s);
+    } else if (h->aux) {
+      coarse_aux_solve(h, b, z, s);
     } else {
       Prof p(h, AMGE_PROF_COARSE, s);
       launch_coarse_inv<V, V>(h->nC, h->Ainv, b, h->ct, z, s);
@@ -498,6 +565,10 @@ void vcycle_fp64_iface(amge_hier* h, const double* r, double* z, int precision, 
                        bool x0_ready = false, bool z32_only = false) {
   if (precision == AMGE_FP64) {
     if (h->L == 1) {
+      if (h->aux) {
+        coarse_aux_solve(h, r, z, s);
+        return;
+      }
       Prof p(h, AMGE_PROF_COARSE, s);
       launch_coarse_inv<double, double>(h->nC, h->Ainv, r, h->ct, z, s);
       return;
@@ -2013,6 +2084,10 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
           h->Ainv = upload<double>(h, keepd.back().data(), (size_t)n[l] * n[l], s);
           h->Ainv_df = dalloc<float2>(h, (size_t)n[l] * n[l]);
           launch_df_split_entries((int64_t)n[l] * n[l], h->Ainv, h->Ainv_df, s);
+          h->cAL.nr = A.nr, h->cAL.nc = A.nc, h->cAL.nnz = A.nnz();
+          h->cAL.rp = upload<int>(h, A.rp.data(), A.rp.size(), s);
+          h->cAL.ci = upload<int>(h, A.ci.data(), A.ci.size(), s);
+          h->cAL.val = upload<double>(h, A.v.data(), A.v.size(), s);
         }
         keepd.push_back(std::move(LiT));
         h->LinvT = upload<double>(h, keepd.back().data(), (size_t)n[l] * n[l], s);
@@ -2469,6 +2544,118 @@ amge_status amge_autotune_times(const amge_hier* h, float* us) {
   return AMGE_OK;
 }
 
+amge_status amge_set_coarse_solver(amge_hier* h, int32_t solver, int32_t iters, const amge_csr* pihat,
+                                   const amge_csr* D, const amge_csr* pihat_inner, void* stream) {
+  if (!h) {
+    set_error("NULL hierarchy");
+    return AMGE_EINVAL;
+  }
+  if (h->base) {
+    set_error("a workspace view uses its hierarchy's coarsest solver");
+    return AMGE_EINVAL;
+  }
+  auto drop = [&]() {
+    for (GraphPcg& G : h->gpcg) {  // the captured V-cycle changes
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      if (G.g) cudaGraphDestroy(G.g);
+      G = GraphPcg{};
+    }
+  };
+  if (solver == AMGE_COARSE_DENSE) {
+    h->aux = nullptr;  // its device data stays allocated with the hierarchy
+    drop();
+    return AMGE_OK;
+  }
+  if (solver != AMGE_COARSE_AUX) {
+    set_error("solver must be AMGE_COARSE_DENSE or AMGE_COARSE_AUX");
+    return AMGE_EINVAL;
+  }
+  const bool ads = h->form == AMGE_HDIV;
+  if (iters < 1 || iters > 64 || !pihat || !D || (ads != (pihat_inner != nullptr)) || !h->cAL.rp) {
+    set_error("iters in [1, 64], pihat and D required, pihat_inner exactly for H(div), a dense coarsest level");
+    return AMGE_EINVAL;
+  }
+  const int n = h->nC;
+  std::string err;
+  if (!check_csr(*pihat, n, pihat->n_cols, "pihat", err) || pihat->n_cols % 3 != 0 ||
+      !check_csr(*D, n, D->n_cols, "D", err) ||
+      (ads && (!check_csr(*pihat_inner, D->n_cols, pihat_inner->n_cols, "pihat_inner", err) ||
+               pihat_inner->n_cols % 3 != 0))) {
+    set_error(err.empty() ? std::string("vector-H1 interpolations need 3 columns per vertex") : err);
+    return AMGE_EINVAL;
+  }
+  cudaStream_t s = as_stream(stream);
+  // the coarsest matrix back on the host
+  HostCsr A;
+  A.nr = A.nc = n;
+  A.rp.resize((size_t)n + 1);
+  A.ci.resize((size_t)h->cAL.nnz);
+  A.v.resize((size_t)h->cAL.nnz);
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpy(A.rp.data(), h->cAL.rp, A.rp.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(A.ci.data(), h->cAL.ci, A.ci.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(A.v.data(), h->cAL.val, A.v.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  const HostCsr Pv = to_host(*pihat), Dm = to_host(*D);
+  const HostCsr PvT = transpose(Pv), DT = transpose(Dm);
+  CoarseAux c;
+  c.iters = iters, c.ads = ads;
+  c.nv = Pv.nc, c.nd = Dm.nc;
+  // the auxiliary matrices (exact products) and their generalized inverses
+  std::vector<double> Gv, Gd, Gc, mc;
+  c.rank_v = generalized_inverse(c.nv, dense_product(PvT, sparse_product(A, Pv, false)), Gv, 1e-12);
+  HostCsr Pi1, Pi1T;
+  if (!ads) {
+    c.rank_d = generalized_inverse(c.nd, dense_product(DT, sparse_product(A, Dm, false)), Gd, 1e-12);
+  } else {
+    const HostCsr Ac = sparse_product(DT, sparse_product(A, Dm, false), false);
+    mc = l1_row_sums(Ac);
+    Pi1 = to_host(*pihat_inner), Pi1T = transpose(Pi1);
+    c.nv1 = Pi1.nc;
+    c.rank_d = generalized_inverse(c.nv1, dense_product(Pi1T, sparse_product(Ac, Pi1, false)), Gc, 1e-12);
+  }
+  std::vector<double> minv = l1_row_sums(A), mcinv(mc.size());
+  for (double& v : minv) v = 1.0 / v;
+  for (size_t i = 0; i < mc.size(); i++) mcinv[i] = mc[i] > 0 ? 1.0 / mc[i] : 0.0;
+  try {
+    auto up = [&](const HostCsr& M, DevCsr<double>& d) {
+      d.nr = M.nr, d.nc = M.nc, d.nnz = M.nnz();
+      d.rp = upload<int>(h, M.rp.data(), M.rp.size(), s);
+      d.ci = upload<int>(h, M.ci.data(), M.ci.size(), s);
+      d.val = upload<double>(h, M.v.data(), M.v.size(), s);
+    };
+    up(A, c.A);
+    up(Pv, c.Pv);
+    up(PvT, c.PvT);
+    up(Dm, c.D);
+    up(DT, c.DT);
+    c.Gv = upload<double>(h, Gv.data(), Gv.size(), s);
+    if (!ads) {
+      c.Gd = upload<double>(h, Gd.data(), Gd.size(), s);
+    } else {
+      up(Pi1, c.Pi1);
+      up(Pi1T, c.Pi1T);
+      c.Gc = upload<double>(h, Gc.data(), Gc.size(), s);
+      c.mcinv = upload<double>(h, mcinv.data(), mcinv.size(), s);
+    }
+    c.minv = upload<double>(h, minv.data(), minv.size(), s);
+    for (double** v : {&c.x, &c.r, &c.z, &c.p, &c.q, &c.bd, &c.zd}) *v = dalloc<double>(h, n);
+    c.u = dalloc<double>(h, c.nv), c.w = dalloc<double>(h, c.nv);
+    c.t = dalloc<double>(h, c.nd), c.y = dalloc<double>(h, c.nd);
+    if (ads) c.u2 = dalloc<double>(h, c.nv1), c.w2 = dalloc<double>(h, c.nv1);
+    c.tmp = dalloc<double>(h, std::max({c.nv, c.nd, c.nv1, 1}));
+    c.red.partials = dalloc<double>(h, (size_t)kRedSlots * kMaxRedBlocks);
+    c.red.sc = dalloc<double>(h, SC_COUNT + 2 * (size_t)iters + 4);
+  } catch (const UploadError& e) {
+    return e.st;
+  }
+  CK(cudaStreamSynchronize(s));  // the host arrays above must outlive the copies
+  if (!h->aux_store) h->aux_store = new CoarseAux;
+  *h->aux_store = c;
+  h->aux = h->aux_store;
+  drop();
+  return AMGE_OK;
+}
+
 amge_status amge_df_form(amge_hier* h, int32_t level, int32_t set, int32_t* form, float* us, int32_t* layout) {
   if (!h || !form) {
     set_error("NULL argument");
@@ -2818,6 +3005,7 @@ void amge_hier_free(amge_hier* h) {
   }
   drop_graphs_mm(h);
   if (h->upd) free_update_plan(h->upd);
+  delete h->aux_store;
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->pinned_state) cudaFreeHost(h->pinned_state);
   if (h->pinned_state_mm) cudaFreeHost(h->pinned_state_mm);

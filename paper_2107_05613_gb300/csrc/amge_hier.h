@@ -81,6 +81,25 @@ struct GraphPcg {
   int64_t body[AMGE_PROF_CLASSES] = {};  // kernel launches of one body replay, per class
 };
 
+// The auxiliary-space coarsest solver (amge_set_coarse_solver, Section 4.2 eq. 4.2):
+// operators of the coarsest level, the generalized inverses of its auxiliary
+// matrices, work vectors and a reduction scratch of its own (the outer PCG's
+// scalars stay live across the V-cycle).
+struct CoarseAux {
+  int iters = 5;
+  int nv = 0, nd = 0, nv1 = 0;  // sizes: vector-H1 aux, D's columns, inner vector-H1 (ADS)
+  bool ads = false;
+  DevCsr<double> A, Pv, PvT, D, DT, Pi1, Pi1T;
+  double *Gv = nullptr, *Gd = nullptr, *Gc = nullptr;  // generalized inverses (row-major)
+  double *minv = nullptr, *mcinv = nullptr;
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *u = nullptr, *w = nullptr, *t = nullptr, *y = nullptr, *u2 = nullptr, *w2 = nullptr;
+  double *bd = nullptr, *zd = nullptr;  // FP32 V-cycle: widened input, FP64 output
+  double* tmp = nullptr;                // dense products' scratch
+  RedScratch red;
+  int rank_v = 0, rank_d = 0;           // ranks found for the generalized inverses
+};
+
 struct amge_hier {
   int form = 0, L = 0, nu_pre = 1, nu_post = 1;
   // smoother: AMGE_SMOOTHER_L1_JACOBI, or AMGE_SMOOTHER_SYM_GS on the gs_levels finest
@@ -98,6 +117,9 @@ struct amge_hier {
   double *Linv = nullptr, *LinvT = nullptr, *ct = nullptr;
   double* Ainv = nullptr;  // explicit coarsest inverse (single-vector V-cycles)
   float2* Ainv_df = nullptr;  // the same as double-float pairs (FP32 V-cycles, AMGE_WIDE_DF)
+  DevCsr<double> cAL;         // the coarsest matrix (CSR, FP64), for the auxiliary-space solver's setup
+  CoarseAux* aux = nullptr;   // auxiliary-space coarsest solver, when selected (single vectors)
+  CoarseAux* aux_store = nullptr;  // its data (owned; kept when the dense solver is selected again)
   double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
   double *stage_b = nullptr, *stage_x = nullptr;
   float *s32_in = nullptr, *s32_out = nullptr;

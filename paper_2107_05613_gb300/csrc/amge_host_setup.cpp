@@ -84,10 +84,10 @@ std::vector<double> l1_row_sums(const HostCsr& A) {
 // bound, so dropping it perturbs (A B) y by no more than rounding does.  On the H(curl)
 // 64^3 hierarchy the genuine entries of A_0 G_0 sit at 4e-9 of their term magnitudes
 // and above, the residue at 1.2e-16 and below; the residue is 19% of the entries.
-HostCsr sparse_product(const HostCsr& A, const HostCsr& B) {
+HostCsr sparse_product(const HostCsr& A, const HostCsr& B, bool drop_residue) {
   HostCsr C;
   C.nr = A.nr, C.nc = B.nc;
-  constexpr double kResidue = 64.0 * 2.220446049250313e-16;
+  const double kResidue = drop_residue ? 64.0 * 2.220446049250313e-16 : -1.0;
   std::vector<std::vector<std::pair<int, double>>> rows(A.nr);
 #pragma omp parallel
   {
@@ -109,7 +109,7 @@ HostCsr sparse_product(const HostCsr& A, const HostCsr& B) {
       }
       std::sort(touched.begin(), touched.end());
       for (int j : touched) {
-        if (std::fabs(acc[j]) > kResidue * mag[j]) rows[i].push_back({j, acc[j]});
+        if (kResidue < 0.0 || std::fabs(acc[j]) > kResidue * mag[j]) rows[i].push_back({j, acc[j]});
         acc[j] = 0.0;
         mag[j] = 0.0;
         seen[j] = 0;
@@ -415,6 +415,92 @@ HostCsr symbolic_product(const HostCsr& A, const HostCsr& B) {
   C.v.assign(C.rp[A.nr], 1.0);
   for (int i = 0; i < A.nr; i++) std::copy(rows[i].begin(), rows[i].end(), C.ci.begin() + C.rp[i]);
   return C;
+}
+
+}  // namespace amge
+
+namespace amge {
+
+// S = Q (A W) as a dense row-major m x m matrix, from Q (m x n, CSR) and AW (n x m, CSR):
+// row i of S sums row i of Q's entries times AW's rows, in stored order.
+std::vector<double> dense_product(const HostCsr& Q, const HostCsr& AW) {
+  const int m = Q.nr;
+  std::vector<double> S((size_t)m * AW.nc, 0.0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int i = 0; i < m; i++) {
+    double* row = &S[(size_t)i * AW.nc];
+    for (int p = Q.rp[i]; p < Q.rp[i + 1]; p++) {
+      const int k = Q.ci[p];
+      const double q = Q.v[p];
+      for (int t = AW.rp[k]; t < AW.rp[k + 1]; t++) row[AW.ci[t]] += q * AW.v[t];
+    }
+  }
+  return S;
+}
+
+// A symmetric generalized inverse of the symmetric positive semi-definite S (n x n,
+// row-major): Cholesky with diagonal pivoting stops when the largest remaining pivot
+// is below tol times the largest diagonal entry; with the r pivoted rows and columns
+// as the leading block S11 (nonsingular, of S's rank), G = P^T [S11^{-1} 0; 0 0] P
+// satisfies S G S = S.  For t in the range of S every such G gives the same S-range
+// part of G t, which is all the auxiliary-space preconditioner uses (its kernels are
+// mapped to zero).  Returns the rank.
+int generalized_inverse(int n, const std::vector<double>& S, std::vector<double>& G, double tol) {
+  // W holds the Schur complements and the factor in the original indexing, kept
+  // symmetric; perm[0 .. k) are the rows pivoted so far
+  std::vector<double> W(S);
+  std::vector<int> perm(n);
+  for (int i = 0; i < n; i++) perm[i] = i;
+  auto w = [&](int a, int b) -> double& { return W[(size_t)a * n + b]; };
+  double dmax = 0.0;
+  for (int i = 0; i < n; i++) dmax = std::max(dmax, S[(size_t)i * n + i]);
+  int r = 0;
+  for (int k = 0; k < n; k++) {
+    int j = k;
+    for (int i = k + 1; i < n; i++)
+      if (w(perm[i], perm[i]) > w(perm[j], perm[j])) j = i;
+    if (!(w(perm[j], perm[j]) > tol * dmax)) break;
+    std::swap(perm[k], perm[j]);
+    const int pk = perm[k];
+    const double d = std::sqrt(w(pk, pk));
+    w(pk, pk) = d;
+    for (int i = k + 1; i < n; i++) w(perm[i], pk) /= d, w(pk, perm[i]) = w(perm[i], pk);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = k + 1; i < n; i++) {
+      const int pi = perm[i];
+      const double li = w(pi, pk);
+      for (int c = k + 1; c <= i; c++) {
+        const int pc = perm[c];
+        const double v = w(pi, pc) - li * w(pc, pk);
+        w(pi, pc) = v;
+        w(pc, pi) = v;
+      }
+    }
+    r = k + 1;
+  }
+  // L11 (r x r, lower, in pivot order): L(i, c) = w(perm[i], perm[c]); its inverse by
+  // forward substitution, column by column
+  std::vector<double> Li((size_t)r * r, 0.0);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int c = 0; c < r; c++) {
+    Li[(size_t)c * r + c] = 1.0 / w(perm[c], perm[c]);
+    for (int i = c + 1; i < r; i++) {
+      double s = 0.0;
+      for (int k = c; k < i; k++) s += w(perm[i], perm[k]) * Li[(size_t)k * r + c];
+      Li[(size_t)i * r + c] = -s / w(perm[i], perm[i]);
+    }
+  }
+  // S11^{-1} = L11^{-T} L11^{-1}, scattered back through the permutation
+  G.assign((size_t)n * n, 0.0);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int a = 0; a < r; a++)
+    for (int b = 0; b <= a; b++) {
+      double s = 0.0;
+      for (int k = a; k < r; k++) s += Li[(size_t)k * r + a] * Li[(size_t)k * r + b];
+      G[(size_t)perm[a] * n + perm[b]] = s;
+      G[(size_t)perm[b] * n + perm[a]] = s;
+    }
+  return r;
 }
 
 }  // namespace amge

@@ -214,6 +214,10 @@ void launch_df_split(int64_t npairs, const double* v, float4* out, cudaStream_t 
 // Coarsest solve of the FP32 V-cycle in double-float arithmetic: z = A^{-1} b with
 // the inverse as {hi, lo} float pairs (launch_df_split_entries of the FP64 inverse).
 void launch_coarse_inv_df(int n, const float2* Ainv_df, const float* b, float* z, cudaStream_t s);
+// The auxiliary-space coarsest solver's PCG updates (k_aux_xr, k_aux_p).
+void launch_aux_xr(int n, double* x, double* r, const double* p, const double* q, const double* sc, int ia, int ib,
+                   cudaStream_t s);
+void launch_aux_p(int n, double* p, const double* z, const double* sc, int ia, int ib, cudaStream_t s);
 void launch_df_split_entries(int64_t n, const double* v, float2* out, cudaStream_t s);
 
 // Gauss-Seidel update of one colour's rows: slices [s0, s1) of a colour-grouped
@@ -458,8 +462,13 @@ bool check_csr(const amge_csr& c, int nr, int nc, const char* what, std::string&
 HostCsr to_host(const amge_csr& c);
 HostCsr transpose(const HostCsr& A);
 std::vector<double> l1_row_sums(const HostCsr& A);
-// C = A B (FP64; entries that cancel to exactly zero are dropped).
-HostCsr sparse_product(const HostCsr& A, const HostCsr& B);
+// C = A B (FP64; with drop_residue, entries at the cancellation-residue level are dropped).
+HostCsr sparse_product(const HostCsr& A, const HostCsr& B, bool drop_residue = true);
+// Dense Q (A W) (m x AW.nc, row-major).
+std::vector<double> dense_product(const HostCsr& Q, const HostCsr& AW);
+// Symmetric generalized inverse of a positive semi-definite S by pivoted Cholesky
+// (pivots below tol * max diag are zero); returns the rank.
+int generalized_inverse(int n, const std::vector<double>& S, std::vector<double>& G, double tol);
 std::vector<double> aux_l1_row_sums(const HostCsr& A, const HostCsr& G, const HostCsr& GT);
 // Dense Cholesky of the coarsest matrix; returns false if not SPD.  Linv = L^{-1}
 // (row-major, lower triangle), LinvT its transpose (row-major, upper triangle).

@@ -1005,6 +1005,29 @@ __global__ void __launch_bounds__(kTriBlock, 16) k_densemv_df(int n, const float
   if (threadIdx.x == 0) y[row] = __fadd_rn(t.h, t.l);
 }
 
+// The auxiliary-space coarsest solver's PCG updates (scalars on the device, in the
+// solver's own scratch): x += alpha p and r -= alpha q with alpha = sc[ia] / sc[ib];
+// p = z + beta p with beta = sc[ia] / sc[ib].  A zero denominator (a zero right-hand
+// side) gives a zero step.
+__global__ void __launch_bounds__(kBlock) k_aux_xr(int n, double* __restrict__ x, double* __restrict__ r,
+                                                   const double* __restrict__ p, const double* __restrict__ q,
+                                                   const double* __restrict__ sc, int ia, int ib) {
+  pdl_begin();
+  const double den = sc[ib];
+  const double alpha = den != 0.0 ? sc[ia] / den : 0.0;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+    x[i] = fma(alpha, p[i], x[i]);
+    r[i] = fma(-alpha, q[i], r[i]);
+  }
+}
+__global__ void __launch_bounds__(kBlock) k_aux_p(int n, double* __restrict__ p, const double* __restrict__ z,
+                                                  const double* __restrict__ sc, int ia, int ib) {
+  pdl_begin();
+  const double den = sc[ib];
+  const double beta = den != 0.0 ? sc[ia] / den : 0.0;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) p[i] = fma(beta, p[i], z[i]);
+}
+
 // Double-float copy {hi, lo} of n doubles.
 __global__ void k_df_split_entries(int64_t n, const double* __restrict__ v, float2* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1727,6 +1750,14 @@ void launch_coarse_inv(int n, const double* Ainv, const Tin* b, double* t, Tout*
     launch_k(k_densemv<double, Tout>, n, kTriBlock, s, n, Ainv, (const double*)t, z);
   }
 }
+void launch_aux_xr(int n, double* x, double* r, const double* p, const double* q, const double* sc, int ia, int ib,
+                   cudaStream_t s) {
+  if (n > 0) launch_k(k_aux_xr, std::min((n + kBlock - 1) / kBlock, 152 * 8), kBlock, s, n, x, r, p, q, sc, ia, ib);
+}
+void launch_aux_p(int n, double* p, const double* z, const double* sc, int ia, int ib, cudaStream_t s) {
+  if (n > 0) launch_k(k_aux_p, std::min((n + kBlock - 1) / kBlock, 152 * 8), kBlock, s, n, p, z, sc, ia, ib);
+}
+
 void launch_coarse_inv_df(int n, const float2* Ainv_df, const float* b, float* z, cudaStream_t s) {
   if (n <= 0) return;
   launch_k(k_densemv_df, n, kTriBlock, s, n, Ainv_df, b, z);

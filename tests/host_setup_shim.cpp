@@ -115,4 +115,12 @@ int shim_sell16(const void* s, int* bases, uint32_t* c16, int64_t* nbases) {
   return rb ? 2 : 1;
 }
 
+// Generalized inverse of a dense symmetric positive semi-definite matrix.
+int shim_ginv(int n, const double* S, double* G, double tol) {
+  std::vector<double> s(S, S + (size_t)n * n), g;
+  const int r = amge::generalized_inverse(n, s, g, tol);
+  std::memcpy(G, g.data(), g.size() * sizeof(double));
+  return r;
+}
+
 }  // extern "C"

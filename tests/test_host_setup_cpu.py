@@ -56,6 +56,7 @@ def lib(tmp_path_factory):
         ("shim_sell_info", [vp, ip], None),
         ("shim_sell_copy", [vp, ip, ip, ip, dp], None),
         ("shim_sell16", [vp, ip, ip, ip], i32),
+        ("shim_ginv", [i32, dp, dp, ctypes.c_double], i32),
         ("shim_error", [], ctypes.c_char_p),
     ]:
         f = getattr(L, name)
@@ -344,3 +345,20 @@ def test_sliced_ell_16bit_columns(lib):
     # a row spanning more than 65,535 columns: not built
     M = sp.csr_matrix((np.ones(2), ([0, 0], [0, 70000])), shape=(40, n))
     assert _sell16(lib, M)[0] == 0
+
+
+@pytest.mark.parametrize("rank", [40, 33, 1])
+def test_generalized_inverse(lib, rank):
+    """Pivoted-Cholesky generalized inverse of a positive semi-definite matrix:
+    symmetric, S G S = S, the rank found; the inverse itself for a nonsingular S."""
+    rng = np.random.default_rng(rank)
+    n = 40
+    B = rng.standard_normal((n, rank)) * np.exp(rng.uniform(-3, 3, rank))
+    S = B @ B.T
+    G = np.zeros((n, n))
+    r = lib.shim_ginv(n, _ptr(np.ascontiguousarray(S)), _ptr(G), 1e-12)
+    assert r == rank
+    assert np.abs(G - G.T).max() == 0
+    assert np.abs(S @ G @ S - S).max() <= 1e-8 * np.abs(S).max()
+    if rank == n:
+        assert np.abs(G @ S - np.eye(n)).max() <= 1e-6
