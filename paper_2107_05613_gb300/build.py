@@ -41,7 +41,7 @@ def _run(cmds):
 def build_hierarchy_lib():
     src = os.path.join(PKG, "inputs", "amge_hierarchy.cpp")
     tmp = HIER_SO + ".tmp"
-    _run([["g++", "-O3", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src]])
+    _run([["g++", "-O3", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src]])
     os.replace(tmp, HIER_SO)
     return HIER_SO
 
@@ -54,7 +54,7 @@ def build_amge_lib(verbose_ptxas=False):
         src = os.path.join(CSRC, s)
         obj = os.path.join(objdir, os.path.basename(s) + ".o")
         objs.append(obj)
-        cmd = [NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-fopenmp",
+        cmd = [NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-fopenmp,-ffp-contract=off",
                "-I", INCLUDE, "-I", CSRC, "-I", INPUTS, "-c", src, "-o", obj]
         if verbose_ptxas and s.endswith(".cu"):
             cmd.insert(1, "-Xptxas=-v")

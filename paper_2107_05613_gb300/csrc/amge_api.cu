@@ -2602,16 +2602,16 @@ amge_status amge_set_coarse_solver(amge_hier* h, int32_t solver, int32_t iters, 
   c.nv = Pv.nc, c.nd = Dm.nc;
   // the auxiliary matrices (exact products) and their generalized inverses
   std::vector<double> Gv, Gd, Gc, mc;
-  c.rank_v = generalized_inverse(c.nv, dense_product(PvT, sparse_product(A, Pv, false)), Gv, 1e-12);
+  c.rank_v = generalized_inverse(c.nv, dense_product(PvT, sparse_product(A, Pv, false)), Gv, 1e-10);
   HostCsr Pi1, Pi1T;
   if (!ads) {
-    c.rank_d = generalized_inverse(c.nd, dense_product(DT, sparse_product(A, Dm, false)), Gd, 1e-12);
+    c.rank_d = generalized_inverse(c.nd, dense_product(DT, sparse_product(A, Dm, false)), Gd, 1e-10);
   } else {
     const HostCsr Ac = sparse_product(DT, sparse_product(A, Dm, false), false);
     mc = l1_row_sums(Ac);
     Pi1 = to_host(*pihat_inner), Pi1T = transpose(Pi1);
     c.nv1 = Pi1.nc;
-    c.rank_d = generalized_inverse(c.nv1, dense_product(Pi1T, sparse_product(Ac, Pi1, false)), Gc, 1e-12);
+    c.rank_d = generalized_inverse(c.nv1, dense_product(Pi1T, sparse_product(Ac, Pi1, false)), Gc, 1e-10);
   }
   std::vector<double> minv = l1_row_sums(A), mcinv(mc.size());
   for (double& v : minv) v = 1.0 / v;

@@ -439,8 +439,9 @@ std::vector<double> dense_product(const HostCsr& Q, const HostCsr& AW) {
 }
 
 // A symmetric generalized inverse of the symmetric positive semi-definite S (n x n,
-// row-major): Cholesky with diagonal pivoting stops when the largest remaining pivot
-// is below tol times the largest diagonal entry; with the r pivoted rows and columns
+// row-major): Cholesky with diagonal pivoting stops when no remaining pivot exceeds
+// tol times its row's diagonal entry in S (a column that is, to that relative
+// precision, a combination of the pivoted ones); with the r pivoted rows and columns
 // as the leading block S11 (nonsingular, of S's rank), G = P^T [S11^{-1} 0; 0 0] P
 // satisfies S G S = S.  For t in the range of S every such G gives the same S-range
 // part of G t, which is all the auxiliary-space preconditioner uses (its kernels are
@@ -452,14 +453,13 @@ int generalized_inverse(int n, const std::vector<double>& S, std::vector<double>
   std::vector<int> perm(n);
   for (int i = 0; i < n; i++) perm[i] = i;
   auto w = [&](int a, int b) -> double& { return W[(size_t)a * n + b]; };
-  double dmax = 0.0;
-  for (int i = 0; i < n; i++) dmax = std::max(dmax, S[(size_t)i * n + i]);
+  auto live = [&](int i) { return w(perm[i], perm[i]) > tol * S[(size_t)perm[i] * n + perm[i]]; };
   int r = 0;
   for (int k = 0; k < n; k++) {
-    int j = k;
-    for (int i = k + 1; i < n; i++)
-      if (w(perm[i], perm[i]) > w(perm[j], perm[j])) j = i;
-    if (!(w(perm[j], perm[j]) > tol * dmax)) break;
+    int j = -1;  // the largest remaining pivot among the live ones
+    for (int i = k; i < n; i++)
+      if (live(i) && (j < 0 || w(perm[i], perm[i]) > w(perm[j], perm[j]))) j = i;
+    if (j < 0) break;
     std::swap(perm[k], perm[j]);
     const int pk = perm[k];
     const double d = std::sqrt(w(pk, pk));

@@ -467,7 +467,7 @@ HostCsr sparse_product(const HostCsr& A, const HostCsr& B, bool drop_residue = t
 // Dense Q (A W) (m x AW.nc, row-major).
 std::vector<double> dense_product(const HostCsr& Q, const HostCsr& AW);
 // Symmetric generalized inverse of a positive semi-definite S by pivoted Cholesky
-// (pivots below tol * max diag are zero); returns the rank.
+// (a pivot below tol times its row's diagonal is zero); returns the rank.
 int generalized_inverse(int n, const std::vector<double>& S, std::vector<double>& G, double tol);
 std::vector<double> aux_l1_row_sums(const HostCsr& A, const HostCsr& G, const HostCsr& GT);
 // Dense Cholesky of the coarsest matrix; returns false if not SPD.  Linv = L^{-1}
