@@ -217,6 +217,9 @@ def test_dependent_launch_does_not_change_results(amge, prec):
     for (l, p, o), v in rep1.items():      # same kernels on both
         if v >= 0:
             amge.amge_set_kernel(h0, l, p, o, v)
+    for l in range(2):                     # and the same double-float forms and PCG product
+        amge.amge_df_form(h0, l, amge.amge_df_form(h1, l)[0])
+    amge.amge_pcg_kernel(h0, amge.amge_pcg_kernel(h1)[0])
     amge.amge_set_dependent_launch(False)
     try:
         z0, x0 = torch.empty_like(b), torch.empty_like(b)
