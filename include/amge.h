@@ -489,7 +489,7 @@ amge_status amge_wait_status(amge_hier* h, void* stream, int32_t* timed_out);
  * lanes must hold (levels-1)*12 entries. */
 amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
 
-/* The autotuner's evidence: us[((l * 2 + p) * 6 + op) * 11 + c] = measured time per
+/* The autotuner's evidence: us[((l * 2 + p) * 6 + op) * 14 + c] = measured time per
  * launch in microseconds (STORE epilogue, ten launches replayed from a graph).  Where
  * a level's operators and the coarser ones take more than half of L2, so that a
  * V-cycle finds them evicted, each launch follows a read of twice L2's capacity and is
