@@ -545,12 +545,12 @@ amge_status amge_set_coarse_solver(amge_hier* h, int32_t solver, int32_t iters, 
 
 /* The PCG product q = A_0 p (FP64, with the p.q partials): code 0 = 32-bit columns,
  * 1700 = 16-bit column offsets with each slice's entries prefetched into L2 (where
- * A_0's slices span fewer than 65,536 columns).  Chosen at upload by timing both
- * (us[0], us[1]: time per launch, -1 where not measured); both form the same sums.
- * set = 0: report the choice in *code; set = 1: take *code as the choice (1700 acts
- * as 0 without 16-bit columns) and report what is used.  us may be NULL.  Captured
- * PCG graphs are rebuilt on the next solve.  AMGE_EINVAL for NULL h or code, or
- * another code. */
+ * A_0 has 16-bit columns), 1000 = 32-bit columns with the prefetch.  Chosen at upload
+ * by timing each (us[0..2] for 0, 1700, 1000: time per launch, -1 where not measured);
+ * all form the same sums.  set = 0: report the choice in *code; set = 1: take *code as
+ * the choice (1700 acts as 0 without 16-bit columns) and report what is used.  us (3
+ * floats) may be NULL.  Captured PCG graphs are rebuilt on the next solve.
+ * AMGE_EINVAL for NULL h or code, or another code. */
 amge_status amge_pcg_kernel(amge_hier* h, int32_t set, int32_t* code, float* us);
 
 /* Form of the FP32 V-cycle's double-float product on smoothing level `level`

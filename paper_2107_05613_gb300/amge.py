@@ -332,12 +332,12 @@ def amge_set_wide_arith(h: Hier, arith: int):
 
 
 def amge_pcg_kernel(h: Hier, code=None):
-    """The PCG product's kernel (0 or 1700) and the upload-time timings [us, us];
-    with `code`, set it first."""
+    """The PCG product's kernel (0, 1700 or 1000) and the upload-time timings [us for 0,
+    1700, 1000]; with `code`, set it first."""
     c = _i32(0 if code is None else int(code))
-    us = (ctypes.c_float * 2)()
+    us = (ctypes.c_float * 3)()
     _check(_lib.amge_pcg_kernel(h.handle, 0 if code is None else 1, ctypes.byref(c), us), "amge_pcg_kernel")
-    return c.value, [round(float(us[0]), 2), round(float(us[1]), 2)]
+    return c.value, [round(float(u), 2) for u in us]
 
 
 def amge_df_form(h: Hier, level: int, form=None, layout: bool = False):

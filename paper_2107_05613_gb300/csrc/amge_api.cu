@@ -657,7 +657,7 @@ amge_status build_pcg_graph(amge_hier* h, int prec) {
     launch_pcg_dots<double>(n, h->pr, h->pz, h->pq, flexible, h->red, h->cap);
     launch_pcg_update_p<double>(n, h->pp, h->pz, h->red, h->cap);
   }
-  launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, h->cap, h->pcg_c16);
+  launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, h->cap, h->pcg_form);
   launch_pcg_axpy_norm(n, h->gx, h->pr, h->pp, h->pq, h->red, h->cap, pcg_x0_out(h, prec));
   launch_pcg_loop_cond(G.hw, n, h->red, h->gstate, h->cap);
   cudaGraph_t captured = nullptr;
@@ -786,7 +786,7 @@ amge_status run_step(PcgRun& r) {
       CK(cudaMemcpyAsync(h->pp, h->pz, n * sizeof(double), cudaMemcpyDeviceToDevice, r.s));
       {
         Prof p(h, AMGE_PROF_PCG_SPMV, r.s, 2);
-        launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, r.s, h->pcg_c16);
+        launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, r.s, h->pcg_form);
       }
       {
         Prof p(h, AMGE_PROF_PCG_VEC, r.s, 2);
@@ -1880,20 +1880,22 @@ amge_status autotune_df(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, cud
   return AMGE_OK;
 }
 
-// The PCG product q = A_0 p (with the p.q partials) in its two forms, 32-bit columns
-// and 16-bit columns with per-slice L2 prefetch (where A_0 has them): kTuneReps
-// launches back to back from a graph, best of three; the faster is kept.  Both form
-// the same sums.
+// The PCG product q = A_0 p (with the p.q partials) in its forms (32-bit columns;
+// 16-bit columns with per-slice L2 prefetch where A_0 has them; 32-bit columns with
+// the prefetch): kTuneReps launches back to back from a graph, best of three; the
+// fastest is kept.  All form the same sums.
 amge_status autotune_pcg_spmv(amge_hier* h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
-  h->pcg_c16 = false;
-  h->pcg_spmv_us[0] = h->pcg_spmv_us[1] = -1.f;
-  if (!h->A0.c16 || !h->pp) return AMGE_OK;
+  h->pcg_form = 0;
+  h->pcg_spmv_us[0] = h->pcg_spmv_us[1] = h->pcg_spmv_us[2] = -1.f;
+  if (!h->pp || h->L < 2) return AMGE_OK;
   CK(cudaMemsetAsync(h->pp, 0, (size_t)h->n0 * sizeof(double), s));
-  for (int c = 0; c <= 1; c++) {
+  float best = -1.f;
+  for (int f = 0; f <= 2; f++) {
+    if (f == 1 && !h->A0.c16) continue;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    for (int r = 0; r < kTuneReps; r++) launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, s, c == 1);
+    for (int r = 0; r < kTuneReps; r++) launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, s, f);
     CK(cudaStreamEndCapture(s, &g));
     cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
@@ -1902,9 +1904,9 @@ amge_status autotune_pcg_spmv(amge_hier* h, cudaStream_t s, cudaEvent_t e0, cuda
     cudaError_t le = time_graph(ge, s, e0, e1, &ms);
     cudaGraphExecDestroy(ge);
     CK(le);
-    h->pcg_spmv_us[c] = ms * (1e3f / kTuneReps);
+    h->pcg_spmv_us[f] = ms * (1e3f / kTuneReps);
+    if (best < 0.f || ms < best) best = ms, h->pcg_form = f;
   }
-  h->pcg_c16 = h->pcg_spmv_us[1] < h->pcg_spmv_us[0];
   return AMGE_OK;
 }
 
@@ -2173,7 +2175,7 @@ amge_status pcg_one(amge_hier* h, const double* b, double* x, const amge_solve_o
   while (it < o.maxit) {
     {
       Prof p(h, AMGE_PROF_PCG_SPMV, s, 2);
-      launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, s, h->pcg_c16);
+      launch_pcg_spmv_dot(h->A0, h->pp, h->pq, h->red, s, h->pcg_form);
     }
     {
       Prof p(h, AMGE_PROF_PCG_VEC, s, 2);
@@ -2242,7 +2244,7 @@ amge_status amge::hier_make_view(const amge_hier* src, cudaStream_t s, amge_hier
   v->lv32 = src->lv32;
   v->A0 = src->A0, v->cA0 = src->cA0;
   v->nC = src->nC, v->Linv = src->Linv, v->LinvT = src->LinvT, v->Ainv = src->Ainv, v->Ainv_df = src->Ainv_df;
-  v->wide_arith = src->wide_arith, v->pcg_c16 = src->pcg_c16;
+  v->wide_arith = src->wide_arith, v->pcg_form = src->pcg_form;
   v->use_graphs = src->use_graphs;
   v->device = src->device;
   v->smoother = src->smoother, v->sweeps = src->sweeps, v->gs_levels = src->gs_levels, v->gs_built = src->gs_built;
@@ -2690,19 +2692,19 @@ amge_status amge_pcg_kernel(amge_hier* h, int32_t set, int32_t* code, float* us)
     return AMGE_EINVAL;
   }
   if (set) {
-    if (*code != 0 && *code != 1700) {
-      set_error("PCG product code must be 0 or 1700");
+    if (*code != 0 && *code != 1700 && *code != 1000) {
+      set_error("PCG product code must be 0, 1000 or 1700");
       return AMGE_EINVAL;
     }
-    h->pcg_c16 = (*code == 1700) && h->A0.c16;
+    h->pcg_form = *code == 1700 ? (h->A0.c16 ? 1 : 0) : *code == 1000 ? 2 : 0;
     for (GraphPcg& G : h->gpcg) {  // the captured loop names the old kernel
       if (G.exec) cudaGraphExecDestroy(G.exec);
       if (G.g) cudaGraphDestroy(G.g);
       G = GraphPcg{};
     }
   }
-  *code = h->pcg_c16 ? 1700 : 0;
-  if (us) us[0] = h->pcg_spmv_us[0], us[1] = h->pcg_spmv_us[1];
+  *code = h->pcg_form == 1 ? 1700 : h->pcg_form == 2 ? 1000 : 0;
+  if (us) us[0] = h->pcg_spmv_us[0], us[1] = h->pcg_spmv_us[1], us[2] = h->pcg_spmv_us[2];
   return AMGE_OK;
 }
 

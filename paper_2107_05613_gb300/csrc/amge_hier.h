@@ -149,9 +149,9 @@ struct amge_hier {
   cudaStream_t cap = nullptr;  // capture stream of the graphs
   int* gstate = nullptr;       // device: iterations done, maxit, non-finite flag
   int* kwait = nullptr;        // device: set by a bounded wait that ran out (amge_wait_status)
-  // PCG q = A p with the 16-bit columns and per-slice L2 prefetch (timed at upload)
-  bool pcg_c16 = false;
-  float pcg_spmv_us[2] = {-1.f, -1.f};
+  // form of the PCG product q = A p (launch_pcg_spmv_dot; timed at upload)
+  int pcg_form = 0;
+  float pcg_spmv_us[3] = {-1.f, -1.f, -1.f};
   double* gx = nullptr;        // device: iterate of the graph-driven loop
   int* pinned_state = nullptr;
   bool use_graphs = true;

@@ -363,8 +363,10 @@ void launch_dot(int64_t n, const double* x, const double* y, double* out, const 
 // partials; one-block kernels sum them in index order and set the scalars.
 int pcg_spmv_blocks(const DevSell<double>& A);
 // q = A p and pq = p.q (two launches); alpha = rho / pq.
+// form: 0 = 32-bit columns, 1 = 16-bit columns with the per-slice L2 prefetch (where
+// built), 2 = 32-bit columns with the prefetch
 void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, const RedScratch& r,
-                         cudaStream_t s, bool c16 = false);
+                         cudaStream_t s, int form = 0);
 // Optional extra outputs of the PCG axpy: the next V-cycle's first level-0 sweep from
 // zero (mode 1: x64 = minv64 r; mode 2: r32 = (float) r, x32 = minv32 r32).
 struct X0Out {

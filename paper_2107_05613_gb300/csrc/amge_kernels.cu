@@ -1100,7 +1100,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_dot(int64_t n, const double* __re
 // that finishes its slice leaves its row products in shared memory and exits; the
 // last warp of the block to arrive (a shared-memory counter) sums them in a fixed
 // order, so no warp idles at a block barrier behind a longer slice.
-template <bool CS, bool C16 = false>
+template <bool CS, bool C16 = false, bool PF = false>
 __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, const int64_t* __restrict__ sptr,
                                                                    const int* __restrict__ srow,
                                                                    const int2* __restrict__ ci2,
@@ -1117,8 +1117,9 @@ __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, 
   const int lane = threadIdx.x & 31;
   const int slice = (blockIdx.x * kSpmvDotBlock + threadIdx.x) >> 5;
   // constant slice header and first entry pair before waiting (see k_sell)
-  // C16: 16-bit column offsets from the slice's smallest column, and each slice's
-  // entries prefetched into L2 first (the 1700 form of k_sell16; same sums)
+  // C16: 16-bit column offsets from the slice's smallest column; PF: each slice's
+  // entries prefetched into L2 first (the 1700 / 1000 forms of the sliced-ELL kernels;
+  // same sums)
   int row = -1, np = 0, base = 0;
   const int2* cp = ci2;
   const uint32_t* up = c16;
@@ -1137,11 +1138,12 @@ __global__ void __launch_bounds__(kSpmvDotBlock, 4) k_pcg_spmv_dot(int nslices, 
     const int64_t p0 = ldg(sptr + slice) >> 1;
     np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
     row = ldg(srow + (size_t)slice * 32 + lane);
+    if (PF && lane == 0 && np > 0) {
+      if (C16) prefetch_l2_bulk(c16 + p0, (uint32_t)np * 32u * sizeof(uint32_t));
+      else prefetch_l2_bulk(ci2 + p0, (uint32_t)np * 32u * sizeof(int2));
+      prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(double2));
+    }
     if (C16) {
-      if (lane == 0 && np > 0) {
-        prefetch_l2_bulk(c16 + p0, (uint32_t)np * 32u * sizeof(uint32_t));
-        prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(double2));
-      }
       base = col_base(sbase, rb, slice, lane);
       up += p0 + lane;
     } else {
@@ -1789,11 +1791,12 @@ int pcg_spmv_blocks(const DevSell<double>& A) {
 }
 
 void launch_pcg_spmv_dot(const DevSell<double>& A, const double* p, double* q, const RedScratch& r,
-                         cudaStream_t s, bool c16) {
+                         cudaStream_t s, int form) {
   const int grid = pcg_spmv_blocks(A);
-  const bool use16 = c16 && A.c16 && !A.unit;
-  auto k = use16 ? (A.stream ? k_pcg_spmv_dot<true, true> : k_pcg_spmv_dot<false, true>)
-                 : (A.stream ? k_pcg_spmv_dot<true> : k_pcg_spmv_dot<false>);
+  const bool use16 = form == 1 && A.c16 && !A.unit;
+  auto k = use16 ? (A.stream ? k_pcg_spmv_dot<true, true, true> : k_pcg_spmv_dot<false, true, true>)
+           : form == 2 ? (A.stream ? k_pcg_spmv_dot<true, false, true> : k_pcg_spmv_dot<false, false, true>)
+                       : (A.stream ? k_pcg_spmv_dot<true> : k_pcg_spmv_dot<false>);
   launch_k(k, grid, kSpmvDotBlock, s, A.nslices, A.sptr, A.srow, reinterpret_cast<const int2*>(A.ci),
            reinterpret_cast<const double2*>(A.val), p, q, r.partials + kSlotPQ * kMaxRedBlocks,
            (const int*)A.sbase, A.c16_rb, (const uint32_t*)A.c16);

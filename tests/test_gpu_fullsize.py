@@ -275,14 +275,15 @@ def test_pcg_full_size_fp32_vcycle_block(amge, name):
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 def test_pcg_product_forms_equal(amge, name):
-    """The PCG product q = A_0 p with 32-bit columns and with 16-bit column offsets and
-    per-slice L2 prefetch (where A_0 has them) form the same sums: identical solves."""
+    """The PCG product q = A_0 p with 32-bit columns, with 16-bit column offsets and
+    per-slice L2 prefetch (where A_0 has them) and with 32-bit columns and the prefetch
+    form the same sums: identical solves."""
     h, o, b = workload(amge, name)
     bd = dev(b)
     saved, us = amge.amge_pcg_kernel(h)
     res = []
     try:
-        for code in (0, 1700):
+        for code in (0, 1700, 1000):
             amge.amge_pcg_kernel(h, code)
             x = torch.empty_like(bd)
             st, info = amge.amge_pcg_solve(h, bd, x, rtol=1e-8, precision=amge.AMGE_FP64)
@@ -290,8 +291,9 @@ def test_pcg_product_forms_equal(amge, name):
             res.append((x, info[0]["iters"]))
     finally:
         amge.amge_pcg_kernel(h, saved)
-    print(f"{name}: PCG product {us[0]} us (32-bit columns) / {us[1]} us (16-bit + prefetch), kept {saved}")
-    assert torch.equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+    print(f"{name}: PCG product {us} us (32-bit / 16-bit + prefetch / 32-bit + prefetch), kept {saved}")
+    for x, it in res[1:]:
+        assert torch.equal(res[0][0], x) and res[0][1] == it
 
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
