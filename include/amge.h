@@ -172,7 +172,8 @@ amge_status amge_setup_upload(const amge_problem* problem, void* stream, amge_hi
  * G_l^T A_l G_l, the stored A_l G_l, the FP32 copies and the sliced-ELL values are
  * recomputed on the device, and the coarsest Cholesky factor and inverse on the host
  * from the new A_L.  Kernel choices and captured graphs are kept; Gauss-Seidel data
- * (amge_set_smoother) are rebuilt.  Synchronises `stream`; no solve on h or on a
+ * (amge_set_smoother) are rebuilt; an auxiliary-space coarsest solver
+ * (amge_set_coarse_solver) is dropped for the dense solve, to be set again.  Synchronises `stream`; no solve on h or on a
  * server slot of h may be in flight.  Results equal a fresh amge_setup_upload with
  * these coefficients up to the summation order of the products.
  * Errors: AMGE_EINVAL for NULL h, a hierarchy not made by amge_setup_upload (or with

@@ -2912,6 +2912,16 @@ amge_status amge_update_coefficients(amge_hier* h, const double* beta, const dou
   cudaStream_t s = as_stream(stream);
   amge_status st = update_coefficients(h, beta, alpha, s);
   if (st) return st;
+  // the auxiliary-space coarsest solver's matrices were formed from the old A_L: the
+  // dense solve takes over until amge_set_coarse_solver is called again
+  if (h->aux) {
+    h->aux = nullptr;
+    for (GraphPcg& G : h->gpcg) {
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      if (G.g) cudaGraphDestroy(G.g);
+      G = GraphPcg{};
+    }
+  }
   // the Gauss-Seidel data hold copies of A_l and G^T A_l G: rebuild the levels built
   const int built = h->gs_built;
   h->gs_built = 0;

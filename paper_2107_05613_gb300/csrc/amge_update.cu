@@ -297,6 +297,7 @@ amge_status update_coefficients(amge_hier* h, const double* beta, const double* 
   // coarsest: Cholesky factor, its inverse and the explicit inverse (host, FP64)
   HostCsr AL;
   amge_status st = download(P->AL, AL);
+  h->cAL = P->AL;  // the coarsest CSR the auxiliary-space solver's setup reads
   if (st) return st;
   std::vector<double> Li, LiT, Ai;
   if (!coarse_factor(AL, Li, LiT)) {
