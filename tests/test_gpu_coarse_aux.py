@@ -89,3 +89,34 @@ def test_aux_coarse_refusals(amge):
     with pytest.raises(amge.AmgeError):                 # wrong row count
         amge.amge_set_coarse_solver(h, 1, 5, hh.pihat[0][2], D, inner)
     h.free()
+
+
+def test_aux_coarse_after_coefficient_update(amge):
+    """A hierarchy made by the problem-level setup takes the auxiliary-space solver (the
+    interpolations do not depend on the coefficients); a coefficient update drops it for
+    the dense solve, and setting it again forms its matrices from the new A_L."""
+    from oracle import OracleHierarchy
+    from paper_2107_05613_gb300.inputs import build_hierarchy, rhs_vector
+    from paper_2107_05613_gb300.inputs.rng import block_coefficients, workload_coefficients
+
+    n = 8
+    b1, a1 = workload_coefficients(n, True, 11)
+    b2 = block_coefficients(n, 4, -2.0, 2.0, 12)
+    h = amge.amge_setup_upload("hcurl", n, 2, b1, a1)
+    hh1 = build_hierarchy("hcurl", n, 2, b1, a1, all_spaces=True)
+    hh2 = build_hierarchy("hcurl", n, 2, b2, a1, all_spaces=True)
+    rhs = rhs_vector(41, h.n)
+    z = torch.empty(h.n, dtype=torch.float64, device="cuda")
+
+    def check(o):
+        amge.amge_vcycle(h, dev(rhs), z, 1, amge.AMGE_FP64)
+        ref = o.apply(rhs)
+        assert np.linalg.norm(host(z) - ref) <= 1e-9 * np.linalg.norm(ref)
+
+    amge.amge_set_coarse_solver(h, amge.AMGE_COARSE_AUX, 5, *amge.amge_coarse_aux_inputs(hh1))
+    check(OracleHierarchy.from_hierarchy(hh1, coarse="aux"))
+    amge.amge_update_coefficients(h, b2, a1)
+    check(OracleHierarchy.from_hierarchy(hh2))                 # dense again
+    amge.amge_set_coarse_solver(h, amge.AMGE_COARSE_AUX, 5, *amge.amge_coarse_aux_inputs(hh2))
+    check(OracleHierarchy.from_hierarchy(hh2, coarse="aux"))
+    h.free()
