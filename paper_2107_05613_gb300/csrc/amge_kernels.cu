@@ -226,7 +226,9 @@ __global__ void __launch_bounds__(kBlock) k_sell16(int nslices, const int64_t* _
   const V* xb = a.x + col_base(sbase, rb, slice, lane);
   const uint32_t* cp = c16 + p0 + lane;
   const PV* vp = val2 + p0 + lane;
-  if (PF && lane == 0 && np > 0) {  // code 1700: the slice's entries into L2 first
+  // the slice's entries into L2 first: always for operators that fit in L2 (as k_sell),
+  // with code 1700 for streamed ones
+  if ((!CS || PF) && lane == 0 && np > 0) {
     prefetch_l2_bulk(c16 + p0, (uint32_t)np * 32u * sizeof(uint32_t));
     prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(PV));
   }
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(kBlock) k_sell_df16(int nslices, const int64_t
   const float* xb = a.x + col_base(sbase, rb, slice, lane);
   const uint32_t* cp = c16 + p0 + lane;
   const float4* vp = val4 + p0 + lane;
-  if (PF && lane == 0 && np > 0) {
+  if ((!CS || PF) && lane == 0 && np > 0) {  // as k_sell16
     prefetch_l2_bulk(c16 + p0, (uint32_t)np * 32u * sizeof(uint32_t));
     prefetch_l2_bulk(val4 + p0, (uint32_t)np * 32u * sizeof(float4));
   }
