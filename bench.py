@@ -649,7 +649,7 @@ def run_ours(args, dist):
     peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s (of fallback)"
     hbm = hbm or HBM_FALLBACK_GBS
     ag = tuned.get((0, pname, "AG"), -1) >= 0
-    C16_CODES = (1600, 1700)  # kernel codes with 16-bit column offsets
+    C16_CODES = (1600, 1700, 1800, 1900)  # kernel codes with 16-bit column offsets
     df_form, _, layout16 = amge.amge_df_form(h, 0, layout=True)
     c16 = layout16 if tuned.get((0, pname, "A"), -1) in C16_CODES else 0
     c16_wide = layout16 if (fp32 and args.wide_arith == "df" and df_form > 0) else 0

@@ -480,7 +480,8 @@ amge_status amge_wait_status(amge_hier* h, void* stream, int32_t* timed_out);
  * stored; 6 bytes per FP32 entry instead of 8; the FP32 V-cycle's double-float
  * residuals use the same columns where the FP32 A_l product does, and the fused aux
  * correction where the A G product does), 1700 = the same with each slice's entries
- * prefetched into L2 first (streamed operators),
+ * prefetched into L2 first (streamed operators), 1800 / 1900 = 1600 / 1700 with two warps
+ * per slice,
  * 2..32 = vector CSR with that many lanes per row, -1 = operator not used (AG is stored only where
  * A G = A_l G_l is much sparser than A_l, i.e. for H(curl): there the residual after
  * an aux sweep is updated as r - (A G) y instead of recomputed as b - A x).  The
@@ -490,7 +491,7 @@ amge_status amge_wait_status(amge_hier* h, void* stream, int32_t* timed_out);
  * lanes must hold (levels-1)*12 entries. */
 amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
 
-/* The autotuner's evidence: us[((l * 2 + p) * 6 + op) * 14 + c] = measured time per
+/* The autotuner's evidence: us[((l * 2 + p) * 6 + op) * 16 + c] = measured time per
  * launch in microseconds (STORE epilogue, ten launches replayed from a graph).  Where
  * a level's operators and the coarser ones take more than half of L2, so that a
  * V-cycle finds them evicted, each launch follows a read of twice L2's capacity and is
@@ -498,17 +499,18 @@ amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
  * from HBM as it does inside a V-cycle.  Otherwise, and for streamed operators larger
  * than L2, the ten launches run back to back and are timed as a whole (best of
  * three) -- also where the 2x L2 scratch cannot be allocated.  Candidate c in the order 0,
- * 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000, 1600, 1700; -1 where a candidate was
- * not measured (more warps than the operator's rows have entry pairs, a prefetch or
- * staging variant of an operator that is not streamed, 16-bit columns not built) or the
- * operator is not stored.  us must hold (levels-1)*168 floats. */
+ * 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000, 1600, 1700, 1800, 1900; -1 where a
+ * candidate was not measured (more warps than the operator's rows have entry pairs, a
+ * prefetch or staging variant of an operator that is not streamed, 16-bit columns not
+ * built) or the operator is not stored.  us must hold (levels-1)*192 floats. */
 amge_status amge_autotune_times(const amge_hier* h, float* us);
 
 /* Override one entry of that choice (level l < levels-1, precision 0/1, op 0..5 as
- * above; lanes = a kernel code as above: 0, 200, 400, 800, 1000, 1200, 1600, 1700, 3000 or
- * 2, 4, 8, 16, 32; the prefetch codes act as 0 / 200 / 1600 on operators that are not
- * streamed, 3000 as 0 on sign-coded operators and on those whose longest slice does not
- * fit the stages, 1600 / 1700 as 0 / 1000 where the 16-bit columns are not built).  Captured PCG graphs
+ * above; lanes = a kernel code as above: 0, 200, 400, 800, 1000, 1200, 1600, 1700, 1800,
+ * 1900, 3000 or 2, 4, 8, 16, 32; the prefetch codes act as 0 / 200 / 1600 / 1800 on
+ * operators that are not streamed, 3000 as 0 on sign-coded operators and on those whose
+ * longest slice does not fit the stages, 1600 / 1700 / 1800 / 1900 as 0 / 1000 / 200 /
+ * 1200 where the 16-bit columns are not built).  Captured PCG graphs
  * of h are rebuilt on the next solve.  Every kernel computes the same products (in a
  * different summation order), so a choice changes rounding, not results beyond it;
  * pinning the choices makes results reproducible across uploads.  Not to be called

@@ -205,7 +205,7 @@ void opk(amge_hier* h, int cls, const LevelDev<V>& d, int op, int epi, const Spm
   Prof p(h, cls, s);
   const int code = d.lanes[op];  // sliced ELL (code_wps warps per slice, code_pf) or vector CSR lanes
   if (code_bulk(code) && launch_sell_bulk<V>(op_sell(d, op), epi, a, s, h->kwait)) return;
-  if (code_c16(code) && launch_sell16<V>(op_sell(d, op), epi, a, s, code_pf(code))) return;
+  if (code_c16(code) && launch_sell16<V>(op_sell(d, op), epi, a, s, code_pf(code), code_wps(code))) return;
   if (code_is_sell(code)) launch_sell<V>(op_sell(d, op), epi, a, s, code_wps(code), code_pf(code));
   else launch_csrv<V>(op_csr(d, op), code, epi, a, s);
 }
@@ -491,7 +491,8 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
       Prof p(h, AMGE_PROF_AG, s);
       AgArgs<V> f;  // x += G y; r -= (A G) y
       f.y = d.y, f.g2 = d.g2, f.x = x, f.r = d.r;
-      if (!(code_c16(ag) && launch_ag_fused16<V>(d.AG, 0, f, s, ag_pf))) launch_ag_fused<V>(d.AG, 0, f, s, ag_wps, ag_pf);
+      if (!(code_c16(ag) && ag_wps == 1 && launch_ag_fused16<V>(d.AG, 0, f, s, ag_pf)))
+        launch_ag_fused<V>(d.AG, 0, f, s, ag_wps, ag_pf);
     } else {
       aux_sweep();
       SpmvArgs<V> a;  // r = r - (A G) y (in place: row i reads and writes r_i only)
@@ -511,7 +512,8 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
       Prof p(h, AMGE_PROF_AG, s);
       AgArgs<V> f;  // z = x + G y + M^{-1} (r - (A G) y)
       f.y = d.y, f.g2 = d.g2, f.x = x, f.r = d.r, f.minv = d.minv, f.z = z;
-      if (!(code_c16(ag) && launch_ag_fused16<V>(d.AG, 1, f, s, ag_pf))) launch_ag_fused<V>(d.AG, 1, f, s, ag_wps, ag_pf);
+      if (!(code_c16(ag) && ag_wps == 1 && launch_ag_fused16<V>(d.AG, 1, f, s, ag_pf)))
+        launch_ag_fused<V>(d.AG, 1, f, s, ag_wps, ag_pf);
       return;
     }
     aux_sweep();
@@ -1609,7 +1611,7 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
 // Streamed operators (much larger than L2) come from HBM either way and are timed back
 // to back, where each launch overlaps the previous one's tail as it does behind its
 // predecessor in the V-cycle.
-constexpr int kTuneCodes[kNumTuneCodes] = {0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000, 1600, 1700};
+constexpr int kTuneCodes[kNumTuneCodes] = {0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000, 1600, 1700, 1800, 1900};
 constexpr int kTuneReps = 10;
 
 struct TuneFlush {
@@ -2719,9 +2721,9 @@ amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int3
   }
   if (lanes != 0 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32 && lanes != 200 &&
       lanes != 400 && lanes != 800 && lanes != 1000 && lanes != 1200 && lanes != 1600 && lanes != 1700 &&
-      lanes != 3000) {
-    set_error("kernel code must be 0, 200, 400, 800, 1000, 1200, 1600, 1700, 3000 (sliced ELL) or 2, 4, 8, 16, "
-              "32 (vector CSR)");
+      lanes != 1800 && lanes != 1900 && lanes != 3000) {
+    set_error("kernel code must be 0, 200, 400, 800, 1000, 1200, 1600, 1700, 1800, 1900, 3000 (sliced ELL) or 2, "
+              "4, 8, 16, 32 (vector CSR)");
     return AMGE_EINVAL;
   }
   int& cur = precision == 0 ? h->lv64[level].lanes[op] : h->lv32[level].lanes[op];

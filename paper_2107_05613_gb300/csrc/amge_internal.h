@@ -161,18 +161,19 @@ struct SpmvArgs {
 // with that many lanes per row.
 inline bool code_is_sell(int c) { return c == 0 || c >= 100; }
 inline int code_wps(int c) {
-  if (c == 200 || c == 1200) return 2;
+  if (c == 200 || c == 1200 || c == 1800 || c == 1900) return 2;
   if (c == 400) return 4;
   if (c == 800) return 8;
   return 1;
 }
-inline bool code_pf(int c) { return c == 1000 || c == 1200 || c == 1700; }
+inline bool code_pf(int c) { return c == 1000 || c == 1200 || c == 1700 || c == 1900; }
 // 3000: one warp per slice with the slice's entries staged into shared memory by bulk
 // asynchronous copies (streamed operators with stored values; see k_sell_bulk).
 inline bool code_bulk(int c) { return c == 3000; }
 // 1600 / 1700: one warp per slice with 16-bit column offsets (see k_sell16); 1700
-// also prefetches each slice's entries into L2 (streamed operators).
-inline bool code_c16(int c) { return c == 1600 || c == 1700; }
+// also prefetches each slice's entries into L2 (streamed operators).  1800 / 1900: the
+// same with two warps per slice.
+inline bool code_c16(int c) { return c == 1600 || c == 1700 || c == 1800 || c == 1900; }
 
 // wps = warps per 32-row slice (1, 2, 4, 8); pf: a streamed operator's slices are
 // also prefetched into L2 in bulk (wps 1 or 2).
@@ -188,7 +189,8 @@ template <typename V>
 bool sell_bulk_fits(const DevSell<V>& M);
 // The 16-bit-column forms (false, nothing launched, where M has no 16-bit columns).
 template <typename V>
-bool launch_sell16(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, bool pf = false);
+bool launch_sell16(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, bool pf = false,
+                   int wps = 1);
 bool launch_sell_df16(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a, cudaStream_t s,
                       bool pf = false);
 // Host construction of the 16-bit columns of a sliced-ELL operator: one base per slice

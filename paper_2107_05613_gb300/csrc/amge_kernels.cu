@@ -207,53 +207,70 @@ __device__ __forceinline__ int col_base(const int* __restrict__ base, int rb, in
 // 6 (FP32) or 10 (FP64) bytes instead of 8 or 12; built where every slice spans fewer
 // than 65,536 columns (the H(curl) finest operators, banded by the mesh numbering).
 // Same FMA chain as k_sell with one warp per slice: identical results.
-template <typename V, int EPI, bool CS, bool PF = false>
+template <typename V, int EPI, bool CS, bool PF = false, int WPS = 1>
 __global__ void __launch_bounds__(kBlock) k_sell16(int nslices, const int64_t* __restrict__ sptr,
                                                    const int* __restrict__ srow, const int* __restrict__ sbase, int rb,
                                                    const uint32_t* __restrict__ c16,
                                                    const typename Pair<V>::T* __restrict__ val2, SpmvArgs<V> a) {
   using PV = typename Pair<V>::T;
   constexpr bool NEG = SellNeg<EPI>::value;
+  const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int slice = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
-  if (slice >= nslices) {
-    pdl_begin();
-    return;
-  }
-  const int64_t p0 = ldg(sptr + slice) >> 1;
-  const int np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
-  const int row = ldg(srow + (size_t)slice * 32 + lane);
-  const V* xb = a.x + col_base(sbase, rb, slice, lane);
-  const uint32_t* cp = c16 + p0 + lane;
-  const PV* vp = val2 + p0 + lane;
-  // the slice's entries into L2 first: always for operators that fit in L2 (as k_sell),
-  // with code 1700 for streamed ones
-  if ((!CS || PF) && lane == 0 && np > 0) {
-    prefetch_l2_bulk(c16 + p0, (uint32_t)np * 32u * sizeof(uint32_t));
-    prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(PV));
-  }
+  const int g = wib % WPS;  // WPS warps share a slice, as in k_sell
+  const int slice = (blockIdx.x * (kBlock / 32) + wib) / WPS;
+  const bool live = slice < nslices;
+  int row = -1, np = 0;
+  const V* xb = a.x;
+  const uint32_t* cp = c16;
+  const PV* vp = val2;
   uint32_t u0 = 0;
   PV v0{};
-  if (np > 0) {
-    u0 = ldm<CS>(cp);
-    v0 = ldm<CS>(vp);
+  if (live) {
+    const int64_t p0 = ldg(sptr + slice) >> 1;
+    np = (int)((ldg(sptr + slice + 1) >> 1) - p0) >> 5;
+    row = ldg(srow + (size_t)slice * 32 + lane);
+    xb = a.x + col_base(sbase, rb, slice, lane);
+    cp += p0 + lane;
+    vp += p0 + lane;
+    // the slice's entries into L2 first: always for operators that fit in L2 (as
+    // k_sell), with codes 1700 / 1900 for streamed ones
+    if ((!CS || PF) && g == 0 && lane == 0 && np > 0) {
+      prefetch_l2_bulk(c16 + p0, (uint32_t)np * 32u * sizeof(uint32_t));
+      prefetch_l2_bulk(val2 + p0, (uint32_t)np * 32u * sizeof(PV));
+    }
+    if (g < np) {
+      u0 = ldm<CS>(cp + (size_t)g * 32);
+      v0 = ldm<CS>(vp + (size_t)g * 32);
+    }
   }
   pdl_begin();
-  V s = sell_init<V, EPI>(a, row);
-  if (np > 0) {
-    const V x0 = ldg(xb + (u0 & 0xffffu)), x1 = ldg(xb + (u0 >> 16));
-    s = fma(NEG ? -v0.x : v0.x, x0, s);
-    s = fma(NEG ? -v0.y : v0.y, x1, s);
-  }
+  V s = V(0);
+  if (live) {
+    if (g == 0) s = sell_init<V, EPI>(a, row);
+    if (g < np) {
+      const V x0 = ldg(xb + (u0 & 0xffffu)), x1 = ldg(xb + (u0 >> 16));
+      s = fma(NEG ? -v0.x : v0.x, x0, s);
+      s = fma(NEG ? -v0.y : v0.y, x1, s);
+    }
 #pragma unroll 2
-  for (int k = 1; k < np; k++) {
-    const uint32_t u = ldm<CS>(cp + (size_t)k * 32);
-    const PV v = ldm<CS>(vp + (size_t)k * 32);
-    const V x0 = ldg(xb + (u & 0xffffu)), x1 = ldg(xb + (u >> 16));
-    s = fma(NEG ? -v.x : v.x, x0, s);
-    s = fma(NEG ? -v.y : v.y, x1, s);
+    for (int k = g + WPS; k < np; k += WPS) {
+      const uint32_t u = ldm<CS>(cp + (size_t)k * 32);
+      const PV v = ldm<CS>(vp + (size_t)k * 32);
+      const V x0 = ldg(xb + (u & 0xffffu)), x1 = ldg(xb + (u >> 16));
+      s = fma(NEG ? -v.x : v.x, x0, s);
+      s = fma(NEG ? -v.y : v.y, x1, s);
+    }
   }
-  if (row >= 0) sell_store<V, EPI>(a, row, s);
+  if (WPS > 1) {
+    __shared__ V part[kBlock];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (g != 0) return;
+#pragma unroll
+    for (int j = 1; j < WPS; j++) s += part[threadIdx.x + 32 * j];
+  }
+  if (!live || row < 0) return;
+  sell_store<V, EPI>(a, row, s);
 }
 
 // FP32 -> FP64 without a conversion instruction: a normal float's exponent is
@@ -1392,32 +1409,38 @@ static void launch_sell_u(const DevSell<V>& M, int wps, int epi, const SpmvArgs<
   }
 }
 
-template <typename V, bool CS, bool PF>
+template <typename V, bool CS, bool PF, int WPS>
 static void launch_sell16_t(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
-  const int grid = (M.nslices + (kBlock / 32) - 1) / (kBlock / 32);
+  const int per = (kBlock / 32) / WPS;
+  const int grid = (M.nslices + per - 1) / per;
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(M.val);
+#define AMGE_L16(E) launch_k(k_sell16<V, E, CS, PF, WPS>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a)
   switch (epi) {
-    case EPI_STORE: launch_k(k_sell16<V, EPI_STORE, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a); break;
-    case EPI_RESID: launch_k(k_sell16<V, EPI_RESID, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a); break;
-    case EPI_SCALE: launch_k(k_sell16<V, EPI_SCALE, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a); break;
-    case EPI_ADD: launch_k(k_sell16<V, EPI_ADD, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a); break;
-    case EPI_SWEEP: launch_k(k_sell16<V, EPI_SWEEP, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a); break;
-    case EPI_STORE_MUL:
-      launch_k(k_sell16<V, EPI_STORE_MUL, CS, PF>, grid, kBlock, s, M.nslices, M.sptr, M.srow, M.sbase, M.c16_rb, M.c16, v2, a);
-      break;
+    case EPI_STORE: AMGE_L16(EPI_STORE); break;
+    case EPI_RESID: AMGE_L16(EPI_RESID); break;
+    case EPI_SCALE: AMGE_L16(EPI_SCALE); break;
+    case EPI_ADD: AMGE_L16(EPI_ADD); break;
+    case EPI_SWEEP: AMGE_L16(EPI_SWEEP); break;
+    case EPI_STORE_MUL: AMGE_L16(EPI_STORE_MUL); break;
   }
+#undef AMGE_L16
+}
+template <typename V, int WPS>
+static void launch_sell16_w(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, bool pf) {
+  if (M.stream && pf) launch_sell16_t<V, true, true, WPS>(M, epi, a, s);
+  else if (M.stream) launch_sell16_t<V, true, false, WPS>(M, epi, a, s);
+  else launch_sell16_t<V, false, false, WPS>(M, epi, a, s);
 }
 template <typename V>
-bool launch_sell16(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, bool pf) {
+bool launch_sell16(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, bool pf, int wps) {
   if (!M.c16 || M.unit) return false;
   if (M.nslices == 0) return true;
-  if (M.stream && pf) launch_sell16_t<V, true, true>(M, epi, a, s);
-  else if (M.stream) launch_sell16_t<V, true, false>(M, epi, a, s);
-  else launch_sell16_t<V, false, false>(M, epi, a, s);
+  if (wps == 2) launch_sell16_w<V, 2>(M, epi, a, s, pf);
+  else launch_sell16_w<V, 1>(M, epi, a, s, pf);
   return true;
 }
-template bool launch_sell16<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t, bool);
-template bool launch_sell16<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t, bool);
+template bool launch_sell16<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t, bool, int);
+template bool launch_sell16<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t, bool, int);
 
 template <bool CS, bool PF>
 static void launch_sell_df16_t(const DevSell<double>& M, const float4* v4, int epi, const SpmvArgs<float>& a,

@@ -93,7 +93,7 @@ class pinned_level0:
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200, 3000, 1600, 1700])
+@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200, 3000, 1600, 1700, 1900])
 def test_level0_products_sampled(amge, name, prec, kernels):
     """The level-0 products on the autotuned kernels, on the sliced-ELL kernels that
     prefetch each slice into L2 with one and two warps per slice, and on the one that
@@ -171,16 +171,17 @@ def _level0_wide(amge, h, o, name, arith):
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("code", [3000, 1600])
-def test_level0_bulk_staged_equals_one_warp(amge, name, prec, code):
+@pytest.mark.parametrize("base,code", [(0, 3000), (0, 1600), (200, 1800)])
+def test_level0_bulk_staged_equals_one_warp(amge, name, prec, base, code):
     """At full size, in the launch configuration of the timed solves: the level-0
     operators on the bulk-staged kernel (code 3000) or with 16-bit column offsets
     (1600, where built: H(curl)) give the V-cycle and the PCG solve of the one-warp
-    sliced-ELL kernel (code 0) bit for bit."""
+    sliced-ELL kernel (code 0) bit for bit, and those with 16-bit offsets on two warps
+    per slice (1800) those of the two-warp kernel (200)."""
     h, o, b = workload(amge, name)
     bd = dev(b)
     res = []
-    for c in (0, code):
+    for c in (base, code):
         with pinned_level0(amge, h, c):
             z, x = torch.empty_like(bd), torch.empty_like(bd)
             amge.amge_vcycle(h, bd, z, 1, prec)

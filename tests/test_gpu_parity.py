@@ -91,7 +91,7 @@ class pinned_kernels:
 
 @pytest.mark.parametrize("form,n,L", CASES)
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("lanes", ["tuned", 0, 200, 800, 4, 32, 3000, 1600, 1700])
+@pytest.mark.parametrize("lanes", ["tuned", 0, 200, 800, 4, 32, 3000, 1600, 1700, 1800, 1900])
 def test_single_operators(amge, form, n, L, prec, lanes):
     """Every stored product on every smoothing level, on each kernel: sliced ELL with
     one, two and eight warps per slice (sign-coded for the +-1 incidences G), with the
@@ -162,11 +162,12 @@ def test_fused_aux_correction_equals_separate_products(amge, prec, ag):
 
 @pytest.mark.parametrize("form,n,L", [("hcurl", 8, 2), ("hdiv", 24, 3), ("hcurl", 24, 3)])
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("code", [3000, 1600])
-def test_bulk_staged_equals_one_warp_kernel(amge, form, n, L, prec, code):
+@pytest.mark.parametrize("base,code", [(0, 3000), (0, 1600), (200, 1800)])
+def test_bulk_staged_equals_one_warp_kernel(amge, form, n, L, prec, base, code):
     """The bulk-staged product (code 3000: each warp's slices copied into shared memory
     two ahead) and the 16-bit-column product (1600) form every row's sum in the order
-    of the one-warp sliced-ELL kernel (code 0): products, V-cycles and graph-driven
+    of the one-warp sliced-ELL kernel (code 0), the two-warp 16-bit-column product
+    (1800) in that of the two-warp kernel (200): products, V-cycles and graph-driven
     PCG solves are identical, and no staged copy's wait runs out."""
     from paper_2107_05613_gb300.inputs import rhs_vector
 
@@ -174,7 +175,7 @@ def test_bulk_staged_equals_one_warp_kernel(amge, form, n, L, prec, code):
     o = oracle_hierarchy(form, n, L, True)
     b = dev(rhs_vector(83, h.n))
     res = {}
-    for c in (0, code):
+    for c in (base, code):
         with pinned_kernels(amge, h, c):
             out = []
             for l in range(L - 1):
@@ -192,7 +193,7 @@ def test_bulk_staged_equals_one_warp_kernel(amge, form, n, L, prec, code):
             assert st == amge.AMGE_OK
             res[c] = (out, z, x, info[0]["iters"])
             assert not amge.amge_wait_status(h)
-    (o0, z0, x0, i0), (o1, z1, x1, i1) = res[0], res[code]
+    (o0, z0, x0, i0), (o1, z1, x1, i1) = res[base], res[code]
     assert all(torch.equal(a, c) for a, c in zip(o0, o1))
     assert torch.equal(z0, z1) and torch.equal(x0, x1) and i0 == i1
 
@@ -793,5 +794,5 @@ def test_autotune_report(amge):
     h = upload(amge, "hcurl", 24, 3)
     rep = amge.amge_autotune_report(h)
     assert len(rep) == 2 * 2 * 6
-    assert set(rep.values()) <= {-1, 0, 200, 400, 800, 1000, 1200, 1600, 1700, 3000, 2, 4, 8, 16, 32}
+    assert set(rep.values()) <= {-1, 0, 200, 400, 800, 1000, 1200, 1600, 1700, 1800, 1900, 3000, 2, 4, 8, 16, 32}
     assert rep[(0, "fp64", "AG")] >= 0          # H(curl): A G is stored (much sparser than A)
