@@ -481,7 +481,9 @@ amge_status amge_wait_status(amge_hier* h, void* stream, int32_t* timed_out);
  * residuals use the same columns where the FP32 A_l product does, and the fused aux
  * correction where the A G product does), 1700 = the same with each slice's entries
  * prefetched into L2 first (streamed operators), 1800 / 1900 = 1600 / 1700 with two warps
- * per slice,
+ * per slice, 2000 = one warp per slice on a grid of the resident capacity, each warp
+ * walking many slices and loading the next one's entries while it gathers for the
+ * current one (short-row operators),
  * 2..32 = vector CSR with that many lanes per row, -1 = operator not used (AG is stored only where
  * A G = A_l G_l is much sparser than A_l, i.e. for H(curl): there the residual after
  * an aux sweep is updated as r - (A G) y instead of recomputed as b - A x).  The
@@ -491,7 +493,7 @@ amge_status amge_wait_status(amge_hier* h, void* stream, int32_t* timed_out);
  * lanes must hold (levels-1)*12 entries. */
 amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
 
-/* The autotuner's evidence: us[((l * 2 + p) * 6 + op) * 16 + c] = measured time per
+/* The autotuner's evidence: us[((l * 2 + p) * 6 + op) * 17 + c] = measured time per
  * launch in microseconds (STORE epilogue, ten launches replayed from a graph).  Where
  * a level's operators and the coarser ones take more than half of L2, so that a
  * V-cycle finds them evicted, each launch follows a read of twice L2's capacity and is
@@ -499,15 +501,15 @@ amge_status amge_autotune_report(const amge_hier* h, int32_t* lanes);
  * from HBM as it does inside a V-cycle.  Otherwise, and for streamed operators larger
  * than L2, the ten launches run back to back and are timed as a whole (best of
  * three) -- also where the 2x L2 scratch cannot be allocated.  Candidate c in the order 0,
- * 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000, 1600, 1700, 1800, 1900; -1 where a
- * candidate was not measured (more warps than the operator's rows have entry pairs, a
+ * 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000, 1600, 1700, 1800, 1900, 2000; -1 where
+ * a candidate was not measured (more warps than the operator's rows have entry pairs, a
  * prefetch or staging variant of an operator that is not streamed, 16-bit columns not
- * built) or the operator is not stored.  us must hold (levels-1)*192 floats. */
+ * built) or the operator is not stored.  us must hold (levels-1)*204 floats. */
 amge_status amge_autotune_times(const amge_hier* h, float* us);
 
 /* Override one entry of that choice (level l < levels-1, precision 0/1, op 0..5 as
  * above; lanes = a kernel code as above: 0, 200, 400, 800, 1000, 1200, 1600, 1700, 1800,
- * 1900, 3000 or 2, 4, 8, 16, 32; the prefetch codes act as 0 / 200 / 1600 / 1800 on
+ * 1900, 2000, 3000 or 2, 4, 8, 16, 32; the prefetch codes act as 0 / 200 / 1600 / 1800 on
  * operators that are not streamed, 3000 as 0 on sign-coded operators and on those whose
  * longest slice does not fit the stages, 1600 / 1700 / 1800 / 1900 as 0 / 1000 / 200 /
  * 1200 where the 16-bit columns are not built).  Captured PCG graphs

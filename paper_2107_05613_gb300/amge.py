@@ -293,19 +293,19 @@ def amge_autotune_report(h: Hier):
 
 
 OPS = ["A", "P", "PT", "G", "GT", "AG"]
-TUNE_CODES = [0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000, 1600, 1700, 1800, 1900]
+TUNE_CODES = [0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000, 1600, 1700, 1800, 1900, 2000]
 
 
 def amge_autotune_times(h: Hier):
     """{(level, 'fp64'|'fp32', op): {code: us per launch}} as measured at upload."""
     L = h.levels
-    buf = (ctypes.c_float * max((L - 1) * 192, 1))()
+    buf = (ctypes.c_float * max((L - 1) * 204, 1))()
     _check(_lib.amge_autotune_times(h.handle, buf), "amge_autotune_times")
     out = {}
     for l in range(L - 1):
         for pi, p in enumerate(("fp64", "fp32")):
             for o in range(6):
-                t = {c: round(float(buf[((l * 2 + pi) * 6 + o) * 16 + k]), 2) for k, c in enumerate(TUNE_CODES)}
+                t = {c: round(float(buf[((l * 2 + pi) * 6 + o) * 17 + k]), 2) for k, c in enumerate(TUNE_CODES)}
                 if any(v >= 0 for v in t.values()):
                     out[(l, p, OPS[o])] = {c: v for c, v in t.items() if v >= 0}
     return out

@@ -206,6 +206,10 @@ void opk(amge_hier* h, int cls, const LevelDev<V>& d, int op, int epi, const Spm
   const int code = d.lanes[op];  // sliced ELL (code_wps warps per slice, code_pf) or vector CSR lanes
   if (code_bulk(code) && launch_sell_bulk<V>(op_sell(d, op), epi, a, s, h->kwait)) return;
   if (code_c16(code) && launch_sell16<V>(op_sell(d, op), epi, a, s, code_pf(code), code_wps(code))) return;
+  if (code_pipe(code)) {
+    launch_sell_pipe<V>(op_sell(d, op), epi, a, s);
+    return;
+  }
   if (code_is_sell(code)) launch_sell<V>(op_sell(d, op), epi, a, s, code_wps(code), code_pf(code));
   else launch_csrv<V>(op_csr(d, op), code, epi, a, s);
 }
@@ -1611,7 +1615,7 @@ amge_status alloc_work(amge_hier* h, cudaStream_t s) {
 // Streamed operators (much larger than L2) come from HBM either way and are timed back
 // to back, where each launch overlaps the previous one's tail as it does behind its
 // predecessor in the V-cycle.
-constexpr int kTuneCodes[kNumTuneCodes] = {0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000, 1600, 1700, 1800, 1900};
+constexpr int kTuneCodes[kNumTuneCodes] = {0, 200, 400, 800, 2, 4, 8, 16, 32, 1000, 1200, 3000, 1600, 1700, 1800, 1900, 2000};
 constexpr int kTuneReps = 10;
 
 struct TuneFlush {
@@ -1695,6 +1699,9 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
                                (op == OP_AG && d.g2)))
         continue;  // bulk staging: streamed operators with stored values (AG runs fused with G where it can)
       if (code_c16(lanes) && !op_sell(d, op).c16) continue;  // 16-bit columns: where built
+      if (code_pipe(lanes) && op == OP_AG && d.g2) continue;  // AG runs fused with G there
+      // where the fused A G pass carries x += G y (vcycle_level: G on code 0), G keeps it
+      if (op == OP_G && d.g2 && d.use_ag && lanes != 0) continue;
       if (code_is_sell(lanes) && code_wps(lanes) > 1 && 2.0 * code_wps(lanes) > avg + 1.0) continue;  // more warps than entry pairs
       if (lanes > 2 && lanes < 100 && lanes > 2 * avg) continue;
       d.lanes[op] = lanes;
@@ -2721,9 +2728,9 @@ amge_status amge_set_kernel(amge_hier* h, int32_t level, int32_t precision, int3
   }
   if (lanes != 0 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32 && lanes != 200 &&
       lanes != 400 && lanes != 800 && lanes != 1000 && lanes != 1200 && lanes != 1600 && lanes != 1700 &&
-      lanes != 1800 && lanes != 1900 && lanes != 3000) {
-    set_error("kernel code must be 0, 200, 400, 800, 1000, 1200, 1600, 1700, 1800, 1900, 3000 (sliced ELL) or 2, "
-              "4, 8, 16, 32 (vector CSR)");
+      lanes != 1800 && lanes != 1900 && lanes != 2000 && lanes != 3000) {
+    set_error("kernel code must be 0, 200, 400, 800, 1000, 1200, 1600, 1700, 1800, 1900, 2000, 3000 (sliced ELL) or "
+              "2, 4, 8, 16, 32 (vector CSR)");
     return AMGE_EINVAL;
   }
   int& cur = precision == 0 ? h->lv64[level].lanes[op] : h->lv32[level].lanes[op];

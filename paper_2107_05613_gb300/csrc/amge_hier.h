@@ -11,7 +11,7 @@
 
 namespace amge {
 
-constexpr int kNumTuneCodes = 16;  // candidates of the single-vector autotuner (kTuneCodes)
+constexpr int kNumTuneCodes = 17;  // candidates of the single-vector autotuner (kTuneCodes)
 
 template <typename V>
 struct LevelDev {

@@ -174,6 +174,9 @@ inline bool code_bulk(int c) { return c == 3000; }
 // also prefetches each slice's entries into L2 (streamed operators).  1800 / 1900: the
 // same with two warps per slice.
 inline bool code_c16(int c) { return c == 1600 || c == 1700 || c == 1800 || c == 1900; }
+// 2000: one warp per slice, grid-stride over the slices with the next slice's entries
+// loaded ahead (see k_sell_pipe).
+inline bool code_pipe(int c) { return c == 2000; }
 
 // wps = warps per 32-row slice (1, 2, 4, 8); pf: a streamed operator's slices are
 // also prefetched into L2 in bulk (wps 1 or 2).
@@ -188,6 +191,9 @@ bool launch_sell_bulk(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaSt
 template <typename V>
 bool sell_bulk_fits(const DevSell<V>& M);
 // The 16-bit-column forms (false, nothing launched, where M has no 16-bit columns).
+template <typename V>
+void launch_sell_pipe(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s);
+// the same product on the grid-stride kernel (code 2000, k_sell_pipe)
 template <typename V>
 bool launch_sell16(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s, bool pf = false,
                    int wps = 1);

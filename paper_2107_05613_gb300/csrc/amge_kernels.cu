@@ -207,6 +207,95 @@ __device__ __forceinline__ int col_base(const int* __restrict__ base, int rb, in
 // 6 (FP32) or 10 (FP64) bytes instead of 8 or 12; built where every slice spans fewer
 // than 65,536 columns (the H(curl) finest operators, banded by the mesh numbering).
 // Same FMA chain as k_sell with one warp per slice: identical results.
+// Grid-stride form of the one-warp-per-slice kernel, for operators with many short
+// slices (the sign-coded aux operators, whose rows hold 2 to 14 entries): each warp
+// walks the slices w, w + W, w + 2 W, ... (W = warps of a grid sized to the resident
+// capacity) and, before gathering for its current slice, issues the row map and the
+// first two entry pairs of its next slice and the header of the one after.  The chain
+// slice header -> entries -> gathered x of one slice then overlaps the gathers of the
+// previous one, instead of costing three memory latencies per wave of short slices.
+// Every row's sum is formed in the order of k_sell with one warp per slice.
+template <typename V, int EPI, bool UNIT, bool CS>
+struct PipeSlice {
+  using PV = typename Pair<V>::T;
+  int row = -1, np = 0;
+  int p32 = 0;  // the slice's first entry pair / 32 (slices start on 32-pair rows)
+  int2 c0 = make_int2(kSellPad, kSellPad), c1 = make_int2(kSellPad, kSellPad);
+  PV v0{}, v1{};
+};
+template <typename V, int EPI, bool UNIT, bool CS>
+__global__ void __launch_bounds__(kBlock, UNIT ? 8 : 4) k_sell_pipe(int nslices, const int64_t* __restrict__ sptr,
+                                                                  const int* __restrict__ srow,
+                                                                  const int2* __restrict__ ci2,
+                                                                  const typename Pair<V>::T* __restrict__ val2,
+                                                                  SpmvArgs<V> a) {
+  using PV = typename Pair<V>::T;
+  using S = PipeSlice<V, EPI, UNIT, CS>;
+  constexpr bool NEG = SellNeg<EPI>::value;
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * (kBlock / 32);
+  int slice = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+  auto head = [&](int sl, int& p32, int& np) {
+    p32 = 0, np = 0;
+    if (sl < nslices) {
+      const int64_t p0 = ldg(sptr + sl) >> 1;
+      p32 = (int)(p0 >> 5);
+      np = (int)((ldg(sptr + sl + 1) >> 1) - p0) >> 5;
+    }
+  };
+  auto body = [&](int sl, int p32, int np, S& b) {
+    b.row = -1, b.np = np, b.p32 = p32;
+    if (sl >= nslices) return;
+    b.row = ldg(srow + (size_t)sl * 32 + lane);
+    const size_t q = (size_t)p32 * 32 + lane;
+    if (np > 0) {
+      b.c0 = ldm<CS>(ci2 + q);
+      if (!UNIT) b.v0 = ldm<CS>(val2 + q);
+    }
+    if (np > 1) {
+      b.c1 = ldm<CS>(ci2 + q + 32);
+      if (!UNIT) b.v1 = ldm<CS>(val2 + q + 32);
+    }
+  };
+  auto pair = [&](V s, int2 c, PV v) -> V {
+    if (UNIT) {
+      const V e0 = signed_entry<NEG>(a.x, c.x);
+      const V e1 = signed_entry<NEG>(a.x, c.y);
+      s += e0;
+      s += e1;
+    } else {
+      const V x0 = ldg(a.x + c.x), x1 = ldg(a.x + c.y);
+      s = fma(NEG ? -v.x : v.x, x0, s);
+      s = fma(NEG ? -v.y : v.y, x1, s);
+    }
+    return s;
+  };
+  S cur, nxt;
+  int hp0, hnp;
+  head(slice, hp0, hnp);
+  body(slice, hp0, hnp, cur);
+  head(slice + stride, hp0, hnp);
+  pdl_begin();
+  while (slice < nslices) {
+    body(slice + stride, hp0, hnp, nxt);
+    head(slice + 2 * stride, hp0, hnp);
+    V s = sell_init<V, EPI>(a, cur.row);
+    if (cur.np > 0) s = pair(s, cur.c0, cur.v0);
+    if (cur.np > 1) s = pair(s, cur.c1, cur.v1);
+    const size_t q = (size_t)cur.p32 * 32 + lane;
+#pragma unroll 2
+    for (int k = 2; k < cur.np; k++) {
+      const int2 c = ldm<CS>(ci2 + q + (size_t)k * 32);
+      PV v{};
+      if (!UNIT) v = ldm<CS>(val2 + q + (size_t)k * 32);
+      s = pair(s, c, v);
+    }
+    if (cur.row >= 0) sell_store<V, EPI>(a, cur.row, s);
+    cur = nxt;
+    slice += stride;
+  }
+}
+
 template <typename V, int EPI, bool CS, bool PF = false, int WPS = 1>
 __global__ void __launch_bounds__(kBlock) k_sell16(int nslices, const int64_t* __restrict__ sptr,
                                                    const int* __restrict__ srow, const int* __restrict__ sbase, int rb,
@@ -1408,6 +1497,66 @@ static void launch_sell_u(const DevSell<V>& M, int wps, int epi, const SpmvArgs<
       break;
   }
 }
+
+static int sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+// Resident blocks per SM of one k_sell_pipe instantiation (its register budget decides).
+template <typename V, int EPI, bool UNIT, bool CS>
+int pipe_blocks_per_sm() {
+  static std::atomic<int> cache{0};
+  int v = cache.load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_sell_pipe<V, EPI, UNIT, CS>, kBlock, 0) != cudaSuccess ||
+      v <= 0) {
+    (void)cudaGetLastError();
+    v = 1;
+  }
+  cache.store(v, std::memory_order_relaxed);
+  return v;
+}
+
+template <typename V, int EPI, bool UNIT, bool CS>
+static void launch_sell_pipe_e(const DevSell<V>& M, const SpmvArgs<V>& a, cudaStream_t s) {
+  const int per = kBlock / 32;
+  const int need = (M.nslices + per - 1) / per;
+  const int grid = std::max(1, std::min(need, pipe_blocks_per_sm<V, EPI, UNIT, CS>() * sm_count()));
+  launch_k(k_sell_pipe<V, EPI, UNIT, CS>, grid, kBlock, s, M.nslices, M.sptr, M.srow,
+           reinterpret_cast<const int2*>(M.ci), reinterpret_cast<const typename Pair<V>::T*>(M.val), a);
+}
+template <typename V, bool UNIT, bool CS>
+static void launch_sell_pipe_t(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  switch (epi) {
+    case EPI_STORE: launch_sell_pipe_e<V, EPI_STORE, UNIT, CS>(M, a, s); break;
+    case EPI_RESID: launch_sell_pipe_e<V, EPI_RESID, UNIT, CS>(M, a, s); break;
+    case EPI_SCALE: launch_sell_pipe_e<V, EPI_SCALE, UNIT, CS>(M, a, s); break;
+    case EPI_ADD: launch_sell_pipe_e<V, EPI_ADD, UNIT, CS>(M, a, s); break;
+    case EPI_SWEEP: launch_sell_pipe_e<V, EPI_SWEEP, UNIT, CS>(M, a, s); break;
+    case EPI_STORE_MUL: launch_sell_pipe_e<V, EPI_STORE_MUL, UNIT, CS>(M, a, s); break;
+  }
+}
+template <typename V>
+void launch_sell_pipe(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {
+  if (M.nslices == 0) return;
+  const bool cs = M.stream != 0;
+  if (M.unit) {
+    if (cs) launch_sell_pipe_t<V, true, true>(M, epi, a, s);
+    else launch_sell_pipe_t<V, true, false>(M, epi, a, s);
+  } else {
+    if (cs) launch_sell_pipe_t<V, false, true>(M, epi, a, s);
+    else launch_sell_pipe_t<V, false, false>(M, epi, a, s);
+  }
+}
+template void launch_sell_pipe<double>(const DevSell<double>&, int, const SpmvArgs<double>&, cudaStream_t);
+template void launch_sell_pipe<float>(const DevSell<float>&, int, const SpmvArgs<float>&, cudaStream_t);
 
 template <typename V, bool CS, bool PF, int WPS>
 static void launch_sell16_t(const DevSell<V>& M, int epi, const SpmvArgs<V>& a, cudaStream_t s) {

@@ -93,7 +93,7 @@ class pinned_level0:
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200, 3000, 1600, 1700, 1900])
+@pytest.mark.parametrize("kernels", ["tuned", 1000, 1200, 3000, 1600, 1700, 1900, 2000])
 def test_level0_products_sampled(amge, name, prec, kernels):
     """The level-0 products on the autotuned kernels, on the sliced-ELL kernels that
     prefetch each slice into L2 with one and two warps per slice, and on the one that
@@ -171,7 +171,7 @@ def _level0_wide(amge, h, o, name, arith):
 
 @pytest.mark.parametrize("name", ["hcurl64", "hdiv64"])
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("base,code", [(0, 3000), (0, 1600), (200, 1800)])
+@pytest.mark.parametrize("base,code", [(0, 3000), (0, 1600), (200, 1800), (0, 2000)])
 def test_level0_bulk_staged_equals_one_warp(amge, name, prec, base, code):
     """At full size, in the launch configuration of the timed solves: the level-0
     operators on the bulk-staged kernel (code 3000) or with 16-bit column offsets

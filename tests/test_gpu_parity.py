@@ -91,7 +91,7 @@ class pinned_kernels:
 
 @pytest.mark.parametrize("form,n,L", CASES)
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("lanes", ["tuned", 0, 200, 800, 4, 32, 3000, 1600, 1700, 1800, 1900])
+@pytest.mark.parametrize("lanes", ["tuned", 0, 200, 800, 4, 32, 3000, 1600, 1700, 1800, 1900, 2000])
 def test_single_operators(amge, form, n, L, prec, lanes):
     """Every stored product on every smoothing level, on each kernel: sliced ELL with
     one, two and eight warps per slice (sign-coded for the +-1 incidences G), with the
@@ -162,13 +162,15 @@ def test_fused_aux_correction_equals_separate_products(amge, prec, ag):
 
 @pytest.mark.parametrize("form,n,L", [("hcurl", 8, 2), ("hdiv", 24, 3), ("hcurl", 24, 3)])
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("base,code", [(0, 3000), (0, 1600), (200, 1800)])
+@pytest.mark.parametrize("base,code", [(0, 3000), (0, 1600), (200, 1800), (0, 2000)])
 def test_bulk_staged_equals_one_warp_kernel(amge, form, n, L, prec, base, code):
     """The bulk-staged product (code 3000: each warp's slices copied into shared memory
-    two ahead) and the 16-bit-column product (1600) form every row's sum in the order
-    of the one-warp sliced-ELL kernel (code 0), the two-warp 16-bit-column product
-    (1800) in that of the two-warp kernel (200): products, V-cycles and graph-driven
-    PCG solves are identical, and no staged copy's wait runs out."""
+    two ahead), the 16-bit-column product (1600) and the grid-stride product (2000:
+    each warp walks many slices, loading the next one's entries ahead) form every row's
+    sum in the order of the one-warp sliced-ELL kernel (code 0), the two-warp
+    16-bit-column product (1800) in that of the two-warp kernel (200): products,
+    V-cycles and graph-driven PCG solves are identical, and no staged copy's wait runs
+    out."""
     from paper_2107_05613_gb300.inputs import rhs_vector
 
     h = upload(amge, form, n, L)
@@ -794,5 +796,11 @@ def test_autotune_report(amge):
     h = upload(amge, "hcurl", 24, 3)
     rep = amge.amge_autotune_report(h)
     assert len(rep) == 2 * 2 * 6
-    assert set(rep.values()) <= {-1, 0, 200, 400, 800, 1000, 1200, 1600, 1700, 1800, 1900, 3000, 2, 4, 8, 16, 32}
+    assert set(rep.values()) <= {-1, 0, 200, 400, 800, 1000, 1200, 1600, 1700, 1800, 1900, 2000, 3000, 2, 4, 8, 16,
+                                 32}
     assert rep[(0, "fp64", "AG")] >= 0          # H(curl): A G is stored (much sparser than A)
+    # where A G is stored the two-entry gradient G stays on code 0, so x += G y rides in
+    # the fused A G pass instead of a separate product
+    for (l, p, o), v in rep.items():
+        if o == "AG" and v >= 0:
+            assert rep[(l, p, "G")] == 0, (l, p, rep[(l, p, "G")])
