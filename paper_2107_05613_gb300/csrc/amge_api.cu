@@ -1680,7 +1680,7 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
   LevelDev<V>& d = levels<V>(h)[l];
   LevelDev<V>& c = levels<V>(h)[l + 1];
   for (int op = 0; op < 6; op++) {
-    if (op == OP_AG && !d.use_ag) continue;
+    if (op == OP_AG && !d.has_ag) continue;
     const DevCsr<V>& M = op_csr(d, op);
     const V* in = op == OP_A ? d.x : op == OP_P ? c.b : op == OP_PT ? d.r : op == OP_G ? d.y : op == OP_GT ? d.r : d.y;
     V* out = op == OP_A ? d.tmp : op == OP_P ? d.tmp : op == OP_PT ? c.z : op == OP_G ? d.tmp : op == OP_GT ? d.y : d.tmp;
@@ -1750,7 +1750,7 @@ amge_status autotune_mm_level(amge_hier* h, int l, int nrhs, cudaStream_t s, cud
   LevelDev<V>& d = levels<V>(h)[l];
   LevelDev<V>& c = levels<V>(h)[l + 1];
   for (int op = 0; op < 6; op++) {
-    if (op == OP_AG && !d.use_ag) continue;
+    if (op == OP_AG && !d.has_ag) continue;
     const V* in = op == OP_A ? d.X : op == OP_P ? c.Z : op == OP_PT ? d.R : op == OP_G ? d.Y : op == OP_GT ? d.R : d.Y;
     V* out = op == OP_A ? d.T : op == OP_P ? d.T : op == OP_PT ? c.B : op == OP_G ? d.T : op == OP_GT ? d.Y : d.T;
     SpmvArgs<V> a;
@@ -2048,12 +2048,20 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
         upload_csr(h, PT, d64.cPT, d32.cPT, s, keep);
         upload_csr(h, G, d64.cG, d32.cG, s, keep);
         upload_csr(h, GT, d64.cGT, d32.cGT, s, keep);
-        if (desc->form == AMGE_HCURL && desc->nu_pre == 1 && desc->nu_post == 1) {
+        if (desc->nu_pre == 1 && desc->nu_post == 1) {
+          // FP64 V-cycle: r - (A G) y replaces an FP64 residual at the same bytes per
+          // entry, so A G must be much sparser than A (H(curl): 0.42-0.56 of A's
+          // entries).  FP32 V-cycle: it replaces a double-float residual (12 bytes per
+          // entry) by an FP32 product (8, or 6 with 16-bit columns); H(div) level 0,
+          // where A C = alpha M C holds 1.29 times A's entries, qualifies.
           HostCsr AG = sparse_product(A, G);
-          if (AG.nnz() < 0.6 * A.nnz()) {
+          const bool use64 = AG.nnz() < 0.6 * A.nnz(), use32 = AG.nnz() < 1.35 * A.nnz();
+          if (use64 || use32) {
             upload_sell(h, AG, d64.AG, d32.AG, s, keep, keeps);
             upload_csr(h, AG, d64.cAG, d32.cAG, s, keep);
-            d64.use_ag = d32.use_ag = true;
+            d64.has_ag = d32.has_ag = true;
+            d64.use_ag = use64;
+            d32.use_ag = use32;
             d64.lanes[OP_AG] = d32.lanes[OP_AG] = 0;
             bool two = G.nnz() == 2 * (int64_t)G.nr;
             for (int i = 0; two && i < G.nr; i++)
@@ -2465,7 +2473,7 @@ amge_status amge_apply(amge_hier* h, int32_t op, int32_t level, const double* x_
     launch_cast<float, double>(M.nr, h->s32_out, y_dev, s);
     return launch_status();
   }
-  if (op == AMGE_OP_AG && !h->lv64[level].use_ag) {
+  if (op == AMGE_OP_AG && !h->lv64[level].has_ag) {
     set_error("A G is not stored on this level");
     return AMGE_EINVAL;
   }
@@ -2771,7 +2779,7 @@ amge_status amge_autotune_report_mm(amge_hier* h, int32_t nrhs, int32_t precisio
   }
   for (int l = 0; l + 1 < h->L; l++)
     for (int op = 0; op < 6; op++) {
-      const bool stored = op != OP_AG || h->lv64[l].use_ag;
+      const bool stored = op != OP_AG || h->lv64[l].has_ag;
       const int code = precision == AMGE_FP64 ? h->lv64[l].mmk[op][nrhs] : h->lv32[l].mmk[op][nrhs];
       codes[l * 6 + op] = stored ? code : -1;
       if (us)
@@ -2804,7 +2812,7 @@ amge_status amge_set_kernel_mm(amge_hier* h, int32_t level, int32_t precision, i
     set_error("invalid level, op, nrhs, code or precision");
     return AMGE_EINVAL;
   }
-  if (op == OP_AG && !h->lv64[level].use_ag) {
+  if (op == OP_AG && !h->lv64[level].has_ag) {
     set_error("A G is not stored on this level");
     return AMGE_EINVAL;
   }

@@ -18,11 +18,14 @@ struct LevelDev {
   int n = 0, naux = 0;
   DevSell<V> A, P, PT, G, GT;
   DevCsr<V> cA, cP, cPT, cG, cGT;  // CSR copies for the multi-RHS products
-  // A G (n x naux), stored where it is much sparser than A: the residual after an aux
-  // sweep is then updated as r - (A G) y instead of recomputed as b - A x
+  // A G (n x naux), stored where it is cheaper to read than the residual it replaces:
+  // the residual after an aux sweep is then updated as r - (A G) y instead of
+  // recomputed as b - A x.  has_ag: stored (both precisions); use_ag: this precision's
+  // V-cycle updates that way (FP64: A G much sparser than A; FP32: A G in FP32 cheaper
+  // than the double-float residual of A)
   DevSell<V> AG;
   DevCsr<V> cAG;
-  bool use_ag = false;
+  bool has_ag = false, use_ag = false;
   // G sign-coded with two entries per row in row order (the discrete gradient), for
   // the fused aux correction (launch_ag_fused); null where G has another shape
   int2* g2 = nullptr;

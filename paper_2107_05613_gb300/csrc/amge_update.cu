@@ -234,7 +234,7 @@ amge_status prepare_update(amge_hier* h, const FineAssembly& fa, cudaStream_t s)
       return AMGE_EINVAL;
     }
     plan->lv[l].mapA = al.put(keepi.back().data(), keepi.back().size(), s);
-    if (d.use_ag) {
+    if (d.has_ag) {
       HostCsr AG;
       st = download(d.cAG, AG);
       if (st) return st;
@@ -283,7 +283,7 @@ amge_status update_coefficients(amge_hier* h, const double* beta, const double* 
     gemm(A, d.cG, u.W);
     gemm(d.cGT, u.W, u.X);
     k_l1_inv<<<grid_of(u.X.nr), kUpdBlock, 0, s>>>(u.X.nr, u.X.rp, u.X.val, d.mauxinv, f.mauxinv);
-    if (d.use_ag) {  // the stored A G (its pattern omits the cancellation residue)
+    if (d.has_ag) {  // the stored A G (its pattern omits the cancellation residue)
       gemm(A, d.cG, d.cAG);
       k_to_f32<<<grid_of(d.cAG.nnz), kUpdBlock, 0, s>>>(d.cAG.nnz, d.cAG.val, f.cAG.val);
       k_sell_fill<<<grid_of(d.AG.stored), kUpdBlock, 0, s>>>(d.AG.stored, u.mapAG, d.cAG.val, d.AG.val, f.AG.val);

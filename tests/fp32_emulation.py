@@ -109,7 +109,10 @@ class EmulatedVcycle:
             keep = np.abs(AG.data) > 64 * EPS64 * bound
             AG = sp.csr_matrix((AG.data[keep], (AG.row[keep], AG.col[keep])), shape=AG.shape)
             self.AG.append(AG)
-            self.use_ag.append(hh.form == "hcurl" and AG.nnz < 0.6 * A.nnz)
+            # the CUDA upload's rule: r - (A G) y where it reads fewer bytes than the
+            # residual it replaces -- an FP64 residual (A G much sparser than A) in the
+            # FP64 V-cycle, a double-float one (up to 1.35 times A's entries) in FP32
+            self.use_ag.append(AG.nnz < (1.35 if vec == f32 else 0.6) * A.nnz)
         self.GT = [g.T.tocsr() for g in self.G]
         self.PT = [p.T.tocsr() for p in self.P]
         self._f32 = {}

@@ -259,11 +259,17 @@ def test_set_kernel_rebuilds_graph_and_rejects_bad_input(amge):
     for bad in [(5, 0, 0, 0), (0, 2, 0, 0), (0, 0, 6, 0), (0, 0, 0, 3), (0, 0, 0, 64)]:
         with pytest.raises(amge.AmgeError):
             amge.amge_set_kernel(h, *bad)
-    hd = upload(amge, "hdiv", 24, 3)
-    with pytest.raises(amge.AmgeError):             # A G is not stored for H(div)
+    # A G is stored only for one pre- and one post-smoothing step (the updates
+    # r -= (A G) y replace those steps' residuals)
+    hd = amge.amge_upload_levels(hierarchy("hdiv", 24, 3, True), nu_pre=2, nu_post=2)
+    assert all(v < 0 for (l, p, o), v in amge.amge_autotune_report(hd).items() if o == "AG")
+    with pytest.raises(amge.AmgeError):
         amge.amge_set_kernel(hd, 0, 0, "AG", 0)
     with pytest.raises(amge.AmgeError):
         amge.amge_apply(hd, amge.AMGE_OP_AG, 0, b[: 10], b[: 10], 0)
+    # H(div) with one step each: A C (= alpha M C) is stored for the FP32 V-cycle
+    rep = amge.amge_autotune_report(upload(amge, "hdiv", 24, 3))
+    assert rep[(0, "fp32", "AG")] >= 0
 
 
 def _hybrid_step_bound(o, b):
