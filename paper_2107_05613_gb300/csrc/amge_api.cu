@@ -486,7 +486,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
     // G y and (A G) y in one pass where G is the two-entry gradient and both
     // products run sliced-ELL kernels (identical results to the separate products)
     const int ag = d.lanes[OP_AG];
-    const bool fused = d.g2 && code_is_sell(ag) && d.lanes[OP_G] == 0;
+    const bool fused = (d.g2 || d.g4) && code_is_sell(ag) && d.lanes[OP_G] == 0;
     const int ag_wps = code_wps(ag);
     const bool ag_pf = code_pf(ag);
     residual(false);
@@ -494,7 +494,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
       aux_gt();
       Prof p(h, AMGE_PROF_AG, s);
       AgArgs<V> f;  // x += G y; r -= (A G) y
-      f.y = d.y, f.g2 = d.g2, f.x = x, f.r = d.r;
+      f.y = d.y, f.g2 = d.g2, f.g4 = d.g4, f.x = x, f.r = d.r;
       if (!(code_c16(ag) && ag_wps == 1 && launch_ag_fused16<V>(d.AG, 0, f, s, ag_pf)))
         launch_ag_fused<V>(d.AG, 0, f, s, ag_wps, ag_pf);
     } else {
@@ -515,7 +515,7 @@ void vcycle_level(amge_hier* h, int l, const V* b, V* z, cudaStream_t s, bool x_
       aux_gt();
       Prof p(h, AMGE_PROF_AG, s);
       AgArgs<V> f;  // z = x + G y + M^{-1} (r - (A G) y)
-      f.y = d.y, f.g2 = d.g2, f.x = x, f.r = d.r, f.minv = d.minv, f.z = z;
+      f.y = d.y, f.g2 = d.g2, f.g4 = d.g4, f.x = x, f.r = d.r, f.minv = d.minv, f.z = z;
       if (!(code_c16(ag) && ag_wps == 1 && launch_ag_fused16<V>(d.AG, 1, f, s, ag_pf)))
         launch_ag_fused<V>(d.AG, 1, f, s, ag_wps, ag_pf);
       return;
@@ -1696,12 +1696,12 @@ amge_status autotune_level(amge_hier* h, int l, cudaStream_t s, cudaEvent_t e0, 
       d.tune_us[op][ci] = -1.f;
       if (code_pf(lanes) && (!op_sell(d, op).stream || op_sell(d, op).unit)) continue;  // prefetch: streamed only
       if (code_bulk(lanes) && (!op_sell(d, op).stream || op_sell(d, op).unit || !sell_bulk_fits(op_sell(d, op)) ||
-                               (op == OP_AG && d.g2)))
+                               (op == OP_AG && (d.g2 || d.g4))))
         continue;  // bulk staging: streamed operators with stored values (AG runs fused with G where it can)
       if (code_c16(lanes) && !op_sell(d, op).c16) continue;  // 16-bit columns: where built
-      if (code_pipe(lanes) && op == OP_AG && d.g2) continue;  // AG runs fused with G there
+      if (code_pipe(lanes) && op == OP_AG && (d.g2 || d.g4)) continue;  // AG runs fused with G there
       // where the fused A G pass carries x += G y (vcycle_level: G on code 0), G keeps it
-      if (op == OP_G && d.g2 && d.use_ag && lanes != 0) continue;
+      if (op == OP_G && (d.g2 || d.g4) && d.use_ag && lanes != 0) continue;
       if (code_is_sell(lanes) && code_wps(lanes) > 1 && 2.0 * code_wps(lanes) > avg + 1.0) continue;  // more warps than entry pairs
       if (lanes > 2 && lanes < 100 && lanes > 2 * avg) continue;
       d.lanes[op] = lanes;
@@ -2071,6 +2071,21 @@ amge_status do_upload(const amge_hierarchy_desc* desc, cudaStream_t s, amge_hier
               std::vector<int>& g2 = keepi.back();
               for (size_t k = 0; k < g2.size(); k++) g2[k] = G.v[k] > 0 ? G.ci[k] : ~G.ci[k];
               d64.g2 = d32.g2 = reinterpret_cast<int2*>(upload<int>(h, g2.data(), g2.size(), s));
+            } else {
+              // up to four +-1 entries per row (the discrete curl): rows padded to four
+              bool four = true;
+              for (int i = 0; four && i < G.nr; i++) {
+                four = G.rp[i + 1] - G.rp[i] <= 4;
+                for (int p = G.rp[i]; four && p < G.rp[i + 1]; p++) four = std::fabs(G.v[p]) == 1.0;
+              }
+              if (four) {
+                keepi.emplace_back(4 * (size_t)G.nr, kSellPad);
+                std::vector<int>& g4 = keepi.back();
+                for (int i = 0; i < G.nr; i++)
+                  for (int p = G.rp[i]; p < G.rp[i + 1]; p++)
+                    g4[4 * (size_t)i + (p - G.rp[i])] = G.v[p] > 0 ? G.ci[p] : ~G.ci[p];
+                d64.g4 = d32.g4 = reinterpret_cast<int4*>(upload<int>(h, g4.data(), g4.size(), s));
+              }
             }
           }
         }

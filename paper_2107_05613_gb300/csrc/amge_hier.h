@@ -29,6 +29,8 @@ struct LevelDev {
   // G sign-coded with two entries per row in row order (the discrete gradient), for
   // the fused aux correction (launch_ag_fused); null where G has another shape
   int2* g2 = nullptr;
+  // the same with up to four entries per row, padded (the discrete curl; H(div))
+  int4* g4 = nullptr;
   // autotuned single-vector kernel per operator (A, P, PT, G, GT, AG): 0 = sliced
   // ELL, 100 w = sliced ELL with w warps per slice, 2..32 = vector CSR with that many
   // lanes per row, -1 = not stored

@@ -239,16 +239,19 @@ void launch_zero(int64_t n, V* x, cudaStream_t s);
 // CSR copy of an operator for the multi-right-hand-side products (row pointers and
 // columns shared by both precisions).
 // Fused correction of the hybrid smoother's aux sweep where G has two +-1 entries per
-// row (the discrete gradient of every level) and A G is stored:
+// row (the discrete gradient of every level; g2) or up to four (the discrete curl of
+// every level: 3 on the finest, 4 on the coarse ones; g4) and A G is stored:
 //   pre  (post = 0): x_i += (G y)_i and r_i -= ((A G) y)_i
 //   post (post = 1): z_i = x_i + (G y)_i + m_i^-1 (r_i - ((A G) y)_i)
-// g2[i] holds row i of G sign-coded (see kSellPad); the sums are formed in the same
-// order as the separate G and A G products with the same number of warps per slice
-// (wps = 1, 2, 4, 8), so the results are identical.
+// g2[i] / g4[i] holds row i of G sign-coded in its stored order, padded with kSellPad
+// (see kSellPad); the sums are formed in the same order as the separate products of G
+// on one warp per slice and of A G with the same number of warps per slice (wps = 1,
+// 2, 4, 8), so the results are identical.
 template <typename V>
 struct AgArgs {
   const V* y = nullptr;    // aux vector
   const int2* g2 = nullptr;
+  const int4* g4 = nullptr;  // instead of g2 where G has three or four entries per row
   V* x = nullptr;          // iterate (read; written in the pre form)
   V* r = nullptr;          // residual (read; written in the pre form)
   const V* minv = nullptr; // post form

@@ -819,13 +819,14 @@ __global__ void __launch_bounds__(kBulkWarps * 32) k_sell_bulk(int nslices, cons
     for (int st = 0; st < kBulkStages; st++) mbar_inval(&bar[2 * st]);
 }
 
-// G y (two sign-coded entries) and A G y for one row per lane (see AgArgs).  WPS warps
+// G y (two sign-coded entries; GW = 4: up to four, padded) and A G y for one row per
+// lane (see AgArgs).  WPS warps
 // share a slice as in k_sell (the first warp starts from r and adds the others'
 // partial sums in warp order, then applies G y and the epilogue).  As in k_sell, the
 // constant slice header, G's row and the first entry pair are loaded before waiting
 // for the previous kernel.
 // C16: the columns as 16-bit offsets from the slice's smallest column (k_sell16).
-template <typename V, bool POST, bool CS, int WPS, bool PF = false, bool C16 = false>
+template <typename V, bool POST, bool CS, int WPS, bool PF = false, bool C16 = false, int GW = 2>
 __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t* __restrict__ sptr,
                                                      const int* __restrict__ srow, const int2* __restrict__ ci2,
                                                      const typename Pair<V>::T* __restrict__ val2, AgArgs<V> a,
@@ -851,6 +852,7 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
     }
   };
   int2 g2 = make_int2(kSellPad, kSellPad);
+  int4 g4 = make_int4(kSellPad, kSellPad, kSellPad, kSellPad);
   int2 cpre[kPre];
   PV vpre[kPre];
 #pragma unroll
@@ -867,7 +869,10 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
     if (C16) base = col_base(sbase, rb, slice, lane), up += p0 + lane;
     else cp += p0 + lane;
     vp += p0 + lane;
-    if (row >= 0 && g == 0) g2 = ldg(a.g2 + row);
+    if (row >= 0 && g == 0) {
+      if (GW == 2) g2 = ldg(a.g2 + row);
+      else g4 = ldg(a.g4 + row);
+    }
     // rows of A G are short (5.4 entries on the H(curl) finest level): the first kPre
     // pairs hold most of a row's entries, so their gathers below go out at once
 #pragma unroll
@@ -878,14 +883,18 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
       }
   }
   pdl_begin();
-  V s = V(0), gx = V(0), ge0 = V(0), ge1 = V(0);
+  V s = V(0), gx = V(0), ge0 = V(0), ge1 = V(0), ge2 = V(0), ge3 = V(0);
   if (row >= 0) {
     // every load that does not depend on another goes out before the first sum
     if (g == 0) {
       s = a.r[row];
       gx = a.x[row];
-      ge0 = signed_entry<false>(a.y, g2.x);
-      ge1 = signed_entry<false>(a.y, g2.y);
+      ge0 = signed_entry<false>(a.y, GW == 2 ? g2.x : g4.x);
+      ge1 = signed_entry<false>(a.y, GW == 2 ? g2.y : g4.y);
+      if (GW == 4) {
+        ge2 = signed_entry<false>(a.y, g4.z);
+        ge3 = signed_entry<false>(a.y, g4.w);
+      }
     }
     V xv[2 * kPre];
 #pragma unroll
@@ -919,6 +928,10 @@ __global__ void __launch_bounds__(kBlock) k_ag_fused(int nslices, const int64_t*
   if (row < 0) return;
   gx += ge0;
   gx += ge1;
+  if (GW == 4) {  // the second entry pair, in the order of G's one-warp product
+    gx += ge2;
+    gx += ge3;
+  }
   if (POST) {
     a.z[row] = fma(a.minv[row], s, gx);
   } else {
@@ -1830,60 +1843,73 @@ void launch_csrv(const DevCsr<V>& M, int lanes, int epi, const SpmvArgs<V>& a, c
 template void launch_csrv<double>(const DevCsr<double>&, int, int, const SpmvArgs<double>&, cudaStream_t);
 template void launch_csrv<float>(const DevCsr<float>&, int, int, const SpmvArgs<float>&, cudaStream_t);
 
-template <typename V, int WPS>
+template <typename V, int WPS, int GW>
 void launch_ag_fused_t(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, bool pf) {
   const int grid = (int)(((int64_t)AG.nslices * WPS + (kBlock / 32) - 1) / (kBlock / 32));
   const int2* ci2 = reinterpret_cast<const int2*>(AG.ci);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(AG.val);
   const int* sb = nullptr;
   const uint32_t* c16 = nullptr;
+#define AMGE_AGF(P, C, F) \
+  launch_k(k_ag_fused<V, P, C, WPS, F, false, GW>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16)
   if (AG.stream && pf && WPS <= 2) {
-    if (post) launch_k(k_ag_fused<V, true, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
-    else launch_k(k_ag_fused<V, false, true, WPS, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
+    if (post) AMGE_AGF(true, true, true);
+    else AMGE_AGF(false, true, true);
   } else if (AG.stream) {
-    if (post) launch_k(k_ag_fused<V, true, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
-    else launch_k(k_ag_fused<V, false, true, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
+    if (post) AMGE_AGF(true, true, false);
+    else AMGE_AGF(false, true, false);
   } else {
-    if (post) launch_k(k_ag_fused<V, true, false, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
-    else launch_k(k_ag_fused<V, false, false, WPS>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a, sb, 0, c16);
+    if (post) AMGE_AGF(true, false, false);
+    else AMGE_AGF(false, false, false);
   }
+#undef AMGE_AGF
 }
 
 // The fused pass with the 16-bit columns (one warp per slice; pf: the slice's entries
 // prefetched into L2 as with code 1000).
-template <typename V, bool CS, bool PF>
+template <typename V, bool CS, bool PF, int GW>
 void launch_ag_fused16_t(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s) {
   const int grid = (AG.nslices + (kBlock / 32) - 1) / (kBlock / 32);
   const auto* v2 = reinterpret_cast<const typename Pair<V>::T*>(AG.val);
   const int2* ci2 = reinterpret_cast<const int2*>(AG.ci);
   if (post)
-    launch_k(k_ag_fused<V, true, CS, 1, PF, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a,
+    launch_k(k_ag_fused<V, true, CS, 1, PF, true, GW>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a,
              (const int*)AG.sbase, AG.c16_rb, (const uint32_t*)AG.c16);
   else
-    launch_k(k_ag_fused<V, false, CS, 1, PF, true>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a,
+    launch_k(k_ag_fused<V, false, CS, 1, PF, true, GW>, grid, kBlock, s, AG.nslices, AG.sptr, AG.srow, ci2, v2, a,
              (const int*)AG.sbase, AG.c16_rb, (const uint32_t*)AG.c16);
+}
+template <typename V, int GW>
+void launch_ag_fused16_g(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, bool pf) {
+  if (AG.stream && pf) launch_ag_fused16_t<V, true, true, GW>(AG, post, a, s);
+  else if (AG.stream) launch_ag_fused16_t<V, true, false, GW>(AG, post, a, s);
+  else launch_ag_fused16_t<V, false, false, GW>(AG, post, a, s);
 }
 template <typename V>
 bool launch_ag_fused16(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, bool pf) {
   if (!AG.c16) return false;
   if (AG.nslices == 0) return true;
-  if (AG.stream && pf) launch_ag_fused16_t<V, true, true>(AG, post, a, s);
-  else if (AG.stream) launch_ag_fused16_t<V, true, false>(AG, post, a, s);
-  else launch_ag_fused16_t<V, false, false>(AG, post, a, s);
+  if (a.g4) launch_ag_fused16_g<V, 4>(AG, post, a, s, pf);
+  else launch_ag_fused16_g<V, 2>(AG, post, a, s, pf);
   return true;
 }
 template bool launch_ag_fused16<double>(const DevSell<double>&, int, const AgArgs<double>&, cudaStream_t, bool);
 template bool launch_ag_fused16<float>(const DevSell<float>&, int, const AgArgs<float>&, cudaStream_t, bool);
 
+template <typename V, int GW>
+void launch_ag_fused_g(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, int wps, bool pf) {
+  switch (wps) {
+    case 2: launch_ag_fused_t<V, 2, GW>(AG, post, a, s, pf); break;
+    case 4: launch_ag_fused_t<V, 4, GW>(AG, post, a, s, pf); break;
+    case 8: launch_ag_fused_t<V, 8, GW>(AG, post, a, s, pf); break;
+    default: launch_ag_fused_t<V, 1, GW>(AG, post, a, s, pf); break;
+  }
+}
 template <typename V>
 void launch_ag_fused(const DevSell<V>& AG, int post, const AgArgs<V>& a, cudaStream_t s, int wps, bool pf) {
   if (AG.nslices == 0) return;
-  switch (wps) {
-    case 2: launch_ag_fused_t<V, 2>(AG, post, a, s, pf); break;
-    case 4: launch_ag_fused_t<V, 4>(AG, post, a, s, pf); break;
-    case 8: launch_ag_fused_t<V, 8>(AG, post, a, s, pf); break;
-    default: launch_ag_fused_t<V, 1>(AG, post, a, s, pf); break;
-  }
+  if (a.g4) launch_ag_fused_g<V, 4>(AG, post, a, s, wps, pf);
+  else launch_ag_fused_g<V, 2>(AG, post, a, s, wps, pf);
 }
 template void launch_ag_fused<double>(const DevSell<double>&, int, const AgArgs<double>&, cudaStream_t, int, bool);
 template void launch_ag_fused<float>(const DevSell<float>&, int, const AgArgs<float>&, cudaStream_t, int, bool);

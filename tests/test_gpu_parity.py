@@ -126,17 +126,20 @@ def test_single_operators(amge, form, n, L, prec, lanes):
                 assert np.all(err <= slack + 1e-300), (l, op, float((err / (bound + 1e-300)).max()))
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("form,prec,gsep", [("hcurl", 0, 200), ("hcurl", 1, 200), ("hdiv", 1, 2000)])
 @pytest.mark.parametrize("ag", [0, 200, 400, 800, 1600])
-def test_fused_aux_correction_equals_separate_products(amge, prec, ag):
-    """H(curl): with G on the one-warp and A G on a sliced-ELL kernel (1, 2, 4 or 8
-    warps per slice, or 16-bit columns) the V-cycle forms x += G y and r -= (A G) y (and the final
-    z = x + G y + m^-1 (r - (A G) y)) in one pass with that many warps per slice.
-    Forcing G onto the two-warp kernel runs the separate products, whose sums are
-    formed in the same order: the V-cycles must agree exactly."""
+def test_fused_aux_correction_equals_separate_products(amge, form, prec, gsep, ag):
+    """With G on the one-warp and A G on a sliced-ELL kernel (1, 2, 4 or 8 warps per
+    slice, or 16-bit columns) the V-cycle forms x += G y and r -= (A G) y (and the final
+    z = x + G y + m^-1 (r - (A G) y)) in one pass with that many warps per slice: H(curl)
+    with the gradient's two entries per row, H(div)'s FP32 V-cycle with the curl's three
+    (finest level) or four (coarse levels).  Forcing G onto another kernel runs the
+    separate products -- for H(curl) the two-warp kernel (its rows are one entry pair),
+    for H(div) the grid-stride one-warp kernel (code 2000) -- whose sums are formed in
+    the same order: the V-cycles must agree exactly."""
     from paper_2107_05613_gb300.inputs import rhs_vector
 
-    h = upload(amge, "hcurl", 24, 3)
+    h = upload(amge, form, 24, 3)
     rep = amge.amge_autotune_report(h)
     pname = "fp64" if prec == 0 else "fp32"
     b = dev(rhs_vector(73, h.n))
@@ -150,7 +153,7 @@ def test_fused_aux_correction_equals_separate_products(amge, prec, ag):
             amge.amge_set_kernel(h, l, pname, "AG", ag)
         amge.amge_vcycle(h, b, zf, precision=prec)
         for l in levels:
-            amge.amge_set_kernel(h, l, pname, "G", 200)
+            amge.amge_set_kernel(h, l, pname, "G", gsep)
         amge.amge_vcycle(h, b, zs, precision=prec)
     finally:
         for l, (g, ag) in saved.items():
