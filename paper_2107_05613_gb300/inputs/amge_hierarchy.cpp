@@ -7,7 +7,9 @@
 // Section 3.3: PV traces (eq. 3.5) extended by the local saddle-point problems of
 // eq. 3.6 (first extension) and eq. 3.8 (further extensions), built in the order
 // L2 -> H(div) -> H(curl) -> H1.  Section 3.2.1: element-based RAP for coarse local
-// and global matrices.
+// and global matrices.  Optionally (AMGH_TARGETS), Sections 3.3.1 / 3.3.3: polynomial
+// approximation targets projected onto the D-free bubbles of the last coarsening's
+// coarse entities, filtered of linear dependence and added to the coarsest space.
 //
 // Everything is double precision and sequential per entity; entities are processed
 // in parallel with OpenMP (each prolongator entry is written by exactly one task).
@@ -1213,6 +1215,10 @@ struct Hier {
   std::vector<std::array<DCsr, 4>> Pi;
   std::vector<std::array<DCsr, 3>> pihat;
   double diag[4] = {0, 0, 0, 0};
+  // approximation targets (AMGH_TARGETS): coarse basis functions added, and the largest
+  // relative divergence of one of them on a constituent cell
+  int64_t target_functions = 0;
+  double target_constraint = 0;
 };
 
 // ------------------------------------------------------------ auxiliary-space data
@@ -1345,10 +1351,500 @@ void build_aux(Hier* H) {
   }
 }
 
-Hier* build(int form, int n, int num_levels, const double* beta, const double* alpha, int all_spaces) {
+// ------------------------------------------- approximation targets (Section 3.3.1)
+// Eigendecomposition of a small symmetric matrix by cyclic Jacobi rotations: A (n x n,
+// row-major, destroyed) -> eigenvalues w (descending) and eigenvectors in the columns
+// of V (row-major).
+void sym_eig(int n, double* A, double* w, double* V) {
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) V[i * n + j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 64; sweep++) {
+    double off = 0, tot = 0;
+    for (int i = 0; i < n; i++)
+      for (int j = 0; j < n; j++) (i == j ? tot : off) += A[i * n + j] * A[i * n + j];
+    if (off <= 1e-30 * (tot + off)) break;
+    for (int p = 0; p < n; p++)
+      for (int q = p + 1; q < n; q++) {
+        const double apq = A[p * n + q];
+        if (apq == 0.0) continue;
+        // rotation zeroing A[p][q]: t = tan of the angle, the smaller root
+        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; k++) {  // A <- A J (columns p, q)
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - sn * akq;
+          A[k * n + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; k++) {  // A <- J^T A (rows p, q)
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - sn * aqk;
+          A[q * n + k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < n; k++) {  // V <- V J
+          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - sn * vkq;
+          V[k * n + q] = sn * vkp + c * vkq;
+        }
+      }
+  }
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; i++) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return A[a * n + a] > A[b * n + b]; });
+  std::vector<double> Vs((size_t)n * n);
+  for (int j = 0; j < n; j++) {
+    w[j] = A[ord[j] * n + ord[j]];
+    for (int i = 0; i < n; i++) Vs[(size_t)i * n + j] = V[i * n + ord[j]];
+  }
+  std::copy(Vs.begin(), Vs.end(), V);
+}
+
+// The approximation targets of space k (1 edges, 2 faces) at `level`: the finite
+// element interpolants, on the finest level, of the vector monomials up to degree one
+// -- the constant fields e_i and the linear fields x_j e_i (twelve) -- through the
+// interpolation of continuous linear vector fields (exact for them), carried to
+// `level` by the co-chain projectors of the transfers before it (the signed sum over
+// each coarse entity's chain), as Section 3.3.1 transfers targets to coarse levels.
+using Targets = std::vector<std::vector<double>>;
+Targets space_targets(const Hier* H, int level, int k) {
+  const Level& L0 = H->levels[0];
+  const DCsr ph = fine_pihat(L0, k);
+  std::vector<double> xv((size_t)3 * L0.cnt[0]);
+  for (int64_t v = 0; v < L0.cnt[0]; v++) vert_coord(L0, (int)v, &xv[3 * v]);
+  Targets t(12, std::vector<double>(ph.nr, 0.0));
+  for (int e = 0; e < ph.nr; e++)
+    for (int64_t p = ph.a.rp[e]; p < ph.a.rp[e + 1]; p++) {
+      const int v = ph.a.ci[p] / 3, c = ph.a.ci[p] % 3;
+      t[c][e] += ph.v[p];  // e_c
+      for (int j = 0; j < 3; j++) t[3 + 3 * c + j][e] += ph.v[p] * xv[3 * (size_t)v + j];  // x_j e_c
+    }
+  for (int l = 0; l < level; l++) {
+    const Transfer& T = H->transfers[l];
+    for (auto& tc : t) {
+      std::vector<double> u(T.cons[k].rows(), 0.0);
+      for (int X = 0; X < T.cons[k].rows(); X++)
+        for (int64_t p = T.cons[k].rp[X]; p < T.cons[k].rp[X + 1]; p++)
+          u[X] += (double)T.phi[k][p] * tc[T.cons[k].ci[p]];
+      tc.swap(u);
+    }
+  }
+  return t;
+}
+
+// Relative eigenvalue below which a projected target counts as linearly dependent.
+constexpr double kTargetTol = 1e-10;
+
+struct BubbleStats {
+  int64_t count = 0;
+  double constraint = 0;  // max |D psi| / max |psi| over the kept functions psi (face space)
+};
+
+// P with the columns in extra[row] (above P's own, any order within a row) appended;
+// the columns become next.
+void append_columns(DCsr& P, std::vector<std::vector<std::pair<int, double>>>& extra, int next, BubbleStats& st) {
+  st.count += next - P.nc;
+  DCsr Q;
+  Q.nr = P.nr, Q.nc = next;
+  Q.a.rp.assign(P.nr + 1, 0);
+  for (int i = 0; i < P.nr; i++) {
+    std::sort(extra[i].begin(), extra[i].end());
+    Q.a.rp[i + 1] = Q.a.rp[i] + P.a.len(i) + (int64_t)extra[i].size();
+  }
+  Q.a.ci.resize(Q.a.rp[P.nr]);
+  Q.v.resize(Q.a.rp[P.nr]);
+  for (int i = 0; i < P.nr; i++) {
+    int64_t o = Q.a.rp[i];
+    for (int64_t p = P.a.rp[i]; p < P.a.rp[i + 1]; p++, o++) Q.a.ci[o] = P.a.ci[p], Q.v[o] = P.v[p];
+    for (const auto& e : extra[i]) Q.a.ci[o] = e.first, Q.v[o++] = e.second;
+  }
+  P = std::move(Q);
+}
+
+// Linear-dependence filter of Section 3.3.1: phi holds the nt projected targets on nI
+// dofs (phi[a * nt + c]), Mi(a, b) the mass between dofs a and b.  The eigenvectors of
+// their mass Gram matrix whose eigenvalues exceed kTargetTol * tau (tau: the largest
+// target's squared mass norm on the entity) give the kept functions, mass-orthonormal
+// and in descending eigenvalue order, appended to out (nI values each).
+template <class MassAt>
+int filter_targets(int nI, int nt, const std::vector<double>& phi, MassAt Mi, double tau, std::vector<double>& out) {
+  std::vector<double> Mp((size_t)nI * nt, 0.0), Gm((size_t)nt * nt), w(nt), V((size_t)nt * nt);
+  for (int a = 0; a < nI; a++)
+    for (int b = 0; b < nI; b++) {
+      const double m = Mi(a, b);
+      if (m == 0.0) continue;
+      for (int c = 0; c < nt; c++) Mp[(size_t)a * nt + c] += m * phi[(size_t)b * nt + c];
+    }
+  for (int c = 0; c < nt; c++)
+    for (int e = 0; e <= c; e++) {
+      double g = 0;
+      for (int a = 0; a < nI; a++) g += phi[(size_t)a * nt + c] * Mp[(size_t)a * nt + e];
+      Gm[(size_t)c * nt + e] = Gm[(size_t)e * nt + c] = g;
+    }
+  sym_eig(nt, Gm.data(), w.data(), V.data());
+  int kept = 0;
+  for (int i = 0; i < nt; i++) {
+    if (!(w[i] > kTargetTol * tau)) break;  // descending
+    const double sc = 1.0 / std::sqrt(w[i]);
+    for (int a = 0; a < nI; a++) {
+      double v = 0;
+      for (int c = 0; c < nt; c++) v += V[(size_t)c * nt + i] * phi[(size_t)a * nt + c];
+      out.push_back(v * sc);
+    }
+    kept++;
+  }
+  return kept;
+}
+
+// (M t)_i over the dofs S of an entity for every target, and the largest t^T M t.
+double mass_targets(const std::vector<double>& M, const int* S, int nS, const Targets& tgt, std::vector<double>& mt) {
+  const int nt = (int)tgt.size();
+  mt.assign((size_t)nS * nt, 0.0);
+  double tau = 0;
+  for (int c = 0; c < nt; c++) {
+    double tMt = 0;
+    for (int i = 0; i < nS; i++) {
+      double v = 0;
+      for (int j = 0; j < nS; j++) v += M[(size_t)i * nS + j] * tgt[c][S[j]];
+      mt[(size_t)i * nt + c] = v;
+      tMt += tgt[c][S[i]] * v;
+    }
+    tau = std::max(tau, tMt);
+  }
+  return tau;
+}
+
+// D-free bubbles of the face space (Section 3.3.3) for one coarsening: per coarse cell
+// X, each target is projected in the mass inner product of X onto X's div-free bubbles
+// -- face functions on X's interior faces, zero on its boundary faces, with zero
+// divergence on every constituent cell (one constraint per constituent but the last:
+// for such functions the constituents' divergences sum to zero identically) -- and
+// the projections are filtered of linear dependence (filter_targets).  The kept
+// functions are appended to P (space 2) as columns after the coarse faces, cell by
+// cell.  (For the constant fields the projection vanishes: a constant field is mass-
+// orthogonal to the curls of edge bubbles, which span these bubbles.)
+void add_div_bubbles(const Level& L, const Transfer& T, DCsr& P, const Targets& tgt, BubbleStats& st) {
+  const int nt = (int)tgt.size();
+  const int nX = T.cons[3].rows();
+  std::vector<std::vector<double>> vals(nX);
+  std::vector<std::vector<int>> rowsX(nX);
+  std::vector<int> nkeep(nX, 0);
+  double cmax = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : cmax)
+  for (int X = 0; X < nX; X++) {
+    std::vector<double> M, buf, Dm, K, R, mt;
+    const int* S = T.fclo[3][2].row(X);
+    const int nS = T.fclo[3][2].len(X);
+    const uint8_t* in = T.fint[3][2].data() + T.fclo[3][2].rp[X];
+    std::vector<int> I;
+    for (int i = 0; i < nS; i++)
+      if (in[i]) I.push_back(i);
+    const int nI = (int)I.size();
+    const int* S3 = T.cons[3].row(X);
+    const int n3 = T.cons[3].len(X);
+    if (nI == 0 || n3 < 2) continue;
+    assemble_mass(L, T, 3, 2, X, S, nS, M, buf);
+    restrict_D(L.D[2], S3, n3, S, nS, Dm);
+    const int nc = n3 - 1, n = nI + nc;
+    K.assign((size_t)n * n, 0.0);
+    R.assign((size_t)n * nt, 0.0);
+    for (int a = 0; a < nI; a++)
+      for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
+    for (int r = 0; r < nc; r++)
+      for (int b = 0; b < nI; b++) {
+        const double v = Dm[(size_t)r * nS + I[b]];
+        K[(size_t)(nI + r) * n + b] = v;
+        K[(size_t)b * n + nI + r] = v;
+      }
+    const double tau = mass_targets(M, S, nS, tgt, mt);
+    for (int a = 0; a < nI; a++)
+      for (int c = 0; c < nt; c++) R[(size_t)a * nt + c] = mt[(size_t)I[a] * nt + c];
+    if (!lu_solve(n, K.data(), nt, R.data())) throw Fail("singular bubble projection");
+    R.resize((size_t)nI * nt);
+    nkeep[X] = filter_targets(nI, nt, R, [&](int a, int b) { return M[(size_t)I[a] * nS + I[b]]; }, tau, vals[X]);
+    // the divergence of each kept function on every constituent, the dropped one included
+    for (int i = 0; i < nkeep[X]; i++) {
+      const double* psi = vals[X].data() + (size_t)i * nI;
+      double pm = 0;
+      for (int a = 0; a < nI; a++) pm = std::max(pm, std::fabs(psi[a]));
+      for (int r = 0; r < n3; r++) {
+        double d = 0;
+        for (int b = 0; b < nI; b++) d += Dm[(size_t)r * nS + I[b]] * psi[b];
+        if (pm > 0) cmax = std::max(cmax, std::fabs(d) / pm);
+      }
+    }
+    for (int a = 0; a < nI; a++) rowsX[X].push_back(S[I[a]]);
+  }
+  st.constraint = std::max(st.constraint, cmax);
+  std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
+  int next = P.nc;
+  for (int X = 0; X < nX; X++) {
+    const int nI = (int)rowsX[X].size();
+    for (int i = 0; i < nkeep[X]; i++, next++)
+      for (int a = 0; a < nI; a++) {
+        const double v = vals[X][(size_t)i * nI + a];
+        if (v != 0.0) extra[rowsX[X][a]].emplace_back(next, v);
+      }
+  }
+  append_columns(P, extra, next, st);
+}
+
+// D-free bubbles of the edge space on a coarse face or cell Y (dim d = 2 or 3,
+// Section 3.3.3): the curl-free edge functions vanishing on Y's boundary, which on the
+// contractible Y are the gradients of the vertex functions interior to Y (exactness of
+// the finer sequence), Z = D_0[interior edges, interior vertices].  Each target is
+// projected onto span Z in Y's mass inner product, (Z^T M_II Z) y = Z^T (M t)_I, and
+// the projections are filtered (filter_targets).  Returns the kept functions (nI
+// values each, on the interior edges of Y listed in `rows`).  (A constant field is
+// mass-orthogonal to every gradient bubble, so only the linear targets contribute.)
+std::vector<double> grad_bubbles(const Level& L, const Transfer& T, int d, int Y, const Targets& tgt,
+                                 std::vector<int>& rows, int& nkeep) {
+  const int nt = (int)tgt.size();
+  nkeep = 0;
+  rows.clear();
+  std::vector<double> out, M, buf, Z, mt;
+  const int* S = T.fclo[d][1].row(Y);
+  const int nS = T.fclo[d][1].len(Y);
+  const uint8_t* in = T.fint[d][1].data() + T.fclo[d][1].rp[Y];
+  std::vector<int> I, vI;
+  for (int i = 0; i < nS; i++)
+    if (in[i]) I.push_back(i), rows.push_back(S[i]);
+  const int* SV = T.fclo[d][0].row(Y);
+  const uint8_t* inV = T.fint[d][0].data() + T.fclo[d][0].rp[Y];
+  for (int i = 0; i < T.fclo[d][0].len(Y); i++)
+    if (inV[i]) vI.push_back(SV[i]);
+  const int nI = (int)I.size(), nv = (int)vI.size();
+  if (nI == 0 || nv == 0) return out;
+  assemble_mass(L, T, d, 1, Y, S, nS, M, buf);
+  restrict_D(L.D[0], rows.data(), nI, vI.data(), nv, Z);  // nI x nv
+  std::vector<double> MZ((size_t)nI * nv, 0.0), K((size_t)nv * nv, 0.0), R((size_t)nv * nt, 0.0);
+  for (int a = 0; a < nI; a++)
+    for (int b = 0; b < nI; b++) {
+      const double m = M[(size_t)I[a] * nS + I[b]];
+      if (m == 0.0) continue;
+      for (int j = 0; j < nv; j++) MZ[(size_t)a * nv + j] += m * Z[(size_t)b * nv + j];
+    }
+  for (int i = 0; i < nv; i++)
+    for (int j = 0; j < nv; j++) {
+      double v = 0;
+      for (int a = 0; a < nI; a++) v += Z[(size_t)a * nv + i] * MZ[(size_t)a * nv + j];
+      K[(size_t)i * nv + j] = v;
+    }
+  const double tau = mass_targets(M, S, nS, tgt, mt);
+  for (int j = 0; j < nv; j++)
+    for (int c = 0; c < nt; c++) {
+      double v = 0;
+      for (int a = 0; a < nI; a++) v += Z[(size_t)a * nv + j] * mt[(size_t)I[a] * nt + c];
+      R[(size_t)j * nt + c] = v;
+    }
+  if (!lu_solve(nv, K.data(), nt, R.data())) throw Fail("singular gradient-bubble projection");
+  std::vector<double> phi((size_t)nI * nt, 0.0);  // projections on the interior edges
+  for (int a = 0; a < nI; a++)
+    for (int c = 0; c < nt; c++) {
+      double v = 0;
+      for (int j = 0; j < nv; j++) v += Z[(size_t)a * nv + j] * R[(size_t)j * nt + c];
+      phi[(size_t)a * nt + c] = v;
+    }
+  nkeep = filter_targets(nI, nt, phi, [&](int a, int b) { return M[(size_t)I[a] * nS + I[b]]; }, tau, out);
+  return out;
+}
+
+// Extension of nJ edge-space traces from the boundary of coarse cell X into its
+// interior by the local problem of eq. 3.8 (the same system as `extend` solves for the
+// PV-based functions): unknowns the interior edge values and chi on X's interior faces,
+// with boundary data phiB (nB x nJ, X's boundary edges in closure order) and target
+// s = 0 -- the traces extended here are curl-free on the faces they live on, so their
+// coarse derivative, and with it s, vanishes.  Returns the interior values (nI x nJ).
+std::vector<double> extend_cell_zero_target(const Level& L, const Transfer& T, int X, const std::vector<double>& phiB,
+                                            int nJ) {
+  const int k = 1, d = 3;
+  std::vector<double> M, W, W2, Dm, D2m, buf, K, R;
+  const int* S = T.fclo[d][k].row(X);
+  const int nS = T.fclo[d][k].len(X);
+  const uint8_t* in = T.fint[d][k].data() + T.fclo[d][k].rp[X];
+  std::vector<int> I, B;
+  for (int i = 0; i < nS; i++) (in[i] ? I : B).push_back(i);
+  const int nI = (int)I.size(), nB = (int)B.size();
+  const int* S1 = T.fclo[d][k + 1].row(X);
+  const int n1 = T.fclo[d][k + 1].len(X);
+  const uint8_t* in1 = T.fint[d][k + 1].data() + T.fclo[d][k + 1].rp[X];
+  const int* S2 = T.fclo[d][k + 2].row(X);
+  const int n2 = T.fclo[d][k + 2].len(X);
+  std::vector<int> I1;
+  for (int i = 0; i < n1; i++)
+    if (in1[i]) I1.push_back(i);
+  const int nI1 = (int)I1.size();
+  assemble_mass(L, T, d, k, X, S, nS, M, buf);
+  assemble_mass(L, T, d, k + 1, X, S1, n1, W, buf);
+  assemble_mass(L, T, d, k + 2, X, S2, n2, W2, buf);
+  restrict_D(L.D[k], S1, n1, S, nS, Dm);
+  restrict_D(L.D[k + 1], S2, n2, S1, n1, D2m);
+  // target t = 0 - D_B phi_B on all faces of X
+  std::vector<double> tgt((size_t)n1 * nJ, 0.0);
+  for (int a = 0; a < n1; a++)
+    for (int b = 0; b < nB; b++) {
+      const double dv = Dm[(size_t)a * nS + B[b]];
+      if (dv == 0.0) continue;
+      for (int j = 0; j < nJ; j++) tgt[(size_t)a * nJ + j] -= dv * phiB[(size_t)b * nJ + j];
+    }
+  const int n = nI + nI1;
+  K.assign((size_t)n * n, 0.0);
+  R.assign((size_t)n * nJ, 0.0);
+  for (int a = 0; a < nI; a++)
+    for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
+  for (int a = 0; a < nI1; a++)
+    for (int b = 0; b < nI; b++) {
+      double v = 0;
+      for (int c = 0; c < nI1; c++) v += W[(size_t)I1[a] * n1 + I1[c]] * Dm[(size_t)I1[c] * nS + I[b]];
+      K[(size_t)(nI + a) * n + b] = v;
+      K[(size_t)b * n + nI + a] = v;
+    }
+  std::vector<double> W2D((size_t)n2 * nI1, 0.0);
+  for (int a = 0; a < n2; a++)
+    for (int c = 0; c < n2; c++) {
+      const double w = W2[(size_t)a * n2 + c];
+      if (w == 0.0) continue;
+      for (int b = 0; b < nI1; b++) W2D[(size_t)a * nI1 + b] += w * D2m[(size_t)c * n1 + I1[b]];
+    }
+  for (int a = 0; a < nI1; a++)
+    for (int b = 0; b < nI1; b++) {
+      double v = 0;
+      for (int c = 0; c < n2; c++) v += D2m[(size_t)c * n1 + I1[a]] * W2D[(size_t)c * nI1 + b];
+      K[(size_t)(nI + a) * n + nI + b] = -v;
+    }
+  for (int j = 0; j < nJ; j++) {
+    for (int a = 0; a < nI; a++) {
+      double v = 0;
+      for (int b = 0; b < nB; b++) v += M[(size_t)I[a] * nS + B[b]] * phiB[(size_t)b * nJ + j];
+      R[(size_t)a * nJ + j] = -v;
+    }
+    for (int a = 0; a < nI1; a++) {
+      double v = 0;
+      for (int c = 0; c < n1; c++) v += W[(size_t)I1[a] * n1 + c] * tgt[(size_t)c * nJ + j];
+      R[(size_t)(nI + a) * nJ + j] = v;
+    }
+  }
+  if (!lu_solve(n, K.data(), nJ, R.data())) throw Fail("singular extension of a face bubble");
+  R.resize((size_t)nI * nJ);
+  return R;
+}
+
+// Approximation targets of the edge space for one coarsening (Section 3.3.1 with the
+// D-free bubbles of Section 3.3.3): on every coarse face F the targets' projections
+// onto F's gradient bubbles, extended into the cells that share F by eq. 3.8; then in
+// every coarse cell X its own gradient bubbles.  The constant fields' tangential
+// traces on the straight coarse edges are multiples of the PV traces and add nothing
+// there.  The functions are appended to P (space 1) after the coarse edges: the face
+// functions face by face, then the cell functions cell by cell.
+void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P, const Targets& tgt,
+                      BubbleStats& st) {
+  const int nF = T.cons[2].rows(), nX = T.cons[3].rows();
+  std::vector<std::vector<double>> fv(nF), cv(nX);
+  std::vector<std::vector<int>> frows(nF), crows(nX);
+  std::vector<int> fk(nF, 0), ck(nX, 0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int F = 0; F < nF; F++) fv[F] = grad_bubbles(L, T, 2, F, tgt, frows[F], fk[F]);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int X = 0; X < nX; X++) cv[X] = grad_bubbles(L, T, 3, X, tgt, crows[X], ck[X]);
+  std::vector<int> ffirst(nF), cfirst(nX);
+  int next = P.nc;
+  for (int F = 0; F < nF; F++) ffirst[F] = next, next += fk[F];
+  for (int X = 0; X < nX; X++) cfirst[X] = next, next += ck[X];
+  // the face functions' extensions into every cell X, with the traces of all X's faces
+  std::vector<std::vector<double>> xv(nX);
+  std::vector<std::vector<int>> xcol(nX);
+  std::vector<std::vector<int>> xrows(nX);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int X = 0; X < nX; X++) {
+    const int* S = T.fclo[3][1].row(X);
+    const int nS = T.fclo[3][1].len(X);
+    const uint8_t* in = T.fint[3][1].data() + T.fclo[3][1].rp[X];
+    std::vector<int> Bpos;
+    for (int i = 0; i < nS; i++)
+      if (in[i]) xrows[X].push_back(S[i]);
+      else Bpos.push_back(i);
+    const int* Fx = C.clo[3][2].row(X);
+    const int nFx = C.clo[3][2].len(X);
+    int nJ = 0;
+    for (int q = 0; q < nFx; q++) nJ += fk[Fx[q]];
+    if (nJ == 0 || xrows[X].empty()) continue;
+    std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
+    int j0 = 0;
+    for (int q = 0; q < nFx; q++) {
+      const int F = Fx[q];
+      const int nIF = (int)frows[F].size();
+      for (int i = 0; i < fk[F]; i++) {
+        xcol[X].push_back(ffirst[F] + i);
+        for (int a = 0; a < nIF; a++) {  // F's interior edges among X's boundary edges
+          const int e = frows[F][a];
+          const int* pos = std::lower_bound(S, S + nS, e);
+          const int bi = (int)(std::lower_bound(Bpos.begin(), Bpos.end(), (int)(pos - S)) - Bpos.begin());
+          phiB[(size_t)bi * nJ + j0 + i] = fv[F][(size_t)i * nIF + a];
+        }
+      }
+      j0 += fk[F];
+    }
+    xv[X] = extend_cell_zero_target(L, T, X, phiB, nJ);
+  }
+  std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
+  for (int F = 0; F < nF; F++) {
+    const int nIF = (int)frows[F].size();
+    for (int i = 0; i < fk[F]; i++)
+      for (int a = 0; a < nIF; a++)
+        if (fv[F][(size_t)i * nIF + a] != 0.0) extra[frows[F][a]].emplace_back(ffirst[F] + i, fv[F][(size_t)i * nIF + a]);
+  }
+  for (int X = 0; X < nX; X++) {
+    const int nI = (int)xrows[X].size(), nJ = (int)xcol[X].size();
+    for (int a = 0; a < nI && nJ > 0; a++)
+      for (int j = 0; j < nJ; j++)
+        if (xv[X][(size_t)a * nJ + j] != 0.0) extra[xrows[X][a]].emplace_back(xcol[X][j], xv[X][(size_t)a * nJ + j]);
+    const int nIX = (int)crows[X].size();
+    for (int i = 0; i < ck[X]; i++)
+      for (int a = 0; a < nIX; a++)
+        if (cv[X][(size_t)i * nIX + a] != 0.0) extra[crows[X][a]].emplace_back(cfirst[X] + i, cv[X][(size_t)i * nIX + a]);
+  }
+  append_columns(P, extra, next, st);
+}
+
+DCsr transpose_d(const DCsr& A) {
+  DCsr T;
+  T.nr = A.nc, T.nc = A.nr;
+  T.a.rp.assign(A.nc + 1, 0);
+  for (int64_t p = 0; p < A.a.rp[A.nr]; p++) T.a.rp[A.a.ci[p] + 1]++;
+  for (int j = 0; j < A.nc; j++) T.a.rp[j + 1] += T.a.rp[j];
+  T.a.ci.resize(A.a.rp[A.nr]);
+  T.v.resize(A.a.rp[A.nr]);
+  std::vector<int64_t> at(T.a.rp.begin(), T.a.rp.end() - 1);
+  for (int i = 0; i < A.nr; i++)  // rows in order: each column's entries come out sorted
+    for (int64_t p = A.a.rp[i]; p < A.a.rp[i + 1]; p++) {
+      const int64_t q = at[A.a.ci[p]]++;
+      T.a.ci[q] = i, T.v[q] = A.v[p];
+    }
+  return T;
+}
+
+// Galerkin product P^T A P, made exactly symmetric (its pattern is symmetric: the
+// mean of the two mirrored entries).
+DCsr galerkin(const DCsr& A, const DCsr& P) {
+  DCsr C = spgemm(transpose_d(P), spgemm(A, P));
+  for (int i = 0; i < C.nr; i++)
+    for (int64_t p = C.a.rp[i]; p < C.a.rp[i + 1]; p++) {
+      const int j = C.a.ci[p];
+      if (j <= i) continue;
+      const int q = C.a.find(j, i);
+      REQUIRE(q >= 0, "Galerkin pattern not symmetric");
+      const double m = 0.5 * (C.v[p] + C.v[C.a.rp[j] + q]);
+      C.v[p] = C.v[C.a.rp[j] + q] = m;
+    }
+  return C;
+}
+
+Hier* build(int form, int n, int num_levels, const double* beta, const double* alpha, int flags) {
   auto t0 = std::chrono::steady_clock::now();
   REQUIRE(form == AMGH_FORM_HCURL || form == AMGH_FORM_HDIV, "form");
   REQUIRE(n >= 1 && n <= 127, "n out of range");
+  REQUIRE((flags & ~(AMGH_ALL_SPACES | AMGH_TARGETS)) == 0, "unknown flags");
+  const bool all_spaces = (flags & AMGH_ALL_SPACES) != 0, targets = (flags & AMGH_TARGETS) != 0;
+  REQUIRE(!(targets && all_spaces), "approximation targets and the auxiliary-space data exclude each other");
   Hier* H = new Hier;
   try {
     H->form_k = form;  // H(curl) -> space 1, H(div) -> space 2
@@ -1370,6 +1866,7 @@ Hier* build(int form, int n, int num_levels, const double* beta, const double* a
     H->transfers.resize(nl - 1);
     { Stage s("fine mesh"); build_fine(H->levels[0], n, beta, alpha); }
     ExtStats st;
+    BubbleStats bst;
     double incid = 0;
     { Stage s("assemble A0"); H->A.push_back(assemble_global(H->levels[0], kf)); }
     for (int l = 0; l + 1 < nl; l++) {
@@ -1382,6 +1879,15 @@ Hier* build(int form, int n, int num_levels, const double* beta, const double* a
       for (int k = 3; k >= kmin; k--) { Stage s("prolongator"); build_P(L, C, T, k, st); }
       { Stage s("coarse local RAP"); coarse_local(L, C, T, kmin, kf); }
       { Stage s("assemble coarse A"); H->A.push_back(assemble_global(C, kf)); }
+      if (targets && l + 2 == nl) {
+        // the last coarsening: the targets' D-free bubbles join the coarsest space,
+        // whose matrix is then the Galerkin product with the enlarged prolongator
+        Stage s("approximation targets");
+        const Targets tg = space_targets(H, l, kf);
+        if (kf == 2) add_div_bubbles(L, T, T.P[kf], tg, bst);
+        else add_curl_bubbles(L, C, T, T.P[kf], tg, bst);
+        H->A[l + 1] = galerkin(H->A[l], T.P[kf]);
+      }
       // the finer level's local data is no longer needed
       if (!L.fine) {
         for (int d = 0; d < 4; d++)
@@ -1405,6 +1911,8 @@ Hier* build(int form, int n, int num_levels, const double* beta, const double* a
     H->diag[1] = st.resid;
     H->diag[2] = incid;
     H->diag[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    H->target_functions = bst.count;
+    H->target_constraint = bst.constraint;
   } catch (...) {
     delete H;
     throw;
@@ -1424,7 +1932,7 @@ extern "C" {
 
 const char* amgh_error(void) { return g_err.c_str(); }
 
-int amgh_build(int form, int n, int num_levels, const double* beta, const double* alpha, int all_spaces,
+int amgh_build(int form, int n, int num_levels, const double* beta, const double* alpha, int flags,
                int nthreads, void** out) {
   if (!out) {
     g_err = "out is NULL";
@@ -1437,7 +1945,7 @@ int amgh_build(int form, int n, int num_levels, const double* beta, const double
   (void)nthreads;
 #endif
   try {
-    *out = build(form, n, num_levels, beta, alpha, all_spaces);
+    *out = build(form, n, num_levels, beta, alpha, flags);
     return 0;
   } catch (const std::exception& e) {
     g_err = e.what();
@@ -1503,6 +2011,14 @@ int amgh_diagnostics(const void* h, double out[4]) {
   const Hier* H = (const Hier*)h;
   if (!H) return 1;
   for (int i = 0; i < 4; i++) out[i] = H->diag[i];
+  return 0;
+}
+
+int amgh_target_info(const void* h, int64_t* functions, double* constraint) {
+  const Hier* H = (const Hier*)h;
+  if (!H || !functions || !constraint) return 1;
+  *functions = H->target_functions;
+  *constraint = H->target_constraint;
   return 0;
 }
 

@@ -29,19 +29,27 @@ extern "C" {
 
 enum { AMGH_FORM_HCURL = 1, AMGH_FORM_HDIV = 2 };
 enum { AMGH_KIND_A = 0, AMGH_KIND_P = 1, AMGH_KIND_D = 2, AMGH_KIND_PI = 3, AMGH_KIND_PIHAT = 4 };
+enum { AMGH_ALL_SPACES = 1, AMGH_TARGETS = 2 };
 
 /* Build the hierarchy on an n^3 Kuhn-split unit cube.
  *   form        AMGH_FORM_HCURL (Nedelec edges) or AMGH_FORM_HDIV (Raviart-Thomas faces)
  *   num_levels  >= 1; 0 = coarsen 2x2x2 while the cell grid side m > 8 (and m even)
  *   beta, alpha per fine tetrahedron (6 n^3 values, tet t = 6*cube + permutation),
  *               NULL = all ones.  Must be > 0.
- *   all_spaces  1 = also build the prolongators of every lower space of the
- *               sequence (H1 for H(curl), H(curl) and H1 for H(div)); 0 = only
- *               the spaces the problem needs.
+ *   flags       AMGH_ALL_SPACES: also build the prolongators of every lower space of
+ *               the sequence (H1 for H(curl), H(curl) and H1 for H(div)) and the
+ *               auxiliary-space data; otherwise only the spaces the problem needs.
+ *               AMGH_TARGETS (H(div) only, not with AMGH_ALL_SPACES): polynomial
+ *               approximation targets (Section 3.3.1) -- the interpolants of the
+ *               constant vector fields -- enrich the last coarsening: per coarse
+ *               cell, their mass projections onto its div-free bubbles, filtered of
+ *               linear dependence (Section 3.3.3's D-free bubbles), become extra
+ *               coarse basis functions (columns of P after the coarse faces), and the
+ *               coarsest matrix is the Galerkin product P^T A P with that P.
  *   nthreads    OpenMP threads (<= 0: library default).
  * Returns 0 and a handle in *out, or nonzero with amgh_error() describing it. */
 int amgh_build(int form, int n, int num_levels, const double* beta, const double* alpha,
-               int all_spaces, int nthreads, void** out);
+               int flags, int nthreads, void** out);
 const char* amgh_error(void);
 int amgh_num_levels(const void* h);
 /* entity counts V, E, F, T at a level */
@@ -62,6 +70,9 @@ int amgh_matrix_copy(const void* h, int kind, int level, int k, int32_t* row_ptr
  *              [2] max disagreement of coarse incidence over constituent choices,
  *              [3] setup seconds */
 int amgh_diagnostics(const void* h, double out[4]);
+/* approximation targets (AMGH_TARGETS): the coarse basis functions added and the
+ * largest relative divergence of one of them on a constituent cell (0 without) */
+int amgh_target_info(const void* h, int64_t* functions, double* constraint);
 /* Fine-level assembly of the problem matrix A_0 written as a gather, for re-assembling
  * it from new coefficients: every stored entry q of A_0 (the CSR order of
  * amgh_matrix_copy) is the sum, in order, of

@@ -43,6 +43,7 @@ def _load():
     lib.amgh_matrix_copy.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.amgh_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    lib.amgh_target_info.argtypes = [ctypes.c_void_p, i64p, ctypes.POINTER(ctypes.c_double)]
     lib.amgh_free.argtypes = [ctypes.c_void_p]
     lib.amgh_free.restype = None
     lib.amgh_fine_assembly_info.argtypes = [ctypes.c_void_p, i64p, ctypes.POINTER(ctypes.c_int)]
@@ -117,13 +118,18 @@ def _copy(lib, h, kind, level, k):
 
 
 def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=None,
-                    all_spaces: bool = False, nthreads: int = 0, assembly: bool = False) -> Hierarchy:
+                    all_spaces: bool = False, nthreads: int = 0, assembly: bool = False,
+                    targets: bool = False) -> Hierarchy:
     """Build the hierarchy on an n^3 Kuhn-split cube (6 n^3 tetrahedra).
 
     beta, alpha: per-tet coefficients of (Du, Dv) and (u, v) (None = 1).
     num_levels: 0 = coarsen 2x2x2 while the cell grid side m > 8.
     assembly: also return the fine assembly of A_0 as a gather (diagnostics
     "assembly": dict of K, M [6, s, s], coff, ccell, cidx; see amge_hierarchy.h).
+    targets: (H(div)) enrich the last coarsening with the D-free bubbles of the
+    constant-field approximation targets (Sections 3.3.1, 3.3.3; AMGH_TARGETS in
+    amge_hierarchy.h): P[-1] gains columns after the coarse faces and A[-1] is
+    P[-1]^T A[-2] P[-1]; diagnostics "target_functions", "target_constraint".
     """
     lib = _load()
     kf = FORMS[form]
@@ -134,8 +140,9 @@ def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=Non
         if arr is not None and arr.shape != (nt,):
             raise ValueError(f"coefficient array must have {nt} entries")
     h = ctypes.c_void_p()
+    flags = (1 if all_spaces else 0) | (2 if targets else 0)   # AMGH_ALL_SPACES, AMGH_TARGETS
     rc = lib.amgh_build(kf, n, num_levels, None if b is None else b.ctypes.data,
-                        None if a is None else a.ctypes.data, int(all_spaces), nthreads, ctypes.byref(h))
+                        None if a is None else a.ctypes.data, flags, nthreads, ctypes.byref(h))
     if rc != 0:
         raise RuntimeError("hierarchy generator: " + lib.amgh_error().decode())
     try:
@@ -158,6 +165,9 @@ def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=Non
         d = (ctypes.c_double * 4)()
         lib.amgh_diagnostics(h, d)
         diag = {"lambda_dev": d[0], "local_residual": d[1], "incidence_dev": d[2], "seconds": d[3]}
+        nf, tc = ctypes.c_int64(), ctypes.c_double()
+        lib.amgh_target_info(h, ctypes.byref(nf), ctypes.byref(tc))
+        diag["target_functions"], diag["target_constraint"] = nf.value, tc.value
         if assembly:
             nct, sz = ctypes.c_int64(), ctypes.c_int()
             assert lib.amgh_fine_assembly_info(h, ctypes.byref(nct), ctypes.byref(sz)) == 0
