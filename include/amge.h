@@ -116,6 +116,13 @@ typedef struct amge_hier amge_hier; /* opaque, device-resident hierarchy */
  *               beta), > 0 and finite; NULL = all ones
  *   nu_pre, nu_post  hybrid smoothing steps before / after the coarse correction,
  *               1 .. 8
+ *   flags       0, or AMGE_SETUP_TARGETS: the last coarsening's coarse space also
+ *               takes the D-free bubbles of the polynomial approximation targets
+ *               (Sections 3.3.1, 3.3.3: the interpolants of the vector monomials of
+ *               degree <= 1 projected in each coarse face's / cell's mass inner product
+ *               onto its D-free bubbles and filtered of linear dependence; extra
+ *               columns of P after the coarse entities' ones), and the coarsest matrix
+ *               is then the Galerkin product P^T A P.  Other bits: AMGE_EINVAL.
  * Tetrahedron t = 6 ((i n + j) n + k) + p lies in cube (i, j, k) (i, j, k the x, y, z
  * cube indices), p = 0 .. 5 the Kuhn permutation index in the order
  * (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y), (z,y,x) of the monotone path from the
@@ -128,7 +135,9 @@ typedef struct {
   const double* alpha;
   int32_t nu_pre;
   int32_t nu_post;
+  int32_t flags;
 } amge_problem;
+#define AMGE_SETUP_TARGETS 1
 
 /* Options of a PCG solve.  rtol: stop when the true FP64 relative residual
  * ||b - A x||_2 / ||b||_2 <= rtol (x0 = 0); maxit >= 1; precision: amge_precision. */

@@ -22,6 +22,7 @@ _lib = ctypes.CDLL(AMGE_SO)
 AMGE_OK, AMGE_EINVAL, AMGE_ENOMEM, AMGE_ECUDA, AMGE_ENOTCONV, AMGE_ENONFINITE = 0, 1, 2, 3, 4, 5
 AMGE_EAGAIN, AMGE_ETIMEOUT, AMGE_ECANCELED = 6, 7, 8
 AMGE_HCURL, AMGE_HDIV = 2, 3
+AMGE_SETUP_TARGETS = 1
 AMGE_FP64, AMGE_FP32_VCYCLE = 0, 1
 AMGE_OP_A, AMGE_OP_P, AMGE_OP_PT, AMGE_OP_G, AMGE_OP_GT, AMGE_OP_SMOOTH_PRE, AMGE_OP_COARSE, AMGE_OP_AG, AMGE_OP_A_WIDE = range(9)
 PROF_CLASSES = ["A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "pcg_spmv", "pcg_vec", "vcycle_vec", "AG",
@@ -47,7 +48,7 @@ class amge_hierarchy_desc(ctypes.Structure):
 class amge_problem(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("n", ctypes.c_int32), ("num_levels", ctypes.c_int32),
                 ("beta", ctypes.c_void_p), ("alpha", ctypes.c_void_p), ("nu_pre", ctypes.c_int32),
-                ("nu_post", ctypes.c_int32)]
+                ("nu_post", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class amge_solve_opts(ctypes.Structure):
@@ -182,10 +183,11 @@ def _hier_from(h):
 
 
 def amge_setup_upload(form: str, n: int, num_levels: int = 0, beta=None, alpha=None, nu_pre: int = 1,
-                      nu_post: int = 1, stream=None) -> Hier:
+                      nu_post: int = 1, stream=None, targets: bool = False, flags: int = None) -> Hier:
     """Build the hierarchy of the problem (eq. 2.2 on n^3 Kuhn-split cubes) on the host
     and upload it.  form: 'hcurl' or 'hdiv'; beta / alpha: per-tet coefficients of the
-    derivative / mass term (6 n^3 values, None = 1)."""
+    derivative / mass term (6 n^3 values, None = 1); targets: AMGE_SETUP_TARGETS (flags,
+    when given, is passed as it is)."""
     keep = []
 
     def coef(c):
@@ -197,8 +199,10 @@ def amge_setup_upload(form: str, n: int, num_levels: int = 0, beta=None, alpha=N
         keep.append(a)
         return a.ctypes.data
 
+    if flags is None:
+        flags = AMGE_SETUP_TARGETS if targets else 0
     prob = amge_problem({"hcurl": AMGE_HCURL, "hdiv": AMGE_HDIV}[form], n, num_levels, coef(beta), coef(alpha),
-                        nu_pre, nu_post)
+                        nu_pre, nu_post, flags)
     h = ctypes.c_void_p()
     _check(_lib.amge_setup_upload(ctypes.byref(prob), _stream(stream), ctypes.byref(h)), "amge_setup_upload")
     return _hier_from(h)
