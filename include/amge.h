@@ -117,12 +117,14 @@ typedef struct amge_hier amge_hier; /* opaque, device-resident hierarchy */
  *   nu_pre, nu_post  hybrid smoothing steps before / after the coarse correction,
  *               1 .. 8
  *   flags       0, or AMGE_SETUP_TARGETS: the last coarsening's coarse space also
- *               takes the D-free bubbles of the polynomial approximation targets
- *               (Sections 3.3.1, 3.3.3: the interpolants of the vector monomials of
- *               degree <= 1 projected in each coarse face's / cell's mass inner product
- *               onto its D-free bubbles and filtered of linear dependence; extra
- *               columns of P after the coarse entities' ones), and the coarsest matrix
- *               is then the Galerkin product P^T A P.  Other bits: AMGE_EINVAL.
+ *               takes the polynomial approximation targets (Sections 3.3.1-3.3.3: the
+ *               interpolants of the vector monomials of degree <= 1 -- their traces on
+ *               coarse edges / faces orthogonal to the PV traces, and their mass
+ *               projections onto the D-free bubbles of coarse faces and cells --
+ *               filtered of linear dependence, extended by eqs. 3.6 / 3.8, as extra
+ *               columns of P after the coarse entities' ones); the coarsest space then
+ *               reproduces every linear field, and the coarsest matrix is the Galerkin
+ *               product P^T A P.  Other bits: AMGE_EINVAL.
  * Tetrahedron t = 6 ((i n + j) n + k) + p lies in cube (i, j, k) (i, j, k the x, y, z
  * cube indices), p = 0 .. 5 the Kuhn permutation index in the order
  * (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y), (z,y,x) of the monotone path from the

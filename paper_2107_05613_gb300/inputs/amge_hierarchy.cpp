@@ -7,9 +7,10 @@
 // Section 3.3: PV traces (eq. 3.5) extended by the local saddle-point problems of
 // eq. 3.6 (first extension) and eq. 3.8 (further extensions), built in the order
 // L2 -> H(div) -> H(curl) -> H1.  Section 3.2.1: element-based RAP for coarse local
-// and global matrices.  Optionally (AMGH_TARGETS), Sections 3.3.1 / 3.3.3: polynomial
-// approximation targets projected onto the D-free bubbles of the last coarsening's
-// coarse entities, filtered of linear dependence and added to the coarsest space.
+// and global matrices.  Optionally (AMGH_TARGETS), Sections 3.3.1-3.3.3: polynomial
+// approximation targets on the last coarsening -- their traces on coarse edges or
+// faces beyond the PV traces, and their projections onto the D-free bubbles of coarse
+// faces and cells -- filtered of linear dependence and added to the coarsest space.
 //
 // Everything is double precision and sequential per entity; entities are processed
 // in parallel with OpenMP (each prolongator entry is written by exactly one task).
@@ -1513,6 +1514,158 @@ double mass_targets(const std::vector<double>& M, const int* S, int nS, const Ta
   return tau;
 }
 
+// Extension of nJ space-k traces from the boundary of the coarse entity X of dimension
+// d = k + 1 (a face for the edge space, a cell for the face space) into its interior by
+// the local problem of eq. 3.6 (the system `extend` solves for the PV traces):
+// unknowns the interior dofs, psi on X's constituents and the multiplier lambda of the
+// orthogonality to X's PV trace, with boundary data phiB (nB x nJ, X's boundary dofs
+// in closure order).  Returns the interior values (nI x nJ).
+std::vector<double> extend_eq36(const Level& L, const Transfer& T, int k, int X, const std::vector<double>& phiB,
+                                int nJ) {
+  const int d = k + 1;
+  std::vector<double> M, W, Dm, buf, K, R;
+  const int* S = T.fclo[d][k].row(X);
+  const int nS = T.fclo[d][k].len(X);
+  const uint8_t* in = T.fint[d][k].data() + T.fclo[d][k].rp[X];
+  std::vector<int> I, B;
+  for (int i = 0; i < nS; i++) (in[i] ? I : B).push_back(i);
+  const int nI = (int)I.size(), nB = (int)B.size();
+  assemble_mass(L, T, d, k, X, S, nS, M, buf);
+  const int* S1 = T.cons[d].row(X);
+  const int n1 = T.cons[d].len(X);
+  assemble_mass(L, T, d, d, X, S1, n1, W, buf);
+  restrict_D(L.D[k], S1, n1, S, nS, Dm);
+  std::vector<double> pv(n1), Wp(n1, 0.0), WD((size_t)n1 * nS, 0.0);
+  for (int a = 0; a < n1; a++) pv[a] = T.phi[d][T.cons[d].rp[X] + a] / (double)n1;
+  for (int a = 0; a < n1; a++)
+    for (int b = 0; b < n1; b++) Wp[a] += W[(size_t)a * n1 + b] * pv[b];
+  for (int a = 0; a < n1; a++)
+    for (int c = 0; c < n1; c++) {
+      const double w = W[(size_t)a * n1 + c];
+      if (w == 0.0) continue;
+      for (int i = 0; i < nS; i++) WD[(size_t)a * nS + i] += w * Dm[(size_t)c * nS + i];
+    }
+  const int n = nI + n1 + 1;
+  K.assign((size_t)n * n, 0.0);
+  R.assign((size_t)n * nJ, 0.0);
+  for (int a = 0; a < nI; a++)
+    for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
+  for (int a = 0; a < n1; a++) {
+    for (int b = 0; b < nI; b++) {
+      const double v = WD[(size_t)a * nS + I[b]];
+      K[(size_t)(nI + a) * n + b] = v;
+      K[(size_t)b * n + nI + a] = v;
+    }
+    K[(size_t)(nI + a) * n + nI + n1] = -Wp[a];
+    K[(size_t)(nI + n1) * n + nI + a] = -Wp[a];
+  }
+  for (int j = 0; j < nJ; j++) {
+    for (int a = 0; a < nI; a++) {
+      double v = 0;
+      for (int b = 0; b < nB; b++) v += M[(size_t)I[a] * nS + B[b]] * phiB[(size_t)b * nJ + j];
+      R[(size_t)a * nJ + j] = -v;
+    }
+    for (int a = 0; a < n1; a++) {
+      double v = 0;
+      for (int b = 0; b < nB; b++) v += WD[(size_t)a * nS + B[b]] * phiB[(size_t)b * nJ + j];
+      R[(size_t)(nI + a) * nJ + j] = -v;
+    }
+  }
+  if (!lu_solve(n, K.data(), nJ, R.data())) throw Fail("singular extension of a face trace");
+  R.resize((size_t)nI * nJ);
+  return R;
+}
+
+// Trace targets of the face space for one coarsening (Section 3.3.2's coarse trace
+// spaces with Section 3.3.1's targets): on every coarse face F the targets' traces --
+// their values on F's constituent fine faces -- are made orthogonal, in F's trace
+// mass, to F's PV trace, then filtered of linear dependence (filter_targets); each
+// kept trace is a new coarse dof of F, extended into the cells that share F by
+// eq. 3.6 (its multiplier vanishes: a trace orthogonal to the PV trace carries no net
+// flux).  The functions are appended to P (space 2), face by face.
+void add_face_traces(const Level& L, const Level& C, const Transfer& T, DCsr& P, const Targets& tgt,
+                     BubbleStats& st) {
+  const int nt = (int)tgt.size();
+  const int nF = T.cons[2].rows(), nX = T.cons[3].rows();
+  std::vector<std::vector<double>> fv(nF);
+  std::vector<int> fk(nF, 0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int F = 0; F < nF; F++) {
+    std::vector<double> M, buf, mt;
+    const int* S = T.cons[2].row(F);
+    const int nS = T.cons[2].len(F);
+    assemble_mass(L, T, 2, 2, F, S, nS, M, buf);
+    std::vector<double> pv(nS), Mp(nS, 0.0);
+    for (int a = 0; a < nS; a++) pv[a] = T.phi[2][T.cons[2].rp[F] + a] / (double)nS;
+    double pMp = 0;
+    for (int a = 0; a < nS; a++) {
+      for (int b = 0; b < nS; b++) Mp[a] += M[(size_t)a * nS + b] * pv[b];
+      pMp += pv[a] * Mp[a];
+    }
+    const double tau = mass_targets(M, S, nS, tgt, mt);
+    std::vector<double> phi((size_t)nS * nt);
+    for (int c = 0; c < nt; c++) {
+      double pMt = 0;
+      for (int a = 0; a < nS; a++) pMt += Mp[a] * tgt[c][S[a]];
+      for (int a = 0; a < nS; a++) phi[(size_t)a * nt + c] = tgt[c][S[a]] - pv[a] * (pMt / pMp);
+    }
+    fk[F] = filter_targets(nS, nt, phi, [&](int a, int b) { return M[(size_t)a * nS + b]; }, tau, fv[F]);
+  }
+  std::vector<int> ffirst(nF);
+  int next = P.nc;
+  for (int F = 0; F < nF; F++) ffirst[F] = next, next += fk[F];
+  std::vector<std::vector<double>> xv(nX);
+  std::vector<std::vector<int>> xcol(nX), xrows(nX);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int X = 0; X < nX; X++) {
+    const int* S = T.fclo[3][2].row(X);
+    const int nS = T.fclo[3][2].len(X);
+    const uint8_t* in = T.fint[3][2].data() + T.fclo[3][2].rp[X];
+    std::vector<int> Bpos;
+    for (int i = 0; i < nS; i++)
+      if (in[i]) xrows[X].push_back(S[i]);
+      else Bpos.push_back(i);
+    const int* Fx = C.clo[3][2].row(X);
+    const int nFx = C.clo[3][2].len(X);
+    int nJ = 0;
+    for (int q = 0; q < nFx; q++) nJ += fk[Fx[q]];
+    if (nJ == 0 || xrows[X].empty()) continue;
+    std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
+    int j0 = 0;
+    for (int q = 0; q < nFx; q++) {
+      const int F = Fx[q];
+      const int nSF = T.cons[2].len(F);
+      const int* SF = T.cons[2].row(F);
+      for (int i = 0; i < fk[F]; i++) {
+        xcol[X].push_back(ffirst[F] + i);
+        for (int a = 0; a < nSF; a++) {  // F's fine faces among X's boundary faces
+          const int* pos = std::lower_bound(S, S + nS, SF[a]);
+          REQUIRE(pos != S + nS && *pos == SF[a], "coarse face outside its cell's closure");
+          const int bi = (int)(std::lower_bound(Bpos.begin(), Bpos.end(), (int)(pos - S)) - Bpos.begin());
+          phiB[(size_t)bi * nJ + j0 + i] = fv[F][(size_t)i * nSF + a];
+        }
+      }
+      j0 += fk[F];
+    }
+    xv[X] = extend_eq36(L, T, 2, X, phiB, nJ);
+  }
+  std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
+  for (int F = 0; F < nF; F++) {
+    const int nSF = T.cons[2].len(F);
+    const int* SF = T.cons[2].row(F);
+    for (int i = 0; i < fk[F]; i++)
+      for (int a = 0; a < nSF; a++)
+        if (fv[F][(size_t)i * nSF + a] != 0.0) extra[SF[a]].emplace_back(ffirst[F] + i, fv[F][(size_t)i * nSF + a]);
+  }
+  for (int X = 0; X < nX; X++) {
+    const int nI = (int)xrows[X].size(), nJ = (int)xcol[X].size();
+    for (int a = 0; a < nI && nJ > 0; a++)
+      for (int j = 0; j < nJ; j++)
+        if (xv[X][(size_t)a * nJ + j] != 0.0) extra[xrows[X][a]].emplace_back(xcol[X][j], xv[X][(size_t)a * nJ + j]);
+  }
+  append_columns(P, extra, next, st);
+}
+
 // D-free bubbles of the face space (Section 3.3.3) for one coarsening: per coarse cell
 // X, each target is projected in the mass inner product of X onto X's div-free bubbles
 // -- face functions on X's interior faces, zero on its boundary faces, with zero
@@ -1728,31 +1881,106 @@ std::vector<double> extend_cell_zero_target(const Level& L, const Transfer& T, i
   return R;
 }
 
+// Position of `v` in the sorted list [b, b + n) (it must be there).
+inline int pos_in(const int* b, int n, int v) {
+  const int* p = std::lower_bound(b, b + n, v);
+  REQUIRE(p != b + n && *p == v, "dof outside the expected closure");
+  return (int)(p - b);
+}
+
 // Approximation targets of the edge space for one coarsening (Section 3.3.1 with the
-// D-free bubbles of Section 3.3.3): on every coarse face F the targets' projections
-// onto F's gradient bubbles, extended into the cells that share F by eq. 3.8; then in
-// every coarse cell X its own gradient bubbles.  The constant fields' tangential
-// traces on the straight coarse edges are multiples of the PV traces and add nothing
-// there.  The functions are appended to P (space 1) after the coarse edges: the face
-// functions face by face, then the cell functions cell by cell.
+// coarse trace spaces of Section 3.3.2 and the D-free bubbles of Section 3.3.3):
+//  1. on every coarse edge E, the targets' traces (values on E's fine edges) made
+//     orthogonal in E's trace mass to E's PV trace and filtered: new dofs of E;
+//  2. those extended into every coarse face F containing E by eq. 3.6 (multiplier 0:
+//     a trace orthogonal to the PV trace has zero net circulation);
+//  3. on every coarse face F, the targets' projections onto F's gradient bubbles;
+//  4. the functions of 1-3 extended into every coarse cell X by eq. 3.8 with a zero
+//     target -- their surface curls on X's faces vanish, so their coarse curl does;
+//  5. in every coarse cell X, its own gradient bubbles.
+// For the constant and linear fields the curl is constant, so the cross-space
+// bubbles of eqs. 3.7 / 3.9, whose curls are non-constant traces or div-free bubbles,
+// would receive no target component; they are not built.  The functions are appended
+// to P (space 1) after the coarse edges: edge, then face, then cell functions.
 void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P, const Targets& tgt,
                       BubbleStats& st) {
-  const int nF = T.cons[2].rows(), nX = T.cons[3].rows();
-  std::vector<std::vector<double>> fv(nF), cv(nX);
-  std::vector<std::vector<int>> frows(nF), crows(nX);
-  std::vector<int> fk(nF, 0), ck(nX, 0);
+  const int nt = (int)tgt.size();
+  const int nE = T.cons[1].rows(), nF = T.cons[2].rows(), nX = T.cons[3].rows();
+  // 1. edge traces
+  std::vector<std::vector<double>> ev(nE);
+  std::vector<int> ek(nE, 0);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int E = 0; E < nE; E++) {
+    std::vector<double> M, buf, mt;
+    const int* S = T.cons[1].row(E);
+    const int nS = T.cons[1].len(E);
+    if (nS < 2) continue;
+    assemble_mass(L, T, 1, 1, E, S, nS, M, buf);
+    std::vector<double> pv(nS), Mp(nS, 0.0);
+    for (int a = 0; a < nS; a++) pv[a] = T.phi[1][T.cons[1].rp[E] + a] / (double)nS;
+    double pMp = 0;
+    for (int a = 0; a < nS; a++) {
+      for (int b = 0; b < nS; b++) Mp[a] += M[(size_t)a * nS + b] * pv[b];
+      pMp += pv[a] * Mp[a];
+    }
+    const double tau = mass_targets(M, S, nS, tgt, mt);
+    std::vector<double> phi((size_t)nS * nt);
+    for (int c = 0; c < nt; c++) {
+      double pMt = 0;
+      for (int a = 0; a < nS; a++) pMt += Mp[a] * tgt[c][S[a]];
+      for (int a = 0; a < nS; a++) phi[(size_t)a * nt + c] = tgt[c][S[a]] - pv[a] * (pMt / pMp);
+    }
+    ek[E] = filter_targets(nS, nt, phi, [&](int a, int b) { return M[(size_t)a * nS + b]; }, tau, ev[E]);
+  }
+  std::vector<int> efirst(nE), ffirst(nF), cfirst(nX);
+  int next = P.nc;
+  for (int E = 0; E < nE; E++) efirst[E] = next, next += ek[E];
+  // 2. edge functions extended into the coarse faces; 3. face gradient bubbles
+  std::vector<std::vector<double>> fxv(nF), fv(nF);
+  std::vector<std::vector<int>> fxcol(nF), frows(nF);
+  std::vector<int> fk(nF, 0);
 #pragma omp parallel for schedule(dynamic, 16)
-  for (int F = 0; F < nF; F++) fv[F] = grad_bubbles(L, T, 2, F, tgt, frows[F], fk[F]);
+  for (int F = 0; F < nF; F++) {
+    fv[F] = grad_bubbles(L, T, 2, F, tgt, frows[F], fk[F]);
+    const int* S = T.fclo[2][1].row(F);
+    const int nS = T.fclo[2][1].len(F);
+    const uint8_t* in = T.fint[2][1].data() + T.fclo[2][1].rp[F];
+    std::vector<int> Bpos;
+    for (int i = 0; i < nS; i++)
+      if (!in[i]) Bpos.push_back(i);
+    const int* Ef = C.clo[2][1].row(F);
+    const int nEf = C.clo[2][1].len(F);
+    int nJ = 0;
+    for (int q = 0; q < nEf; q++) nJ += ek[Ef[q]];
+    if (nJ == 0 || Bpos.size() == (size_t)nS) continue;
+    std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
+    int j0 = 0;
+    for (int q = 0; q < nEf; q++) {
+      const int E = Ef[q];
+      const int nSE = T.cons[1].len(E);
+      const int* SE = T.cons[1].row(E);
+      for (int i = 0; i < ek[E]; i++) {
+        fxcol[F].push_back(efirst[E] + i);
+        for (int a = 0; a < nSE; a++) {
+          const int bi = pos_in(Bpos.data(), (int)Bpos.size(), pos_in(S, nS, SE[a]));
+          phiB[(size_t)bi * nJ + j0 + i] = ev[E][(size_t)i * nSE + a];
+        }
+      }
+      j0 += ek[E];
+    }
+    fxv[F] = extend_eq36(L, T, 1, F, phiB, nJ);  // F's interior edges x nJ
+  }
+  for (int F = 0; F < nF; F++) ffirst[F] = next, next += fk[F];
+  // 5. cell gradient bubbles
+  std::vector<std::vector<double>> cv(nX);
+  std::vector<std::vector<int>> crows(nX);
+  std::vector<int> ck(nX, 0);
 #pragma omp parallel for schedule(dynamic, 16)
   for (int X = 0; X < nX; X++) cv[X] = grad_bubbles(L, T, 3, X, tgt, crows[X], ck[X]);
-  std::vector<int> ffirst(nF), cfirst(nX);
-  int next = P.nc;
-  for (int F = 0; F < nF; F++) ffirst[F] = next, next += fk[F];
   for (int X = 0; X < nX; X++) cfirst[X] = next, next += ck[X];
-  // the face functions' extensions into every cell X, with the traces of all X's faces
+  // 4. the edge and face functions extended into every cell
   std::vector<std::vector<double>> xv(nX);
-  std::vector<std::vector<int>> xcol(nX);
-  std::vector<std::vector<int>> xrows(nX);
+  std::vector<std::vector<int>> xcol(nX), xrows(nX);
 #pragma omp parallel for schedule(dynamic, 16)
   for (int X = 0; X < nX; X++) {
     const int* S = T.fclo[3][1].row(X);
@@ -1762,45 +1990,61 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
     for (int i = 0; i < nS; i++)
       if (in[i]) xrows[X].push_back(S[i]);
       else Bpos.push_back(i);
+    if (xrows[X].empty()) continue;
+    const int* Ex = C.clo[3][1].row(X);
+    const int nEx = C.clo[3][1].len(X);
     const int* Fx = C.clo[3][2].row(X);
     const int nFx = C.clo[3][2].len(X);
-    int nJ = 0;
-    for (int q = 0; q < nFx; q++) nJ += fk[Fx[q]];
-    if (nJ == 0 || xrows[X].empty()) continue;
+    for (int q = 0; q < nEx; q++)
+      for (int i = 0; i < ek[Ex[q]]; i++) xcol[X].push_back(efirst[Ex[q]] + i);
+    for (int q = 0; q < nFx; q++)
+      for (int i = 0; i < fk[Fx[q]]; i++) xcol[X].push_back(ffirst[Fx[q]] + i);
+    const int nJ = (int)xcol[X].size();  // ascending: edges' columns precede faces'
+    if (nJ == 0) continue;
+    auto jof = [&](int col) { return pos_in(xcol[X].data(), nJ, col); };
     std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
-    int j0 = 0;
-    for (int q = 0; q < nFx; q++) {
-      const int F = Fx[q];
-      const int nIF = (int)frows[F].size();
-      for (int i = 0; i < fk[F]; i++) {
-        xcol[X].push_back(ffirst[F] + i);
-        for (int a = 0; a < nIF; a++) {  // F's interior edges among X's boundary edges
-          const int e = frows[F][a];
-          const int* pos = std::lower_bound(S, S + nS, e);
-          const int bi = (int)(std::lower_bound(Bpos.begin(), Bpos.end(), (int)(pos - S)) - Bpos.begin());
-          phiB[(size_t)bi * nJ + j0 + i] = fv[F][(size_t)i * nIF + a];
-        }
+    for (size_t b = 0; b < Bpos.size(); b++) {
+      const int y = S[Bpos[b]];
+      const int od = T.own_dim[1][y], oid = T.own_id[1][y];
+      if (od == 1) {  // on a coarse edge: that edge's trace functions
+        const int E = oid;
+        const int a = pos_in(T.cons[1].row(E), T.cons[1].len(E), y);
+        for (int i = 0; i < ek[E]; i++)
+          phiB[b * nJ + jof(efirst[E] + i)] = ev[E][(size_t)i * T.cons[1].len(E) + a];
+      } else if (od == 2) {  // interior to a coarse face: its bubbles and the edge functions' extensions
+        const int F = oid;
+        const int nIF = (int)frows[F].size();
+        const int a = pos_in(frows[F].data(), nIF, y);
+        for (int i = 0; i < fk[F]; i++) phiB[b * nJ + jof(ffirst[F] + i)] = fv[F][(size_t)i * nIF + a];
+        const int nJF = (int)fxcol[F].size();
+        for (int jj = 0; jj < nJF; jj++) phiB[b * nJ + jof(fxcol[F][jj])] = fxv[F][(size_t)a * nJF + jj];
       }
-      j0 += fk[F];
     }
     xv[X] = extend_cell_zero_target(L, T, X, phiB, nJ);
   }
   std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
+  auto put = [&](int row, int col, double v) {
+    if (v != 0.0) extra[row].emplace_back(col, v);
+  };
+  for (int E = 0; E < nE; E++) {
+    const int nSE = T.cons[1].len(E);
+    for (int i = 0; i < ek[E]; i++)
+      for (int a = 0; a < nSE; a++) put(T.cons[1].row(E)[a], efirst[E] + i, ev[E][(size_t)i * nSE + a]);
+  }
   for (int F = 0; F < nF; F++) {
-    const int nIF = (int)frows[F].size();
+    const int nIF = (int)frows[F].size(), nJF = (int)fxcol[F].size();
     for (int i = 0; i < fk[F]; i++)
-      for (int a = 0; a < nIF; a++)
-        if (fv[F][(size_t)i * nIF + a] != 0.0) extra[frows[F][a]].emplace_back(ffirst[F] + i, fv[F][(size_t)i * nIF + a]);
+      for (int a = 0; a < nIF; a++) put(frows[F][a], ffirst[F] + i, fv[F][(size_t)i * nIF + a]);
+    for (int a = 0; a < nIF && nJF > 0; a++)
+      for (int jj = 0; jj < nJF; jj++) put(frows[F][a], fxcol[F][jj], fxv[F][(size_t)a * nJF + jj]);
   }
   for (int X = 0; X < nX; X++) {
     const int nI = (int)xrows[X].size(), nJ = (int)xcol[X].size();
     for (int a = 0; a < nI && nJ > 0; a++)
-      for (int j = 0; j < nJ; j++)
-        if (xv[X][(size_t)a * nJ + j] != 0.0) extra[xrows[X][a]].emplace_back(xcol[X][j], xv[X][(size_t)a * nJ + j]);
+      for (int j = 0; j < nJ; j++) put(xrows[X][a], xcol[X][j], xv[X][(size_t)a * nJ + j]);
     const int nIX = (int)crows[X].size();
     for (int i = 0; i < ck[X]; i++)
-      for (int a = 0; a < nIX; a++)
-        if (cv[X][(size_t)i * nIX + a] != 0.0) extra[crows[X][a]].emplace_back(cfirst[X] + i, cv[X][(size_t)i * nIX + a]);
+      for (int a = 0; a < nIX; a++) put(crows[X][a], cfirst[X] + i, cv[X][(size_t)i * nIX + a]);
   }
   append_columns(P, extra, next, st);
 }
@@ -1884,7 +2128,10 @@ Hier* build(int form, int n, int num_levels, const double* beta, const double* a
         // whose matrix is then the Galerkin product with the enlarged prolongator
         Stage s("approximation targets");
         const Targets tg = space_targets(H, l, kf);
-        if (kf == 2) add_div_bubbles(L, T, T.P[kf], tg, bst);
+        if (kf == 2) {
+          add_face_traces(L, C, T, T.P[kf], tg, bst);
+          add_div_bubbles(L, T, T.P[kf], tg, bst);
+        }
         else add_curl_bubbles(L, C, T, T.P[kf], tg, bst);
         H->A[l + 1] = galerkin(H->A[l], T.P[kf]);
       }

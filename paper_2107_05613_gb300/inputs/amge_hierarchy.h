@@ -39,13 +39,15 @@ enum { AMGH_ALL_SPACES = 1, AMGH_TARGETS = 2 };
  *   flags       AMGH_ALL_SPACES: also build the prolongators of every lower space of
  *               the sequence (H1 for H(curl), H(curl) and H1 for H(div)) and the
  *               auxiliary-space data; otherwise only the spaces the problem needs.
- *               AMGH_TARGETS (H(div) only, not with AMGH_ALL_SPACES): polynomial
- *               approximation targets (Section 3.3.1) -- the interpolants of the
- *               constant vector fields -- enrich the last coarsening: per coarse
- *               cell, their mass projections onto its div-free bubbles, filtered of
- *               linear dependence (Section 3.3.3's D-free bubbles), become extra
- *               coarse basis functions (columns of P after the coarse faces), and the
- *               coarsest matrix is the Galerkin product P^T A P with that P.
+ *               AMGH_TARGETS (not with AMGH_ALL_SPACES): polynomial approximation
+ *               targets (Section 3.3.1) -- the interpolants of the vector monomials of
+ *               degree <= 1 -- enrich the last coarsening: their traces on coarse
+ *               edges (H(curl)) or faces (H(div)) orthogonal to the PV traces, and
+ *               their mass projections onto the D-free bubbles of coarse faces and
+ *               cells (Section 3.3.3), filtered of linear dependence and extended by
+ *               eqs. 3.6 / 3.8, become extra coarse basis functions (columns of P
+ *               after the coarse entities' ones); the coarsest matrix is the Galerkin
+ *               product P^T A P with that P.
  *   nthreads    OpenMP threads (<= 0: library default).
  * Returns 0 and a handle in *out, or nonzero with amgh_error() describing it. */
 int amgh_build(int form, int n, int num_levels, const double* beta, const double* alpha,

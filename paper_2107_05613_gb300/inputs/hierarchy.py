@@ -126,10 +126,10 @@ def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=Non
     num_levels: 0 = coarsen 2x2x2 while the cell grid side m > 8.
     assembly: also return the fine assembly of A_0 as a gather (diagnostics
     "assembly": dict of K, M [6, s, s], coff, ccell, cidx; see amge_hierarchy.h).
-    targets: (H(div)) enrich the last coarsening with the D-free bubbles of the
-    constant-field approximation targets (Sections 3.3.1, 3.3.3; AMGH_TARGETS in
-    amge_hierarchy.h): P[-1] gains columns after the coarse faces and A[-1] is
-    P[-1]^T A[-2] P[-1]; diagnostics "target_functions", "target_constraint".
+    targets: enrich the last coarsening with the degree-one polynomial approximation
+    targets (Sections 3.3.1-3.3.3; AMGH_TARGETS in amge_hierarchy.h): P[-1] gains
+    columns after the coarse entities' ones and A[-1] is P[-1]^T A[-2] P[-1];
+    diagnostics "target_functions", "target_constraint".
     """
     lib = _load()
     kf = FORMS[form]
