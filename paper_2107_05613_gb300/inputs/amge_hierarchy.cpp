@@ -898,6 +898,175 @@ struct ExtStats {
   double lam_dev = 0, resid = 0;
 };
 
+// Largest relative residual ||K x_j - r_j|| / ||r_j|| of a solve, over the columns j.
+double solve_residual(int n, int nJ, const std::vector<double>& K0, const std::vector<double>& R0,
+                      const std::vector<double>& X) {
+  double worst = 0;
+  for (int j = 0; j < nJ; j++) {
+    double rn = 0, bn = 0;
+    for (int a = 0; a < n; a++) {
+      double v = -R0[(size_t)a * nJ + j];
+      for (int b = 0; b < n; b++) v += K0[(size_t)a * n + b] * X[(size_t)b * nJ + j];
+      rn += v * v;
+      bn += R0[(size_t)a * nJ + j] * R0[(size_t)a * nJ + j];
+    }
+    if (bn > 0) worst = std::max(worst, std::sqrt(rn / bn));
+  }
+  return worst;
+}
+
+// The local problems of the extensions, on the coarse entity X of dimension d, for
+// nJ traces of space k given on X's boundary dofs (phiB, nB x nJ, closure order).  Both
+// return the whole solution (rows: X's interior dofs, then the multipliers), and with
+// `resid` the largest relative residual of the solve over the nJ right-hand sides.
+//
+// Eq. 3.6 (d = k + 1): unknowns the interior values, psi on X's constituents and the
+// multiplier lambda of psi's orthogonality to X's PV trace; discretised as the
+// symmetric saddle-point system
+//   [ M_II      (W D)_I^T   0   ] [phi_I ]   [ -M_IB phi_B     ]
+//   [ (W D)_I   0          -W p ] [psi   ] = [ -(W D)_B phi_B  ]
+//   [ 0        -(W p)^T     0   ] [lambda]   [ 0               ]
+// with M the space-k mass on X, W the space-(k+1) mass on its constituents and p the
+// PV trace of X.
+std::vector<double> solve_eq36(const Level& L, const Transfer& T, int k, int X, const std::vector<double>& phiB,
+                               int nJ, double* resid) {
+  const int d = k + 1;
+  std::vector<double> M, W, Dm, buf, K, R;
+  const int* S = T.fclo[d][k].row(X);
+  const int nS = T.fclo[d][k].len(X);
+  const uint8_t* in = T.fint[d][k].data() + T.fclo[d][k].rp[X];
+  std::vector<int> I, B;
+  for (int i = 0; i < nS; i++) (in[i] ? I : B).push_back(i);
+  const int nI = (int)I.size(), nB = (int)B.size();
+  assemble_mass(L, T, d, k, X, S, nS, M, buf);
+  const int* S1 = T.cons[d].row(X);
+  const int n1 = T.cons[d].len(X);
+  assemble_mass(L, T, d, d, X, S1, n1, W, buf);
+  restrict_D(L.D[k], S1, n1, S, nS, Dm);
+  std::vector<double> pv(n1), Wp(n1, 0.0), WD((size_t)n1 * nS, 0.0);
+  for (int a = 0; a < n1; a++) pv[a] = T.phi[d][T.cons[d].rp[X] + a] / (double)n1;
+  for (int a = 0; a < n1; a++)
+    for (int b = 0; b < n1; b++) Wp[a] += W[(size_t)a * n1 + b] * pv[b];
+  for (int a = 0; a < n1; a++)
+    for (int c = 0; c < n1; c++) {
+      const double w = W[(size_t)a * n1 + c];
+      if (w == 0.0) continue;
+      for (int i = 0; i < nS; i++) WD[(size_t)a * nS + i] += w * Dm[(size_t)c * nS + i];
+    }
+  const int n = nI + n1 + 1;
+  K.assign((size_t)n * n, 0.0);
+  R.assign((size_t)n * nJ, 0.0);
+  for (int a = 0; a < nI; a++)
+    for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
+  for (int a = 0; a < n1; a++) {
+    for (int b = 0; b < nI; b++) {
+      const double v = WD[(size_t)a * nS + I[b]];
+      K[(size_t)(nI + a) * n + b] = v;
+      K[(size_t)b * n + nI + a] = v;
+    }
+    K[(size_t)(nI + a) * n + nI + n1] = -Wp[a];
+    K[(size_t)(nI + n1) * n + nI + a] = -Wp[a];
+  }
+  for (int j = 0; j < nJ; j++) {
+    for (int a = 0; a < nI; a++) {
+      double v = 0;
+      for (int b = 0; b < nB; b++) v += M[(size_t)I[a] * nS + B[b]] * phiB[(size_t)b * nJ + j];
+      R[(size_t)a * nJ + j] = -v;
+    }
+    for (int a = 0; a < n1; a++) {
+      double v = 0;
+      for (int b = 0; b < nB; b++) v += WD[(size_t)a * nS + B[b]] * phiB[(size_t)b * nJ + j];
+      R[(size_t)(nI + a) * nJ + j] = -v;
+    }
+  }
+  const std::vector<double> K0 = K, R0 = R;
+  if (!lu_solve(n, K.data(), nJ, R.data())) throw Fail("singular local extension problem (eq. 3.6)");
+  if (resid) *resid = solve_residual(n, nJ, K0, R0, R);
+  return R;
+}
+
+// Eq. 3.8 (d >= k + 2: the further extensions, edge -> face -> cell for the vertex
+// space and face -> cell for the edge space): unknowns the interior values and chi on
+// X's interior (k+1)-dofs, with the stabilisation -D_{k+1}^T W2 D_{k+1} on chi:
+//   [ M_II        (W D)_{I1,I}^T        ] [phi_I]   [ -M_IB phi_B                 ]
+//   [ (W D)_{I1,I}  -(D2^T W2 D2)_{I1,I1} ] [chi  ] = [ W_{I1,:} (s - D_{:,B} phi_B) ]
+// s (n1 x nJ, on all (k+1)-dofs of X): the target, the extension of the coarse
+// derivative of the traces; null for a zero target.
+std::vector<double> solve_eq38(const Level& L, const Transfer& T, int k, int d, int X,
+                               const std::vector<double>* s, const std::vector<double>& phiB, int nJ,
+                               double* resid) {
+  std::vector<double> M, W, W2, Dm, D2m, buf, K, R;
+  const int* S = T.fclo[d][k].row(X);
+  const int nS = T.fclo[d][k].len(X);
+  const uint8_t* in = T.fint[d][k].data() + T.fclo[d][k].rp[X];
+  std::vector<int> I, B;
+  for (int i = 0; i < nS; i++) (in[i] ? I : B).push_back(i);
+  const int nI = (int)I.size(), nB = (int)B.size();
+  assemble_mass(L, T, d, k, X, S, nS, M, buf);
+  const int* S1 = T.fclo[d][k + 1].row(X);
+  const int n1 = T.fclo[d][k + 1].len(X);
+  const uint8_t* in1 = T.fint[d][k + 1].data() + T.fclo[d][k + 1].rp[X];
+  const int* S2 = T.fclo[d][k + 2].row(X);
+  const int n2 = T.fclo[d][k + 2].len(X);
+  std::vector<int> I1;
+  for (int i = 0; i < n1; i++)
+    if (in1[i]) I1.push_back(i);
+  const int nI1 = (int)I1.size();
+  assemble_mass(L, T, d, k + 1, X, S1, n1, W, buf);
+  assemble_mass(L, T, d, k + 2, X, S2, n2, W2, buf);
+  restrict_D(L.D[k], S1, n1, S, nS, Dm);
+  restrict_D(L.D[k + 1], S2, n2, S1, n1, D2m);
+  // residual target t = s - D_B phi_B on all (k+1)-dofs of X
+  std::vector<double> tgt = s ? *s : std::vector<double>((size_t)n1 * nJ, 0.0);
+  for (int a = 0; a < n1; a++)
+    for (int b = 0; b < nB; b++) {
+      const double dv = Dm[(size_t)a * nS + B[b]];
+      if (dv == 0.0) continue;
+      for (int j = 0; j < nJ; j++) tgt[(size_t)a * nJ + j] -= dv * phiB[(size_t)b * nJ + j];
+    }
+  const int n = nI + nI1;
+  K.assign((size_t)n * n, 0.0);
+  R.assign((size_t)n * nJ, 0.0);
+  for (int a = 0; a < nI; a++)
+    for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
+  for (int a = 0; a < nI1; a++)  // W_{I1,I1} D_{I1,I}
+    for (int b = 0; b < nI; b++) {
+      double v = 0;
+      for (int c = 0; c < nI1; c++) v += W[(size_t)I1[a] * n1 + I1[c]] * Dm[(size_t)I1[c] * nS + I[b]];
+      K[(size_t)(nI + a) * n + b] = v;
+      K[(size_t)b * n + nI + a] = v;
+    }
+  std::vector<double> W2D((size_t)n2 * nI1, 0.0);  // -D2_{:,I1}^T W2 D2_{:,I1}
+  for (int a = 0; a < n2; a++)
+    for (int c = 0; c < n2; c++) {
+      const double w = W2[(size_t)a * n2 + c];
+      if (w == 0.0) continue;
+      for (int b = 0; b < nI1; b++) W2D[(size_t)a * nI1 + b] += w * D2m[(size_t)c * n1 + I1[b]];
+    }
+  for (int a = 0; a < nI1; a++)
+    for (int b = 0; b < nI1; b++) {
+      double v = 0;
+      for (int c = 0; c < n2; c++) v += D2m[(size_t)c * n1 + I1[a]] * W2D[(size_t)c * nI1 + b];
+      K[(size_t)(nI + a) * n + nI + b] = -v;
+    }
+  for (int j = 0; j < nJ; j++) {
+    for (int a = 0; a < nI; a++) {
+      double v = 0;
+      for (int b = 0; b < nB; b++) v += M[(size_t)I[a] * nS + B[b]] * phiB[(size_t)b * nJ + j];
+      R[(size_t)a * nJ + j] = -v;
+    }
+    for (int a = 0; a < nI1; a++) {
+      double v = 0;
+      for (int c = 0; c < n1; c++) v += W[(size_t)I1[a] * n1 + c] * tgt[(size_t)c * nJ + j];
+      R[(size_t)(nI + a) * nJ + j] = v;
+    }
+  }
+  const std::vector<double> K0 = K, R0 = R;
+  if (!lu_solve(n, K.data(), nJ, R.data())) throw Fail("singular local extension problem (eq. 3.8)");
+  if (resid) *resid = solve_residual(n, nJ, K0, R0, R);
+  return R;
+}
+
 // Extend space-k coarse dofs into the interior of every coarse entity of dimension d.
 void extend(const Level& L, const Level& C, Transfer& T, int k, int d, ExtStats& st) {
   DCsr& P = T.P[k];
@@ -905,7 +1074,6 @@ void extend(const Level& L, const Level& C, Transfer& T, int k, int d, ExtStats&
   double lam_dev = 0, resid = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(max : lam_dev, resid)
   for (int X = 0; X < nX; X++) {
-    std::vector<double> M, W, W2, Dm, D2m, buf, K, R, K0, R0, s;
     const int* S = T.fclo[d][k].row(X);
     const int nS = T.fclo[d][k].len(X);
     const uint8_t* in = T.fint[d][k].data() + T.fclo[d][k].rp[X];
@@ -919,143 +1087,31 @@ void extend(const Level& L, const Level& C, Transfer& T, int k, int d, ExtStats&
     std::vector<double> phiB((size_t)nB * nJ);
     for (int b = 0; b < nB; b++)
       for (int j = 0; j < nJ; j++) phiB[(size_t)b * nJ + j] = P.get(S[B[b]], J[j]);
-    assemble_mass(L, T, d, k, X, S, nS, M, buf);
-    int n;
+    std::vector<double> R;
+    double rx = 0;
     if (d == k + 1) {
-      // eq. 3.6: unknowns (phi_I, psi on all constituents, lambda)
-      const int* S1 = T.cons[d].row(X);
-      const int n1 = T.cons[d].len(X);
-      assemble_mass(L, T, d, d, X, S1, n1, W, buf);
-      restrict_D(L.D[k], S1, n1, S, nS, Dm);
-      std::vector<double> p(n1), Wp(n1, 0.0);
-      for (int a = 0; a < n1; a++) p[a] = T.phi[d][T.cons[d].rp[X] + a] / (double)n1;
-      for (int a = 0; a < n1; a++)
-        for (int b = 0; b < n1; b++) Wp[a] += W[(size_t)a * n1 + b] * p[b];
-      std::vector<double> WD((size_t)n1 * nS, 0.0);
-      for (int a = 0; a < n1; a++)
-        for (int c = 0; c < n1; c++) {
-          double w = W[(size_t)a * n1 + c];
-          if (w == 0.0) continue;
-          for (int i = 0; i < nS; i++) WD[(size_t)a * nS + i] += w * Dm[(size_t)c * nS + i];
-        }
-      n = nI + n1 + 1;
-      K.assign((size_t)n * n, 0.0);
-      R.assign((size_t)n * nJ, 0.0);
-      for (int a = 0; a < nI; a++)
-        for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
-      for (int a = 0; a < n1; a++)
-        for (int b = 0; b < nI; b++) {
-          double v = WD[(size_t)a * nS + I[b]];
-          K[(size_t)(nI + a) * n + b] = v;
-          K[(size_t)b * n + nI + a] = v;
-        }
-      for (int a = 0; a < n1; a++) {
-        K[(size_t)(nI + a) * n + nI + n1] = -Wp[a];
-        K[(size_t)(nI + n1) * n + nI + a] = -Wp[a];
-      }
-      for (int j = 0; j < nJ; j++) {
-        for (int a = 0; a < nI; a++) {
-          double v = 0;
-          for (int b = 0; b < nB; b++) v += M[(size_t)I[a] * nS + B[b]] * phiB[(size_t)b * nJ + j];
-          R[(size_t)a * nJ + j] = -v;
-        }
-        for (int a = 0; a < n1; a++) {
-          double v = 0;
-          for (int b = 0; b < nB; b++) v += WD[(size_t)a * nS + B[b]] * phiB[(size_t)b * nJ + j];
-          R[(size_t)(nI + a) * nJ + j] = -v;
-        }
+      R = solve_eq36(L, T, k, X, phiB, nJ, &rx);
+      const int n = (int)(R.size() / nJ);
+      for (int j = 0; j < nJ; j++) {  // Stokes: the multiplier equals the coarse incidence (D_k^H)_{X,J}
+        const double lam = R[(size_t)(n - 1) * nJ + j];
+        lam_dev = std::max(lam_dev, std::fabs(lam - (double)C.D[k].get(X, J[j])));
       }
     } else {
-      // eq. 3.8: unknowns (phi_I, chi on interior (k+1)-dofs)
+      // s_J = sum_J' (D_k^H)_{J',J} * (space-(k+1) shape function of J' on X)
       const int* S1 = T.fclo[d][k + 1].row(X);
       const int n1 = T.fclo[d][k + 1].len(X);
-      const uint8_t* in1 = T.fint[d][k + 1].data() + T.fclo[d][k + 1].rp[X];
-      const int* S2 = T.fclo[d][k + 2].row(X);
-      const int n2 = T.fclo[d][k + 2].len(X);
-      std::vector<int> I1;
-      for (int i = 0; i < n1; i++)
-        if (in1[i]) I1.push_back(i);
-      const int nI1 = (int)I1.size();
-      assemble_mass(L, T, d, k + 1, X, S1, n1, W, buf);
-      assemble_mass(L, T, d, k + 2, X, S2, n2, W2, buf);
-      restrict_D(L.D[k], S1, n1, S, nS, Dm);
-      restrict_D(L.D[k + 1], S2, n2, S1, n1, D2m);
-      // s_J = sum_J' (D_k^H)_{J',J} * (space-(k+1) shape function of J' on X)
       const int* J1;
       const int nJ1 = coarse_dofs(C, d, k + 1, X, &J1);
-      s.assign((size_t)n1 * nJ, 0.0);
+      std::vector<double> s((size_t)n1 * nJ, 0.0);
       for (int j1 = 0; j1 < nJ1; j1++)
         for (int j = 0; j < nJ; j++) {
           int8_t inc = C.D[k].get(J1[j1], J[j]);
           if (!inc) continue;
           for (int a = 0; a < n1; a++) s[(size_t)a * nJ + j] += inc * T.P[k + 1].get(S1[a], J1[j1]);
         }
-      // residual target t = s - D_B phi_B on all (k+1)-dofs of X
-      std::vector<double> tgt = s;
-      for (int a = 0; a < n1; a++)
-        for (int b = 0; b < nB; b++) {
-          double dv = Dm[(size_t)a * nS + B[b]];
-          if (dv == 0.0) continue;
-          for (int j = 0; j < nJ; j++) tgt[(size_t)a * nJ + j] -= dv * phiB[(size_t)b * nJ + j];
-        }
-      n = nI + nI1;
-      K.assign((size_t)n * n, 0.0);
-      R.assign((size_t)n * nJ, 0.0);
-      for (int a = 0; a < nI; a++)
-        for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
-      // W_{I1,I1} D_{I1,I}
-      for (int a = 0; a < nI1; a++)
-        for (int b = 0; b < nI; b++) {
-          double v = 0;
-          for (int c = 0; c < nI1; c++) v += W[(size_t)I1[a] * n1 + I1[c]] * Dm[(size_t)I1[c] * nS + I[b]];
-          K[(size_t)(nI + a) * n + b] = v;
-          K[(size_t)b * n + nI + a] = v;
-        }
-      // -D2_{:,I1}^T W2 D2_{:,I1}
-      std::vector<double> W2D((size_t)n2 * nI1, 0.0);
-      for (int a = 0; a < n2; a++)
-        for (int c = 0; c < n2; c++) {
-          double w = W2[(size_t)a * n2 + c];
-          if (w == 0.0) continue;
-          for (int b = 0; b < nI1; b++) W2D[(size_t)a * nI1 + b] += w * D2m[(size_t)c * n1 + I1[b]];
-        }
-      for (int a = 0; a < nI1; a++)
-        for (int b = 0; b < nI1; b++) {
-          double v = 0;
-          for (int c = 0; c < n2; c++) v += D2m[(size_t)c * n1 + I1[a]] * W2D[(size_t)c * nI1 + b];
-          K[(size_t)(nI + a) * n + nI + b] = -v;
-        }
-      for (int j = 0; j < nJ; j++) {
-        for (int a = 0; a < nI; a++) {
-          double v = 0;
-          for (int b = 0; b < nB; b++) v += M[(size_t)I[a] * nS + B[b]] * phiB[(size_t)b * nJ + j];
-          R[(size_t)a * nJ + j] = -v;
-        }
-        for (int a = 0; a < nI1; a++) {
-          double v = 0;
-          for (int c = 0; c < n1; c++) v += W[(size_t)I1[a] * n1 + c] * tgt[(size_t)c * nJ + j];
-          R[(size_t)(nI + a) * nJ + j] = v;
-        }
-      }
+      R = solve_eq38(L, T, k, d, X, &s, phiB, nJ, &rx);
     }
-    K0 = K;
-    R0 = R;
-    if (!lu_solve(n, K.data(), nJ, R.data())) throw Fail("singular local extension problem");
-    // residual of the local solve
-    for (int j = 0; j < nJ; j++) {
-      double rn = 0, bn = 0;
-      for (int a = 0; a < n; a++) {
-        double v = -R0[(size_t)a * nJ + j];
-        for (int b = 0; b < n; b++) v += K0[(size_t)a * n + b] * R[(size_t)b * nJ + j];
-        rn += v * v;
-        bn += R0[(size_t)a * nJ + j] * R0[(size_t)a * nJ + j];
-      }
-      if (bn > 0) resid = std::max(resid, std::sqrt(rn / bn));
-      if (d == k + 1) {  // Stokes: the multiplier equals the coarse incidence (D_k^H)_{X,J}
-        double lam = R[(size_t)(n - 1) * nJ + j];
-        lam_dev = std::max(lam_dev, std::fabs(lam - (double)C.D[k].get(X, J[j])));
-      }
-    }
+    resid = std::max(resid, rx);
     for (int a = 0; a < nI; a++) {
       int row = S[I[a]];
       for (int j = 0; j < nJ; j++) {
@@ -1514,68 +1570,6 @@ double mass_targets(const std::vector<double>& M, const int* S, int nS, const Ta
   return tau;
 }
 
-// Extension of nJ space-k traces from the boundary of the coarse entity X of dimension
-// d = k + 1 (a face for the edge space, a cell for the face space) into its interior by
-// the local problem of eq. 3.6 (the system `extend` solves for the PV traces):
-// unknowns the interior dofs, psi on X's constituents and the multiplier lambda of the
-// orthogonality to X's PV trace, with boundary data phiB (nB x nJ, X's boundary dofs
-// in closure order).  Returns the interior values (nI x nJ).
-std::vector<double> extend_eq36(const Level& L, const Transfer& T, int k, int X, const std::vector<double>& phiB,
-                                int nJ) {
-  const int d = k + 1;
-  std::vector<double> M, W, Dm, buf, K, R;
-  const int* S = T.fclo[d][k].row(X);
-  const int nS = T.fclo[d][k].len(X);
-  const uint8_t* in = T.fint[d][k].data() + T.fclo[d][k].rp[X];
-  std::vector<int> I, B;
-  for (int i = 0; i < nS; i++) (in[i] ? I : B).push_back(i);
-  const int nI = (int)I.size(), nB = (int)B.size();
-  assemble_mass(L, T, d, k, X, S, nS, M, buf);
-  const int* S1 = T.cons[d].row(X);
-  const int n1 = T.cons[d].len(X);
-  assemble_mass(L, T, d, d, X, S1, n1, W, buf);
-  restrict_D(L.D[k], S1, n1, S, nS, Dm);
-  std::vector<double> pv(n1), Wp(n1, 0.0), WD((size_t)n1 * nS, 0.0);
-  for (int a = 0; a < n1; a++) pv[a] = T.phi[d][T.cons[d].rp[X] + a] / (double)n1;
-  for (int a = 0; a < n1; a++)
-    for (int b = 0; b < n1; b++) Wp[a] += W[(size_t)a * n1 + b] * pv[b];
-  for (int a = 0; a < n1; a++)
-    for (int c = 0; c < n1; c++) {
-      const double w = W[(size_t)a * n1 + c];
-      if (w == 0.0) continue;
-      for (int i = 0; i < nS; i++) WD[(size_t)a * nS + i] += w * Dm[(size_t)c * nS + i];
-    }
-  const int n = nI + n1 + 1;
-  K.assign((size_t)n * n, 0.0);
-  R.assign((size_t)n * nJ, 0.0);
-  for (int a = 0; a < nI; a++)
-    for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
-  for (int a = 0; a < n1; a++) {
-    for (int b = 0; b < nI; b++) {
-      const double v = WD[(size_t)a * nS + I[b]];
-      K[(size_t)(nI + a) * n + b] = v;
-      K[(size_t)b * n + nI + a] = v;
-    }
-    K[(size_t)(nI + a) * n + nI + n1] = -Wp[a];
-    K[(size_t)(nI + n1) * n + nI + a] = -Wp[a];
-  }
-  for (int j = 0; j < nJ; j++) {
-    for (int a = 0; a < nI; a++) {
-      double v = 0;
-      for (int b = 0; b < nB; b++) v += M[(size_t)I[a] * nS + B[b]] * phiB[(size_t)b * nJ + j];
-      R[(size_t)a * nJ + j] = -v;
-    }
-    for (int a = 0; a < n1; a++) {
-      double v = 0;
-      for (int b = 0; b < nB; b++) v += WD[(size_t)a * nS + B[b]] * phiB[(size_t)b * nJ + j];
-      R[(size_t)(nI + a) * nJ + j] = -v;
-    }
-  }
-  if (!lu_solve(n, K.data(), nJ, R.data())) throw Fail("singular extension of a face trace");
-  R.resize((size_t)nI * nJ);
-  return R;
-}
-
 // Trace targets of the face space for one coarsening (Section 3.3.2's coarse trace
 // spaces with Section 3.3.1's targets): on every coarse face F the targets' traces --
 // their values on F's constituent fine faces -- are made orthogonal, in F's trace
@@ -1647,7 +1641,8 @@ void add_face_traces(const Level& L, const Level& C, const Transfer& T, DCsr& P,
       }
       j0 += fk[F];
     }
-    xv[X] = extend_eq36(L, T, 2, X, phiB, nJ);
+    xv[X] = solve_eq36(L, T, 2, X, phiB, nJ, nullptr);
+    xv[X].resize(xrows[X].size() * (size_t)nJ);  // the interior values
   }
   std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
   for (int F = 0; F < nF; F++) {
@@ -1801,86 +1796,6 @@ std::vector<double> grad_bubbles(const Level& L, const Transfer& T, int d, int Y
   return out;
 }
 
-// Extension of nJ edge-space traces from the boundary of coarse cell X into its
-// interior by the local problem of eq. 3.8 (the same system as `extend` solves for the
-// PV-based functions): unknowns the interior edge values and chi on X's interior faces,
-// with boundary data phiB (nB x nJ, X's boundary edges in closure order) and target
-// s = 0 -- the traces extended here are curl-free on the faces they live on, so their
-// coarse derivative, and with it s, vanishes.  Returns the interior values (nI x nJ).
-std::vector<double> extend_cell_zero_target(const Level& L, const Transfer& T, int X, const std::vector<double>& phiB,
-                                            int nJ) {
-  const int k = 1, d = 3;
-  std::vector<double> M, W, W2, Dm, D2m, buf, K, R;
-  const int* S = T.fclo[d][k].row(X);
-  const int nS = T.fclo[d][k].len(X);
-  const uint8_t* in = T.fint[d][k].data() + T.fclo[d][k].rp[X];
-  std::vector<int> I, B;
-  for (int i = 0; i < nS; i++) (in[i] ? I : B).push_back(i);
-  const int nI = (int)I.size(), nB = (int)B.size();
-  const int* S1 = T.fclo[d][k + 1].row(X);
-  const int n1 = T.fclo[d][k + 1].len(X);
-  const uint8_t* in1 = T.fint[d][k + 1].data() + T.fclo[d][k + 1].rp[X];
-  const int* S2 = T.fclo[d][k + 2].row(X);
-  const int n2 = T.fclo[d][k + 2].len(X);
-  std::vector<int> I1;
-  for (int i = 0; i < n1; i++)
-    if (in1[i]) I1.push_back(i);
-  const int nI1 = (int)I1.size();
-  assemble_mass(L, T, d, k, X, S, nS, M, buf);
-  assemble_mass(L, T, d, k + 1, X, S1, n1, W, buf);
-  assemble_mass(L, T, d, k + 2, X, S2, n2, W2, buf);
-  restrict_D(L.D[k], S1, n1, S, nS, Dm);
-  restrict_D(L.D[k + 1], S2, n2, S1, n1, D2m);
-  // target t = 0 - D_B phi_B on all faces of X
-  std::vector<double> tgt((size_t)n1 * nJ, 0.0);
-  for (int a = 0; a < n1; a++)
-    for (int b = 0; b < nB; b++) {
-      const double dv = Dm[(size_t)a * nS + B[b]];
-      if (dv == 0.0) continue;
-      for (int j = 0; j < nJ; j++) tgt[(size_t)a * nJ + j] -= dv * phiB[(size_t)b * nJ + j];
-    }
-  const int n = nI + nI1;
-  K.assign((size_t)n * n, 0.0);
-  R.assign((size_t)n * nJ, 0.0);
-  for (int a = 0; a < nI; a++)
-    for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
-  for (int a = 0; a < nI1; a++)
-    for (int b = 0; b < nI; b++) {
-      double v = 0;
-      for (int c = 0; c < nI1; c++) v += W[(size_t)I1[a] * n1 + I1[c]] * Dm[(size_t)I1[c] * nS + I[b]];
-      K[(size_t)(nI + a) * n + b] = v;
-      K[(size_t)b * n + nI + a] = v;
-    }
-  std::vector<double> W2D((size_t)n2 * nI1, 0.0);
-  for (int a = 0; a < n2; a++)
-    for (int c = 0; c < n2; c++) {
-      const double w = W2[(size_t)a * n2 + c];
-      if (w == 0.0) continue;
-      for (int b = 0; b < nI1; b++) W2D[(size_t)a * nI1 + b] += w * D2m[(size_t)c * n1 + I1[b]];
-    }
-  for (int a = 0; a < nI1; a++)
-    for (int b = 0; b < nI1; b++) {
-      double v = 0;
-      for (int c = 0; c < n2; c++) v += D2m[(size_t)c * n1 + I1[a]] * W2D[(size_t)c * nI1 + b];
-      K[(size_t)(nI + a) * n + nI + b] = -v;
-    }
-  for (int j = 0; j < nJ; j++) {
-    for (int a = 0; a < nI; a++) {
-      double v = 0;
-      for (int b = 0; b < nB; b++) v += M[(size_t)I[a] * nS + B[b]] * phiB[(size_t)b * nJ + j];
-      R[(size_t)a * nJ + j] = -v;
-    }
-    for (int a = 0; a < nI1; a++) {
-      double v = 0;
-      for (int c = 0; c < n1; c++) v += W[(size_t)I1[a] * n1 + c] * tgt[(size_t)c * nJ + j];
-      R[(size_t)(nI + a) * nJ + j] = v;
-    }
-  }
-  if (!lu_solve(n, K.data(), nJ, R.data())) throw Fail("singular extension of a face bubble");
-  R.resize((size_t)nI * nJ);
-  return R;
-}
-
 // Position of `v` in the sorted list [b, b + n) (it must be there).
 inline int pos_in(const int* b, int n, int v) {
   const int* p = std::lower_bound(b, b + n, v);
@@ -1968,7 +1883,8 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
       }
       j0 += ek[E];
     }
-    fxv[F] = extend_eq36(L, T, 1, F, phiB, nJ);  // F's interior edges x nJ
+    fxv[F] = solve_eq36(L, T, 1, F, phiB, nJ, nullptr);
+    fxv[F].resize(((size_t)nS - Bpos.size()) * nJ);  // F's interior edges x nJ
   }
   for (int F = 0; F < nF; F++) ffirst[F] = next, next += fk[F];
   // 5. cell gradient bubbles
@@ -2020,7 +1936,8 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
         for (int jj = 0; jj < nJF; jj++) phiB[b * nJ + jof(fxcol[F][jj])] = fxv[F][(size_t)a * nJF + jj];
       }
     }
-    xv[X] = extend_cell_zero_target(L, T, X, phiB, nJ);
+    xv[X] = solve_eq38(L, T, 1, 3, X, nullptr, phiB, nJ, nullptr);
+    xv[X].resize(xrows[X].size() * (size_t)nJ);  // the interior values
   }
   std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
   auto put = [&](int row, int col, double v) {
