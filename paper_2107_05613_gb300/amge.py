@@ -22,7 +22,7 @@ _lib = ctypes.CDLL(AMGE_SO)
 AMGE_OK, AMGE_EINVAL, AMGE_ENOMEM, AMGE_ECUDA, AMGE_ENOTCONV, AMGE_ENONFINITE = 0, 1, 2, 3, 4, 5
 AMGE_EAGAIN, AMGE_ETIMEOUT, AMGE_ECANCELED = 6, 7, 8
 AMGE_HCURL, AMGE_HDIV = 2, 3
-AMGE_SETUP_TARGETS = 1
+AMGE_SETUP_TARGETS, AMGE_SETUP_TARGETS2 = 1, 2
 AMGE_FP64, AMGE_FP32_VCYCLE = 0, 1
 AMGE_OP_A, AMGE_OP_P, AMGE_OP_PT, AMGE_OP_G, AMGE_OP_GT, AMGE_OP_SMOOTH_PRE, AMGE_OP_COARSE, AMGE_OP_AG, AMGE_OP_A_WIDE = range(9)
 PROF_CLASSES = ["A_fine", "A_coarse", "GT", "G", "PT", "P", "coarse", "pcg_spmv", "pcg_vec", "vcycle_vec", "AG",
@@ -186,8 +186,9 @@ def amge_setup_upload(form: str, n: int, num_levels: int = 0, beta=None, alpha=N
                       nu_post: int = 1, stream=None, targets: bool = False, flags: int = None) -> Hier:
     """Build the hierarchy of the problem (eq. 2.2 on n^3 Kuhn-split cubes) on the host
     and upload it.  form: 'hcurl' or 'hdiv'; beta / alpha: per-tet coefficients of the
-    derivative / mass term (6 n^3 values, None = 1); targets: AMGE_SETUP_TARGETS (flags,
-    when given, is passed as it is)."""
+    derivative / mass term (6 n^3 values, None = 1); targets: True / 1 for
+    AMGE_SETUP_TARGETS, 2 for AMGE_SETUP_TARGETS2 (flags, when given, is passed as it
+    is)."""
     keep = []
 
     def coef(c):
@@ -200,7 +201,7 @@ def amge_setup_upload(form: str, n: int, num_levels: int = 0, beta=None, alpha=N
         return a.ctypes.data
 
     if flags is None:
-        flags = AMGE_SETUP_TARGETS if targets else 0
+        flags = {0: 0, 1: AMGE_SETUP_TARGETS, 2: AMGE_SETUP_TARGETS2}[int(targets)]
     prob = amge_problem({"hcurl": AMGE_HCURL, "hdiv": AMGE_HDIV}[form], n, num_levels, coef(beta), coef(alpha),
                         nu_pre, nu_post, flags)
     h = ctypes.c_void_p()

@@ -104,8 +104,8 @@ extern "C" amge_status amge_setup_upload(const amge_problem* p, void* stream, am
     amge::set_error("nu_pre / nu_post must be in [1, 8]");
     return AMGE_EINVAL;
   }
-  if ((p->flags & ~AMGE_SETUP_TARGETS) != 0) {
-    amge::set_error("flags must be 0 or AMGE_SETUP_TARGETS");
+  if ((p->flags & ~(AMGE_SETUP_TARGETS | AMGE_SETUP_TARGETS2)) != 0) {
+    amge::set_error("flags must be 0, AMGE_SETUP_TARGETS or AMGE_SETUP_TARGETS2");
     return AMGE_EINVAL;
   }
   const int64_t ntet = 6 * (int64_t)p->n * p->n * p->n;
@@ -121,7 +121,7 @@ extern "C" amge_status amge_setup_upload(const amge_problem* p, void* stream, am
   }
   const int gform = p->form == AMGE_HCURL ? AMGH_FORM_HCURL : AMGH_FORM_HDIV;
   GenHandle g;
-  const int gflags = (p->flags & AMGE_SETUP_TARGETS) ? AMGH_TARGETS : 0;
+  const int gflags = (p->flags & AMGE_SETUP_TARGETS2) ? AMGH_TARGETS2 : (p->flags & AMGE_SETUP_TARGETS) ? AMGH_TARGETS : 0;
   if (amgh_build(gform, p->n, p->num_levels, p->beta, p->alpha, gflags, 0, &g.h) != 0) {
     amge::set_error(std::string("hierarchy setup: ") + amgh_error());
     return AMGE_EINVAL;

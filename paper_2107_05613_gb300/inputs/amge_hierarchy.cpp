@@ -927,9 +927,10 @@ double solve_residual(int n, int nJ, const std::vector<double>& K0, const std::v
 //   [ (W D)_I   0          -W p ] [psi   ] = [ -(W D)_B phi_B  ]
 //   [ 0        -(W p)^T     0   ] [lambda]   [ 0               ]
 // with M the space-k mass on X, W the space-(k+1) mass on its constituents and p the
-// PV trace of X.
+// PV trace of X.  With div_rhs (n1 x nJ, on X's constituents) the divergence rows get
+// W f as well: eq. 3.7's bubbles, D phi = f + c PV with zero boundary data.
 std::vector<double> solve_eq36(const Level& L, const Transfer& T, int k, int X, const std::vector<double>& phiB,
-                               int nJ, double* resid) {
+                               int nJ, double* resid, const std::vector<double>* div_rhs = nullptr) {
   const int d = k + 1;
   std::vector<double> M, W, Dm, buf, K, R;
   const int* S = T.fclo[d][k].row(X);
@@ -977,6 +978,11 @@ std::vector<double> solve_eq36(const Level& L, const Transfer& T, int k, int X, 
       double v = 0;
       for (int b = 0; b < nB; b++) v += WD[(size_t)a * nS + B[b]] * phiB[(size_t)b * nJ + j];
       R[(size_t)(nI + a) * nJ + j] = -v;
+      if (div_rhs) {  // eq. 3.7: the prescribed divergence, W f
+        double f = 0;
+        for (int c = 0; c < n1; c++) f += W[(size_t)a * n1 + c] * (*div_rhs)[(size_t)c * nJ + j];
+        R[(size_t)(nI + a) * nJ + j] += f;
+      }
     }
   }
   const std::vector<double> K0 = K, R0 = R;
@@ -1457,13 +1463,17 @@ void sym_eig(int n, double* A, double* w, double* V) {
 }
 
 // The approximation targets of space k (1 edges, 2 faces) at `level`: the finite
-// element interpolants, on the finest level, of the vector monomials up to degree one
-// -- the constant fields e_i and the linear fields x_j e_i (twelve) -- through the
-// interpolation of continuous linear vector fields (exact for them), carried to
-// `level` by the co-chain projectors of the transfers before it (the signed sum over
-// each coarse entity's chain), as Section 3.3.1 transfers targets to coarse levels.
+// element interpolants, on the finest level, of the vector monomials up to `degree`
+// -- the constant fields e_i and the linear fields x_j e_i (twelve) through the
+// interpolation of continuous linear vector fields (exact for them); with degree 2
+// (faces only) also the quadratic fields x_j x_m e_i (eighteen), whose fluxes through
+// each fine face come from the rule on the edge midpoints with weights 1/3 (exact for
+// quadratics) -- carried to `level` by the co-chain projectors of the transfers before
+// it (the signed sum over each coarse entity's chain), as Section 3.3.1 transfers
+// targets to coarse levels.
 using Targets = std::vector<std::vector<double>>;
-Targets space_targets(const Hier* H, int level, int k) {
+Targets space_targets(const Hier* H, int level, int k, int degree = 1) {
+  REQUIRE(degree == 1 || (degree == 2 && k == 2), "target degree");
   const Level& L0 = H->levels[0];
   const DCsr ph = fine_pihat(L0, k);
   std::vector<double> xv((size_t)3 * L0.cnt[0]);
@@ -1475,6 +1485,29 @@ Targets space_targets(const Hier* H, int level, int k) {
       t[c][e] += ph.v[p];  // e_c
       for (int j = 0; j < 3; j++) t[3 + 3 * c + j][e] += ph.v[p] * xv[3 * (size_t)v + j];  // x_j e_c
     }
+  if (degree == 2) {
+    for (int q = 0; q < 18; q++) t.emplace_back(ph.nr, 0.0);
+    for (int f = 0; f < ph.nr; f++) {
+      const int* vv = L0.clo[2][0].row(f);  // a < b < c: the face's orientation
+      double x[3][3], e1[3], e2[3], nr[3], mid[3][3];
+      for (int a = 0; a < 3; a++) vert_coord(L0, vv[a], x[a]);
+      for (int c = 0; c < 3; c++) e1[c] = x[1][c] - x[0][c], e2[c] = x[2][c] - x[0][c];
+      cross3(e1, e2, nr);  // twice the area normal
+      for (int c = 0; c < 3; c++) {
+        mid[0][c] = 0.5 * (x[0][c] + x[1][c]);
+        mid[1][c] = 0.5 * (x[1][c] + x[2][c]);
+        mid[2][c] = 0.5 * (x[0][c] + x[2][c]);
+      }
+      int q = 12;
+      for (int c = 0; c < 3; c++)
+        for (int j = 0; j < 3; j++)
+          for (int m = j; m < 3; m++, q++) {  // x_j x_m e_c
+            double avg = 0;
+            for (int r = 0; r < 3; r++) avg += mid[r][j] * mid[r][m];
+            t[q][f] = 0.5 * nr[c] * (avg / 3.0);
+          }
+    }
+  }
   for (int l = 0; l < level; l++) {
     const Transfer& T = H->transfers[l];
     for (auto& tc : t) {
@@ -1568,6 +1601,101 @@ double mass_targets(const std::vector<double>& M, const int* S, int nS, const Ta
     tau = std::max(tau, tMt);
   }
   return tau;
+}
+
+// Targets of the cell space (space 3) at `level` for the cross-space bubbles: the
+// scalar monomials up to degree `degree` - 1 (the divergences of the vector targets)
+// through the cell integrals on the finest level (|tau| g(centroid), exact for
+// linear g), carried to `level` by the co-chain projectors.
+Targets cell_targets(const Hier* H, int level, int degree) {
+  const Level& L0 = H->levels[0];
+  const int nc = (int)L0.cnt[3];
+  Targets t(degree >= 2 ? 4 : 1, std::vector<double>(nc, 0.0));
+  for (int c = 0; c < nc; c++) {
+    const int* vv = L0.clo[3][0].row(c);
+    double x[4][3], e[3][3], cr[3], ctr[3] = {0, 0, 0};
+    for (int a = 0; a < 4; a++) {
+      vert_coord(L0, vv[a], x[a]);
+      for (int j = 0; j < 3; j++) ctr[j] += 0.25 * x[a][j];
+    }
+    for (int a = 0; a < 3; a++)
+      for (int j = 0; j < 3; j++) e[a][j] = x[a + 1][j] - x[0][j];
+    cross3(e[1], e[2], cr);
+    const double vol = std::fabs(dot3(e[0], cr)) / 6.0;
+    t[0][c] = vol;
+    for (size_t q = 1; q < t.size(); q++) t[q][c] = vol * ctr[q - 1];
+  }
+  for (int l = 0; l < level; l++) {
+    const Transfer& T = H->transfers[l];
+    for (auto& tc : t) {
+      std::vector<double> u(T.cons[3].rows(), 0.0);
+      for (int X = 0; X < T.cons[3].rows(); X++)
+        for (int64_t p = T.cons[3].rp[X]; p < T.cons[3].rp[X + 1]; p++)
+          u[X] += (double)T.phi[3][p] * tc[T.cons[3].ci[p]];
+      tc.swap(u);
+    }
+  }
+  return t;
+}
+
+// Cross-space bubbles of the face space (eq. 3.7) for one coarsening: in every coarse
+// cell X, the cell-space targets made orthogonal to X's PV trace in the cell mass and
+// filtered (filter_targets) give divergences f; each bubble solves eq. 3.6's system
+// with zero boundary data and D phi = f (+ c PV, c = 0 by the orthogonality).  They
+// keep the coarse divergence onto the enriched cell space and carry the targets'
+// non-constant divergences.  Appended to P (space 2), cell by cell.
+void add_div_cross_bubbles(const Level& L, const Transfer& T, DCsr& P, const Targets& ctg, BubbleStats& st) {
+  const int nt = (int)ctg.size();
+  const int nX = T.cons[3].rows();
+  std::vector<std::vector<double>> xv(nX);
+  std::vector<std::vector<int>> xrows(nX);
+  std::vector<int> xk(nX, 0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int X = 0; X < nX; X++) {
+    std::vector<double> W, buf, mt, fkeep;
+    const int* S1 = T.cons[3].row(X);
+    const int n1 = T.cons[3].len(X);
+    assemble_mass(L, T, 3, 3, X, S1, n1, W, buf);
+    std::vector<double> pv(n1), Wp(n1, 0.0);
+    for (int a = 0; a < n1; a++) pv[a] = T.phi[3][T.cons[3].rp[X] + a] / (double)n1;
+    double pWp = 0;
+    for (int a = 0; a < n1; a++) {
+      for (int b = 0; b < n1; b++) Wp[a] += W[(size_t)a * n1 + b] * pv[b];
+      pWp += pv[a] * Wp[a];
+    }
+    const double tau = mass_targets(W, S1, n1, ctg, mt);
+    std::vector<double> phi((size_t)n1 * nt);
+    for (int c = 0; c < nt; c++) {
+      double pWt = 0;
+      for (int a = 0; a < n1; a++) pWt += Wp[a] * ctg[c][S1[a]];
+      for (int a = 0; a < n1; a++) phi[(size_t)a * nt + c] = ctg[c][S1[a]] - pv[a] * (pWt / pWp);
+    }
+    const int nf = filter_targets(n1, nt, phi, [&](int a, int b) { return W[(size_t)a * n1 + b]; }, tau, fkeep);
+    const int* S = T.fclo[3][2].row(X);
+    const int nS = T.fclo[3][2].len(X);
+    const uint8_t* in = T.fint[3][2].data() + T.fclo[3][2].rp[X];
+    size_t nB = 0;
+    for (int i = 0; i < nS; i++)
+      if (in[i]) xrows[X].push_back(S[i]);
+      else nB++;
+    if (nf == 0 || xrows[X].empty()) continue;
+    std::vector<double> f((size_t)n1 * nf);  // the divergences, one column per bubble
+    for (int i = 0; i < nf; i++)
+      for (int a = 0; a < n1; a++) f[(size_t)a * nf + i] = fkeep[(size_t)i * n1 + a];
+    const std::vector<double> zeroB(nB * (size_t)nf, 0.0);
+    xv[X] = solve_eq36(L, T, 2, X, zeroB, nf, nullptr, &f);
+    xv[X].resize(xrows[X].size() * (size_t)nf);
+    xk[X] = nf;
+  }
+  std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
+  int next = P.nc;
+  for (int X = 0; X < nX; X++) {
+    const int nI = (int)xrows[X].size();
+    for (int i = 0; i < xk[X]; i++, next++)
+      for (int a = 0; a < nI; a++)
+        if (xv[X][(size_t)a * xk[X] + i] != 0.0) extra[xrows[X][a]].emplace_back(next, xv[X][(size_t)a * xk[X] + i]);
+  }
+  append_columns(P, extra, next, st);
 }
 
 // Trace targets of the face space for one coarsening (Section 3.3.2's coarse trace
@@ -2003,8 +2131,11 @@ Hier* build(int form, int n, int num_levels, const double* beta, const double* a
   auto t0 = std::chrono::steady_clock::now();
   REQUIRE(form == AMGH_FORM_HCURL || form == AMGH_FORM_HDIV, "form");
   REQUIRE(n >= 1 && n <= 127, "n out of range");
-  REQUIRE((flags & ~(AMGH_ALL_SPACES | AMGH_TARGETS)) == 0, "unknown flags");
-  const bool all_spaces = (flags & AMGH_ALL_SPACES) != 0, targets = (flags & AMGH_TARGETS) != 0;
+  REQUIRE((flags & ~(AMGH_ALL_SPACES | AMGH_TARGETS | AMGH_TARGETS2)) == 0, "unknown flags");
+  const bool all_spaces = (flags & AMGH_ALL_SPACES) != 0;
+  const int tdeg = (flags & AMGH_TARGETS2) ? 2 : (flags & AMGH_TARGETS) ? 1 : 0;
+  const bool targets = tdeg > 0;
+  REQUIRE(tdeg < 2 || form == AMGH_FORM_HDIV, "degree-two targets are built for H(div) only");
   REQUIRE(!(targets && all_spaces), "approximation targets and the auxiliary-space data exclude each other");
   Hier* H = new Hier;
   try {
@@ -2044,9 +2175,10 @@ Hier* build(int form, int n, int num_levels, const double* beta, const double* a
         // the last coarsening: the targets' D-free bubbles join the coarsest space,
         // whose matrix is then the Galerkin product with the enlarged prolongator
         Stage s("approximation targets");
-        const Targets tg = space_targets(H, l, kf);
+        const Targets tg = space_targets(H, l, kf, tdeg);
         if (kf == 2) {
           add_face_traces(L, C, T, T.P[kf], tg, bst);
+          if (tdeg >= 2) add_div_cross_bubbles(L, T, T.P[kf], cell_targets(H, l, tdeg), bst);
           add_div_bubbles(L, T, T.P[kf], tg, bst);
         }
         else add_curl_bubbles(L, C, T, T.P[kf], tg, bst);

@@ -29,7 +29,7 @@ extern "C" {
 
 enum { AMGH_FORM_HCURL = 1, AMGH_FORM_HDIV = 2 };
 enum { AMGH_KIND_A = 0, AMGH_KIND_P = 1, AMGH_KIND_D = 2, AMGH_KIND_PI = 3, AMGH_KIND_PIHAT = 4 };
-enum { AMGH_ALL_SPACES = 1, AMGH_TARGETS = 2 };
+enum { AMGH_ALL_SPACES = 1, AMGH_TARGETS = 2, AMGH_TARGETS2 = 4 };
 
 /* Build the hierarchy on an n^3 Kuhn-split unit cube.
  *   form        AMGH_FORM_HCURL (Nedelec edges) or AMGH_FORM_HDIV (Raviart-Thomas faces)
@@ -48,6 +48,9 @@ enum { AMGH_ALL_SPACES = 1, AMGH_TARGETS = 2 };
  *               eqs. 3.6 / 3.8, become extra coarse basis functions (columns of P
  *               after the coarse entities' ones); the coarsest matrix is the Galerkin
  *               product P^T A P with that P.
+ *               AMGH_TARGETS2 (H(div) only): the same with the monomials of degree
+ *               <= 2, which also brings the cross-space bubbles of eq. 3.7 (the
+ *               targets' non-constant divergences) into the coarsest space.
  *   nthreads    OpenMP threads (<= 0: library default).
  * Returns 0 and a handle in *out, or nonzero with amgh_error() describing it. */
 int amgh_build(int form, int n, int num_levels, const double* beta, const double* alpha,

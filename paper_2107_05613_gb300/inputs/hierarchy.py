@@ -127,9 +127,10 @@ def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=Non
     assembly: also return the fine assembly of A_0 as a gather (diagnostics
     "assembly": dict of K, M [6, s, s], coff, ccell, cidx; see amge_hierarchy.h).
     targets: enrich the last coarsening with the degree-one polynomial approximation
-    targets (Sections 3.3.1-3.3.3; AMGH_TARGETS in amge_hierarchy.h): P[-1] gains
-    columns after the coarse entities' ones and A[-1] is P[-1]^T A[-2] P[-1];
-    diagnostics "target_functions", "target_constraint".
+    targets (Sections 3.3.1-3.3.3; AMGH_TARGETS in amge_hierarchy.h), or with 2 (H(div)
+    only, AMGH_TARGETS2) the degree-two ones and the cross-space bubbles of eq. 3.7:
+    P[-1] gains columns after the coarse entities' ones and A[-1] is
+    P[-1]^T A[-2] P[-1]; diagnostics "target_functions", "target_constraint".
     """
     lib = _load()
     kf = FORMS[form]
@@ -140,7 +141,10 @@ def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=Non
         if arr is not None and arr.shape != (nt,):
             raise ValueError(f"coefficient array must have {nt} entries")
     h = ctypes.c_void_p()
-    flags = (1 if all_spaces else 0) | (2 if targets else 0)   # AMGH_ALL_SPACES, AMGH_TARGETS
+    deg = int(targets)
+    if deg not in (0, 1, 2):
+        raise ValueError("targets: False / True (degree one) or 2")
+    flags = (1 if all_spaces else 0) | {0: 0, 1: 2, 2: 4}[deg]   # AMGH_ALL_SPACES, AMGH_TARGETS(2)
     rc = lib.amgh_build(kf, n, num_levels, None if b is None else b.ctypes.data,
                         None if a is None else a.ctypes.data, flags, nthreads, ctypes.byref(h))
     if rc != 0:

@@ -54,7 +54,7 @@ def test_validation_without_gpu(lib):
     # problem-level setup: unknown flag bits are refused before any CUDA call
     from paper_2107_05613_gb300.amge import AMGE_HCURL, AMGE_SETUP_TARGETS, amge_problem
 
-    for flags, ok in ((4, False), (AMGE_SETUP_TARGETS | 2, False)):
+    for flags, ok in ((4, False), (AMGE_SETUP_TARGETS | 8, False)):
         p = amge_problem(AMGE_HCURL, 4, 0, None, None, 1, 1, flags)
         assert lib.amge_setup_upload(ctypes.byref(p), None, ctypes.byref(out)) == 1
         assert b"flags" in lib.amge_last_error()
