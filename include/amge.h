@@ -124,10 +124,10 @@ typedef struct amge_hier amge_hier; /* opaque, device-resident hierarchy */
  *               filtered of linear dependence, extended by eqs. 3.6 / 3.8, as extra
  *               columns of P after the coarse entities' ones); the coarsest space then
  *               reproduces every linear field, and the coarsest matrix is the Galerkin
- *               product P^T A P.  AMGE_SETUP_TARGETS2 (H(div) only): the same with
- *               the monomials of degree <= 2 and the cross-space bubbles of eq. 3.7;
- *               the coarsest space then reproduces every quadratic field.  Other
- *               bits: AMGE_EINVAL.
+ *               product P^T A P.  AMGE_SETUP_TARGETS2: the same with the monomials
+ *               of degree <= 2 and the cross-space bubbles of eqs. 3.7 / 3.9; the
+ *               coarsest space then reproduces every quadratic field.  Other bits:
+ *               AMGE_EINVAL.
  * Tetrahedron t = 6 ((i n + j) n + k) + p lies in cube (i, j, k) (i, j, k the x, y, z
  * cube indices), p = 0 .. 5 the Kuhn permutation index in the order
  * (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y), (z,y,x) of the monotone path from the

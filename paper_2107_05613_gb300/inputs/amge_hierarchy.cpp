@@ -1466,14 +1466,15 @@ void sym_eig(int n, double* A, double* w, double* V) {
 // element interpolants, on the finest level, of the vector monomials up to `degree`
 // -- the constant fields e_i and the linear fields x_j e_i (twelve) through the
 // interpolation of continuous linear vector fields (exact for them); with degree 2
-// (faces only) also the quadratic fields x_j x_m e_i (eighteen), whose fluxes through
-// each fine face come from the rule on the edge midpoints with weights 1/3 (exact for
-// quadratics) -- carried to `level` by the co-chain projectors of the transfers before
+// also the quadratic fields x_j x_m e_i (eighteen), whose edge integrals come from
+// Simpson's rule and whose fluxes through each fine face from the rule on the edge
+// midpoints with weights 1/3 (both exact for quadratics) -- carried to `level` by the
+// co-chain projectors of the transfers before
 // it (the signed sum over each coarse entity's chain), as Section 3.3.1 transfers
 // targets to coarse levels.
 using Targets = std::vector<std::vector<double>>;
 Targets space_targets(const Hier* H, int level, int k, int degree = 1) {
-  REQUIRE(degree == 1 || (degree == 2 && k == 2), "target degree");
+  REQUIRE(degree == 1 || degree == 2, "target degree");
   const Level& L0 = H->levels[0];
   const DCsr ph = fine_pihat(L0, k);
   std::vector<double> xv((size_t)3 * L0.cnt[0]);
@@ -1485,7 +1486,22 @@ Targets space_targets(const Hier* H, int level, int k, int degree = 1) {
       t[c][e] += ph.v[p];  // e_c
       for (int j = 0; j < 3; j++) t[3 + 3 * c + j][e] += ph.v[p] * xv[3 * (size_t)v + j];  // x_j e_c
     }
-  if (degree == 2) {
+  if (degree == 2 && k == 1) {
+    // edge integrals of the tangential component by Simpson's rule (exact for quadratics)
+    for (int q = 0; q < 18; q++) t.emplace_back(ph.nr, 0.0);
+    for (int e = 0; e < ph.nr; e++) {
+      const int* vv = L0.clo[1][0].row(e);  // a < b: the edge's orientation
+      double x[2][3], m[3], tv[3];
+      for (int a = 0; a < 2; a++) vert_coord(L0, vv[a], x[a]);
+      for (int c = 0; c < 3; c++) m[c] = 0.5 * (x[0][c] + x[1][c]), tv[c] = x[1][c] - x[0][c];
+      int q = 12;
+      for (int c = 0; c < 3; c++)
+        for (int j = 0; j < 3; j++)
+          for (int mm = j; mm < 3; mm++, q++)  // x_j x_mm e_c
+            t[q][e] = tv[c] * (x[0][j] * x[0][mm] + 4.0 * m[j] * m[mm] + x[1][j] * x[1][mm]) / 6.0;
+    }
+  }
+  if (degree == 2 && k == 2) {
     for (int q = 0; q < 18; q++) t.emplace_back(ph.nr, 0.0);
     for (int f = 0; f < ph.nr; f++) {
       const int* vv = L0.clo[2][0].row(f);  // a < b < c: the face's orientation
@@ -1798,8 +1814,60 @@ void add_face_traces(const Level& L, const Level& C, const Transfer& T, DCsr& P,
 // functions are appended to P (space 2) as columns after the coarse faces, cell by
 // cell.  (For the constant fields the projection vanishes: a constant field is mass-
 // orthogonal to the curls of edge bubbles, which span these bubbles.)
-void add_div_bubbles(const Level& L, const Transfer& T, DCsr& P, const Targets& tgt, BubbleStats& st) {
+// The div-free bubbles of coarse cell X kept from the targets' projections (see
+// add_div_bubbles): nkeep functions on X's interior faces (listed in `rows`), and the
+// largest relative divergence of one of them on a constituent in *cmax.
+std::vector<double> div_bubbles_cell(const Level& L, const Transfer& T, int X, const Targets& tgt,
+                                     std::vector<int>& rows, int& nkeep, double* cmax) {
   const int nt = (int)tgt.size();
+  std::vector<double> vals, M, buf, Dm, K, R, mt;
+  nkeep = 0;
+  rows.clear();
+  const int* S = T.fclo[3][2].row(X);
+  const int nS = T.fclo[3][2].len(X);
+  const uint8_t* in = T.fint[3][2].data() + T.fclo[3][2].rp[X];
+  std::vector<int> I;
+  for (int i = 0; i < nS; i++)
+    if (in[i]) I.push_back(i);
+  const int nI = (int)I.size();
+  const int* S3 = T.cons[3].row(X);
+  const int n3 = T.cons[3].len(X);
+  if (nI == 0 || n3 < 2) return vals;
+  assemble_mass(L, T, 3, 2, X, S, nS, M, buf);
+  restrict_D(L.D[2], S3, n3, S, nS, Dm);
+  const int nc = n3 - 1, n = nI + nc;
+  K.assign((size_t)n * n, 0.0);
+  R.assign((size_t)n * nt, 0.0);
+  for (int a = 0; a < nI; a++)
+    for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
+  for (int r = 0; r < nc; r++)
+    for (int b = 0; b < nI; b++) {
+      const double v = Dm[(size_t)r * nS + I[b]];
+      K[(size_t)(nI + r) * n + b] = v;
+      K[(size_t)b * n + nI + r] = v;
+    }
+  const double tau = mass_targets(M, S, nS, tgt, mt);
+  for (int a = 0; a < nI; a++)
+    for (int c = 0; c < nt; c++) R[(size_t)a * nt + c] = mt[(size_t)I[a] * nt + c];
+  if (!lu_solve(n, K.data(), nt, R.data())) throw Fail("singular bubble projection");
+  R.resize((size_t)nI * nt);
+  nkeep = filter_targets(nI, nt, R, [&](int a, int b) { return M[(size_t)I[a] * nS + I[b]]; }, tau, vals);
+  // the divergence of each kept function on every constituent, the dropped one included
+  for (int i = 0; i < nkeep; i++) {
+    const double* psi = vals.data() + (size_t)i * nI;
+    double pm = 0;
+    for (int a = 0; a < nI; a++) pm = std::max(pm, std::fabs(psi[a]));
+    for (int r = 0; r < n3; r++) {
+      double d = 0;
+      for (int b = 0; b < nI; b++) d += Dm[(size_t)r * nS + I[b]] * psi[b];
+      if (pm > 0 && cmax) *cmax = std::max(*cmax, std::fabs(d) / pm);
+    }
+  }
+  for (int a = 0; a < nI; a++) rows.push_back(S[I[a]]);
+  return vals;
+}
+
+void add_div_bubbles(const Level& L, const Transfer& T, DCsr& P, const Targets& tgt, BubbleStats& st) {
   const int nX = T.cons[3].rows();
   std::vector<std::vector<double>> vals(nX);
   std::vector<std::vector<int>> rowsX(nX);
@@ -1807,48 +1875,9 @@ void add_div_bubbles(const Level& L, const Transfer& T, DCsr& P, const Targets& 
   double cmax = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(max : cmax)
   for (int X = 0; X < nX; X++) {
-    std::vector<double> M, buf, Dm, K, R, mt;
-    const int* S = T.fclo[3][2].row(X);
-    const int nS = T.fclo[3][2].len(X);
-    const uint8_t* in = T.fint[3][2].data() + T.fclo[3][2].rp[X];
-    std::vector<int> I;
-    for (int i = 0; i < nS; i++)
-      if (in[i]) I.push_back(i);
-    const int nI = (int)I.size();
-    const int* S3 = T.cons[3].row(X);
-    const int n3 = T.cons[3].len(X);
-    if (nI == 0 || n3 < 2) continue;
-    assemble_mass(L, T, 3, 2, X, S, nS, M, buf);
-    restrict_D(L.D[2], S3, n3, S, nS, Dm);
-    const int nc = n3 - 1, n = nI + nc;
-    K.assign((size_t)n * n, 0.0);
-    R.assign((size_t)n * nt, 0.0);
-    for (int a = 0; a < nI; a++)
-      for (int b = 0; b < nI; b++) K[(size_t)a * n + b] = M[(size_t)I[a] * nS + I[b]];
-    for (int r = 0; r < nc; r++)
-      for (int b = 0; b < nI; b++) {
-        const double v = Dm[(size_t)r * nS + I[b]];
-        K[(size_t)(nI + r) * n + b] = v;
-        K[(size_t)b * n + nI + r] = v;
-      }
-    const double tau = mass_targets(M, S, nS, tgt, mt);
-    for (int a = 0; a < nI; a++)
-      for (int c = 0; c < nt; c++) R[(size_t)a * nt + c] = mt[(size_t)I[a] * nt + c];
-    if (!lu_solve(n, K.data(), nt, R.data())) throw Fail("singular bubble projection");
-    R.resize((size_t)nI * nt);
-    nkeep[X] = filter_targets(nI, nt, R, [&](int a, int b) { return M[(size_t)I[a] * nS + I[b]]; }, tau, vals[X]);
-    // the divergence of each kept function on every constituent, the dropped one included
-    for (int i = 0; i < nkeep[X]; i++) {
-      const double* psi = vals[X].data() + (size_t)i * nI;
-      double pm = 0;
-      for (int a = 0; a < nI; a++) pm = std::max(pm, std::fabs(psi[a]));
-      for (int r = 0; r < n3; r++) {
-        double d = 0;
-        for (int b = 0; b < nI; b++) d += Dm[(size_t)r * nS + I[b]] * psi[b];
-        if (pm > 0) cmax = std::max(cmax, std::fabs(d) / pm);
-      }
-    }
-    for (int a = 0; a < nI; a++) rowsX[X].push_back(S[I[a]]);
+    double cx = 0;
+    vals[X] = div_bubbles_cell(L, T, X, tgt, rowsX[X], nkeep[X], &cx);
+    cmax = std::max(cmax, cx);
   }
   st.constraint = std::max(st.constraint, cmax);
   std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
@@ -1932,21 +1961,27 @@ inline int pos_in(const int* b, int n, int v) {
 }
 
 // Approximation targets of the edge space for one coarsening (Section 3.3.1 with the
-// coarse trace spaces of Section 3.3.2 and the D-free bubbles of Section 3.3.3):
+// coarse trace spaces of Section 3.3.2 and the bubbles of Section 3.3.3):
 //  1. on every coarse edge E, the targets' traces (values on E's fine edges) made
 //     orthogonal in E's trace mass to E's PV trace and filtered: new dofs of E;
 //  2. those extended into every coarse face F containing E by eq. 3.6 (multiplier 0:
 //     a trace orthogonal to the PV trace has zero net circulation);
-//  3. on every coarse face F, the targets' projections onto F's gradient bubbles;
-//  4. the functions of 1-3 extended into every coarse cell X by eq. 3.8 with a zero
-//     target -- their surface curls on X's faces vanish, so their coarse curl does;
+//  3. on every coarse face F, the targets' projections onto F's gradient bubbles, and
+//     with the face-space targets `dtg` (degree two) the cross-space bubbles of eq. 3.7
+//     on F: surface curl = each face-space target trace on F orthogonal to F's PV
+//     trace (filtered), zero on F's boundary;
+//  4. the functions of 1-3 extended into every coarse cell X by eq. 3.8 -- target zero
+//     for those whose surface curls vanish, for a cross-space bubble of F the eq. 3.6
+//     extension into X of its curl trace -- and with `dtg` the cross-space bubbles of
+//     eq. 3.9 in X: curl = each of X's div-free face-space bubbles (the face-space
+//     targets' D-free projections), zero on X's boundary;
 //  5. in every coarse cell X, its own gradient bubbles.
-// For the constant and linear fields the curl is constant, so the cross-space
-// bubbles of eqs. 3.7 / 3.9, whose curls are non-constant traces or div-free bubbles,
-// would receive no target component; they are not built.  The functions are appended
-// to P (space 1) after the coarse edges: edge, then face, then cell functions.
+// The functions are appended to P (space 1) after the coarse edges: edge functions,
+// then per face its gradient then cross-space bubbles, then per cell its cross-space
+// then gradient bubbles.  (For degree-one targets the curl is constant and the cross-
+// space bubbles receive no component, so `dtg` is given for degree two only.)
 void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P, const Targets& tgt,
-                      BubbleStats& st) {
+                      const Targets* dtg, BubbleStats& st) {
   const int nt = (int)tgt.size();
   const int nE = T.cons[1].rows(), nF = T.cons[2].rows(), nX = T.cons[3].rows();
   // 1. edge traces
@@ -1978,10 +2013,10 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
   std::vector<int> efirst(nE), ffirst(nF), cfirst(nX);
   int next = P.nc;
   for (int E = 0; E < nE; E++) efirst[E] = next, next += ek[E];
-  // 2. edge functions extended into the coarse faces; 3. face gradient bubbles
-  std::vector<std::vector<double>> fxv(nF), fv(nF);
+  // 2. edge functions extended into the coarse faces; 3. face gradient and cross-space bubbles
+  std::vector<std::vector<double>> fxv(nF), fv(nF), fcv(nF), ff(nF);
   std::vector<std::vector<int>> fxcol(nF), frows(nF);
-  std::vector<int> fk(nF, 0);
+  std::vector<int> fk(nF, 0), fck(nF, 0);
 #pragma omp parallel for schedule(dynamic, 16)
   for (int F = 0; F < nF; F++) {
     fv[F] = grad_bubbles(L, T, 2, F, tgt, frows[F], fk[F]);
@@ -1991,11 +2026,42 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
     std::vector<int> Bpos;
     for (int i = 0; i < nS; i++)
       if (!in[i]) Bpos.push_back(i);
+    const size_t nIF = (size_t)nS - Bpos.size();
+    if (dtg && nIF > 0) {  // eq. 3.7 on F
+      std::vector<double> Mf, buf, mt;
+      const int* SF = T.cons[2].row(F);
+      const int nSF = T.cons[2].len(F);
+      const int ntd = (int)dtg->size();
+      assemble_mass(L, T, 2, 2, F, SF, nSF, Mf, buf);
+      std::vector<double> pv(nSF), Mp(nSF, 0.0);
+      for (int a = 0; a < nSF; a++) pv[a] = T.phi[2][T.cons[2].rp[F] + a] / (double)nSF;
+      double pMp = 0;
+      for (int a = 0; a < nSF; a++) {
+        for (int b = 0; b < nSF; b++) Mp[a] += Mf[(size_t)a * nSF + b] * pv[b];
+        pMp += pv[a] * Mp[a];
+      }
+      const double tau = mass_targets(Mf, SF, nSF, *dtg, mt);
+      std::vector<double> phi((size_t)nSF * ntd);
+      for (int c = 0; c < ntd; c++) {
+        double pMt = 0;
+        for (int a = 0; a < nSF; a++) pMt += Mp[a] * (*dtg)[c][SF[a]];
+        for (int a = 0; a < nSF; a++) phi[(size_t)a * ntd + c] = (*dtg)[c][SF[a]] - pv[a] * (pMt / pMp);
+      }
+      fck[F] = filter_targets(nSF, ntd, phi, [&](int a, int b) { return Mf[(size_t)a * nSF + b]; }, tau, ff[F]);
+      if (fck[F] > 0) {
+        std::vector<double> rhs((size_t)nSF * fck[F]);
+        for (int i = 0; i < fck[F]; i++)
+          for (int a = 0; a < nSF; a++) rhs[(size_t)a * fck[F] + i] = ff[F][(size_t)i * nSF + a];
+        const std::vector<double> zeroB(Bpos.size() * (size_t)fck[F], 0.0);
+        fcv[F] = solve_eq36(L, T, 1, F, zeroB, fck[F], nullptr, &rhs);
+        fcv[F].resize(nIF * fck[F]);  // F's interior edges x fck
+      }
+    }
     const int* Ef = C.clo[2][1].row(F);
     const int nEf = C.clo[2][1].len(F);
     int nJ = 0;
     for (int q = 0; q < nEf; q++) nJ += ek[Ef[q]];
-    if (nJ == 0 || Bpos.size() == (size_t)nS) continue;
+    if (nJ == 0 || nIF == 0) continue;
     std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
     int j0 = 0;
     for (int q = 0; q < nEf; q++) {
@@ -2012,17 +2078,20 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
       j0 += ek[E];
     }
     fxv[F] = solve_eq36(L, T, 1, F, phiB, nJ, nullptr);
-    fxv[F].resize(((size_t)nS - Bpos.size()) * nJ);  // F's interior edges x nJ
+    fxv[F].resize(nIF * nJ);  // F's interior edges x nJ
   }
-  for (int F = 0; F < nF; F++) ffirst[F] = next, next += fk[F];
-  // 5. cell gradient bubbles
-  std::vector<std::vector<double>> cv(nX);
-  std::vector<std::vector<int>> crows(nX);
-  std::vector<int> ck(nX, 0);
+  for (int F = 0; F < nF; F++) ffirst[F] = next, next += fk[F] + fck[F];
+  // 5. cell gradient bubbles; the face space's div-free bubbles of every cell (eq. 3.9)
+  std::vector<std::vector<double>> cv(nX), bv(nX);
+  std::vector<std::vector<int>> crows(nX), brows(nX);
+  std::vector<int> ck(nX, 0), bk(nX, 0);
 #pragma omp parallel for schedule(dynamic, 16)
-  for (int X = 0; X < nX; X++) cv[X] = grad_bubbles(L, T, 3, X, tgt, crows[X], ck[X]);
-  for (int X = 0; X < nX; X++) cfirst[X] = next, next += ck[X];
-  // 4. the edge and face functions extended into every cell
+  for (int X = 0; X < nX; X++) {
+    cv[X] = grad_bubbles(L, T, 3, X, tgt, crows[X], ck[X]);
+    if (dtg) bv[X] = div_bubbles_cell(L, T, X, *dtg, brows[X], bk[X], nullptr);
+  }
+  for (int X = 0; X < nX; X++) cfirst[X] = next, next += bk[X] + ck[X];
+  // 4. the edge and face functions extended into every cell, and eq. 3.9's bubbles
   std::vector<std::vector<double>> xv(nX);
   std::vector<std::vector<int>> xcol(nX), xrows(nX);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -2042,8 +2111,9 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
     for (int q = 0; q < nEx; q++)
       for (int i = 0; i < ek[Ex[q]]; i++) xcol[X].push_back(efirst[Ex[q]] + i);
     for (int q = 0; q < nFx; q++)
-      for (int i = 0; i < fk[Fx[q]]; i++) xcol[X].push_back(ffirst[Fx[q]] + i);
-    const int nJ = (int)xcol[X].size();  // ascending: edges' columns precede faces'
+      for (int i = 0; i < fk[Fx[q]] + fck[Fx[q]]; i++) xcol[X].push_back(ffirst[Fx[q]] + i);
+    for (int i = 0; i < bk[X]; i++) xcol[X].push_back(cfirst[X] + i);
+    const int nJ = (int)xcol[X].size();  // ascending: edges', faces', then X's own columns
     if (nJ == 0) continue;
     auto jof = [&](int col) { return pos_in(xcol[X].data(), nJ, col); };
     std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
@@ -2060,11 +2130,54 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
         const int nIF = (int)frows[F].size();
         const int a = pos_in(frows[F].data(), nIF, y);
         for (int i = 0; i < fk[F]; i++) phiB[b * nJ + jof(ffirst[F] + i)] = fv[F][(size_t)i * nIF + a];
+        for (int i = 0; i < fck[F]; i++)
+          phiB[b * nJ + jof(ffirst[F] + fk[F] + i)] = fcv[F][(size_t)a * fck[F] + i];
         const int nJF = (int)fxcol[F].size();
         for (int jj = 0; jj < nJF; jj++) phiB[b * nJ + jof(fxcol[F][jj])] = fxv[F][(size_t)a * nJF + jj];
       }
     }
-    xv[X] = solve_eq38(L, T, 1, 3, X, nullptr, phiB, nJ, nullptr);
+    std::vector<double> sx;  // eq. 3.8 targets on X's faces (closure order); zero without dtg
+    if (dtg) {
+      const int* S1 = T.fclo[3][2].row(X);
+      const int n1 = T.fclo[3][2].len(X);
+      const uint8_t* in1 = T.fint[3][2].data() + T.fclo[3][2].rp[X];
+      std::vector<int> B1, I1;
+      for (int i = 0; i < n1; i++) (in1[i] ? I1 : B1).push_back(i);
+      sx.assign((size_t)n1 * nJ, 0.0);
+      // a face cross-space bubble's curl: its trace f on F, extended into X by eq. 3.6
+      int nd = 0;
+      for (int q = 0; q < nFx; q++) nd += fck[Fx[q]];
+      if (nd > 0) {
+        std::vector<double> pB(B1.size() * (size_t)nd, 0.0);
+        std::vector<int> dcol;
+        for (int q = 0; q < nFx; q++) {
+          const int F = Fx[q];
+          const int* SF = T.cons[2].row(F);
+          const int nSF = T.cons[2].len(F);
+          for (int i = 0; i < fck[F]; i++) {
+            const int jd = (int)dcol.size();
+            dcol.push_back(ffirst[F] + fk[F] + i);
+            for (int a = 0; a < nSF; a++) {
+              const int bi = pos_in(B1.data(), (int)B1.size(), pos_in(S1, n1, SF[a]));
+              pB[(size_t)bi * nd + jd] = ff[F][(size_t)i * nSF + a];
+            }
+          }
+        }
+        const std::vector<double> ext = solve_eq36(L, T, 2, X, pB, nd, nullptr);
+        for (int jd = 0; jd < nd; jd++) {
+          const int j = jof(dcol[jd]);
+          for (size_t bi = 0; bi < B1.size(); bi++) sx[(size_t)B1[bi] * nJ + j] = pB[bi * nd + jd];
+          for (size_t a = 0; a < I1.size(); a++) sx[(size_t)I1[a] * nJ + j] = ext[a * nd + jd];
+        }
+      }
+      // eq. 3.9: curl = X's div-free face-space bubbles (zero on X's boundary faces)
+      const int nIb = (int)brows[X].size();
+      for (int i = 0; i < bk[X]; i++) {
+        const int j = jof(cfirst[X] + i);
+        for (int a = 0; a < nIb; a++) sx[(size_t)I1[a] * nJ + j] = bv[X][(size_t)i * nIb + a];
+      }
+    }
+    xv[X] = solve_eq38(L, T, 1, 3, X, dtg ? &sx : nullptr, phiB, nJ, nullptr);
     xv[X].resize(xrows[X].size() * (size_t)nJ);  // the interior values
   }
   std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
@@ -2080,6 +2193,8 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
     const int nIF = (int)frows[F].size(), nJF = (int)fxcol[F].size();
     for (int i = 0; i < fk[F]; i++)
       for (int a = 0; a < nIF; a++) put(frows[F][a], ffirst[F] + i, fv[F][(size_t)i * nIF + a]);
+    for (int i = 0; i < fck[F]; i++)
+      for (int a = 0; a < nIF; a++) put(frows[F][a], ffirst[F] + fk[F] + i, fcv[F][(size_t)a * fck[F] + i]);
     for (int a = 0; a < nIF && nJF > 0; a++)
       for (int jj = 0; jj < nJF; jj++) put(frows[F][a], fxcol[F][jj], fxv[F][(size_t)a * nJF + jj]);
   }
@@ -2089,7 +2204,7 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
       for (int j = 0; j < nJ; j++) put(xrows[X][a], xcol[X][j], xv[X][(size_t)a * nJ + j]);
     const int nIX = (int)crows[X].size();
     for (int i = 0; i < ck[X]; i++)
-      for (int a = 0; a < nIX; a++) put(crows[X][a], cfirst[X] + i, cv[X][(size_t)i * nIX + a]);
+      for (int a = 0; a < nIX; a++) put(crows[X][a], cfirst[X] + bk[X] + i, cv[X][(size_t)i * nIX + a]);
   }
   append_columns(P, extra, next, st);
 }
@@ -2135,7 +2250,6 @@ Hier* build(int form, int n, int num_levels, const double* beta, const double* a
   const bool all_spaces = (flags & AMGH_ALL_SPACES) != 0;
   const int tdeg = (flags & AMGH_TARGETS2) ? 2 : (flags & AMGH_TARGETS) ? 1 : 0;
   const bool targets = tdeg > 0;
-  REQUIRE(tdeg < 2 || form == AMGH_FORM_HDIV, "degree-two targets are built for H(div) only");
   REQUIRE(!(targets && all_spaces), "approximation targets and the auxiliary-space data exclude each other");
   Hier* H = new Hier;
   try {
@@ -2181,7 +2295,12 @@ Hier* build(int form, int n, int num_levels, const double* beta, const double* a
           if (tdeg >= 2) add_div_cross_bubbles(L, T, T.P[kf], cell_targets(H, l, tdeg), bst);
           add_div_bubbles(L, T, T.P[kf], tg, bst);
         }
-        else add_curl_bubbles(L, C, T, T.P[kf], tg, bst);
+        else if (tdeg >= 2) {
+          const Targets dtg = space_targets(H, l, 2, 1);
+          add_curl_bubbles(L, C, T, T.P[kf], tg, &dtg, bst);
+        } else {
+          add_curl_bubbles(L, C, T, T.P[kf], tg, nullptr, bst);
+        }
         H->A[l + 1] = galerkin(H->A[l], T.P[kf]);
       }
       // the finer level's local data is no longer needed

@@ -48,9 +48,9 @@ enum { AMGH_ALL_SPACES = 1, AMGH_TARGETS = 2, AMGH_TARGETS2 = 4 };
  *               eqs. 3.6 / 3.8, become extra coarse basis functions (columns of P
  *               after the coarse entities' ones); the coarsest matrix is the Galerkin
  *               product P^T A P with that P.
- *               AMGH_TARGETS2 (H(div) only): the same with the monomials of degree
- *               <= 2, which also brings the cross-space bubbles of eq. 3.7 (the
- *               targets' non-constant divergences) into the coarsest space.
+ *               AMGH_TARGETS2: the same with the monomials of degree <= 2, which also
+ *               brings the cross-space bubbles of eqs. 3.7 / 3.9 (the targets'
+ *               non-constant divergences and curls) into the coarsest space.
  *   nthreads    OpenMP threads (<= 0: library default).
  * Returns 0 and a handle in *out, or nonzero with amgh_error() describing it. */
 int amgh_build(int form, int n, int num_levels, const double* beta, const double* alpha,

@@ -127,8 +127,8 @@ def build_hierarchy(form: str, n: int, num_levels: int = 0, beta=None, alpha=Non
     assembly: also return the fine assembly of A_0 as a gather (diagnostics
     "assembly": dict of K, M [6, s, s], coff, ccell, cidx; see amge_hierarchy.h).
     targets: enrich the last coarsening with the degree-one polynomial approximation
-    targets (Sections 3.3.1-3.3.3; AMGH_TARGETS in amge_hierarchy.h), or with 2 (H(div)
-    only, AMGH_TARGETS2) the degree-two ones and the cross-space bubbles of eq. 3.7:
+    targets (Sections 3.3.1-3.3.3; AMGH_TARGETS in amge_hierarchy.h), or with 2
+    (AMGH_TARGETS2) the degree-two ones and the cross-space bubbles of eqs. 3.7 / 3.9:
     P[-1] gains columns after the coarse entities' ones and A[-1] is
     P[-1]^T A[-2] P[-1]; diagnostics "target_functions", "target_constraint".
     """
