@@ -13,7 +13,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 EPS64 = np.finfo(np.float64).eps
-CASES = [("hcurl", 8, 2), ("hdiv", 8, 2), ("hcurl", 16, 3), ("hdiv", 16, 3)]
+CASES = [("hcurl", 8, 2, 1), ("hdiv", 8, 2, 1), ("hcurl", 16, 3, 1), ("hdiv", 16, 3, 1), ("hcurl", 8, 2, 2),
+         ("hdiv", 8, 2, 2)]
 
 
 @pytest.fixture(scope="module")
@@ -26,27 +27,27 @@ def amge():
 
 
 @functools.lru_cache(maxsize=None)
-def _hier(form, n, L):
+def _hier(form, n, L, deg=1):
     from paper_2107_05613_gb300.inputs import build_hierarchy, workload_coefficients
 
     beta, alpha = workload_coefficients(n, True, 13)
-    return build_hierarchy(form, n, L, beta, alpha, targets=True)
+    return build_hierarchy(form, n, L, beta, alpha, targets=deg)
 
 
 @functools.lru_cache(maxsize=None)
-def _oracle(form, n, L):
+def _oracle(form, n, L, deg=1):
     from oracle import OracleHierarchy
 
-    return OracleHierarchy.from_hierarchy(_hier(form, n, L))
+    return OracleHierarchy.from_hierarchy(_hier(form, n, L, deg))
 
 
 _up = {}
 
 
-def _upload(amge, form, n, L):
-    if (form, n, L) not in _up:
-        _up[(form, n, L)] = amge.amge_upload_levels(_hier(form, n, L))
-    return _up[(form, n, L)]
+def _upload(amge, form, n, L, deg=1):
+    if (form, n, L, deg) not in _up:
+        _up[(form, n, L, deg)] = amge.amge_upload_levels(_hier(form, n, L, deg))
+    return _up[(form, n, L, deg)]
 
 
 def dev(a):
@@ -58,12 +59,12 @@ def host(t):
     return t.cpu().numpy()
 
 
-@pytest.mark.parametrize("form,n,L", CASES)
-def test_vcycle_on_enriched_hierarchy_matches_oracle(amge, form, n, L):
+@pytest.mark.parametrize("form,n,L,deg", CASES)
+def test_vcycle_on_enriched_hierarchy_matches_oracle(amge, form, n, L, deg):
     from paper_2107_05613_gb300.inputs import rhs_vector
 
-    assert _hier(form, n, L).diagnostics["target_functions"] > 0
-    h, o = _upload(amge, form, n, L), _oracle(form, n, L)
+    assert _hier(form, n, L, deg).diagnostics["target_functions"] > 0
+    h, o = _upload(amge, form, n, L, deg), _oracle(form, n, L, deg)
     r = rhs_vector(41, o.A[0].shape[0])
     z = torch.empty_like(dev(r))
     amge.amge_vcycle(h, dev(r), z, 1, amge.AMGE_FP64)
@@ -72,13 +73,13 @@ def test_vcycle_on_enriched_hierarchy_matches_oracle(amge, form, n, L):
     assert np.linalg.norm(host(z) - ref) <= tol * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("form,n,L", CASES)
+@pytest.mark.parametrize("form,n,L,deg", CASES)
 @pytest.mark.parametrize("prec", [0, 1])
-def test_pcg_on_enriched_hierarchy(amge, form, n, L, prec):
+def test_pcg_on_enriched_hierarchy(amge, form, n, L, deg, prec):
     from oracle import pcg
     from paper_2107_05613_gb300.inputs import rhs_vector
 
-    h, o = _upload(amge, form, n, L), _oracle(form, n, L)
+    h, o = _upload(amge, form, n, L, deg), _oracle(form, n, L, deg)
     b = rhs_vector(43, o.A[0].shape[0])
     x = torch.empty_like(dev(b))
     st, info = amge.amge_pcg_solve(h, dev(b), x, rtol=1e-8,
