@@ -73,3 +73,31 @@ def test_binding_names_match_abi():
         if name in ("amge_hier_free",):
             continue
         assert hasattr(amge, name), name
+
+
+def test_binding_structs_match_header():
+    """Every struct the header defines has a ctypes twin in the binding with the same
+    fields, in the same order, of the same sizes -- so an added or reordered field in
+    include/amge.h cannot silently shift the binding's layout."""
+    import ctypes as ct
+    import importlib
+
+    amge = importlib.import_module("paper_2107_05613_gb300.amge")
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "amge.h")).read(), flags=re.S)
+    sizes = {"int32_t": 4, "int64_t": 8, "double": 8}
+    structs = re.findall(r"typedef struct \{(.*?)\}\s*(\w+);", text, flags=re.S)
+    assert len(structs) >= 5
+    for body, name in structs:
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            m = re.match(r"(?:const\s+)?(\w+)\s*(\*?)\s*(\w+)$", decl)
+            assert m, (name, decl)
+            ctype, ptr, fname = m.groups()
+            fields.append((fname, 8 if ptr else sizes[ctype]))
+        py = getattr(amge, name)
+        assert [f[0] for f in py._fields_] == [f[0] for f in fields], name
+        for (fname, size), (_, pytype) in zip(fields, py._fields_):
+            assert ct.sizeof(pytype) == size, (name, fname)
