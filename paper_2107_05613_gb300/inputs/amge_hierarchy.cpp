@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -145,6 +146,24 @@ Adj compose_union(const Adj& outer, const Adj& inner) {
   for (int r = 0; r < n; r++) std::copy(rows[r].begin(), rows[r].end(), R.ci.begin() + R.rp[r]);
   return R;
 }
+
+// An exception must not leave an OpenMP region -- it would terminate the process,
+// where the library's callers expect an error code.  Loops whose bodies can throw
+// catch per iteration, keep the first message and skip the remaining iterations; the
+// code after the loop rethrows it.
+struct LoopErrors {
+  std::atomic<bool> failed{false};
+  std::string msg;
+  void record(const std::exception& e) {
+#pragma omp critical(amgh_loop_errors)
+    {
+      if (!failed.exchange(true)) msg = e.what();
+    }
+  }
+  void rethrow() const {
+    if (failed) throw Fail(msg);
+  }
+};
 
 // ---------------------------------------------------------------- dense helpers
 // Solve A X = B with partial pivoting; A n x n row-major (destroyed), B n x m row-major.
@@ -559,45 +578,52 @@ void group_sorted(std::vector<std::pair<K, int>>& kv, Adj& groups, std::vector<K
 void orient_chain(const Adj& cons, const ICsr& Dsub, std::vector<int8_t>& phi) {
   phi.assign(cons.ci.size(), 0);
   int nc = cons.rows();
+  LoopErrors errs0;
 #pragma omp parallel for schedule(dynamic, 64)
   for (int X = 0; X < nc; X++) {
-    int len = cons.len(X);
-    const int* c = cons.row(X);
-    int8_t* ph = phi.data() + cons.rp[X];
-    // incidence list: (sub-entity, constituent position, sign)
-    std::vector<std::array<int, 3>> inc;
-    for (int i = 0; i < len; i++) {
-      int x = c[i];
-      for (int64_t p = Dsub.a.rp[x]; p < Dsub.a.rp[x + 1]; p++) inc.push_back({Dsub.a.ci[p], i, Dsub.v[p]});
-    }
-    std::sort(inc.begin(), inc.end());
-    std::vector<std::vector<std::array<int, 2>>> nb(len);  // neighbor, sign product
-    for (size_t a = 0; a < inc.size();) {
-      size_t b = a;
-      while (b < inc.size() && inc[b][0] == inc[a][0]) b++;
-      if (b - a == 2) {
-        int i = inc[a][1], j = inc[a + 1][1], s = inc[a][2] * inc[a + 1][2];
-        nb[i].push_back({j, s});
-        nb[j].push_back({i, s});
+    if (errs0.failed) continue;
+    try {
+      int len = cons.len(X);
+      const int* c = cons.row(X);
+      int8_t* ph = phi.data() + cons.rp[X];
+      // incidence list: (sub-entity, constituent position, sign)
+      std::vector<std::array<int, 3>> inc;
+      for (int i = 0; i < len; i++) {
+        int x = c[i];
+        for (int64_t p = Dsub.a.rp[x]; p < Dsub.a.rp[x + 1]; p++) inc.push_back({Dsub.a.ci[p], i, Dsub.v[p]});
       }
-      a = b;
-    }
-    std::vector<int> queue{0};
-    ph[0] = 1;
-    for (size_t q = 0; q < queue.size(); q++) {
-      int i = queue[q];
-      for (auto& e : nb[i]) {
-        int8_t want = (int8_t)(-ph[i] * e[1]);
-        if (ph[e[0]] == 0) {
-          ph[e[0]] = want;
-          queue.push_back(e[0]);
-        } else if (ph[e[0]] != want) {
-          throw Fail("coarse entity is not orientable");
+      std::sort(inc.begin(), inc.end());
+      std::vector<std::vector<std::array<int, 2>>> nb(len);  // neighbor, sign product
+      for (size_t a = 0; a < inc.size();) {
+        size_t b = a;
+        while (b < inc.size() && inc[b][0] == inc[a][0]) b++;
+        if (b - a == 2) {
+          int i = inc[a][1], j = inc[a + 1][1], s = inc[a][2] * inc[a + 1][2];
+          nb[i].push_back({j, s});
+          nb[j].push_back({i, s});
+        }
+        a = b;
+      }
+      std::vector<int> queue{0};
+      ph[0] = 1;
+      for (size_t q = 0; q < queue.size(); q++) {
+        int i = queue[q];
+        for (auto& e : nb[i]) {
+          int8_t want = (int8_t)(-ph[i] * e[1]);
+          if (ph[e[0]] == 0) {
+            ph[e[0]] = want;
+            queue.push_back(e[0]);
+          } else if (ph[e[0]] != want) {
+            throw Fail("coarse entity is not orientable");
+          }
         }
       }
+      if ((int)queue.size() != len) throw Fail("coarse entity is not connected");
+    } catch (const std::exception& e) {
+      errs0.record(e);
     }
-    if ((int)queue.size() != len) throw Fail("coarse entity is not connected");
   }
+  errs0.rethrow();
 }
 
 // Build the coarse topology (Section 3.1) and owner / closure maps of the transfer.
@@ -721,47 +747,54 @@ void coarsen_topology(const Level& L, Level& C, Transfer& T, double& incid_dev) 
     const int nX = T.cons[d].rows();
     std::vector<std::vector<std::pair<int, int>>> rows(nX);
     double dev = 0.0;
+    LoopErrors errs1;
 #pragma omp parallel for schedule(dynamic, 64) reduction(max : dev)
     for (int X = 0; X < nX; X++) {
-      std::vector<std::pair<int, int>> b;  // (fine sub-entity, coefficient)
-      for (int64_t p = T.cons[d].rp[X]; p < T.cons[d].rp[X + 1]; p++) {
-        int x = T.cons[d].ci[p];
-        int ph = T.phi[d][p];
-        for (int64_t q = Dk.a.rp[x]; q < Dk.a.rp[x + 1]; q++) b.push_back({Dk.a.ci[q], ph * Dk.v[q]});
-      }
-      std::sort(b.begin(), b.end());
-      std::vector<std::pair<int, int>> acc;
-      for (size_t i = 0; i < b.size();) {
-        size_t j = i;
-        int s = 0;
-        while (j < b.size() && b[j].first == b[i].first) s += b[j].second, j++;
-        if (s != 0) acc.push_back({b[i].first, s});
-        i = j;
-      }
-      // group nonzero boundary coefficients by the coarse sub-entity that owns them
-      std::vector<std::array<int, 3>> g;  // coarse sub-entity, value * phi, fine sub-entity
-      for (auto& pr : acc) {
-        int y = pr.first;
-        if (T.own_dim[k][y] != k) throw Fail("chain boundary leaves the coarse skeleton");
-        int Y = T.own_id[k][y];
-        int py = T.cons[k].find(Y, y);
-        int ph = T.phi[k][T.cons[k].rp[Y] + py];
-        g.push_back({Y, pr.second * ph, y});
-      }
-      std::sort(g.begin(), g.end());
-      for (size_t i = 0; i < g.size();) {
-        size_t j = i;
-        int cnt = 0;
-        while (j < g.size() && g[j][0] == g[i][0]) {
-          if (g[j][1] != g[i][1]) dev = std::max(dev, (double)std::abs(g[j][1] - g[i][1]));
-          cnt++, j++;
+      if (errs1.failed) continue;
+      try {
+        std::vector<std::pair<int, int>> b;  // (fine sub-entity, coefficient)
+        for (int64_t p = T.cons[d].rp[X]; p < T.cons[d].rp[X + 1]; p++) {
+          int x = T.cons[d].ci[p];
+          int ph = T.phi[d][p];
+          for (int64_t q = Dk.a.rp[x]; q < Dk.a.rp[x + 1]; q++) b.push_back({Dk.a.ci[q], ph * Dk.v[q]});
         }
-        if (cnt != T.cons[k].len(g[i][0])) dev = std::max(dev, 1.0);
-        if (std::abs(g[i][1]) != 1) dev = std::max(dev, (double)std::abs(g[i][1]));
-        rows[X].push_back({g[i][0], g[i][1]});
-        i = j;
+        std::sort(b.begin(), b.end());
+        std::vector<std::pair<int, int>> acc;
+        for (size_t i = 0; i < b.size();) {
+          size_t j = i;
+          int s = 0;
+          while (j < b.size() && b[j].first == b[i].first) s += b[j].second, j++;
+          if (s != 0) acc.push_back({b[i].first, s});
+          i = j;
+        }
+        // group nonzero boundary coefficients by the coarse sub-entity that owns them
+        std::vector<std::array<int, 3>> g;  // coarse sub-entity, value * phi, fine sub-entity
+        for (auto& pr : acc) {
+          int y = pr.first;
+          if (T.own_dim[k][y] != k) throw Fail("chain boundary leaves the coarse skeleton");
+          int Y = T.own_id[k][y];
+          int py = T.cons[k].find(Y, y);
+          int ph = T.phi[k][T.cons[k].rp[Y] + py];
+          g.push_back({Y, pr.second * ph, y});
+        }
+        std::sort(g.begin(), g.end());
+        for (size_t i = 0; i < g.size();) {
+          size_t j = i;
+          int cnt = 0;
+          while (j < g.size() && g[j][0] == g[i][0]) {
+            if (g[j][1] != g[i][1]) dev = std::max(dev, (double)std::abs(g[j][1] - g[i][1]));
+            cnt++, j++;
+          }
+          if (cnt != T.cons[k].len(g[i][0])) dev = std::max(dev, 1.0);
+          if (std::abs(g[i][1]) != 1) dev = std::max(dev, (double)std::abs(g[i][1]));
+          rows[X].push_back({g[i][0], g[i][1]});
+          i = j;
+        }
+      } catch (const std::exception& e) {
+        errs1.record(e);
       }
     }
+    errs1.rethrow();
     incid_dev = std::max(incid_dev, dev);
     ICsr& DH = C.D[k];
     DH.nr = nX, DH.nc = (int)C.cnt[k];
@@ -1078,55 +1111,62 @@ void extend(const Level& L, const Level& C, Transfer& T, int k, int d, ExtStats&
   DCsr& P = T.P[k];
   const int nX = T.cons[d].rows();
   double lam_dev = 0, resid = 0;
+  LoopErrors errs2;
 #pragma omp parallel for schedule(dynamic, 16) reduction(max : lam_dev, resid)
   for (int X = 0; X < nX; X++) {
-    const int* S = T.fclo[d][k].row(X);
-    const int nS = T.fclo[d][k].len(X);
-    const uint8_t* in = T.fint[d][k].data() + T.fclo[d][k].rp[X];
-    std::vector<int> I, B;
-    for (int i = 0; i < nS; i++) (in[i] ? I : B).push_back(i);
-    const int nI = (int)I.size(), nB = (int)B.size();
-    const int* J;
-    const int nJ = coarse_dofs(C, d, k, X, &J);
-    if (nI == 0 || nJ == 0) continue;
-    // boundary data: the already-built traces of each coarse dof on the boundary
-    std::vector<double> phiB((size_t)nB * nJ);
-    for (int b = 0; b < nB; b++)
-      for (int j = 0; j < nJ; j++) phiB[(size_t)b * nJ + j] = P.get(S[B[b]], J[j]);
-    std::vector<double> R;
-    double rx = 0;
-    if (d == k + 1) {
-      R = solve_eq36(L, T, k, X, phiB, nJ, &rx);
-      const int n = (int)(R.size() / nJ);
-      for (int j = 0; j < nJ; j++) {  // Stokes: the multiplier equals the coarse incidence (D_k^H)_{X,J}
-        const double lam = R[(size_t)(n - 1) * nJ + j];
-        lam_dev = std::max(lam_dev, std::fabs(lam - (double)C.D[k].get(X, J[j])));
-      }
-    } else {
-      // s_J = sum_J' (D_k^H)_{J',J} * (space-(k+1) shape function of J' on X)
-      const int* S1 = T.fclo[d][k + 1].row(X);
-      const int n1 = T.fclo[d][k + 1].len(X);
-      const int* J1;
-      const int nJ1 = coarse_dofs(C, d, k + 1, X, &J1);
-      std::vector<double> s((size_t)n1 * nJ, 0.0);
-      for (int j1 = 0; j1 < nJ1; j1++)
-        for (int j = 0; j < nJ; j++) {
-          int8_t inc = C.D[k].get(J1[j1], J[j]);
-          if (!inc) continue;
-          for (int a = 0; a < n1; a++) s[(size_t)a * nJ + j] += inc * T.P[k + 1].get(S1[a], J1[j1]);
+    if (errs2.failed) continue;
+    try {
+      const int* S = T.fclo[d][k].row(X);
+      const int nS = T.fclo[d][k].len(X);
+      const uint8_t* in = T.fint[d][k].data() + T.fclo[d][k].rp[X];
+      std::vector<int> I, B;
+      for (int i = 0; i < nS; i++) (in[i] ? I : B).push_back(i);
+      const int nI = (int)I.size(), nB = (int)B.size();
+      const int* J;
+      const int nJ = coarse_dofs(C, d, k, X, &J);
+      if (nI == 0 || nJ == 0) continue;
+      // boundary data: the already-built traces of each coarse dof on the boundary
+      std::vector<double> phiB((size_t)nB * nJ);
+      for (int b = 0; b < nB; b++)
+        for (int j = 0; j < nJ; j++) phiB[(size_t)b * nJ + j] = P.get(S[B[b]], J[j]);
+      std::vector<double> R;
+      double rx = 0;
+      if (d == k + 1) {
+        R = solve_eq36(L, T, k, X, phiB, nJ, &rx);
+        const int n = (int)(R.size() / nJ);
+        for (int j = 0; j < nJ; j++) {  // Stokes: the multiplier equals the coarse incidence (D_k^H)_{X,J}
+          const double lam = R[(size_t)(n - 1) * nJ + j];
+          lam_dev = std::max(lam_dev, std::fabs(lam - (double)C.D[k].get(X, J[j])));
         }
-      R = solve_eq38(L, T, k, d, X, &s, phiB, nJ, &rx);
-    }
-    resid = std::max(resid, rx);
-    for (int a = 0; a < nI; a++) {
-      int row = S[I[a]];
-      for (int j = 0; j < nJ; j++) {
-        int pos = P.a.find(row, J[j]);
-        if (pos < 0) throw Fail("prolongator pattern mismatch");
-        P.v[P.a.rp[row] + pos] = R[(size_t)a * nJ + j];
+      } else {
+        // s_J = sum_J' (D_k^H)_{J',J} * (space-(k+1) shape function of J' on X)
+        const int* S1 = T.fclo[d][k + 1].row(X);
+        const int n1 = T.fclo[d][k + 1].len(X);
+        const int* J1;
+        const int nJ1 = coarse_dofs(C, d, k + 1, X, &J1);
+        std::vector<double> s((size_t)n1 * nJ, 0.0);
+        for (int j1 = 0; j1 < nJ1; j1++)
+          for (int j = 0; j < nJ; j++) {
+            int8_t inc = C.D[k].get(J1[j1], J[j]);
+            if (!inc) continue;
+            for (int a = 0; a < n1; a++) s[(size_t)a * nJ + j] += inc * T.P[k + 1].get(S1[a], J1[j1]);
+          }
+        R = solve_eq38(L, T, k, d, X, &s, phiB, nJ, &rx);
       }
+      resid = std::max(resid, rx);
+      for (int a = 0; a < nI; a++) {
+        int row = S[I[a]];
+        for (int j = 0; j < nJ; j++) {
+          int pos = P.a.find(row, J[j]);
+          if (pos < 0) throw Fail("prolongator pattern mismatch");
+          P.v[P.a.rp[row] + pos] = R[(size_t)a * nJ + j];
+        }
+      }
+    } catch (const std::exception& e) {
+      errs2.record(e);
     }
   }
+  errs2.rethrow();
   st.lam_dev = std::max(st.lam_dev, lam_dev);
   st.resid = std::max(st.resid, resid);
 }
@@ -1197,32 +1237,39 @@ void coarse_local(const Level& L, Level& C, const Transfer& T, int kmin, int kf)
   };
   for (int d = 1; d <= 3; d++) {
     const int nX = T.cons[d].rows();
+    LoopErrors errs3;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int X = 0; X < nX; X++) {
-      std::vector<double> M, buf;
-      for (int k = kmin; k <= d; k++) {
-        const int* S = T.fclo[d][k].row(X);
-        const int nS = T.fclo[d][k].len(X);
-        assemble_mass(L, T, d, k, X, S, nS, M, buf);
-        rap(d, k, X, M, C.lm[d][k].data() + C.lmoff[d][k][X]);
-      }
-      if (d == 3) {
-        const int* S = T.fclo[3][kf].row(X);
-        const int nS = T.fclo[3][kf].len(X);
-        M.assign((size_t)nS * nS, 0.0);
-        for (int64_t p = T.cons[3].rp[X]; p < T.cons[3].rp[X + 1]; p++) {
-          int x = T.cons[3].ci[p];
-          int s = local_size(L, 3, kf, x);
-          buf.resize((size_t)s * s);
-          local_form(L, kf, x, buf.data());
-          int loc[64];
-          for (int i = 0; i < s; i++) loc[i] = (int)(std::lower_bound(S, S + nS, L.clo[3][kf].row(x)[i]) - S);
-          for (int i = 0; i < s; i++)
-            for (int j = 0; j < s; j++) M[(size_t)loc[i] * nS + loc[j]] += buf[(size_t)i * s + j];
+      if (errs3.failed) continue;
+      try {
+        std::vector<double> M, buf;
+        for (int k = kmin; k <= d; k++) {
+          const int* S = T.fclo[d][k].row(X);
+          const int nS = T.fclo[d][k].len(X);
+          assemble_mass(L, T, d, k, X, S, nS, M, buf);
+          rap(d, k, X, M, C.lm[d][k].data() + C.lmoff[d][k][X]);
         }
-        rap(3, kf, X, M, C.la.data() + C.laoff[X]);
+        if (d == 3) {
+          const int* S = T.fclo[3][kf].row(X);
+          const int nS = T.fclo[3][kf].len(X);
+          M.assign((size_t)nS * nS, 0.0);
+          for (int64_t p = T.cons[3].rp[X]; p < T.cons[3].rp[X + 1]; p++) {
+            int x = T.cons[3].ci[p];
+            int s = local_size(L, 3, kf, x);
+            buf.resize((size_t)s * s);
+            local_form(L, kf, x, buf.data());
+            int loc[64];
+            for (int i = 0; i < s; i++) loc[i] = (int)(std::lower_bound(S, S + nS, L.clo[3][kf].row(x)[i]) - S);
+            for (int i = 0; i < s; i++)
+              for (int j = 0; j < s; j++) M[(size_t)loc[i] * nS + loc[j]] += buf[(size_t)i * s + j];
+          }
+          rap(3, kf, X, M, C.la.data() + C.laoff[X]);
+        }
+      } catch (const std::exception& e) {
+        errs3.record(e);
       }
     }
+    errs3.rethrow();
   }
 }
 
@@ -1666,43 +1713,50 @@ void add_div_cross_bubbles(const Level& L, const Transfer& T, DCsr& P, const Tar
   std::vector<std::vector<double>> xv(nX);
   std::vector<std::vector<int>> xrows(nX);
   std::vector<int> xk(nX, 0);
+  LoopErrors errs4;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int X = 0; X < nX; X++) {
-    std::vector<double> W, buf, mt, fkeep;
-    const int* S1 = T.cons[3].row(X);
-    const int n1 = T.cons[3].len(X);
-    assemble_mass(L, T, 3, 3, X, S1, n1, W, buf);
-    std::vector<double> pv(n1), Wp(n1, 0.0);
-    for (int a = 0; a < n1; a++) pv[a] = T.phi[3][T.cons[3].rp[X] + a] / (double)n1;
-    double pWp = 0;
-    for (int a = 0; a < n1; a++) {
-      for (int b = 0; b < n1; b++) Wp[a] += W[(size_t)a * n1 + b] * pv[b];
-      pWp += pv[a] * Wp[a];
+    if (errs4.failed) continue;
+    try {
+      std::vector<double> W, buf, mt, fkeep;
+      const int* S1 = T.cons[3].row(X);
+      const int n1 = T.cons[3].len(X);
+      assemble_mass(L, T, 3, 3, X, S1, n1, W, buf);
+      std::vector<double> pv(n1), Wp(n1, 0.0);
+      for (int a = 0; a < n1; a++) pv[a] = T.phi[3][T.cons[3].rp[X] + a] / (double)n1;
+      double pWp = 0;
+      for (int a = 0; a < n1; a++) {
+        for (int b = 0; b < n1; b++) Wp[a] += W[(size_t)a * n1 + b] * pv[b];
+        pWp += pv[a] * Wp[a];
+      }
+      const double tau = mass_targets(W, S1, n1, ctg, mt);
+      std::vector<double> phi((size_t)n1 * nt);
+      for (int c = 0; c < nt; c++) {
+        double pWt = 0;
+        for (int a = 0; a < n1; a++) pWt += Wp[a] * ctg[c][S1[a]];
+        for (int a = 0; a < n1; a++) phi[(size_t)a * nt + c] = ctg[c][S1[a]] - pv[a] * (pWt / pWp);
+      }
+      const int nf = filter_targets(n1, nt, phi, [&](int a, int b) { return W[(size_t)a * n1 + b]; }, tau, fkeep);
+      const int* S = T.fclo[3][2].row(X);
+      const int nS = T.fclo[3][2].len(X);
+      const uint8_t* in = T.fint[3][2].data() + T.fclo[3][2].rp[X];
+      size_t nB = 0;
+      for (int i = 0; i < nS; i++)
+        if (in[i]) xrows[X].push_back(S[i]);
+        else nB++;
+      if (nf == 0 || xrows[X].empty()) continue;
+      std::vector<double> f((size_t)n1 * nf);  // the divergences, one column per bubble
+      for (int i = 0; i < nf; i++)
+        for (int a = 0; a < n1; a++) f[(size_t)a * nf + i] = fkeep[(size_t)i * n1 + a];
+      const std::vector<double> zeroB(nB * (size_t)nf, 0.0);
+      xv[X] = solve_eq36(L, T, 2, X, zeroB, nf, nullptr, &f);
+      xv[X].resize(xrows[X].size() * (size_t)nf);
+      xk[X] = nf;
+    } catch (const std::exception& e) {
+      errs4.record(e);
     }
-    const double tau = mass_targets(W, S1, n1, ctg, mt);
-    std::vector<double> phi((size_t)n1 * nt);
-    for (int c = 0; c < nt; c++) {
-      double pWt = 0;
-      for (int a = 0; a < n1; a++) pWt += Wp[a] * ctg[c][S1[a]];
-      for (int a = 0; a < n1; a++) phi[(size_t)a * nt + c] = ctg[c][S1[a]] - pv[a] * (pWt / pWp);
-    }
-    const int nf = filter_targets(n1, nt, phi, [&](int a, int b) { return W[(size_t)a * n1 + b]; }, tau, fkeep);
-    const int* S = T.fclo[3][2].row(X);
-    const int nS = T.fclo[3][2].len(X);
-    const uint8_t* in = T.fint[3][2].data() + T.fclo[3][2].rp[X];
-    size_t nB = 0;
-    for (int i = 0; i < nS; i++)
-      if (in[i]) xrows[X].push_back(S[i]);
-      else nB++;
-    if (nf == 0 || xrows[X].empty()) continue;
-    std::vector<double> f((size_t)n1 * nf);  // the divergences, one column per bubble
-    for (int i = 0; i < nf; i++)
-      for (int a = 0; a < n1; a++) f[(size_t)a * nf + i] = fkeep[(size_t)i * n1 + a];
-    const std::vector<double> zeroB(nB * (size_t)nf, 0.0);
-    xv[X] = solve_eq36(L, T, 2, X, zeroB, nf, nullptr, &f);
-    xv[X].resize(xrows[X].size() * (size_t)nf);
-    xk[X] = nf;
   }
+  errs4.rethrow();
   std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
   int next = P.nc;
   for (int X = 0; X < nX; X++) {
@@ -1727,67 +1781,81 @@ void add_face_traces(const Level& L, const Level& C, const Transfer& T, DCsr& P,
   const int nF = T.cons[2].rows(), nX = T.cons[3].rows();
   std::vector<std::vector<double>> fv(nF);
   std::vector<int> fk(nF, 0);
+  LoopErrors errs5;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int F = 0; F < nF; F++) {
-    std::vector<double> M, buf, mt;
-    const int* S = T.cons[2].row(F);
-    const int nS = T.cons[2].len(F);
-    assemble_mass(L, T, 2, 2, F, S, nS, M, buf);
-    std::vector<double> pv(nS), Mp(nS, 0.0);
-    for (int a = 0; a < nS; a++) pv[a] = T.phi[2][T.cons[2].rp[F] + a] / (double)nS;
-    double pMp = 0;
-    for (int a = 0; a < nS; a++) {
-      for (int b = 0; b < nS; b++) Mp[a] += M[(size_t)a * nS + b] * pv[b];
-      pMp += pv[a] * Mp[a];
+    if (errs5.failed) continue;
+    try {
+      std::vector<double> M, buf, mt;
+      const int* S = T.cons[2].row(F);
+      const int nS = T.cons[2].len(F);
+      assemble_mass(L, T, 2, 2, F, S, nS, M, buf);
+      std::vector<double> pv(nS), Mp(nS, 0.0);
+      for (int a = 0; a < nS; a++) pv[a] = T.phi[2][T.cons[2].rp[F] + a] / (double)nS;
+      double pMp = 0;
+      for (int a = 0; a < nS; a++) {
+        for (int b = 0; b < nS; b++) Mp[a] += M[(size_t)a * nS + b] * pv[b];
+        pMp += pv[a] * Mp[a];
+      }
+      const double tau = mass_targets(M, S, nS, tgt, mt);
+      std::vector<double> phi((size_t)nS * nt);
+      for (int c = 0; c < nt; c++) {
+        double pMt = 0;
+        for (int a = 0; a < nS; a++) pMt += Mp[a] * tgt[c][S[a]];
+        for (int a = 0; a < nS; a++) phi[(size_t)a * nt + c] = tgt[c][S[a]] - pv[a] * (pMt / pMp);
+      }
+      fk[F] = filter_targets(nS, nt, phi, [&](int a, int b) { return M[(size_t)a * nS + b]; }, tau, fv[F]);
+    } catch (const std::exception& e) {
+      errs5.record(e);
     }
-    const double tau = mass_targets(M, S, nS, tgt, mt);
-    std::vector<double> phi((size_t)nS * nt);
-    for (int c = 0; c < nt; c++) {
-      double pMt = 0;
-      for (int a = 0; a < nS; a++) pMt += Mp[a] * tgt[c][S[a]];
-      for (int a = 0; a < nS; a++) phi[(size_t)a * nt + c] = tgt[c][S[a]] - pv[a] * (pMt / pMp);
-    }
-    fk[F] = filter_targets(nS, nt, phi, [&](int a, int b) { return M[(size_t)a * nS + b]; }, tau, fv[F]);
   }
+  errs5.rethrow();
   std::vector<int> ffirst(nF);
   int next = P.nc;
   for (int F = 0; F < nF; F++) ffirst[F] = next, next += fk[F];
   std::vector<std::vector<double>> xv(nX);
   std::vector<std::vector<int>> xcol(nX), xrows(nX);
+  LoopErrors errs6;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int X = 0; X < nX; X++) {
-    const int* S = T.fclo[3][2].row(X);
-    const int nS = T.fclo[3][2].len(X);
-    const uint8_t* in = T.fint[3][2].data() + T.fclo[3][2].rp[X];
-    std::vector<int> Bpos;
-    for (int i = 0; i < nS; i++)
-      if (in[i]) xrows[X].push_back(S[i]);
-      else Bpos.push_back(i);
-    const int* Fx = C.clo[3][2].row(X);
-    const int nFx = C.clo[3][2].len(X);
-    int nJ = 0;
-    for (int q = 0; q < nFx; q++) nJ += fk[Fx[q]];
-    if (nJ == 0 || xrows[X].empty()) continue;
-    std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
-    int j0 = 0;
-    for (int q = 0; q < nFx; q++) {
-      const int F = Fx[q];
-      const int nSF = T.cons[2].len(F);
-      const int* SF = T.cons[2].row(F);
-      for (int i = 0; i < fk[F]; i++) {
-        xcol[X].push_back(ffirst[F] + i);
-        for (int a = 0; a < nSF; a++) {  // F's fine faces among X's boundary faces
-          const int* pos = std::lower_bound(S, S + nS, SF[a]);
-          REQUIRE(pos != S + nS && *pos == SF[a], "coarse face outside its cell's closure");
-          const int bi = (int)(std::lower_bound(Bpos.begin(), Bpos.end(), (int)(pos - S)) - Bpos.begin());
-          phiB[(size_t)bi * nJ + j0 + i] = fv[F][(size_t)i * nSF + a];
+    if (errs6.failed) continue;
+    try {
+      const int* S = T.fclo[3][2].row(X);
+      const int nS = T.fclo[3][2].len(X);
+      const uint8_t* in = T.fint[3][2].data() + T.fclo[3][2].rp[X];
+      std::vector<int> Bpos;
+      for (int i = 0; i < nS; i++)
+        if (in[i]) xrows[X].push_back(S[i]);
+        else Bpos.push_back(i);
+      const int* Fx = C.clo[3][2].row(X);
+      const int nFx = C.clo[3][2].len(X);
+      int nJ = 0;
+      for (int q = 0; q < nFx; q++) nJ += fk[Fx[q]];
+      if (nJ == 0 || xrows[X].empty()) continue;
+      std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
+      int j0 = 0;
+      for (int q = 0; q < nFx; q++) {
+        const int F = Fx[q];
+        const int nSF = T.cons[2].len(F);
+        const int* SF = T.cons[2].row(F);
+        for (int i = 0; i < fk[F]; i++) {
+          xcol[X].push_back(ffirst[F] + i);
+          for (int a = 0; a < nSF; a++) {  // F's fine faces among X's boundary faces
+            const int* pos = std::lower_bound(S, S + nS, SF[a]);
+            REQUIRE(pos != S + nS && *pos == SF[a], "coarse face outside its cell's closure");
+            const int bi = (int)(std::lower_bound(Bpos.begin(), Bpos.end(), (int)(pos - S)) - Bpos.begin());
+            phiB[(size_t)bi * nJ + j0 + i] = fv[F][(size_t)i * nSF + a];
+          }
         }
+        j0 += fk[F];
       }
-      j0 += fk[F];
+      xv[X] = solve_eq36(L, T, 2, X, phiB, nJ, nullptr);
+      xv[X].resize(xrows[X].size() * (size_t)nJ);  // the interior values
+    } catch (const std::exception& e) {
+      errs6.record(e);
     }
-    xv[X] = solve_eq36(L, T, 2, X, phiB, nJ, nullptr);
-    xv[X].resize(xrows[X].size() * (size_t)nJ);  // the interior values
   }
+  errs6.rethrow();
   std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
   for (int F = 0; F < nF; F++) {
     const int nSF = T.cons[2].len(F);
@@ -1873,12 +1941,19 @@ void add_div_bubbles(const Level& L, const Transfer& T, DCsr& P, const Targets& 
   std::vector<std::vector<int>> rowsX(nX);
   std::vector<int> nkeep(nX, 0);
   double cmax = 0;
+  LoopErrors errs7;
 #pragma omp parallel for schedule(dynamic, 16) reduction(max : cmax)
   for (int X = 0; X < nX; X++) {
-    double cx = 0;
-    vals[X] = div_bubbles_cell(L, T, X, tgt, rowsX[X], nkeep[X], &cx);
-    cmax = std::max(cmax, cx);
+    if (errs7.failed) continue;
+    try {
+      double cx = 0;
+      vals[X] = div_bubbles_cell(L, T, X, tgt, rowsX[X], nkeep[X], &cx);
+      cmax = std::max(cmax, cx);
+    } catch (const std::exception& e) {
+      errs7.record(e);
+    }
   }
+  errs7.rethrow();
   st.constraint = std::max(st.constraint, cmax);
   std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
   int next = P.nc;
@@ -1987,29 +2062,36 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
   // 1. edge traces
   std::vector<std::vector<double>> ev(nE);
   std::vector<int> ek(nE, 0);
+  LoopErrors errs8;
 #pragma omp parallel for schedule(dynamic, 64)
   for (int E = 0; E < nE; E++) {
-    std::vector<double> M, buf, mt;
-    const int* S = T.cons[1].row(E);
-    const int nS = T.cons[1].len(E);
-    if (nS < 2) continue;
-    assemble_mass(L, T, 1, 1, E, S, nS, M, buf);
-    std::vector<double> pv(nS), Mp(nS, 0.0);
-    for (int a = 0; a < nS; a++) pv[a] = T.phi[1][T.cons[1].rp[E] + a] / (double)nS;
-    double pMp = 0;
-    for (int a = 0; a < nS; a++) {
-      for (int b = 0; b < nS; b++) Mp[a] += M[(size_t)a * nS + b] * pv[b];
-      pMp += pv[a] * Mp[a];
+    if (errs8.failed) continue;
+    try {
+      std::vector<double> M, buf, mt;
+      const int* S = T.cons[1].row(E);
+      const int nS = T.cons[1].len(E);
+      if (nS < 2) continue;
+      assemble_mass(L, T, 1, 1, E, S, nS, M, buf);
+      std::vector<double> pv(nS), Mp(nS, 0.0);
+      for (int a = 0; a < nS; a++) pv[a] = T.phi[1][T.cons[1].rp[E] + a] / (double)nS;
+      double pMp = 0;
+      for (int a = 0; a < nS; a++) {
+        for (int b = 0; b < nS; b++) Mp[a] += M[(size_t)a * nS + b] * pv[b];
+        pMp += pv[a] * Mp[a];
+      }
+      const double tau = mass_targets(M, S, nS, tgt, mt);
+      std::vector<double> phi((size_t)nS * nt);
+      for (int c = 0; c < nt; c++) {
+        double pMt = 0;
+        for (int a = 0; a < nS; a++) pMt += Mp[a] * tgt[c][S[a]];
+        for (int a = 0; a < nS; a++) phi[(size_t)a * nt + c] = tgt[c][S[a]] - pv[a] * (pMt / pMp);
+      }
+      ek[E] = filter_targets(nS, nt, phi, [&](int a, int b) { return M[(size_t)a * nS + b]; }, tau, ev[E]);
+    } catch (const std::exception& e) {
+      errs8.record(e);
     }
-    const double tau = mass_targets(M, S, nS, tgt, mt);
-    std::vector<double> phi((size_t)nS * nt);
-    for (int c = 0; c < nt; c++) {
-      double pMt = 0;
-      for (int a = 0; a < nS; a++) pMt += Mp[a] * tgt[c][S[a]];
-      for (int a = 0; a < nS; a++) phi[(size_t)a * nt + c] = tgt[c][S[a]] - pv[a] * (pMt / pMp);
-    }
-    ek[E] = filter_targets(nS, nt, phi, [&](int a, int b) { return M[(size_t)a * nS + b]; }, tau, ev[E]);
   }
+  errs8.rethrow();
   std::vector<int> efirst(nE), ffirst(nF), cfirst(nX);
   int next = P.nc;
   for (int E = 0; E < nE; E++) efirst[E] = next, next += ek[E];
@@ -2017,169 +2099,190 @@ void add_curl_bubbles(const Level& L, const Level& C, const Transfer& T, DCsr& P
   std::vector<std::vector<double>> fxv(nF), fv(nF), fcv(nF), ff(nF);
   std::vector<std::vector<int>> fxcol(nF), frows(nF);
   std::vector<int> fk(nF, 0), fck(nF, 0);
+  LoopErrors errs9;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int F = 0; F < nF; F++) {
-    fv[F] = grad_bubbles(L, T, 2, F, tgt, frows[F], fk[F]);
-    const int* S = T.fclo[2][1].row(F);
-    const int nS = T.fclo[2][1].len(F);
-    const uint8_t* in = T.fint[2][1].data() + T.fclo[2][1].rp[F];
-    std::vector<int> Bpos;
-    for (int i = 0; i < nS; i++)
-      if (!in[i]) Bpos.push_back(i);
-    const size_t nIF = (size_t)nS - Bpos.size();
-    if (dtg && nIF > 0) {  // eq. 3.7 on F
-      std::vector<double> Mf, buf, mt;
-      const int* SF = T.cons[2].row(F);
-      const int nSF = T.cons[2].len(F);
-      const int ntd = (int)dtg->size();
-      assemble_mass(L, T, 2, 2, F, SF, nSF, Mf, buf);
-      std::vector<double> pv(nSF), Mp(nSF, 0.0);
-      for (int a = 0; a < nSF; a++) pv[a] = T.phi[2][T.cons[2].rp[F] + a] / (double)nSF;
-      double pMp = 0;
-      for (int a = 0; a < nSF; a++) {
-        for (int b = 0; b < nSF; b++) Mp[a] += Mf[(size_t)a * nSF + b] * pv[b];
-        pMp += pv[a] * Mp[a];
-      }
-      const double tau = mass_targets(Mf, SF, nSF, *dtg, mt);
-      std::vector<double> phi((size_t)nSF * ntd);
-      for (int c = 0; c < ntd; c++) {
-        double pMt = 0;
-        for (int a = 0; a < nSF; a++) pMt += Mp[a] * (*dtg)[c][SF[a]];
-        for (int a = 0; a < nSF; a++) phi[(size_t)a * ntd + c] = (*dtg)[c][SF[a]] - pv[a] * (pMt / pMp);
-      }
-      fck[F] = filter_targets(nSF, ntd, phi, [&](int a, int b) { return Mf[(size_t)a * nSF + b]; }, tau, ff[F]);
-      if (fck[F] > 0) {
-        std::vector<double> rhs((size_t)nSF * fck[F]);
-        for (int i = 0; i < fck[F]; i++)
-          for (int a = 0; a < nSF; a++) rhs[(size_t)a * fck[F] + i] = ff[F][(size_t)i * nSF + a];
-        const std::vector<double> zeroB(Bpos.size() * (size_t)fck[F], 0.0);
-        fcv[F] = solve_eq36(L, T, 1, F, zeroB, fck[F], nullptr, &rhs);
-        fcv[F].resize(nIF * fck[F]);  // F's interior edges x fck
-      }
-    }
-    const int* Ef = C.clo[2][1].row(F);
-    const int nEf = C.clo[2][1].len(F);
-    int nJ = 0;
-    for (int q = 0; q < nEf; q++) nJ += ek[Ef[q]];
-    if (nJ == 0 || nIF == 0) continue;
-    std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
-    int j0 = 0;
-    for (int q = 0; q < nEf; q++) {
-      const int E = Ef[q];
-      const int nSE = T.cons[1].len(E);
-      const int* SE = T.cons[1].row(E);
-      for (int i = 0; i < ek[E]; i++) {
-        fxcol[F].push_back(efirst[E] + i);
-        for (int a = 0; a < nSE; a++) {
-          const int bi = pos_in(Bpos.data(), (int)Bpos.size(), pos_in(S, nS, SE[a]));
-          phiB[(size_t)bi * nJ + j0 + i] = ev[E][(size_t)i * nSE + a];
+    if (errs9.failed) continue;
+    try {
+      fv[F] = grad_bubbles(L, T, 2, F, tgt, frows[F], fk[F]);
+      const int* S = T.fclo[2][1].row(F);
+      const int nS = T.fclo[2][1].len(F);
+      const uint8_t* in = T.fint[2][1].data() + T.fclo[2][1].rp[F];
+      std::vector<int> Bpos;
+      for (int i = 0; i < nS; i++)
+        if (!in[i]) Bpos.push_back(i);
+      const size_t nIF = (size_t)nS - Bpos.size();
+      if (dtg && nIF > 0) {  // eq. 3.7 on F
+        std::vector<double> Mf, buf, mt;
+        const int* SF = T.cons[2].row(F);
+        const int nSF = T.cons[2].len(F);
+        const int ntd = (int)dtg->size();
+        assemble_mass(L, T, 2, 2, F, SF, nSF, Mf, buf);
+        std::vector<double> pv(nSF), Mp(nSF, 0.0);
+        for (int a = 0; a < nSF; a++) pv[a] = T.phi[2][T.cons[2].rp[F] + a] / (double)nSF;
+        double pMp = 0;
+        for (int a = 0; a < nSF; a++) {
+          for (int b = 0; b < nSF; b++) Mp[a] += Mf[(size_t)a * nSF + b] * pv[b];
+          pMp += pv[a] * Mp[a];
+        }
+        const double tau = mass_targets(Mf, SF, nSF, *dtg, mt);
+        std::vector<double> phi((size_t)nSF * ntd);
+        for (int c = 0; c < ntd; c++) {
+          double pMt = 0;
+          for (int a = 0; a < nSF; a++) pMt += Mp[a] * (*dtg)[c][SF[a]];
+          for (int a = 0; a < nSF; a++) phi[(size_t)a * ntd + c] = (*dtg)[c][SF[a]] - pv[a] * (pMt / pMp);
+        }
+        fck[F] = filter_targets(nSF, ntd, phi, [&](int a, int b) { return Mf[(size_t)a * nSF + b]; }, tau, ff[F]);
+        if (fck[F] > 0) {
+          std::vector<double> rhs((size_t)nSF * fck[F]);
+          for (int i = 0; i < fck[F]; i++)
+            for (int a = 0; a < nSF; a++) rhs[(size_t)a * fck[F] + i] = ff[F][(size_t)i * nSF + a];
+          const std::vector<double> zeroB(Bpos.size() * (size_t)fck[F], 0.0);
+          fcv[F] = solve_eq36(L, T, 1, F, zeroB, fck[F], nullptr, &rhs);
+          fcv[F].resize(nIF * fck[F]);  // F's interior edges x fck
         }
       }
-      j0 += ek[E];
+      const int* Ef = C.clo[2][1].row(F);
+      const int nEf = C.clo[2][1].len(F);
+      int nJ = 0;
+      for (int q = 0; q < nEf; q++) nJ += ek[Ef[q]];
+      if (nJ == 0 || nIF == 0) continue;
+      std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
+      int j0 = 0;
+      for (int q = 0; q < nEf; q++) {
+        const int E = Ef[q];
+        const int nSE = T.cons[1].len(E);
+        const int* SE = T.cons[1].row(E);
+        for (int i = 0; i < ek[E]; i++) {
+          fxcol[F].push_back(efirst[E] + i);
+          for (int a = 0; a < nSE; a++) {
+            const int bi = pos_in(Bpos.data(), (int)Bpos.size(), pos_in(S, nS, SE[a]));
+            phiB[(size_t)bi * nJ + j0 + i] = ev[E][(size_t)i * nSE + a];
+          }
+        }
+        j0 += ek[E];
+      }
+      fxv[F] = solve_eq36(L, T, 1, F, phiB, nJ, nullptr);
+      fxv[F].resize(nIF * nJ);  // F's interior edges x nJ
+    } catch (const std::exception& e) {
+      errs9.record(e);
     }
-    fxv[F] = solve_eq36(L, T, 1, F, phiB, nJ, nullptr);
-    fxv[F].resize(nIF * nJ);  // F's interior edges x nJ
   }
+  errs9.rethrow();
   for (int F = 0; F < nF; F++) ffirst[F] = next, next += fk[F] + fck[F];
   // 5. cell gradient bubbles; the face space's div-free bubbles of every cell (eq. 3.9)
   std::vector<std::vector<double>> cv(nX), bv(nX);
   std::vector<std::vector<int>> crows(nX), brows(nX);
   std::vector<int> ck(nX, 0), bk(nX, 0);
+  LoopErrors errs10;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int X = 0; X < nX; X++) {
-    cv[X] = grad_bubbles(L, T, 3, X, tgt, crows[X], ck[X]);
-    if (dtg) bv[X] = div_bubbles_cell(L, T, X, *dtg, brows[X], bk[X], nullptr);
+    if (errs10.failed) continue;
+    try {
+      cv[X] = grad_bubbles(L, T, 3, X, tgt, crows[X], ck[X]);
+      if (dtg) bv[X] = div_bubbles_cell(L, T, X, *dtg, brows[X], bk[X], nullptr);
+    } catch (const std::exception& e) {
+      errs10.record(e);
+    }
   }
+  errs10.rethrow();
   for (int X = 0; X < nX; X++) cfirst[X] = next, next += bk[X] + ck[X];
   // 4. the edge and face functions extended into every cell, and eq. 3.9's bubbles
   std::vector<std::vector<double>> xv(nX);
   std::vector<std::vector<int>> xcol(nX), xrows(nX);
+  LoopErrors errs11;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int X = 0; X < nX; X++) {
-    const int* S = T.fclo[3][1].row(X);
-    const int nS = T.fclo[3][1].len(X);
-    const uint8_t* in = T.fint[3][1].data() + T.fclo[3][1].rp[X];
-    std::vector<int> Bpos;
-    for (int i = 0; i < nS; i++)
-      if (in[i]) xrows[X].push_back(S[i]);
-      else Bpos.push_back(i);
-    if (xrows[X].empty()) continue;
-    const int* Ex = C.clo[3][1].row(X);
-    const int nEx = C.clo[3][1].len(X);
-    const int* Fx = C.clo[3][2].row(X);
-    const int nFx = C.clo[3][2].len(X);
-    for (int q = 0; q < nEx; q++)
-      for (int i = 0; i < ek[Ex[q]]; i++) xcol[X].push_back(efirst[Ex[q]] + i);
-    for (int q = 0; q < nFx; q++)
-      for (int i = 0; i < fk[Fx[q]] + fck[Fx[q]]; i++) xcol[X].push_back(ffirst[Fx[q]] + i);
-    for (int i = 0; i < bk[X]; i++) xcol[X].push_back(cfirst[X] + i);
-    const int nJ = (int)xcol[X].size();  // ascending: edges', faces', then X's own columns
-    if (nJ == 0) continue;
-    auto jof = [&](int col) { return pos_in(xcol[X].data(), nJ, col); };
-    std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
-    for (size_t b = 0; b < Bpos.size(); b++) {
-      const int y = S[Bpos[b]];
-      const int od = T.own_dim[1][y], oid = T.own_id[1][y];
-      if (od == 1) {  // on a coarse edge: that edge's trace functions
-        const int E = oid;
-        const int a = pos_in(T.cons[1].row(E), T.cons[1].len(E), y);
-        for (int i = 0; i < ek[E]; i++)
-          phiB[b * nJ + jof(efirst[E] + i)] = ev[E][(size_t)i * T.cons[1].len(E) + a];
-      } else if (od == 2) {  // interior to a coarse face: its bubbles and the edge functions' extensions
-        const int F = oid;
-        const int nIF = (int)frows[F].size();
-        const int a = pos_in(frows[F].data(), nIF, y);
-        for (int i = 0; i < fk[F]; i++) phiB[b * nJ + jof(ffirst[F] + i)] = fv[F][(size_t)i * nIF + a];
-        for (int i = 0; i < fck[F]; i++)
-          phiB[b * nJ + jof(ffirst[F] + fk[F] + i)] = fcv[F][(size_t)a * fck[F] + i];
-        const int nJF = (int)fxcol[F].size();
-        for (int jj = 0; jj < nJF; jj++) phiB[b * nJ + jof(fxcol[F][jj])] = fxv[F][(size_t)a * nJF + jj];
+    if (errs11.failed) continue;
+    try {
+      const int* S = T.fclo[3][1].row(X);
+      const int nS = T.fclo[3][1].len(X);
+      const uint8_t* in = T.fint[3][1].data() + T.fclo[3][1].rp[X];
+      std::vector<int> Bpos;
+      for (int i = 0; i < nS; i++)
+        if (in[i]) xrows[X].push_back(S[i]);
+        else Bpos.push_back(i);
+      if (xrows[X].empty()) continue;
+      const int* Ex = C.clo[3][1].row(X);
+      const int nEx = C.clo[3][1].len(X);
+      const int* Fx = C.clo[3][2].row(X);
+      const int nFx = C.clo[3][2].len(X);
+      for (int q = 0; q < nEx; q++)
+        for (int i = 0; i < ek[Ex[q]]; i++) xcol[X].push_back(efirst[Ex[q]] + i);
+      for (int q = 0; q < nFx; q++)
+        for (int i = 0; i < fk[Fx[q]] + fck[Fx[q]]; i++) xcol[X].push_back(ffirst[Fx[q]] + i);
+      for (int i = 0; i < bk[X]; i++) xcol[X].push_back(cfirst[X] + i);
+      const int nJ = (int)xcol[X].size();  // ascending: edges', faces', then X's own columns
+      if (nJ == 0) continue;
+      auto jof = [&](int col) { return pos_in(xcol[X].data(), nJ, col); };
+      std::vector<double> phiB(Bpos.size() * (size_t)nJ, 0.0);
+      for (size_t b = 0; b < Bpos.size(); b++) {
+        const int y = S[Bpos[b]];
+        const int od = T.own_dim[1][y], oid = T.own_id[1][y];
+        if (od == 1) {  // on a coarse edge: that edge's trace functions
+          const int E = oid;
+          const int a = pos_in(T.cons[1].row(E), T.cons[1].len(E), y);
+          for (int i = 0; i < ek[E]; i++)
+            phiB[b * nJ + jof(efirst[E] + i)] = ev[E][(size_t)i * T.cons[1].len(E) + a];
+        } else if (od == 2) {  // interior to a coarse face: its bubbles and the edge functions' extensions
+          const int F = oid;
+          const int nIF = (int)frows[F].size();
+          const int a = pos_in(frows[F].data(), nIF, y);
+          for (int i = 0; i < fk[F]; i++) phiB[b * nJ + jof(ffirst[F] + i)] = fv[F][(size_t)i * nIF + a];
+          for (int i = 0; i < fck[F]; i++)
+            phiB[b * nJ + jof(ffirst[F] + fk[F] + i)] = fcv[F][(size_t)a * fck[F] + i];
+          const int nJF = (int)fxcol[F].size();
+          for (int jj = 0; jj < nJF; jj++) phiB[b * nJ + jof(fxcol[F][jj])] = fxv[F][(size_t)a * nJF + jj];
+        }
       }
-    }
-    std::vector<double> sx;  // eq. 3.8 targets on X's faces (closure order); zero without dtg
-    if (dtg) {
-      const int* S1 = T.fclo[3][2].row(X);
-      const int n1 = T.fclo[3][2].len(X);
-      const uint8_t* in1 = T.fint[3][2].data() + T.fclo[3][2].rp[X];
-      std::vector<int> B1, I1;
-      for (int i = 0; i < n1; i++) (in1[i] ? I1 : B1).push_back(i);
-      sx.assign((size_t)n1 * nJ, 0.0);
-      // a face cross-space bubble's curl: its trace f on F, extended into X by eq. 3.6
-      int nd = 0;
-      for (int q = 0; q < nFx; q++) nd += fck[Fx[q]];
-      if (nd > 0) {
-        std::vector<double> pB(B1.size() * (size_t)nd, 0.0);
-        std::vector<int> dcol;
-        for (int q = 0; q < nFx; q++) {
-          const int F = Fx[q];
-          const int* SF = T.cons[2].row(F);
-          const int nSF = T.cons[2].len(F);
-          for (int i = 0; i < fck[F]; i++) {
-            const int jd = (int)dcol.size();
-            dcol.push_back(ffirst[F] + fk[F] + i);
-            for (int a = 0; a < nSF; a++) {
-              const int bi = pos_in(B1.data(), (int)B1.size(), pos_in(S1, n1, SF[a]));
-              pB[(size_t)bi * nd + jd] = ff[F][(size_t)i * nSF + a];
+      std::vector<double> sx;  // eq. 3.8 targets on X's faces (closure order); zero without dtg
+      if (dtg) {
+        const int* S1 = T.fclo[3][2].row(X);
+        const int n1 = T.fclo[3][2].len(X);
+        const uint8_t* in1 = T.fint[3][2].data() + T.fclo[3][2].rp[X];
+        std::vector<int> B1, I1;
+        for (int i = 0; i < n1; i++) (in1[i] ? I1 : B1).push_back(i);
+        sx.assign((size_t)n1 * nJ, 0.0);
+        // a face cross-space bubble's curl: its trace f on F, extended into X by eq. 3.6
+        int nd = 0;
+        for (int q = 0; q < nFx; q++) nd += fck[Fx[q]];
+        if (nd > 0) {
+          std::vector<double> pB(B1.size() * (size_t)nd, 0.0);
+          std::vector<int> dcol;
+          for (int q = 0; q < nFx; q++) {
+            const int F = Fx[q];
+            const int* SF = T.cons[2].row(F);
+            const int nSF = T.cons[2].len(F);
+            for (int i = 0; i < fck[F]; i++) {
+              const int jd = (int)dcol.size();
+              dcol.push_back(ffirst[F] + fk[F] + i);
+              for (int a = 0; a < nSF; a++) {
+                const int bi = pos_in(B1.data(), (int)B1.size(), pos_in(S1, n1, SF[a]));
+                pB[(size_t)bi * nd + jd] = ff[F][(size_t)i * nSF + a];
+              }
             }
           }
+          const std::vector<double> ext = solve_eq36(L, T, 2, X, pB, nd, nullptr);
+          for (int jd = 0; jd < nd; jd++) {
+            const int j = jof(dcol[jd]);
+            for (size_t bi = 0; bi < B1.size(); bi++) sx[(size_t)B1[bi] * nJ + j] = pB[bi * nd + jd];
+            for (size_t a = 0; a < I1.size(); a++) sx[(size_t)I1[a] * nJ + j] = ext[a * nd + jd];
+          }
         }
-        const std::vector<double> ext = solve_eq36(L, T, 2, X, pB, nd, nullptr);
-        for (int jd = 0; jd < nd; jd++) {
-          const int j = jof(dcol[jd]);
-          for (size_t bi = 0; bi < B1.size(); bi++) sx[(size_t)B1[bi] * nJ + j] = pB[bi * nd + jd];
-          for (size_t a = 0; a < I1.size(); a++) sx[(size_t)I1[a] * nJ + j] = ext[a * nd + jd];
+        // eq. 3.9: curl = X's div-free face-space bubbles (zero on X's boundary faces)
+        const int nIb = (int)brows[X].size();
+        for (int i = 0; i < bk[X]; i++) {
+          const int j = jof(cfirst[X] + i);
+          for (int a = 0; a < nIb; a++) sx[(size_t)I1[a] * nJ + j] = bv[X][(size_t)i * nIb + a];
         }
       }
-      // eq. 3.9: curl = X's div-free face-space bubbles (zero on X's boundary faces)
-      const int nIb = (int)brows[X].size();
-      for (int i = 0; i < bk[X]; i++) {
-        const int j = jof(cfirst[X] + i);
-        for (int a = 0; a < nIb; a++) sx[(size_t)I1[a] * nJ + j] = bv[X][(size_t)i * nIb + a];
-      }
+      xv[X] = solve_eq38(L, T, 1, 3, X, dtg ? &sx : nullptr, phiB, nJ, nullptr);
+      xv[X].resize(xrows[X].size() * (size_t)nJ);  // the interior values
+    } catch (const std::exception& e) {
+      errs11.record(e);
     }
-    xv[X] = solve_eq38(L, T, 1, 3, X, dtg ? &sx : nullptr, phiB, nJ, nullptr);
-    xv[X].resize(xrows[X].size() * (size_t)nJ);  // the interior values
   }
+  errs11.rethrow();
   std::vector<std::vector<std::pair<int, double>>> extra(P.nr);
   auto put = [&](int row, int col, double v) {
     if (v != 0.0) extra[row].emplace_back(col, v);
